@@ -1,0 +1,239 @@
+/*
+ * radgeb.h -- C ABI of the GB300 (sm_103a) radiative hot path:
+ *   Monte Carlo ray tracing (MCRT) of view factors  ->  closure / reciprocity
+ *   enforcement  ->  multi-node aggregation  ->  Gebhart radiative exchange
+ *   factors (REFs)  ->  steady radiative balance, with adjoint gradients.
+ *
+ * Thesis: "Novel Numerical Methods for Accurate Space Thermal Analysis"
+ * (arXiv:2511.04277). Section, equation and appendix numbers below are the
+ * thesis's.
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * - Status: every call returns an rg_status; nothing throws or aborts across the
+ *   ABI. rg_last_error(ctx) gives a human-readable message for the last failure
+ *   on that context (never NULL).
+ * - Ownership: the caller owns every buffer it passes (host or device, as each
+ *   argument says). The library owns only the opaque rg_ctx and rg_mesh objects
+ *   and the device workspace held by a context.
+ * - Layout: matrices are dense, row-major, fp64 unless stated. A view-factor or
+ *   REF matrix of N faces is N x (N+1): column N is the environment (deep space),
+ *   Sec. 2.4.12. Batched data of S sets is set-major ([S][...]).
+ * - Streams: `stream` is a cudaStream_t (NULL = the legacy default stream). Work
+ *   is enqueued on it; calls that return a host-side scalar (iteration counts,
+ *   residuals) synchronise that stream before returning.
+ * - Devices: a context is bound to one device; device pointers must belong to it.
+ * - Errors detected on the device (traversal stack overflow, non-finite values,
+ *   non-convergence) are reported through the status of the call that detected
+ *   them; the context stays usable.
+ * - No call traps, asserts or waits without a bound on the device.
+ */
+#ifndef RADGEB_H
+#define RADGEB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  RG_OK = 0,
+  RG_ERR_ARG = -1,            /* invalid argument (NULL pointer, size, layout)       */
+  RG_ERR_CUDA = -2,           /* a CUDA runtime/driver call failed                   */
+  RG_ERR_OOM = -3,            /* host or device allocation failed                    */
+  RG_ERR_NOT_CONVERGED = -4,  /* an iteration hit its limit; outputs hold the last iterate */
+  RG_ERR_STACK = -5,          /* BVH deeper than the traversal stack                  */
+  RG_ERR_NUMERIC = -6,        /* non-finite value, zero pivot or singular system      */
+  RG_ERR_UNSUPPORTED = -7     /* device is not sm_103 or size exceeds a stated limit   */
+} rg_status;
+
+typedef struct rg_ctx rg_ctx;
+typedef struct rg_mesh rg_mesh;
+
+/* Precision of the dense solves (Gebhart, adjoints, radiative balance). The
+ * factorisation and triangular solves run on tcgen05 tensor cores in 16-bit
+ * floating point with fp32 accumulation; iterative refinement with an fp64-
+ * accurate residual brings the result to the requested tolerance. */
+typedef enum {
+  RG_PREC_BF16_IR = 1,
+  RG_PREC_FP16_IR = 2
+} rg_precision;
+
+/* ---------------------------------------------------------------- context */
+
+/* Create a context on CUDA device `device` (must be sm_103). *ctx_out receives a
+ * library-owned handle; free it with rg_destroy. */
+rg_status rg_create(rg_ctx** ctx_out, int device);
+void rg_destroy(rg_ctx* ctx);
+const char* rg_last_error(const rg_ctx* ctx);
+const char* rg_version(void);
+
+/* ---------------------------------------------------------------- mesh (P1) */
+
+/* Upload a triangle mesh and build its bounding-volume hierarchy (host binned
+ * SAH, leaves of at most 4 triangles, boxes padded so that the traversal never
+ * rejects a triangle the brute-force test would accept).
+ *   verts_h     host float32 [nv][3]       vertex positions
+ *   tris_h      host int32   [nt][3]       vertex indices; the winding (v1-v0) x
+ *                                          (v2-v0) gives the emitting side
+ *   tri_face_h  host int32   [nt]          face (row of F) of every triangle;
+ *                                          the triangles of a face must be coplanar
+ *   n_faces     number of faces N (every face needs >= 1 triangle of area > 0)
+ *   use_bvh     1 = traverse the BVH, 0 = test every triangle (tiny meshes),
+ *               -1 = choose (brute force when nt <= 64)
+ * The host arrays are copied; they may be freed after the call.
+ * Errors: RG_ERR_ARG (bad index, empty or degenerate face), RG_ERR_STACK (BVH
+ * deeper than the 64-entry traversal stack), RG_ERR_OOM, RG_ERR_CUDA. */
+rg_status rg_mesh_create(rg_ctx* ctx, const float* verts_h, int64_t nv, const int32_t* tris_h,
+                         int64_t nt, const int32_t* tri_face_h, int32_t n_faces, int32_t use_bvh,
+                         rg_mesh** mesh_out);
+rg_status rg_mesh_destroy(rg_mesh* mesh);
+
+typedef struct {
+  int32_t n_faces;
+  int64_t n_tris;
+  int32_t bvh_nodes;   /* 0 when brute force is used */
+  int32_t bvh_depth;
+  float lift;          /* ray origins sit this far off their face: 1e-6 x bounding-box diagonal */
+} rg_mesh_info;
+rg_status rg_mesh_get_info(const rg_mesh* mesh, rg_mesh_info* info_out);
+
+/* Face areas A_i (fp64 sum of the triangle areas), written to host double[N]. */
+rg_status rg_face_areas(const rg_mesh* mesh, double* areas_out_h);
+
+/* ---------------------------------------------------------------- MCRT (P2) */
+
+/* Hit counts N_ij of the MCRT estimator F_ij = N_ij / N_i (Sec. 3.5.1, Eq. 3.15).
+ *   rays_per_face_h  host int64 [N]: rays emitted from face i (N_i >= 0)
+ *   seed             Philox4x32-10 key; ray r of face i uses the counter
+ *                    (ray_offset + r, i, attempt), so disjoint ray ranges of
+ *                    separate calls are independent and their counts add up
+ *   fma_free         1: every float operation of sampling and intersection is
+ *                    individually rounded (bit-exact with the reference ray
+ *                    definition); 0: the compiler may fuse multiply-adds
+ *   counts_d         device int64 [N][N+1], ACCUMULATED into (zero it first);
+ *                    column N counts rays that escape to the environment
+ * Emission is diffuse (cosine-weighted about the face normal, Sec. 2.4.12) from
+ * points uniform over the face area (Sec. 5.2.1), lifted off the face by `lift`
+ * along its normal. The closest hit with t > 0 (smallest t, then smallest
+ * triangle index) receives the ray; the source triangle is ignored.
+ * Limit: N + 1 <= 49152 (one shared-memory tally row per block).
+ * Errors: RG_ERR_ARG, RG_ERR_STACK, RG_ERR_CUDA, RG_ERR_UNSUPPORTED. */
+rg_status rg_trace(rg_ctx* ctx, const rg_mesh* mesh, const int64_t* rays_per_face_h, uint64_t seed,
+                   uint64_t ray_offset, int32_t fma_free, int64_t* counts_d, void* stream);
+
+/* F_ij = N_ij / N_i (Eq. 3.15) for N x (N+1) counts.
+ *   counts_d  device int64 [n][n+1];  rays_d device int64 [n] (N_i > 0)
+ *   F_d       device fp64 [n][n+1] (output) */
+rg_status rg_counts_to_F(rg_ctx* ctx, int32_t n, const int64_t* counts_d, const int64_t* rays_d,
+                         double* F_d, void* stream);
+
+/* ---------------------------------------------------------------- enforcement (P3) */
+
+/* Iterative closure + reciprocity enforcer for open systems (Sec. 3.5.5), in place.
+ * With eta_ij = Omega_i F_ij (Eq. 3.18) each iteration
+ *   (1) averages eta_ij and eta_ji on the N x N block (Eq. 3.20, kappa = 1/2), the
+ *       environment column carried over from the previous iterate, then
+ *   (2) enforces closure by open-system least squares with w = eta (Eq. 3.39-3.40),
+ *       i.e. scales row i to sum Omega_i.
+ * It stops after the first iteration whose reciprocity defect of the previous
+ * iterate and closure defect after step (1) are both <= tol * max_i Omega_i.
+ *   omega_d   device fp64 [n]: Omega_i (A_i for view factors, eps_i A_i for REFs)
+ *   F_d       device fp64 [n][n+1], in: F, out: enforced F
+ *   iters_out_h  host int32 (may be NULL): iterations performed
+ * Rows with a zero sum are left unchanged. Errors: RG_ERR_NOT_CONVERGED (after
+ * maxit iterations; F_d holds the last iterate), RG_ERR_NUMERIC, RG_ERR_ARG. */
+rg_status rg_enforce_iterative(rg_ctx* ctx, int32_t n, const double* omega_d, double* F_d, double tol,
+                               int32_t maxit, int32_t* iters_out_h, void* stream);
+
+/* Least-squares optimum for open systems (Sec. 3.5.5, Eq. 3.41-3.52) with
+ * non-negativity rectification (App. A.1) and small-positive-value avoidance
+ * (App. A.2), in place. The unknowns are the entries of F; the restrictions are
+ * sum_j F_ij = 1 and Omega_i F_ij - Omega_j F_ji = 0 (i < j); the result is the
+ * orthogonal projection of the active entries of F onto them.
+ *   spva = 1: MCRT zeros stay 0 and are not unknowns; restrictions left without
+ *             unknowns are dropped (App. A.2).
+ *   nnr  = 1: negative results are set to 0, removed from the unknowns and the
+ *             original values of the remaining unknowns projected again, until no
+ *             entry is negative (App. A.1); at most max_passes projections.
+ *   passes_out_h host int32 (may be NULL): projections performed.
+ * Limit: n <= 4096 (one dense n x n Schur complement is factorised).
+ * Errors: RG_ERR_NUMERIC (singular restriction system), RG_ERR_NOT_CONVERGED. */
+rg_status rg_enforce_lsq(rg_ctx* ctx, int32_t n, const double* omega_d, double* F_d, int32_t nnr,
+                         int32_t spva, int32_t max_passes, int32_t* passes_out_h, void* stream);
+
+/* ---------------------------------------------------------------- multi-node (P4) */
+
+/* Group view factors from sub-surface view factors (Eq. 5.6-5.7, 5.28):
+ *   F_group[n][m] = sum_{i in n} sum_{j in m} F_sub[i][j] * S_i / S_n
+ *   F_group[n][G] = sum_{i in n} F_sub[i][n_sub] * S_i / S_n   (environment)
+ * with S_n = sum_{i in n} S_i. With groups = the faces of one node (equal-area
+ * sides A and B) this is the node relation C_n F_ij = sum_{X,Y} F^{X->Y} of
+ * Eq. 5.17; with singleton groups it is the identity.
+ *   F_sub_d       device fp64 [n_sub][n_sub+1]
+ *   sub_area_d    device fp64 [n_sub]
+ *   sub_group_d   device int32 [n_sub], values in [0, n_group)
+ *   F_group_d     device fp64 [n_group][n_group+1] (output)
+ *   group_area_d  device fp64 [n_group] (output, may be NULL) */
+rg_status rg_aggregate(rg_ctx* ctx, int32_t n_sub, const double* F_sub_d, const double* sub_area_d,
+                       const int32_t* sub_group_d, int32_t n_group, double* F_group_d,
+                       double* group_area_d, void* stream);
+
+/* ---------------------------------------------------------------- Gebhart REFs (P5) */
+
+/* Radiative exchange factors of an open system (Eq. 4.5, App. B.2, Eq. B.6-B.11):
+ *   K B = E,  K = I - F_NN diag(rho),  E = [F_NN diag(eps) | F_inf]
+ * for n_sets independent (eps, rho) sets sharing F.
+ *   F_d      device fp64 [n][n+1]
+ *   eps_d    device fp64 [n_sets][n];  rho_d device fp64 [n_sets][n], 0 <= rho < 1
+ *   B_d      device fp64 [n_sets][n][n+1] (output)
+ *   tol      refinement stops when max_ij |R_ij| <= tol * max_ij |B_ij| for the
+ *            residual R = E - K B of every set (tol >= 1e-13)
+ *   max_sweeps  refinement sweeps at most (>= 1)
+ *   sweeps_out_h host int32 (may be NULL); resid_out_h host fp64 (may be NULL):
+ *            the final relative residual (max over sets)
+ * K must be strictly diagonally dominant (rows of F_NN sum to <= 1 and rho < 1), which
+ * is what makes the factorisation without pivoting stable.
+ * Limit: n <= 32768. Errors: RG_ERR_NOT_CONVERGED, RG_ERR_NUMERIC, RG_ERR_OOM. */
+rg_status rg_gebhart(rg_ctx* ctx, int32_t n, const double* F_d, int32_t n_sets, const double* eps_d,
+                     const double* rho_d, int32_t precision, double tol, int32_t max_sweeps,
+                     double* B_d, int32_t* sweeps_out_h, double* resid_out_h, void* stream);
+
+/* Adjoint of rg_gebhart: given dB = dL/dB, the gradients of L with respect to eps
+ * and rho. It solves K^T Lambda = dB (a fresh factorisation of K^T, no stored
+ * factors) and forms dL/deps_j = sum_i Lambda_ij F_ij and
+ * dL/drho_k = sum_i F_ik (Lambda B^T)_ik.
+ *   B_d, dB_d  device fp64 [n_sets][n][n+1];  deps_d, drho_d device fp64 [n_sets][n]
+ * Errors as rg_gebhart. */
+rg_status rg_gebhart_adjoint(rg_ctx* ctx, int32_t n, const double* F_d, int32_t n_sets,
+                             const double* eps_d, const double* rho_d, const double* B_d,
+                             const double* dB_d, int32_t precision, double tol, int32_t max_sweeps,
+                             double* deps_d, double* drho_d, void* stream);
+
+/* ---------------------------------------------------------------- radiative balance (P6) */
+
+/* Steady node temperatures of the radiative network (Eq. 3.13, 4.1-4.2):
+ *   sum_j GR_ij (T_i^4 - T_j^4) + GR_i,inf (T_i^4 - T_sink^4) = Q_i,
+ *   GR_ij = sigma eps_i A_i B_ij,
+ * solved in u = T^4 (fp64-accurate refinement) and T = u^(1/4).
+ *   B_d device fp64 [n][n+1]; eps_d, area_d, Q_d device fp64 [n]; T_d output [n]
+ * Errors: RG_ERR_NUMERIC (a node with no path to the environment makes the
+ * system singular), RG_ERR_NOT_CONVERGED. */
+rg_status rg_temperatures(rg_ctx* ctx, int32_t n, const double* B_d, const double* eps_d,
+                          const double* area_d, const double* Q_d, double T_sink, double sigma,
+                          int32_t precision, double tol, double* T_d, void* stream);
+
+/* Adjoint of rg_temperatures: given dT = dL/dT, writes dB = dL/dB (device fp64
+ * [n][n+1]) and the direct part of dL/deps (device fp64 [n]); the part through B
+ * follows from rg_gebhart_adjoint with dB. */
+rg_status rg_temperatures_adjoint(rg_ctx* ctx, int32_t n, const double* B_d, const double* eps_d,
+                                  const double* area_d, double T_sink, double sigma,
+                                  const double* T_d, const double* dT_d, int32_t precision, double tol,
+                                  double* dB_d, double* deps_d, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RADGEB_H */

@@ -18,16 +18,21 @@
  *              seed hi), counter = (ray lo, ray hi, face, attempt).
  *   uniform    u = (x >> 8) * 2^-24.
  *   triangle   first k with x0 < thr[k] (uint32 area CDF of the face), else last.
- *   point      (u,v) = draws 1,2; folded to (1-u,1-v) if u+v > 1;
- *              p = (v0 + u*e1) + v*e2.
+ *   point      (u,v) = draws 1,2; folded to (1-u,1-v) if u+v > 1; pulled toward
+ *              the centroid, u' = u*k + w with k = 1 - 2^-20 and w = float(2^-20/3),
+ *              so that no origin lies on an edge; p = (v0 + u'*e1) + v'*e2, then
+ *              lifted off the face: o = p + lift*n.
  *   direction  Malley's method: attempt a = 1..64 gives two candidates
  *              (x,y) = (2u-1, 2v-1) from draws (0,1) and (2,3); the first with
  *              x*x+y*y < 1 is taken; z = sqrt(1 - (x*x+y*y)); none -> (0,0,1).
  *              d = (x*t + y*b) + z*n in the face frame (t, b, n).
  *   hit        Moller-Trumbore, every operation rounded to float (no FMA),
- *              u,v >= -eb, u+v <= 1+eb with eb = 2^-20, t > t_min, the source
+ *              u,v >= -eb, u+v <= 1+eb with eb = 2^-20, t > 0, the source
  *              triangle skipped; closest = lexicographically smallest (t, tri).
- *   t_min      1e-6 * length of the diagonal of the vertex bounding box.
+ *   lift       1e-6 * length of the diagonal of the vertex bounding box. The
+ *              lifted origin puts the source plane strictly behind the ray, so
+ *              hits on an adjacent face at t ~ 1e-7 (rays born next to an edge of
+ *              an enclosure) are kept and a closed enclosure loses no ray.
  * Face frame: from the face's lowest-index triangle (v0,v1,v2):
  *   n = c/|c| with c = cross(v1-v0, v2-v0); t = e1/|e1|; b = cross(n, t).
  *
@@ -123,7 +128,7 @@ typedef struct {
   uint32_t* face_thr;    /* nt, aligned with face_tris */
   v3* fn; v3* ft; v3* fb;
   double* face_area;
-  float t_min;
+  float lift;
 } omesh;
 
 static double tri_area_d(const float* verts, const int32_t* t) {
@@ -196,7 +201,7 @@ static int omesh_init(omesh* m, const float* verts, int64_t nv, const int32_t* t
     v3 t = vnormalize(m->te1[k0]);
     m->fn[f] = n; m->ft[f] = t; m->fb[f] = vcross(n, t);
   }
-  /* t_min from the bounding box diagonal */
+  /* origin lift from the bounding box diagonal */
   double lo[3] = {verts[0], verts[1], verts[2]}, hi[3] = {verts[0], verts[1], verts[2]};
   for (int64_t i = 0; i < nv; ++i)
     for (int c = 0; c < 3; ++c) {
@@ -205,7 +210,7 @@ static int omesh_init(omesh* m, const float* verts, int64_t nv, const int32_t* t
       if (x > hi[c]) hi[c] = x;
     }
   double dx = hi[0] - lo[0], dy = hi[1] - lo[1], dz = hi[2] - lo[2];
-  m->t_min = (float)(1e-6 * sqrt((dx * dx + dy * dy) + dz * dz));
+  m->lift = (float)(1e-6 * sqrt((dx * dx + dy * dy) + dz * dz));
   return ORC_OK;
 }
 
@@ -224,11 +229,17 @@ static void sample_ray(const omesh* m, uint64_t seed, int32_t f, uint64_t ray, v
   int32_t tri = m->face_tris[q];
   float u = unit_float(x[1]), v = unit_float(x[2]);
   if (u + v > 1.0f) { u = 1.0f - u; v = 1.0f - v; }
+  u = u * 0x1.ffffep-1f + 0x1.555556p-22f;   /* k = 1 - 2^-20, w = float(2^-20 / 3) */
+  v = v * 0x1.ffffep-1f + 0x1.555556p-22f;
   v3 v0 = m->tv0[tri], e1 = m->te1[tri], e2 = m->te2[tri];
   v3 p;
   p.x = v0.x + u * e1.x; p.x = p.x + v * e2.x;
   p.y = v0.y + u * e1.y; p.y = p.y + v * e2.y;
   p.z = v0.z + u * e1.z; p.z = p.z + v * e2.z;
+  v3 nf = m->fn[f];
+  p.x = p.x + m->lift * nf.x;
+  p.y = p.y + m->lift * nf.y;
+  p.z = p.z + m->lift * nf.z;
 
   float dx = 0.0f, dy = 0.0f, s2 = 0.0f;
   int used = 0;
@@ -270,7 +281,7 @@ static int intersect(const omesh* m, int32_t k, v3 o, v3 d, float* t_out) {
   float v = vdot(d, qvec) * inv;
   if (!(v >= eb_lo && u + v <= eb_hi)) return 0;
   float t = vdot(e2, qvec) * inv;
-  if (!(t > m->t_min)) return 0;
+  if (!(t > 0.0f)) return 0;
   *t_out = t;
   return 1;
 }
@@ -350,7 +361,7 @@ static int bvh_build(obvh* b, const omesh* m) {
     }
   }
   /* padding: 1e-4 of the scene diagonal, far above float rounding of the hit point */
-  b->pad = 1e-4 * ((double)m->t_min / 1e-6);
+  b->pad = 1e-4 * ((double)m->lift / 1e-6);
   b->n_nodes = 0;
   bvh_build_rec(b, m, cent, 0, (int32_t)nt);
   free(cent);
@@ -358,8 +369,8 @@ static int bvh_build(obvh* b, const omesh* m) {
 }
 
 /* slab test in double; returns the entry distance or +inf on a miss */
-static double slab(const onode* nd, const double o[3], const double d[3], double t_hi) {
-  double t0 = 0.0, t1 = t_hi;
+static double slab(const onode* nd, const double o[3], const double d[3], double t_lo, double t_hi) {
+  double t0 = t_lo, t1 = t_hi;
   for (int c = 0; c < 3; ++c) {
     if (d[c] == 0.0) {
       if (o[c] < nd->lo[c] || o[c] > nd->hi[c]) return INFINITY;
@@ -385,7 +396,8 @@ static void closest_bvh(const omesh* m, const obvh* b, int32_t src, v3 o, v3 d, 
        current best hit: every point within `pad` of a triangle is inside its
        box, so the box is entered at least `pad` before the triangle's t */
     double limit = isinf(*best_t) ? INFINITY : (double)*best_t;
-    if (slab(nd, od, dd, limit) == INFINITY) continue;
+    /* boxes left behind the origin by more than the padding cannot hold a hit */
+    if (slab(nd, od, dd, -b->pad, limit) == INFINITY) continue;
     if (nd->left < 0) {
       for (int32_t q = nd->first; q < nd->first + nd->count; ++q)
         consider(m, b->order[q], src, o, d, best_t, best_k);
@@ -403,7 +415,7 @@ static void closest_bvh(const omesh* m, const obvh* b, int32_t src, v3 o, v3 d, 
 /* Face areas (double) and frames (float, 9 per face: t, b, n). */
 int oracle_face_geometry(const float* verts, int64_t nv, const int32_t* tris, int64_t nt,
                          const int32_t* tri_face, int32_t n_faces, double* area_out,
-                         float* frame_out, uint32_t* thr_out, float* t_min_out) {
+                         float* frame_out, uint32_t* thr_out, float* lift_out) {
   omesh m;
   int st = omesh_init(&m, verts, nv, tris, nt, tri_face, n_faces);
   if (st) return st;
@@ -417,7 +429,7 @@ int oracle_face_geometry(const float* verts, int64_t nv, const int32_t* tris, in
     }
   }
   if (thr_out) for (int64_t q = 0; q < nt; ++q) thr_out[m.face_tris[q]] = m.face_thr[q];
-  if (t_min_out) *t_min_out = m.t_min;
+  if (lift_out) *lift_out = m.lift;
   omesh_free(&m);
   return ORC_OK;
 }

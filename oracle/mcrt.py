@@ -77,7 +77,7 @@ def philox4x32_10(counter, key):
 
 
 def face_geometry(verts, tris, tri_face, n_faces):
-    """Face areas (fp64), frames (t, b, n as float32[N,3,3]), triangle CDF thresholds, t_min."""
+    """Face areas (fp64), frames (t, b, n as float32[N,3,3]), triangle CDF thresholds, origin lift."""
     lib = _load()
     v, t, f = _mesh_arrays(verts, tris, tri_face)
     area = np.zeros(n_faces, dtype=np.float64)

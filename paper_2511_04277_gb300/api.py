@@ -1,0 +1,251 @@
+"""Python front end of libradgeb: the C calls of include/radgeb.h with torch tensors.
+
+Argument marshalling only: every step runs in the library's CUDA kernels. Device
+buffers are torch tensors on the context's device (torch is used for memory and
+streams); host-side arguments are numpy arrays or Python numbers. Every call is
+enqueued on ``stream`` (default: torch's current stream).
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+import torch
+
+from . import _native
+from ._native import RadgebError
+
+
+def _stream(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _dptr(t: torch.Tensor, dtype, name, numel=None, device=None):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if numel is not None and t.numel() != numel:
+        raise ValueError(f"{name} must have {numel} elements, got {t.numel()}")
+    if device is not None and t.device.index != device:
+        raise ValueError(f"{name} is on cuda:{t.device.index}, the context on cuda:{device}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _hptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+class Context:
+    """A library context bound to one CUDA device (rg_create / rg_destroy)."""
+
+    def __init__(self, device: int = 0):
+        self.lib = _native.load()
+        self.device = int(device)
+        h = ctypes.c_void_p()
+        st = self.lib.rg_create(ctypes.byref(h), self.device)
+        if st != 0:
+            raise RadgebError(st, f"rg_create(device={device}) failed")
+        self.handle = h
+
+    def check(self, st: int, what: str):
+        if st != 0:
+            msg = self.lib.rg_last_error(self.handle)
+            raise RadgebError(st, f"{what}: {msg.decode() if msg else ''}")
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self.lib.rg_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+class Mesh:
+    """A mesh uploaded with its BVH (rg_mesh_create)."""
+
+    def __init__(self, ctx: Context, verts, tris, tri_face, n_faces: int, use_bvh: int = -1):
+        self.ctx = ctx
+        v = np.ascontiguousarray(verts, np.float32)
+        t = np.ascontiguousarray(tris, np.int32)
+        f = np.ascontiguousarray(tri_face, np.int32)
+        h = ctypes.c_void_p()
+        ctx.check(ctx.lib.rg_mesh_create(ctx.handle, _hptr(v), len(v), _hptr(t), len(t), _hptr(f), int(n_faces),
+                                         int(use_bvh), ctypes.byref(h)), "rg_mesh_create")
+        self.handle = h
+        self.n_faces = int(n_faces)
+
+    @classmethod
+    def from_synth(cls, ctx, m, use_bvh=-1):
+        return cls(ctx, m.verts, m.tris, m.tri_face, m.n_faces, use_bvh)
+
+    def info(self) -> dict:
+        mi = _native.MeshInfo()
+        self.ctx.check(self.ctx.lib.rg_mesh_get_info(self.handle, ctypes.byref(mi)), "rg_mesh_get_info")
+        return {k: getattr(mi, k) for k, _ in mi._fields_}
+
+    def face_areas(self) -> np.ndarray:
+        out = np.zeros(self.n_faces, np.float64)
+        self.ctx.check(self.ctx.lib.rg_face_areas(self.handle, _hptr(out)), "rg_face_areas")
+        return out
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self.ctx.lib.rg_mesh_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def trace(ctx: Context, mesh: Mesh, rays_per_face, seed: int, ray_offset: int = 0, fma_free: bool = True,
+          counts: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """MCRT hit counts N_ij, int64 [N, N+1] on the device (rg_trace); accumulates into ``counts``."""
+    N = mesh.n_faces
+    rays = np.ascontiguousarray(rays_per_face, np.int64)
+    if rays.shape != (N,):
+        raise ValueError("rays_per_face must have one entry per face")
+    if counts is None:
+        counts = torch.zeros((N, N + 1), dtype=torch.int64, device=f"cuda:{ctx.device}")
+    ctx.check(ctx.lib.rg_trace(ctx.handle, mesh.handle, _hptr(rays), int(seed) & (2 ** 64 - 1), int(ray_offset),
+                               int(bool(fma_free)), _dptr(counts, torch.int64, "counts", N * (N + 1), ctx.device),
+                               _stream(stream)), "rg_trace")
+    return counts
+
+
+def counts_to_F(ctx: Context, counts: torch.Tensor, rays: torch.Tensor, F: torch.Tensor | None = None,
+                stream=None) -> torch.Tensor:
+    """F_ij = N_ij / N_i (rg_counts_to_F)."""
+    n = counts.shape[0]
+    if F is None:
+        F = torch.empty((n, n + 1), dtype=torch.float64, device=counts.device)
+    ctx.check(ctx.lib.rg_counts_to_F(ctx.handle, n, _dptr(counts, torch.int64, "counts", n * (n + 1), ctx.device),
+                                     _dptr(rays, torch.int64, "rays", n, ctx.device),
+                                     _dptr(F, torch.float64, "F", n * (n + 1), ctx.device), _stream(stream)),
+              "rg_counts_to_F")
+    return F
+
+
+def enforce_iterative(ctx: Context, F: torch.Tensor, omega: torch.Tensor, tol: float = 1e-12, maxit: int = 10000,
+                      stream=None) -> int:
+    """In-place iterative closure + reciprocity enforcer (rg_enforce_iterative); returns iterations."""
+    n = F.shape[0]
+    it = ctypes.c_int32(0)
+    ctx.check(ctx.lib.rg_enforce_iterative(ctx.handle, n, _dptr(omega, torch.float64, "omega", n, ctx.device),
+                                           _dptr(F, torch.float64, "F", n * (n + 1), ctx.device), float(tol),
+                                           int(maxit), ctypes.byref(it), _stream(stream)), "rg_enforce_iterative")
+    return it.value
+
+
+def enforce_lsq(ctx: Context, F: torch.Tensor, omega: torch.Tensor, nnr: bool = True, spva: bool = True,
+                max_passes: int = 1000, stream=None) -> int:
+    """In-place least-squares optimum with NNR / SPVA (rg_enforce_lsq); returns projections."""
+    n = F.shape[0]
+    p = ctypes.c_int32(0)
+    ctx.check(ctx.lib.rg_enforce_lsq(ctx.handle, n, _dptr(omega, torch.float64, "omega", n, ctx.device),
+                                     _dptr(F, torch.float64, "F", n * (n + 1), ctx.device), int(bool(nnr)),
+                                     int(bool(spva)), int(max_passes), ctypes.byref(p), _stream(stream)),
+              "rg_enforce_lsq")
+    return p.value
+
+
+def aggregate(ctx: Context, F_sub: torch.Tensor, sub_area: torch.Tensor, sub_group: torch.Tensor, n_group: int,
+              stream=None):
+    """Group view factors (rg_aggregate) -> (F_group [G, G+1], group areas [G])."""
+    n = F_sub.shape[0]
+    Fg = torch.empty((n_group, n_group + 1), dtype=torch.float64, device=F_sub.device)
+    Sg = torch.empty(n_group, dtype=torch.float64, device=F_sub.device)
+    ctx.check(ctx.lib.rg_aggregate(ctx.handle, n, _dptr(F_sub, torch.float64, "F_sub", n * (n + 1), ctx.device),
+                                   _dptr(sub_area, torch.float64, "sub_area", n, ctx.device),
+                                   _dptr(sub_group, torch.int32, "sub_group", n, ctx.device), int(n_group),
+                                   _dptr(Fg, torch.float64, "F_group"), _dptr(Sg, torch.float64, "group_area"),
+                                   _stream(stream)), "rg_aggregate")
+    return Fg, Sg
+
+
+def _prec(p):
+    return _native.PREC[p] if isinstance(p, str) else int(p)
+
+
+def gebhart(ctx: Context, F: torch.Tensor, eps: torch.Tensor, rho: torch.Tensor, precision="bf16",
+            tol: float = 1e-12, max_sweeps: int = 12, B: torch.Tensor | None = None, stream=None):
+    """REFs of every (eps, rho) set (rg_gebhart) -> (B [S, N, N+1], sweeps, relative residual)."""
+    n = F.shape[0]
+    eps2 = eps.reshape(-1, n)
+    S = eps2.shape[0]
+    if B is None:
+        B = torch.empty((S, n, n + 1), dtype=torch.float64, device=F.device)
+    sw = ctypes.c_int32(0)
+    res = ctypes.c_double(0.0)
+    ctx.check(ctx.lib.rg_gebhart(ctx.handle, n, _dptr(F, torch.float64, "F", n * (n + 1), ctx.device), S,
+                                 _dptr(eps2, torch.float64, "eps", S * n, ctx.device),
+                                 _dptr(rho, torch.float64, "rho", S * n, ctx.device), _prec(precision), float(tol),
+                                 int(max_sweeps), _dptr(B, torch.float64, "B", S * n * (n + 1), ctx.device),
+                                 ctypes.byref(sw), ctypes.byref(res), _stream(stream)), "rg_gebhart")
+    return B, sw.value, res.value
+
+
+def gebhart_adjoint(ctx: Context, F, eps, rho, B, dB, precision="bf16", tol: float = 1e-12, max_sweeps: int = 12,
+                    stream=None):
+    """(dL/deps, dL/drho) [S, N] from dB = dL/dB (rg_gebhart_adjoint)."""
+    n = F.shape[0]
+    S = eps.numel() // n
+    deps = torch.empty((S, n), dtype=torch.float64, device=F.device)
+    drho = torch.empty((S, n), dtype=torch.float64, device=F.device)
+    ctx.check(ctx.lib.rg_gebhart_adjoint(ctx.handle, n, _dptr(F, torch.float64, "F", n * (n + 1), ctx.device), S,
+                                         _dptr(eps, torch.float64, "eps", S * n, ctx.device),
+                                         _dptr(rho, torch.float64, "rho", S * n, ctx.device),
+                                         _dptr(B, torch.float64, "B", S * n * (n + 1), ctx.device),
+                                         _dptr(dB, torch.float64, "dB", S * n * (n + 1), ctx.device),
+                                         _prec(precision), float(tol), int(max_sweeps),
+                                         _dptr(deps, torch.float64, "deps"), _dptr(drho, torch.float64, "drho"),
+                                         _stream(stream)), "rg_gebhart_adjoint")
+    return deps, drho
+
+
+def temperatures(ctx: Context, B, eps, area, Q, T_sink: float, sigma: float = 5.67e-8, precision="bf16",
+                 tol: float = 1e-13, stream=None) -> torch.Tensor:
+    """Steady node temperatures (rg_temperatures)."""
+    n = B.shape[-2]
+    T = torch.empty(n, dtype=torch.float64, device=B.device)
+    ctx.check(ctx.lib.rg_temperatures(ctx.handle, n, _dptr(B, torch.float64, "B", n * (n + 1), ctx.device),
+                                      _dptr(eps, torch.float64, "eps", n, ctx.device),
+                                      _dptr(area, torch.float64, "area", n, ctx.device),
+                                      _dptr(Q, torch.float64, "Q", n, ctx.device), float(T_sink), float(sigma),
+                                      _prec(precision), float(tol), _dptr(T, torch.float64, "T"), _stream(stream)),
+              "rg_temperatures")
+    return T
+
+
+def temperatures_adjoint(ctx: Context, B, eps, area, T_sink: float, T, dT, sigma: float = 5.67e-8,
+                         precision="bf16", tol: float = 1e-13, stream=None):
+    """(dL/dB [N, N+1], direct dL/deps [N]) from dT = dL/dT (rg_temperatures_adjoint)."""
+    n = B.shape[-2]
+    dB = torch.empty((n, n + 1), dtype=torch.float64, device=B.device)
+    deps = torch.empty(n, dtype=torch.float64, device=B.device)
+    ctx.check(ctx.lib.rg_temperatures_adjoint(ctx.handle, n, _dptr(B, torch.float64, "B", n * (n + 1), ctx.device),
+                                              _dptr(eps, torch.float64, "eps", n, ctx.device),
+                                              _dptr(area, torch.float64, "area", n, ctx.device), float(T_sink),
+                                              float(sigma), _dptr(T, torch.float64, "T", n, ctx.device),
+                                              _dptr(dT, torch.float64, "dT", n, ctx.device), _prec(precision),
+                                              float(tol), _dptr(dB, torch.float64, "dB"),
+                                              _dptr(deps, torch.float64, "deps"), _stream(stream)),
+              "rg_temperatures_adjoint")
+    return dB, deps

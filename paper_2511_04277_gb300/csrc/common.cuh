@@ -1,0 +1,70 @@
+// Internal declarations shared by the translation units of libradgeb.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cstdarg>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "radgeb.h"
+
+struct rg_ctx {
+  int device = 0;
+  int sm_count = 0;
+  int smem_optin = 0;
+  std::string last_error;
+  // device workspace owned by the context, grown on demand (never shrunk)
+  void* ws = nullptr;
+  size_t ws_bytes = 0;
+  // small device scratch: error words, counters, flags (zeroed per call as needed)
+  int* d_scratch = nullptr;
+  // pinned host scratch for scalar read-backs
+  int* h_scratch = nullptr;
+};
+
+namespace rg {
+
+constexpr int kScratchInts = 1024;
+
+rg_status fail(rg_ctx* ctx, rg_status st, const char* fmt, ...);
+rg_status cuda_fail(rg_ctx* ctx, cudaError_t e, const char* what);
+
+// Device workspace of at least `bytes` (256-byte aligned), owned by ctx.
+rg_status workspace(rg_ctx* ctx, size_t bytes, void** out);
+
+inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// Carves consecutive 256-byte aligned sub-buffers out of one allocation.
+struct Carver {
+  char* base;
+  size_t off = 0;
+  explicit Carver(void* b) : base(static_cast<char*>(b)) {}
+  template <class T>
+  T* take(size_t count) {
+    T* p = reinterpret_cast<T*>(base + off);
+    off = align_up(off + count * sizeof(T), 256);
+    return p;
+  }
+};
+// Bytes a sequence of takes needs.
+struct Sizer {
+  size_t off = 0;
+  template <class T>
+  void take(size_t count) { off = align_up(off + count * sizeof(T), 256); }
+};
+
+}  // namespace rg
+
+#define RG_CUDA_TRY(ctx, call)                                   \
+  do {                                                           \
+    cudaError_t e_ = (call);                                     \
+    if (e_ != cudaSuccess) return rg::cuda_fail((ctx), e_, #call); \
+  } while (0)
+
+#define RG_ARG_CHECK(ctx, cond, ...)                                   \
+  do {                                                                 \
+    if (!(cond)) return rg::fail((ctx), RG_ERR_ARG, __VA_ARGS__);      \
+  } while (0)

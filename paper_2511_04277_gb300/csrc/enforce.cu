@@ -1,0 +1,325 @@
+// F from counts (Eq. 3.15), the iterative closure + reciprocity enforcer (Sec. 3.5.5)
+// and the multi-node aggregation (Eq. 5.6-5.7), all fp64.
+//
+// Iterative enforcer layout: the caller's F (N x (N+1), row-major, ld = N+1) is turned
+// into H = Omega_i F_ij in place, and a row scale s (initially 1) is kept beside it, so
+// that the current iterate is eta_ij = s_i H_ij. One iteration is two kernels:
+//   sym_pass  one block per tile pair (I, J), I <= J, of 64 x 64 tiles: loads eta on
+//             both sides of the diagonal, writes H'_ij = H'_ji = (eta_ij + eta_ji)/2,
+//             records the largest |eta_ij - eta_ji|/2 and per-tile row sums;
+//   row_pass  carries the environment column (eta_i,inf = s_i H_i,inf), adds the row
+//             sums, records |r_i - Omega_i| and sets s_i = Omega_i / r_i (Eq. 3.39-3.40
+//             with w = eta); its last block applies the stopping rule.
+// Every entry is read and written once per iteration: 16 bytes of HBM traffic.
+#include <cfloat>
+
+#include "common.cuh"
+
+namespace {
+
+constexpr int kT = 64;        // tile edge
+constexpr int kThreads = 256;
+
+__global__ void counts_to_F_kernel(const long long* __restrict__ c, const long long* __restrict__ rays,
+                                   double* __restrict__ F, int32_t n, int64_t total) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    int64_t i = e / (n + 1);
+    F[e] = (double)c[e] / (double)rays[i];
+  }
+}
+
+__global__ void to_exchange_kernel(double* __restrict__ H, const double* __restrict__ omega, double* __restrict__ s,
+                                   int32_t n, int64_t total) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    int64_t i = e / (n + 1);
+    H[e] = omega[i] * H[e];
+    if (e % (n + 1) == 0) s[i] = 1.0;
+  }
+}
+
+__global__ void from_exchange_kernel(double* __restrict__ H, const double* __restrict__ omega,
+                                     const double* __restrict__ s, int32_t n, int64_t total) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    int64_t i = e / (n + 1);
+    H[e] = s[i] * H[e] / omega[i];
+  }
+}
+
+struct EnforceState {
+  unsigned long long d_recip;  // bits of the largest reciprocity defect this iteration
+  unsigned long long d_close;  // bits of the largest closure defect this iteration
+  int32_t done;                // 0 running, 1 converged, 2 iteration limit, 3 non-finite
+  int32_t iters;
+  int32_t blocks_seen;
+  int32_t pad;
+};
+
+__global__ void __launch_bounds__(kThreads) sym_pass(double* __restrict__ H, const double* __restrict__ s,
+                                                     int32_t n, double* __restrict__ P, EnforceState* st) {
+  if (st->done) return;
+  const int I = blockIdx.y, J = blockIdx.x;
+  if (I > J) return;
+  __shared__ double A[kT][kT + 1];
+  __shared__ double B[kT][kT + 1];
+  __shared__ double red[kThreads];
+  const int64_t ld = n + 1;
+  const int tid = threadIdx.x;
+  for (int e = tid; e < kT * kT; e += kThreads) {
+    int r = e / kT, c = e % kT;
+    int64_t i = (int64_t)I * kT + r, j = (int64_t)J * kT + c;
+    A[r][c] = (i < n && j < n) ? s[i] * H[i * ld + j] : 0.0;
+    if (I != J) {
+      int64_t i2 = (int64_t)J * kT + r, j2 = (int64_t)I * kT + c;
+      B[r][c] = (i2 < n && j2 < n) ? s[i2] * H[i2 * ld + j2] : 0.0;
+    }
+  }
+  __syncthreads();
+  double dmax = 0.0;
+  // tile (I, J): h(r, c) = (A[r][c] + other(c, r)) / 2
+  for (int e = tid; e < kT * kT; e += kThreads) {
+    int r = e / kT, c = e % kT;
+    int64_t i = (int64_t)I * kT + r, j = (int64_t)J * kT + c;
+    if (i < n && j < n) {
+      double a = A[r][c], b = (I != J) ? B[c][r] : A[c][r];
+      H[i * ld + j] = 0.5 * (a + b);
+      dmax = fmax(dmax, 0.5 * fabs(a - b));
+    }
+    if (I != J) {
+      int64_t i2 = (int64_t)J * kT + r, j2 = (int64_t)I * kT + c;
+      if (i2 < n && j2 < n) H[i2 * ld + j2] = 0.5 * (B[r][c] + A[c][r]);
+    }
+  }
+  // row sums: 4 threads per row, 16 columns each, fixed order
+  const int row = tid >> 2, part = tid & 3;
+  double acc = 0.0, acc2 = 0.0;
+  for (int c = part * 16; c < part * 16 + 16; ++c) {
+    double b = (I != J) ? B[c][row] : A[c][row];
+    acc += 0.5 * (A[row][c] + b);
+    if (I != J) acc2 += 0.5 * (B[row][c] + A[c][row]);
+  }
+  acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+  acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+  acc2 += __shfl_xor_sync(0xffffffffu, acc2, 1);
+  acc2 += __shfl_xor_sync(0xffffffffu, acc2, 2);
+  if (part == 0) {
+    int64_t i = (int64_t)I * kT + row;
+    if (i < n) P[(int64_t)J * n + i] = acc;
+    int64_t j = (int64_t)J * kT + row;
+    if (I != J && j < n) P[(int64_t)I * n + j] = acc2;
+  }
+  red[tid] = dmax;
+  __syncthreads();
+  for (int w = kThreads / 2; w > 0; w >>= 1) {
+    if (tid < w) red[tid] = fmax(red[tid], red[tid + w]);
+    __syncthreads();
+  }
+  if (tid == 0) atomicMax(&st->d_recip, (unsigned long long)__double_as_longlong(red[0]));
+}
+
+__global__ void __launch_bounds__(kThreads) row_pass(double* __restrict__ H, double* __restrict__ s,
+                                                     const double* __restrict__ omega, const double* __restrict__ P,
+                                                     int32_t n, int32_t n_tiles, EnforceState* st, double tol_abs,
+                                                     int32_t maxit) {
+  if (st->done) return;
+  __shared__ double red[kThreads];
+  __shared__ int s_last;
+  const int64_t ld = n + 1;
+  const int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x;
+  double dc = 0.0;
+  bool bad = false;
+  if (i < n) {
+    double env = s[i] * H[i * ld + n];
+    H[i * ld + n] = env;
+    double r = 0.0;
+    for (int J = 0; J < n_tiles; ++J) r += P[(int64_t)J * n + i];
+    r += env;
+    dc = fabs(r - omega[i]);
+    s[i] = (r > 0.0) ? omega[i] / r : 1.0;
+    bad = !isfinite(r);
+  }
+  red[threadIdx.x] = dc;
+  if (bad) st->done = 3;
+  __syncthreads();
+  for (int w = kThreads / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + w]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    atomicMax(&st->d_close, (unsigned long long)__double_as_longlong(red[0]));
+    __threadfence();
+    s_last = (atomicAdd(&st->blocks_seen, 1) == (int)gridDim.x - 1);
+  }
+  __syncthreads();
+  if (s_last && threadIdx.x == 0) {
+    __threadfence();
+    volatile EnforceState* v = st;
+    double dr = __longlong_as_double((long long)v->d_recip);
+    double dcl = __longlong_as_double((long long)v->d_close);
+    int it = v->iters + 1;
+    v->iters = it;
+    if (v->done == 0) {
+      if (fmax(dr, dcl) <= tol_abs) v->done = 1;
+      else if (it >= maxit) v->done = 2;
+    }
+    v->d_recip = 0ull;
+    v->d_close = 0ull;
+    v->blocks_seen = 0;
+  }
+}
+
+__global__ void max_kernel(const double* __restrict__ x, int32_t n, unsigned long long* out) {
+  __shared__ double red[kThreads];
+  double m = 0.0;
+  for (int i = threadIdx.x; i < n; i += kThreads) m = fmax(m, fabs(x[i]));
+  red[threadIdx.x] = m;
+  __syncthreads();
+  for (int w = kThreads / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + w]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = (unsigned long long)__double_as_longlong(red[0]);
+}
+
+// ---------------------------------------------------------------- aggregation
+__global__ void group_area_kernel(const double* __restrict__ S, const int32_t* __restrict__ g, int32_t n_sub,
+                                  double* __restrict__ Sg, int32_t n_group, int32_t* err) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_sub; i += gridDim.x * blockDim.x) {
+    int32_t k = g[i];
+    if (k < 0 || k >= n_group) { atomicExch(err, 1); continue; }
+    atomicAdd(&Sg[k], S[i]);
+  }
+}
+
+// One block per sub-surface row i: T[m] = sum_{j in group m} F_ij (shared memory), then
+// out[g(i)][m] += T[m] * S_i / S_g(i).
+__global__ void __launch_bounds__(kThreads) aggregate_rows(const double* __restrict__ F, const double* __restrict__ S,
+                                                           const int32_t* __restrict__ g, int32_t n_sub,
+                                                           const double* __restrict__ Sg, int32_t n_group,
+                                                           double* __restrict__ out) {
+  extern __shared__ double acc[];
+  const int cols = n_group + 1;
+  const int64_t ld = n_sub + 1;
+  for (int i = blockIdx.x; i < n_sub; i += gridDim.x) {
+    for (int m = threadIdx.x; m < cols; m += kThreads) acc[m] = 0.0;
+    __syncthreads();
+    for (int j = threadIdx.x; j <= n_sub; j += kThreads) {
+      int m = (j == n_sub) ? n_group : g[j];
+      if ((unsigned)m > (unsigned)n_group) continue;  // reported by group_area_kernel
+      double f = F[i * ld + j];
+      if (f != 0.0) atomicAdd(&acc[m], f);
+    }
+    __syncthreads();
+    const int gi = g[i];
+    if ((unsigned)gi < (unsigned)n_group) {
+      const double w = S[i] / Sg[gi];
+      for (int m = threadIdx.x; m < cols; m += kThreads)
+        if (acc[m] != 0.0) atomicAdd(&out[(int64_t)gi * cols + m], acc[m] * w);
+    }
+    __syncthreads();
+  }
+}
+
+inline int blocks_for(int64_t total, int sm) {
+  int64_t b = (total + kThreads - 1) / kThreads;
+  int64_t cap = (int64_t)sm * 8;
+  return (int)(b < 1 ? 1 : (b > cap ? cap : b));
+}
+
+}  // namespace
+
+extern "C" {
+
+rg_status rg_counts_to_F(rg_ctx* ctx, int32_t n, const int64_t* counts_d, const int64_t* rays_d, double* F_d,
+                         void* stream) {
+  if (!ctx) return RG_ERR_ARG;
+  RG_ARG_CHECK(ctx, n > 0 && counts_d && rays_d && F_d, "rg_counts_to_F: bad argument");
+  RG_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+  int64_t total = (int64_t)n * (n + 1);
+  counts_to_F_kernel<<<blocks_for(total, ctx->sm_count), kThreads, 0, (cudaStream_t)stream>>>(
+      reinterpret_cast<const long long*>(counts_d), reinterpret_cast<const long long*>(rays_d), F_d, n, total);
+  RG_CUDA_TRY(ctx, cudaGetLastError());
+  return RG_OK;
+}
+
+rg_status rg_enforce_iterative(rg_ctx* ctx, int32_t n, const double* omega_d, double* F_d, double tol, int32_t maxit,
+                               int32_t* iters_out_h, void* stream) {
+  if (!ctx) return RG_ERR_ARG;
+  RG_ARG_CHECK(ctx, n > 0 && omega_d && F_d && maxit > 0 && tol >= 0.0, "rg_enforce_iterative: bad argument");
+  RG_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+  cudaStream_t s = (cudaStream_t)stream;
+  const int n_tiles = (n + kT - 1) / kT;
+  rg::Sizer sz;
+  sz.take<double>(n);                          // s
+  sz.take<double>((size_t)n_tiles * n);        // P
+  sz.take<EnforceState>(1);
+  void* ws = nullptr;
+  rg_status rs = rg::workspace(ctx, sz.off, &ws);
+  if (rs != RG_OK) return rs;
+  rg::Carver cv(ws);
+  double* sc = cv.take<double>(n);
+  double* P = cv.take<double>((size_t)n_tiles * n);
+  EnforceState* st = cv.take<EnforceState>(1);
+  const int64_t total = (int64_t)n * (n + 1);
+  RG_CUDA_TRY(ctx, cudaMemsetAsync(st, 0, sizeof(EnforceState), s));
+  // tolerance scale: max Omega
+  max_kernel<<<1, kThreads, 0, s>>>(omega_d, n, reinterpret_cast<unsigned long long*>(ctx->d_scratch));
+  RG_CUDA_TRY(ctx, cudaMemcpyAsync(ctx->h_scratch, ctx->d_scratch, 8, cudaMemcpyDeviceToHost, s));
+  to_exchange_kernel<<<blocks_for(total, ctx->sm_count), kThreads, 0, s>>>(F_d, omega_d, sc, n, total);
+  RG_CUDA_TRY(ctx, cudaGetLastError());
+  RG_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+  double om_max;
+  memcpy(&om_max, ctx->h_scratch, 8);
+  const double tol_abs = tol * om_max;
+  dim3 sym_grid(n_tiles, n_tiles);
+  const int row_blocks = (n + kThreads - 1) / kThreads;
+  EnforceState h{};
+  for (int launched = 0; launched < maxit;) {
+    int batch = std::min(8, maxit - launched);
+    for (int b = 0; b < batch; ++b) {
+      sym_pass<<<sym_grid, kThreads, 0, s>>>(F_d, sc, n, P, st);
+      row_pass<<<row_blocks, kThreads, 0, s>>>(F_d, sc, omega_d, P, n, n_tiles, st, tol_abs, maxit);
+    }
+    launched += batch;
+    RG_CUDA_TRY(ctx, cudaGetLastError());
+    RG_CUDA_TRY(ctx, cudaMemcpyAsync(&h, st, sizeof(EnforceState), cudaMemcpyDeviceToHost, s));
+    RG_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+    if (h.done) break;
+  }
+  from_exchange_kernel<<<blocks_for(total, ctx->sm_count), kThreads, 0, s>>>(F_d, omega_d, sc, n, total);
+  RG_CUDA_TRY(ctx, cudaGetLastError());
+  if (iters_out_h) *iters_out_h = h.iters;
+  if (h.done == 3) return rg::fail(ctx, RG_ERR_NUMERIC, "rg_enforce_iterative: non-finite row sum");
+  if (h.done != 1) return rg::fail(ctx, RG_ERR_NOT_CONVERGED, "rg_enforce_iterative: no convergence in %d iterations", maxit);
+  return RG_OK;
+}
+
+rg_status rg_aggregate(rg_ctx* ctx, int32_t n_sub, const double* F_sub_d, const double* sub_area_d,
+                       const int32_t* sub_group_d, int32_t n_group, double* F_group_d, double* group_area_d,
+                       void* stream) {
+  if (!ctx) return RG_ERR_ARG;
+  RG_ARG_CHECK(ctx, n_sub > 0 && n_group > 0 && F_sub_d && sub_area_d && sub_group_d && F_group_d,
+               "rg_aggregate: bad argument");
+  const size_t smem = (size_t)(n_group + 1) * sizeof(double);
+  RG_ARG_CHECK(ctx, (int)smem <= ctx->smem_optin - 1024, "rg_aggregate: too many groups (%d)", n_group);
+  RG_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+  cudaStream_t s = (cudaStream_t)stream;
+  void* ws = nullptr;
+  rg_status rs = rg::workspace(ctx, (size_t)n_group * sizeof(double), &ws);
+  if (rs != RG_OK) return rs;
+  double* Sg = group_area_d ? group_area_d : static_cast<double*>(ws);
+  RG_CUDA_TRY(ctx, cudaMemsetAsync(Sg, 0, (size_t)n_group * sizeof(double), s));
+  RG_CUDA_TRY(ctx, cudaMemsetAsync(F_group_d, 0, (size_t)n_group * (n_group + 1) * sizeof(double), s));
+  RG_CUDA_TRY(ctx, cudaMemsetAsync(ctx->d_scratch, 0, sizeof(int32_t), s));
+  group_area_kernel<<<blocks_for(n_sub, ctx->sm_count), kThreads, 0, s>>>(sub_area_d, sub_group_d, n_sub, Sg, n_group,
+                                                                         ctx->d_scratch);
+  RG_CUDA_TRY(ctx, cudaFuncSetAttribute(aggregate_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int grid = std::min(n_sub, ctx->sm_count * 4);
+  aggregate_rows<<<grid, kThreads, smem, s>>>(F_sub_d, sub_area_d, sub_group_d, n_sub, Sg, n_group, F_group_d);
+  RG_CUDA_TRY(ctx, cudaGetLastError());
+  RG_CUDA_TRY(ctx, cudaMemcpyAsync(ctx->h_scratch, ctx->d_scratch, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  RG_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+  if (ctx->h_scratch[0]) return rg::fail(ctx, RG_ERR_ARG, "rg_aggregate: group index out of range");
+  return RG_OK;
+}
+
+}  // extern "C"

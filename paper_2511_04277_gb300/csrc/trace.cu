@@ -1,0 +1,340 @@
+// Monte Carlo ray tracing of view factors (Sec. 3.5.1, Eq. 3.15) on sm_103a.
+//
+// One persistent kernel: each block repeatedly takes a work item (one face, a range
+// of its rays), keeps a shared-memory tally row of N+1 counters for that face, traces
+// the rays (Philox4x32-10 draws, area-CDF triangle choice, uniform point, Malley
+// cosine-weighted direction, origin lifted off the face along its normal, BVH
+// traversal with Moller-Trumbore leaf tests, closest hit by (t > 0, triangle index)),
+// adds warp-aggregated hits to the row and flushes the non-zero counters to the int64
+// count matrix in HBM.
+//
+// kExact = true rounds every float operation of sampling and intersection on its
+// own (no fused multiply-add), which makes the counts bit-identical to any other
+// implementation of the same ray definition that does the same.
+#include <climits>
+
+#include "mesh.cuh"
+
+namespace {
+
+struct WorkItem {
+  int64_t begin;
+  int32_t face;
+  int32_t count;
+};
+
+struct TraceParams {
+  DevMesh m;
+  const WorkItem* items;
+  int32_t n_items;
+  int32_t* item_counter;  // next item to take (zeroed before the launch)
+  int32_t* error_word;    // non-zero: a ray overflowed the traversal stack
+  uint32_t key0, key1;
+  uint64_t ray_offset;
+  unsigned long long* counts;  // [N][N+1]
+  int32_t n_bins;              // N + 1
+};
+
+template <bool kExact>
+struct Ar;
+template <>
+struct Ar<true> {
+  static __device__ __forceinline__ float mul(float a, float b) { return __fmul_rn(a, b); }
+  static __device__ __forceinline__ float add(float a, float b) { return __fadd_rn(a, b); }
+  static __device__ __forceinline__ float sub(float a, float b) { return __fsub_rn(a, b); }
+};
+template <>
+struct Ar<false> {
+  static __device__ __forceinline__ float mul(float a, float b) { return a * b; }
+  static __device__ __forceinline__ float add(float a, float b) { return a + b; }
+  static __device__ __forceinline__ float sub(float a, float b) { return a - b; }
+};
+
+struct V3 {
+  float x, y, z;
+};
+
+template <bool E>
+__device__ __forceinline__ V3 cross3(V3 a, V3 b) {
+  using A = Ar<E>;
+  return {A::sub(A::mul(a.y, b.z), A::mul(a.z, b.y)), A::sub(A::mul(a.z, b.x), A::mul(a.x, b.z)),
+          A::sub(A::mul(a.x, b.y), A::mul(a.y, b.x))};
+}
+template <bool E>
+__device__ __forceinline__ float dot3(V3 a, V3 b) {
+  using A = Ar<E>;
+  return A::add(A::add(A::mul(a.x, b.x), A::mul(a.y, b.y)), A::mul(a.z, b.z));
+}
+
+// Philox4x32-10 (Salmon et al., SC'11).
+__device__ __forceinline__ uint4 philox(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r) {
+      k0 += 0x9E3779B9u;
+      k1 += 0xBB67AE85u;
+    }
+    uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+    uint32_t hi2 = __umulhi(0xCD9E8D57u, c.z), lo2 = 0xCD9E8D57u * c.z;
+    c = make_uint4(hi2 ^ c.y ^ k0, lo2, hi0 ^ c.w ^ k1, lo0);
+  }
+  return c;
+}
+
+__device__ __forceinline__ float unit24(uint32_t x) { return __uint2float_rn(x >> 8) * 5.9604644775390625e-08f; }
+__device__ __forceinline__ float sym24(uint32_t x) {
+  return __fsub_rn(__uint2float_rn(x >> 8) * 1.1920928955078125e-07f, 1.0f);  // exact: 2u - 1
+}
+
+template <bool E>
+__device__ __forceinline__ bool moller_trumbore(const float4 r0, const float4 r1, const float4 r2, V3 o, V3 d,
+                                                float* t_out) {
+  using A = Ar<E>;
+  const float lo = -9.5367431640625e-07f, hi = 1.00000095367431640625f;  // -2^-20, 1 + 2^-20
+  V3 v0{r0.x, r0.y, r0.z}, e1{r0.w, r1.x, r1.y}, e2{r1.z, r1.w, r2.x};
+  V3 p = cross3<E>(d, e2);
+  float det = dot3<E>(e1, p);
+  if (det == 0.0f) return false;
+  float inv = __frcp_rn(det);
+  V3 tv{A::sub(o.x, v0.x), A::sub(o.y, v0.y), A::sub(o.z, v0.z)};
+  float u = A::mul(dot3<E>(tv, p), inv);
+  if (!(u >= lo && u <= hi)) return false;
+  V3 q = cross3<E>(tv, e1);
+  float v = A::mul(dot3<E>(d, q), inv);
+  if (!(v >= lo && A::add(u, v) <= hi)) return false;
+  float t = A::mul(dot3<E>(e2, q), inv);
+  if (!(t > 0.0f)) return false;
+  *t_out = t;
+  return true;
+}
+
+template <bool E>
+__device__ __forceinline__ void test_record(const float4* __restrict__ rec, int32_t src, V3 o, V3 d, float& best_t,
+                                            int32_t& best_id, int32_t& best_face) {
+  float4 r0 = __ldg(rec), r1 = __ldg(rec + 1), r2 = __ldg(rec + 2);
+  int32_t id = __float_as_int(r2.y);
+  if (id == src) return;
+  float t;
+  if (!moller_trumbore<E>(r0, r1, r2, o, d, &t)) return;
+  if (t < best_t || (t == best_t && id < best_id)) {
+    best_t = t;
+    best_id = id;
+    best_face = __float_as_int(r2.z);
+  }
+}
+
+// Closest hit; returns the face index or n_faces (environment). Sets *overflow on a
+// traversal stack overflow.
+template <bool E, bool kBVH>
+__device__ int32_t closest_face(const DevMesh& m, int32_t src, V3 o, V3 d, bool* overflow) {
+  float best_t = __int_as_float(0x7f800000);
+  int32_t best_id = INT_MAX, best_face = m.n_faces;
+  if (!kBVH) {
+    for (int64_t k = 0; k < m.nt; ++k) test_record<E>(m.tris + 3 * k, src, o, d, best_t, best_id, best_face);
+    return best_face;
+  }
+  const float ix = __frcp_rn(d.x), iy = __frcp_rn(d.y), iz = __frcp_rn(d.z);
+  int32_t stack[kTraceStack];
+  int sp = 0;
+  int32_t node = 0;
+  while (true) {
+    const float4* nd = m.nodes + 4 * node;
+    float4 a = __ldg(nd), b = __ldg(nd + 1), c = __ldg(nd + 2), w = __ldg(nd + 3);
+    int32_t refL = __float_as_int(w.x), refR = __float_as_int(w.y);
+    int32_t cntL = __float_as_int(w.z), cntR = __float_as_int(w.w);
+    float limit = best_t + m.slack;
+    float x0 = (a.x - o.x) * ix, x1 = (a.y - o.x) * ix, y0 = (a.z - o.y) * iy, y1 = (a.w - o.y) * iy;
+    float z0 = (c.x - o.z) * iz, z1 = (c.y - o.z) * iz;
+    float lmin = fmaxf(fmaxf(fminf(x0, x1), fminf(y0, y1)), fmaxf(fminf(z0, z1), m.t_lo));
+    float lmax = fminf(fminf(fmaxf(x0, x1), fmaxf(y0, y1)), fminf(fmaxf(z0, z1), limit));
+    x0 = (b.x - o.x) * ix; x1 = (b.y - o.x) * ix; y0 = (b.z - o.y) * iy; y1 = (b.w - o.y) * iy;
+    z0 = (c.z - o.z) * iz; z1 = (c.w - o.z) * iz;
+    float rmin = fmaxf(fmaxf(fminf(x0, x1), fminf(y0, y1)), fmaxf(fminf(z0, z1), m.t_lo));
+    float rmax = fminf(fminf(fmaxf(x0, x1), fmaxf(y0, y1)), fminf(fmaxf(z0, z1), limit));
+    bool hl = lmin <= lmax, hr = rmin <= rmax;
+    if (hl && cntL > 0) {
+      for (int q = 0; q < cntL; ++q)
+        test_record<E>(m.tris + 3 * (int64_t)(refL + q), src, o, d, best_t, best_id, best_face);
+      hl = false;
+    }
+    if (hr && cntR > 0) {
+      for (int q = 0; q < cntR; ++q)
+        test_record<E>(m.tris + 3 * (int64_t)(refR + q), src, o, d, best_t, best_id, best_face);
+      hr = false;
+    }
+    if (hl && hr) {
+      bool left_first = lmin <= rmin;
+      if (sp >= kTraceStack) { *overflow = true; break; }
+      stack[sp++] = left_first ? refR : refL;
+      node = left_first ? refL : refR;
+    } else if (hl) {
+      node = refL;
+    } else if (hr) {
+      node = refR;
+    } else {
+      if (sp == 0) break;
+      node = stack[--sp];
+    }
+  }
+  return best_face;
+}
+
+template <bool E>
+__device__ __forceinline__ void sample_ray(const DevMesh& m, uint32_t k0, uint32_t k1, uint64_t ray, int32_t face,
+                                           V3* o, V3* d, int32_t* src) {
+  using A = Ar<E>;
+  const uint32_t rlo = (uint32_t)ray, rhi = (uint32_t)(ray >> 32);
+  uint4 x = philox(make_uint4(rlo, rhi, (uint32_t)face, 0u), k0, k1);
+  int64_t lo = m.face_start[face], hi = m.face_start[face + 1];
+  // first record whose threshold exceeds x.x (thresholds are non-decreasing)
+  int64_t a = lo, b = hi - 1;
+  while (a < b) {
+    int64_t mid = (a + b) >> 1;
+    if (x.x < __ldg(m.ethr + mid)) b = mid; else a = mid + 1;
+  }
+  const float4* rec = m.etris + 3 * a;
+  float4 r0 = __ldg(rec), r1 = __ldg(rec + 1), r2 = __ldg(rec + 2);
+  *src = __float_as_int(r2.y);
+  float u = unit24(x.y), v = unit24(x.z);
+  if (A::add(u, v) > 1.0f) {
+    u = A::sub(1.0f, u);
+    v = A::sub(1.0f, v);
+  }
+  // pull (u, v) toward the centroid by 2^-20 so that no origin lies on an edge
+  u = A::add(A::mul(u, 0x1.ffffep-1f), 0x1.555556p-22f);
+  v = A::add(A::mul(v, 0x1.ffffep-1f), 0x1.555556p-22f);
+  const float* fr = m.frames + 9 * (int64_t)face;
+  float tx = __ldg(fr), ty = __ldg(fr + 1), tz = __ldg(fr + 2), bx = __ldg(fr + 3), by = __ldg(fr + 4),
+        bz = __ldg(fr + 5), nx = __ldg(fr + 6), ny = __ldg(fr + 7), nz = __ldg(fr + 8);
+  // point on the triangle, lifted off the face along its normal
+  o->x = A::add(A::add(A::add(r0.x, A::mul(u, r0.w)), A::mul(v, r1.z)), A::mul(m.lift, nx));
+  o->y = A::add(A::add(A::add(r0.y, A::mul(u, r1.x)), A::mul(v, r1.w)), A::mul(m.lift, ny));
+  o->z = A::add(A::add(A::add(r0.z, A::mul(u, r1.y)), A::mul(v, r2.x)), A::mul(m.lift, nz));
+  float dx = 0.f, dy = 0.f, s2 = 0.f;
+  for (uint32_t att = 1; att <= 64; ++att) {
+    uint4 y = philox(make_uint4(rlo, rhi, (uint32_t)face, att), k0, k1);
+    float cx = sym24(y.x), cy = sym24(y.y);
+    float cs = A::add(A::mul(cx, cx), A::mul(cy, cy));
+    if (cs < 1.0f) { dx = cx; dy = cy; s2 = cs; break; }
+    cx = sym24(y.z); cy = sym24(y.w);
+    cs = A::add(A::mul(cx, cx), A::mul(cy, cy));
+    if (cs < 1.0f) { dx = cx; dy = cy; s2 = cs; break; }
+  }
+  float dz = __fsqrt_rn(A::sub(1.0f, s2));
+  d->x = A::add(A::add(A::mul(dx, tx), A::mul(dy, bx)), A::mul(dz, nx));
+  d->y = A::add(A::add(A::mul(dx, ty), A::mul(dy, by)), A::mul(dz, ny));
+  d->z = A::add(A::add(A::mul(dx, tz), A::mul(dy, bz)), A::mul(dz, nz));
+}
+
+constexpr int kThreads = 256;
+
+template <bool E, bool kBVH>
+__global__ void __launch_bounds__(kThreads, 2) trace_kernel(const TraceParams p) {
+  extern __shared__ uint32_t hist[];
+  __shared__ int32_t s_item;
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  bool overflow = false;
+  while (true) {
+    if (threadIdx.x == 0) s_item = atomicAdd(p.item_counter, 1);
+    for (int b = threadIdx.x; b < p.n_bins; b += kThreads) hist[b] = 0u;
+    __syncthreads();
+    const int32_t item = s_item;
+    if (item >= p.n_items) break;
+    const WorkItem w = p.items[item];
+    for (int32_t base = warp * 32; base < w.count; base += kThreads) {
+      const int32_t r = base + lane;
+      const bool valid = r < w.count;
+      int32_t bin = 0;
+      if (valid) {
+        V3 o, d;
+        int32_t src;
+        sample_ray<E>(p.m, p.key0, p.key1, p.ray_offset + (uint64_t)(w.begin + r), w.face, &o, &d, &src);
+        bin = closest_face<E, kBVH>(p.m, src, o, d, &overflow);
+      }
+      __syncwarp();
+      const unsigned vmask = __ballot_sync(0xffffffffu, valid);
+      if (valid) {
+        const unsigned peers = __match_any_sync(vmask, bin);
+        if (lane == __ffs(peers) - 1) atomicAdd(&hist[bin], (uint32_t)__popc(peers));
+      }
+    }
+    __syncthreads();
+    unsigned long long* row = p.counts + (int64_t)w.face * p.n_bins;
+    for (int b = threadIdx.x; b < p.n_bins; b += kThreads) {
+      uint32_t c = hist[b];
+      if (c) atomicAdd(row + b, (unsigned long long)c);
+    }
+    __syncthreads();
+  }
+  if (overflow) atomicExch(p.error_word, 1);
+}
+
+template <bool E, bool B>
+cudaError_t launch(const TraceParams& p, int sm_count, size_t smem, cudaStream_t s) {
+  auto k = trace_kernel<E, B>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kThreads, smem);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  int grid = sm_count * per_sm;
+  if (grid > p.n_items) grid = p.n_items;
+  k<<<grid, kThreads, smem, s>>>(p);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+extern "C" rg_status rg_trace(rg_ctx* ctx, const rg_mesh* mesh, const int64_t* rays_per_face_h, uint64_t seed,
+                              uint64_t ray_offset, int32_t fma_free, int64_t* counts_d, void* stream) {
+  if (!ctx) return RG_ERR_ARG;
+  RG_ARG_CHECK(ctx, mesh && rays_per_face_h && counts_d, "rg_trace: NULL argument");
+  const DevMesh& m = mesh_device_view(mesh);
+  RG_ARG_CHECK(ctx, mesh_device(mesh) == ctx->device, "rg_trace: mesh belongs to another device");
+  const int32_t N = m.n_faces;
+  const int32_t n_bins = N + 1;
+  const size_t smem = (size_t)n_bins * sizeof(uint32_t);
+  if (n_bins > 49152 || (int)smem > ctx->smem_optin - 1024)
+    return rg::fail(ctx, RG_ERR_UNSUPPORTED, "rg_trace: %d faces exceed the shared-memory tally row", N);
+  // work items: chunks of at most kChunk rays of one face
+  constexpr int64_t kChunk = 1 << 16;
+  std::vector<WorkItem> items;
+  for (int32_t f = 0; f < N; ++f) {
+    int64_t n = rays_per_face_h[f];
+    RG_ARG_CHECK(ctx, n >= 0, "rg_trace: negative ray count for face %d", f);
+    for (int64_t b = 0; b < n; b += kChunk) items.push_back({b, f, (int32_t)std::min(kChunk, n - b)});
+  }
+  if (items.empty()) return RG_OK;
+  RG_ARG_CHECK(ctx, items.size() < (size_t)INT32_MAX, "rg_trace: too many rays");
+  RG_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+  cudaStream_t s = (cudaStream_t)stream;
+  void* ws = nullptr;
+  rg_status st = rg::workspace(ctx, items.size() * sizeof(WorkItem), &ws);
+  if (st != RG_OK) return st;
+  RG_CUDA_TRY(ctx, cudaMemcpyAsync(ws, items.data(), items.size() * sizeof(WorkItem), cudaMemcpyHostToDevice, s));
+  RG_CUDA_TRY(ctx, cudaMemsetAsync(ctx->d_scratch, 0, 2 * sizeof(int32_t), s));
+  TraceParams p;
+  p.m = m;
+  p.items = static_cast<const WorkItem*>(ws);
+  p.n_items = (int32_t)items.size();
+  p.item_counter = ctx->d_scratch;
+  p.error_word = ctx->d_scratch + 1;
+  p.key0 = (uint32_t)seed;
+  p.key1 = (uint32_t)(seed >> 32);
+  p.ray_offset = ray_offset;
+  p.counts = reinterpret_cast<unsigned long long*>(counts_d);
+  p.n_bins = n_bins;
+  cudaError_t e;
+  if (fma_free)
+    e = m.use_bvh ? launch<true, true>(p, ctx->sm_count, smem, s) : launch<true, false>(p, ctx->sm_count, smem, s);
+  else
+    e = m.use_bvh ? launch<false, true>(p, ctx->sm_count, smem, s) : launch<false, false>(p, ctx->sm_count, smem, s);
+  if (e != cudaSuccess) return rg::cuda_fail(ctx, e, "rg_trace: launch");
+  // the host copy of the items must outlive the async upload, and the error word is read back
+  RG_CUDA_TRY(ctx, cudaMemcpyAsync(ctx->h_scratch, ctx->d_scratch + 1, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  RG_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+  if (ctx->h_scratch[0]) return rg::fail(ctx, RG_ERR_STACK, "rg_trace: traversal stack overflow");
+  return RG_OK;
+}

@@ -37,3 +37,15 @@ def load_table(name):
 @pytest.fixture
 def golden():
     return load_matrix
+
+
+@pytest.fixture(scope="session")
+def rg_ctx():
+    """A library context on cuda:0 (GPU tests only)."""
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2511_04277_gb300 import api
+    ctx = api.Context(0)
+    yield ctx
+    ctx.close()

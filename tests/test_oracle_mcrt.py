@@ -72,7 +72,8 @@ def test_sampling_moments():
     m = synth.cube()
     n = 200_000
     o, d, tri, att = mcrt.sample_rays(m.verts, m.tris, m.tri_face, m.n_faces, 4, 0, 0, n)  # z=0, normal +z
-    assert np.all(o[:, 2] == 0.0)
+    lift = np.float32(1e-6 * math.sqrt(3))
+    assert np.all(o[:, 2] == lift)             # origins lifted off the face along its normal
     assert abs(o[:, 0].mean() - 0.5) < 4 * math.sqrt(1 / 12 / n)
     assert abs(o[:, 1].mean() - 0.5) < 4 * math.sqrt(1 / 12 / n)
     cz = d[:, 2].astype(np.float64) / np.linalg.norm(d.astype(np.float64), axis=1)
@@ -91,7 +92,7 @@ def test_sampling_moments():
 
 def test_face_geometry():
     m = synth.cube()
-    area, frame, thr, tmin = mcrt.face_geometry(m.verts, m.tris, m.tri_face, m.n_faces)
+    area, frame, thr, lift = mcrt.face_geometry(m.verts, m.tris, m.tri_face, m.n_faces)
     assert np.allclose(area, 1.0)
     n = frame[:, 2, :]
     assert np.allclose(n, [[1, 0, 0], [-1, 0, 0], [0, 1, 0], [0, -1, 0], [0, 0, 1], [0, 0, -1]])
@@ -99,7 +100,7 @@ def test_face_geometry():
     for f in range(6):
         R = frame[f].astype(np.float64)
         assert np.allclose(R @ R.T, np.eye(3), atol=1e-6)
-    assert abs(tmin - 1e-6 * math.sqrt(3)) < 1e-12
+    assert abs(lift - 1e-6 * math.sqrt(3)) < 1e-12
 
 
 def _stat_ok(F, ref, n_rays, k=5.0):
@@ -126,6 +127,17 @@ def test_cube_closed_forms_and_closure():
                 continue
             ref = opp if (min(i, j), max(i, j)) in pairs_opp else adj
             assert _stat_ok(F[i, j], ref, n), (i, j, F[i, j], ref)
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3, 4])
+def test_closed_cube_loses_no_ray(seed):
+    # rays born within ~1e-7 of an edge hit the adjacent wall at t ~ 1e-7: they must
+    # be counted (Sec. 3.5.4: MCRT accounts for every emitted ray)
+    m = synth.cube()
+    rays = np.full(6, 100_000, np.int64)
+    c = mcrt.trace_counts(m.verts, m.tris, m.tri_face, 6, rays, seed, use_bvh=False)
+    assert np.all(c[:, -1] == 0)
+    assert np.all(c.sum(axis=1) == rays)
 
 
 def test_brute_force_equals_bvh_bit_exact():
