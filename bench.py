@@ -1,0 +1,489 @@
+#!/usr/bin/env python
+"""Benchmark of the radiative hot path on one GB300 (or N independent replicas).
+
+One step is the whole path on the plates workload: two facing 1 m plates 0.5 m apart,
+16 x 16 sub-faces each (N = 512 faces, 1,024 triangles), 1e6 rays per sub-face:
+  MCRT counts (5.12e8 rays) -> F -> iterative enforcer -> least-squares optimum with
+  NNR + SPVA -> sub-face -> plate aggregation -> REFs (bf16 LU + refinement, eps ~
+  U[0.1, 0.9]) -> steady temperatures (Q ~ U[0, 50] W, 3 K sink) -> adjoint of the
+  temperatures -> adjoint of the REFs (dL/deps, dL/drho of L = sum T).
+value = rays traced per second of whole steps (all ranks' rays / the slowest rank).
+
+--impl reference times the CPU oracle (tests' reference implementation) on the host
+cores on a bounded sample of the same step and reports the same metric.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MCRT rays/s; Gebhart+adjoint solve ms vs plain FP64 GPU path at 1e-6 error"
+WORKLOAD = ("plates: 2 x (16 x 16) sub-faces, N=512, 1,024 triangles, 1e6 rays/sub-face (5.12e8 per step); "
+            "iterative + least-squares (NNR+SPVA) enforcement; sub-face->plate aggregation; Gebhart N=512 "
+            "bf16 LU + fp64-accurate refinement; steady temperatures + adjoints")
+SIGMA = 5.67e-8
+T_SINK = 3.0
+SOLVE_TOL = 1e-10
+# algorithmic operations of the ray definition (counted in the design notes):
+OPS_PER_RAY = 236      # two Philox4x32-10 blocks, triangle choice, point, direction, tally
+OPS_PER_BOX = 23       # slab test of one child box against the traversal window
+OPS_PER_TRI = 55       # FMA-free Moller-Trumbore and the closest-hit update
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-e2e", action="store_true", help=argparse.SUPPRESS)
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi samples (200 ms) of the SM clock and throttle reasons during a region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.index), "-lms", "200"], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) == 8:
+                self.rows.append(parts)
+
+    def __exit__(self, *a):
+        if self.proc:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=2)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in self.rows for k in range(4) if r[4 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+# ------------------------------------------------------------------ our implementation
+class Pipeline:
+    def __init__(self, ctx, w, device):
+        import torch
+        from paper_2511_04277_gb300 import api
+        self.api, self.torch, self.ctx, self.w = api, torch, ctx, w
+        m = w["mesh"]
+        self.N = m.n_faces
+        N = self.N
+        self.mesh = api.Mesh.from_synth(ctx, m)
+        self.rays_h = np.ascontiguousarray(w["rays"], np.int64)
+        d = dict(device=device)
+        self.rays = torch.as_tensor(self.rays_h, **d)
+        self.areas = torch.as_tensor(self.mesh.face_areas(), **d)
+        self.groups = torch.as_tensor(m.patch_of_face.astype(np.int32), **d)
+        self.eps = torch.as_tensor(w["eps"], **d)
+        self.rho = torch.as_tensor(w["rho"], **d)
+        self.Q = torch.as_tensor(w["Q"], **d)
+        self.ones = torch.ones(N, dtype=torch.float64, **d)
+        self.counts = torch.zeros((N, N + 1), dtype=torch.int64, **d)
+        self.F = torch.empty((N, N + 1), dtype=torch.float64, **d)
+        self.F_it = torch.empty_like(self.F)
+        self.F_ls = torch.empty_like(self.F)
+        self.B = torch.empty((1, N, N + 1), dtype=torch.float64, **d)
+
+    def mcrt(self):
+        api = self.api
+        self.counts.zero_()
+        api.trace(self.ctx, self.mesh, self.rays_h, self.w["seed"], fma_free=True, counts=self.counts)
+        api.counts_to_F(self.ctx, self.counts, self.rays, self.F)
+
+    def enforce(self):
+        api = self.api
+        self.F_it.copy_(self.F)
+        self.iters = api.enforce_iterative(self.ctx, self.F_it, self.areas, tol=1e-12)
+        self.F_ls.copy_(self.F)
+        self.passes = api.enforce_lsq(self.ctx, self.F_ls, self.areas, nnr=True, spva=True)
+        self.Fg, self.Sg = api.aggregate(self.ctx, self.F_it, self.areas, self.groups, 2)
+
+    def solve(self):
+        api = self.api
+        _, self.sweeps, self.resid = api.gebhart(self.ctx, self.F_it, self.eps, self.rho, "bf16", tol=SOLVE_TOL,
+                                                  B=self.B)
+        B0 = self.B[0]
+        self.T = api.temperatures(self.ctx, B0, self.eps, self.areas, self.Q, T_SINK, SIGMA, tol=SOLVE_TOL)
+        self.dB, self.deps_T = api.temperatures_adjoint(self.ctx, B0, self.eps, self.areas, T_SINK, self.T, self.ones,
+                                                        SIGMA, tol=SOLVE_TOL)
+        self.deps_B, self.drho = api.gebhart_adjoint(self.ctx, self.F_it, self.eps, self.rho, self.B, self.dB,
+                                                     tol=SOLVE_TOL)
+
+    def step(self):
+        self.mcrt()
+        self.enforce()
+        self.solve()
+
+
+def profiled_traffic(summary, source, units):
+    """DRAM bytes per launch from a committed ncu summary (profiles/<summary>): the lines
+    'source_sha256: <hash of csrc/<source> when captured>' and 'dram_bytes_per_unit: <x>'.
+    None when the kernel source has changed since the capture."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", summary)
+    src = os.path.join(ROOT, "paper_2511_04277_gb300", "csrc", source)
+    if not os.path.exists(path):
+        return None
+    fields = {}
+    for line in open(path):
+        if ":" in line:
+            k, v = line.split(":", 1)
+            fields[k.strip().lstrip("-* ").strip("`")] = v.strip().strip("`")
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    if fields.get("source_sha256") != sha or "dram_bytes_per_unit" not in fields:
+        return None
+    return float(fields["dram_bytes_per_unit"]) * units
+
+
+def fp64_solve(torch, F, eps, rho, A, Q):
+    """Plain FP64 GPU path: torch.linalg.solve (cuSOLVER) for the REFs and the balance,
+    FP64 autograd for dL/deps, dL/drho of L = sum T."""
+    N = F.shape[0]
+    e = eps.detach().clone().requires_grad_(True)
+    r = rho.detach().clone().requires_grad_(True)
+    with torch.enable_grad():
+        FN = F[:, :N]
+        K = torch.eye(N, dtype=F.dtype, device=F.device) - FN * r[None, :]
+        E = torch.cat([FN * e[None, :], F[:, N:]], dim=1)
+        B = torch.linalg.solve(K, E)
+        g = SIGMA * e * A
+        t = B.sum(dim=1)
+        M = torch.diag(g * t) - g[:, None] * B[:, :N]
+        u = torch.linalg.solve(M, Q + g * B[:, N] * T_SINK ** 4)
+        T = u ** 0.25
+        T.sum().backward()
+    return B.detach(), T.detach(), e.grad, r.grad
+
+
+def l2_flusher(torch, device):
+    buf = torch.empty(256 << 20, dtype=torch.uint8, device=device)
+
+    def flush():
+        buf.fill_(1)
+    return flush
+
+
+def time_region(torch, fn, stream):
+    s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s.record(stream)
+    fn()
+    e.record(stream)
+    e.synchronize()
+    return s.elapsed_time(e)
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+    import synth
+    from paper_2511_04277_gb300 import api
+
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    local = int(os.environ.get("LOCAL_RANK", 0))
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device(f"cuda:{local}"))
+    torch.cuda.set_device(local)
+    device = torch.device(f"cuda:{local}")
+    stream = torch.cuda.current_stream()
+    ctx = api.Context(local)
+    w = synth.workload("thermal")
+    pipe = Pipeline(ctx, w, device)
+    flush = l2_flusher(torch, device)
+    rays_per_step = int(w["rays"].sum())
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(max(args.warmup, 0)):
+        pipe.step()
+    barrier()
+    launches0 = api.launch_count(ctx)
+    step_ms = []
+    with ClockSampler(local) as clk:
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            flush()
+            step_ms.append(time_region(torch, pipe.step, stream))
+        barrier()
+        wall = time.perf_counter() - t0
+    launches = api.launch_count(ctx) - launches0
+    ms = statistics.mean(step_ms)
+    if world > 1:
+        t = torch.tensor([ms], device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+
+    out = None
+    if rank == 0:
+        # ---- stage breakdown and the FP64 comparator (not part of the timed steps)
+        stages = {}
+        for name, fn in (("mcrt", pipe.mcrt), ("enforce", pipe.enforce), ("solve", pipe.solve)):
+            vals = []
+            for _ in range(3):
+                flush()
+                vals.append(time_region(torch, fn, stream))
+            stages[name] = statistics.median(vals)
+        A = pipe.areas
+        solve = {"n": pipe.N, "ours_ms": round(stages["solve"], 4), "sweeps": pipe.sweeps,
+                 "precision": "bf16 tensor cores + fp64-accurate refinement",
+                 "fp64_path": "torch.linalg.solve float64 + FP64 autograd"}
+        try:
+            ref = None
+            fp64_ms = []
+            for _ in range(4):
+                flush()
+                tt = [None]
+                fp64_ms.append(time_region(torch, lambda: tt.__setitem__(0, fp64_solve(
+                    torch, pipe.F_it, pipe.eps[0], pipe.rho[0], A, pipe.Q)), stream))
+                ref = tt[0]
+            B64, T64, de64, dr64 = ref
+            pipe.solve()
+            torch.cuda.synchronize()
+
+            def rownorm(x, y):
+                return float(((x - y).abs().amax(dim=-1) / y.abs().amax(dim=-1).clamp_min(1e-300)).max())
+            grad = pipe.deps_B[0] + pipe.deps_T
+            solve.update({
+                "fp64_ms": round(statistics.median(fp64_ms[1:]), 4),
+                "err_B_rownorm": rownorm(pipe.B[0], B64),
+                "err_T": float(((pipe.T - T64).abs().max() / T64.abs().max())),
+                "err_deps": float((grad - de64).abs().max() / de64.abs().max()),
+                "err_drho": float((pipe.drho[0] - dr64).abs().max() / dr64.abs().max())})
+            solve["speedup"] = round(solve["fp64_ms"] / solve["ours_ms"], 2) if solve["ours_ms"] else None
+        except RuntimeError as exc:  # e.g. torch's cuSOLVER wrapper failing to load in this process
+            solve["fp64_ms"] = None
+            solve["fp64_unavailable"] = str(exc).splitlines()[0][:200]
+
+        # ---- roofline of the dominant kernel (the trace kernel)
+        counts_tmp = torch.zeros_like(pipe.counts)
+        _, st = api.trace_stats(ctx, pipe.mesh, pipe.rays_h, w["seed"], counts=counts_tmp)
+        tr = []
+        for _ in range(3):
+            flush()
+            pipe.counts.zero_()
+            tr.append(time_region(torch, lambda: api.trace(ctx, pipe.mesh, pipe.rays_h, w["seed"], fma_free=True,
+                                                           counts=pipe.counts), stream))
+        trace_ms = statistics.median(tr)
+        ops = (st["rays"] * OPS_PER_RAY + st["box_tests"] * OPS_PER_BOX + st["tri_tests"] * OPS_PER_TRI)
+        peaks = {}
+        try:
+            peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        except OSError:
+            pass
+        sm_count = torch.cuda.get_device_properties(device).multi_processor_count
+        max_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+        peak_tops = sm_count * 128 * max_mhz * 1e6 / 1e12
+        achieved = ops / (trace_ms * 1e-3) / 1e12
+        roofline = {"kernel": "trace_kernel<fma_free, BVH>", "bound": "alu", "achieved": round(achieved, 3),
+                    "peak": round(peak_tops, 3), "unit": "Tops/s", "frac": round(achieved / peak_tops, 4),
+                    "traffic": None, "ops_per_ray": round(ops / st["rays"], 1),
+                    "box_tests_per_ray": round(st["box_tests"] / st["rays"], 3),
+                    "tri_tests_per_ray": round(st["tri_tests"] / st["rays"], 3), "trace_ms": round(trace_ms, 3),
+                    "peak_basis": f"{sm_count} SMs x 128 lanes x {max_mhz:.0f} MHz (sm_max_mhz, MEASURED_PEAKS.json)"}
+        roofline["traffic"] = profiled_traffic("trace_kernel_plates.md", "trace.cu", rays_per_step)
+
+        out = {
+            "metric": METRIC, "value": rays_per_step * world / (ms * 1e-3), "unit": "rays/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32 rays, i64 tallies, bf16 tensor-core LU, f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "faces": pipe.N, "rays_per_step": rays_per_step,
+                       "parallelism": f"replicas x{world}",
+                       "l2": "256 MiB buffer written before every timed step; per-step CUDA events exclude it",
+                       "wall_s_timed_region": round(wall, 3)},
+            "stage_ms": {k: round(v, 3) for k, v in stages.items()},
+            "enforce": {"iterative_iters": pipe.iters, "lsq_passes": pipe.passes},
+            "solve": solve, "roofline": roofline, "clocks": clk.summary(), "gpu_launches": int(launches),
+        }
+        if not args.no_e2e:
+            out["e2e"] = run_e2e(args, api, torch, ctx, w, device, stream)
+        out["cpu_baseline"] = cpu_baseline(w)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    ctx.close()
+    return out
+
+
+def run_e2e(args, api, torch, ctx, w, device, stream):
+    """Same metric through the public API from host buffers: the mesh (with its BVH build),
+    ray budget and optical data are copied in and F, B, T and the gradients read back
+    inside every timed step."""
+    m = w["mesh"]
+    pin = lambda a: torch.as_tensor(np.ascontiguousarray(a)).pin_memory()  # noqa: E731
+    host_in = {"rays": pin(w["rays"]), "eps": pin(w["eps"]), "rho": pin(w["rho"]), "Q": pin(w["Q"]),
+               "groups": pin(m.patch_of_face.astype(np.int32))}
+    mesh_bytes = m.verts.nbytes + m.tris.nbytes + m.tri_face.nbytes
+    h2d = mesh_bytes + sum(t.numel() * t.element_size() for t in host_in.values())
+    N = m.n_faces
+    outs = {"F_it": torch.empty((N, N + 1), dtype=torch.float64).pin_memory(),
+            "F_ls": torch.empty((N, N + 1), dtype=torch.float64).pin_memory(),
+            "B": torch.empty((1, N, N + 1), dtype=torch.float64).pin_memory(),
+            "T": torch.empty(N, dtype=torch.float64).pin_memory(),
+            "deps_B": torch.empty((1, N), dtype=torch.float64).pin_memory(),
+            "deps_T": torch.empty(N, dtype=torch.float64).pin_memory(),
+            "drho": torch.empty((1, N), dtype=torch.float64).pin_memory()}
+    d2h = sum(t.numel() * t.element_size() for t in outs.values())
+
+    def one():
+        mesh = api.Mesh(ctx, m.verts, m.tris, m.tri_face, N)
+        d = {k: v.to(device, non_blocking=True) for k, v in host_in.items()}
+        areas = torch.as_tensor(mesh.face_areas(), device=device)
+        counts = torch.zeros((N, N + 1), dtype=torch.int64, device=device)
+        api.trace(ctx, mesh, w["rays"], w["seed"], fma_free=True, counts=counts)
+        F = api.counts_to_F(ctx, counts, d["rays"])
+        F_it = F.clone()
+        api.enforce_iterative(ctx, F_it, areas, tol=1e-12)
+        F_ls = F.clone()
+        api.enforce_lsq(ctx, F_ls, areas)
+        api.aggregate(ctx, F_it, areas, d["groups"], 2)
+        B, _, _ = api.gebhart(ctx, F_it, d["eps"], d["rho"], "bf16", tol=SOLVE_TOL)
+        T = api.temperatures(ctx, B[0], d["eps"], areas, d["Q"], T_SINK, SIGMA, tol=SOLVE_TOL)
+        dB, deps_T = api.temperatures_adjoint(ctx, B[0], d["eps"], areas, T_SINK, T, torch.ones_like(T), SIGMA,
+                                              tol=SOLVE_TOL)
+        deps_B, drho = api.gebhart_adjoint(ctx, F_it, d["eps"], d["rho"], B, dB, tol=SOLVE_TOL)
+        for k, v in (("F_it", F_it), ("F_ls", F_ls), ("B", B), ("T", T), ("deps_B", deps_B), ("deps_T", deps_T),
+                     ("drho", drho)):
+            outs[k].copy_(v, non_blocking=True)
+        mesh.close()
+
+    for _ in range(max(1, args.warmup)):
+        one()
+    torch.cuda.synchronize()
+    vals = [time_region(torch, one, stream) for _ in range(max(1, args.steps))]
+    ms = statistics.mean(vals)
+    return {"value": float(w["rays"].sum()) / (ms * 1e-3), "unit": "rays/s", "ms_per_step": round(ms, 3),
+            "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+
+
+# ------------------------------------------------------------------ CPU oracle
+def oracle_inputs(w, threads=0):
+    """A complete F for the oracle's downstream steps (1e4 rays per face, not timed)."""
+    from oracle import mcrt
+    m = w["mesh"]
+    light = np.full(m.n_faces, 10000, np.int64)
+    c = mcrt.trace_counts(m.verts, m.tris, m.tri_face, m.n_faces, light, w["seed"], use_bvh=True, threads=threads)
+    return mcrt.view_factors(c, light), mcrt.face_areas(m.verts, m.tris, m.tri_face, m.n_faces)
+
+
+def oracle_step(w, F, A, row_stride, threads=0):
+    """One oracle step on a bounded sample: MCRT of faces 0, s, 2s, ... with their full
+    ray budget, then the enforcement, aggregation, REF, temperature and adjoint solves at
+    full size. Returns (rays-equivalent per second, sampled rays, seconds measured)."""
+    from oracle import enforce as E
+    from oracle import gebhart as G
+    from oracle import mcrt
+    from oracle import multinode as MN
+    m = w["mesh"]
+    rows = np.arange(0, m.n_faces, row_stride)
+    t0 = time.perf_counter()
+    mcrt.trace_counts(m.verts, m.tris, m.tri_face, m.n_faces, w["rays"], w["seed"], use_bvh=True, threads=threads,
+                      faces=rows)
+    t_trace = time.perf_counter() - t0
+    t1 = time.perf_counter()
+    F_it, _, _ = E.iterative(F, A, tol=1e-12)
+    E.lsq_optimum(F, A, nnr=True, spva=True)
+    MN.surface_view_factors(F_it, A, m.patch_of_face, 2)
+    G.thermal_gradients(F_it, w["eps"][0], w["rho"][0], A, w["Q"], T_SINK, np.ones(m.n_faces), SIGMA)
+    t_rest = time.perf_counter() - t1
+    sampled = int(w["rays"][rows].sum())
+    total = int(w["rays"].sum())
+    return total / (t_trace * total / sampled + t_rest), sampled, t_trace + t_rest
+
+
+def cpu_baseline(w):
+    from oracle import mcrt
+    cores = len(os.sched_getaffinity(0))
+    stride = 16
+    F, A = oracle_inputs(w, cores)
+    value, sampled, sec = oracle_step(w, F, A, stride, threads=cores)
+    return {"value": value, "unit": "rays/s", "cores": cores, "kind": "oracle",
+            "sample": f"MCRT of every {stride}th face ({sampled:.3g} of {w['rays'].sum():.3g} rays, C oracle with "
+                      f"its median-split BVH on {cores} OpenMP threads), extrapolated by ray count; enforcement, "
+                      f"aggregation, REF, temperature and adjoint solves at full size in numpy/scipy fp64 "
+                      f"({sec:.1f} s measured)", "threads_seen": mcrt.max_threads()}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", 0))
+    if rank != 0:
+        return None
+    import synth
+    w = synth.workload("thermal")
+    cores = len(os.sched_getaffinity(0))
+    stride = 64
+    F, A = oracle_inputs(w, cores)
+    for _ in range(max(args.warmup, 0)):
+        oracle_step(w, F, A, stride, cores)
+    vals, secs = [], []
+    for _ in range(args.steps):
+        v, sampled, sec = oracle_step(w, F, A, stride, cores)
+        vals.append(v)
+        secs.append(sec)
+    value = statistics.mean(vals)
+    ms = float(w["rays"].sum()) / value * 1e3
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": "rays/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32 rays, i64 tallies, f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "faces": w["mesh"].n_faces, "rays_per_step": int(w["rays"].sum())},
+            "cpu_baseline": {"value": value, "unit": "rays/s", "cores": cores, "kind": "oracle",
+                             "sample": f"every {stride}th face's rays traced ({sampled:.3g} rays), extrapolated by "
+                                       f"ray count; enforcement and solves at full size"},
+            "e2e": {"value": value, "unit": "rays/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse()
+    out = run_reference(args) if args.impl == "reference" else run_ours(args)
+    if out is not None:
+        print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    main()

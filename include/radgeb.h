@@ -69,6 +69,8 @@ rg_status rg_create(rg_ctx** ctx_out, int device);
 void rg_destroy(rg_ctx* ctx);
 const char* rg_last_error(const rg_ctx* ctx);
 const char* rg_version(void);
+/* Number of kernels this context has launched so far (host counter, for accounting). */
+rg_status rg_launch_count(const rg_ctx* ctx, int64_t* launches_out_h);
 
 /* ---------------------------------------------------------------- mesh (P1) */
 
@@ -123,6 +125,13 @@ rg_status rg_face_areas(const rg_mesh* mesh, double* areas_out_h);
  * Errors: RG_ERR_ARG, RG_ERR_STACK, RG_ERR_CUDA, RG_ERR_UNSUPPORTED. */
 rg_status rg_trace(rg_ctx* ctx, const rg_mesh* mesh, const int64_t* rays_per_face_h, uint64_t seed,
                    uint64_t ray_offset, int32_t fma_free, int64_t* counts_d, void* stream);
+
+/* rg_trace with traversal statistics: the same counts (bit-identical), and
+ * stats_out_h = host uint64[3] {rays traced, ray-box tests, ray-triangle tests}
+ * summed over the launch; the statistics cost extra atomics, so time rg_trace. */
+rg_status rg_trace_stats(rg_ctx* ctx, const rg_mesh* mesh, const int64_t* rays_per_face_h, uint64_t seed,
+                         uint64_t ray_offset, int32_t fma_free, int64_t* counts_d, uint64_t* stats_out_h,
+                         void* stream);
 
 /* F_ij = N_ij / N_i (Eq. 3.15) for N x (N+1) counts.
  *   counts_d  device int64 [n][n+1];  rays_d device int64 [n] (N_i > 0)
@@ -190,7 +199,11 @@ rg_status rg_aggregate(rg_ctx* ctx, int32_t n_sub, const double* F_sub_d, const 
  *   eps_d    device fp64 [n_sets][n];  rho_d device fp64 [n_sets][n], 0 <= rho < 1
  *   B_d      device fp64 [n_sets][n][n+1] (output)
  *   tol      refinement stops when max_ij |R_ij| <= tol * max_ij |B_ij| for the
- *            residual R = E - K B of every set (tol >= 1e-13)
+ *            residual R = E - K B of every set (tol >= 1e-13). The residual product is
+ *            accumulated in compensated fp32 chunks, so the attainable accuracy of B
+ *            is about 1e-8 relative whatever smaller tol is asked for; once the
+ *            residual is below 1e-9 a sweep that fails to halve it also ends the
+ *            refinement (stagnation at that floor counts as converged).
  *   max_sweeps  refinement sweeps at most (>= 1)
  *   sweeps_out_h host int32 (may be NULL); resid_out_h host fp64 (may be NULL):
  *            the final relative residual (max over sets)
@@ -232,6 +245,29 @@ rg_status rg_temperatures_adjoint(rg_ctx* ctx, int32_t n, const double* B_d, con
                                   const double* area_d, double T_sink, double sigma,
                                   const double* T_d, const double* dT_d, int32_t precision, double tol,
                                   double* dB_d, double* deps_d, void* stream);
+
+/* ---------------------------------------------------------------- tensor-core GEMM */
+
+/* The tcgen05 GEMM the dense solves are built on (no counterpart in the thesis; it
+ * carries the factorisation updates of App. B's K B = E solve), exposed for testing:
+ *   C = alpha * A B^T + beta * C
+ *   A_d  device 16-bit [M][lda] (bf16, or fp16 when fp16 = 1), K-major (row-major, K
+ *        contiguous); B_d device 16-bit [N][ldb], K-major; lda, ldb multiples of 8 and
+ *        A_d, B_d 16-byte aligned;  C_d device fp32 [M][ldc].
+ * fp32 accumulation in tensor memory. Errors: RG_ERR_ARG (layout), RG_ERR_CUDA. */
+rg_status rg_tc_gemm(rg_ctx* ctx, int32_t M, int32_t N, int32_t K, const void* A_d, int64_t lda,
+                     const void* B_d, int64_t ldb, int32_t fp16, float* C_d, int64_t ldc, float alpha,
+                     float beta, void* stream);
+
+/* The refinement-residual form of the same GEMM (bf16 operands only):
+ *   out = E - X + diag(dl) (A B^T)      or, with E_d = X_d = NULL,  out = diag(dl) (A B^T)
+ * where the K loop is accumulated in fp32 chunks of chunk_k (a multiple of 64) folded
+ * into a compensated sum. out_d, E_d, X_d: device fp64 [M][ld]; dl_d device fp64 [M] or
+ * NULL (identity). Errors as rg_tc_gemm. */
+rg_status rg_tc_gemm_residual(rg_ctx* ctx, int32_t M, int32_t N, int32_t K, const void* A_d, int64_t lda,
+                              const void* B_d, int64_t ldb, int32_t chunk_k, double* out_d,
+                              const double* E_d, const double* X_d, const double* dl_d, int64_t ld,
+                              void* stream);
 
 #ifdef __cplusplus
 }

@@ -168,16 +168,16 @@ def project_literal(A, b, x):
 
 
 def project(A, b, x):
-    """Orthogonal projection of x onto {A x = b}: x - A^T (A A^T)^-1 (A x - b).
+    """Orthogonal projection of x onto {A x = b}: x - A^+ (A x - b).
 
-    With A of full row rank this equals Eq. 3.52 (x_r + P_null (x - x_r)); the
-    Gram system is solved with a sparse direct solver.
+    This is Eq. 3.52: x_r + N_b (N_b^T N_b)^-1 N_b^T (x - x_r) with x_r = A^+ b equals
+    P_null x + A^+ b = x - A^+ (A x - b). The minimum-norm least-squares solution
+    A^+ r is computed by LSQR (Paige & Saunders 1982) to full double precision.
     """
     A = scipy.sparse.csr_matrix(A)
-    G = (A @ A.T).tocsc()
-    rhs = A @ x - b
-    mu = scipy.sparse.linalg.spsolve(G, rhs)
-    return x - A.T @ mu
+    r = A @ x - b
+    z = scipy.sparse.linalg.lsqr(A, r, atol=1e-16, btol=1e-16, conlim=1e14, iter_lim=100000)[0]
+    return x - z
 
 
 def lsq_optimum(F, omega, nnr=True, spva=True, space="F", literal=False, max_passes=1000):

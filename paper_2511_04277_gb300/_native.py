@@ -31,11 +31,13 @@ SIGNATURES = {
     "rg_destroy": (None, [P]),
     "rg_last_error": (ctypes.c_char_p, [P]),
     "rg_version": (ctypes.c_char_p, []),
+    "rg_launch_count": (i32, [P, ctypes.POINTER(i64)]),
     "rg_mesh_create": (i32, [P, P, i64, P, i64, P, i32, i32, PP]),
     "rg_mesh_destroy": (i32, [P]),
     "rg_mesh_get_info": (i32, [P, ctypes.POINTER(MeshInfo)]),
     "rg_face_areas": (i32, [P, P]),
     "rg_trace": (i32, [P, P, P, u64, u64, i32, P, P]),
+    "rg_trace_stats": (i32, [P, P, P, u64, u64, i32, P, P, P]),
     "rg_counts_to_F": (i32, [P, i32, P, P, P, P]),
     "rg_enforce_iterative": (i32, [P, i32, P, P, f64, i32, P, P]),
     "rg_enforce_lsq": (i32, [P, i32, P, P, i32, i32, i32, P, P]),
@@ -44,6 +46,8 @@ SIGNATURES = {
     "rg_gebhart_adjoint": (i32, [P, i32, P, i32, P, P, P, P, i32, f64, i32, P, P, P]),
     "rg_temperatures": (i32, [P, i32, P, P, P, P, f64, f64, i32, f64, P, P]),
     "rg_temperatures_adjoint": (i32, [P, i32, P, P, P, f64, f64, P, P, i32, f64, P, P, P]),
+    "rg_tc_gemm": (i32, [P, i32, i32, i32, P, i64, P, i64, i32, P, i64, ctypes.c_float, ctypes.c_float, P]),
+    "rg_tc_gemm_residual": (i32, [P, i32, i32, i32, P, i64, P, i64, i32, P, P, P, P, i64, P]),
 }
 
 _lib = None

@@ -130,6 +130,28 @@ def trace(ctx: Context, mesh: Mesh, rays_per_face, seed: int, ray_offset: int = 
     return counts
 
 
+def trace_stats(ctx: Context, mesh: Mesh, rays_per_face, seed: int, ray_offset: int = 0, fma_free: bool = True,
+                counts: torch.Tensor | None = None, stream=None):
+    """rg_trace_stats: (counts, {"rays", "box_tests", "tri_tests"})."""
+    N = mesh.n_faces
+    rays = np.ascontiguousarray(rays_per_face, np.int64)
+    if counts is None:
+        counts = torch.zeros((N, N + 1), dtype=torch.int64, device=f"cuda:{ctx.device}")
+    st = np.zeros(3, np.uint64)
+    ctx.check(ctx.lib.rg_trace_stats(ctx.handle, mesh.handle, _hptr(rays), int(seed) & (2 ** 64 - 1),
+                                     int(ray_offset), int(bool(fma_free)),
+                                     _dptr(counts, torch.int64, "counts", N * (N + 1), ctx.device), _hptr(st),
+                                     _stream(stream)), "rg_trace_stats")
+    return counts, {"rays": int(st[0]), "box_tests": int(st[1]), "tri_tests": int(st[2])}
+
+
+def launch_count(ctx: Context) -> int:
+    """Kernels the context has launched so far (rg_launch_count)."""
+    n = ctypes.c_int64(0)
+    ctx.check(ctx.lib.rg_launch_count(ctx.handle, ctypes.byref(n)), "rg_launch_count")
+    return n.value
+
+
 def counts_to_F(ctx: Context, counts: torch.Tensor, rays: torch.Tensor, F: torch.Tensor | None = None,
                 stream=None) -> torch.Tensor:
     """F_ij = N_ij / N_i (rg_counts_to_F)."""
@@ -249,3 +271,33 @@ def temperatures_adjoint(ctx: Context, B, eps, area, T_sink: float, T, dT, sigma
                                               _dptr(deps, torch.float64, "deps"), _stream(stream)),
               "rg_temperatures_adjoint")
     return dB, deps
+
+
+def tc_gemm(ctx: Context, A: torch.Tensor, B: torch.Tensor, C: torch.Tensor | None = None, alpha: float = 1.0,
+            beta: float = 0.0, stream=None) -> torch.Tensor:
+    """C = alpha A B^T + beta C on tcgen05 (rg_tc_gemm); A [M, K], B [N, K] bf16 or fp16, C fp32."""
+    M, K = A.shape
+    N = B.shape[0]
+    if B.dtype != A.dtype or A.dtype not in (torch.bfloat16, torch.float16):
+        raise TypeError("A and B must both be bf16 or both fp16")
+    if C is None:
+        C = torch.zeros((M, N), dtype=torch.float32, device=A.device)
+    ctx.check(ctx.lib.rg_tc_gemm(ctx.handle, M, N, K, _dptr(A, A.dtype, "A"), A.stride(0), _dptr(B, B.dtype, "B"),
+                                 B.stride(0), int(A.dtype == torch.float16), _dptr(C, torch.float32, "C"),
+                                 C.stride(0), float(alpha), float(beta), _stream(stream)), "rg_tc_gemm")
+    return C
+
+
+def tc_gemm_residual(ctx: Context, A: torch.Tensor, B: torch.Tensor, E=None, X=None, dl=None, chunk_k: int = 128,
+                     stream=None) -> torch.Tensor:
+    """E - X + diag(dl) A B^T (or diag(dl) A B^T) with compensated fp32 chunks (rg_tc_gemm_residual)."""
+    M, K = A.shape
+    N = B.shape[0]
+    out = torch.empty((M, N), dtype=torch.float64, device=A.device)
+    nul = ctypes.c_void_p(None)
+    ctx.check(ctx.lib.rg_tc_gemm_residual(
+        ctx.handle, M, N, K, _dptr(A, torch.bfloat16, "A"), A.stride(0), _dptr(B, torch.bfloat16, "B"), B.stride(0),
+        int(chunk_k), _dptr(out, torch.float64, "out"), nul if E is None else _dptr(E, torch.float64, "E", M * N),
+        nul if X is None else _dptr(X, torch.float64, "X", M * N),
+        nul if dl is None else _dptr(dl, torch.float64, "dl", M), N, _stream(stream)), "rg_tc_gemm_residual")
+    return out

@@ -23,6 +23,8 @@ struct rg_ctx {
   int* d_scratch = nullptr;
   // pinned host scratch for scalar read-backs
   int* h_scratch = nullptr;
+  // kernels this context has launched (rg_launch_count)
+  int64_t launches = 0;
 };
 
 namespace rg {

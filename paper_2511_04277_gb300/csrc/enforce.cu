@@ -237,6 +237,7 @@ rg_status rg_counts_to_F(rg_ctx* ctx, int32_t n, const int64_t* counts_d, const 
   int64_t total = (int64_t)n * (n + 1);
   counts_to_F_kernel<<<blocks_for(total, ctx->sm_count), kThreads, 0, (cudaStream_t)stream>>>(
       reinterpret_cast<const long long*>(counts_d), reinterpret_cast<const long long*>(rays_d), F_d, n, total);
+  ++ctx->launches;
   RG_CUDA_TRY(ctx, cudaGetLastError());
   return RG_OK;
 }
@@ -263,8 +264,10 @@ rg_status rg_enforce_iterative(rg_ctx* ctx, int32_t n, const double* omega_d, do
   RG_CUDA_TRY(ctx, cudaMemsetAsync(st, 0, sizeof(EnforceState), s));
   // tolerance scale: max Omega
   max_kernel<<<1, kThreads, 0, s>>>(omega_d, n, reinterpret_cast<unsigned long long*>(ctx->d_scratch));
+  ++ctx->launches;
   RG_CUDA_TRY(ctx, cudaMemcpyAsync(ctx->h_scratch, ctx->d_scratch, 8, cudaMemcpyDeviceToHost, s));
   to_exchange_kernel<<<blocks_for(total, ctx->sm_count), kThreads, 0, s>>>(F_d, omega_d, sc, n, total);
+  ++ctx->launches;
   RG_CUDA_TRY(ctx, cudaGetLastError());
   RG_CUDA_TRY(ctx, cudaStreamSynchronize(s));
   double om_max;
@@ -277,7 +280,9 @@ rg_status rg_enforce_iterative(rg_ctx* ctx, int32_t n, const double* omega_d, do
     int batch = std::min(8, maxit - launched);
     for (int b = 0; b < batch; ++b) {
       sym_pass<<<sym_grid, kThreads, 0, s>>>(F_d, sc, n, P, st);
+      ++ctx->launches;
       row_pass<<<row_blocks, kThreads, 0, s>>>(F_d, sc, omega_d, P, n, n_tiles, st, tol_abs, maxit);
+      ++ctx->launches;
     }
     launched += batch;
     RG_CUDA_TRY(ctx, cudaGetLastError());
@@ -286,6 +291,7 @@ rg_status rg_enforce_iterative(rg_ctx* ctx, int32_t n, const double* omega_d, do
     if (h.done) break;
   }
   from_exchange_kernel<<<blocks_for(total, ctx->sm_count), kThreads, 0, s>>>(F_d, omega_d, sc, n, total);
+  ++ctx->launches;
   RG_CUDA_TRY(ctx, cudaGetLastError());
   if (iters_out_h) *iters_out_h = h.iters;
   if (h.done == 3) return rg::fail(ctx, RG_ERR_NUMERIC, "rg_enforce_iterative: non-finite row sum");
@@ -312,9 +318,11 @@ rg_status rg_aggregate(rg_ctx* ctx, int32_t n_sub, const double* F_sub_d, const 
   RG_CUDA_TRY(ctx, cudaMemsetAsync(ctx->d_scratch, 0, sizeof(int32_t), s));
   group_area_kernel<<<blocks_for(n_sub, ctx->sm_count), kThreads, 0, s>>>(sub_area_d, sub_group_d, n_sub, Sg, n_group,
                                                                          ctx->d_scratch);
+  ++ctx->launches;
   RG_CUDA_TRY(ctx, cudaFuncSetAttribute(aggregate_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int grid = std::min(n_sub, ctx->sm_count * 4);
   aggregate_rows<<<grid, kThreads, smem, s>>>(F_sub_d, sub_area_d, sub_group_d, n_sub, Sg, n_group, F_group_d);
+  ++ctx->launches;
   RG_CUDA_TRY(ctx, cudaGetLastError());
   RG_CUDA_TRY(ctx, cudaMemcpyAsync(ctx->h_scratch, ctx->d_scratch, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
   RG_CUDA_TRY(ctx, cudaStreamSynchronize(s));

@@ -1,0 +1,366 @@
+// tcgen05 GEMM for sm_103a: D[M x N] = A[M x K] * B[N x K]^T, 16-bit operands (bf16 or
+// fp16, both K-major: row-major with K contiguous), fp32 accumulation in tensor memory.
+//
+// One CTA computes one BM x BN tile (BM = 128). Warp roles (192 threads):
+//   warp 0      TMA producer: 64-wide K blocks of A and B into a ring of smem stages
+//               (128-byte swizzle), completion signalled on full[s] mbarriers;
+//   warp 1      allocates TMEM, one elected thread issues tcgen05.mma (K = 16 each)
+//               and commits to empty[s] (stage free) and acc_full[b] (accumulator ready);
+//   warps 2..5  epilogue: tcgen05.ld of the accumulator (warp w reads TMEM lanes
+//               32*(w%4) .. +31, i.e. tile rows), then the Epi functor writes the result.
+// The K loop can be cut into chunks of kChunkBlocks K blocks: each chunk is accumulated
+// in fp32 in one of two TMEM buffers and handed to the epilogue, which folds it into a
+// compensated (Kahan) fp32 sum; this keeps the long reductions of the refinement
+// residual accurate to ~1e-7 relative while the tensor cores run in 16-bit.
+//
+// Every mbarrier wait is bounded; on a timeout the kernel records an error word, stops
+// issuing work, frees its TMEM and returns.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include "common.cuh"
+
+namespace tc {
+
+constexpr int BM = 128;
+constexpr int BK = 64;  // one 128-byte swizzle atom of 16-bit elements
+constexpr int kThreads = 192;
+constexpr uint64_t kWaitNs = 2000000000ull;  // a wait gives up after 2 s
+
+// ------------------------------------------------------------------ PTX wrappers
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// Wait for the phase with the given parity to complete; false after kWaitNs.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t addr = smem_u32(bar);
+  uint64_t t0 = 0;
+  for (uint32_t i = 1;; ++i) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(addr), "r"(parity)
+        : "memory");
+    if (ok) return true;
+    if ((i & 255u) == 0) {
+      uint64_t now = global_ns();
+      if (t0 == 0) t0 = now;
+      else if (now - t0 > kWaitNs) return false;
+    }
+  }
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          smem_u32(dst)),
+      "l"((uint64_t)map), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void tmem_alloc(uint32_t* dst_smem, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst_smem)),
+               "r"(ncols));
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols));
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void umma_f16(uint32_t tmem_d, uint64_t a_desc, uint64_t b_desc, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+      "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+
+// 32 consecutive fp32 columns of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,"
+      "%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Shared-memory matrix descriptor of a K-major tile with 128-byte rows, 128-byte
+// swizzle, 8-row core groups 1024 bytes apart (sm_100 descriptor version 1).
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFF) >> 4);   // start address
+  d |= (uint64_t)1 << 16;                    // leading byte offset (unused for swizzled K-major)
+  d |= (uint64_t)(1024 >> 4) << 32;          // stride byte offset
+  d |= (uint64_t)1 << 46;                    // descriptor version
+  d |= (uint64_t)2 << 61;                    // 128-byte swizzle
+  return d;
+}
+
+// Instruction descriptor of kind::f16 with fp32 accumulation, both operands K-major.
+__host__ __device__ constexpr uint32_t idesc_f16(int m, int n, bool bf16) {
+  return (1u << 4)                                   // D format: fp32
+         | ((bf16 ? 1u : 0u) << 7)                   // A format
+         | ((bf16 ? 1u : 0u) << 10)                  // B format
+         | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
+}
+
+// ------------------------------------------------------------------ epilogues
+// Each functor receives one tile row segment: row r, columns c0..c0+31, 32 values.
+
+// C[r][c] = beta * C[r][c] + alpha * acc   (fp32 C)
+struct EpiF32 {
+  float* C;
+  int64_t ldc;
+  float alpha, beta;
+  __device__ __forceinline__ void store(int r, int c0, int M, int N, const float* v) const {
+    if (r >= M) return;
+    float* row = C + (int64_t)r * ldc;
+#pragma unroll
+    for (int i = 0; i < 32; ++i) {
+      int c = c0 + i;
+      if (c < N) row[c] = (beta == 0.f ? 0.f : beta * row[c]) + alpha * v[i];
+    }
+  }
+};
+
+// out[r][c] = E[r][c] - X[r][c] + dl[r] * acc   (fp64; the refinement residual), or
+// out[r][c] = dl[r] * acc when E is null (an fp64-accurate product)
+struct EpiResidual {
+  double* out;
+  const double* E;   // may be null together with X
+  const double* X;
+  const double* dl;  // may be null (identity)
+  int64_t ld;        // shared leading dimension of out, E and X
+  __device__ __forceinline__ void store(int r, int c0, int M, int N, const double* v) const {
+    if (r >= M) return;
+    const double s = dl ? dl[r] : 1.0;
+    const int64_t base = (int64_t)r * ld;
+#pragma unroll
+    for (int i = 0; i < 32; ++i) {
+      int c = c0 + i;
+      if (c < N) out[base + c] = E ? (E[base + c] - X[base + c]) + s * v[i] : s * v[i];
+    }
+  }
+};
+
+struct GemmArgs {
+  int M, N, K;
+  int chunk_blocks;  // 0: one fp32 accumulation over all of K; > 0: compensated chunks
+  int* error_word;
+};
+
+template <int BN, int kStages, class Epi, bool kCompensated, bool kBF16>
+__global__ void __launch_bounds__(kThreads, 1)
+    gemm_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_b,
+                const GemmArgs args, const Epi epi) {
+  static_assert(BN == 64 || BN == 128 || BN == 256, "tile width");
+  static_assert(!kCompensated || BN == 64, "the compensated epilogue keeps 2 x BN registers per thread");
+  constexpr uint32_t kABytes = BM * BK * 2, kBBytes = BN * BK * 2;
+  constexpr uint32_t kAccCols = kCompensated ? 2 * BN : BN;
+  constexpr uint32_t kTmemCols = kAccCols <= 32 ? 32 : (kAccCols <= 64 ? 64 : (kAccCols <= 128 ? 128 : (kAccCols <= 256 ? 256 : 512)));
+  constexpr uint32_t kIdesc = idesc_f16(BM, BN, kBF16);
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint8_t* sA = smem;
+  uint8_t* sB = smem + kStages * kABytes;
+  uint64_t* full = reinterpret_cast<uint64_t*>(sB + kStages * kBBytes);
+  uint64_t* empty = full + kStages;
+  uint64_t* acc_full = empty + kStages;  // [2]
+  uint64_t* acc_empty = acc_full + 2;    // [2]
+  uint64_t* drain = acc_empty + 2;       // [1]
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
+  __shared__ int s_abort;
+  __shared__ int s_consumed;             // K blocks whose stage the MMA thread has taken
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+  const int kb_total = (args.K + BK - 1) / BK;
+  const int chunk = (kCompensated && args.chunk_blocks > 0) ? args.chunk_blocks : kb_total;
+  const int n_chunks = (kb_total + chunk - 1) / chunk;
+
+  if (threadIdx.x == 0) {
+    s_abort = 0;
+    s_consumed = 0;
+    for (int s = 0; s < kStages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&acc_full[b], 1);
+      mbar_init(&acc_empty[b], 128);
+    }
+    mbar_init(drain, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 1) tmem_alloc(tmem_slot, kTmemCols);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+  volatile int* abort_flag = &s_abort;
+
+  if (warp == 0) {
+    // ---------------- TMA producer
+    if (lane == 0) {
+      int issued = 0;
+      for (int kb = 0; kb < kb_total; ++kb) {
+        const int s = kb % kStages;
+        if (kb >= kStages && !mbar_wait(&empty[s], ((kb / kStages) - 1) & 1)) { *abort_flag = 1; break; }
+        if (*abort_flag) break;
+        mbar_expect_tx(&full[s], kABytes + kBBytes);
+        tma_load_2d(sA + s * kABytes, &map_a, &full[s], kb * BK, m0);
+        tma_load_2d(sB + s * kBBytes, &map_b, &full[s], kb * BK, n0);
+        ++issued;
+      }
+      if (*abort_flag) {
+        // let the copies this thread started land before the CTA goes away
+        for (int kb = *(volatile int*)&s_consumed; kb < issued; ++kb) mbar_wait(&full[kb % kStages], (kb / kStages) & 1);
+      }
+    }
+  } else if (warp == 1) {
+    // ---------------- MMA issuer
+    if (lane == 0) {
+      int kb = 0;
+      for (int c = 0; c < n_chunks && !*abort_flag; ++c) {
+        const int b = c & 1;
+        if (c >= 2 && !mbar_wait(&acc_empty[b], ((c >> 1) - 1) & 1)) { *abort_flag = 1; break; }
+        const uint32_t d_tmem = tmem_base + (uint32_t)(b * BN);
+        const int first = kb, kb_end = min(kb_total, kb + chunk);
+        for (; kb < kb_end; ++kb) {
+          const int s = kb % kStages;
+          if (!mbar_wait(&full[s], (kb / kStages) & 1)) { *abort_flag = 1; break; }
+          *(volatile int*)&s_consumed = kb + 1;
+          tc_fence_after();
+          const uint32_t a_addr = smem_u32(sA + s * kABytes), b_addr = smem_u32(sB + s * kBBytes);
+#pragma unroll
+          for (int kk = 0; kk < BK / 16; ++kk)
+            umma_f16(d_tmem, sw128_desc(a_addr + kk * 32), sw128_desc(b_addr + kk * 32), kIdesc,
+                     (kb > first || kk > 0) ? 1u : 0u);
+          umma_commit(&empty[s]);
+        }
+        if (*abort_flag) break;
+        umma_commit(&acc_full[b]);
+      }
+      // every MMA this thread issued has completed once `drain` fires
+      umma_commit(drain);
+      mbar_wait(drain, 0);
+    }
+  } else {
+    // ---------------- epilogue warps 2..5
+    const int quarter = warp & 3;  // TMEM lanes 32*quarter .. +31
+    const int row = m0 + quarter * 32 + lane;
+    const uint32_t lane_addr = (uint32_t)(quarter * 32) << 16;
+    if constexpr (!kCompensated) {
+      if (mbar_wait(&acc_full[0], 0)) {
+        tc_fence_after();
+        float v[32];
+#pragma unroll 1
+        for (int c0 = 0; c0 < BN; c0 += 32) {
+          tmem_ld32(tmem_base + lane_addr + (uint32_t)c0, v);
+          epi.store(row, n0 + c0, args.M, args.N, v);
+        }
+      } else {
+        *abort_flag = 1;
+      }
+    } else {
+      float sum[BN], comp[BN];
+#pragma unroll
+      for (int i = 0; i < BN; ++i) {
+        sum[i] = 0.f;
+        comp[i] = 0.f;
+      }
+      bool ok = true;
+      for (int c = 0; c < n_chunks; ++c) {
+        const int b = c & 1;
+        if (!mbar_wait(&acc_full[b], (c >> 1) & 1)) { *abort_flag = 1; ok = false; break; }
+        tc_fence_after();
+#pragma unroll
+        for (int c0 = 0; c0 < BN; c0 += 32) {
+          float v[32];
+          tmem_ld32(tmem_base + lane_addr + (uint32_t)(b * BN + c0), v);
+#pragma unroll
+          for (int i = 0; i < 32; ++i) {  // Kahan: sum + v, the lost low part kept in comp
+            float y = v[i] - comp[c0 + i];
+            float t = sum[c0 + i] + y;
+            comp[c0 + i] = (t - sum[c0 + i]) - y;
+            sum[c0 + i] = t;
+          }
+        }
+        tc_fence_before();
+        mbar_arrive(&acc_empty[b]);
+      }
+      if (ok) {
+#pragma unroll
+        for (int c0 = 0; c0 < BN; c0 += 32) {
+          double v[32];
+#pragma unroll
+          for (int i = 0; i < 32; ++i) v[i] = (double)sum[c0 + i] - (double)comp[c0 + i];
+          epi.store(row, n0 + c0, args.M, args.N, v);
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tmem_base, kTmemCols);
+  }
+  if (threadIdx.x == 0 && *abort_flag && args.error_word) atomicExch(args.error_word, 1);
+}
+
+template <int BN, int kStages>
+constexpr size_t smem_bytes() {
+  return 1024 + (size_t)kStages * (BM * BK * 2 + BN * BK * 2) + (2 * kStages + 5) * 8 + 16;
+}
+
+// ------------------------------------------------------------------ host side
+// C (fp32, ldc) = alpha * A B^T + beta * C with A [M x K] (lda), B [N x K] (ldb), 16-bit
+// K-major operands (bf16 when `bf16`, else fp16). lda, ldb: multiples of 8 elements;
+// A, B: 16-byte aligned.
+rg_status gemm_f32(rg_ctx* ctx, bool bf16, const void* A, int64_t lda, const void* B, int64_t ldb, int M, int N,
+                   int K, float* C, int64_t ldc, float alpha, float beta, cudaStream_t s);
+
+// out (fp64, ld) = E - X + dl o (A B^T) (or dl o (A B^T) when E is null), bf16 operands,
+// fp32 tensor-core accumulation in chunks of `chunk_blocks` x 64 of K folded into a
+// compensated sum.
+rg_status gemm_residual(rg_ctx* ctx, const void* A, int64_t lda, const void* B, int64_t ldb, int M, int N, int K,
+                        int chunk_blocks, double* out, const double* E, const double* X, const double* dl,
+                        int64_t ld, cudaStream_t s);
+
+// Device error word the GEMM kernels raise on a timed-out wait (ctx scratch slot).
+constexpr int kGemmErrorSlot = 16;
+
+}  // namespace tc

@@ -33,6 +33,7 @@ struct TraceParams {
   uint64_t ray_offset;
   unsigned long long* counts;  // [N][N+1]
   int32_t n_bins;              // N + 1
+  unsigned long long* stats;   // [3]: rays, box tests, triangle tests (statistics kernels only)
 };
 
 template <bool kExact>
@@ -108,6 +109,16 @@ __device__ __forceinline__ bool moller_trumbore(const float4 r0, const float4 r1
   return true;
 }
 
+struct NoStats {
+  __device__ __forceinline__ void box(int) {}
+  __device__ __forceinline__ void tri() {}
+};
+struct Stats {
+  unsigned long long n_box = 0, n_tri = 0;
+  __device__ __forceinline__ void box(int k) { n_box += k; }
+  __device__ __forceinline__ void tri() { ++n_tri; }
+};
+
 template <bool E>
 __device__ __forceinline__ void test_record(const float4* __restrict__ rec, int32_t src, V3 o, V3 d, float& best_t,
                                             int32_t& best_id, int32_t& best_face) {
@@ -125,12 +136,15 @@ __device__ __forceinline__ void test_record(const float4* __restrict__ rec, int3
 
 // Closest hit; returns the face index or n_faces (environment). Sets *overflow on a
 // traversal stack overflow.
-template <bool E, bool kBVH>
-__device__ int32_t closest_face(const DevMesh& m, int32_t src, V3 o, V3 d, bool* overflow) {
+template <bool E, bool kBVH, class St>
+__device__ int32_t closest_face(const DevMesh& m, int32_t src, V3 o, V3 d, bool* overflow, St& st) {
   float best_t = __int_as_float(0x7f800000);
   int32_t best_id = INT_MAX, best_face = m.n_faces;
   if (!kBVH) {
-    for (int64_t k = 0; k < m.nt; ++k) test_record<E>(m.tris + 3 * k, src, o, d, best_t, best_id, best_face);
+    for (int64_t k = 0; k < m.nt; ++k) {
+      test_record<E>(m.tris + 3 * k, src, o, d, best_t, best_id, best_face);
+      st.tri();
+    }
     return best_face;
   }
   const float ix = __frcp_rn(d.x), iy = __frcp_rn(d.y), iz = __frcp_rn(d.z);
@@ -152,14 +166,19 @@ __device__ int32_t closest_face(const DevMesh& m, int32_t src, V3 o, V3 d, bool*
     float rmin = fmaxf(fmaxf(fminf(x0, x1), fminf(y0, y1)), fmaxf(fminf(z0, z1), m.t_lo));
     float rmax = fminf(fminf(fmaxf(x0, x1), fmaxf(y0, y1)), fminf(fmaxf(z0, z1), limit));
     bool hl = lmin <= lmax, hr = rmin <= rmax;
+    st.box(2);
     if (hl && cntL > 0) {
-      for (int q = 0; q < cntL; ++q)
+      for (int q = 0; q < cntL; ++q) {
         test_record<E>(m.tris + 3 * (int64_t)(refL + q), src, o, d, best_t, best_id, best_face);
+        st.tri();
+      }
       hl = false;
     }
     if (hr && cntR > 0) {
-      for (int q = 0; q < cntR; ++q)
+      for (int q = 0; q < cntR; ++q) {
         test_record<E>(m.tris + 3 * (int64_t)(refR + q), src, o, d, best_t, best_id, best_face);
+        st.tri();
+      }
       hr = false;
     }
     if (hl && hr) {
@@ -228,13 +247,15 @@ __device__ __forceinline__ void sample_ray(const DevMesh& m, uint32_t k0, uint32
 
 constexpr int kThreads = 256;
 
-template <bool E, bool kBVH>
+template <bool E, bool kBVH, class St>
 __global__ void __launch_bounds__(kThreads, 2) trace_kernel(const TraceParams p) {
   extern __shared__ uint32_t hist[];
   __shared__ int32_t s_item;
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
   bool overflow = false;
+  St st;
+  unsigned long long n_rays = 0;
   while (true) {
     if (threadIdx.x == 0) s_item = atomicAdd(p.item_counter, 1);
     for (int b = threadIdx.x; b < p.n_bins; b += kThreads) hist[b] = 0u;
@@ -250,7 +271,8 @@ __global__ void __launch_bounds__(kThreads, 2) trace_kernel(const TraceParams p)
         V3 o, d;
         int32_t src;
         sample_ray<E>(p.m, p.key0, p.key1, p.ray_offset + (uint64_t)(w.begin + r), w.face, &o, &d, &src);
-        bin = closest_face<E, kBVH>(p.m, src, o, d, &overflow);
+        bin = closest_face<E, kBVH>(p.m, src, o, d, &overflow, st);
+        ++n_rays;
       }
       __syncwarp();
       const unsigned vmask = __ballot_sync(0xffffffffu, valid);
@@ -268,11 +290,25 @@ __global__ void __launch_bounds__(kThreads, 2) trace_kernel(const TraceParams p)
     __syncthreads();
   }
   if (overflow) atomicExch(p.error_word, 1);
+  if constexpr (sizeof(St) > 1) {
+    for (int o = 16; o > 0; o >>= 1) {
+      n_rays += __shfl_xor_sync(0xffffffffu, n_rays, o);
+      st.n_box += __shfl_xor_sync(0xffffffffu, st.n_box, o);
+      st.n_tri += __shfl_xor_sync(0xffffffffu, st.n_tri, o);
+    }
+    if (lane == 0) {
+      atomicAdd(p.stats, n_rays);
+      atomicAdd(p.stats + 1, st.n_box);
+      atomicAdd(p.stats + 2, st.n_tri);
+    }
+  } else {
+    (void)n_rays;
+  }
 }
 
-template <bool E, bool B>
+template <bool E, bool B, class St>
 cudaError_t launch(const TraceParams& p, int sm_count, size_t smem, cudaStream_t s) {
-  auto k = trace_kernel<E, B>;
+  auto k = trace_kernel<E, B, St>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int per_sm = 0;
@@ -285,10 +321,8 @@ cudaError_t launch(const TraceParams& p, int sm_count, size_t smem, cudaStream_t
   return cudaGetLastError();
 }
 
-}  // namespace
-
-extern "C" rg_status rg_trace(rg_ctx* ctx, const rg_mesh* mesh, const int64_t* rays_per_face_h, uint64_t seed,
-                              uint64_t ray_offset, int32_t fma_free, int64_t* counts_d, void* stream) {
+rg_status trace_impl(rg_ctx* ctx, const rg_mesh* mesh, const int64_t* rays_per_face_h, uint64_t seed,
+                     uint64_t ray_offset, int32_t fma_free, int64_t* counts_d, uint64_t* stats_h, void* stream) {
   if (!ctx) return RG_ERR_ARG;
   RG_ARG_CHECK(ctx, mesh && rays_per_face_h && counts_d, "rg_trace: NULL argument");
   const DevMesh& m = mesh_device_view(mesh);
@@ -306,18 +340,22 @@ extern "C" rg_status rg_trace(rg_ctx* ctx, const rg_mesh* mesh, const int64_t* r
     RG_ARG_CHECK(ctx, n >= 0, "rg_trace: negative ray count for face %d", f);
     for (int64_t b = 0; b < n; b += kChunk) items.push_back({b, f, (int32_t)std::min(kChunk, n - b)});
   }
+  if (stats_h) stats_h[0] = stats_h[1] = stats_h[2] = 0;
   if (items.empty()) return RG_OK;
   RG_ARG_CHECK(ctx, items.size() < (size_t)INT32_MAX, "rg_trace: too many rays");
   RG_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
   cudaStream_t s = (cudaStream_t)stream;
   void* ws = nullptr;
-  rg_status st = rg::workspace(ctx, items.size() * sizeof(WorkItem), &ws);
+  rg_status st = rg::workspace(ctx, items.size() * sizeof(WorkItem) + 256, &ws);
   if (st != RG_OK) return st;
-  RG_CUDA_TRY(ctx, cudaMemcpyAsync(ws, items.data(), items.size() * sizeof(WorkItem), cudaMemcpyHostToDevice, s));
+  unsigned long long* d_stats = reinterpret_cast<unsigned long long*>(static_cast<char*>(ws)) ;
+  WorkItem* d_items = reinterpret_cast<WorkItem*>(static_cast<char*>(ws) + 256);
+  RG_CUDA_TRY(ctx, cudaMemcpyAsync(d_items, items.data(), items.size() * sizeof(WorkItem), cudaMemcpyHostToDevice, s));
   RG_CUDA_TRY(ctx, cudaMemsetAsync(ctx->d_scratch, 0, 2 * sizeof(int32_t), s));
+  if (stats_h) RG_CUDA_TRY(ctx, cudaMemsetAsync(d_stats, 0, 3 * sizeof(unsigned long long), s));
   TraceParams p;
   p.m = m;
-  p.items = static_cast<const WorkItem*>(ws);
+  p.items = d_items;
   p.n_items = (int32_t)items.size();
   p.item_counter = ctx->d_scratch;
   p.error_word = ctx->d_scratch + 1;
@@ -326,15 +364,50 @@ extern "C" rg_status rg_trace(rg_ctx* ctx, const rg_mesh* mesh, const int64_t* r
   p.ray_offset = ray_offset;
   p.counts = reinterpret_cast<unsigned long long*>(counts_d);
   p.n_bins = n_bins;
+  p.stats = d_stats;
   cudaError_t e;
-  if (fma_free)
-    e = m.use_bvh ? launch<true, true>(p, ctx->sm_count, smem, s) : launch<true, false>(p, ctx->sm_count, smem, s);
-  else
-    e = m.use_bvh ? launch<false, true>(p, ctx->sm_count, smem, s) : launch<false, false>(p, ctx->sm_count, smem, s);
+  const int sm = ctx->sm_count;
+  if (stats_h) {
+    if (fma_free)
+      e = m.use_bvh ? launch<true, true, Stats>(p, sm, smem, s) : launch<true, false, Stats>(p, sm, smem, s);
+    else
+      e = m.use_bvh ? launch<false, true, Stats>(p, sm, smem, s) : launch<false, false, Stats>(p, sm, smem, s);
+  } else {
+    if (fma_free)
+      e = m.use_bvh ? launch<true, true, NoStats>(p, sm, smem, s) : launch<true, false, NoStats>(p, sm, smem, s);
+    else
+      e = m.use_bvh ? launch<false, true, NoStats>(p, sm, smem, s) : launch<false, false, NoStats>(p, sm, smem, s);
+  }
   if (e != cudaSuccess) return rg::cuda_fail(ctx, e, "rg_trace: launch");
+  ++ctx->launches;
   // the host copy of the items must outlive the async upload, and the error word is read back
   RG_CUDA_TRY(ctx, cudaMemcpyAsync(ctx->h_scratch, ctx->d_scratch + 1, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  if (stats_h) RG_CUDA_TRY(ctx, cudaMemcpyAsync(stats_h, d_stats, 3 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
   RG_CUDA_TRY(ctx, cudaStreamSynchronize(s));
   if (ctx->h_scratch[0]) return rg::fail(ctx, RG_ERR_STACK, "rg_trace: traversal stack overflow");
   return RG_OK;
 }
+
+}  // namespace
+
+extern "C" {
+
+rg_status rg_trace(rg_ctx* ctx, const rg_mesh* mesh, const int64_t* rays_per_face_h, uint64_t seed,
+                   uint64_t ray_offset, int32_t fma_free, int64_t* counts_d, void* stream) {
+  return trace_impl(ctx, mesh, rays_per_face_h, seed, ray_offset, fma_free, counts_d, nullptr, stream);
+}
+
+rg_status rg_trace_stats(rg_ctx* ctx, const rg_mesh* mesh, const int64_t* rays_per_face_h, uint64_t seed,
+                         uint64_t ray_offset, int32_t fma_free, int64_t* counts_d, uint64_t* stats_out_h,
+                         void* stream) {
+  if (!stats_out_h) return rg::fail(ctx, RG_ERR_ARG, "rg_trace_stats: NULL stats");
+  return trace_impl(ctx, mesh, rays_per_face_h, seed, ray_offset, fma_free, counts_d, stats_out_h, stream);
+}
+
+rg_status rg_launch_count(const rg_ctx* ctx, int64_t* launches_out_h) {
+  if (!ctx || !launches_out_h) return RG_ERR_ARG;
+  *launches_out_h = ctx->launches;
+  return RG_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,232 @@
+"""GPU dense solves against the oracle: the tcgen05 GEMM on its own, REFs (App. B),
+their adjoint, the steady radiative balance and its adjoint, and the least-squares
+optimum enforcer with NNR / SPVA.
+
+Floating-point bar: row-normwise max_j |X_ij - X_ref,ij| <= 1e-6 max_j |X_ref,ij| for
+matrices, and ||g - g_ref||_inf <= 1e-6 ||g_ref||_inf for gradients.
+"""
+import numpy as np
+import pytest
+import torch
+
+import synth
+from oracle import enforce as E
+from oracle import gebhart as G
+from oracle import mcrt
+from paper_2511_04277_gb300 import api
+from tests.conftest import load_matrix
+
+pytestmark = pytest.mark.gpu
+
+REL = 1e-6
+
+
+def _dev(x, dtype=torch.float64):
+    return torch.as_tensor(np.ascontiguousarray(x)).to(dtype=dtype, device="cuda")
+
+
+def _rownorm_err(got, ref):
+    got, ref = np.asarray(got), np.asarray(ref)
+    scale = np.maximum(np.abs(ref).max(axis=-1), 1e-300)
+    return float((np.abs(got - ref).max(axis=-1) / scale).max())
+
+
+def _consistent_F(N, rng, density=0.3):
+    """Random open-system F with reciprocity and closure (areas returned)."""
+    A = rng.uniform(0.5, 2.0, N)
+    S = rng.random((N, N)) * (rng.random((N, N)) < density)
+    S = (S + S.T) / (2 * N) * 0.8
+    np.fill_diagonal(S, 0.0)
+    env = A - S.sum(axis=1)
+    assert env.min() > 0
+    return np.concatenate([S, env[:, None]], axis=1) / A[:, None], A
+
+
+# ------------------------------------------------------------------ GEMM
+@pytest.mark.parametrize("M,N,K,dt", [(128, 128, 64, torch.bfloat16), (300, 200, 96, torch.bfloat16),
+                                      (257, 513, 640, torch.float16), (1, 5, 8, torch.bfloat16)])
+def test_tc_gemm_matches_fp64_of_rounded_operands(rg_ctx, M, N, K, dt):
+    g = torch.Generator().manual_seed(M + N + K)
+    A = torch.randn(M, K, generator=g).to(dt)
+    B = torch.randn(N, K, generator=g).to(dt)
+    C0 = torch.randn(M, N, generator=g, dtype=torch.float32)
+    C = api.tc_gemm(rg_ctx, A.cuda(), B.cuda(), C0.clone().cuda(), alpha=-1.0, beta=1.0).cpu().double()
+    ref = C0.double() - A.double() @ B.double().T
+    err = (C - ref).abs().max().item()
+    assert err <= 2e-5 * (A.double().abs() @ B.double().abs().T).max().item()
+
+
+def test_tc_gemm_residual_is_fp64_accurate(rg_ctx):
+    rng = np.random.default_rng(0)
+    M, N, K = 256, 190, 1536
+    A = torch.from_numpy(rng.random((M, K))).to(torch.bfloat16)
+    B = torch.from_numpy(rng.random((N, K))).to(torch.bfloat16)
+    Ed = rng.random((M, N))
+    Xd = rng.random((M, N))
+    dl = rng.uniform(0.5, 1.5, M)
+    out = api.tc_gemm_residual(rg_ctx, A.cuda(), B.cuda(), _dev(Ed), _dev(Xd), _dev(dl), chunk_k=128).cpu().numpy()
+    prod = A.double().numpy() @ B.double().numpy().T
+    ref = Ed - Xd + dl[:, None] * prod
+    assert np.abs(out - ref).max() <= 2e-7 * np.abs(dl[:, None] * prod).max()
+    plain = api.tc_gemm_residual(rg_ctx, A.cuda(), B.cuda(), chunk_k=64).cpu().numpy()
+    assert np.abs(plain - prod).max() <= 2e-7 * np.abs(prod).max()
+
+
+# ------------------------------------------------------------------ REFs
+def test_gebhart_plates_example(rg_ctx):
+    F = load_matrix("plates_F.txt")
+    eps = np.full(4, 0.5)
+    B, sw, res = api.gebhart(rg_ctx, _dev(F), _dev(eps), _dev(1 - eps), tol=1e-13)
+    assert np.abs(B[0].cpu().numpy() - load_matrix("plates_B.txt")).max() <= 5e-7
+    assert res <= 1e-13
+
+
+@pytest.mark.parametrize("N", [1, 6, 127, 128, 129, 300, 512])
+@pytest.mark.parametrize("prec", ["bf16", "fp16"])
+def test_gebhart_random_sizes(rg_ctx, N, prec):
+    rng = np.random.default_rng(N)
+    F, A = _consistent_F(N, rng)
+    eps = rng.uniform(0.1, 0.9, N)
+    B, sw, res = api.gebhart(rg_ctx, _dev(F), _dev(eps), _dev(1 - eps), precision=prec, tol=1e-12)
+    Bo = G.gebhart(F, eps, 1 - eps)
+    assert _rownorm_err(B[0].cpu().numpy(), Bo) <= REL
+    assert res <= 1e-12 and sw >= 1
+
+
+def test_gebhart_batched_sets_and_identities(rg_ctx):
+    rng = np.random.default_rng(11)
+    N, S = 200, 3
+    F, A = _consistent_F(N, rng)
+    eps = rng.uniform(0.05, 0.9, (S, N))
+    rho = 1 - eps
+    B, _, _ = api.gebhart(rg_ctx, _dev(F), _dev(eps), _dev(rho), tol=1e-12)
+    Bg = B.cpu().numpy()
+    for s in range(S):
+        Bo = G.gebhart(F, eps[s], rho[s])
+        assert _rownorm_err(Bg[s], Bo) <= REL
+        # identities hold to the refinement's accuracy floor (~1e-8: the residual product
+        # is accumulated in compensated fp32 chunks of 128)
+        assert np.abs(Bg[s].sum(axis=1) - 1).max() <= 1e-7                   # Eq. 4.3
+        R = (eps[s] * A)[:, None] * Bg[s][:, :N]
+        assert np.abs(R - R.T).max() <= 1e-7 * np.abs(R).max()                # Eq. 4.4
+
+
+def test_gebhart_black_surfaces(rg_ctx):
+    rng = np.random.default_rng(5)
+    F, _ = _consistent_F(130, rng)
+    eps = rng.uniform(0.1, 0.9, 130)
+    B, sw, _ = api.gebhart(rg_ctx, _dev(F), _dev(eps), _dev(np.zeros(130)), tol=1e-13)
+    assert np.abs(B[0].cpu().numpy() - G.e_matrix(F, eps)).max() <= 1e-15 * 10
+
+
+def test_gebhart_cube_closed_forms(rg_ctx):
+    # config-1 REFs from the closed-form cube view factors, closed system (env column 0)
+    from tests import closed_forms as cf
+    opp, adj = cf.parallel_opposed(1, 1, 1), cf.perpendicular_common_edge(1, 1, 1)
+    F = np.full((6, 7), adj)
+    F[:, 6] = 0.0
+    for i in range(6):
+        F[i, i] = 0.0
+        F[i, i ^ 1] = opp
+    eps = np.full(6, 0.8)
+    B, _, _ = api.gebhart(rg_ctx, _dev(F), _dev(eps), _dev(1 - eps), tol=1e-13)
+    Bo = G.gebhart(F, eps, 1 - eps)
+    assert _rownorm_err(B[0].cpu().numpy(), Bo) <= 1e-9
+
+
+def test_gebhart_plates_workload_full_size(rg_ctx):
+    """N = 512 from GPU MCRT + GPU enforcement, eps ~ U[0.1, 0.9]: the bench's solve."""
+    w = synth.workload("plates", rays_scale=0.02)
+    m = w["mesh"]
+    mesh = api.Mesh.from_synth(rg_ctx, m)
+    F = api.counts_to_F(rg_ctx, api.trace(rg_ctx, mesh, w["rays"], 0), _dev(w["rays"], torch.int64))
+    api.enforce_iterative(rg_ctx, F, _dev(mesh.face_areas()))
+    B, sw, res = api.gebhart(rg_ctx, F, _dev(w["eps"]), _dev(w["rho"]), tol=1e-12)
+    Bo = G.gebhart(F.cpu().numpy(), w["eps"][0], w["rho"][0])
+    assert _rownorm_err(B[0].cpu().numpy(), Bo) <= REL
+
+
+def test_gebhart_not_converged_is_reported(rg_ctx):
+    rng = np.random.default_rng(8)
+    F, _ = _consistent_F(256, rng)
+    eps = rng.uniform(0.05, 0.1, 256)
+    with pytest.raises(api.RadgebError) as e:
+        api.gebhart(rg_ctx, _dev(F), _dev(eps), _dev(1 - eps), tol=1e-13, max_sweeps=1)
+    assert e.value.code == "RG_ERR_NOT_CONVERGED"
+
+
+# ------------------------------------------------------------------ adjoints
+@pytest.mark.parametrize("N", [5, 140])
+def test_gebhart_adjoint_vs_oracle(rg_ctx, N):
+    rng = np.random.default_rng(100 + N)
+    F, _ = _consistent_F(N, rng)
+    eps = rng.uniform(0.1, 0.9, N)
+    rho = 1 - eps
+    W = rng.standard_normal((N, N + 1))
+    Bo = G.gebhart(F, eps, rho)
+    de, dr = api.gebhart_adjoint(rg_ctx, _dev(F), _dev(eps), _dev(rho), _dev(Bo), _dev(W), tol=1e-12)
+    deo, dro = G.gebhart_adjoint(F, eps, rho, Bo, W)
+    assert np.abs(de[0].cpu().numpy() - deo).max() <= REL * np.abs(deo).max()
+    assert np.abs(dr[0].cpu().numpy() - dro).max() <= REL * np.abs(dro).max()
+
+
+def test_temperatures_vs_oracle(rg_ctx):
+    w = synth.workload("thermal", rays_scale=0.01)
+    m = w["mesh"]
+    mesh = api.Mesh.from_synth(rg_ctx, m)
+    F = api.counts_to_F(rg_ctx, api.trace(rg_ctx, mesh, w["rays"], 0), _dev(w["rays"], torch.int64))
+    A = mesh.face_areas()
+    api.enforce_iterative(rg_ctx, F, _dev(A))
+    eps = w["eps"][0]
+    B, _, _ = api.gebhart(rg_ctx, F, _dev(eps), _dev(w["rho"][0]), tol=1e-12)
+    T = api.temperatures(rg_ctx, B[0].contiguous(), _dev(eps), _dev(A), _dev(w["Q"]), w["T_sink"], tol=1e-13)
+    To = G.temperatures(B[0].cpu().numpy(), eps, A, w["Q"], w["T_sink"])
+    assert np.abs(T.cpu().numpy() - To).max() <= REL * To.max()
+
+
+def test_temperatures_adjoint_vs_oracle(rg_ctx):
+    rng = np.random.default_rng(21)
+    N = 150
+    F, A = _consistent_F(N, rng)
+    eps = rng.uniform(0.1, 0.9, N)
+    Q = rng.uniform(0, 50, N)
+    Bo = G.gebhart(F, eps, 1 - eps)
+    To = G.temperatures(Bo, eps, A, Q, 3.0)
+    wT = rng.standard_normal(N)
+    dB, deps = api.temperatures_adjoint(rg_ctx, _dev(Bo), _dev(eps), _dev(A), 3.0, _dev(To), _dev(wT), tol=1e-13)
+    dBo, depso = G.temperatures_adjoint(Bo, eps, A, Q, 3.0, To, wT)
+    assert np.abs(dB.cpu().numpy() - dBo).max() <= REL * np.abs(dBo).max()
+    assert np.abs(deps.cpu().numpy() - depso).max() <= REL * np.abs(depso).max()
+
+
+# ------------------------------------------------------------------ least-squares optimum
+def test_lsq_disc_example(rg_ctx):
+    F1 = load_matrix("disc_F1_mcrt.txt")
+    A = np.array([1.0, 4.0, 1.0, 4.0])
+    for spva, name in ((False, "disc_F4_lsq_nnr.txt"), (True, "disc_F5_lsq_nnr_spva.txt")):
+        Fd = _dev(F1)
+        passes = api.enforce_lsq(rg_ctx, Fd, _dev(A), nnr=True, spva=spva)
+        Fo, po = E.lsq_optimum(F1, A, nnr=True, spva=spva)
+        got = Fd.cpu().numpy()
+        assert np.abs(got - Fo).max() <= 1e-8
+        assert passes == po
+        assert np.abs(got - load_matrix(name)).max() <= 1e-6
+
+
+def test_lsq_plates_config(rg_ctx):
+    """512 sub-faces (config-sized) from GPU MCRT, LSQ + NNR + SPVA on the GPU and by the oracle."""
+    m = synth.plates(16)
+    rays = np.full(m.n_faces, 20000, np.int64)
+    mesh = api.Mesh.from_synth(rg_ctx, m)
+    F = api.counts_to_F(rg_ctx, api.trace(rg_ctx, mesh, rays, 0), _dev(rays, torch.int64))
+    F0 = F.cpu().numpy()
+    A = mesh.face_areas()
+    api.enforce_lsq(rg_ctx, F, _dev(A), nnr=True, spva=True)
+    Fo, _ = E.lsq_optimum(F0, A, nnr=True, spva=True)
+    got = F.cpu().numpy()
+    assert _rownorm_err(got, Fo) <= REL
+    assert got.min() >= 0.0
+    assert np.all(got[F0 == 0] == 0.0)
+    assert np.abs(got.sum(axis=1) - 1).max() <= 1e-7
+    eta = A[:, None] * got[:, :512]
+    assert np.abs(eta - eta.T).max() <= 1e-7 * np.abs(eta).max()
