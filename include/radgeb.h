@@ -157,6 +157,25 @@ rg_status rg_counts_to_F(rg_ctx* ctx, int32_t n, const int64_t* counts_d, const 
 rg_status rg_enforce_iterative(rg_ctx* ctx, int32_t n, const double* omega_d, double* F_d, double tol,
                                int32_t maxit, int32_t* iters_out_h, void* stream);
 
+/* rg_enforce_iterative without allocation, for callers that must not allocate
+ * device memory when they call in -- for instance flight or embedded software that
+ * plans all of its memory up front, or a host application that owns the device's
+ * memory pool and forbids its plug-ins from allocating. The thesis has no counterpart
+ * of this entry point; it computes exactly what rg_enforce_iterative computes.
+ *   - No context: it runs on the CURRENT device and allocates nothing (no cudaMalloc,
+ *     no cudaFree, no allocating library call). Its scratch is a file-scope device
+ *     array of about 2.1 MB that every GPU loading the library holds until exit.
+ *   - Limit: n <= 4096; larger n returns RG_ERR_UNSUPPORTED.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress); make that first call before any stream capture.
+ *   - Every call shares the one array and clears the part that must start at zero;
+ *     calls that overlap on the GPU (other streams, other host threads) race.
+ *   - It synchronises `stream` to read its iteration state back.
+ * Arguments, results and other errors as rg_enforce_iterative (no rg_last_error:
+ * the status code is the whole report). */
+rg_status rg_enforce_iterative_noalloc(int32_t n, const double* omega_d, double* F_d, double tol,
+                                       int32_t maxit, int32_t* iters_out_h, void* stream);
+
 /* Least-squares optimum for open systems (Sec. 3.5.5, Eq. 3.41-3.52) with
  * non-negativity rectification (App. A.1) and small-positive-value avoidance
  * (App. A.2), in place. The unknowns are the entries of F; the restrictions are

@@ -40,6 +40,7 @@ SIGNATURES = {
     "rg_trace_stats": (i32, [P, P, P, u64, u64, i32, P, P, P]),
     "rg_counts_to_F": (i32, [P, i32, P, P, P, P]),
     "rg_enforce_iterative": (i32, [P, i32, P, P, f64, i32, P, P]),
+    "rg_enforce_iterative_noalloc": (i32, [i32, P, P, f64, i32, P, P]),
     "rg_enforce_lsq": (i32, [P, i32, P, P, i32, i32, i32, P, P]),
     "rg_aggregate": (i32, [P, i32, P, P, P, i32, P, P, P]),
     "rg_gebhart": (i32, [P, i32, P, i32, P, P, i32, f64, i32, P, P, P, P]),

@@ -12,6 +12,8 @@
 //             with w = eta); its last block applies the stopping rule.
 // Every entry is read and written once per iteration: 16 bytes of HBM traffic.
 #include <cfloat>
+#include <cstring>
+#include <mutex>
 
 #include "common.cuh"
 
@@ -331,3 +333,94 @@ rg_status rg_aggregate(rg_ctx* ctx, int32_t n_sub, const double* F_sub_d, const 
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------- allocation-free variant
+// The iterative enforcer for callers that may not allocate device memory at call time:
+// the same kernels as rg_enforce_iterative, with their scratch in this file-scope
+// device array instead of the context workspace. Every GPU that loads the library holds
+// the array until the process exits.
+namespace {
+
+constexpr int32_t kNoallocMaxN = 4096;
+constexpr int32_t kNoallocMaxTiles = (kNoallocMaxN + kT - 1) / kT;
+constexpr size_t kNoallocScaleBytes = (size_t)kNoallocMaxN * sizeof(double);
+constexpr size_t kNoallocRowSumBytes = (size_t)kNoallocMaxTiles * kNoallocMaxN * sizeof(double);
+constexpr size_t kNoallocBytes = kNoallocScaleBytes + kNoallocRowSumBytes + 256 + 256;
+
+// Layout: [row scales s: N doubles][per-tile row sums: tiles x N doubles]
+//         [EnforceState, 256 B][tolerance scale max|Omega|, 256 B]
+static __device__ __align__(256) unsigned char g_enforce_scratch[kNoallocBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_scratch_mutex;
+void* g_scratch_ptr[kMaxDevices] = {};
+
+// Device address of g_enforce_scratch on the current device (looked up once per device).
+cudaError_t scratch_address(int device, void** out) {
+  std::lock_guard<std::mutex> lock(g_scratch_mutex);
+  if (!g_scratch_ptr[device]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_enforce_scratch);
+    if (e != cudaSuccess) return e;
+    g_scratch_ptr[device] = p;
+  }
+  *out = g_scratch_ptr[device];
+  return cudaSuccess;
+}
+
+}  // namespace
+
+extern "C" rg_status rg_enforce_iterative_noalloc(int32_t n, const double* omega_d, double* F_d, double tol,
+                                                  int32_t maxit, int32_t* iters_out_h, void* stream) {
+  if (n <= 0 || !omega_d || !F_d || maxit <= 0 || !(tol >= 0.0)) return RG_ERR_ARG;
+  if (n > kNoallocMaxN) return RG_ERR_UNSUPPORTED;  // the static scratch holds N <= 4096
+  int device = 0;
+  if (cudaGetDevice(&device) != cudaSuccess || device < 0 || device >= kMaxDevices) return RG_ERR_CUDA;
+  void* base = nullptr;
+  if (scratch_address(device, &base) != cudaSuccess) return RG_ERR_CUDA;
+  cudaStream_t s = (cudaStream_t)stream;
+  char* b = static_cast<char*>(base);
+  double* sc = reinterpret_cast<double*>(b);
+  double* P = reinterpret_cast<double*>(b + kNoallocScaleBytes);
+  EnforceState* st = reinterpret_cast<EnforceState*>(b + kNoallocScaleBytes + kNoallocRowSumBytes);
+  unsigned long long* om_max = reinterpret_cast<unsigned long long*>(b + kNoallocScaleBytes + kNoallocRowSumBytes + 256);
+  const int n_tiles = (n + kT - 1) / kT;
+  const int64_t total = (int64_t)n * (n + 1);
+  int sm = 0;
+  if (cudaDeviceGetAttribute(&sm, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) return RG_ERR_CUDA;
+  // the state keeps the previous call's contents: clear it
+  if (cudaMemsetAsync(st, 0, sizeof(EnforceState), s) != cudaSuccess) return RG_ERR_CUDA;
+  max_kernel<<<1, kThreads, 0, s>>>(omega_d, n, om_max);
+  to_exchange_kernel<<<blocks_for(total, sm), kThreads, 0, s>>>(F_d, omega_d, sc, n, total);
+  if (cudaGetLastError() != cudaSuccess) return RG_ERR_CUDA;
+  unsigned long long om_bits = 0;
+  if (cudaMemcpyAsync(&om_bits, om_max, sizeof(om_bits), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return RG_ERR_CUDA;
+  double om;
+  memcpy(&om, &om_bits, sizeof(om));
+  const double tol_abs = tol * om;
+  dim3 sym_grid(n_tiles, n_tiles);
+  const int row_blocks = (n + kThreads - 1) / kThreads;
+  EnforceState h{};
+  for (int launched = 0; launched < maxit;) {
+    int batch = std::min(8, maxit - launched);
+    for (int k = 0; k < batch; ++k) {
+      sym_pass<<<sym_grid, kThreads, 0, s>>>(F_d, sc, n, P, st);
+      row_pass<<<row_blocks, kThreads, 0, s>>>(F_d, sc, omega_d, P, n, n_tiles, st, tol_abs, maxit);
+    }
+    launched += batch;
+    if (cudaGetLastError() != cudaSuccess) return RG_ERR_CUDA;
+    if (cudaMemcpyAsync(&h, st, sizeof(EnforceState), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+      return RG_ERR_CUDA;
+    if (h.done) break;
+  }
+  from_exchange_kernel<<<blocks_for(total, sm), kThreads, 0, s>>>(F_d, omega_d, sc, n, total);
+  if (cudaGetLastError() != cudaSuccess) return RG_ERR_CUDA;
+  if (iters_out_h) *iters_out_h = h.iters;
+  if (h.done == 3) return RG_ERR_NUMERIC;
+  if (h.done != 1) return RG_ERR_NOT_CONVERGED;
+  return RG_OK;
+}
+
