@@ -8,6 +8,9 @@
 namespace tc {
 namespace {
 
+rg_status encode_kmajor(rg_ctx* ctx, CUtensorMap* map, const void* base, bool bf16, int64_t rows, int64_t cols,
+                        int64_t ld, int box_rows);
+
 PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
 std::once_flag g_once;
 
@@ -41,6 +44,44 @@ rg_status encode_kmajor(rg_ctx* ctx, CUtensorMap* map, const void* base, bool bf
   if (r != CUDA_SUCCESS) return rg::fail(ctx, RG_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
   return RG_OK;
 }
+
+template <int BN, int kStages, class Epi, bool kComp, bool kBF16>
+rg_status launch(rg_ctx* ctx, const CUtensorMap& ma, const CUtensorMap& mb, const GemmArgs& args, const Epi& epi,
+                 cudaStream_t s);
+
+}  // namespace
+
+template <class Epi>
+rg_status gemm(rg_ctx* ctx, bool bf16, const void* A, int64_t lda, const void* B, int64_t ldb, int M, int N, int K,
+               const Epi& epi, cudaStream_t s) {
+  if (M <= 0 || N <= 0) return RG_OK;
+  if (K <= 0) return rg::fail(ctx, RG_ERR_ARG, "gemm: K = %d", K);
+  // 64-wide tiles when 128-wide ones would leave most SMs idle
+  const bool narrow = (int64_t)((M + BM - 1) / BM) * ((N + 127) / 128) < 2 * ctx->sm_count;
+  CUtensorMap ma, mb;
+  rg_status st = encode_kmajor(ctx, &ma, A, bf16, M, K, lda, BM);
+  if (st == RG_OK) st = encode_kmajor(ctx, &mb, B, bf16, N, K, ldb, narrow ? 64 : 128);
+  if (st != RG_OK) return st;
+  GemmArgs args{M, N, K, 0, ctx->d_scratch + kGemmErrorSlot};
+  if (narrow)
+    return bf16 ? launch<64, 6, Epi, false, true>(ctx, ma, mb, args, epi, s)
+                : launch<64, 6, Epi, false, false>(ctx, ma, mb, args, epi, s);
+  return bf16 ? launch<128, 4, Epi, false, true>(ctx, ma, mb, args, epi, s)
+              : launch<128, 4, Epi, false, false>(ctx, ma, mb, args, epi, s);
+}
+
+template rg_status gemm<EpiTwoIMinusT<__nv_bfloat16>>(rg_ctx*, bool, const void*, int64_t, const void*, int64_t, int,
+                                                      int, int, const EpiTwoIMinusT<__nv_bfloat16>&, cudaStream_t);
+template rg_status gemm<EpiTwoIMinusT<__half>>(rg_ctx*, bool, const void*, int64_t, const void*, int64_t, int, int,
+                                               int, const EpiTwoIMinusT<__half>&, cudaStream_t);
+template rg_status gemm<EpiStore16Both<__nv_bfloat16>>(rg_ctx*, bool, const void*, int64_t, const void*, int64_t, int,
+                                                       int, int, const EpiStore16Both<__nv_bfloat16>&, cudaStream_t);
+template rg_status gemm<EpiStore16Both<__half>>(rg_ctx*, bool, const void*, int64_t, const void*, int64_t, int, int,
+                                                int, const EpiStore16Both<__half>&, cudaStream_t);
+template rg_status gemm<EpiAddF64>(rg_ctx*, bool, const void*, int64_t, const void*, int64_t, int, int, int,
+                                   const EpiAddF64&, cudaStream_t);
+
+namespace {
 
 template <int BN, int kStages, class Epi, bool kComp, bool kBF16>
 rg_status launch(rg_ctx* ctx, const CUtensorMap& ma, const CUtensorMap& mb, const GemmArgs& args, const Epi& epi,

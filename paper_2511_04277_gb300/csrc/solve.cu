@@ -12,17 +12,19 @@
 // diagonally dominant in all four cases, so Gaussian elimination needs no pivoting.
 //
 // Algorithm (per set):
-//   1. A = I - Dl P Dr in fp32, padded to a multiple of 128 with the identity.
-//   2. Blocked LU, 128-wide panels: the diagonal block is factored and its triangular
-//      inverses formed by one block (fp32); the row and column panels are multiplied by
-//      those inverses (fp32); the trailing update A22 -= L21 U12 runs on tcgen05 with
-//      16-bit (bf16 or fp16) copies of the panels and fp32 accumulation.
-//   3. Triangular solves, block by block: the diagonal inverse (fp32) then a tcgen05
-//      update of the remaining rows.
-//   4. Iterative refinement: R = R0 - X + Dl (P (Dr X)) with P and Dr X each split into
-//      three bf16 slices (24 bits) and the six leading slice products summed by one
-//      tcgen05 GEMM over a 6N-long K with compensated fp32 chunks (fp64-accurate); the
-//      correction comes from the 16-bit factors. It stops when max|R| <= tol max|X|.
+//   1. A = I - Dl P Dr in 16-bit (bf16 or fp16), padded to a multiple of 128 with the
+//      identity, and e0 = ||Dl P Dr||_inf.
+//   2. Approximate inverse by Newton-Schulz iteration X <- X (2I - A X) from X = I: the
+//      error I - A X squares every step (its inf-norm starts at e0 < 1), so
+//      ceil(log2(log(tol16) / log(e0))) + 1 steps reach the 16-bit floor. Each step is two
+//      tcgen05 GEMMs whose epilogues write the 16-bit operands of the next one (the
+//      transposed copies the K-major layout needs included).
+//   3. Solve and refine: X64 = M R0, then R = R0 - X + Dl (P (Dr X)) with P and Dr X each
+//      split into three bf16 slices (24 bits) and the six leading slice products summed by
+//      one tcgen05 GEMM over a 6N-long K with compensated fp32 chunks (fp64-accurate);
+//      X64 += M R is one more GEMM. It stops when max|R| <= tol max|X| (or stalls below
+//      1e-9, the accuracy floor of that product).
+// The transposed systems reuse the same code with P read transposed.
 #include <cmath>
 #include <utility>
 
@@ -37,6 +39,7 @@ constexpr int kThreads = 256;
 // Below this relative residual a sweep that no longer halves it ends the refinement:
 // the residual product itself is only accurate to ~1e-8 relative.
 constexpr double kStallFloor = 1e-9;
+constexpr int kMaxNewtonSchulz = 24;
 
 __device__ __forceinline__ double p_elem(const double* P, int64_t ldp, bool trans, int i, int k) {
   return trans ? P[(int64_t)k * ldp + i] : P[(int64_t)i * ldp + k];
@@ -116,184 +119,71 @@ __global__ void build_a32(const double* __restrict__ P, int64_t ldp, bool trans,
   }
 }
 
-// Factor the 128 x 128 diagonal block at (k0, k0) in place (no pivoting) and form the
-// inverses of its unit-lower and upper triangles. One block of 1024 threads.
+// A16 = I - Dl P Dr (16-bit, identity padding), X16 = Xt16 = I, and the largest row sum
+// of |Dl P Dr| (atomicMax on its bits). One warp per row.
 template <class T16>
-__global__ void __launch_bounds__(1024) panel_factor(float* __restrict__ A, int np, int k0, float* __restrict__ Linv,
-                                                     float* __restrict__ Uinv, T16* __restrict__ Abf,
-                                                     int* __restrict__ err) {
-  extern __shared__ float sm[];
-  float* a = sm;               // [NB][NB + 1]
-  float* w = sm + NB * (NB + 1);  // [NB][NB + 1] scratch for the inverses
-  constexpr int ld = NB + 1;
-  const int tid = threadIdx.x;
-  for (int e = tid; e < NB * NB; e += blockDim.x) {
-    int r = e / NB, c = e % NB;
-    a[r * ld + c] = A[(int64_t)(k0 + r) * np + k0 + c];
+__global__ void build_ns_start(const double* __restrict__ P, int64_t ldp, bool trans, const double* __restrict__ dl,
+                               const double* __restrict__ dr, int n, int np, T16* __restrict__ A16,
+                               T16* __restrict__ X16, T16* __restrict__ Xt16, unsigned long long* e0_bits) {
+  const int i = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+  const int lane = threadIdx.x & 31;
+  if (i >= np) return;
+  double rs = 0.0;
+  const double li = (i < n && dl) ? dl[i] : 1.0;
+  for (int k = lane; k < np; k += 32) {
+    double e = 0.0;
+    if (i < n && k < n) e = li * p_elem(P, ldp, trans, i, k) * (dr ? dr[k] : 1.0);
+    rs += fabs(e);
+    const float one = (i == k) ? 1.f : 0.f;
+    const int64_t o = (int64_t)i * np + k;
+    A16[o] = to16<T16>((float)((i == k ? 1.0 : 0.0) - e));
+    X16[o] = to16<T16>(one);
+    Xt16[o] = to16<T16>(one);
   }
-  __syncthreads();
-  for (int p = 0; p < NB; ++p) {
-    float piv = a[p * ld + p];
-    if (!(fabsf(piv) > 0.f) || !isfinite(piv)) {
-      if (tid == 0) atomicExch(err, 1);
-      piv = 1.f;
-    }
-    for (int r = p + 1 + tid; r < NB; r += blockDim.x) a[r * ld + p] /= piv;
-    __syncthreads();
-    const int rows = NB - p - 1;
-    for (int e = tid; e < rows * rows; e += blockDim.x) {
-      int r = p + 1 + e / rows, c = p + 1 + e % rows;
-      a[r * ld + c] -= a[r * ld + p] * a[p * ld + c];
-    }
-    __syncthreads();
-  }
-  // Linv: inverse of the unit lower triangle, column by column (forward substitution)
-  for (int c = tid; c < NB; c += blockDim.x) {
-    for (int r = 0; r < NB; ++r) {
-      float s = (r == c) ? 1.f : 0.f;
-      for (int q = c; q < r; ++q) s -= a[r * ld + q] * w[q * ld + c];
-      w[r * ld + c] = (r < c) ? 0.f : s;
-    }
-  }
-  __syncthreads();
-  for (int e = tid; e < NB * NB; e += blockDim.x) Linv[e] = w[(e / NB) * ld + e % NB];
-  __syncthreads();
-  // Uinv: inverse of the upper triangle (back substitution), column by column
-  for (int c = tid; c < NB; c += blockDim.x) {
-    for (int r = NB - 1; r >= 0; --r) {
-      float s = (r == c) ? 1.f : 0.f;
-      for (int q = r + 1; q <= c; ++q) s -= a[r * ld + q] * w[q * ld + c];
-      w[r * ld + c] = (r > c) ? 0.f : s / a[r * ld + r];
-    }
-  }
-  __syncthreads();
-  for (int e = tid; e < NB * NB; e += blockDim.x) {
-    int r = e / NB, c = e % NB;
-    Uinv[e] = w[r * ld + c];
-    float v = a[r * ld + c];
-    A[(int64_t)(k0 + r) * np + k0 + c] = v;
-    Abf[(int64_t)(k0 + r) * np + k0 + c] = to16<T16>(v);
-  }
+  for (int o = 16; o > 0; o >>= 1) rs += __shfl_xor_sync(0xffffffffu, rs, o);
+  if (lane == 0) atomicMax(e0_bits, (unsigned long long)__double_as_longlong(rs));
 }
 
-// Row panel: A[k-block rows, c] <- Linv * A[k-block rows, c] for columns c >= k0 + NB;
-// also writes its 16-bit copy and the transposed copy Ut[c - (k0+NB)][r].
-template <class T16>
-__global__ void __launch_bounds__(kThreads) row_panel(float* __restrict__ A, int np, int k0,
-                                                      const float* __restrict__ Linv, T16* __restrict__ Abf,
-                                                      T16* __restrict__ Ut) {
-  __shared__ float col[NB][33];
-  const int c0 = k0 + NB + blockIdx.x * 32;
-  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
-  for (int r = ty; r < NB; r += 8) col[r][tx] = A[(int64_t)(k0 + r) * np + c0 + tx];
-  __syncthreads();
-  float out[NB / 8];
-#pragma unroll
-  for (int q = 0; q < NB / 8; ++q) {
-    int r = ty + 8 * q;
-    float s = 0.f;
-    for (int p = 0; p <= r; ++p) s += Linv[r * NB + p] * col[p][tx];
-    out[q] = s;
-  }
-#pragma unroll
-  for (int q = 0; q < NB / 8; ++q) {
-    int r = ty + 8 * q;
-    A[(int64_t)(k0 + r) * np + c0 + tx] = out[q];
-    Abf[(int64_t)(k0 + r) * np + c0 + tx] = to16<T16>(out[q]);
-    Ut[(int64_t)(c0 - k0 - NB + tx) * NB + r] = to16<T16>(out[q]);
-  }
-}
-
-// Column panel: A[r, k-block cols] <- A[r, k-block cols] * Uinv for rows r >= k0 + NB.
-template <class T16>
-__global__ void __launch_bounds__(kThreads) col_panel(float* __restrict__ A, int np, int k0,
-                                                      const float* __restrict__ Uinv, T16* __restrict__ Abf) {
-  __shared__ float rowv[32][NB + 1];
-  const int r0 = k0 + NB + blockIdx.x * 32;
-  for (int e = threadIdx.x; e < 32 * NB; e += kThreads) {
-    int r = e / NB, c = e % NB;
-    rowv[r][c] = A[(int64_t)(r0 + r) * np + k0 + c];
-  }
-  __syncthreads();
-  for (int e = threadIdx.x; e < 32 * NB; e += kThreads) {
-    int r = e / NB, c = e % NB;
-    float s = 0.f;
-    for (int p = 0; p <= c; ++p) s += rowv[r][p] * Uinv[p * NB + c];
-    A[(int64_t)(r0 + r) * np + k0 + c] = s;
-    Abf[(int64_t)(r0 + r) * np + k0 + c] = to16<T16>(s);
-  }
-}
-
-// Largest |x| of every column j < m of an fp64 matrix -> power-of-two scale 2^-e with
-// max * 2^-e in [0.5, 1) (1 for an all-zero column).
-__global__ void column_scales(const double* __restrict__ X, int64_t ld, int n, int m, float* __restrict__ scale,
-                              float* __restrict__ inv_scale) {
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= m) return;
+// Largest |R_ij| of each column j < m (bits, atomicMax); block (32 x 8) per 32 columns x 256 rows.
+__global__ void column_max(const double* __restrict__ R, int64_t ld, int n, int m, unsigned long long* colmax) {
+  __shared__ double red[8][33];
+  const int c = blockIdx.x * 32 + threadIdx.x;
+  const int r0 = blockIdx.y * 256;
   double mx = 0.0;
-  for (int i = 0; i < n; ++i) mx = fmax(mx, fabs(X[(int64_t)i * ld + j]));
+  if (c < m)
+    for (int r = r0 + threadIdx.y; r < min(n, r0 + 256); r += 8) mx = fmax(mx, fabs(R[(int64_t)r * ld + c]));
+  red[threadIdx.y][threadIdx.x] = mx;
+  __syncthreads();
+  if (threadIdx.y == 0 && c < m) {
+    for (int y = 1; y < 8; ++y) mx = fmax(mx, red[y][threadIdx.x]);
+    atomicMax(&colmax[c], (unsigned long long)__double_as_longlong(mx));
+  }
+}
+
+// Rt16[j][i] = 16-bit (R_ij * 2^-e_j) with max_i |R_ij| 2^-e_j in [0.5, 1), zero padding;
+// colscale[j] = 2^e_j. Tiled transpose through shared memory, block (32 x 8).
+template <class T16>
+__global__ void scaled_transpose16(const double* __restrict__ R, int64_t ld, int n, int m, int np, int mp,
+                                   const unsigned long long* __restrict__ colmax, T16* __restrict__ Rt,
+                                   float* __restrict__ colscale) {
+  __shared__ float tile[32][33];
+  const int i0 = blockIdx.y * 32, j0 = blockIdx.x * 32;
+  const int j = j0 + threadIdx.x;
   int e = 0;
-  if (mx > 0.0 && isfinite(mx)) frexp(mx, &e);
-  scale[j] = ldexpf(1.f, -e);
-  inv_scale[j] = ldexpf(1.f, e);
-}
-
-// W[i][j] = (float)(R[i][j] * scale[j]) for i < n, j < m; zero elsewhere (padding).
-__global__ void to_w32(const double* __restrict__ R, int64_t ldr, int n, int m, const float* __restrict__ scale,
-                       float* __restrict__ W, int np, int mp) {
-  const int64_t total = (int64_t)np * mp;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-    int i = (int)(e / mp), j = (int)(e % mp);
-    W[e] = (i < n && j < m) ? (float)(R[(int64_t)i * ldr + j] * (double)scale[j]) : 0.f;
+  if (j < m) {
+    double mx = __longlong_as_double((long long)colmax[j]);
+    if (mx > 0.0 && isfinite(mx)) frexp(mx, &e);
   }
-}
-
-// X[i][j] (+)= W[i][j] * inv_scale[j]  (first = overwrite).
-__global__ void add_w32(double* __restrict__ X, int64_t ldx, int n, int m, const float* __restrict__ W, int mp,
-                        const float* __restrict__ inv_scale, bool first) {
-  const int64_t total = (int64_t)n * m;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-    int i = (int)(e / m), j = (int)(e % m);
-    double d = (double)W[(int64_t)i * mp + j] * (double)inv_scale[j];
-    double* x = X + (int64_t)i * ldx + j;
-    *x = first ? d : *x + d;
-  }
-}
-
-// In place W[k-block] <- T * W[k-block] (T = 128 x 128 triangular inverse, lower or
-// upper), and Yt[j][r] = 16-bit copy of the result, transposed (the update's B operand).
-template <class T16, bool kLower>
-__global__ void __launch_bounds__(kThreads) diag_apply(float* __restrict__ W, int mp, int k0,
-                                                       const float* __restrict__ T, T16* __restrict__ Yt) {
-  __shared__ float col[NB][33];
-  const int j0 = blockIdx.x * 32;
-  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-  for (int r = ty; r < NB; r += 8) col[r][tx] = W[(int64_t)(k0 + r) * mp + j0 + tx];
-  __syncthreads();
-  float out[NB / 8];
-#pragma unroll
-  for (int q = 0; q < NB / 8; ++q) {
-    int r = ty + 8 * q;
-    float s = 0.f;
-    if (kLower) {
-      for (int p = 0; p <= r; ++p) s += T[r * NB + p] * col[p][tx];
-    } else {
-      for (int p = r; p < NB; ++p) s += T[r * NB + p] * col[p][tx];
-    }
-    out[q] = s;
+  const double sc = ldexp(1.0, -e);
+  if (blockIdx.y == 0 && j < mp) colscale[j] = ldexpf(1.f, e);
+  for (int r = threadIdx.y; r < 32; r += 8) {
+    const int i = i0 + r;
+    tile[r][threadIdx.x] = (i < n && j < m) ? (float)(R[(int64_t)i * ld + j] * sc) : 0.f;
   }
   __syncthreads();
-#pragma unroll
-  for (int q = 0; q < NB / 8; ++q) {
-    int r = ty + 8 * q;
-    W[(int64_t)(k0 + r) * mp + j0 + tx] = out[q];
-    col[r][tx] = out[q];
-  }
-  __syncthreads();
-  // transposed 16-bit copy: Yt[j0 + c][r]
-  for (int e = threadIdx.x; e < 32 * NB; e += kThreads) {
-    int c = e / NB, r = e % NB;
-    Yt[(int64_t)(j0 + c) * NB + r] = to16<T16>(col[r][c]);
+  for (int r = threadIdx.y; r < 32; r += 8) {
+    const int jj = j0 + r, ii = i0 + threadIdx.x;
+    if (jj < mp && ii < np) Rt[(int64_t)jj * np + ii] = to16<T16>(tile[threadIdx.x][r]);
   }
 }
 
@@ -327,46 +217,39 @@ inline int grid_for(int64_t total, int sm) {
 
 // ------------------------------------------------------------------ solver object
 struct Layout {
-  int n, m, np, mp, nblk;
+  int n, m, np, mp;
 };
 
 struct Buffers {
-  float* A32;
-  void* Abf;
-  void* Ut;
-  float* Linv;
-  float* Uinv;
-  float* W;
-  void* Yt;
-  float* scale;
-  float* inv_scale;
-  __nv_bfloat16* Aext;
-  __nv_bfloat16* Bext;
-  double* R0;   // right-hand side (padded, ld = mp)
+  void* A16;      // np x np
+  void* X16[2];   // np x np, Newton-Schulz iterates (ping-pong)
+  void* Xt16;     // np x np, transpose of the current iterate
+  void* Zt16;     // np x np, (2I - A X)^T
+  void* Rt16;     // mp x np, scaled transposed right-hand side / residual
+  float* colscale;               // mp
+  unsigned long long* colmax;    // mp
+  __nv_bfloat16* Aext;           // np x 6np
+  __nv_bfloat16* Bext;           // mp x 6np
+  double* R0;   // right-hand side (ld = mp)
   double* X;    // solution (ld = mp)
   double* R;    // residual (ld = mp)
   double* vec;  // [2][np] per-row scratch (row sums, diagonal scalings)
-  unsigned long long* red;  // [2] max|R|, max|X| bits
+  unsigned long long* red;  // [3] max|R|, max|X|, e0 bits
 };
 
 template <class Take>
 void plan(const Layout& L, Take&& t) {
-  t.template take<float>((size_t)L.np * L.np);                    // A32
-  t.template take<uint16_t>((size_t)L.np * L.np);                 // Abf
-  t.template take<uint16_t>((size_t)L.np * NB);                   // Ut
-  t.template take<float>((size_t)L.nblk * NB * NB);               // Linv
-  t.template take<float>((size_t)L.nblk * NB * NB);               // Uinv
-  t.template take<float>((size_t)L.np * L.mp);                    // W
-  t.template take<uint16_t>((size_t)L.mp * NB);                   // Yt
-  t.template take<float>((size_t)L.mp);                           // scale
-  t.template take<float>((size_t)L.mp);                           // inv_scale
+  for (int k = 0; k < 5; ++k) t.template take<uint16_t>((size_t)L.np * L.np);  // A16, X16 x2, Xt16, Zt16
+  t.template take<uint16_t>((size_t)L.mp * L.np);                 // Rt16
+  t.template take<float>((size_t)L.mp);                           // colscale
+  t.template take<unsigned long long>((size_t)L.mp);              // colmax
   t.template take<__nv_bfloat16>((size_t)L.np * kSlices * L.np);  // Aext
   t.template take<__nv_bfloat16>((size_t)L.mp * kSlices * L.np);  // Bext
   t.template take<double>((size_t)L.np * L.mp);                   // R0
   t.template take<double>((size_t)L.np * L.mp);                   // X
   t.template take<double>((size_t)L.np * L.mp);                   // R
   t.template take<double>((size_t)2 * L.np);                      // vec
-  t.template take<unsigned long long>(2);                         // red
+  t.template take<unsigned long long>(4);                         // red
 }
 
 struct Solver {
@@ -375,10 +258,12 @@ struct Solver {
   Buffers b;
   bool bf16;
   cudaStream_t s;
-  int* err;          // device error words: [0] zero pivot, [1] non-finite
+  int* err;          // device error words: [0] unused, [1] non-finite
   const double* P;
   int64_t ldp;
   bool transP;
+  int cur = 0;       // which X16 buffer holds the current inverse
+  int ns_steps = 0;
 
   // Carves the solver's buffers out of the context workspace, after `extra_bytes`
   // reserved for the caller (returned in *extra).
@@ -387,7 +272,6 @@ struct Solver {
     L.m = m;
     L.np = (n + NB - 1) / NB * NB;
     L.mp = (m + NB - 1) / NB * NB;
-    L.nblk = L.np / NB;
     bf16 = use_bf16;
     s = stream;
     extra_bytes = rg::align_up(extra_bytes, 256);
@@ -398,22 +282,21 @@ struct Solver {
     if (st != RG_OK) return st;
     if (extra) *extra = ws;
     rg::Carver cv(static_cast<char*>(ws) + extra_bytes);
-    b.A32 = cv.take<float>((size_t)L.np * L.np);
-    b.Abf = cv.take<uint16_t>((size_t)L.np * L.np);
-    b.Ut = cv.take<uint16_t>((size_t)L.np * NB);
-    b.Linv = cv.take<float>((size_t)L.nblk * NB * NB);
-    b.Uinv = cv.take<float>((size_t)L.nblk * NB * NB);
-    b.W = cv.take<float>((size_t)L.np * L.mp);
-    b.Yt = cv.take<uint16_t>((size_t)L.mp * NB);
-    b.scale = cv.take<float>(L.mp);
-    b.inv_scale = cv.take<float>(L.mp);
+    b.A16 = cv.take<uint16_t>((size_t)L.np * L.np);
+    b.X16[0] = cv.take<uint16_t>((size_t)L.np * L.np);
+    b.X16[1] = cv.take<uint16_t>((size_t)L.np * L.np);
+    b.Xt16 = cv.take<uint16_t>((size_t)L.np * L.np);
+    b.Zt16 = cv.take<uint16_t>((size_t)L.np * L.np);
+    b.Rt16 = cv.take<uint16_t>((size_t)L.mp * L.np);
+    b.colscale = cv.take<float>(L.mp);
+    b.colmax = cv.take<unsigned long long>(L.mp);
     b.Aext = cv.take<__nv_bfloat16>((size_t)L.np * kSlices * L.np);
     b.Bext = cv.take<__nv_bfloat16>((size_t)L.mp * kSlices * L.np);
     b.R0 = cv.take<double>((size_t)L.np * L.mp);
     b.X = cv.take<double>((size_t)L.np * L.mp);
     b.R = cv.take<double>((size_t)L.np * L.mp);
     b.vec = cv.take<double>((size_t)2 * L.np);
-    b.red = cv.take<unsigned long long>(2);
+    b.red = cv.take<unsigned long long>(4);
     err = ctx->d_scratch + 32;
     RG_CUDA_TRY(ctx, cudaMemsetAsync(err, 0, 2 * sizeof(int), s));
     RG_CUDA_TRY(ctx, cudaMemsetAsync(ctx->d_scratch + tc::kGemmErrorSlot, 0, sizeof(int), s));
@@ -427,38 +310,44 @@ struct Solver {
     transP = trans;
     build_p_slices<<<grid_for((int64_t)L.np * L.np, ctx->sm_count), kThreads, 0, s>>>(P, ldp, transP, L.n, L.np,
                                                                                       b.Aext);
-    ++ctx->launches;
     RG_CUDA_TRY(ctx, cudaGetLastError());
     return RG_OK;
   }
 
+  // Newton-Schulz approximate inverse of A = I - Dl P Dr into b.X16[cur].
   template <class T16>
   rg_status factor_t(const double* dl, const double* dr) {
-    build_a32<<<grid_for((int64_t)L.np * L.np, ctx->sm_count), kThreads, 0, s>>>(P, ldp, transP, dl, dr, L.n, L.np,
-                                                                                 b.A32);
-    ++ctx->launches;
+    RG_CUDA_TRY(ctx, cudaMemsetAsync(b.red + 2, 0, sizeof(unsigned long long), s));
+    T16* A16 = static_cast<T16*>(b.A16);
+    T16* X[2] = {static_cast<T16*>(b.X16[0]), static_cast<T16*>(b.X16[1])};
+    T16* Xt = static_cast<T16*>(b.Xt16);
+    T16* Zt = static_cast<T16*>(b.Zt16);
+    build_ns_start<T16><<<(L.np + 7) / 8, 256, 0, s>>>(P, ldp, transP, dl, dr, L.n, L.np, A16, X[0], Xt, b.red + 2);
     RG_CUDA_TRY(ctx, cudaGetLastError());
-    T16* Abf = static_cast<T16*>(b.Abf);
-    T16* Ut = static_cast<T16*>(b.Ut);
-    const size_t psmem = 2 * NB * (NB + 1) * sizeof(float);
-    RG_CUDA_TRY(ctx, cudaFuncSetAttribute(panel_factor<T16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psmem));
-    for (int k = 0; k < L.nblk; ++k) {
-      const int k0 = k * NB;
-      panel_factor<T16><<<1, 1024, psmem, s>>>(b.A32, L.np, k0, b.Linv + (size_t)k * NB * NB,
-                                               b.Uinv + (size_t)k * NB * NB, Abf, err);
-      ++ctx->launches;
-      const int rest = L.np - k0 - NB;
-      if (rest > 0) {
-        row_panel<T16><<<rest / 32, kThreads, 0, s>>>(b.A32, L.np, k0, b.Linv + (size_t)k * NB * NB, Abf, Ut);
-        ++ctx->launches;
-        col_panel<T16><<<rest / 32, kThreads, 0, s>>>(b.A32, L.np, k0, b.Uinv + (size_t)k * NB * NB, Abf);
-        ++ctx->launches;
-        RG_CUDA_TRY(ctx, cudaGetLastError());
-        rg_status st = tc::gemm_f32(ctx, bf16, Abf + (size_t)(k0 + NB) * L.np + k0, L.np, Ut, NB, rest, rest, NB,
-                                    b.A32 + (size_t)(k0 + NB) * L.np + k0 + NB, L.np, -1.f, 1.f, s);
-        if (st != RG_OK) return st;
-      }
-      RG_CUDA_TRY(ctx, cudaGetLastError());
+    unsigned long long bits = 0;
+    RG_CUDA_TRY(ctx, cudaMemcpyAsync(&bits, b.red + 2, sizeof(bits), cudaMemcpyDeviceToHost, s));
+    RG_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+    double e0;
+    memcpy(&e0, &bits, sizeof(e0));
+    if (!std::isfinite(e0)) return rg::fail(ctx, RG_ERR_NUMERIC, "non-finite system matrix");
+    const double floor16 = bf16 ? 0x1p-10 : 0x1p-13;
+    int steps = kMaxNewtonSchulz;
+    if (e0 < 1.0) {
+      steps = 1;
+      if (e0 > 0.0) steps = (int)std::ceil(std::log2(std::log(floor16) / std::log(e0))) + 1;
+      steps = std::max(1, std::min(steps, kMaxNewtonSchulz));
+    }
+    ns_steps = steps;
+    cur = 0;
+    for (int k = 0; k < steps; ++k) {
+      // Zt = (2I - A X)^T : A operand A16 [i][k], B operand X^T rows = X columns
+      rg_status st = tc::gemm(ctx, bf16, A16, L.np, Xt, L.np, L.np, L.np, L.np, tc::EpiTwoIMinusT<T16>{Zt, L.np}, s);
+      if (st != RG_OK) return st;
+      // X' = X (2I - A X) : A operand X [i][k], B operand Z^T
+      st = tc::gemm(ctx, bf16, X[cur], L.np, Zt, L.np, L.np, L.np, L.np, tc::EpiStore16Both<T16>{X[cur ^ 1], Xt, L.np},
+                    s);
+      if (st != RG_OK) return st;
+      cur ^= 1;
     }
     return RG_OK;
   }
@@ -466,65 +355,35 @@ struct Solver {
     return bf16 ? factor_t<__nv_bfloat16>(dl, dr) : factor_t<__half>(dl, dr);
   }
 
-  // X (+)= A^-1 src, where src is an fp64 n x m matrix (ld = mp), through the 16-bit factors.
+  // X (+)= M src, where src is an fp64 n x m matrix (ld = mp): one tensor-core GEMM with
+  // src scaled column by column into 16 bits.
   template <class T16>
-  rg_status solve_t(const double* src, bool first) {
-    const int cs_blocks = (L.m + 127) / 128;
-    column_scales<<<cs_blocks, 128, 0, s>>>(src, L.mp, L.n, L.m, b.scale, b.inv_scale);
-    ++ctx->launches;
-    to_w32<<<grid_for((int64_t)L.np * L.mp, ctx->sm_count), kThreads, 0, s>>>(src, L.mp, L.n, L.m, b.scale, b.W,
-                                                                               L.np, L.mp);
-    ++ctx->launches;
+  rg_status apply_t(const double* src, bool first) {
+    RG_CUDA_TRY(ctx, cudaMemsetAsync(b.colmax, 0, (size_t)L.mp * sizeof(unsigned long long), s));
+    dim3 cg((L.m + 31) / 32, (L.n + 255) / 256);
+    column_max<<<cg, dim3(32, 8), 0, s>>>(src, L.mp, L.n, L.m, b.colmax);
+    dim3 tg(L.mp / 32, L.np / 32);
+    T16* Rt = static_cast<T16*>(b.Rt16);
+    scaled_transpose16<T16><<<tg, dim3(32, 8), 0, s>>>(src, L.mp, L.n, L.m, L.np, L.mp, b.colmax, Rt, b.colscale);
     RG_CUDA_TRY(ctx, cudaGetLastError());
-    const T16* Abf = static_cast<const T16*>(b.Abf);
-    T16* Yt = static_cast<T16*>(b.Yt);
-    const int jb = L.mp / 32;
-    for (int k = 0; k < L.nblk; ++k) {  // forward: L y = w
-      const int k0 = k * NB;
-      diag_apply<T16, true><<<jb, kThreads, 0, s>>>(b.W, L.mp, k0, b.Linv + (size_t)k * NB * NB, Yt);
-      ++ctx->launches;
-      RG_CUDA_TRY(ctx, cudaGetLastError());
-      const int rest = L.np - k0 - NB;
-      if (rest > 0) {
-        rg_status st = tc::gemm_f32(ctx, bf16, Abf + (size_t)(k0 + NB) * L.np + k0, L.np, Yt, NB, rest, L.mp, NB,
-                                    b.W + (size_t)(k0 + NB) * L.mp, L.mp, -1.f, 1.f, s);
-        if (st != RG_OK) return st;
-      }
-    }
-    for (int k = L.nblk - 1; k >= 0; --k) {  // backward: U x = y
-      const int k0 = k * NB;
-      diag_apply<T16, false><<<jb, kThreads, 0, s>>>(b.W, L.mp, k0, b.Uinv + (size_t)k * NB * NB, Yt);
-      ++ctx->launches;
-      RG_CUDA_TRY(ctx, cudaGetLastError());
-      if (k0 > 0) {
-        rg_status st = tc::gemm_f32(ctx, bf16, Abf + k0, L.np, Yt, NB, k0, L.mp, NB, b.W, L.mp, -1.f, 1.f, s);
-        if (st != RG_OK) return st;
-      }
-    }
-    add_w32<<<grid_for((int64_t)L.n * L.m, ctx->sm_count), kThreads, 0, s>>>(b.X, L.mp, L.n, L.m, b.W, L.mp,
-                                                                              b.inv_scale, first);
-    ++ctx->launches;
-    RG_CUDA_TRY(ctx, cudaGetLastError());
-    return RG_OK;
+    return tc::gemm(ctx, bf16, b.X16[cur], L.np, Rt, L.np, L.n, L.m, L.np,
+                    tc::EpiAddF64{b.X, L.mp, b.colscale, first ? 1 : 0}, s);
   }
-  rg_status solve(const double* src, bool first) {
-    return bf16 ? solve_t<__nv_bfloat16>(src, first) : solve_t<__half>(src, first);
+  rg_status apply(const double* src, bool first) {
+    return bf16 ? apply_t<__nv_bfloat16>(src, first) : apply_t<__half>(src, first);
   }
 
   // R = R0 - X + Dl (P (Dr X)); returns max|R| / max|X| (synchronises the stream).
   rg_status residual(const double* dl, const double* dr, double* rel) {
     dim3 tg((L.mp + 31) / 32, (L.np + 31) / 32);
     build_x_slices<<<tg, dim3(32, 8), 0, s>>>(b.X, L.mp, dr, L.n, L.m, L.np, L.mp, b.Bext);
-    ++ctx->launches;
     RG_CUDA_TRY(ctx, cudaGetLastError());
     rg_status st = tc::gemm_residual(ctx, b.Aext, (int64_t)kSlices * L.np, b.Bext, (int64_t)kSlices * L.np, L.n, L.m,
                                      kSlices * L.np, kResidualChunk, b.R, b.R0, b.X, dl, L.mp, s);
     if (st != RG_OK) return st;
     RG_CUDA_TRY(ctx, cudaMemsetAsync(b.red, 0, 2 * sizeof(unsigned long long), s));
     max_abs<<<grid_for((int64_t)L.n * L.m, ctx->sm_count), kThreads, 0, s>>>(b.R, L.mp, L.n, L.m, b.red, err + 1);
-    ++ctx->launches;
     max_abs<<<grid_for((int64_t)L.n * L.m, ctx->sm_count), kThreads, 0, s>>>(b.X, L.mp, L.n, L.m, b.red + 1, err + 1);
-    ++ctx->launches;
     RG_CUDA_TRY(ctx, cudaGetLastError());
     unsigned long long h[2];
     RG_CUDA_TRY(ctx, cudaMemcpyAsync(h, b.red, sizeof(h), cudaMemcpyDeviceToHost, s));
@@ -542,7 +401,6 @@ struct Solver {
     RG_CUDA_TRY(ctx, cudaMemcpyAsync(&g, ctx->d_scratch + tc::kGemmErrorSlot, sizeof(int), cudaMemcpyDeviceToHost, s));
     RG_CUDA_TRY(ctx, cudaStreamSynchronize(s));
     if (g) return rg::fail(ctx, RG_ERR_CUDA, "tensor-core GEMM timed out waiting on a barrier");
-    if (h[0]) return rg::fail(ctx, RG_ERR_NUMERIC, "zero or non-finite pivot in the factorisation");
     if (h[1]) return rg::fail(ctx, RG_ERR_NUMERIC, "non-finite value in the solution or residual");
     return RG_OK;
   }
@@ -550,7 +408,7 @@ struct Solver {
   // Factor, solve and refine one set whose right-hand side is already in b.R0.
   rg_status run(const double* dl, const double* dr, double tol, int max_sweeps, int* sweeps, double* rel_out) {
     rg_status st = factor(dl, dr);
-    if (st == RG_OK) st = solve(b.R0, true);
+    if (st == RG_OK) st = apply(b.R0, true);
     if (st != RG_OK) return st;
     double rel = INFINITY, prev = INFINITY;
     int sw = 0;
@@ -561,7 +419,7 @@ struct Solver {
       // converged, or stalled at the accuracy floor of the fp32-chunked residual product
       if (rel <= tol || (rel <= kStallFloor && rel > 0.5 * prev)) { done = true; break; }
       prev = rel;
-      st = solve(b.R, false);
+      st = apply(b.R, false);
       if (st != RG_OK) return st;
     }
     *sweeps = sw + (done ? 1 : 0);

@@ -21,6 +21,8 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
+#include <type_traits>
+
 #include "common.cuh"
 
 namespace tc {
@@ -136,21 +138,100 @@ __host__ __device__ constexpr uint32_t idesc_f16(int m, int n, bool bf16) {
 }
 
 // ------------------------------------------------------------------ epilogues
-// Each functor receives one tile row segment: row r, columns c0..c0+31, 32 values.
+// An epilogue receives, per warp and per 32-column slab, the 32 x 32 block of the tile
+// owned by that warp: lane l holds row row0 + l, columns c0 .. c0+31 in v[0..31]. `stage`
+// is a [32][33] shared-memory block private to the warp, used to turn the row-per-lane
+// layout into coalesced row stores.
+
+// Straight store through the staging block: out(r, c) for r in row0..row0+31 with each
+// warp instruction writing 32 consecutive columns of one row.
+template <class T, class F>
+__device__ __forceinline__ void staged_rows(int row0, int lane, int c0, int M, int N, const T* v, T (*stage)[33],
+                                            F&& put) {
+#pragma unroll
+  for (int i = 0; i < 32; ++i) stage[lane][i] = v[i];
+  __syncwarp();
+  const int c = c0 + lane;
+#pragma unroll 4
+  for (int rr = 0; rr < 32; ++rr) {
+    const int r = row0 + rr;
+    if (r < M && c < N) put(r, c, stage[rr][lane]);
+  }
+  __syncwarp();
+}
+
+template <class T16>
+__device__ __forceinline__ T16 to_16(float x);
+template <>
+__device__ __forceinline__ __nv_bfloat16 to_16<__nv_bfloat16>(float x) { return __float2bfloat16_rn(x); }
+template <>
+__device__ __forceinline__ __half to_16<__half>(float x) { return __float2half_rn(x); }
 
 // C[r][c] = beta * C[r][c] + alpha * acc   (fp32 C)
 struct EpiF32 {
   float* C;
   int64_t ldc;
   float alpha, beta;
-  __device__ __forceinline__ void store(int r, int c0, int M, int N, const float* v) const {
+  __device__ __forceinline__ void store(int row0, int lane, int c0, int M, int N, const float* v,
+                                        float (*stage)[33]) const {
+    staged_rows(row0, lane, c0, M, N, v, stage, [&](int r, int c, float x) {
+      float* p = C + (int64_t)r * ldc + c;
+      *p = (beta == 0.f ? 0.f : beta * *p) + alpha * x;
+    });
+  }
+};
+
+// Newton-Schulz half step: Zt[c][r] = 16-bit (2 delta_rc - acc) -- the transposed store is
+// coalesced as it is (the warp's 32 rows are 32 consecutive elements of a row of Zt).
+template <class T16>
+struct EpiTwoIMinusT {
+  T16* Zt;
+  int64_t ld;
+  __device__ __forceinline__ void store(int row0, int lane, int c0, int M, int N, const float* v,
+                                        float (*)[33]) const {
+    const int r = row0 + lane;
     if (r >= M) return;
-    float* row = C + (int64_t)r * ldc;
-#pragma unroll
+#pragma unroll 8
     for (int i = 0; i < 32; ++i) {
-      int c = c0 + i;
-      if (c < N) row[c] = (beta == 0.f ? 0.f : beta * row[c]) + alpha * v[i];
+      const int c = c0 + i;
+      if (c < N) Zt[(int64_t)c * ld + r] = to_16<T16>((r == c ? 2.f : 0.f) - v[i]);
     }
+  }
+};
+
+// Newton-Schulz step result: X[r][c] and Xt[c][r] = 16-bit acc.
+template <class T16>
+struct EpiStore16Both {
+  T16* X;
+  T16* Xt;
+  int64_t ld;
+  __device__ __forceinline__ void store(int row0, int lane, int c0, int M, int N, const float* v,
+                                        float (*stage)[33]) const {
+    const int r = row0 + lane;
+    if (r < M) {
+#pragma unroll 8
+      for (int i = 0; i < 32; ++i) {
+        const int c = c0 + i;
+        if (c < N) Xt[(int64_t)c * ld + r] = to_16<T16>(v[i]);
+      }
+    }
+    staged_rows(row0, lane, c0, M, N, v, stage, [&](int rr, int c, float x) { X[(int64_t)rr * ld + c] = to_16<T16>(x); });
+  }
+};
+
+// X64[r][c] = (first ? 0 : X64[r][c]) + acc * colscale[c]   (the refinement correction)
+struct EpiAddF64 {
+  double* X;
+  int64_t ld;
+  const float* colscale;
+  int first;
+  __device__ __forceinline__ void store(int row0, int lane, int c0, int M, int N, const float* v,
+                                        float (*stage)[33]) const {
+    staged_rows(row0, lane, c0, M, N, v, stage, [&](int r, int c, float x) {
+      double* p = X + (int64_t)r * ld + c;
+      const double d = (double)x * (double)colscale[c];
+      *p = first ? d : *p + d;
+    });
   }
 };
 
@@ -162,15 +243,13 @@ struct EpiResidual {
   const double* X;
   const double* dl;  // may be null (identity)
   int64_t ld;        // shared leading dimension of out, E and X
-  __device__ __forceinline__ void store(int r, int c0, int M, int N, const double* v) const {
-    if (r >= M) return;
-    const double s = dl ? dl[r] : 1.0;
-    const int64_t base = (int64_t)r * ld;
-#pragma unroll
-    for (int i = 0; i < 32; ++i) {
-      int c = c0 + i;
-      if (c < N) out[base + c] = E ? (E[base + c] - X[base + c]) + s * v[i] : s * v[i];
-    }
+  __device__ __forceinline__ void store(int row0, int lane, int c0, int M, int N, const double* v,
+                                        double (*stage)[33]) const {
+    staged_rows(row0, lane, c0, M, N, v, stage, [&](int r, int c, double x) {
+      const double s = dl ? dl[r] : 1.0;
+      const int64_t i = (int64_t)r * ld + c;
+      out[i] = E ? (E[i] - X[i]) + s * x : s * x;
+    });
   }
 };
 
@@ -202,6 +281,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
   __shared__ int s_abort;
   __shared__ int s_consumed;             // K blocks whose stage the MMA thread has taken
+  using StageT = typename std::conditional<kCompensated, double, float>::type;
+  __shared__ StageT s_stage[4][32][33];  // per epilogue warp: coalescing block
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
@@ -280,8 +361,9 @@ __global__ void __launch_bounds__(kThreads, 1)
   } else {
     // ---------------- epilogue warps 2..5
     const int quarter = warp & 3;  // TMEM lanes 32*quarter .. +31
-    const int row = m0 + quarter * 32 + lane;
+    const int row0 = m0 + quarter * 32;
     const uint32_t lane_addr = (uint32_t)(quarter * 32) << 16;
+    StageT (*stage)[33] = s_stage[quarter];
     if constexpr (!kCompensated) {
       if (mbar_wait(&acc_full[0], 0)) {
         tc_fence_after();
@@ -289,7 +371,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll 1
         for (int c0 = 0; c0 < BN; c0 += 32) {
           tmem_ld32(tmem_base + lane_addr + (uint32_t)c0, v);
-          epi.store(row, n0 + c0, args.M, args.N, v);
+          epi.store(row0, lane, n0 + c0, args.M, args.N, v, stage);
         }
       } else {
         *abort_flag = 1;
@@ -327,7 +409,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           double v[32];
 #pragma unroll
           for (int i = 0; i < 32; ++i) v[i] = (double)sum[c0 + i] - (double)comp[c0 + i];
-          epi.store(row, n0 + c0, args.M, args.N, v);
+          epi.store(row0, lane, n0 + c0, args.M, args.N, v, stage);
         }
       }
     }
@@ -347,6 +429,12 @@ constexpr size_t smem_bytes() {
 }
 
 // ------------------------------------------------------------------ host side
+// Launch D = A B^T (A [M x K], B [N x K], 16-bit K-major) with the epilogue `epi`;
+// instantiated in gemm.cu for the epilogues above (bf16 selects the operand type).
+template <class Epi>
+rg_status gemm(rg_ctx* ctx, bool bf16, const void* A, int64_t lda, const void* B, int64_t ldb, int M, int N, int K,
+               const Epi& epi, cudaStream_t s);
+
 // C (fp32, ldc) = alpha * A B^T + beta * C with A [M x K] (lda), B [N x K] (ldb), 16-bit
 // K-major operands (bf16 when `bf16`, else fp16). lda, ldb: multiples of 8 elements;
 // A, B: 16-byte aligned.
