@@ -84,7 +84,10 @@ rg_status rg_launch_count(const rg_ctx* ctx, int64_t* launches_out_h);
  *                                          the triangles of a face must be coplanar
  *   n_faces     number of faces N (every face needs >= 1 triangle of area > 0)
  *   use_bvh     1 = traverse the BVH, 0 = test every triangle (tiny meshes),
- *               -1 = choose (brute force when nt <= 64)
+ *               -1 = choose (brute force when nt <= 64); 2 / 3 = traverse the BVH
+ *               with the lock-step / refill schedule of the trace kernel (1 and -1
+ *               take refill for BVHs of depth >= 12, lock-step otherwise).
+ *               All choices give bit-identical counts.
  * The host arrays are copied; they may be freed after the call.
  * Errors: RG_ERR_ARG (bad index, empty or degenerate face), RG_ERR_STACK (BVH
  * deeper than the 64-entry traversal stack), RG_ERR_OOM, RG_ERR_CUDA. */
@@ -99,6 +102,8 @@ typedef struct {
   int32_t bvh_nodes;   /* 0 when brute force is used */
   int32_t bvh_depth;
   float lift;          /* ray origins sit this far off their face: 1e-6 x bounding-box diagonal */
+  float sah_visits;    /* expected BVH node visits of a random line (surface-area heuristic) */
+  int32_t refill;      /* 1: the trace kernel refills finished lanes, 0: lock-step rays */
 } rg_mesh_info;
 rg_status rg_mesh_get_info(const rg_mesh* mesh, rg_mesh_info* info_out);
 

@@ -22,7 +22,8 @@ PREC = {"bf16": 1, "fp16": 2}
 
 
 class MeshInfo(ctypes.Structure):
-    _fields_ = [("n_faces", i32), ("n_tris", i64), ("bvh_nodes", i32), ("bvh_depth", i32), ("lift", ctypes.c_float)]
+    _fields_ = [("n_faces", i32), ("n_tris", i64), ("bvh_nodes", i32), ("bvh_depth", i32), ("lift", ctypes.c_float),
+                ("sah_visits", ctypes.c_float), ("refill", i32)]
 
 
 # name -> (restype, argtypes), in the order of include/radgeb.h

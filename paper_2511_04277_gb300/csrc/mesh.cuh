@@ -20,6 +20,8 @@ struct DevMesh {
   float lift = 0.f;       // origins are lifted this far off the face along its normal
   float t_lo = 0.f;       // lower end of the traversal window (-lift / 2)
   float slack = 0.f;      // the window's upper end is best_t + slack
+  int32_t refill = 0;     // 1: refill scheduling of the trace kernel, 0: lock-step
+  float sah_visits = 0.f; // expected node visits of a random line (surface-area heuristic)
   const float4* nodes = nullptr;
   const float4* tris = nullptr;     // nt records in leaf order (BVH) or index order
   const float4* etris = nullptr;    // nt records in face order (emission)

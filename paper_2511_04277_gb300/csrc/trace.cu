@@ -1,12 +1,19 @@
 // Monte Carlo ray tracing of view factors (Sec. 3.5.1, Eq. 3.15) on sm_103a.
 //
 // One persistent kernel: each block repeatedly takes a work item (one face, a range
-// of its rays), keeps a shared-memory tally row of N+1 counters for that face, traces
-// the rays (Philox4x32-10 draws, area-CDF triangle choice, uniform point, Malley
-// cosine-weighted direction, origin lifted off the face along its normal, BVH
-// traversal with Moller-Trumbore leaf tests, closest hit by (t > 0, triangle index)),
-// adds warp-aggregated hits to the row and flushes the non-zero counters to the int64
-// count matrix in HBM.
+// of its rays) and keeps a shared-memory tally row of N+1 counters for that face. The
+// warps of the block share the item's rays through a counter; each warp runs one
+// warp-synchronous loop whose iteration is one BVH node visit per lane (child-box slab
+// tests, Moller-Trumbore tests of leaf triangles, stack push/pop). Lanes whose ray is
+// finished wait until half of the warp is; then their rays go to the tally row
+// (aggregated per target face) and they take new rays from a private 64-ray ring in
+// shared memory, which the whole warp refills 32 rays at a time, in step, when it runs
+// short (Philox4x32-10 draws, area-CDF triangle choice, uniform point lifted off the
+// face, Malley cosine-weighted direction). Sampling thus stays convergent and lanes do
+// not wait for the slowest ray of their warp. At the end of an item the non-zero
+// counters are flushed to the int64 count matrix in HBM. The closest
+// hit is the smallest (t > 0, triangle index), so the counts do not depend on the order
+// in which rays are traced.
 //
 // kExact = true rounds every float operation of sampling and intersection on its
 // own (no fused multiply-add), which makes the counts bit-identical to any other
@@ -14,6 +21,14 @@
 #include <climits>
 
 #include "mesh.cuh"
+
+// Resident blocks per SM the two schedules are compiled for (register caps).
+#ifndef RG_LOCKSTEP_MIN_BLOCKS
+#define RG_LOCKSTEP_MIN_BLOCKS 4
+#endif
+#ifndef RG_REFILL_MIN_BLOCKS
+#define RG_REFILL_MIN_BLOCKS 4
+#endif
 
 namespace {
 
@@ -134,6 +149,19 @@ __device__ __forceinline__ void test_record(const float4* __restrict__ rec, int3
   }
 }
 
+// Reciprocal of a direction component for the slab tests t = box * (1/d) - o * (1/d).
+// The boxes are padded far beyond the error of the approximate reciprocal. Components
+// are kept at least 1e-30 in magnitude so that 1/d stays finite: with 1/d = inf the fused
+// form would give fma(box, inf, -inf) = NaN on one side of the slab and -inf on the
+// other, and cull a box the ray lies in (a component is exactly 0 for about one ray in
+// 2^24).
+__device__ __forceinline__ float rcp_approx(float x) {
+  x = fabsf(x) < 1e-30f ? copysignf(1e-30f, x) : x;
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
 // Closest hit; returns the face index or n_faces (environment). Sets *overflow on a
 // traversal stack overflow.
 template <bool E, bool kBVH, class St>
@@ -147,7 +175,10 @@ __device__ int32_t closest_face(const DevMesh& m, int32_t src, V3 o, V3 d, bool*
     }
     return best_face;
   }
-  const float ix = __frcp_rn(d.x), iy = __frcp_rn(d.y), iz = __frcp_rn(d.z);
+  // slab tests in the form t = box * (1/d) - o/d; the boxes are padded far beyond the
+  // rounding of this form, so it needs neither IEEE reciprocals nor separate roundings
+  const float ix = rcp_approx(d.x), iy = rcp_approx(d.y), iz = rcp_approx(d.z);
+  const float ox = o.x * ix, oy = o.y * iy, oz = o.z * iz;
   int32_t stack[kTraceStack];
   int sp = 0;
   int32_t node = 0;
@@ -157,12 +188,12 @@ __device__ int32_t closest_face(const DevMesh& m, int32_t src, V3 o, V3 d, bool*
     int32_t refL = __float_as_int(w.x), refR = __float_as_int(w.y);
     int32_t cntL = __float_as_int(w.z), cntR = __float_as_int(w.w);
     float limit = best_t + m.slack;
-    float x0 = (a.x - o.x) * ix, x1 = (a.y - o.x) * ix, y0 = (a.z - o.y) * iy, y1 = (a.w - o.y) * iy;
-    float z0 = (c.x - o.z) * iz, z1 = (c.y - o.z) * iz;
+    float x0 = fmaf(a.x, ix, -ox), x1 = fmaf(a.y, ix, -ox), y0 = fmaf(a.z, iy, -oy), y1 = fmaf(a.w, iy, -oy);
+    float z0 = fmaf(c.x, iz, -oz), z1 = fmaf(c.y, iz, -oz);
     float lmin = fmaxf(fmaxf(fminf(x0, x1), fminf(y0, y1)), fmaxf(fminf(z0, z1), m.t_lo));
     float lmax = fminf(fminf(fmaxf(x0, x1), fmaxf(y0, y1)), fminf(fmaxf(z0, z1), limit));
-    x0 = (b.x - o.x) * ix; x1 = (b.y - o.x) * ix; y0 = (b.z - o.y) * iy; y1 = (b.w - o.y) * iy;
-    z0 = (c.z - o.z) * iz; z1 = (c.w - o.z) * iz;
+    x0 = fmaf(b.x, ix, -ox); x1 = fmaf(b.y, ix, -ox); y0 = fmaf(b.z, iy, -oy); y1 = fmaf(b.w, iy, -oy);
+    z0 = fmaf(c.z, iz, -oz); z1 = fmaf(c.w, iz, -oz);
     float rmin = fmaxf(fmaxf(fminf(x0, x1), fminf(y0, y1)), fmaxf(fminf(z0, z1), m.t_lo));
     float rmax = fminf(fminf(fmaxf(x0, x1), fmaxf(y0, y1)), fminf(fmaxf(z0, z1), limit));
     bool hl = lmin <= lmax, hr = rmin <= rmax;
@@ -246,9 +277,199 @@ __device__ __forceinline__ void sample_ray(const DevMesh& m, uint32_t k0, uint32
 }
 
 constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
+constexpr int kRing = 64;         // rays per warp ring (two sampling rounds)
+constexpr int kRefillLanes = 16;  // finished lanes of a warp that trigger a refill
 
+struct Ring {  // one warp's sampled rays, structure of arrays in shared memory
+  float ox[kRing], oy[kRing], oz[kRing], dx[kRing], dy[kRing], dz[kRing];
+  int32_t src[kRing];
+};
+
+struct Walker {
+  V3 o, d;
+  float ix, iy, iz;
+  int32_t src;
+  float best_t;
+  int32_t best_id, best_face;
+  int32_t node;
+  int sp;
+};
+
+template <bool E, class St>
+__device__ __forceinline__ void test_leaf(const DevMesh& m, Walker& w, int32_t ref, int32_t cnt, St& st) {
+  for (int q = 0; q < cnt; ++q) {
+    test_record<E>(m.tris + 3 * (int64_t)(ref + q), w.src, w.o, w.d, w.best_t, w.best_id, w.best_face);
+    st.tri();
+  }
+}
+
+// One BVH node visit. Returns false once the ray's traversal is complete.
+template <bool E, class St>
+__device__ __forceinline__ bool visit(const DevMesh& m, Walker& w, int32_t* stack, bool* overflow, St& st) {
+  const float4* nd = m.nodes + 4 * w.node;
+  const float4 a = __ldg(nd), b = __ldg(nd + 1), c = __ldg(nd + 2), q = __ldg(nd + 3);
+  const int32_t refL = __float_as_int(q.x), refR = __float_as_int(q.y);
+  const int32_t cntL = __float_as_int(q.z), cntR = __float_as_int(q.w);
+  const float limit = w.best_t + m.slack;
+  const float ox = w.o.x * w.ix, oy = w.o.y * w.iy, oz = w.o.z * w.iz;
+  float x0 = fmaf(a.x, w.ix, -ox), x1 = fmaf(a.y, w.ix, -ox), y0 = fmaf(a.z, w.iy, -oy), y1 = fmaf(a.w, w.iy, -oy);
+  float z0 = fmaf(c.x, w.iz, -oz), z1 = fmaf(c.y, w.iz, -oz);
+  const float lmin = fmaxf(fmaxf(fminf(x0, x1), fminf(y0, y1)), fmaxf(fminf(z0, z1), m.t_lo));
+  const float lmax = fminf(fminf(fmaxf(x0, x1), fmaxf(y0, y1)), fminf(fmaxf(z0, z1), limit));
+  x0 = fmaf(b.x, w.ix, -ox); x1 = fmaf(b.y, w.ix, -ox); y0 = fmaf(b.z, w.iy, -oy); y1 = fmaf(b.w, w.iy, -oy);
+  z0 = fmaf(c.z, w.iz, -oz); z1 = fmaf(c.w, w.iz, -oz);
+  const float rmin = fmaxf(fmaxf(fminf(x0, x1), fminf(y0, y1)), fmaxf(fminf(z0, z1), m.t_lo));
+  const float rmax = fminf(fminf(fmaxf(x0, x1), fmaxf(y0, y1)), fminf(fmaxf(z0, z1), limit));
+  bool hl = lmin <= lmax, hr = rmin <= rmax;
+  st.box(2);
+  if (hl && cntL > 0) { test_leaf<E>(m, w, refL, cntL, st); hl = false; }
+  if (hr && cntR > 0) { test_leaf<E>(m, w, refR, cntR, st); hr = false; }
+  if (hl && hr) {
+    const bool left_first = lmin <= rmin;
+    if (w.sp >= kTraceStack) { *overflow = true; return false; }
+    stack[w.sp++] = left_first ? refR : refL;
+    w.node = left_first ? refL : refR;
+  } else if (hl) {
+    w.node = refL;
+  } else if (hr) {
+    w.node = refR;
+  } else {
+    if (w.sp == 0) return false;
+    w.node = stack[--w.sp];
+  }
+  return true;
+}
+
+__device__ __forceinline__ void start_ray(Walker& w, const Ring& r, int k, int32_t env) {
+  w.o = V3{r.ox[k], r.oy[k], r.oz[k]};
+  w.d = V3{r.dx[k], r.dy[k], r.dz[k]};
+  w.ix = rcp_approx(w.d.x);
+  w.iy = rcp_approx(w.d.y);
+  w.iz = rcp_approx(w.d.z);
+  w.src = r.src[k];
+  w.best_t = __int_as_float(0x7f800000);
+  w.best_id = INT_MAX;
+  w.best_face = env;
+  w.node = 0;
+  w.sp = 0;
+}
+
+// Refill variant (see the file comment). Best when traversals are long and uneven.
 template <bool E, bool kBVH, class St>
-__global__ void __launch_bounds__(kThreads, 2) trace_kernel(const TraceParams p) {
+__global__ void __launch_bounds__(kThreads, RG_REFILL_MIN_BLOCKS) trace_kernel_refill(const TraceParams p) {
+  extern __shared__ __align__(16) uint32_t hist[];
+  __shared__ Ring s_ring[kWarps];
+  __shared__ int32_t s_item;
+  __shared__ int32_t s_next;
+  const int lane = threadIdx.x & 31;
+  const unsigned lt_mask = (1u << lane) - 1u;
+  Ring& ring = s_ring[threadIdx.x >> 5];
+  bool overflow = false;
+  St st;
+  unsigned long long n_rays = 0;
+  int32_t stack[kTraceStack];
+  const DevMesh& m = p.m;
+  while (true) {
+    if (threadIdx.x == 0) {
+      s_item = atomicAdd(p.item_counter, 1);
+      s_next = 0;
+    }
+    for (int b = threadIdx.x; b < p.n_bins; b += kThreads) hist[b] = 0u;
+    __syncthreads();
+    const int32_t item = s_item;
+    if (item >= p.n_items) break;
+    const WorkItem wi = p.items[item];
+    // warp-uniform ring state: `avail` sampled rays from position `head`
+    int head = 0, avail = 0;
+    bool more = true;  // rays of the item left to sample
+    bool has_ray = false, done = false;
+    Walker w;
+    while (true) {
+      if (has_ray && !done) {
+        if (kBVH) {
+          done = !visit<E>(m, w, stack, &overflow, st);
+        } else {
+          for (int64_t t = 0; t < m.nt; ++t) {
+            test_record<E>(m.tris + 3 * t, w.src, w.o, w.d, w.best_t, w.best_id, w.best_face);
+            st.tri();
+          }
+          done = true;
+        }
+      }
+      const unsigned tracing = __ballot_sync(0xffffffffu, has_ray && !done);
+      const unsigned idle = ~tracing;
+      if (tracing && __popc(idle) < kRefillLanes) continue;
+      // ---- refill: tally finished rays, then hand out new ones
+      const unsigned fin = __ballot_sync(0xffffffffu, has_ray && done);
+      if (has_ray && done) {
+        const unsigned peers = __match_any_sync(fin, w.best_face);
+        if (lane == __ffs(peers) - 1) atomicAdd(&hist[w.best_face], (uint32_t)__popc(peers));
+        ++n_rays;
+        has_ray = false;
+      }
+      const int need = __popc(idle);
+      if (avail < need && more) {  // sample 32 rays, all lanes in step
+        int base = 0;
+        if (lane == 0) base = atomicAdd(&s_next, 32);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        const int r = base + lane;
+        const bool valid = r < wi.count;
+        const unsigned vm = __ballot_sync(0xffffffffu, valid);
+        if (valid) {
+          V3 o, d;
+          int32_t src;
+          sample_ray<E>(m, p.key0, p.key1, p.ray_offset + (uint64_t)(wi.begin + r), wi.face, &o, &d, &src);
+          const int slot = (head + avail + lane) & (kRing - 1);
+          ring.ox[slot] = o.x; ring.oy[slot] = o.y; ring.oz[slot] = o.z;
+          ring.dx[slot] = d.x; ring.dy[slot] = d.y; ring.dz[slot] = d.z;
+          ring.src[slot] = src;
+        }
+        avail += __popc(vm);
+        if (base + 32 >= wi.count) more = false;
+        __syncwarp();
+      }
+      const int rank = __popc(idle & lt_mask);
+      if (!(tracing >> lane & 1u) && rank < avail) {
+        start_ray(w, ring, (head + rank) & (kRing - 1), m.n_faces);
+        has_ray = true;
+        done = false;
+      }
+      const int used = min(need, avail);
+      head = (head + used) & (kRing - 1);
+      avail -= used;
+      __syncwarp();
+      if (!__any_sync(0xffffffffu, has_ray)) break;  // ring empty and nothing left to sample
+    }
+    __syncthreads();
+    unsigned long long* row = p.counts + (int64_t)wi.face * p.n_bins;
+    for (int b = threadIdx.x; b < p.n_bins; b += kThreads) {
+      uint32_t c = hist[b];
+      if (c) atomicAdd(row + b, (unsigned long long)c);
+    }
+    __syncthreads();
+  }
+  if (overflow) atomicExch(p.error_word, 1);
+  if constexpr (sizeof(St) > 1) {
+    for (int o = 16; o > 0; o >>= 1) {
+      n_rays += __shfl_xor_sync(0xffffffffu, n_rays, o);
+      st.n_box += __shfl_xor_sync(0xffffffffu, st.n_box, o);
+      st.n_tri += __shfl_xor_sync(0xffffffffu, st.n_tri, o);
+    }
+    if (lane == 0) {
+      atomicAdd(p.stats, n_rays);
+      atomicAdd(p.stats + 1, st.n_box);
+      atomicAdd(p.stats + 2, st.n_tri);
+    }
+  } else {
+    (void)n_rays;
+  }
+}
+
+// Lock-step variant: each lane traces one ray to completion, the warp samples its next
+// 32 rays together. Best when traversals are short and similar (few node visits).
+template <bool E, bool kBVH, class St>
+__global__ void __launch_bounds__(kThreads, RG_LOCKSTEP_MIN_BLOCKS) trace_kernel_lockstep(const TraceParams p) {
   extern __shared__ uint32_t hist[];
   __shared__ int32_t s_item;
   const int lane = threadIdx.x & 31;
@@ -306,9 +527,11 @@ __global__ void __launch_bounds__(kThreads, 2) trace_kernel(const TraceParams p)
   }
 }
 
+inline size_t trace_smem_bytes(int n_bins) { return (size_t)((n_bins + 3) & ~3) * sizeof(uint32_t); }
+
 template <bool E, bool B, class St>
 cudaError_t launch(const TraceParams& p, int sm_count, size_t smem, cudaStream_t s) {
-  auto k = trace_kernel<E, B, St>;
+  auto k = p.m.refill ? trace_kernel_refill<E, B, St> : trace_kernel_lockstep<E, B, St>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int per_sm = 0;
@@ -329,7 +552,7 @@ rg_status trace_impl(rg_ctx* ctx, const rg_mesh* mesh, const int64_t* rays_per_f
   RG_ARG_CHECK(ctx, mesh_device(mesh) == ctx->device, "rg_trace: mesh belongs to another device");
   const int32_t N = m.n_faces;
   const int32_t n_bins = N + 1;
-  const size_t smem = (size_t)n_bins * sizeof(uint32_t);
+  const size_t smem = trace_smem_bytes(n_bins);
   if (n_bins > 49152 || (int)smem > ctx->smem_optin - 1024)
     return rg::fail(ctx, RG_ERR_UNSUPPORTED, "rg_trace: %d faces exceed the shared-memory tally row", N);
   // work items: chunks of at most kChunk rays of one face

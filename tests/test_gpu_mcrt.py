@@ -136,3 +136,32 @@ def test_bad_arguments_are_reported(rg_ctx):
     mesh = api.Mesh.from_synth(rg_ctx, m)
     with pytest.raises(api.RadgebError):
         api.trace(rg_ctx, mesh, np.array([-1, 1, 1, 1, 1, 1]), 0)
+
+
+@pytest.mark.parametrize("name", ["plates", "small_sat"])
+def test_lockstep_and_refill_schedules_agree(rg_ctx, name):
+    m = synth.workload(name)["mesh"]
+    rays = np.full(m.n_faces, 1500, np.int64)
+    rays[::7] = 65536 + 3
+    a, ma = _gpu_counts(rg_ctx, m, rays, 13, use_bvh=2)
+    b, mb = _gpu_counts(rg_ctx, m, rays, 13, use_bvh=3)
+    assert ma.info()["refill"] == 0 and mb.info()["refill"] == 1
+    assert np.array_equal(a, b)
+    rows = [0, 5, m.n_faces // 2, m.n_faces - 1]
+    o = mcrt.trace_counts(m.verts, m.tris, m.tri_face, m.n_faces, rays, 13, use_bvh=True, faces=rows)
+    for r in rows:
+        assert np.array_equal(a[r], o[r])
+
+
+def test_rays_with_zero_direction_components(rg_ctx):
+    """Ray 2731 of face 12 (seed 0) has a direction component of exactly 0 (one ray in
+    2^24 has one): the slab tests must not cull the boxes it passes through."""
+    m = synth.plates(16)
+    _, d, _, _ = mcrt.sample_rays(m.verts, m.tris, m.tri_face, m.n_faces, 12, 0, 0, 3000)
+    assert d[2731, 1] == 0.0                  # the case is really exercised
+    rays = np.zeros(m.n_faces, np.int64)
+    rays[12] = 3000
+    for sched in (2, 3):
+        g, _ = _gpu_counts(rg_ctx, m, rays, 0, use_bvh=sched)
+        o = mcrt.trace_counts(m.verts, m.tris, m.tri_face, m.n_faces, rays, 0, use_bvh=False, faces=[12])
+        assert np.array_equal(g, o), sched
