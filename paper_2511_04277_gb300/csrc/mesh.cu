@@ -29,7 +29,7 @@ const DevMesh& mesh_device_view(const rg_mesh* m) { return m->dev; }
 
 // BVH depth from which the trace kernel refills finished lanes (measured on GB300: the
 // 1,024-triangle plates, depth 8, run 1.5x faster lock-step; the 20,736- and
-// 204,512-triangle spacecraft meshes, depths 14 and 19, run 1.6-2x faster with refills).
+// 204,512-triangle spacecraft meshes, depths 14 and 19, run 3-7 % faster with refills).
 constexpr int kRefillDepth = 12;
 int mesh_device(const rg_mesh* m) { return m->ctx->device; }
 

@@ -2,10 +2,15 @@
 //
 // One persistent kernel: each block repeatedly takes a work item (one face, a range
 // of its rays) and keeps a shared-memory tally row of N+1 counters for that face. The
-// warps of the block share the item's rays through a counter; each warp runs one
-// warp-synchronous loop whose iteration is one BVH node visit per lane (child-box slab
-// tests, Moller-Trumbore tests of leaf triangles, stack push/pop). Lanes whose ray is
-// finished wait until half of the warp is; then their rays go to the tally row
+// warps of the block share the item's rays through a counter. Two schedules (chosen per
+// mesh, identical counts):
+//   lock-step (shallow BVHs): the warp samples 32 rays in step, gives each one root
+//     visit, tallies the rays already finished (most rays leaving the scene) and queues
+//     the rest; queued rays are traced to completion 32 at a time;
+//   refill (deep BVHs): each warp runs one warp-synchronous loop whose iteration is one
+//     BVH node visit per lane (child-box slab tests, Moller-Trumbore tests of leaf
+//     triangles, stack push/pop). Lanes whose ray is finished wait until 24 of the 32
+//     lanes are; then their rays go to the tally row
 // (aggregated per target face) and they take new rays from a private 64-ray ring in
 // shared memory, which the whole warp refills 32 rays at a time, in step, when it runs
 // short (Philox4x32-10 draws, area-CDF triangle choice, uniform point lifted off the
@@ -279,7 +284,10 @@ __device__ __forceinline__ void sample_ray(const DevMesh& m, uint32_t k0, uint32
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
 constexpr int kRing = 64;         // rays per warp ring (two sampling rounds)
-constexpr int kRefillLanes = 16;  // finished lanes of a warp that trigger a refill
+#ifndef RG_REFILL_LANES
+#define RG_REFILL_LANES 24
+#endif
+constexpr int kRefillLanes = RG_REFILL_LANES;  // finished lanes of a warp that trigger a refill
 
 struct Ring {  // one warp's sampled rays, structure of arrays in shared memory
   float ox[kRing], oy[kRing], oz[kRing], dx[kRing], dy[kRing], dz[kRing];
@@ -466,44 +474,126 @@ __global__ void __launch_bounds__(kThreads, RG_REFILL_MIN_BLOCKS) trace_kernel_r
   }
 }
 
-// Lock-step variant: each lane traces one ray to completion, the warp samples its next
-// 32 rays together. Best when traversals are short and similar (few node visits).
+// Lock-step variant for shallow BVHs. Each round the warp samples 32 rays in step and
+// gives every ray one node visit (the root); rays that are finished by then (typically
+// those leaving the scene) go straight to the tally, and the others are queued in a
+// per-warp shared-memory queue. Whenever 32 rays are queued the warp traces them from
+// the root to completion in step, so the long traversals run with full warps instead
+// of next to lanes that finished after one visit.
 template <bool E, bool kBVH, class St>
 __global__ void __launch_bounds__(kThreads, RG_LOCKSTEP_MIN_BLOCKS) trace_kernel_lockstep(const TraceParams p) {
-  extern __shared__ uint32_t hist[];
+  extern __shared__ __align__(16) uint32_t hist[];
+  __shared__ Ring s_queue[kWarps];
   __shared__ int32_t s_item;
+  __shared__ int32_t s_next;
   const int lane = threadIdx.x & 31;
-  const int warp = threadIdx.x >> 5;
+  const unsigned lt_mask = (1u << lane) - 1u;
+  Ring& q = s_queue[threadIdx.x >> 5];
   bool overflow = false;
   St st;
   unsigned long long n_rays = 0;
+  int32_t stack[kTraceStack];
+  const DevMesh& m = p.m;
+
+  auto tally = [&](bool fin, int32_t face) {
+    const unsigned fm = __ballot_sync(0xffffffffu, fin);
+    if (fin) {
+      const unsigned peers = __match_any_sync(fm, face);
+      if (lane == __ffs(peers) - 1) atomicAdd(&hist[face], (uint32_t)__popc(peers));
+      ++n_rays;
+    }
+  };
+  // Trace the queued rays q[0 .. count) (count <= 32) from the root to completion.
+  auto drain = [&](int count) {
+    const bool has = lane < count;
+    Walker w;
+    if (has) start_ray(w, q, lane, m.n_faces);
+    bool more = has;
+    while (__any_sync(0xffffffffu, more)) {
+      if (more) more = visit<E>(m, w, stack, &overflow, st);
+    }
+    tally(has, has ? w.best_face : 0);
+  };
+
   while (true) {
-    if (threadIdx.x == 0) s_item = atomicAdd(p.item_counter, 1);
+    if (threadIdx.x == 0) {
+      s_item = atomicAdd(p.item_counter, 1);
+      s_next = 0;
+    }
     for (int b = threadIdx.x; b < p.n_bins; b += kThreads) hist[b] = 0u;
     __syncthreads();
     const int32_t item = s_item;
     if (item >= p.n_items) break;
-    const WorkItem w = p.items[item];
-    for (int32_t base = warp * 32; base < w.count; base += kThreads) {
-      const int32_t r = base + lane;
-      const bool valid = r < w.count;
-      int32_t bin = 0;
+    const WorkItem wi = p.items[item];
+    int queued = 0;  // warp-uniform
+    while (true) {
+      int base = 0;
+      if (lane == 0) base = atomicAdd(&s_next, 32);
+      base = __shfl_sync(0xffffffffu, base, 0);
+      if (base >= wi.count) break;
+      const int r = base + lane;
+      const bool valid = r < wi.count;
+      V3 o, d;
+      int32_t src = -1;
+      if (valid) sample_ray<E>(m, p.key0, p.key1, p.ray_offset + (uint64_t)(wi.begin + r), wi.face, &o, &d, &src);
+      bool more = false;
+      int32_t face = m.n_faces;
       if (valid) {
-        V3 o, d;
-        int32_t src;
-        sample_ray<E>(p.m, p.key0, p.key1, p.ray_offset + (uint64_t)(w.begin + r), w.face, &o, &d, &src);
-        bin = closest_face<E, kBVH>(p.m, src, o, d, &overflow, st);
-        ++n_rays;
+        if (kBVH) {
+          Walker w;
+          w.o = o; w.d = d;
+          w.ix = rcp_approx(d.x); w.iy = rcp_approx(d.y); w.iz = rcp_approx(d.z);
+          w.src = src;
+          w.best_t = __int_as_float(0x7f800000);
+          w.best_id = INT_MAX;
+          w.best_face = m.n_faces;
+          w.node = 0;
+          w.sp = 0;
+          more = visit<E>(m, w, stack, &overflow, st);
+          face = w.best_face;
+        } else {
+          face = closest_face<E, false>(m, src, o, d, &overflow, st);
+        }
       }
+      tally(valid && !more, face);
+      // queue the rays that need more visits; they restart from the root
+      const unsigned sm = __ballot_sync(0xffffffffu, more);
+      if (more) {
+        const int slot = queued + __popc(sm & lt_mask);
+        q.ox[slot] = o.x; q.oy[slot] = o.y; q.oz[slot] = o.z;
+        q.dx[slot] = d.x; q.dy[slot] = d.y; q.dz[slot] = d.z;
+        q.src[slot] = src;
+      }
+      queued += __popc(sm);
       __syncwarp();
-      const unsigned vmask = __ballot_sync(0xffffffffu, valid);
-      if (valid) {
-        const unsigned peers = __match_any_sync(vmask, bin);
-        if (lane == __ffs(peers) - 1) atomicAdd(&hist[bin], (uint32_t)__popc(peers));
+      if (queued >= 32) {
+        drain(32);
+        __syncwarp();
+        // move the overflow (queued - 32 <= 31 rays) to the front
+        const int rest = queued - 32;
+        float ox = 0.f, oy = 0.f, oz = 0.f, dx = 0.f, dy = 0.f, dz = 0.f;
+        int32_t sr = 0;
+        if (lane < rest) {
+          ox = q.ox[32 + lane]; oy = q.oy[32 + lane]; oz = q.oz[32 + lane];
+          dx = q.dx[32 + lane]; dy = q.dy[32 + lane]; dz = q.dz[32 + lane];
+          sr = q.src[32 + lane];
+        }
+        __syncwarp();
+        if (lane < rest) {
+          q.ox[lane] = ox; q.oy[lane] = oy; q.oz[lane] = oz;
+          q.dx[lane] = dx; q.dy[lane] = dy; q.dz[lane] = dz;
+          q.src[lane] = sr;
+        }
+        __syncwarp();
+        queued = rest;
       }
     }
+    if (queued > 0) {
+      drain(queued);
+      __syncwarp();
+    }
     __syncthreads();
-    unsigned long long* row = p.counts + (int64_t)w.face * p.n_bins;
+    unsigned long long* row = p.counts + (int64_t)wi.face * p.n_bins;
     for (int b = threadIdx.x; b < p.n_bins; b += kThreads) {
       uint32_t c = hist[b];
       if (c) atomicAdd(row + b, (unsigned long long)c);
