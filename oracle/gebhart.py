@@ -46,6 +46,13 @@ def gebhart(F, eps, rho):
     return np.linalg.solve(k_matrix(F, rho), e_matrix(F, eps))
 
 
+def gebhart_rows(F, eps, rho, rows):
+    """Selected rows of B = K^-1 E (Eq. B.11): B[rows] = Y^T E with K^T Y = I[:, rows]."""
+    K = k_matrix(F, rho)
+    Y = np.linalg.solve(K.T, np.eye(K.shape[0])[:, list(rows)])
+    return Y.T @ e_matrix(F, eps)
+
+
 def gebhart_batched(F, eps_sets, rho_sets):
     """One REF matrix per (eps, rho) set: [S, N, N+1]."""
     return np.stack([gebhart(F, e, r) for e, r in zip(eps_sets, rho_sets)])

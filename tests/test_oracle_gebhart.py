@@ -16,6 +16,17 @@ def test_plates_B_matches_eq_6_11():
     assert np.abs(B - load_matrix("plates_B.txt")).max() <= 5e-7
 
 
+def test_gebhart_rows_match_printed_plates_B_and_the_full_solve():
+    F = load_matrix("plates_F.txt")
+    eps = np.full(4, 0.5)
+    assert np.abs(G.gebhart_rows(F, eps, 1 - eps, [3, 1]) - load_matrix("plates_B.txt")[[3, 1]]).max() <= 5e-7
+    rng = np.random.default_rng(4)
+    F, _ = _consistent_F(40, rng)
+    eps = rng.uniform(0.05, 0.9, 40)
+    rows = [0, 17, 39]
+    assert np.abs(G.gebhart_rows(F, eps, 1 - eps, rows) - G.gebhart(F, eps, 1 - eps)[rows]).max() <= 1e-14
+
+
 def test_table_6_2_temperatures():
     F = load_matrix("plates_F.txt")
     t = load_table("plates_table_6_2.txt")
