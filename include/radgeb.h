@@ -224,10 +224,11 @@ rg_status rg_aggregate(rg_ctx* ctx, int32_t n_sub, const double* F_sub_d, const 
  *   B_d      device fp64 [n_sets][n][n+1] (output)
  *   tol      refinement stops when max_ij |R_ij| <= tol * max_ij |B_ij| for the
  *            residual R = E - K B of every set (tol >= 1e-13). The residual product is
- *            accumulated in compensated fp32 chunks, so the attainable accuracy of B
- *            is about 1e-8 relative whatever smaller tol is asked for; once the
- *            residual is below 1e-9 a sweep that fails to halve it also ends the
- *            refinement (stagnation at that floor counts as converged).
+ *            accumulated in compensated fp32 chunks, so the attainable residual is
+ *            about 1e-10 to 1e-9 relative whatever smaller tol is asked for; once
+ *            the residual is below 1e-8 a sweep that fails to halve it also ends
+ *            the refinement (stagnation at that floor counts as converged, and
+ *            resid_out_h reports where it stopped).
  *   max_sweeps  refinement sweeps at most (>= 1)
  *   sweeps_out_h host int32 (may be NULL); resid_out_h host fp64 (may be NULL):
  *            the final relative residual (max over sets)

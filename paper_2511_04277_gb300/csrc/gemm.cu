@@ -119,7 +119,8 @@ rg_status gemm_f32(rg_ctx* ctx, bool bf16, const void* A, int64_t lda, const voi
 
 rg_status gemm_residual(rg_ctx* ctx, const void* A, int64_t lda, const void* B, int64_t ldb, int M, int N, int K,
                         int chunk_blocks, double* out, const double* E, const double* X, const double* dl,
-                        int64_t ld, cudaStream_t s) {
+                        int64_t ld, cudaStream_t s, unsigned long long* red, unsigned long long* colmax,
+                        int* nonfinite) {
   if (M <= 0 || N <= 0) return RG_OK;
   if (K <= 0) return rg::fail(ctx, RG_ERR_ARG, "gemm_residual: K = %d", K);
   constexpr int BN = 64;
@@ -128,7 +129,7 @@ rg_status gemm_residual(rg_ctx* ctx, const void* A, int64_t lda, const void* B, 
   if (st == RG_OK) st = encode_kmajor(ctx, &mb, B, true, N, K, ldb, BN);
   if (st != RG_OK) return st;
   GemmArgs args{M, N, K, chunk_blocks, ctx->d_scratch + kGemmErrorSlot};
-  EpiResidual epi{out, E, X, dl, ld};
+  EpiResidual epi{out, E, X, dl, ld, red, colmax, nonfinite};
   return launch<BN, 6, EpiResidual, true, true>(ctx, ma, mb, args, epi, s);
 }
 

@@ -235,21 +235,58 @@ struct EpiAddF64 {
   }
 };
 
+// Largest non-negative double into *dst (its bit pattern orders like the value).
+__device__ __forceinline__ void atomic_max_nonneg(unsigned long long* dst, double x) {
+  atomicMax(dst, (unsigned long long)__double_as_longlong(x));
+}
+
 // out[r][c] = E[r][c] - X[r][c] + dl[r] * acc   (fp64; the refinement residual), or
-// out[r][c] = dl[r] * acc when E is null (an fp64-accurate product)
+// out[r][c] = dl[r] * acc when E is null (an fp64-accurate product). With `red` set it
+// also folds max|out| into red[0], max|X| into red[1], max_r |out[r][c]| into
+// colmax[c] (all as double bits) and raises *nonfinite on an inf or NaN.
 struct EpiResidual {
   double* out;
   const double* E;   // may be null together with X
   const double* X;
   const double* dl;  // may be null (identity)
   int64_t ld;        // shared leading dimension of out, E and X
+  unsigned long long* red = nullptr;     // [2], zeroed by the caller
+  unsigned long long* colmax = nullptr;  // [N], zeroed by the caller (may be null)
+  int* nonfinite = nullptr;
   __device__ __forceinline__ void store(int row0, int lane, int c0, int M, int N, const double* v,
                                         double (*stage)[33]) const {
+    double m_out = 0.0, m_x = 0.0;
+    bool bad = false;
     staged_rows(row0, lane, c0, M, N, v, stage, [&](int r, int c, double x) {
       const double s = dl ? dl[r] : 1.0;
       const int64_t i = (int64_t)r * ld + c;
-      out[i] = E ? (E[i] - X[i]) + s * x : s * x;
+      double o;
+      if (E) {
+        const double xi = X[i];
+        o = (E[i] - xi) + s * x;
+        m_x = fmax(m_x, fabs(xi));
+        bad |= !isfinite(xi);
+      } else {
+        o = s * x;
+      }
+      out[i] = o;
+      m_out = fmax(m_out, fabs(o));
+      bad |= !isfinite(o);
     });
+    if (red) {
+      // this lane saw column c0 + lane of the warp's 32 rows
+      if (colmax && c0 + lane < N) atomic_max_nonneg(&colmax[c0 + lane], m_out);
+      for (int o = 16; o > 0; o >>= 1) {
+        m_out = fmax(m_out, __shfl_xor_sync(0xffffffffu, m_out, o));
+        m_x = fmax(m_x, __shfl_xor_sync(0xffffffffu, m_x, o));
+      }
+      bad = __any_sync(0xffffffffu, bad);
+      if (lane == 0) {
+        atomic_max_nonneg(&red[0], m_out);
+        atomic_max_nonneg(&red[1], m_x);
+        if (bad && nonfinite) atomicExch(nonfinite, 1);
+      }
+    }
   }
 };
 
@@ -446,7 +483,8 @@ rg_status gemm_f32(rg_ctx* ctx, bool bf16, const void* A, int64_t lda, const voi
 // compensated sum.
 rg_status gemm_residual(rg_ctx* ctx, const void* A, int64_t lda, const void* B, int64_t ldb, int M, int N, int K,
                         int chunk_blocks, double* out, const double* E, const double* X, const double* dl,
-                        int64_t ld, cudaStream_t s);
+                        int64_t ld, cudaStream_t s, unsigned long long* red = nullptr,
+                        unsigned long long* colmax = nullptr, int* nonfinite = nullptr);
 
 // Device error word the GEMM kernels raise on a timed-out wait (ctx scratch slot).
 constexpr int kGemmErrorSlot = 16;

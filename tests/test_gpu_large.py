@@ -1,0 +1,146 @@
+"""The spacecraft-sized workloads at their full sizes.
+
+* MCRT on the small-satellite mesh (2,048 faces, 1e8 rays split by area) and on the
+  spacecraft mesh (10,240 faces, 1e9 rays) at the full ray budget, in the launch
+  configuration the library picks for them; rows are sampled and recomputed by the
+  oracle one by one, bit for bit.
+* REFs at N = 2,048 (both 16-bit precisions) against the oracle's full solve.
+* dT/deps and dT/drho of the steady balance at N = 2,048 through the autograd wrappers,
+  against the oracle's fp64 gradient and central differences.
+* REFs at N = 10,240 with 16 optical sets: sampled rows of two sets against the oracle,
+  closure and reciprocity (Eq. 4.3-4.4) over every set.
+"""
+import time
+
+import numpy as np
+import pytest
+import torch
+
+import synth
+from oracle import gebhart as G
+from oracle import mcrt
+from paper_2511_04277_gb300 import api, autograd
+
+pytestmark = pytest.mark.gpu
+
+REL = 1e-6
+
+
+def _dev(x, dtype=torch.float64):
+    return torch.as_tensor(np.ascontiguousarray(x)).to(dtype=dtype, device="cuda")
+
+
+def _rownorm_err(got, ref):
+    got, ref = np.asarray(got), np.asarray(ref)
+    scale = np.maximum(np.abs(ref).max(axis=-1), 1e-300)
+    return float((np.abs(got - ref).max(axis=-1) / scale).max())
+
+
+def _full_budget_rows(rg_ctx, name, rows):
+    w = synth.workload(name)
+    m = w["mesh"]
+    mesh = api.Mesh.from_synth(rg_ctx, m)
+    c = api.trace(rg_ctx, mesh, w["rays"], w["seed"]).cpu().numpy()
+    assert np.array_equal(c.sum(axis=1), w["rays"])
+    t0 = time.time()
+    o = mcrt.trace_counts(m.verts, m.tris, m.tri_face, m.n_faces, w["rays"], w["seed"], use_bvh=True, faces=rows)
+    print(f"{name}: oracle rows {rows} in {time.time() - t0:.1f} s")
+    for r in rows:
+        assert np.array_equal(c[r], o[r]), r
+
+
+def test_small_sat_full_budget_sampled_rows(rg_ctx):
+    _full_budget_rows(rg_ctx, "small_sat", [0, 777, 1500, 2047])
+
+
+def test_spacecraft_full_budget_sampled_rows(rg_ctx):
+    _full_budget_rows(rg_ctx, "spacecraft", [0, 5000, 10239])
+
+
+def _enforced_F(rg_ctx, name, rays_scale):
+    w = synth.workload(name, rays_scale=rays_scale)
+    mesh = api.Mesh.from_synth(rg_ctx, w["mesh"])
+    F = api.counts_to_F(rg_ctx, api.trace(rg_ctx, mesh, w["rays"], w["seed"]), _dev(w["rays"], torch.int64))
+    A = mesh.face_areas()
+    api.enforce_iterative(rg_ctx, F, _dev(A), tol=1e-12)
+    return w, F, A
+
+
+@pytest.mark.parametrize("prec", ["bf16", "fp16"])
+def test_gebhart_small_sat_n2048(rg_ctx, prec):
+    w, F, A = _enforced_F(rg_ctx, "small_sat", 0.02)
+    eps, rho = w["eps"][0], w["rho"][0]
+    B, sw, res = api.gebhart(rg_ctx, F, _dev(eps), _dev(rho), precision=prec, tol=1e-12)
+    Bo = G.gebhart(F.cpu().numpy(), eps, rho)
+    Bg = B[0].cpu().numpy()
+    assert _rownorm_err(Bg, Bo) <= REL
+    # Eq. 4.3; each row sums 2,049 entries and the residual product's fp32 accumulation
+    # on the tensor cores rounds toward zero, a bias of a few 1e-8 relative per entry
+    assert np.abs(Bg.sum(axis=1) - 1).max() <= 1e-6
+    assert res <= 1e-8
+
+
+def test_steady_temperature_gradients_small_sat(rg_ctx):
+    """Steady balance with Q ~ U[0, 50] W and a 3 K sink on the 2,048-face mesh."""
+    w, F, A = _enforced_F(rg_ctx, "small_sat", 0.02)
+    N = F.shape[0]
+    eps0, rho0 = w["eps"][0], w["rho"][0]
+    Q = synth.heat_loads(N, seed=3)
+    wT = np.random.default_rng(7).standard_normal(N)
+    eps = _dev(eps0).requires_grad_(True)
+    rho = _dev(rho0).requires_grad_(True)
+    T = autograd.steady_temperatures(rg_ctx, F, eps, rho, _dev(A), _dev(Q), 3.0)
+    loss = (T * _dev(wT)).sum()
+    loss.backward()
+    ge, gr = eps.grad.cpu().numpy(), rho.grad.cpu().numpy()
+
+    Fh = F.cpu().numpy()
+    To = G.temperatures(G.gebhart(Fh, eps0, rho0), eps0, A, Q, 3.0)
+    assert np.abs(T.detach().cpu().numpy() - To).max() <= REL * To.max()
+    geo, gro = G.thermal_gradients(Fh, eps0, rho0, A, Q, 3.0, wT)
+    assert np.abs(ge - geo).max() <= REL * np.abs(geo).max()
+    assert np.abs(gr - gro).max() <= REL * np.abs(gro).max()
+
+    # central differences of the fp64 oracle (h = 1e-6) on the faces of largest gradient
+    def L(e, r):
+        return float(np.sum(wT * G.temperatures(G.gebhart(Fh, e, r), e, A, Q, 3.0)))
+
+    h = 1e-6
+    for k in (int(np.argmax(np.abs(geo))), int(np.argmax(np.abs(gro)))):
+        d = np.zeros(N)
+        d[k] = h
+        fe = (L(eps0 + d, rho0) - L(eps0 - d, rho0)) / (2 * h)
+        fr = (L(eps0, rho0 + d) - L(eps0, rho0 - d)) / (2 * h)
+        assert abs(ge[k] - fe) <= 1e-5 * np.abs(geo).max()
+        assert abs(gr[k] - fr) <= 1e-5 * np.abs(gro).max()
+
+
+def test_gebhart_spacecraft_16_sets(rg_ctx):
+    w, F, A = _enforced_F(rg_ctx, "spacecraft", 0.01)
+    N = F.shape[0]
+    eps, rho = w["eps"], w["rho"]
+    S = eps.shape[0]
+    assert (N, S) == (10240, 16)
+    t0 = time.time()
+    B, sw, res = api.gebhart(rg_ctx, F, _dev(eps), _dev(rho), tol=1e-12)
+    torch.cuda.synchronize()
+    print(f"spacecraft REFs, 16 sets: {time.time() - t0:.2f} s, {sw} sweeps, residual {res:.2e}")
+    assert res <= 1e-8
+    # Eq. 4.3 (closure with the environment column) on every row of every set: each row
+    # sums 10,241 entries whose errors (~1e-11 each) add up
+    assert (B.sum(dim=2) - 1).abs().max().item() <= 1e-6
+    # Eq. 4.4 (eps_i A_i B_ij = eps_j A_j B_ji) on sampled rows of every set
+    rows = [0, 3333, 6000, 10239]
+    Ad, ed = _dev(A), _dev(eps)
+    for s in range(S):
+        for i in rows:
+            lhs = ed[s, i] * Ad[i] * B[s, i, :N]
+            rhs = ed[s] * Ad * B[s, :, i]
+            assert (lhs - rhs).abs().max().item() <= REL * lhs.abs().max().item()
+    # sampled rows of two sets against the oracle (fp64 LU of K^T)
+    Fh = F.cpu().numpy()
+    for s in (0, S - 1):
+        t0 = time.time()
+        Bo = G.gebhart_rows(Fh, eps[s], rho[s], rows)
+        print(f"oracle rows of set {s}: {time.time() - t0:.1f} s")
+        assert _rownorm_err(B[s, rows].cpu().numpy(), Bo) <= REL

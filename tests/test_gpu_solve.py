@@ -78,7 +78,7 @@ def test_gebhart_plates_example(rg_ctx):
     eps = np.full(4, 0.5)
     B, sw, res = api.gebhart(rg_ctx, _dev(F), _dev(eps), _dev(1 - eps), tol=1e-13)
     assert np.abs(B[0].cpu().numpy() - load_matrix("plates_B.txt")).max() <= 5e-7
-    assert res <= 1e-9
+    assert res <= 1e-8
 
 
 @pytest.mark.parametrize("N", [1, 6, 127, 128, 129, 300, 512])
@@ -90,8 +90,8 @@ def test_gebhart_random_sizes(rg_ctx, N, prec):
     B, sw, res = api.gebhart(rg_ctx, _dev(F), _dev(eps), _dev(1 - eps), precision=prec, tol=1e-12)
     Bo = G.gebhart(F, eps, 1 - eps)
     assert _rownorm_err(B[0].cpu().numpy(), Bo) <= REL
-    # converged to tol, or stalled below 1e-9 (the residual product's accuracy floor)
-    assert res <= 1e-9 and sw >= 1
+    # converged to tol, or stalled below 1e-8 (above the residual product's accuracy floor)
+    assert res <= 1e-8 and sw >= 1
 
 
 def test_gebhart_batched_sets_and_identities(rg_ctx):
