@@ -95,9 +95,9 @@ __device__ __forceinline__ uint4 philox(uint4 c, uint32_t k0, uint32_t k1) {
       k0 += 0x9E3779B9u;
       k1 += 0xBB67AE85u;
     }
-    uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
-    uint32_t hi2 = __umulhi(0xCD9E8D57u, c.z), lo2 = 0xCD9E8D57u * c.z;
-    c = make_uint4(hi2 ^ c.y ^ k0, lo2, hi0 ^ c.w ^ k1, lo0);
+    // one 32 x 32 -> 64-bit product gives both halves
+    const uint64_t p0 = (uint64_t)0xD2511F53u * c.x, p2 = (uint64_t)0xCD9E8D57u * c.z;
+    c = make_uint4((uint32_t)(p2 >> 32) ^ c.y ^ k0, (uint32_t)p2, (uint32_t)(p0 >> 32) ^ c.w ^ k1, (uint32_t)p0);
   }
   return c;
 }
@@ -167,6 +167,26 @@ __device__ __forceinline__ float rcp_approx(float x) {
   return r;
 }
 
+// Three-input min / max (one instruction each on sm_100 and later).
+__device__ __forceinline__ float max3f(float a, float b, float c) {
+  float r;
+  asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+  return r;
+}
+__device__ __forceinline__ float min3f(float a, float b, float c) {
+  float r;
+  asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+  return r;
+}
+
+// Entry and exit parameters of the ray in a box given the slab parameters of its faces:
+// [max(min x, min y, min z, lo), min(max x, max y, max z, hi)].
+__device__ __forceinline__ void slab_window(float x0, float x1, float y0, float y1, float z0, float z1, float lo,
+                                            float hi, float& tmin, float& tmax) {
+  tmin = max3f(fminf(x0, x1), fminf(y0, y1), fmaxf(fminf(z0, z1), lo));
+  tmax = min3f(fmaxf(x0, x1), fmaxf(y0, y1), fminf(fmaxf(z0, z1), hi));
+}
+
 // Closest hit; returns the face index or n_faces (environment). Sets *overflow on a
 // traversal stack overflow.
 template <bool E, bool kBVH, class St>
@@ -193,14 +213,11 @@ __device__ int32_t closest_face(const DevMesh& m, int32_t src, V3 o, V3 d, bool*
     int32_t refL = __float_as_int(w.x), refR = __float_as_int(w.y);
     int32_t cntL = __float_as_int(w.z), cntR = __float_as_int(w.w);
     float limit = best_t + m.slack;
-    float x0 = fmaf(a.x, ix, -ox), x1 = fmaf(a.y, ix, -ox), y0 = fmaf(a.z, iy, -oy), y1 = fmaf(a.w, iy, -oy);
-    float z0 = fmaf(c.x, iz, -oz), z1 = fmaf(c.y, iz, -oz);
-    float lmin = fmaxf(fmaxf(fminf(x0, x1), fminf(y0, y1)), fmaxf(fminf(z0, z1), m.t_lo));
-    float lmax = fminf(fminf(fmaxf(x0, x1), fmaxf(y0, y1)), fminf(fmaxf(z0, z1), limit));
-    x0 = fmaf(b.x, ix, -ox); x1 = fmaf(b.y, ix, -ox); y0 = fmaf(b.z, iy, -oy); y1 = fmaf(b.w, iy, -oy);
-    z0 = fmaf(c.z, iz, -oz); z1 = fmaf(c.w, iz, -oz);
-    float rmin = fmaxf(fmaxf(fminf(x0, x1), fminf(y0, y1)), fmaxf(fminf(z0, z1), m.t_lo));
-    float rmax = fminf(fminf(fmaxf(x0, x1), fmaxf(y0, y1)), fminf(fmaxf(z0, z1), limit));
+    float lmin, lmax, rmin, rmax;
+    slab_window(fmaf(a.x, ix, -ox), fmaf(a.y, ix, -ox), fmaf(a.z, iy, -oy), fmaf(a.w, iy, -oy), fmaf(c.x, iz, -oz),
+                fmaf(c.y, iz, -oz), m.t_lo, limit, lmin, lmax);
+    slab_window(fmaf(b.x, ix, -ox), fmaf(b.y, ix, -ox), fmaf(b.z, iy, -oy), fmaf(b.w, iy, -oy), fmaf(c.z, iz, -oz),
+                fmaf(c.w, iz, -oz), m.t_lo, limit, rmin, rmax);
     bool hl = lmin <= lmax, hr = rmin <= rmax;
     st.box(2);
     if (hl && cntL > 0) {
@@ -240,14 +257,14 @@ __device__ __forceinline__ void sample_ray(const DevMesh& m, uint32_t k0, uint32
   using A = Ar<E>;
   const uint32_t rlo = (uint32_t)ray, rhi = (uint32_t)(ray >> 32);
   uint4 x = philox(make_uint4(rlo, rhi, (uint32_t)face, 0u), k0, k1);
-  int64_t lo = m.face_start[face], hi = m.face_start[face + 1];
-  // first record whose threshold exceeds x.x (thresholds are non-decreasing)
-  int64_t a = lo, b = hi - 1;
+  // first record whose threshold exceeds x.x (thresholds are non-decreasing; meshes
+  // have fewer than 2^30 triangles)
+  int32_t a = (int32_t)m.face_start[face], b = (int32_t)m.face_start[face + 1] - 1;
   while (a < b) {
-    int64_t mid = (a + b) >> 1;
+    const int32_t mid = (a + b) >> 1;
     if (x.x < __ldg(m.ethr + mid)) b = mid; else a = mid + 1;
   }
-  const float4* rec = m.etris + 3 * a;
+  const float4* rec = m.etris + 3 * (int64_t)a;
   float4 r0 = __ldg(rec), r1 = __ldg(rec + 1), r2 = __ldg(rec + 2);
   *src = __float_as_int(r2.y);
   float u = unit24(x.y), v = unit24(x.z);
@@ -321,14 +338,11 @@ __device__ __forceinline__ bool visit(const DevMesh& m, Walker& w, int32_t* stac
   const int32_t cntL = __float_as_int(q.z), cntR = __float_as_int(q.w);
   const float limit = w.best_t + m.slack;
   const float ox = w.o.x * w.ix, oy = w.o.y * w.iy, oz = w.o.z * w.iz;
-  float x0 = fmaf(a.x, w.ix, -ox), x1 = fmaf(a.y, w.ix, -ox), y0 = fmaf(a.z, w.iy, -oy), y1 = fmaf(a.w, w.iy, -oy);
-  float z0 = fmaf(c.x, w.iz, -oz), z1 = fmaf(c.y, w.iz, -oz);
-  const float lmin = fmaxf(fmaxf(fminf(x0, x1), fminf(y0, y1)), fmaxf(fminf(z0, z1), m.t_lo));
-  const float lmax = fminf(fminf(fmaxf(x0, x1), fmaxf(y0, y1)), fminf(fmaxf(z0, z1), limit));
-  x0 = fmaf(b.x, w.ix, -ox); x1 = fmaf(b.y, w.ix, -ox); y0 = fmaf(b.z, w.iy, -oy); y1 = fmaf(b.w, w.iy, -oy);
-  z0 = fmaf(c.z, w.iz, -oz); z1 = fmaf(c.w, w.iz, -oz);
-  const float rmin = fmaxf(fmaxf(fminf(x0, x1), fminf(y0, y1)), fmaxf(fminf(z0, z1), m.t_lo));
-  const float rmax = fminf(fminf(fmaxf(x0, x1), fmaxf(y0, y1)), fminf(fmaxf(z0, z1), limit));
+  float lmin, lmax, rmin, rmax;
+  slab_window(fmaf(a.x, w.ix, -ox), fmaf(a.y, w.ix, -ox), fmaf(a.z, w.iy, -oy), fmaf(a.w, w.iy, -oy),
+              fmaf(c.x, w.iz, -oz), fmaf(c.y, w.iz, -oz), m.t_lo, limit, lmin, lmax);
+  slab_window(fmaf(b.x, w.ix, -ox), fmaf(b.y, w.ix, -ox), fmaf(b.z, w.iy, -oy), fmaf(b.w, w.iy, -oy),
+              fmaf(c.z, w.iz, -oz), fmaf(c.w, w.iz, -oz), m.t_lo, limit, rmin, rmax);
   bool hl = lmin <= lmax, hr = rmin <= rmax;
   st.box(2);
   if (hl && cntL > 0) { test_leaf<E>(m, w, refL, cntL, st); hl = false; }
@@ -476,10 +490,10 @@ __global__ void __launch_bounds__(kThreads, RG_REFILL_MIN_BLOCKS) trace_kernel_r
 
 // Lock-step variant for shallow BVHs. Each round the warp samples 32 rays in step and
 // gives every ray one node visit (the root); rays that are finished by then (typically
-// those leaving the scene) go straight to the tally, and the others are queued in a
-// per-warp shared-memory queue. Whenever 32 rays are queued the warp traces them from
-// the root to completion in step, so the long traversals run with full warps instead
-// of next to lanes that finished after one visit.
+// those leaving the scene) go straight to the tally, and the others are queued, with
+// their traversal state, in a per-warp shared-memory queue. Whenever 32 rays are queued
+// the warp continues them to completion in step, so the long traversals run with full
+// warps instead of next to lanes that finished after one visit.
 template <bool E, bool kBVH, class St>
 __global__ void __launch_bounds__(kThreads, RG_LOCKSTEP_MIN_BLOCKS) trace_kernel_lockstep(const TraceParams p) {
   extern __shared__ __align__(16) uint32_t hist[];
@@ -503,7 +517,7 @@ __global__ void __launch_bounds__(kThreads, RG_LOCKSTEP_MIN_BLOCKS) trace_kernel
       ++n_rays;
     }
   };
-  // Trace the queued rays q[0 .. count) (count <= 32) from the root to completion.
+  // Trace the queued rays q[0 .. count) (count <= 32) to completion.
   auto drain = [&](int count) {
     const bool has = lane < count;
     Walker w;
@@ -569,7 +583,6 @@ __global__ void __launch_bounds__(kThreads, RG_LOCKSTEP_MIN_BLOCKS) trace_kernel
       if (queued >= 32) {
         drain(32);
         __syncwarp();
-        // move the overflow (queued - 32 <= 31 rays) to the front
         const int rest = queued - 32;
         float ox = 0.f, oy = 0.f, oz = 0.f, dx = 0.f, dy = 0.f, dz = 0.f;
         int32_t sr = 0;
