@@ -19,6 +19,7 @@ RG_OK = 0
 STATUS = {0: "RG_OK", -1: "RG_ERR_ARG", -2: "RG_ERR_CUDA", -3: "RG_ERR_OOM", -4: "RG_ERR_NOT_CONVERGED",
           -5: "RG_ERR_STACK", -6: "RG_ERR_NUMERIC", -7: "RG_ERR_UNSUPPORTED"}
 PREC = {"bf16": 1, "fp16": 2}
+KAPPA = {"triangulation": 1, "fractional_variance": 2}
 
 
 class MeshInfo(ctypes.Structure):
@@ -42,6 +43,8 @@ SIGNATURES = {
     "rg_counts_to_F": (i32, [P, i32, P, P, P, P]),
     "rg_enforce_iterative": (i32, [P, i32, P, P, f64, i32, P, P]),
     "rg_enforce_iterative_noalloc": (i32, [i32, P, P, f64, i32, P, P]),
+    "rg_enforce_iterative_kappa": (i32, [P, i32, P, P, P, f64, i32, P, P]),
+    "rg_kappa": (i32, [P, i32, i32, P, P, P, f64, P, P]),
     "rg_enforce_lsq": (i32, [P, i32, P, P, i32, i32, i32, P, P]),
     "rg_aggregate": (i32, [P, i32, P, P, P, i32, P, P, P]),
     "rg_gebhart": (i32, [P, i32, P, i32, P, P, i32, f64, i32, P, P, P, P]),

@@ -176,6 +176,36 @@ def enforce_iterative(ctx: Context, F: torch.Tensor, omega: torch.Tensor, tol: f
     return it.value
 
 
+def kappa(ctx: Context, rays: torch.Tensor, omega: torch.Tensor, mode="fractional_variance", F=None,
+          param: float | None = None, K: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """Reciprocity weights kappa [N, N] (rg_kappa): "triangulation" (param = exponent,
+    default 0.4) or "fractional_variance" (needs the MCRT F; param = z, default 1.96)."""
+    n = omega.numel()
+    m = _native.KAPPA[mode] if isinstance(mode, str) else int(mode)
+    if param is None:
+        param = 0.4 if m == _native.KAPPA["triangulation"] else 1.96
+    if K is None:
+        K = torch.empty((n, n), dtype=torch.float64, device=omega.device)
+    Fp = ctypes.c_void_p(None) if F is None else _dptr(F, torch.float64, "F", n * (n + 1), ctx.device)
+    ctx.check(ctx.lib.rg_kappa(ctx.handle, n, m, Fp, _dptr(rays, torch.int64, "rays", n, ctx.device),
+                               _dptr(omega, torch.float64, "omega", n, ctx.device), float(param),
+                               _dptr(K, torch.float64, "kappa", n * n, ctx.device), _stream(stream)), "rg_kappa")
+    return K
+
+
+def enforce_iterative_kappa(ctx: Context, F: torch.Tensor, omega: torch.Tensor, K: torch.Tensor, tol: float = 1e-12,
+                            maxit: int = 10000, stream=None) -> int:
+    """In-place iterative enforcer with per-pair reciprocity weights (rg_enforce_iterative_kappa)."""
+    n = F.shape[0]
+    it = ctypes.c_int32(0)
+    ctx.check(ctx.lib.rg_enforce_iterative_kappa(ctx.handle, n, _dptr(omega, torch.float64, "omega", n, ctx.device),
+                                                 _dptr(K, torch.float64, "kappa", n * n, ctx.device),
+                                                 _dptr(F, torch.float64, "F", n * (n + 1), ctx.device), float(tol),
+                                                 int(maxit), ctypes.byref(it), _stream(stream)),
+              "rg_enforce_iterative_kappa")
+    return it.value
+
+
 def enforce_lsq(ctx: Context, F: torch.Tensor, omega: torch.Tensor, nnr: bool = True, spva: bool = True,
                 max_passes: int = 1000, stream=None) -> int:
     """In-place least-squares optimum with NNR / SPVA (rg_enforce_lsq); returns projections."""

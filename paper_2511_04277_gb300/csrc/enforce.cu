@@ -5,13 +5,16 @@
 // into H = Omega_i F_ij in place, and a row scale s (initially 1) is kept beside it, so
 // that the current iterate is eta_ij = s_i H_ij. One iteration is two kernels:
 //   sym_pass  one block per tile pair (I, J), I <= J, of 64 x 64 tiles: loads eta on
-//             both sides of the diagonal, writes H'_ij = H'_ji = (eta_ij + eta_ji)/2,
-//             records the largest |eta_ij - eta_ji|/2 and per-tile row sums;
+//             both sides of the diagonal, writes H'_ij = kappa_ij eta_ij + (1 - kappa_ij)
+//             eta_ji (kappa = 1/2, or per pair from a kappa matrix), records the largest
+//             |eta_ij - eta_ji|/2 and per-tile row sums;
 //   row_pass  carries the environment column (eta_i,inf = s_i H_i,inf), adds the row
 //             sums, records |r_i - Omega_i| and sets s_i = Omega_i / r_i (Eq. 3.39-3.40
 //             with w = eta); its last block applies the stopping rule.
-// Every entry is read and written once per iteration: 16 bytes of HBM traffic.
+// Every entry is read and written once per iteration: 16 bytes of HBM traffic (24 with
+// a kappa matrix).
 #include <cfloat>
+#include <cmath>
 #include <cstring>
 #include <mutex>
 
@@ -56,8 +59,11 @@ struct EnforceState {
   int32_t pad;
 };
 
+// kW: weights from kappa [n][n] (kappa_ij multiplies eta_ij); otherwise 1/2.
+template <bool kW>
 __global__ void __launch_bounds__(kThreads) sym_pass(double* __restrict__ H, const double* __restrict__ s,
-                                                     int32_t n, double* __restrict__ P, EnforceState* st) {
+                                                     const double* __restrict__ kappa, int32_t n,
+                                                     double* __restrict__ P, EnforceState* st) {
   if (st->done) return;
   const int I = blockIdx.y, J = blockIdx.x;
   if (I > J) return;
@@ -66,48 +72,56 @@ __global__ void __launch_bounds__(kThreads) sym_pass(double* __restrict__ H, con
   __shared__ double red[kThreads];
   const int64_t ld = n + 1;
   const int tid = threadIdx.x;
+  const bool off = I != J;
   for (int e = tid; e < kT * kT; e += kThreads) {
     int r = e / kT, c = e % kT;
     int64_t i = (int64_t)I * kT + r, j = (int64_t)J * kT + c;
     A[r][c] = (i < n && j < n) ? s[i] * H[i * ld + j] : 0.0;
-    if (I != J) {
+    if (off) {
       int64_t i2 = (int64_t)J * kT + r, j2 = (int64_t)I * kT + c;
       B[r][c] = (i2 < n && j2 < n) ? s[i2] * H[i2 * ld + j2] : 0.0;
     }
   }
   __syncthreads();
+  auto pair = [&](double a, double b, int64_t i, int64_t j) {
+    if constexpr (kW) {
+      const double k = kappa[i * n + j];
+      return k * a + (1.0 - k) * b;
+    } else {
+      return 0.5 * (a + b);
+    }
+  };
   double dmax = 0.0;
-  // tile (I, J): h(r, c) = (A[r][c] + other(c, r)) / 2
+  // tile (I, J): h(r, c) from A[r][c] and other(c, r); tile (J, I) likewise from B
   for (int e = tid; e < kT * kT; e += kThreads) {
-    int r = e / kT, c = e % kT;
-    int64_t i = (int64_t)I * kT + r, j = (int64_t)J * kT + c;
+    const int r = e / kT, c = e % kT;
+    const int64_t i = (int64_t)I * kT + r, j = (int64_t)J * kT + c;
     if (i < n && j < n) {
-      double a = A[r][c], b = (I != J) ? B[c][r] : A[c][r];
-      H[i * ld + j] = 0.5 * (a + b);
+      const double a = A[r][c], b = off ? B[c][r] : A[c][r];
+      H[i * ld + j] = pair(a, b, i, j);
       dmax = fmax(dmax, 0.5 * fabs(a - b));
     }
-    if (I != J) {
-      int64_t i2 = (int64_t)J * kT + r, j2 = (int64_t)I * kT + c;
-      if (i2 < n && j2 < n) H[i2 * ld + j2] = 0.5 * (B[r][c] + A[c][r]);
+    if (off) {
+      const int64_t i2 = (int64_t)J * kT + r, j2 = (int64_t)I * kT + c;
+      if (i2 < n && j2 < n) H[i2 * ld + j2] = pair(B[r][c], A[c][r], i2, j2);
     }
   }
-  // row sums: 4 threads per row, 16 columns each, fixed order
+  // row sums of the written values: 4 threads per row, 16 columns each, fixed order
   const int row = tid >> 2, part = tid & 3;
   double acc = 0.0, acc2 = 0.0;
+  const int64_t ri = (int64_t)I * kT + row, rj = (int64_t)J * kT + row;
   for (int c = part * 16; c < part * 16 + 16; ++c) {
-    double b = (I != J) ? B[c][row] : A[c][row];
-    acc += 0.5 * (A[row][c] + b);
-    if (I != J) acc2 += 0.5 * (B[row][c] + A[c][row]);
+    const int64_t ci = (int64_t)I * kT + c, cj = (int64_t)J * kT + c;
+    if (ri < n && cj < n) acc += pair(A[row][c], off ? B[c][row] : A[c][row], ri, cj);
+    if (off && rj < n && ci < n) acc2 += pair(B[row][c], A[c][row], rj, ci);
   }
   acc += __shfl_xor_sync(0xffffffffu, acc, 1);
   acc += __shfl_xor_sync(0xffffffffu, acc, 2);
   acc2 += __shfl_xor_sync(0xffffffffu, acc2, 1);
   acc2 += __shfl_xor_sync(0xffffffffu, acc2, 2);
   if (part == 0) {
-    int64_t i = (int64_t)I * kT + row;
-    if (i < n) P[(int64_t)J * n + i] = acc;
-    int64_t j = (int64_t)J * kT + row;
-    if (I != J && j < n) P[(int64_t)I * n + j] = acc2;
+    if (ri < n) P[(int64_t)J * n + ri] = acc;
+    if (off && rj < n) P[(int64_t)I * n + rj] = acc2;
   }
   red[tid] = dmax;
   __syncthreads();
@@ -116,6 +130,49 @@ __global__ void __launch_bounds__(kThreads) sym_pass(double* __restrict__ H, con
     __syncthreads();
   }
   if (tid == 0) atomicMax(&st->d_recip, (unsigned long long)__double_as_longlong(red[0]));
+}
+
+// kappa_ij (rg_kappa): matrix triangulation (Eq. 3.21-3.22) or fractional variance
+// (Eq. 3.23-3.25). *bad is raised for a non-positive ray count or Omega.
+__global__ void kappa_kernel(int32_t mode, const double* __restrict__ F, const long long* __restrict__ rays,
+                             const double* __restrict__ omega, double param, int32_t n, double* __restrict__ K,
+                             int* bad) {
+  const int64_t total = (int64_t)n * n;
+  const int64_t ld = n + 1;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / n, j = e % n;
+    const double Ni = (double)rays[i], Nj = (double)rays[j], oi = omega[i], oj = omega[j];
+    if (!(Ni > 0.0 && Nj > 0.0 && oi > 0.0 && oj > 0.0)) {
+      atomicExch(bad, 1);
+      K[e] = 0.5;
+      continue;
+    }
+    double k = 0.5;
+    if (i != j) {
+      if (mode == RG_KAPPA_TRIANGULATION) {
+        const double ri = oi / Ni, rj = oj / Nj;
+        const double Y = (rj - ri) / (rj + ri);
+        const double sg = Y > 0.0 ? 1.0 : (Y < 0.0 ? -1.0 : 0.0);
+        k = 0.5 * (1.0 + sg * pow(fabs(Y), param));
+      } else {
+        const double fij = F[i * ld + j], fji = F[j * ld + i];
+        const double zz = param * param;
+        const bool zi = !(fij > 0.0), zj = !(fji > 0.0);
+        if (zi && zj) {
+          k = 0.5;
+        } else if (zi) {
+          k = 0.0;
+        } else if (zj) {
+          k = 1.0;
+        } else {
+          const double vij = zz * oi * oi * (1.0 - fij) / (Ni * fij);
+          const double vji = zz * oj * oj * (1.0 - fji) / (Nj * fji);
+          k = vji / (vij + vji);
+        }
+      }
+    }
+    K[e] = k;
+  }
 }
 
 __global__ void __launch_bounds__(kThreads) row_pass(double* __restrict__ H, double* __restrict__ s,
@@ -244,8 +301,12 @@ rg_status rg_counts_to_F(rg_ctx* ctx, int32_t n, const int64_t* counts_d, const 
   return RG_OK;
 }
 
-rg_status rg_enforce_iterative(rg_ctx* ctx, int32_t n, const double* omega_d, double* F_d, double tol, int32_t maxit,
-                               int32_t* iters_out_h, void* stream) {
+}  // extern "C"
+
+namespace {
+
+rg_status enforce_iterative(rg_ctx* ctx, int32_t n, const double* omega_d, const double* kappa_d, double* F_d,
+                            double tol, int32_t maxit, int32_t* iters_out_h, void* stream) {
   if (!ctx) return RG_ERR_ARG;
   RG_ARG_CHECK(ctx, n > 0 && omega_d && F_d && maxit > 0 && tol >= 0.0, "rg_enforce_iterative: bad argument");
   RG_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
@@ -281,7 +342,10 @@ rg_status rg_enforce_iterative(rg_ctx* ctx, int32_t n, const double* omega_d, do
   for (int launched = 0; launched < maxit;) {
     int batch = std::min(8, maxit - launched);
     for (int b = 0; b < batch; ++b) {
-      sym_pass<<<sym_grid, kThreads, 0, s>>>(F_d, sc, n, P, st);
+      if (kappa_d)
+        sym_pass<true><<<sym_grid, kThreads, 0, s>>>(F_d, sc, kappa_d, n, P, st);
+      else
+        sym_pass<false><<<sym_grid, kThreads, 0, s>>>(F_d, sc, nullptr, n, P, st);
       ++ctx->launches;
       row_pass<<<row_blocks, kThreads, 0, s>>>(F_d, sc, omega_d, P, n, n_tiles, st, tol_abs, maxit);
       ++ctx->launches;
@@ -298,6 +362,42 @@ rg_status rg_enforce_iterative(rg_ctx* ctx, int32_t n, const double* omega_d, do
   if (iters_out_h) *iters_out_h = h.iters;
   if (h.done == 3) return rg::fail(ctx, RG_ERR_NUMERIC, "rg_enforce_iterative: non-finite row sum");
   if (h.done != 1) return rg::fail(ctx, RG_ERR_NOT_CONVERGED, "rg_enforce_iterative: no convergence in %d iterations", maxit);
+  return RG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+rg_status rg_enforce_iterative(rg_ctx* ctx, int32_t n, const double* omega_d, double* F_d, double tol, int32_t maxit,
+                               int32_t* iters_out_h, void* stream) {
+  return enforce_iterative(ctx, n, omega_d, nullptr, F_d, tol, maxit, iters_out_h, stream);
+}
+
+rg_status rg_enforce_iterative_kappa(rg_ctx* ctx, int32_t n, const double* omega_d, const double* kappa_d,
+                                     double* F_d, double tol, int32_t maxit, int32_t* iters_out_h, void* stream) {
+  if (!ctx) return RG_ERR_ARG;
+  RG_ARG_CHECK(ctx, kappa_d != nullptr, "rg_enforce_iterative_kappa: NULL kappa");
+  return enforce_iterative(ctx, n, omega_d, kappa_d, F_d, tol, maxit, iters_out_h, stream);
+}
+
+rg_status rg_kappa(rg_ctx* ctx, int32_t n, int32_t mode, const double* F_d, const int64_t* rays_d,
+                   const double* omega_d, double param, double* kappa_d, void* stream) {
+  if (!ctx) return RG_ERR_ARG;
+  RG_ARG_CHECK(ctx, n > 0 && rays_d && omega_d && kappa_d, "rg_kappa: bad argument");
+  RG_ARG_CHECK(ctx, mode == RG_KAPPA_TRIANGULATION || (mode == RG_KAPPA_FRACTIONAL_VARIANCE && F_d),
+               "rg_kappa: unknown mode %d (or NULL F for fractional variance)", mode);
+  RG_ARG_CHECK(ctx, std::isfinite(param) && param > 0.0, "rg_kappa: parameter %.3e must be positive", param);
+  RG_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+  cudaStream_t s = (cudaStream_t)stream;
+  RG_CUDA_TRY(ctx, cudaMemsetAsync(ctx->d_scratch, 0, sizeof(int32_t), s));
+  kappa_kernel<<<blocks_for((int64_t)n * n, ctx->sm_count), kThreads, 0, s>>>(
+      mode, F_d, reinterpret_cast<const long long*>(rays_d), omega_d, param, n, kappa_d, ctx->d_scratch);
+  ++ctx->launches;
+  RG_CUDA_TRY(ctx, cudaGetLastError());
+  RG_CUDA_TRY(ctx, cudaMemcpyAsync(ctx->h_scratch, ctx->d_scratch, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  RG_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+  if (ctx->h_scratch[0]) return rg::fail(ctx, RG_ERR_ARG, "rg_kappa: a ray count or Omega is not positive");
   return RG_OK;
 }
 
@@ -406,7 +506,7 @@ extern "C" rg_status rg_enforce_iterative_noalloc(int32_t n, const double* omega
   for (int launched = 0; launched < maxit;) {
     int batch = std::min(8, maxit - launched);
     for (int k = 0; k < batch; ++k) {
-      sym_pass<<<sym_grid, kThreads, 0, s>>>(F_d, sc, n, P, st);
+      sym_pass<false><<<sym_grid, kThreads, 0, s>>>(F_d, sc, nullptr, n, P, st);
       row_pass<<<row_blocks, kThreads, 0, s>>>(F_d, sc, omega_d, P, n, n_tiles, st, tol_abs, maxit);
     }
     launched += batch;

@@ -116,3 +116,83 @@ def test_aggregate_rejects_bad_group(rg_ctx):
     grp = np.array([0, 1, 2, 3, 0, 1, 2, 9], np.int32)
     with pytest.raises(api.RadgebError):
         api.aggregate(rg_ctx, _dev(F), _dev(np.ones(8)), _dev(grp, torch.int32), 4)
+
+
+# ------------------------------------------------------------------ weighted reciprocity
+def _plates_mcrt(rg_ctx, per_face=20000, seed=0):
+    m = synth.plates(16)
+    rays = np.full(m.n_faces, per_face, np.int64)
+    rays[::7] = per_face // 4           # unequal ray budgets, so kappa is not 1/2
+    mesh = api.Mesh.from_synth(rg_ctx, m)
+    F = api.counts_to_F(rg_ctx, api.trace(rg_ctx, mesh, rays, seed), _dev(rays, torch.int64))
+    return F, rays, mesh.face_areas()
+
+
+@pytest.mark.parametrize("mode", ["triangulation", "fractional_variance"])
+def test_kappa_matches_oracle(rg_ctx, mode):
+    F, rays, A = _plates_mcrt(rg_ctx)
+    K = api.kappa(rg_ctx, _dev(rays, torch.int64), _dev(A), mode, F=F).cpu().numpy()
+    F0 = F.cpu().numpy()
+    if mode == "triangulation":
+        Ko = E.kappa_triangulation(rays, A, n=0.4)
+    else:
+        Ko = E.kappa_fractional_variance(F0, rays, A, z=1.96)
+    assert np.abs(K - Ko).max() <= 1e-14
+    assert np.abs(K - 0.5).max() > 0.1
+
+
+@pytest.mark.parametrize("mode", ["triangulation", "fractional_variance"])
+def test_iterative_kappa_vs_oracle(rg_ctx, mode):
+    F, rays, A = _plates_mcrt(rg_ctx)
+    F0 = F.cpu().numpy()
+    K = api.kappa(rg_ctx, _dev(rays, torch.int64), _dev(A), mode, F=F)
+    it = api.enforce_iterative_kappa(rg_ctx, F, _dev(A), K, tol=TOL)
+    Fo, it_o, ok = E.iterative(F0, A, tol=TOL, kappa=K.cpu().numpy())
+    assert ok and abs(it - it_o) <= 1
+    got = F.cpu().numpy()
+    assert np.all(np.abs(got - Fo).max(axis=1) <= 1e-10 * np.abs(Fo).max(axis=1))
+    assert np.abs(got.sum(axis=1) - 1).max() < 1e-13
+    eta = A[:, None] * got[:, :512]
+    assert np.abs(eta - eta.T).max() < 1e-11
+
+
+def test_iterative_kappa_one_half_is_the_default(rg_ctx):
+    rng = np.random.default_rng(21)
+    N = 200
+    F = _random_F(N, rng)
+    A = _dev(rng.uniform(0.5, 2.0, N))
+    Fa, Fb = _dev(F), _dev(F)
+    ia = api.enforce_iterative(rg_ctx, Fa, A, tol=TOL)
+    ib = api.enforce_iterative_kappa(rg_ctx, Fb, A, torch.full((N, N), 0.5, dtype=torch.float64, device="cuda"),
+                                     tol=TOL)
+    assert ia == ib and torch.equal(Fa, Fb)
+
+
+def test_kappa_rejects_bad_input(rg_ctx):
+    rays = torch.tensor([10, 0, 5], dtype=torch.int64, device="cuda")
+    with pytest.raises(api.RadgebError) as e:
+        api.kappa(rg_ctx, rays, torch.ones(3, dtype=torch.float64, device="cuda"), "triangulation")
+    assert e.value.code == "RG_ERR_ARG"
+    with pytest.raises(api.RadgebError):
+        api.kappa(rg_ctx, rays.abs() + 1, torch.ones(3, dtype=torch.float64, device="cuda"), "fractional_variance")
+
+
+def test_ref_enforcement_with_eps_area(rg_ctx):
+    """REFs from an un-enforced F break Eq. 4.4; the iterative enforcer with Omega = eps A
+    (Sec. 4.2.3) restores closure and eps_i A_i B_ij = eps_j A_j B_ji."""
+    F, rays, A = _plates_mcrt(rg_ctx, per_face=5000)
+    w = synth.workload("plates")
+    eps = w["eps"][0]
+    B, _, _ = api.gebhart(rg_ctx, F, _dev(eps), _dev(1 - eps), tol=1e-12)
+    B0 = B[0].cpu().numpy()
+    om = eps * A
+    R0 = om[:, None] * B0[:, :512]
+    assert np.abs(R0 - R0.T).max() > 1e-4 * np.abs(R0).max()       # not reciprocal before
+    Bd = B[0].contiguous()
+    api.enforce_iterative(rg_ctx, Bd, _dev(om), tol=TOL)
+    Bo, _, ok = E.iterative(B0, om, tol=TOL)
+    got = Bd.cpu().numpy()
+    assert ok and np.all(np.abs(got - Bo).max(axis=1) <= 1e-10 * np.abs(Bo).max(axis=1))
+    assert np.abs(got.sum(axis=1) - 1).max() < 1e-13
+    R = om[:, None] * got[:, :512]
+    assert np.abs(R - R.T).max() < 1e-11 * np.abs(R).max()

@@ -165,3 +165,73 @@ def test_kappa_variants():
     v01 = 1.0 ** 2 * (1 - 0.3) / (1000 * 0.3)
     v10 = 1.5 ** 2 * (1 - 0.2) / (4000 * 0.2)
     assert abs(kf[0, 1] - v10 / (v01 + v10)) < 1e-12
+
+
+def test_kappa_triangulation_pins():
+    rng = np.random.default_rng(11)
+    N = 12
+    rays = rng.integers(100, 10000, N).astype(np.float64)
+    om = rng.uniform(0.2, 3.0, N)
+    k = E.kappa_triangulation(rays, om)
+    # Y_ji = -Y_ij (Eq. 3.22), so the two weights of a pair add up to one
+    assert np.abs(k + k.T - 1.0).max() < 1e-15
+    assert np.all(np.diag(k) == 0.5)
+    # with the exponent n = 1, Eq. 3.21 collapses to r_j / (r_i + r_j), r = Omega / N
+    r = om / rays
+    k1 = E.kappa_triangulation(rays, om, n=1.0)
+    assert np.abs(k1 - r[None, :] / (r[:, None] + r[None, :])).max() < 1e-14
+    # n -> 0 keeps only the sign of Y: all weight on eta_ij where Omega_j/N_j > Omega_i/N_i
+    k0 = E.kappa_triangulation(rays, om, n=1e-12)
+    target = np.where(r[None, :] > r[:, None], 1.0, np.where(r[None, :] < r[:, None], 0.0, 0.5))
+    assert np.abs(k0 - target).max() < 1e-9
+
+
+def test_kappa_fractional_variance_pins():
+    rng = np.random.default_rng(12)
+    N = 10
+    rays = rng.integers(1000, 100000, N).astype(np.float64)
+    om = rng.uniform(0.5, 2.0, N)
+    F = _random_F(N, rng, zeros=0.0)
+    k = E.kappa_fractional_variance(F, rays, om)
+    # Eq. 3.23 in its exchange-coefficient form: sigma_ij = z Omega_i sqrt((Omega_i - eta_ij) / (N_i eta_ij))
+    eta = om[:, None] * F[:, :N]
+    with np.errstate(divide="ignore", invalid="ignore"):
+        sig2 = (1.96 * om[:, None]) ** 2 * (om[:, None] - eta) / (rays[:, None] * eta)
+    off = ~np.eye(N, dtype=bool)
+
+    def var(kk):  # Eq. 3.24
+        return kk ** 2 * sig2 + (1 - kk) ** 2 * sig2.T
+
+    # Eq. 3.25 minimises Eq. 3.24: moving kappa either way raises the estimator variance
+    for d in (1e-3, -1e-3):
+        assert np.all(var(k + d)[off] > var(k)[off])
+    assert np.abs(k + k.T - 1.0)[off].max() < 1e-15
+    # z cancels
+    assert np.abs(E.kappa_fractional_variance(F, rays, om, z=3.0) - k).max() < 1e-15
+    # a zero estimate has infinite variance: the other side is taken; both zero -> 1/2
+    F0 = F.copy()
+    F0[0, 1] = 0.0
+    F0[2, 3] = F0[3, 2] = 0.0
+    k0 = E.kappa_fractional_variance(F0, rays, om)
+    assert k0[0, 1] == 0.0 and k0[1, 0] == 1.0
+    assert k0[2, 3] == 0.5 and k0[3, 2] == 0.5
+
+
+def test_iterative_with_kappa_weights():
+    rng = np.random.default_rng(13)
+    N = 25
+    F = _random_F(N, rng)
+    A = rng.uniform(0.5, 2.0, N)
+    rays = rng.integers(1000, 50000, N)
+    # constant 1/2 weights are the default enforcer
+    Fh, it, _ = E.iterative(F, A, tol=1e-13)
+    Fk, itk, _ = E.iterative(F, A, tol=1e-13, kappa=np.full((N, N), 0.5))
+    assert it == itk and np.array_equal(Fh, Fk)
+    # variance weights: closure and reciprocity still hold at the fixed point
+    K = E.kappa_fractional_variance(F, rays, A)
+    Fv, itv, ok = E.iterative(F, A, tol=1e-13, kappa=K)
+    assert ok
+    assert np.abs(Fv.sum(axis=1) - 1).max() < 1e-13
+    eta = A[:, None] * Fv[:, :N]
+    assert np.abs(eta - eta.T).max() < 1e-12 * A.max()
+    assert np.abs(Fv - Fh).max() > 1e-6          # the weights change the result
