@@ -36,6 +36,22 @@
  * Face frame: from the face's lowest-index triangle (v0,v1,v2):
  *   n = c/|c| with c = cross(v1-v0, v2-v0); t = e1/|e1|; b = cross(n, t).
  *
+ * Diffuse reflections (Sec. 4.2.2, REFs directly from MCRT): a random walk whose
+ * expectation is B_ij of Eq. 4.5, the fraction of the energy emitted by i that is
+ * absorbed by j. A ray emitted from face i as above is followed through bounces
+ * b = 1, 2, ...: at its closest hit on face j, word 3 of the draw of counter
+ * (ray lo, ray hi, i, b*128) decides
+ *   x < floor(eps_j 2^32)            absorbed: counted for column j, path ends;
+ *   x < floor((eps_j + rho_j) 2^32)  reflected diffusely;
+ *   otherwise                        lost (neither absorbed nor reflected), path ends;
+ * a miss is counted for the environment column. A reflection re-emits from face j
+ * exactly as an emission of face j would, with the counter words of bounce b: the
+ * same draw's words 0-2 choose the triangle and the point, counters
+ * (ray lo, ray hi, i, b*128 + a), a = 1..64, Malley's direction. Re-emitting from a
+ * uniform point of the face is the face-level model of Eq. 4.5 (each face reflects
+ * with one uniform radiosity), so the walk estimates the same B as Gebhart's method
+ * for the same faces. A path still reflecting after max_bounces counts as overflow.
+ *
  * Build: gcc -O2 -ffp-contract=off -fopenmp -fPIC -shared (no fast-math), so
  * every float operation is one IEEE-rounded operation.
  */
@@ -217,10 +233,36 @@ static int omesh_init(omesh* m, const float* verts, int64_t nv, const int32_t* t
 /* ------------------------------------------------------------------------ */
 /* Ray generation for ray `ray` of face `f`.                                  */
 /* ------------------------------------------------------------------------ */
-static void sample_ray(const omesh* m, uint64_t seed, int32_t f, uint64_t ray, v3* o, v3* d,
-                       int32_t* src_tri, int32_t* attempts_used) {
+/* Malley's cosine-weighted (x, y, z) from the draws of attempts a = 1..64 of counter
+   word 3 = base + a; (0, 0, 1) when no candidate falls inside the unit disc. */
+static void malley(uint64_t seed, uint64_t ray, uint32_t f, uint32_t base, float* px, float* py, float* pz,
+                   int32_t* used_out) {
+  float dx = 0.0f, dy = 0.0f, s2 = 0.0f;
+  int used = 0;
+  for (uint32_t a = 1; a <= 64; ++a) {
+    uint32_t y[4];
+    draw(seed, ray, f, base + a, y);
+    float cx = (float)(y[0] >> 8) * 1.1920928955078125e-07f - 1.0f;
+    float cy = (float)(y[1] >> 8) * 1.1920928955078125e-07f - 1.0f;
+    float cs = cx * cx + cy * cy;
+    if (cs < 1.0f) { dx = cx; dy = cy; s2 = cs; used = (int)a; break; }
+    cx = (float)(y[2] >> 8) * 1.1920928955078125e-07f - 1.0f;
+    cy = (float)(y[3] >> 8) * 1.1920928955078125e-07f - 1.0f;
+    cs = cx * cx + cy * cy;
+    if (cs < 1.0f) { dx = cx; dy = cy; s2 = cs; used = (int)a; break; }
+  }
+  *px = dx; *py = dy; *pz = sqrtf(1.0f - s2);
+  if (used_out) *used_out = used;
+}
+
+/* Emission from face f with the draws of counters (ray, stream, base + a): a = 0 for the
+   triangle and the point, a = 1..64 for the direction. Emission proper uses stream = f
+   and base = 0; a reflection of bounce b uses stream = the path's source face and
+   base = b*128. */
+static void emit_from(const omesh* m, uint64_t seed, int32_t f, uint32_t stream, uint32_t base, uint64_t ray,
+                      v3* o, v3* d, int32_t* src_tri, int32_t* attempts_used) {
   uint32_t x[4];
-  draw(seed, ray, (uint32_t)f, 0u, x);
+  draw(seed, ray, stream, base, x);
   int64_t s = m->face_start[f], e = m->face_start[f + 1];
   int64_t q = e - 1;
   for (int64_t k = s; k < e; ++k) {
@@ -241,21 +283,9 @@ static void sample_ray(const omesh* m, uint64_t seed, int32_t f, uint64_t ray, v
   p.y = p.y + m->lift * nf.y;
   p.z = p.z + m->lift * nf.z;
 
-  float dx = 0.0f, dy = 0.0f, s2 = 0.0f;
+  float dx, dy, dz;
   int used = 0;
-  for (uint32_t a = 1; a <= 64; ++a) {
-    uint32_t y[4];
-    draw(seed, ray, (uint32_t)f, a, y);
-    float cx = (float)(y[0] >> 8) * 1.1920928955078125e-07f - 1.0f;
-    float cy = (float)(y[1] >> 8) * 1.1920928955078125e-07f - 1.0f;
-    float cs = cx * cx + cy * cy;
-    if (cs < 1.0f) { dx = cx; dy = cy; s2 = cs; used = (int)a; break; }
-    cx = (float)(y[2] >> 8) * 1.1920928955078125e-07f - 1.0f;
-    cy = (float)(y[3] >> 8) * 1.1920928955078125e-07f - 1.0f;
-    cs = cx * cx + cy * cy;
-    if (cs < 1.0f) { dx = cx; dy = cy; s2 = cs; used = (int)a; break; }
-  }
-  float dz = sqrtf(1.0f - s2);
+  malley(seed, ray, stream, base, &dx, &dy, &dz, &used);
   v3 t = m->ft[f], b = m->fb[f], n = m->fn[f];
   v3 dir;
   dir.x = dx * t.x + dy * b.x; dir.x = dir.x + dz * n.x;
@@ -263,6 +293,11 @@ static void sample_ray(const omesh* m, uint64_t seed, int32_t f, uint64_t ray, v
   dir.z = dx * t.z + dy * b.z; dir.z = dir.z + dz * n.z;
   *o = p; *d = dir; *src_tri = tri;
   if (attempts_used) *attempts_used = used;
+}
+
+static void sample_ray(const omesh* m, uint64_t seed, int32_t f, uint64_t ray, v3* o, v3* d,
+                       int32_t* src_tri, int32_t* attempts_used) {
+  emit_from(m, seed, f, (uint32_t)f, 0u, ray, o, d, src_tri, attempts_used);
 }
 
 /* Moller-Trumbore; returns 1 and t if the ray hits triangle k. */
@@ -513,6 +548,75 @@ int oracle_trace_counts(const float* verts, int64_t nv, const int32_t* tris, int
     }
   }
   free(b.nodes); free(b.order);
+  omesh_free(&m);
+  return ORC_OK;
+}
+
+/*
+ * Direct Monte Carlo of Gebhart factors with diffuse reflections (see the header):
+ * counts[i][j] += rays of face i absorbed on face j (column n_faces: escaped), with
+ * per-face absorptivity eps[j] and diffuse reflectivity rho[j] (eps + rho <= 1).
+ * stats (may be NULL) += {rays, bounces (hits), lost, overflow}.
+ */
+int oracle_trace_reflect(const float* verts, int64_t nv, const int32_t* tris, int64_t nt,
+                         const int32_t* tri_face, int32_t n_faces, const int64_t* rays_per_face,
+                         const double* eps, const double* rho, int32_t max_bounces, uint64_t seed,
+                         uint64_t ray_offset, int use_bvh, int n_threads, const int32_t* face_subset,
+                         int32_t n_subset, int64_t* counts, int64_t* stats) {
+  if (!eps || !rho || max_bounces < 1 || max_bounces >= (1 << 25)) return ORC_ERR_ARG;
+  omesh m;
+  int st = omesh_init(&m, verts, nv, tris, nt, tri_face, n_faces);
+  if (st) return st;
+  uint64_t* thr_a = malloc(sizeof(uint64_t) * n_faces);
+  uint64_t* thr_r = malloc(sizeof(uint64_t) * n_faces);
+  if (!thr_a || !thr_r) { free(thr_a); free(thr_r); omesh_free(&m); return ORC_ERR_OOM; }
+  for (int32_t f = 0; f < n_faces; ++f) {
+    double a = eps[f], r = rho[f];
+    if (rays_per_face[f] < 0 || !(a >= 0.0 && r >= 0.0 && a + r <= 1.0)) {
+      free(thr_a); free(thr_r); omesh_free(&m); return ORC_ERR_ARG;
+    }
+    thr_a[f] = (uint64_t)floor(a * 4294967296.0);
+    thr_r[f] = (uint64_t)floor((a + r) * 4294967296.0);
+  }
+  obvh b; memset(&b, 0, sizeof(b));
+  if (use_bvh) {
+    st = bvh_build(&b, &m);
+    if (st) { free(thr_a); free(thr_r); omesh_free(&m); return st; }
+  }
+  int32_t n_rows = face_subset ? n_subset : n_faces;
+  int64_t n_rays = 0, n_hits = 0, n_lost = 0, n_over = 0;
+#ifdef _OPENMP
+  if (n_threads > 0) omp_set_num_threads(n_threads);
+#pragma omp parallel for schedule(dynamic, 1) reduction(+ : n_rays, n_hits, n_lost, n_over)
+#endif
+  for (int32_t q = 0; q < n_rows; ++q) {
+    int32_t f = face_subset ? face_subset[q] : q;
+    int64_t* row = &counts[(int64_t)f * (n_faces + 1)];
+    for (int64_t r = 0; r < rays_per_face[f]; ++r) {
+      uint64_t ray = ray_offset + (uint64_t)r;
+      v3 o, d; int32_t src;
+      sample_ray(&m, seed, f, ray, &o, &d, &src, NULL);
+      ++n_rays;
+      for (int32_t bounce = 1;; ++bounce) {
+        float bt = INFINITY; int32_t bk = -1;
+        if (use_bvh) closest_bvh(&m, &b, src, o, d, &bt, &bk);
+        else for (int64_t k = 0; k < nt; ++k) consider(&m, (int32_t)k, src, o, d, &bt, &bk);
+        if (bk < 0) { row[n_faces] += 1; break; }
+        ++n_hits;
+        int32_t j = m.tri_face[bk];
+        uint32_t x[4];
+        const uint32_t base = (uint32_t)bounce << 7;
+        draw(seed, ray, (uint32_t)f, base, x);
+        if ((uint64_t)x[3] < thr_a[j]) { row[j] += 1; break; }
+        if ((uint64_t)x[3] >= thr_r[j]) { ++n_lost; break; }
+        if (bounce >= max_bounces) { ++n_over; break; }
+        /* diffuse reflection: re-emission from face j */
+        emit_from(&m, seed, j, (uint32_t)f, base, ray, &o, &d, &src, NULL);
+      }
+    }
+  }
+  if (stats) { stats[0] += n_rays; stats[1] += n_hits; stats[2] += n_lost; stats[3] += n_over; }
+  free(b.nodes); free(b.order); free(thr_a); free(thr_r);
   omesh_free(&m);
   return ORC_OK;
 }

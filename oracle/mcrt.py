@@ -42,6 +42,8 @@ def _load():
         lib.oracle_closest_hits.argtypes = [P, i64, P, i64, P, i32, P, P, P, i64, P, P]
         lib.oracle_trace_counts.argtypes = [P, i64, P, i64, P, i32, P, u64, u64, ctypes.c_int,
                                             ctypes.c_int, P, i32, P]
+        lib.oracle_trace_reflect.argtypes = [P, i64, P, i64, P, i32, P, P, P, i32, u64, u64, ctypes.c_int,
+                                             ctypes.c_int, P, i32, P, P]
         lib.oracle_max_threads.argtypes = []
         for fn in ("oracle_face_geometry", "oracle_sample_rays", "oracle_closest_hits",
                    "oracle_trace_counts", "oracle_max_threads"):
@@ -139,6 +141,29 @@ def trace_counts(verts, tris, tri_face, n_faces, rays_per_face, seed, ray_offset
                                    seed, ray_offset, int(bool(use_bvh)), int(threads), _ptr(sub),
                                    0 if sub is None else len(sub), _ptr(counts)), "trace_counts")
     return counts
+
+
+def trace_reflect(verts, tris, tri_face, n_faces, rays_per_face, eps, rho, seed, ray_offset=0, max_bounces=4096,
+                  use_bvh=True, threads=0, faces=None):
+    """Direct Monte Carlo of Gebhart factors with diffuse reflections (Eq. 4.5 as a random
+    walk): counts int64[N, N+1] of rays of face i absorbed on face j (column N: escaped)
+    and stats {rays, hits, lost, overflow}. B_ij is estimated by counts_ij / N_i."""
+    lib = _load()
+    v, t, f = _mesh_arrays(verts, tris, tri_face)
+    rays = np.ascontiguousarray(rays_per_face, dtype=np.int64)
+    e = np.ascontiguousarray(eps, dtype=np.float64)
+    r = np.ascontiguousarray(rho, dtype=np.float64)
+    if rays.shape != (n_faces,) or e.shape != (n_faces,) or r.shape != (n_faces,):
+        raise ValueError("rays_per_face, eps and rho must have one entry per face")
+    counts = np.zeros((n_faces, n_faces + 1), dtype=np.int64)
+    stats = np.zeros(4, dtype=np.int64)
+    sub = None if faces is None else np.ascontiguousarray(faces, dtype=np.int32)
+    _check(lib.oracle_trace_reflect(_ptr(v), len(v), _ptr(t), len(t), _ptr(f), n_faces, _ptr(rays), _ptr(e),
+                                    _ptr(r), int(max_bounces), seed, ray_offset, int(bool(use_bvh)), int(threads),
+                                    _ptr(sub), 0 if sub is None else len(sub), _ptr(counts), _ptr(stats)),
+           "trace_reflect")
+    return counts, {"rays": int(stats[0]), "hits": int(stats[1]), "lost": int(stats[2]),
+                    "overflow": int(stats[3])}
 
 
 def max_threads() -> int:

@@ -6,8 +6,8 @@ Both the CPU oracle's callers and the CUDA library's callers take their inputs
 from here.
 """
 from .meshes import (Mesh, cube, plates, discs, perpendicular_squares, small_sat,
-                     spacecraft, patch_mesh)
+                     spacecraft, patch_mesh, two_sided_plates)
 from .params import (optical_sets, heat_loads, rays_by_area, uniform_rays, workload)
 
 __all__ = ["Mesh", "cube", "plates", "discs", "perpendicular_squares", "small_sat", "spacecraft",
-           "patch_mesh", "optical_sets", "heat_loads", "rays_by_area", "uniform_rays", "workload"]
+           "patch_mesh", "two_sided_plates", "optical_sets", "heat_loads", "rays_by_area", "uniform_rays", "workload"]

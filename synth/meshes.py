@@ -168,6 +168,23 @@ def discs(r1: float = 1.0, r2: float = 2.0, h: float = 1.0, segments: int = 256,
                 patch_of_face=np.arange(4, dtype=np.int32), n_patches=4)
 
 
+def two_sided_plates(size: float = 1.0, gap: float = 1.0, back_gap: float = 1e-4):
+    """Two coaxial size x size plates ``gap`` apart, each with its outer side as a face.
+
+    Faces (the numbering of the thesis's parallel-plates model, 0-based): 0 = outer side
+    of the bottom plate (z = -back_gap, normal -z), 1 = inner side of the bottom plate
+    (z = 0, normal +z), 2 = inner side of the top plate (z = gap, normal -z), 3 = outer
+    side of the top plate (z = gap + back_gap, normal +z). Two triangles each; open system.
+    """
+    patches = [
+        ((0, 0, -back_gap), (0, size, 0), (size, 0, 0), 1, 1),
+        ((0, 0, 0), (size, 0, 0), (0, size, 0), 1, 1),
+        ((0, 0, gap), (0, size, 0), (size, 0, 0), 1, 1),
+        ((0, 0, gap + back_gap), (size, 0, 0), (0, size, 0), 1, 1),
+    ]
+    return patch_mesh("two_sided_plates", patches, [1] * 4)
+
+
 def _grouped(name, patches, n_faces):
     quads = [nu * nv for (_, _, _, nu, nv) in patches]
     return patch_mesh(name, patches, _split_counts(n_faces, quads))

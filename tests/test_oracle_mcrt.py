@@ -10,6 +10,7 @@ import pytest
 import synth
 from oracle import mcrt
 from tests import closed_forms as cf
+from tests.conftest import load_matrix
 
 
 # Known-answer vectors published with Random123 (Salmon et al. 2011) for Philox4x32-10.
@@ -197,3 +198,64 @@ def test_discs_against_eq_6_1():
     sigma = math.sqrt(ref * (1 - ref) / per)
     assert abs(F[0, 1] - ref) <= 5 * sigma + poly
     assert F[2, 4] == 1.0 and F[3, 4] == 1.0        # back faces see only the environment
+
+
+# ------------------------------------------------------------------ diffuse reflections
+def test_reflections_with_black_faces_are_the_view_factor_counts():
+    # eps = 1, rho = 0: every path ends at its first hit, so the counts are Eq. 3.15's
+    m = synth.plates(4)
+    rays = np.full(m.n_faces, 3000, np.int64)
+    n = m.n_faces
+    c0 = mcrt.trace_counts(m.verts, m.tris, m.tri_face, n, rays, 3)
+    c1, st = mcrt.trace_reflect(m.verts, m.tris, m.tri_face, n, rays, np.ones(n), np.zeros(n), 3)
+    assert np.array_equal(c0, c1)
+    assert st["lost"] == 0 and st["overflow"] == 0 and st["rays"] == rays.sum()
+
+
+def test_reflections_in_a_closed_cube_conserve_every_ray():
+    m = synth.cube()
+    rays = np.full(6, 20000, np.int64)
+    c, st = mcrt.trace_reflect(m.verts, m.tris, m.tri_face, 6, rays, np.full(6, 0.8), np.full(6, 0.2), 1)
+    assert np.array_equal(c.sum(axis=1), rays) and np.all(c[:, 6] == 0)
+    assert st["lost"] == 0 and st["overflow"] == 0
+    # expected hits per path: 1 / eps
+    assert abs(st["hits"] / rays.sum() - 1.25) < 0.01
+
+
+def _within_sigma(counts, rays, B, k=5.0):
+    Bh = counts / rays[:, None]
+    sig = np.sqrt(np.maximum(B * (1 - B), 1e-12) / rays[:, None])
+    return np.abs(Bh - B) <= k * sig
+
+
+def test_reflections_estimate_the_gebhart_factors_of_the_cube():
+    # closed-form cube view factors -> fp64 REFs (Eq. B.5) -> the random walk's expectation
+    from oracle import gebhart as G
+    opp, adj = cf.parallel_opposed(1, 1, 1), cf.perpendicular_common_edge(1, 1, 1)
+    F = np.full((6, 7), adj)
+    F[:, 6] = 0.0
+    for i in range(6):
+        F[i, i] = 0.0
+        F[i, i ^ 1] = opp
+    eps = np.array([0.9, 0.3, 0.6, 0.8, 0.5, 0.7])
+    B = G.gebhart(F, eps, 1 - eps)
+    m = synth.cube()
+    rays = np.full(6, 200000, np.int64)
+    c, _ = mcrt.trace_reflect(m.verts, m.tris, m.tri_face, 6, rays, eps, 1 - eps, 2)
+    assert np.all(_within_sigma(c, rays, B))
+
+
+def test_reflections_reproduce_the_printed_parallel_plate_refs():
+    # Sec. 6.3: eps = 0.5 on every face; the plates are set at the distance whose exact
+    # view factor is the printed F_23 = 0.285913 (Eq. 6.10), so the walk's expectation is
+    # the printed B (Eq. 6.11) up to its 6 decimals
+    from scipy.optimize import brentq
+    gap = brentq(lambda h: cf.parallel_opposed(1, 1, h) - 0.285913, 0.2, 5.0)
+    m = synth.two_sided_plates(gap=gap)
+    rays = np.full(4, 400000, np.int64)
+    c, st = mcrt.trace_reflect(m.verts, m.tris, m.tri_face, 4, rays, np.full(4, 0.5), np.full(4, 0.5), 5)
+    Bp = load_matrix("plates_B.txt")
+    Bh = c / rays[:, None]
+    sig = np.sqrt(np.maximum(Bp * (1 - Bp), 1e-12) / rays[:, None])
+    assert np.all(np.abs(Bh - Bp) <= 5 * sig + 1e-6)
+    assert np.all(c[[0, 3], :4] == 0)           # the outer sides only see the environment
