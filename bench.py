@@ -52,6 +52,12 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-e2e", action="store_true", help=argparse.SUPPRESS)
+    ap.add_argument("--trace-once", type=float, default=None, metavar="SCALE",
+                    help="instead of the bench line, run the plates trace launch once at SCALE x its ray "
+                         "budget (the small case the ncu captures use) and print the ray count")
+    ap.add_argument("--solve-scaling", action="store_true",
+                    help="instead of the bench line, print one JSON line with tensor-core GEMM rates and REF "
+                         "solve + adjoint times against the FP64 GPU path at N = 512, 2,048 and 10,240")
     return ap.parse_args()
 
 
@@ -180,6 +186,45 @@ def profiled_traffic(summary, source, units):
     if fields.get("source_sha256") != sha or "dram_bytes_per_unit" not in fields:
         return None
     return float(fields["dram_bytes_per_unit"]) * units
+
+
+def stage_rooflines(api, torch, ctx, pipe, flush, stream, peaks):
+    """Achieved fractions of the iterative enforcer (HBM bound: 16 B per matrix entry per
+    iteration) and of the REF solve (tensor bound; algorithmic flops of an LU-based solve,
+    2/3 N^3 + 2 N^2 (N+1), plus 2 N^2 (N+1) per refinement sweep) on the bench workload."""
+    N = pipe.N
+    F = torch.empty_like(pipe.F)
+    t_enf, iters = [], 0
+    for _ in range(3):
+        F.copy_(pipe.F)
+        flush()
+        box = [0]
+        t_enf.append(time_region(torch, lambda: box.__setitem__(0, api.enforce_iterative(ctx, F, pipe.areas,
+                                                                                          tol=1e-12)), stream))
+        iters = box[0]
+    ms_e = statistics.median(t_enf)
+    gbs = 16.0 * N * (N + 1) * iters / (ms_e * 1e-3) / 1e9
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    t_ref, sweeps = [], 0
+    for _ in range(3):
+        flush()
+        box = [0]
+        t_ref.append(time_region(torch, lambda: box.__setitem__(0, api.gebhart(
+            ctx, pipe.F_it, pipe.eps, pipe.rho, SOLVE_PRECISION, tol=SOLVE_TOL, B=pipe.B)[1]), stream))
+        sweeps = box[0]
+    ms_r = statistics.median(t_ref)
+    flops = 2.0 / 3.0 * N ** 3 + 2.0 * N * N * (N + 1) * (1 + sweeps)
+    tf = flops / (ms_r * 1e-3) / 1e12
+    bf = float(peaks.get("bf16_tflops", 1900.0))
+    return {
+        "enforce_iterative": {"kernel": "sym_pass + row_pass", "bound": "hbm", "achieved": round(gbs, 1),
+                              "peak": hbm, "unit": "GB/s", "frac": round(gbs / hbm, 4), "iterations": iters,
+                              "ms": round(ms_e, 4),
+                              "note": f"{16 * N * (N + 1) / 1e6:.1f} MB per iteration, L2-resident at N={N}"},
+        "gebhart": {"kernel": "gemm_kernel (tcgen05) + helpers", "bound": "tensor", "achieved": round(tf, 3),
+                    "peak": bf, "unit": "TFLOP/s", "frac": round(tf / bf, 5), "sweeps": sweeps, "ms": round(ms_r, 4),
+                    "note": f"N={N}: launch- and latency-bound ({SOLVE_PRECISION} peak = bf16 peak)"},
+    }
 
 
 def fp64_solve(torch, F, eps, rho, A, Q):
@@ -342,6 +387,7 @@ def run_ours(args):
                     "tri_tests_per_ray": round(st["tri_tests"] / st["rays"], 3), "trace_ms": round(trace_ms, 3),
                     "peak_basis": f"{sm_count} SMs x 128 lanes x {max_mhz:.0f} MHz (sm_max_mhz, MEASURED_PEAKS.json)"}
         roofline["traffic"] = profiled_traffic("trace_kernel_plates.md", "trace.cu", rays_per_step)
+        other_rooflines = stage_rooflines(api, torch, ctx, pipe, flush, stream, peaks)
 
         out = {
             "metric": METRIC, "value": job_throughput(rays_per_step, world, ms), "unit": "rays/s", "n_gpus": world,
@@ -354,7 +400,8 @@ def run_ours(args):
                        "wall_s_timed_region": round(wall, 3)},
             "stage_ms": {k: round(v, 3) for k, v in stages.items()},
             "enforce": {"iterative_iters": pipe.iters, "lsq_passes": pipe.passes},
-            "solve": solve, "roofline": roofline, "clocks": clk.summary(), "gpu_launches": int(launches),
+            "solve": solve, "roofline": roofline, "stage_rooflines": other_rooflines, "clocks": clk.summary(),
+            "gpu_launches": int(launches),
         }
         if not args.no_e2e:
             out["e2e"] = run_e2e(args, api, torch, ctx, w, device, stream)
@@ -494,8 +541,107 @@ def run_reference(args):
             "e2e": {"value": value, "unit": "rays/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+def solve_scaling(args):
+    """REF solve + adjoint at the three solve sizes of the workloads (enforced MCRT F at a
+    reduced ray budget), ours against torch.linalg.solve float64, and the tcgen05 GEMM
+    rates the solves are built on. CUDA events, after one warm-up call each."""
+    import torch
+    import synth
+    from paper_2511_04277_gb300 import api
+    ctx = api.Context(0)
+    dev = torch.device("cuda:0")
+
+    def ev(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        return statistics.mean(time_region(torch, fn, torch.cuda.current_stream()) for _ in range(reps))
+
+    out = {"kind": "solve_scaling", "precision": SOLVE_PRECISION, "gemm": [], "solves": []}
+    g = torch.Generator().manual_seed(0)
+    for M, N, K in ((4096, 4096, 4096), (10240, 10240, 10240)):
+        A = torch.randn(M, K, generator=g).to(torch.bfloat16).to(dev)
+        B = torch.randn(N, K, generator=g).to(torch.bfloat16).to(dev)
+        C = torch.zeros(M, N, dtype=torch.float32, device=dev)
+        ms = ev(lambda: api.tc_gemm(ctx, A, B, C), 5)
+        out["gemm"].append({"op": "bf16 A B^T -> fp32", "M": M, "N": N, "K": K, "ms": round(ms, 3),
+                            "tflops": round(2 * M * N * K / ms / 1e9, 1)})
+        del A, B, C
+    for M, N, K in ((10240, 10241, 61440),):
+        A = torch.randn(M, K, generator=g).to(torch.bfloat16).to(dev)
+        B = torch.randn(N, K, generator=g).to(torch.bfloat16).to(dev)
+        ms = ev(lambda: api.tc_gemm_residual(ctx, A, B, chunk_k=128), 3)
+        out["gemm"].append({"op": "refinement residual (6 slice pairs, compensated fp32 chunks)", "M": M, "N": N,
+                            "K": K, "ms": round(ms, 3), "tflops": round(2 * M * N * K / ms / 1e9, 1)})
+        del A, B
+    torch.cuda.empty_cache()
+    for name, scale, S in (("plates", 0.02, 1), ("small_sat", 0.02, 1), ("spacecraft", 0.01, 16)):
+        w = synth.workload(name, rays_scale=scale)
+        mesh = api.Mesh.from_synth(ctx, w["mesh"])
+        rays = torch.as_tensor(w["rays"], device=dev)
+        F = api.counts_to_F(ctx, api.trace(ctx, mesh, w["rays"], w["seed"]), rays)
+        api.enforce_iterative(ctx, F, torch.as_tensor(mesh.face_areas(), device=dev), tol=1e-12)
+        n = F.shape[0]
+        eps = torch.as_tensor(w["eps"][:S], device=dev)
+        rho = torch.as_tensor(w["rho"][:S], device=dev)
+        reps = 1 if n > 4096 else 5
+        box = {}
+        ms_f = ev(lambda: box.__setitem__("B", api.gebhart(ctx, F, eps, rho, SOLVE_PRECISION, tol=SOLVE_TOL)), reps)
+        B, sweeps, res = box["B"]
+        dB = torch.ones_like(B)
+        ms_a = ev(lambda: api.gebhart_adjoint(ctx, F, eps, rho, B, dB, SOLVE_PRECISION, tol=SOLVE_TOL), reps)
+        del dB
+        Fn = F[:, :n]
+
+        def fp64_pair():
+            K = torch.eye(n, dtype=torch.float64, device=dev) - Fn * rho[0][None, :]
+            E = F.clone()
+            E[:, :n] *= eps[0][None, :]
+            X = torch.linalg.solve(K, E)
+            return torch.linalg.solve(K.T, torch.ones_like(X))
+        try:
+            ms64 = ev(fp64_pair, reps) * S
+            Kd = torch.eye(n, dtype=torch.float64, device=dev) - Fn * rho[0][None, :]
+            Ed = F.clone()
+            Ed[:, :n] *= eps[0][None, :]
+            B64 = torch.linalg.solve(Kd, Ed)
+            err = float(((B[0] - B64).abs().amax(dim=-1) / B64.abs().amax(dim=-1)).max())
+            del Kd, Ed, B64
+        except RuntimeError as exc:
+            ms64, err = None, str(exc).splitlines()[0][:120]
+        out["solves"].append({"workload": name, "n": n, "sets": S, "ours_ms": round(ms_f + ms_a, 2),
+                              "refs_ms": round(ms_f, 2), "adjoint_ms": round(ms_a, 2), "sweeps": sweeps,
+                              "residual": res, "fp64_ms": None if ms64 is None else round(ms64, 2),
+                              "fp64_basis": "one set timed" + (f", x{S}" if S > 1 else ""),
+                              "speedup": None if ms64 is None else round(ms64 / (ms_f + ms_a), 2),
+                              "err_B_rownorm_set0": err})
+        del B, F
+        torch.cuda.empty_cache()
+    ctx.close()
+    return out
+
+
+def trace_once(scale):
+    import torch
+    import synth
+    from paper_2511_04277_gb300 import api
+    ctx = api.Context(0)
+    w = synth.workload("plates", rays_scale=scale)
+    mesh = api.Mesh.from_synth(ctx, w["mesh"])
+    c = api.trace(ctx, mesh, w["rays"], w["seed"], fma_free=True)
+    torch.cuda.synchronize()
+    print(json.dumps({"kind": "trace_once", "rays": int(c.sum()), "bvh": mesh.info()}), flush=True)
+    mesh.close()
+    ctx.close()
+
+
 def main():
     args = parse()
+    if args.trace_once is not None:
+        trace_once(args.trace_once)
+        return
+    if args.solve_scaling:
+        print(json.dumps(solve_scaling(args)), flush=True)
+        return
     out = run_reference(args) if args.impl == "reference" else run_ours(args)
     if out is not None:
         print(json.dumps(out), flush=True)

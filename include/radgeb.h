@@ -138,6 +138,28 @@ rg_status rg_trace_stats(rg_ctx* ctx, const rg_mesh* mesh, const int64_t* rays_p
                          uint64_t ray_offset, int32_t fma_free, int64_t* counts_d, uint64_t* stats_out_h,
                          void* stream);
 
+/* REFs directly from MCRT (Sec. 4.2.2): rays emitted as in rg_trace are followed
+ * through diffuse reflections. At bounce b (b = 1, 2, ...) the closest hit on face j
+ * is decided by word 3 of the Philox draw of counter (ray lo, ray hi, i, 128 b), i the
+ * path's source face: below floor(eps_j 2^32) the ray is absorbed and counted for
+ * column j; below floor((eps_j + rho_j) 2^32) it is reflected, i.e. re-emitted from
+ * face j exactly as an emission of face j (triangle and point from words 0-2 of that
+ * draw, Malley's direction from counters (ray lo, ray hi, i, 128 b + a), a = 1..64);
+ * otherwise it is lost. A miss is counted for the environment column. Re-emission
+ * from a uniform point of the hit face is the face-level model of Eq. 4.5, so
+ * counts_ij / N_i estimates the B_ij that rg_gebhart solves for from the exact view
+ * factors of the same faces.
+ *   eps_h, rho_h host fp64 [n_faces]: absorptivity and diffuse reflectivity,
+ *             eps, rho >= 0 and eps + rho <= 1 (the rest is lost)
+ *   max_bounces  a path still reflecting after this many hits ends as overflow
+ *             (1 <= max_bounces < 2^25)
+ *   counts_d  device int64 [N][N+1], ADDED to (absorbed on face j; column N escaped)
+ *   stats_out_h  host uint64[4] (may be NULL): rays, hits, lost, overflow
+ * fma_free, seed, ray_offset and the errors as rg_trace. */
+rg_status rg_trace_reflect(rg_ctx* ctx, const rg_mesh* mesh, const int64_t* rays_per_face_h, const double* eps_h,
+                           const double* rho_h, int32_t max_bounces, uint64_t seed, uint64_t ray_offset,
+                           int32_t fma_free, int64_t* counts_d, uint64_t* stats_out_h, void* stream);
+
 /* F_ij = N_ij / N_i (Eq. 3.15) for N x (N+1) counts.
  *   counts_d  device int64 [n][n+1];  rays_d device int64 [n] (N_i > 0)
  *   F_d       device fp64 [n][n+1] (output) */

@@ -45,6 +45,7 @@ SIGNATURES = {
     "rg_enforce_iterative_noalloc": (i32, [i32, P, P, f64, i32, P, P]),
     "rg_enforce_iterative_kappa": (i32, [P, i32, P, P, P, f64, i32, P, P]),
     "rg_kappa": (i32, [P, i32, i32, P, P, P, f64, P, P]),
+    "rg_trace_reflect": (i32, [P, P, P, P, P, i32, u64, u64, i32, P, P, P]),
     "rg_enforce_lsq": (i32, [P, i32, P, P, i32, i32, i32, P, P]),
     "rg_aggregate": (i32, [P, i32, P, P, P, i32, P, P, P]),
     "rg_gebhart": (i32, [P, i32, P, i32, P, P, i32, f64, i32, P, P, P, P]),

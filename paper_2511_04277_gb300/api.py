@@ -145,6 +145,27 @@ def trace_stats(ctx: Context, mesh: Mesh, rays_per_face, seed: int, ray_offset: 
     return counts, {"rays": int(st[0]), "box_tests": int(st[1]), "tri_tests": int(st[2])}
 
 
+def trace_reflect(ctx: Context, mesh: Mesh, rays_per_face, eps, rho, seed: int, max_bounces: int = 4096,
+                  ray_offset: int = 0, fma_free: bool = True, counts: torch.Tensor | None = None, stream=None):
+    """REFs directly from MCRT with diffuse reflections (rg_trace_reflect): (counts int64
+    [N, N+1] of rays absorbed per face, {"rays", "hits", "lost", "overflow"}).
+    ``eps`` and ``rho`` are per-face host arrays."""
+    N = mesh.n_faces
+    rays = np.ascontiguousarray(rays_per_face, np.int64)
+    e = np.ascontiguousarray(eps, np.float64)
+    r = np.ascontiguousarray(rho, np.float64)
+    if rays.shape != (N,) or e.shape != (N,) or r.shape != (N,):
+        raise ValueError("rays_per_face, eps and rho must have one entry per face")
+    if counts is None:
+        counts = torch.zeros((N, N + 1), dtype=torch.int64, device=f"cuda:{ctx.device}")
+    st = np.zeros(4, np.uint64)
+    ctx.check(ctx.lib.rg_trace_reflect(ctx.handle, mesh.handle, _hptr(rays), _hptr(e), _hptr(r), int(max_bounces),
+                                       int(seed) & (2 ** 64 - 1), int(ray_offset), int(bool(fma_free)),
+                                       _dptr(counts, torch.int64, "counts", N * (N + 1), ctx.device), _hptr(st),
+                                       _stream(stream)), "rg_trace_reflect")
+    return counts, {"rays": int(st[0]), "hits": int(st[1]), "lost": int(st[2]), "overflow": int(st[3])}
+
+
 def launch_count(ctx: Context) -> int:
     """Kernels the context has launched so far (rg_launch_count)."""
     n = ctypes.c_int64(0)

@@ -24,6 +24,9 @@
 // own (no fused multiply-add), which makes the counts bit-identical to any other
 // implementation of the same ray definition that does the same.
 #include <climits>
+#include <cmath>
+#include <cstring>
+#include <vector>
 
 #include "mesh.cuh"
 
@@ -53,7 +56,12 @@ struct TraceParams {
   uint64_t ray_offset;
   unsigned long long* counts;  // [N][N+1]
   int32_t n_bins;              // N + 1
-  unsigned long long* stats;   // [3]: rays, box tests, triangle tests (statistics kernels only)
+  unsigned long long* stats;   // [3]: rays, box tests, triangle tests (statistics kernels only);
+                               // [4] for the reflection kernel: rays, hits, lost, overflow
+  // reflection kernel only: per-face floor(eps 2^32) and floor((eps + rho) 2^32)
+  const unsigned long long* thr_absorb;
+  const unsigned long long* thr_reflect;
+  int32_t max_bounces;
 };
 
 template <bool kExact>
@@ -251,12 +259,16 @@ __device__ int32_t closest_face(const DevMesh& m, int32_t src, V3 o, V3 d, bool*
   return best_face;
 }
 
+// Emission from `face` with the draws of counters (ray lo, ray hi, stream, base + a):
+// a = 0 for the triangle and the point, a = 1..64 for Malley's direction. Emission
+// proper uses stream = face and base = 0; the reflection of bounce b of a path from
+// face i uses stream = i and base = 128 b (re-emission from the hit face).
 template <bool E>
 __device__ __forceinline__ void sample_ray(const DevMesh& m, uint32_t k0, uint32_t k1, uint64_t ray, int32_t face,
-                                           V3* o, V3* d, int32_t* src) {
+                                           V3* o, V3* d, int32_t* src, uint32_t stream, uint32_t base) {
   using A = Ar<E>;
   const uint32_t rlo = (uint32_t)ray, rhi = (uint32_t)(ray >> 32);
-  uint4 x = philox(make_uint4(rlo, rhi, (uint32_t)face, 0u), k0, k1);
+  uint4 x = philox(make_uint4(rlo, rhi, stream, base), k0, k1);
   // first record whose threshold exceeds x.x (thresholds are non-decreasing; meshes
   // have fewer than 2^30 triangles)
   int32_t a = (int32_t)m.face_start[face], b = (int32_t)m.face_start[face + 1] - 1;
@@ -284,7 +296,7 @@ __device__ __forceinline__ void sample_ray(const DevMesh& m, uint32_t k0, uint32
   o->z = A::add(A::add(A::add(r0.z, A::mul(u, r1.y)), A::mul(v, r2.x)), A::mul(m.lift, nz));
   float dx = 0.f, dy = 0.f, s2 = 0.f;
   for (uint32_t att = 1; att <= 64; ++att) {
-    uint4 y = philox(make_uint4(rlo, rhi, (uint32_t)face, att), k0, k1);
+    uint4 y = philox(make_uint4(rlo, rhi, stream, base + att), k0, k1);
     float cx = sym24(y.x), cy = sym24(y.y);
     float cs = A::add(A::mul(cx, cx), A::mul(cy, cy));
     if (cs < 1.0f) { dx = cx; dy = cy; s2 = cs; break; }
@@ -441,7 +453,8 @@ __global__ void __launch_bounds__(kThreads, RG_REFILL_MIN_BLOCKS) trace_kernel_r
         if (valid) {
           V3 o, d;
           int32_t src;
-          sample_ray<E>(m, p.key0, p.key1, p.ray_offset + (uint64_t)(wi.begin + r), wi.face, &o, &d, &src);
+          sample_ray<E>(m, p.key0, p.key1, p.ray_offset + (uint64_t)(wi.begin + r), wi.face, &o, &d, &src,
+                              (uint32_t)wi.face, 0u);
           const int slot = (head + avail + lane) & (kRing - 1);
           ring.ox[slot] = o.x; ring.oy[slot] = o.y; ring.oz[slot] = o.z;
           ring.dx[slot] = d.x; ring.dy[slot] = d.y; ring.dz[slot] = d.z;
@@ -549,7 +562,8 @@ __global__ void __launch_bounds__(kThreads, RG_LOCKSTEP_MIN_BLOCKS) trace_kernel
       const bool valid = r < wi.count;
       V3 o, d;
       int32_t src = -1;
-      if (valid) sample_ray<E>(m, p.key0, p.key1, p.ray_offset + (uint64_t)(wi.begin + r), wi.face, &o, &d, &src);
+      if (valid) sample_ray<E>(m, p.key0, p.key1, p.ray_offset + (uint64_t)(wi.begin + r), wi.face, &o, &d, &src,
+                              (uint32_t)wi.face, 0u);
       bool more = false;
       int32_t face = m.n_faces;
       if (valid) {
@@ -630,11 +644,108 @@ __global__ void __launch_bounds__(kThreads, RG_LOCKSTEP_MIN_BLOCKS) trace_kernel
   }
 }
 
+// REFs directly from MCRT (Sec. 4.2.2): every lane follows its own path through its
+// bounces (closest hit, Philox decision between absorption, diffuse re-emission from the
+// hit face and loss); finished paths are tallied per absorbing face (column N: escaped)
+// in the block's shared-memory row of the item's source face.
+template <bool E, bool kBVH>
+__global__ void __launch_bounds__(kThreads) trace_kernel_reflect(const TraceParams p) {
+  extern __shared__ __align__(16) uint32_t hist[];
+  __shared__ int32_t s_item;
+  __shared__ int32_t s_next;
+  const int lane = threadIdx.x & 31;
+  bool overflow = false;
+  NoStats st;
+  unsigned long long n_rays = 0, n_hits = 0, n_lost = 0, n_over = 0;
+  const DevMesh& m = p.m;
+  while (true) {
+    if (threadIdx.x == 0) {
+      s_item = atomicAdd(p.item_counter, 1);
+      s_next = 0;
+    }
+    for (int b = threadIdx.x; b < p.n_bins; b += kThreads) hist[b] = 0u;
+    __syncthreads();
+    const int32_t item = s_item;
+    if (item >= p.n_items) break;
+    const WorkItem wi = p.items[item];
+    while (true) {
+      int base = 0;
+      if (lane == 0) base = atomicAdd(&s_next, 32);
+      base = __shfl_sync(0xffffffffu, base, 0);
+      if (base >= wi.count) break;
+      const int r = base + lane;
+      int32_t col = -1;  // absorbing face, N (escaped) or -1 (lost / overflow / no ray)
+      if (r < wi.count) {
+        const uint64_t ray = p.ray_offset + (uint64_t)(wi.begin + r);
+        const uint32_t stream = (uint32_t)wi.face;
+        V3 o, d;
+        int32_t src;
+        sample_ray<E>(m, p.key0, p.key1, ray, wi.face, &o, &d, &src, stream, 0u);
+        ++n_rays;
+        for (int32_t bounce = 1;; ++bounce) {
+          const int32_t j = closest_face<E, kBVH>(m, src, o, d, &overflow, st);
+          if (j == m.n_faces) { col = j; break; }
+          ++n_hits;
+          const uint32_t cb = (uint32_t)bounce << 7;
+          const uint4 x = philox(make_uint4((uint32_t)ray, (uint32_t)(ray >> 32), stream, cb), p.key0, p.key1);
+          const unsigned long long dec = x.w;
+          if (dec < p.thr_absorb[j]) { col = j; break; }
+          if (dec >= p.thr_reflect[j]) { ++n_lost; break; }
+          if (bounce >= p.max_bounces) { ++n_over; break; }
+          sample_ray<E>(m, p.key0, p.key1, ray, j, &o, &d, &src, stream, cb);
+        }
+      }
+      const bool fin = col >= 0;
+      const unsigned fm = __ballot_sync(0xffffffffu, fin);
+      if (fin) {
+        const unsigned peers = __match_any_sync(fm, col);
+        if (lane == __ffs(peers) - 1) atomicAdd(&hist[col], (uint32_t)__popc(peers));
+      }
+    }
+    __syncthreads();
+    unsigned long long* row = p.counts + (int64_t)wi.face * p.n_bins;
+    for (int b = threadIdx.x; b < p.n_bins; b += kThreads) {
+      uint32_t c = hist[b];
+      if (c) atomicAdd(row + b, (unsigned long long)c);
+    }
+    __syncthreads();
+  }
+  if (overflow) atomicExch(p.error_word, 1);
+  for (int o = 16; o > 0; o >>= 1) {
+    n_rays += __shfl_xor_sync(0xffffffffu, n_rays, o);
+    n_hits += __shfl_xor_sync(0xffffffffu, n_hits, o);
+    n_lost += __shfl_xor_sync(0xffffffffu, n_lost, o);
+    n_over += __shfl_xor_sync(0xffffffffu, n_over, o);
+  }
+  if (lane == 0) {
+    atomicAdd(p.stats, n_rays);
+    atomicAdd(p.stats + 1, n_hits);
+    atomicAdd(p.stats + 2, n_lost);
+    atomicAdd(p.stats + 3, n_over);
+  }
+}
+
 inline size_t trace_smem_bytes(int n_bins) { return (size_t)((n_bins + 3) & ~3) * sizeof(uint32_t); }
 
 template <bool E, bool B, class St>
 cudaError_t launch(const TraceParams& p, int sm_count, size_t smem, cudaStream_t s) {
   auto k = p.m.refill ? trace_kernel_refill<E, B, St> : trace_kernel_lockstep<E, B, St>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kThreads, smem);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  int grid = sm_count * per_sm;
+  if (grid > p.n_items) grid = p.n_items;
+  k<<<grid, kThreads, smem, s>>>(p);
+  return cudaGetLastError();
+}
+
+// Reflection launches: one persistent block per resident slot.
+template <bool E, bool B>
+cudaError_t launch_reflect(const TraceParams& p, int sm_count, size_t smem, cudaStream_t s) {
+  auto k = trace_kernel_reflect<E, B>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int per_sm = 0;
@@ -728,6 +839,88 @@ rg_status rg_trace_stats(rg_ctx* ctx, const rg_mesh* mesh, const int64_t* rays_p
                          void* stream) {
   if (!stats_out_h) return rg::fail(ctx, RG_ERR_ARG, "rg_trace_stats: NULL stats");
   return trace_impl(ctx, mesh, rays_per_face_h, seed, ray_offset, fma_free, counts_d, stats_out_h, stream);
+}
+
+rg_status rg_trace_reflect(rg_ctx* ctx, const rg_mesh* mesh, const int64_t* rays_per_face_h, const double* eps_h,
+                           const double* rho_h, int32_t max_bounces, uint64_t seed, uint64_t ray_offset,
+                           int32_t fma_free, int64_t* counts_d, uint64_t* stats_out_h, void* stream) {
+  if (!ctx) return RG_ERR_ARG;
+  RG_ARG_CHECK(ctx, mesh && rays_per_face_h && eps_h && rho_h && counts_d, "rg_trace_reflect: NULL argument");
+  RG_ARG_CHECK(ctx, max_bounces >= 1 && max_bounces < (1 << 25), "rg_trace_reflect: max_bounces %d outside [1, 2^25)",
+               max_bounces);
+  const DevMesh& m = mesh_device_view(mesh);
+  RG_ARG_CHECK(ctx, mesh_device(mesh) == ctx->device, "rg_trace_reflect: mesh belongs to another device");
+  const int32_t N = m.n_faces;
+  const int32_t n_bins = N + 1;
+  const size_t smem = trace_smem_bytes(n_bins);
+  if (n_bins > 49152 || (int)smem > ctx->smem_optin - 1024)
+    return rg::fail(ctx, RG_ERR_UNSUPPORTED, "rg_trace_reflect: %d faces exceed the shared-memory tally row", N);
+  // per-face decision thresholds: x < floor(eps 2^32) absorbs, x < floor((eps + rho) 2^32) reflects
+  std::vector<unsigned long long> thr(2 * (size_t)N);
+  for (int32_t f = 0; f < N; ++f) {
+    const double a = eps_h[f], r = rho_h[f];
+    RG_ARG_CHECK(ctx, a >= 0.0 && r >= 0.0 && a + r <= 1.0, "rg_trace_reflect: face %d has eps %.17g, rho %.17g", f,
+                 a, r);
+    thr[f] = (unsigned long long)std::floor(a * 4294967296.0);
+    thr[N + f] = (unsigned long long)std::floor((a + r) * 4294967296.0);
+  }
+  constexpr int64_t kChunk = 1 << 14;  // paths are long and uneven: smaller items balance the blocks
+  std::vector<WorkItem> items;
+  for (int32_t f = 0; f < N; ++f) {
+    int64_t n = rays_per_face_h[f];
+    RG_ARG_CHECK(ctx, n >= 0, "rg_trace_reflect: negative ray count for face %d", f);
+    for (int64_t b = 0; b < n; b += kChunk) items.push_back({b, f, (int32_t)std::min(kChunk, n - b)});
+  }
+  uint64_t h_stats[4] = {0, 0, 0, 0};
+  if (items.empty()) {
+    if (stats_out_h) memcpy(stats_out_h, h_stats, sizeof(h_stats));
+    return RG_OK;
+  }
+  RG_ARG_CHECK(ctx, items.size() < (size_t)INT32_MAX, "rg_trace_reflect: too many rays");
+  RG_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t thr_off = 256 + rg::align_up(items.size() * sizeof(WorkItem), 256);
+  void* ws = nullptr;
+  rg_status st = rg::workspace(ctx, thr_off + thr.size() * sizeof(unsigned long long), &ws);
+  if (st != RG_OK) return st;
+  char* wb = static_cast<char*>(ws);
+  unsigned long long* d_stats = reinterpret_cast<unsigned long long*>(wb);
+  WorkItem* d_items = reinterpret_cast<WorkItem*>(wb + 256);
+  unsigned long long* d_thr = reinterpret_cast<unsigned long long*>(wb + thr_off);
+  RG_CUDA_TRY(ctx, cudaMemcpyAsync(d_items, items.data(), items.size() * sizeof(WorkItem), cudaMemcpyHostToDevice, s));
+  RG_CUDA_TRY(ctx, cudaMemcpyAsync(d_thr, thr.data(), thr.size() * sizeof(unsigned long long), cudaMemcpyHostToDevice,
+                                   s));
+  RG_CUDA_TRY(ctx, cudaMemsetAsync(ctx->d_scratch, 0, 2 * sizeof(int32_t), s));
+  RG_CUDA_TRY(ctx, cudaMemsetAsync(d_stats, 0, 4 * sizeof(unsigned long long), s));
+  TraceParams p;
+  p.m = m;
+  p.items = d_items;
+  p.n_items = (int32_t)items.size();
+  p.item_counter = ctx->d_scratch;
+  p.error_word = ctx->d_scratch + 1;
+  p.key0 = (uint32_t)seed;
+  p.key1 = (uint32_t)(seed >> 32);
+  p.ray_offset = ray_offset;
+  p.counts = reinterpret_cast<unsigned long long*>(counts_d);
+  p.n_bins = n_bins;
+  p.stats = d_stats;
+  p.thr_absorb = d_thr;
+  p.thr_reflect = d_thr + N;
+  p.max_bounces = max_bounces;
+  const int sm = ctx->sm_count;
+  cudaError_t e;
+  if (fma_free)
+    e = m.use_bvh ? launch_reflect<true, true>(p, sm, smem, s) : launch_reflect<true, false>(p, sm, smem, s);
+  else
+    e = m.use_bvh ? launch_reflect<false, true>(p, sm, smem, s) : launch_reflect<false, false>(p, sm, smem, s);
+  if (e != cudaSuccess) return rg::cuda_fail(ctx, e, "rg_trace_reflect: launch");
+  ++ctx->launches;
+  RG_CUDA_TRY(ctx, cudaMemcpyAsync(ctx->h_scratch, ctx->d_scratch + 1, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  RG_CUDA_TRY(ctx, cudaMemcpyAsync(h_stats, d_stats, sizeof(h_stats), cudaMemcpyDeviceToHost, s));
+  RG_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+  if (stats_out_h) memcpy(stats_out_h, h_stats, sizeof(h_stats));
+  if (ctx->h_scratch[0]) return rg::fail(ctx, RG_ERR_STACK, "rg_trace_reflect: traversal stack overflow");
+  return RG_OK;
 }
 
 rg_status rg_launch_count(const rg_ctx* ctx, int64_t* launches_out_h) {

@@ -165,3 +165,83 @@ def test_rays_with_zero_direction_components(rg_ctx):
         g, _ = _gpu_counts(rg_ctx, m, rays, 0, use_bvh=sched)
         o = mcrt.trace_counts(m.verts, m.tris, m.tri_face, m.n_faces, rays, 0, use_bvh=False, faces=[12])
         assert np.array_equal(g, o), sched
+
+
+# ------------------------------------------------------------------ diffuse reflections
+def _reflect_both(rg_ctx, m, rays, eps, rho, seed, faces=None, max_bounces=4096):
+    mesh = api.Mesh.from_synth(rg_ctx, m)
+    g, st = api.trace_reflect(rg_ctx, mesh, rays, eps, rho, seed, max_bounces=max_bounces)
+    o, ost = mcrt.trace_reflect(m.verts, m.tris, m.tri_face, m.n_faces, rays, eps, rho, seed,
+                                max_bounces=max_bounces, faces=faces)
+    return g.cpu().numpy(), st, o, ost
+
+
+def test_reflect_cube_bit_exact(rg_ctx):
+    m = synth.cube()
+    eps = np.array([0.9, 0.3, 0.6, 0.8, 0.5, 0.7])
+    rays = np.full(6, 50000, np.int64)
+    g, st, o, ost = _reflect_both(rg_ctx, m, rays, eps, 1 - eps, 11)
+    assert np.array_equal(g, o)
+    assert st == ost
+
+
+def test_reflect_plates_bit_exact_with_losses(rg_ctx):
+    # eps + rho < 1 on some faces: the rest of the energy is lost, on both sides alike
+    m = synth.plates(4)
+    rng = np.random.default_rng(3)
+    eps = rng.uniform(0.1, 0.9, m.n_faces)
+    rho = (1 - eps) * rng.uniform(0.5, 1.0, m.n_faces)
+    rays = np.full(m.n_faces, 4000, np.int64)
+    rays[5] = 0
+    g, st, o, ost = _reflect_both(rg_ctx, m, rays, eps, rho, 4)
+    assert np.array_equal(g, o)
+    assert st == ost and st["lost"] > 0
+
+
+def test_reflect_small_sat_sampled_rows(rg_ctx):
+    m = synth.small_sat()
+    w = synth.workload("small_sat")
+    rays = np.full(m.n_faces, 500, np.int64)
+    rows = [0, 999, 2047]
+    g, st, o, _ = _reflect_both(rg_ctx, m, rays, w["eps"][0], w["rho"][0], 6, faces=rows)
+    for r in rows:
+        assert np.array_equal(g[r], o[r]), r
+    assert np.all(g.sum(axis=1) <= rays) and st["lost"] == 0     # eps + rho = 1: only escapes leave
+    assert np.array_equal(g.sum(axis=1), rays)
+
+
+def test_reflect_overflow_is_counted(rg_ctx):
+    # a closed cube of perfect reflectors: every path reflects until the bounce limit
+    m = synth.cube()
+    rays = np.full(6, 1000, np.int64)
+    g, st, o, ost = _reflect_both(rg_ctx, m, rays, np.zeros(6), np.ones(6), 1, max_bounces=7)
+    assert st == ost and st["overflow"] == 6000 and st["hits"] == 6000 * 7
+    assert g.sum() == 0 and np.array_equal(g, o)
+
+
+def test_reflect_estimates_the_refs_at_1e7_paths_per_face(rg_ctx):
+    """The walk's expectation is Eq. 4.5's B: on the cube with closed-form view factors
+    and on the two-sided plates at the printed F_23 (Sec. 6.3, printed B of Eq. 6.11),
+    1e7 paths per face, within 5 sigma."""
+    from oracle import gebhart as G
+    from scipy.optimize import brentq
+    from tests import closed_forms as cf
+    from tests.conftest import load_matrix
+    opp, adj = cf.parallel_opposed(1, 1, 1), cf.perpendicular_common_edge(1, 1, 1)
+    F = np.full((6, 7), adj)
+    F[:, 6] = 0.0
+    for i in range(6):
+        F[i, i] = 0.0
+        F[i, i ^ 1] = opp
+    eps = np.array([0.9, 0.3, 0.6, 0.8, 0.5, 0.7])
+    gap = brentq(lambda h: cf.parallel_opposed(1, 1, h) - 0.285913, 0.2, 5.0)
+    cases = [(synth.cube(), eps, G.gebhart(F, eps, 1 - eps)),
+             (synth.two_sided_plates(gap=gap), np.full(4, 0.5), load_matrix("plates_B.txt"))]
+    for m, e, B in cases:
+        mesh = api.Mesh.from_synth(rg_ctx, m)
+        rays = np.full(m.n_faces, 10_000_000, np.int64)
+        c, st = api.trace_reflect(rg_ctx, mesh, rays, e, 1 - e, 7)
+        Bh = c.cpu().numpy() / rays[:, None]
+        sig = np.sqrt(np.maximum(B * (1 - B), 1e-14) / rays[:, None])
+        assert np.all(np.abs(Bh - B) <= 5 * sig + 1e-6), m.name
+        assert st["lost"] == 0 and st["overflow"] == 0
