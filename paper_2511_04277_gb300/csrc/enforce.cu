@@ -4,7 +4,8 @@
 // Iterative enforcer layout: the caller's F (N x (N+1), row-major, ld = N+1) is turned
 // into H = Omega_i F_ij in place, and a row scale s (initially 1) is kept beside it, so
 // that the current iterate is eta_ij = s_i H_ij. One iteration is two kernels:
-//   sym_pass  one block per tile pair (I, J), I <= J, of 64 x 64 tiles: loads eta on
+//   sym_pass  one block per tile pair (I, J), I <= J, of 32 x 32 tiles (64 x 64 for
+//             N > 2,048): loads eta on
 //             both sides of the diagonal, writes H'_ij = kappa_ij eta_ij + (1 - kappa_ij)
 //             eta_ji (kappa = 1/2, or per pair from a kappa matrix), records the largest
 //             |eta_ij - eta_ji|/2 and per-tile row sums;
@@ -22,7 +23,11 @@
 
 namespace {
 
-constexpr int kT = 64;        // tile edge
+constexpr int kT = 64;        // tile edge for n > kSmallN (and the allocation-free variant's sizing)
+constexpr int kTSmall = 32;   // tile edge for n <= kSmallN: four times the blocks at N = 512
+constexpr int kSmallN = 2048;
+
+inline int tile_edge(int32_t n) { return n <= kSmallN ? kTSmall : kT; }
 constexpr int kThreads = 256;
 
 __global__ void counts_to_F_kernel(const long long* __restrict__ c, const long long* __restrict__ rays,
@@ -59,26 +64,26 @@ struct EnforceState {
   int32_t pad;
 };
 
-// kW: weights from kappa [n][n] (kappa_ij multiplies eta_ij); otherwise 1/2.
-template <bool kW>
+// T: tile edge; kW: weights from kappa [n][n] (kappa_ij multiplies eta_ij), else 1/2.
+template <int T, bool kW>
 __global__ void __launch_bounds__(kThreads) sym_pass(double* __restrict__ H, const double* __restrict__ s,
                                                      const double* __restrict__ kappa, int32_t n,
                                                      double* __restrict__ P, EnforceState* st) {
   if (st->done) return;
   const int I = blockIdx.y, J = blockIdx.x;
   if (I > J) return;
-  __shared__ double A[kT][kT + 1];
-  __shared__ double B[kT][kT + 1];
+  __shared__ double A[T][T + 1];
+  __shared__ double B[T][T + 1];
   __shared__ double red[kThreads];
   const int64_t ld = n + 1;
   const int tid = threadIdx.x;
   const bool off = I != J;
-  for (int e = tid; e < kT * kT; e += kThreads) {
-    int r = e / kT, c = e % kT;
-    int64_t i = (int64_t)I * kT + r, j = (int64_t)J * kT + c;
+  for (int e = tid; e < T * T; e += kThreads) {
+    int r = e / T, c = e % T;
+    int64_t i = (int64_t)I * T + r, j = (int64_t)J * T + c;
     A[r][c] = (i < n && j < n) ? s[i] * H[i * ld + j] : 0.0;
     if (off) {
-      int64_t i2 = (int64_t)J * kT + r, j2 = (int64_t)I * kT + c;
+      int64_t i2 = (int64_t)J * T + r, j2 = (int64_t)I * T + c;
       B[r][c] = (i2 < n && j2 < n) ? s[i2] * H[i2 * ld + j2] : 0.0;
     }
   }
@@ -93,32 +98,34 @@ __global__ void __launch_bounds__(kThreads) sym_pass(double* __restrict__ H, con
   };
   double dmax = 0.0;
   // tile (I, J): h(r, c) from A[r][c] and other(c, r); tile (J, I) likewise from B
-  for (int e = tid; e < kT * kT; e += kThreads) {
-    const int r = e / kT, c = e % kT;
-    const int64_t i = (int64_t)I * kT + r, j = (int64_t)J * kT + c;
+  for (int e = tid; e < T * T; e += kThreads) {
+    const int r = e / T, c = e % T;
+    const int64_t i = (int64_t)I * T + r, j = (int64_t)J * T + c;
     if (i < n && j < n) {
       const double a = A[r][c], b = off ? B[c][r] : A[c][r];
       H[i * ld + j] = pair(a, b, i, j);
       dmax = fmax(dmax, 0.5 * fabs(a - b));
     }
     if (off) {
-      const int64_t i2 = (int64_t)J * kT + r, j2 = (int64_t)I * kT + c;
+      const int64_t i2 = (int64_t)J * T + r, j2 = (int64_t)I * T + c;
       if (i2 < n && j2 < n) H[i2 * ld + j2] = pair(B[r][c], A[c][r], i2, j2);
     }
   }
-  // row sums of the written values: 4 threads per row, 16 columns each, fixed order
-  const int row = tid >> 2, part = tid & 3;
+  // row sums of the written values: kTpr threads per row, kCpt columns each, fixed order
+  constexpr int kTpr = kThreads / T, kCpt = T / kTpr;
+  const int row = tid / kTpr, part = tid % kTpr;
   double acc = 0.0, acc2 = 0.0;
-  const int64_t ri = (int64_t)I * kT + row, rj = (int64_t)J * kT + row;
-  for (int c = part * 16; c < part * 16 + 16; ++c) {
-    const int64_t ci = (int64_t)I * kT + c, cj = (int64_t)J * kT + c;
+  const int64_t ri = (int64_t)I * T + row, rj = (int64_t)J * T + row;
+  for (int c = part * kCpt; c < part * kCpt + kCpt; ++c) {
+    const int64_t ci = (int64_t)I * T + c, cj = (int64_t)J * T + c;
     if (ri < n && cj < n) acc += pair(A[row][c], off ? B[c][row] : A[c][row], ri, cj);
     if (off && rj < n && ci < n) acc2 += pair(B[row][c], A[c][row], rj, ci);
   }
-  acc += __shfl_xor_sync(0xffffffffu, acc, 1);
-  acc += __shfl_xor_sync(0xffffffffu, acc, 2);
-  acc2 += __shfl_xor_sync(0xffffffffu, acc2, 1);
-  acc2 += __shfl_xor_sync(0xffffffffu, acc2, 2);
+#pragma unroll
+  for (int o = 1; o < kTpr; o <<= 1) {
+    acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    acc2 += __shfl_xor_sync(0xffffffffu, acc2, o);
+  }
   if (part == 0) {
     if (ri < n) P[(int64_t)J * n + ri] = acc;
     if (off && rj < n) P[(int64_t)I * n + rj] = acc2;
@@ -311,7 +318,8 @@ rg_status enforce_iterative(rg_ctx* ctx, int32_t n, const double* omega_d, const
   RG_ARG_CHECK(ctx, n > 0 && omega_d && F_d && maxit > 0 && tol >= 0.0, "rg_enforce_iterative: bad argument");
   RG_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
   cudaStream_t s = (cudaStream_t)stream;
-  const int n_tiles = (n + kT - 1) / kT;
+  const int tile = tile_edge(n);
+  const int n_tiles = (n + tile - 1) / tile;
   rg::Sizer sz;
   sz.take<double>(n);                          // s
   sz.take<double>((size_t)n_tiles * n);        // P
@@ -342,10 +350,13 @@ rg_status enforce_iterative(rg_ctx* ctx, int32_t n, const double* omega_d, const
   for (int launched = 0; launched < maxit;) {
     int batch = std::min(8, maxit - launched);
     for (int b = 0; b < batch; ++b) {
-      if (kappa_d)
-        sym_pass<true><<<sym_grid, kThreads, 0, s>>>(F_d, sc, kappa_d, n, P, st);
-      else
-        sym_pass<false><<<sym_grid, kThreads, 0, s>>>(F_d, sc, nullptr, n, P, st);
+      if (tile == kTSmall) {
+        if (kappa_d) sym_pass<kTSmall, true><<<sym_grid, kThreads, 0, s>>>(F_d, sc, kappa_d, n, P, st);
+        else sym_pass<kTSmall, false><<<sym_grid, kThreads, 0, s>>>(F_d, sc, nullptr, n, P, st);
+      } else {
+        if (kappa_d) sym_pass<kT, true><<<sym_grid, kThreads, 0, s>>>(F_d, sc, kappa_d, n, P, st);
+        else sym_pass<kT, false><<<sym_grid, kThreads, 0, s>>>(F_d, sc, nullptr, n, P, st);
+      }
       ++ctx->launches;
       row_pass<<<row_blocks, kThreads, 0, s>>>(F_d, sc, omega_d, P, n, n_tiles, st, tol_abs, maxit);
       ++ctx->launches;
@@ -484,7 +495,8 @@ extern "C" rg_status rg_enforce_iterative_noalloc(int32_t n, const double* omega
   double* P = reinterpret_cast<double*>(b + kNoallocScaleBytes);
   EnforceState* st = reinterpret_cast<EnforceState*>(b + kNoallocScaleBytes + kNoallocRowSumBytes);
   unsigned long long* om_max = reinterpret_cast<unsigned long long*>(b + kNoallocScaleBytes + kNoallocRowSumBytes + 256);
-  const int n_tiles = (n + kT - 1) / kT;
+  const int tile = tile_edge(n);  // n_tiles * n <= kNoallocMaxTiles * kNoallocMaxN either way
+  const int n_tiles = (n + tile - 1) / tile;
   const int64_t total = (int64_t)n * (n + 1);
   int sm = 0;
   if (cudaDeviceGetAttribute(&sm, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) return RG_ERR_CUDA;
@@ -506,7 +518,8 @@ extern "C" rg_status rg_enforce_iterative_noalloc(int32_t n, const double* omega
   for (int launched = 0; launched < maxit;) {
     int batch = std::min(8, maxit - launched);
     for (int k = 0; k < batch; ++k) {
-      sym_pass<false><<<sym_grid, kThreads, 0, s>>>(F_d, sc, nullptr, n, P, st);
+      if (tile == kTSmall) sym_pass<kTSmall, false><<<sym_grid, kThreads, 0, s>>>(F_d, sc, nullptr, n, P, st);
+      else sym_pass<kT, false><<<sym_grid, kThreads, 0, s>>>(F_d, sc, nullptr, n, P, st);
       row_pass<<<row_blocks, kThreads, 0, s>>>(F_d, sc, omega_d, P, n, n_tiles, st, tol_abs, maxit);
     }
     launched += batch;
