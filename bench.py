@@ -554,7 +554,7 @@ def solve_scaling(args):
     def ev(fn, reps):
         fn()
         torch.cuda.synchronize()
-        return statistics.mean(time_region(torch, fn, torch.cuda.current_stream()) for _ in range(reps))
+        return statistics.median(time_region(torch, fn, torch.cuda.current_stream()) for _ in range(reps))
 
     out = {"kind": "solve_scaling", "precision": SOLVE_PRECISION, "gemm": [], "solves": []}
     g = torch.Generator().manual_seed(0)

@@ -47,7 +47,7 @@ rg_status encode_kmajor(rg_ctx* ctx, CUtensorMap* map, const void* base, bool bf
 
 template <int BN, int kStages, class Epi, bool kComp, bool kBF16>
 rg_status launch(rg_ctx* ctx, const CUtensorMap& ma, const CUtensorMap& mb, const GemmArgs& args, const Epi& epi,
-                 cudaStream_t s);
+                 cudaStream_t s, int grid_z = 1);
 
 }  // namespace
 
@@ -85,7 +85,7 @@ namespace {
 
 template <int BN, int kStages, class Epi, bool kComp, bool kBF16>
 rg_status launch(rg_ctx* ctx, const CUtensorMap& ma, const CUtensorMap& mb, const GemmArgs& args, const Epi& epi,
-                 cudaStream_t s) {
+                 cudaStream_t s, int grid_z) {
   auto kern = gemm_kernel<BN, kStages, Epi, kComp, kBF16>;
   constexpr size_t smem = smem_bytes<BN, kStages>();
   static thread_local int configured_device = -1;
@@ -93,7 +93,7 @@ rg_status launch(rg_ctx* ctx, const CUtensorMap& ma, const CUtensorMap& mb, cons
     RG_CUDA_TRY(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     configured_device = ctx->device;
   }
-  dim3 grid((args.N + BN - 1) / BN, (args.M + BM - 1) / BM);
+  dim3 grid((args.N + BN - 1) / BN, (args.M + BM - 1) / BM, grid_z);
   kern<<<grid, kThreads, smem, s>>>(ma, mb, args, epi);
   ++ctx->launches;
   RG_CUDA_TRY(ctx, cudaGetLastError());
@@ -117,10 +117,80 @@ rg_status gemm_f32(rg_ctx* ctx, bool bf16, const void* A, int64_t lda, const voi
               : launch<BN, 4, EpiF32, false, false>(ctx, ma, mb, args, epi, s);
 }
 
+namespace {
+
+// out = E - X + dl o (sum_z partial[z]) (or dl o sum when E is null), the sum over the K
+// splits in order z = 0, 1, ...; with red: max|out| -> red[0], max|X| -> red[1], column
+// maxima of out -> colmax, inf / NaN -> *nonfinite. Block (32 x 8) per 32 columns x 64 rows.
+__global__ void residual_finish(const double* __restrict__ partial, int64_t stride, int splits, int M, int N,
+                                int64_t ld, double* __restrict__ out, const double* __restrict__ E,
+                                const double* __restrict__ X, const double* __restrict__ dl, unsigned long long* red,
+                                unsigned long long* colmax, int* nonfinite) {
+  __shared__ double s_out[8][33], s_x[8][33];
+  const int c = blockIdx.x * 32 + threadIdx.x;
+  const int r0 = blockIdx.y * 64;
+  double m_out = 0.0, m_x = 0.0;
+  bool bad = false;
+  if (c < N) {
+    for (int r = r0 + threadIdx.y; r < min(M, r0 + 64); r += 8) {
+      const int64_t i = (int64_t)r * ld + c;
+      double acc = 0.0;
+      for (int z = 0; z < splits; ++z) acc += partial[(int64_t)z * stride + i];
+      const double sc = dl ? dl[r] : 1.0;
+      double o;
+      if (E) {
+        const double xi = X[i];
+        o = (E[i] - xi) + sc * acc;
+        m_x = fmax(m_x, fabs(xi));
+        bad |= !isfinite(xi);
+      } else {
+        o = sc * acc;
+      }
+      out[i] = o;
+      m_out = fmax(m_out, fabs(o));
+      bad |= !isfinite(o);
+    }
+  }
+  if (!red) return;
+  s_out[threadIdx.y][threadIdx.x] = m_out;
+  s_x[threadIdx.y][threadIdx.x] = m_x;
+  if (__syncthreads_or(bad) && threadIdx.x == 0 && threadIdx.y == 0 && nonfinite) atomicExch(nonfinite, 1);
+  if (threadIdx.y == 0) {
+    for (int y = 1; y < 8; ++y) {
+      m_out = fmax(m_out, s_out[y][threadIdx.x]);
+      m_x = fmax(m_x, s_x[y][threadIdx.x]);
+    }
+    if (colmax && c < N) atomic_max_nonneg(&colmax[c], m_out);
+    for (int o = 16; o > 0; o >>= 1) {
+      m_out = fmax(m_out, __shfl_xor_sync(0xffffffffu, m_out, o));
+      m_x = fmax(m_x, __shfl_xor_sync(0xffffffffu, m_x, o));
+    }
+    if (threadIdx.x == 0) {
+      atomic_max_nonneg(&red[0], m_out);
+      atomic_max_nonneg(&red[1], m_x);
+    }
+  }
+}
+
+}  // namespace
+
+int residual_splits(const rg_ctx* ctx, int M, int N, int K, int chunk_blocks, int split_max) {
+  const int tiles = ((M + BM - 1) / BM) * ((N + 63) / 64);
+  const int kb = (K + BK - 1) / BK;
+  const int chunk = chunk_blocks > 0 ? chunk_blocks : 1;
+  int best = 1;
+  // enough splits to give every SM a tile, in whole chunks
+  for (int z = 2; z <= split_max; ++z) {
+    if (tiles * (z - 1) >= ctx->sm_count) break;
+    if (kb % z == 0 && (kb / z) % chunk == 0) best = z;
+  }
+  return best;
+}
+
 rg_status gemm_residual(rg_ctx* ctx, const void* A, int64_t lda, const void* B, int64_t ldb, int M, int N, int K,
                         int chunk_blocks, double* out, const double* E, const double* X, const double* dl,
                         int64_t ld, cudaStream_t s, unsigned long long* red, unsigned long long* colmax,
-                        int* nonfinite) {
+                        int* nonfinite, double* split_ws, int split_max) {
   if (M <= 0 || N <= 0) return RG_OK;
   if (K <= 0) return rg::fail(ctx, RG_ERR_ARG, "gemm_residual: K = %d", K);
   constexpr int BN = 64;
@@ -129,8 +199,25 @@ rg_status gemm_residual(rg_ctx* ctx, const void* A, int64_t lda, const void* B, 
   if (st == RG_OK) st = encode_kmajor(ctx, &mb, B, true, N, K, ldb, BN);
   if (st != RG_OK) return st;
   GemmArgs args{M, N, K, chunk_blocks, ctx->d_scratch + kGemmErrorSlot};
-  EpiResidual epi{out, E, X, dl, ld, red, colmax, nonfinite};
-  return launch<BN, 6, EpiResidual, true, true>(ctx, ma, mb, args, epi, s);
+  const int splits = split_ws ? residual_splits(ctx, M, N, K, chunk_blocks, split_max) : 1;
+  if (splits <= 1) {
+    EpiResidual epi{out, E, X, dl, ld, red, colmax, nonfinite};
+    return launch<BN, 6, EpiResidual, true, true>(ctx, ma, mb, args, epi, s, 1);
+  }
+  const int kb = (K + BK - 1) / BK;
+  args.split_blocks = kb / splits;
+  const int64_t stride = (int64_t)M * ld;
+  EpiResidual epi{nullptr, nullptr, nullptr, nullptr, ld};
+  epi.partial = split_ws;
+  epi.split_stride = stride;
+  st = launch<BN, 6, EpiResidual, true, true>(ctx, ma, mb, args, epi, s, splits);
+  if (st != RG_OK) return st;
+  dim3 grid((N + 31) / 32, (M + 63) / 64);
+  residual_finish<<<grid, dim3(32, 8), 0, s>>>(split_ws, stride, splits, M, N, ld, out, E, X, dl, red, colmax,
+                                               nonfinite);
+  ++ctx->launches;
+  RG_CUDA_TRY(ctx, cudaGetLastError());
+  return RG_OK;
 }
 
 }  // namespace tc

@@ -205,7 +205,11 @@ inline int grid_for(int64_t total, int sm) {
 // ------------------------------------------------------------------ solver object
 struct Layout {
   int n, m, np, mp;
+  int splits;  // room for this many K splits of the residual GEMM (0: none)
 };
+
+// Most K splits of the refinement residual GEMM (used when its tiles leave SMs idle).
+constexpr int kMaxResidualSplits = 4;
 
 struct Buffers {
   void* A16;      // np x np
@@ -222,6 +226,7 @@ struct Buffers {
   double* R;    // residual (ld = mp)
   double* vec;  // [2][np] per-row scratch (row sums, diagonal scalings)
   unsigned long long* red;  // [3] max|R|, max|X|, e0 bits
+  double* split;  // [splits][np][mp] partial sums of a split residual GEMM (or null)
 };
 
 template <class Take>
@@ -237,6 +242,7 @@ void plan(const Layout& L, Take&& t) {
   t.template take<double>((size_t)L.np * L.mp);                   // R
   t.template take<double>((size_t)2 * L.np);                      // vec
   t.template take<unsigned long long>(4);                         // red
+  t.template take<double>((size_t)L.splits * L.np * L.mp);        // split
 }
 
 struct Solver {
@@ -259,6 +265,9 @@ struct Solver {
     L.m = m;
     L.np = (n + NB - 1) / NB * NB;
     L.mp = (m + NB - 1) / NB * NB;
+    L.splits = tc::residual_splits(ctx, L.n, L.m, kSlices * L.np, kResidualChunk, kMaxResidualSplits) > 1
+                   ? kMaxResidualSplits
+                   : 0;
     bf16 = use_bf16;
     s = stream;
     extra_bytes = rg::align_up(extra_bytes, 256);
@@ -284,6 +293,7 @@ struct Solver {
     b.R = cv.take<double>((size_t)L.np * L.mp);
     b.vec = cv.take<double>((size_t)2 * L.np);
     b.red = cv.take<unsigned long long>(4);
+    b.split = L.splits ? cv.take<double>((size_t)L.splits * L.np * L.mp) : nullptr;
     err = ctx->d_scratch + 32;
     RG_CUDA_TRY(ctx, cudaMemsetAsync(err, 0, 2 * sizeof(int), s));
     RG_CUDA_TRY(ctx, cudaMemsetAsync(ctx->d_scratch + tc::kGemmErrorSlot, 0, sizeof(int), s));
@@ -311,11 +321,11 @@ struct Solver {
     T16* Zt = static_cast<T16*>(b.Zt16);
     build_ns_start<T16><<<(L.np + 7) / 8, 256, 0, s>>>(P, ldp, transP, dl, dr, L.n, L.np, A16, X[0], Xt, b.red + 2);
     RG_CUDA_TRY(ctx, cudaGetLastError());
-    unsigned long long bits = 0;
-    RG_CUDA_TRY(ctx, cudaMemcpyAsync(&bits, b.red + 2, sizeof(bits), cudaMemcpyDeviceToHost, s));
+    // pinned read-back: one wait on the stream
+    RG_CUDA_TRY(ctx, cudaMemcpyAsync(ctx->h_scratch, b.red + 2, 8, cudaMemcpyDeviceToHost, s));
     RG_CUDA_TRY(ctx, cudaStreamSynchronize(s));
     double e0;
-    memcpy(&e0, &bits, sizeof(e0));
+    memcpy(&e0, ctx->h_scratch, sizeof(e0));
     if (!std::isfinite(e0)) return rg::fail(ctx, RG_ERR_NUMERIC, "non-finite system matrix");
     const double floor16 = bf16 ? 0x1p-10 : 0x1p-13;
     int steps = kMaxNewtonSchulz;
@@ -374,25 +384,32 @@ struct Solver {
     RG_CUDA_TRY(ctx, cudaMemsetAsync(b.colmax, 0, (size_t)L.mp * sizeof(unsigned long long), s));
     rg_status st = tc::gemm_residual(ctx, b.Aext, (int64_t)kSlices * L.np, b.Bext, (int64_t)kSlices * L.np, L.n, L.m,
                                      pairs * L.np, kResidualChunk, b.R, b.R0, b.X, dl, L.mp, s, b.red, b.colmax,
-                                     err + 1);
+                                     err + 1, b.split, L.splits);
     if (st != RG_OK) return st;
-    unsigned long long h[2];
-    RG_CUDA_TRY(ctx, cudaMemcpyAsync(h, b.red, sizeof(h), cudaMemcpyDeviceToHost, s));
+    // max|R|, max|X| and the error words in one pinned read-back and one wait
+    int* hs = ctx->h_scratch;
+    RG_CUDA_TRY(ctx, cudaMemcpyAsync(hs, b.red, 16, cudaMemcpyDeviceToHost, s));
+    RG_CUDA_TRY(ctx, cudaMemcpyAsync(hs + 4, err, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
+    RG_CUDA_TRY(ctx, cudaMemcpyAsync(hs + 6, ctx->d_scratch + tc::kGemmErrorSlot, sizeof(int), cudaMemcpyDeviceToHost,
+                                     s));
     RG_CUDA_TRY(ctx, cudaStreamSynchronize(s));
     double r, x;
-    memcpy(&r, &h[0], 8);
-    memcpy(&x, &h[1], 8);
+    memcpy(&r, hs, 8);
+    memcpy(&x, hs + 2, 8);
     *rel = x > 0 ? r / x : r;
-    return check_errors();
+    if (hs[6]) return rg::fail(ctx, RG_ERR_CUDA, "tensor-core GEMM timed out waiting on a barrier");
+    if (hs[5]) return rg::fail(ctx, RG_ERR_NUMERIC, "non-finite value in the solution or residual");
+    return RG_OK;
   }
 
   rg_status check_errors() {
-    int h[2] = {0, 0}, g = 0;
-    RG_CUDA_TRY(ctx, cudaMemcpyAsync(h, err, sizeof(h), cudaMemcpyDeviceToHost, s));
-    RG_CUDA_TRY(ctx, cudaMemcpyAsync(&g, ctx->d_scratch + tc::kGemmErrorSlot, sizeof(int), cudaMemcpyDeviceToHost, s));
+    int* hs = ctx->h_scratch;
+    RG_CUDA_TRY(ctx, cudaMemcpyAsync(hs + 4, err, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
+    RG_CUDA_TRY(ctx, cudaMemcpyAsync(hs + 6, ctx->d_scratch + tc::kGemmErrorSlot, sizeof(int), cudaMemcpyDeviceToHost,
+                                     s));
     RG_CUDA_TRY(ctx, cudaStreamSynchronize(s));
-    if (g) return rg::fail(ctx, RG_ERR_CUDA, "tensor-core GEMM timed out waiting on a barrier");
-    if (h[1]) return rg::fail(ctx, RG_ERR_NUMERIC, "non-finite value in the solution or residual");
+    if (hs[6]) return rg::fail(ctx, RG_ERR_CUDA, "tensor-core GEMM timed out waiting on a barrier");
+    if (hs[5]) return rg::fail(ctx, RG_ERR_NUMERIC, "non-finite value in the solution or residual");
     return RG_OK;
   }
 
@@ -804,7 +821,8 @@ rg_status rg_gebhart_adjoint(rg_ctx* ctx, int32_t n, const double* F_d, int32_t 
     ++ctx->launches;
     RG_CUDA_TRY(ctx, cudaGetLastError());
     st = tc::gemm_residual(ctx, sv.b.Aext, (int64_t)kSlices * sv.L.np, sv.b.Bext, (int64_t)kSlices * sv.L.np, n,
-                           n + 1, kSlices * sv.L.np, kResidualChunk, sv.b.R, nullptr, nullptr, nullptr, sv.L.mp, s);
+                           n + 1, kSlices * sv.L.np, kResidualChunk, sv.b.R, nullptr, nullptr, nullptr, sv.L.mp, s,
+                           nullptr, nullptr, nullptr, sv.b.split, sv.L.splits);
     if (st != RG_OK) return st;
     grad_rho<<<(n + 7) / 8, 256, 0, s>>>(B_d + off, sv.b.R, sv.L.mp, n, drho_d + (size_t)set * n);
     ++ctx->launches;

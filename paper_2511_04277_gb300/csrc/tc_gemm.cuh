@@ -219,6 +219,11 @@ struct EpiStore16Both {
   }
 };
 
+// Epilogues that read fp64 operands of the output tile go through the staging block in
+// batches of kRowBatch rows: the loads of a batch are issued together, so a warp waits
+// for one memory latency per batch rather than one per row.
+constexpr int kRowBatch = 8;
+
 // X64[r][c] = (first ? 0 : X64[r][c]) + acc * colscale[c]   (the refinement correction)
 struct EpiAddF64 {
   double* X;
@@ -227,11 +232,30 @@ struct EpiAddF64 {
   int first;
   __device__ __forceinline__ void store(int row0, int lane, int c0, int M, int N, const float* v,
                                         float (*stage)[33]) const {
-    staged_rows(row0, lane, c0, M, N, v, stage, [&](int r, int c, float x) {
-      double* p = X + (int64_t)r * ld + c;
-      const double d = (double)x * (double)colscale[c];
-      *p = first ? d : *p + d;
-    });
+#pragma unroll
+    for (int i = 0; i < 32; ++i) stage[lane][i] = v[i];
+    __syncwarp();
+    const int c = c0 + lane;
+    const bool cok = c < N;
+    const double cs = cok ? (double)colscale[c] : 0.0;
+#pragma unroll 1
+    for (int rb = 0; rb < 32; rb += kRowBatch) {
+      double old[kRowBatch];
+#pragma unroll
+      for (int q = 0; q < kRowBatch; ++q) {
+        const int r = row0 + rb + q;
+        old[q] = (!first && cok && r < M) ? X[(int64_t)r * ld + c] : 0.0;
+      }
+#pragma unroll
+      for (int q = 0; q < kRowBatch; ++q) {
+        const int r = row0 + rb + q;
+        if (cok && r < M) {
+          const double d = (double)stage[rb + q][lane] * cs;
+          X[(int64_t)r * ld + c] = first ? d : old[q] + d;
+        }
+      }
+    }
+    __syncwarp();
   }
 };
 
@@ -253,26 +277,47 @@ struct EpiResidual {
   unsigned long long* red = nullptr;     // [2], zeroed by the caller
   unsigned long long* colmax = nullptr;  // [N], zeroed by the caller (may be null)
   int* nonfinite = nullptr;
+  double* partial = nullptr;             // split K: CTA z writes its raw sum to partial + z * split_stride
+  int64_t split_stride = 0;
   __device__ __forceinline__ void store(int row0, int lane, int c0, int M, int N, const double* v,
-                                        double (*stage)[33]) const {
+                                        double (*stage)[33], int z) const {
+    if (partial) {
+      double* dst = partial + (int64_t)z * split_stride;
+      staged_rows(row0, lane, c0, M, N, v, stage, [&](int r, int c, double x) { dst[(int64_t)r * ld + c] = x; });
+      return;
+    }
     double m_out = 0.0, m_x = 0.0;
     bool bad = false;
-    staged_rows(row0, lane, c0, M, N, v, stage, [&](int r, int c, double x) {
-      const double s = dl ? dl[r] : 1.0;
-      const int64_t i = (int64_t)r * ld + c;
-      double o;
-      if (E) {
-        const double xi = X[i];
-        o = (E[i] - xi) + s * x;
-        m_x = fmax(m_x, fabs(xi));
-        bad |= !isfinite(xi);
-      } else {
-        o = s * x;
+#pragma unroll
+    for (int i = 0; i < 32; ++i) stage[lane][i] = v[i];
+    __syncwarp();
+    const int c = c0 + lane;
+    const bool cok = c < N;
+#pragma unroll 1
+    for (int rb = 0; rb < 32; rb += kRowBatch) {
+      double e[kRowBatch], xo[kRowBatch], s[kRowBatch];
+#pragma unroll
+      for (int q = 0; q < kRowBatch; ++q) {
+        const int r = row0 + rb + q;
+        const bool ok = cok && r < M;
+        const int64_t i = (int64_t)r * ld + c;
+        e[q] = (ok && E) ? E[i] : 0.0;
+        xo[q] = (ok && E) ? X[i] : 0.0;
+        s[q] = (r < M && dl) ? dl[r] : 1.0;
       }
-      out[i] = o;
-      m_out = fmax(m_out, fabs(o));
-      bad |= !isfinite(o);
-    });
+#pragma unroll
+      for (int q = 0; q < kRowBatch; ++q) {
+        const int r = row0 + rb + q;
+        if (!(cok && r < M)) continue;
+        const double x = stage[rb + q][lane];
+        const double o = E ? (e[q] - xo[q]) + s[q] * x : s[q] * x;
+        out[(int64_t)r * ld + c] = o;
+        m_out = fmax(m_out, fabs(o));
+        m_x = fmax(m_x, fabs(xo[q]));
+        bad |= !isfinite(o) || !isfinite(xo[q]);
+      }
+    }
+    __syncwarp();
     if (red) {
       // this lane saw column c0 + lane of the warp's 32 rows
       if (colmax && c0 + lane < N) atomic_max_nonneg(&colmax[c0 + lane], m_out);
@@ -294,6 +339,7 @@ struct GemmArgs {
   int M, N, K;
   int chunk_blocks;  // 0: one fp32 accumulation over all of K; > 0: compensated chunks
   int* error_word;
+  int split_blocks = 0;  // > 0: CTA z covers K blocks [z * split_blocks, (z + 1) * split_blocks)
 };
 
 template <int BN, int kStages, class Epi, bool kCompensated, bool kBF16>
@@ -323,7 +369,10 @@ __global__ void __launch_bounds__(kThreads, 1)
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
-  const int kb_total = (args.K + BK - 1) / BK;
+  const int kb_all = (args.K + BK - 1) / BK;
+  // split K: this CTA's K blocks are kb_first .. kb_first + kb_total - 1
+  const int kb_first = args.split_blocks > 0 ? blockIdx.z * args.split_blocks : 0;
+  const int kb_total = args.split_blocks > 0 ? min(args.split_blocks, kb_all - kb_first) : kb_all;
   const int chunk = (kCompensated && args.chunk_blocks > 0) ? args.chunk_blocks : kb_total;
   const int n_chunks = (kb_total + chunk - 1) / chunk;
 
@@ -358,8 +407,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (kb >= kStages && !mbar_wait(&empty[s], ((kb / kStages) - 1) & 1)) { *abort_flag = 1; break; }
         if (*abort_flag) break;
         mbar_expect_tx(&full[s], kABytes + kBBytes);
-        tma_load_2d(sA + s * kABytes, &map_a, &full[s], kb * BK, m0);
-        tma_load_2d(sB + s * kBBytes, &map_b, &full[s], kb * BK, n0);
+        tma_load_2d(sA + s * kABytes, &map_a, &full[s], (kb_first + kb) * BK, m0);
+        tma_load_2d(sB + s * kBBytes, &map_b, &full[s], (kb_first + kb) * BK, n0);
         ++issued;
       }
       if (*abort_flag) {
@@ -446,7 +495,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           double v[32];
 #pragma unroll
           for (int i = 0; i < 32; ++i) v[i] = (double)sum[c0 + i] - (double)comp[c0 + i];
-          epi.store(row0, lane, n0 + c0, args.M, args.N, v, stage);
+          epi.store(row0, lane, n0 + c0, args.M, args.N, v, stage, blockIdx.z);
         }
       }
     }
@@ -481,10 +530,17 @@ rg_status gemm_f32(rg_ctx* ctx, bool bf16, const void* A, int64_t lda, const voi
 // out (fp64, ld) = E - X + dl o (A B^T) (or dl o (A B^T) when E is null), bf16 operands,
 // fp32 tensor-core accumulation in chunks of `chunk_blocks` x 64 of K folded into a
 // compensated sum.
+// With split_ws (room for split_max x M x ld doubles) and too few 128 x 64 tiles to fill
+// the GPU, K is split over up to split_max CTAs per tile (in whole chunks); their sums go
+// to split_ws and one more kernel adds them in a fixed order and applies the epilogue.
 rg_status gemm_residual(rg_ctx* ctx, const void* A, int64_t lda, const void* B, int64_t ldb, int M, int N, int K,
                         int chunk_blocks, double* out, const double* E, const double* X, const double* dl,
                         int64_t ld, cudaStream_t s, unsigned long long* red = nullptr,
-                        unsigned long long* colmax = nullptr, int* nonfinite = nullptr);
+                        unsigned long long* colmax = nullptr, int* nonfinite = nullptr, double* split_ws = nullptr,
+                        int split_max = 0);
+
+// K splits gemm_residual uses for an M x N product (1: none).
+int residual_splits(const rg_ctx* ctx, int M, int N, int K, int chunk_blocks, int split_max);
 
 // Device error word the GEMM kernels raise on a timed-out wait (ctx scratch slot).
 constexpr int kGemmErrorSlot = 16;
