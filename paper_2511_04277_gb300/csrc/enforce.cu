@@ -64,14 +64,13 @@ struct EnforceState {
   int32_t pad;
 };
 
-// T: tile edge; kW: weights from kappa [n][n] (kappa_ij multiplies eta_ij), else 1/2.
+// Symmetrisation of the tile pair (I, J), I <= J (one block): T is the tile edge; kW:
+// weights from kappa [n][n] (kappa_ij multiplies eta_ij), else 1/2. Folds the block's
+// largest reciprocity defect into *d_recip.
 template <int T, bool kW>
-__global__ void __launch_bounds__(kThreads) sym_pass(double* __restrict__ H, const double* __restrict__ s,
-                                                     const double* __restrict__ kappa, int32_t n,
-                                                     double* __restrict__ P, EnforceState* st) {
-  if (st->done) return;
-  const int I = blockIdx.y, J = blockIdx.x;
-  if (I > J) return;
+__device__ __forceinline__ void sym_tile(double* __restrict__ H, const double* __restrict__ s,
+                                         const double* __restrict__ kappa, int32_t n, double* __restrict__ P, int I,
+                                         int J, unsigned long long* d_recip) {
   __shared__ double A[T][T + 1];
   __shared__ double B[T][T + 1];
   __shared__ double red[kThreads];
@@ -81,10 +80,10 @@ __global__ void __launch_bounds__(kThreads) sym_pass(double* __restrict__ H, con
   for (int e = tid; e < T * T; e += kThreads) {
     int r = e / T, c = e % T;
     int64_t i = (int64_t)I * T + r, j = (int64_t)J * T + c;
-    A[r][c] = (i < n && j < n) ? s[i] * H[i * ld + j] : 0.0;
+    A[r][c] = (i < n && j < n) ? __ldcg(s + i) * H[i * ld + j] : 0.0;
     if (off) {
       int64_t i2 = (int64_t)J * T + r, j2 = (int64_t)I * T + c;
-      B[r][c] = (i2 < n && j2 < n) ? s[i2] * H[i2 * ld + j2] : 0.0;
+      B[r][c] = (i2 < n && j2 < n) ? __ldcg(s + i2) * H[i2 * ld + j2] : 0.0;
     }
   }
   __syncthreads();
@@ -136,7 +135,134 @@ __global__ void __launch_bounds__(kThreads) sym_pass(double* __restrict__ H, con
     if (tid < w) red[tid] = fmax(red[tid], red[tid + w]);
     __syncthreads();
   }
-  if (tid == 0) atomicMax(&st->d_recip, (unsigned long long)__double_as_longlong(red[0]));
+  if (tid == 0) atomicMax(d_recip, (unsigned long long)__double_as_longlong(red[0]));
+  __syncthreads();  // the tiles are reused by the block's next pair
+}
+
+template <int T, bool kW>
+__global__ void __launch_bounds__(kThreads) sym_pass(double* __restrict__ H, const double* __restrict__ s,
+                                                     const double* __restrict__ kappa, int32_t n,
+                                                     double* __restrict__ P, EnforceState* st) {
+  if (st->done) return;
+  const int I = blockIdx.y, J = blockIdx.x;
+  if (I > J) return;
+  sym_tile<T, kW>(H, s, kappa, n, P, I, J, &st->d_recip);
+}
+
+// ---------------------------------------------------------------- persistent enforcer
+// All iterations in one cooperative launch (every block resident): per iteration the
+// blocks share the tile pairs (sym_tile), meet at a grid barrier, share the rows (the
+// row_pass step), meet again and apply the stop rule, each block reaching the same
+// decision. The defect accumulators alternate by iteration parity, so the ones an
+// iteration reads are never reset under it. Every block owns the same tile pairs and
+// rows in every iteration; what crosses blocks (row scales, per-tile row sums) is read
+// through L2 (__ldcg), never from a block's L1.
+struct PersistState {
+  unsigned long long d_recip[2], d_close[2];
+  int32_t bad[2];
+  unsigned int arrive, gen;
+  int32_t done, iters, timeout, pad;
+};
+
+constexpr unsigned long long kBarrierNs = 2000000000ull;  // a barrier wait gives up after 2 s
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Grid-wide barrier of a cooperative launch; false (and st->timeout set) if the wait
+// exceeded kBarrierNs, after which the caller's block returns.
+__device__ bool grid_barrier(PersistState* st, int* s_ok) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned int* gen = &st->gen;
+    const unsigned int g = *gen;
+    __threadfence();
+    int ok = 1;
+    if (atomicAdd(&st->arrive, 1u) + 1u == gridDim.x) {
+      st->arrive = 0u;
+      __threadfence();
+      atomicAdd(&st->gen, 1u);
+    } else {
+      const unsigned long long t0 = global_ns();
+      for (unsigned int it = 1; *gen == g; ++it) {
+        if ((it & 255u) == 0 && global_ns() - t0 > kBarrierNs) {
+          ok = 0;
+          atomicExch(&st->timeout, 1);
+          break;
+        }
+      }
+    }
+    __threadfence();
+    *s_ok = ok;
+  }
+  __syncthreads();
+  return *s_ok != 0;
+}
+
+template <int T, bool kW>
+__global__ void __launch_bounds__(kThreads) enforce_persistent(double* __restrict__ H, double* __restrict__ s,
+                                                               const double* __restrict__ kappa,
+                                                               const double* __restrict__ omega, int32_t n,
+                                                               int32_t n_tiles, double* __restrict__ P,
+                                                               PersistState* st, double tol_abs, int32_t maxit) {
+  __shared__ double red[kThreads];
+  __shared__ int s_ok;
+  const int n_pairs = n_tiles * (n_tiles + 1) / 2;
+  const int64_t ld = n + 1;
+  for (int k = 0;; ++k) {
+    const int par = k & 1;
+    // (1) reciprocity on the tile pairs (I, J), I <= J, numbered row by row
+    for (int p = blockIdx.x; p < n_pairs; p += gridDim.x) {
+      int I = 0, q = p;
+      while (q >= n_tiles - I) {
+        q -= n_tiles - I;
+        ++I;
+      }
+      sym_tile<T, kW>(H, s, kappa, n, P, I, I + q, &st->d_recip[par]);
+    }
+    if (!grid_barrier(st, &s_ok)) return;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {  // last read before the barrier just passed
+      st->d_recip[par ^ 1] = 0ull;
+      st->d_close[par ^ 1] = 0ull;
+      st->bad[par ^ 1] = 0;
+    }
+    // (2) environment column carried over, closure by row scaling
+    double dc = 0.0;
+    bool bad = false;
+    for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kThreads) {
+      const double env = s[i] * H[i * ld + n];
+      H[i * ld + n] = env;
+      double r = 0.0;
+      for (int J = 0; J < n_tiles; ++J) r += __ldcg(P + (int64_t)J * n + i);  // written by other blocks
+      r += env;
+      dc = fmax(dc, fabs(r - omega[i]));
+      s[i] = (r > 0.0) ? omega[i] / r : 1.0;
+      bad |= !isfinite(r);
+    }
+    red[threadIdx.x] = dc;
+    if (__syncthreads_or(bad) && threadIdx.x == 0) atomicExch(&st->bad[par], 1);
+    for (int w = kThreads / 2; w > 0; w >>= 1) {
+      if (threadIdx.x < w) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + w]);
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) atomicMax(&st->d_close[par], (unsigned long long)__double_as_longlong(red[0]));
+    if (!grid_barrier(st, &s_ok)) return;
+    // (3) stop rule on this iteration's defects
+    volatile PersistState* v = st;
+    const double dr = __longlong_as_double((long long)v->d_recip[par]);
+    const double dcl = __longlong_as_double((long long)v->d_close[par]);
+    const int done = v->bad[par] ? 3 : (fmax(dr, dcl) <= tol_abs ? 1 : (k + 1 >= maxit ? 2 : 0));
+    if (done) {
+      if (blockIdx.x == 0 && threadIdx.x == 0) {
+        st->done = done;
+        st->iters = k + 1;
+      }
+      return;
+    }
+  }
 }
 
 // kappa_ij (rg_kappa): matrix triangulation (Eq. 3.21-3.22) or fractional variance
@@ -324,6 +450,7 @@ rg_status enforce_iterative(rg_ctx* ctx, int32_t n, const double* omega_d, const
   sz.take<double>(n);                          // s
   sz.take<double>((size_t)n_tiles * n);        // P
   sz.take<EnforceState>(1);
+  sz.take<PersistState>(1);
   void* ws = nullptr;
   rg_status rs = rg::workspace(ctx, sz.off, &ws);
   if (rs != RG_OK) return rs;
@@ -331,6 +458,7 @@ rg_status enforce_iterative(rg_ctx* ctx, int32_t n, const double* omega_d, const
   double* sc = cv.take<double>(n);
   double* P = cv.take<double>((size_t)n_tiles * n);
   EnforceState* st = cv.take<EnforceState>(1);
+  PersistState* pst = cv.take<PersistState>(1);
   const int64_t total = (int64_t)n * (n + 1);
   RG_CUDA_TRY(ctx, cudaMemsetAsync(st, 0, sizeof(EnforceState), s));
   // tolerance scale: max Omega
@@ -347,7 +475,36 @@ rg_status enforce_iterative(rg_ctx* ctx, int32_t n, const double* omega_d, const
   dim3 sym_grid(n_tiles, n_tiles);
   const int row_blocks = (n + kThreads - 1) / kThreads;
   EnforceState h{};
-  for (int launched = 0; launched < maxit;) {
+  // one cooperative launch for all iterations (the two-kernel loop below is the same
+  // computation, kept for devices without cooperative launches)
+  int coop = 0;
+  RG_CUDA_TRY(ctx, cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, ctx->device));
+  if (coop) {
+    void (*kern)(double*, double*, const double*, const double*, int32_t, int32_t, double*, PersistState*, double,
+                 int32_t);
+    if (tile == kTSmall) kern = kappa_d ? enforce_persistent<kTSmall, true> : enforce_persistent<kTSmall, false>;
+    else kern = kappa_d ? enforce_persistent<kT, true> : enforce_persistent<kT, false>;
+    int per_sm = 0;
+    RG_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, 0));
+    const int n_pairs = n_tiles * (n_tiles + 1) / 2;
+    const int grid = std::max(1, std::min(n_pairs, per_sm * ctx->sm_count));
+    RG_CUDA_TRY(ctx, cudaMemsetAsync(pst, 0, sizeof(PersistState), s));
+    int32_t nn = n, nt = n_tiles, mi = maxit;
+    double ta = tol_abs;
+    double* Fp = F_d;
+    const double* kp = kappa_d;
+    const double* op = omega_d;
+    void* args[] = {&Fp, &sc, &kp, &op, &nn, &nt, &P, &pst, &ta, &mi};
+    RG_CUDA_TRY(ctx, cudaLaunchCooperativeKernel((const void*)kern, dim3(grid), dim3(kThreads), args, 0, s));
+    ++ctx->launches;
+    PersistState hp{};
+    RG_CUDA_TRY(ctx, cudaMemcpyAsync(&hp, pst, sizeof(PersistState), cudaMemcpyDeviceToHost, s));
+    RG_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+    if (hp.timeout) return rg::fail(ctx, RG_ERR_CUDA, "rg_enforce_iterative: a grid barrier timed out");
+    h.done = hp.done;
+    h.iters = hp.iters;
+  }
+  for (int launched = 0; !coop && launched < maxit;) {
     int batch = std::min(8, maxit - launched);
     for (int b = 0; b < batch; ++b) {
       if (tile == kTSmall) {
