@@ -347,6 +347,22 @@ rg_status rg_tc_gemm_residual(rg_ctx* ctx, int32_t M, int32_t N, int32_t K, cons
                               const double* E_d, const double* X_d, const double* dl_d, int64_t ld,
                               void* stream);
 
+/* ---------------------------------------------------------------- failure-detection checks */
+
+/* Test support with no counterpart in the thesis: each runs one of the library's bounded
+ * device waits against a flag that nothing sets, so that the wait runs out after
+ * limit_s seconds (0 < limit_s <= 2), and returns the status a real timeout produces.
+ *   rg_debug_mbarrier_timeout  the mbarrier wait of the tensor-core GEMM (one block waits
+ *                              on a barrier no one arrives on);
+ *   rg_debug_barrier_timeout   the grid barrier of the persistent iterative enforcer (a
+ *                              cooperative launch of two blocks, one of which never
+ *                              arrives).
+ * Expected result: RG_ERR_CUDA with rg_last_error naming the timeout; the kernel ends
+ * on its own, nothing traps, and the context stays usable. RG_OK means the wait did
+ * not run out (a defect). */
+rg_status rg_debug_mbarrier_timeout(rg_ctx* ctx, double limit_s, void* stream);
+rg_status rg_debug_barrier_timeout(rg_ctx* ctx, double limit_s, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -46,6 +46,8 @@ SIGNATURES = {
     "rg_enforce_iterative_kappa": (i32, [P, i32, P, P, P, f64, i32, P, P]),
     "rg_kappa": (i32, [P, i32, i32, P, P, P, f64, P, P]),
     "rg_trace_reflect": (i32, [P, P, P, P, P, i32, u64, u64, i32, P, P, P]),
+    "rg_debug_mbarrier_timeout": (i32, [P, f64, P]),
+    "rg_debug_barrier_timeout": (i32, [P, f64, P]),
     "rg_enforce_lsq": (i32, [P, i32, P, P, i32, i32, i32, P, P]),
     "rg_aggregate": (i32, [P, i32, P, P, P, i32, P, P, P]),
     "rg_gebhart": (i32, [P, i32, P, i32, P, P, i32, f64, i32, P, P, P, P]),

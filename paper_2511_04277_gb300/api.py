@@ -324,6 +324,13 @@ def temperatures_adjoint(ctx: Context, B, eps, area, T_sink: float, T, dT, sigma
     return dB, deps
 
 
+def debug_wait_timeout(ctx: Context, kind: str, limit_s: float = 0.01, stream=None):
+    """Run one bounded device wait against a flag nothing sets (rg_debug_*_timeout);
+    raises RadgebError(RG_ERR_CUDA) when the wait runs out, as it should."""
+    fn = {"mbarrier": ctx.lib.rg_debug_mbarrier_timeout, "grid": ctx.lib.rg_debug_barrier_timeout}[kind]
+    ctx.check(fn(ctx.handle, float(limit_s), _stream(stream)), f"rg_debug_{kind}_timeout")
+
+
 def tc_gemm(ctx: Context, A: torch.Tensor, B: torch.Tensor, C: torch.Tensor | None = None, alpha: float = 1.0,
             beta: float = 0.0, stream=None) -> torch.Tensor:
     """C = alpha A B^T + beta C on tcgen05 (rg_tc_gemm); A [M, K], B [N, K] bf16 or fp16, C fp32."""

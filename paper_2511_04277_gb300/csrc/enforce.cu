@@ -173,8 +173,8 @@ __device__ __forceinline__ unsigned long long global_ns() {
 }
 
 // Grid-wide barrier of a cooperative launch; false (and st->timeout set) if the wait
-// exceeded kBarrierNs, after which the caller's block returns.
-__device__ bool grid_barrier(PersistState* st, int* s_ok) {
+// exceeded limit_ns, after which the caller's block returns.
+__device__ bool grid_barrier(PersistState* st, int* s_ok, unsigned long long limit_ns = kBarrierNs) {
   __syncthreads();
   if (threadIdx.x == 0) {
     volatile unsigned int* gen = &st->gen;
@@ -188,7 +188,7 @@ __device__ bool grid_barrier(PersistState* st, int* s_ok) {
     } else {
       const unsigned long long t0 = global_ns();
       for (unsigned int it = 1; *gen == g; ++it) {
-        if ((it & 255u) == 0 && global_ns() - t0 > kBarrierNs) {
+        if ((it & 255u) == 0 && global_ns() - t0 > limit_ns) {
           ok = 0;
           atomicExch(&st->timeout, 1);
           break;
@@ -263,6 +263,14 @@ __global__ void __launch_bounds__(kThreads) enforce_persistent(double* __restric
       return;
     }
   }
+}
+
+// Failure-detection check of the grid barrier: every block but block 0 waits at a barrier
+// that block 0 never reaches, so the wait runs out after limit_ns and sets st->timeout.
+__global__ void barrier_timeout_probe(PersistState* st, unsigned long long limit_ns) {
+  __shared__ int s_ok;
+  if (blockIdx.x == 0) return;
+  grid_barrier(st, &s_ok, limit_ns);
 }
 
 // kappa_ij (rg_kappa): matrix triangulation (Eq. 3.21-3.22) or fractional variance
@@ -547,6 +555,28 @@ rg_status rg_enforce_iterative_kappa(rg_ctx* ctx, int32_t n, const double* omega
   if (!ctx) return RG_ERR_ARG;
   RG_ARG_CHECK(ctx, kappa_d != nullptr, "rg_enforce_iterative_kappa: NULL kappa");
   return enforce_iterative(ctx, n, omega_d, kappa_d, F_d, tol, maxit, iters_out_h, stream);
+}
+
+rg_status rg_debug_barrier_timeout(rg_ctx* ctx, double limit_s, void* stream) {
+  if (!ctx) return RG_ERR_ARG;
+  RG_ARG_CHECK(ctx, limit_s > 0.0 && limit_s <= 2.0, "rg_debug_wait_timeout: limit %.3g s outside (0, 2]", limit_s);
+  RG_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+  cudaStream_t s = (cudaStream_t)stream;
+  void* ws = nullptr;
+  rg_status rs = rg::workspace(ctx, sizeof(PersistState), &ws);
+  if (rs != RG_OK) return rs;
+  PersistState* st = static_cast<PersistState*>(ws);
+  RG_CUDA_TRY(ctx, cudaMemsetAsync(st, 0, sizeof(PersistState), s));
+  unsigned long long lim = (unsigned long long)(limit_s * 1e9);
+  void* args[] = {&st, &lim};
+  // two co-resident blocks (a cooperative launch): block 1 waits for block 0, which returns
+  RG_CUDA_TRY(ctx, cudaLaunchCooperativeKernel((const void*)barrier_timeout_probe, dim3(2), dim3(32), args, 0, s));
+  ++ctx->launches;
+  PersistState h{};
+  RG_CUDA_TRY(ctx, cudaMemcpyAsync(&h, st, sizeof(PersistState), cudaMemcpyDeviceToHost, s));
+  RG_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+  if (h.timeout) return rg::fail(ctx, RG_ERR_CUDA, "grid barrier timed out after %.3g s", limit_s);
+  return RG_OK;
 }
 
 rg_status rg_kappa(rg_ctx* ctx, int32_t n, int32_t mode, const double* F_d, const int64_t* rays_d,

@@ -174,6 +174,17 @@ __global__ void residual_finish(const double* __restrict__ partial, int64_t stri
 
 }  // namespace
 
+// Failure-detection check of the GEMM's mbarrier wait: a barrier nobody arrives on.
+__global__ void mbarrier_timeout_probe(int* error_word, unsigned long long limit_ns) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && !mbar_wait(&bar, 0, limit_ns)) atomicExch(error_word, 1);
+}
+
 int residual_splits(const rg_ctx* ctx, int M, int N, int K, int chunk_blocks, int split_max) {
   const int tiles = ((M + BM - 1) / BM) * ((N + 63) / 64);
   const int kb = (K + BK - 1) / BK;
@@ -223,6 +234,23 @@ rg_status gemm_residual(rg_ctx* ctx, const void* A, int64_t lda, const void* B, 
 }  // namespace tc
 
 extern "C" {
+
+rg_status rg_debug_mbarrier_timeout(rg_ctx* ctx, double limit_s, void* stream) {
+  if (!ctx) return RG_ERR_ARG;
+  RG_ARG_CHECK(ctx, limit_s > 0.0 && limit_s <= 2.0, "rg_debug_wait_timeout: limit %.3g s outside (0, 2]", limit_s);
+  RG_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+  cudaStream_t s = (cudaStream_t)stream;
+  RG_CUDA_TRY(ctx, cudaMemsetAsync(ctx->d_scratch + tc::kGemmErrorSlot, 0, sizeof(int), s));
+  tc::mbarrier_timeout_probe<<<1, 32, 0, s>>>(ctx->d_scratch + tc::kGemmErrorSlot,
+                                              (unsigned long long)(limit_s * 1e9));
+  ++ctx->launches;
+  RG_CUDA_TRY(ctx, cudaGetLastError());
+  int h = 0;
+  RG_CUDA_TRY(ctx, cudaMemcpyAsync(&h, ctx->d_scratch + tc::kGemmErrorSlot, sizeof(int), cudaMemcpyDeviceToHost, s));
+  RG_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+  if (h) return rg::fail(ctx, RG_ERR_CUDA, "mbarrier wait timed out after %.3g s", limit_s);
+  return RG_OK;
+}
 
 rg_status rg_tc_gemm(rg_ctx* ctx, int32_t M, int32_t N, int32_t K, const void* A_d, int64_t lda, const void* B_d,
                      int64_t ldb, int32_t fp16, float* C_d, int64_t ldc, float alpha, float beta, void* stream) {

@@ -49,8 +49,8 @@ __device__ __forceinline__ uint64_t global_ns() {
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
   return t;
 }
-// Wait for the phase with the given parity to complete; false after kWaitNs.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+// Wait for the phase with the given parity to complete; false after limit_ns.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint64_t limit_ns = kWaitNs) {
   uint32_t addr = smem_u32(bar);
   uint64_t t0 = 0;
   for (uint32_t i = 1;; ++i) {
@@ -64,7 +64,7 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
     if ((i & 255u) == 0) {
       uint64_t now = global_ns();
       if (t0 == 0) t0 = now;
-      else if (now - t0 > kWaitNs) return false;
+      else if (now - t0 > limit_ns) return false;
     }
   }
 }
