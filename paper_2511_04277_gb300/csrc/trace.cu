@@ -115,6 +115,11 @@ __device__ __forceinline__ float sym24(uint32_t x) {
   return __fsub_rn(__uint2float_rn(x >> 8) * 1.1920928955078125e-07f, 1.0f);  // exact: 2u - 1
 }
 
+// Every quantity is computed whatever the outcome and the hit is one predicate at the
+// end: the lanes of a warp testing different triangles then stay converged (a miss found
+// early saves no warp instruction while another lane still tests). The arithmetic is
+// that of the early-exit form, so the hits are the same; det = 0 gives inv = inf and
+// NaN or infinite u, v, t, which fail their tests.
 template <bool E>
 __device__ __forceinline__ bool moller_trumbore(const float4 r0, const float4 r1, const float4 r2, V3 o, V3 d,
                                                 float* t_out) {
@@ -122,19 +127,15 @@ __device__ __forceinline__ bool moller_trumbore(const float4 r0, const float4 r1
   const float lo = -9.5367431640625e-07f, hi = 1.00000095367431640625f;  // -2^-20, 1 + 2^-20
   V3 v0{r0.x, r0.y, r0.z}, e1{r0.w, r1.x, r1.y}, e2{r1.z, r1.w, r2.x};
   V3 p = cross3<E>(d, e2);
-  float det = dot3<E>(e1, p);
-  if (det == 0.0f) return false;
-  float inv = __frcp_rn(det);
+  const float det = dot3<E>(e1, p);
+  const float inv = __frcp_rn(det);
   V3 tv{A::sub(o.x, v0.x), A::sub(o.y, v0.y), A::sub(o.z, v0.z)};
-  float u = A::mul(dot3<E>(tv, p), inv);
-  if (!(u >= lo && u <= hi)) return false;
+  const float u = A::mul(dot3<E>(tv, p), inv);
   V3 q = cross3<E>(tv, e1);
-  float v = A::mul(dot3<E>(d, q), inv);
-  if (!(v >= lo && A::add(u, v) <= hi)) return false;
-  float t = A::mul(dot3<E>(e2, q), inv);
-  if (!(t > 0.0f)) return false;
+  const float v = A::mul(dot3<E>(d, q), inv);
+  const float t = A::mul(dot3<E>(e2, q), inv);
   *t_out = t;
-  return true;
+  return det != 0.0f && u >= lo && u <= hi && v >= lo && A::add(u, v) <= hi && t > 0.0f;
 }
 
 struct NoStats {
@@ -152,10 +153,9 @@ __device__ __forceinline__ void test_record(const float4* __restrict__ rec, int3
                                             int32_t& best_id, int32_t& best_face) {
   float4 r0 = __ldg(rec), r1 = __ldg(rec + 1), r2 = __ldg(rec + 2);
   int32_t id = __float_as_int(r2.y);
-  if (id == src) return;
   float t;
-  if (!moller_trumbore<E>(r0, r1, r2, o, d, &t)) return;
-  if (t < best_t || (t == best_t && id < best_id)) {
+  const bool hit = moller_trumbore<E>(r0, r1, r2, o, d, &t) && id != src;
+  if (hit && (t < best_t || (t == best_t && id < best_id))) {
     best_t = t;
     best_id = id;
     best_face = __float_as_int(r2.z);
@@ -357,8 +357,21 @@ __device__ __forceinline__ bool visit(const DevMesh& m, Walker& w, int32_t* stac
               fmaf(c.z, w.iz, -oz), fmaf(c.w, w.iz, -oz), m.t_lo, limit, rmin, rmax);
   bool hl = lmin <= lmax, hr = rmin <= rmax;
   st.box(2);
-  if (hl && cntL > 0) { test_leaf<E>(m, w, refL, cntL, st); hl = false; }
-  if (hr && cntR > 0) { test_leaf<E>(m, w, refR, cntR, st); hr = false; }
+  // the hit leaf children, tested through one loop so that lanes at different leaves
+  // run the same instructions: records [r0, r0 + c0) then [r1, r1 + c1), nearer first
+  {
+    const bool ll = hl && cntL > 0, lr = hr && cntR > 0;
+    const bool right_first = lr && (!ll || rmin < lmin);
+    const int32_t r0 = right_first ? refR : refL, c0 = right_first ? (lr ? cntR : 0) : (ll ? cntL : 0);
+    const int32_t r1 = right_first ? refL : refR, c1 = right_first ? (ll ? cntL : 0) : (lr ? cntR : 0);
+    for (int q = 0; q < c0 + c1; ++q) {
+      const int32_t rec = q < c0 ? r0 + q : r1 + (q - c0);
+      test_record<E>(m.tris + 3 * (int64_t)rec, w.src, w.o, w.d, w.best_t, w.best_id, w.best_face);
+      st.tri();
+    }
+    if (ll) hl = false;
+    if (lr) hr = false;
+  }
   if (hl && hr) {
     const bool left_first = lmin <= rmin;
     if (w.sp >= kTraceStack) { *overflow = true; return false; }
