@@ -581,17 +581,19 @@ __global__ void __launch_bounds__(kThreads, RG_LOCKSTEP_MIN_BLOCKS) trace_kernel
       int32_t face = m.n_faces;
       if (valid) {
         if (kBVH) {
-          Walker w;
-          w.o = o; w.d = d;
-          w.ix = rcp_approx(d.x); w.iy = rcp_approx(d.y); w.iz = rcp_approx(d.z);
-          w.src = src;
-          w.best_t = __int_as_float(0x7f800000);
-          w.best_id = INT_MAX;
-          w.best_face = m.n_faces;
-          w.node = 0;
-          w.sp = 0;
-          more = visit<E>(m, w, stack, &overflow, st);
-          face = w.best_face;
+          // escape test: does the ray enter either child box of the root? Rays that do
+          // are traced from the root by drain(); the others leave the scene.
+          const float ix = rcp_approx(d.x), iy = rcp_approx(d.y), iz = rcp_approx(d.z);
+          const float ox = o.x * ix, oy = o.y * iy, oz = o.z * iz;
+          const float4 a = __ldg(m.nodes), b = __ldg(m.nodes + 1), c = __ldg(m.nodes + 2);
+          const float lim = __int_as_float(0x7f800000);
+          float lmin, lmax, rmin, rmax;
+          slab_window(fmaf(a.x, ix, -ox), fmaf(a.y, ix, -ox), fmaf(a.z, iy, -oy), fmaf(a.w, iy, -oy),
+                      fmaf(c.x, iz, -oz), fmaf(c.y, iz, -oz), m.t_lo, lim, lmin, lmax);
+          slab_window(fmaf(b.x, ix, -ox), fmaf(b.y, ix, -ox), fmaf(b.z, iy, -oy), fmaf(b.w, iy, -oy),
+                      fmaf(c.z, iz, -oz), fmaf(c.w, iz, -oz), m.t_lo, lim, rmin, rmax);
+          st.box(2);
+          more = lmin <= lmax || rmin <= rmax;
         } else {
           face = closest_face<E, false>(m, src, o, d, &overflow, st);
         }
