@@ -30,9 +30,11 @@
 
 #include "mesh.cuh"
 
-// Resident blocks per SM the two schedules are compiled for (register caps).
+// Resident blocks per SM the two schedules are compiled for (register caps: 3 blocks of
+// 256 threads allow 85 registers, 4 allow 64). Measured on GB300: the lock-step kernel
+// runs 2.6 % faster with 3 (no spills), the refill kernel 3 % faster with 4.
 #ifndef RG_LOCKSTEP_MIN_BLOCKS
-#define RG_LOCKSTEP_MIN_BLOCKS 4
+#define RG_LOCKSTEP_MIN_BLOCKS 3
 #endif
 #ifndef RG_REFILL_MIN_BLOCKS
 #define RG_REFILL_MIN_BLOCKS 4
