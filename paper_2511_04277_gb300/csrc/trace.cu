@@ -600,7 +600,14 @@ __global__ void __launch_bounds__(kThreads, RG_LOCKSTEP_MIN_BLOCKS) trace_kernel
           face = closest_face<E, false>(m, src, o, d, &overflow, st);
         }
       }
-      tally(valid && !more, face);
+      if (kBVH) {
+        // with a BVH every ray finished here left the scene: one count for all of them
+        const unsigned esc = __ballot_sync(0xffffffffu, valid && !more);
+        if (lane == 0 && esc) atomicAdd(&hist[m.n_faces], (uint32_t)__popc(esc));
+        if (valid && !more) ++n_rays;
+      } else {
+        tally(valid && !more, face);
+      }
       // queue the rays that need more visits; they restart from the root
       const unsigned sm = __ballot_sync(0xffffffffu, more);
       if (more) {
