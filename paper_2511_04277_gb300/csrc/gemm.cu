@@ -121,18 +121,19 @@ namespace {
 
 // out = E - X + dl o (sum_z partial[z]) (or dl o sum when E is null), the sum over the K
 // splits in order z = 0, 1, ...; with red: max|out| -> red[0], max|X| -> red[1], column
-// maxima of out -> colmax, inf / NaN -> *nonfinite. Block (32 x 8) per 32 columns x 64 rows.
+// maxima of out -> colmax, inf / NaN -> *nonfinite. Block (32 x 8) per 32 columns x 16 rows
+// (two rows per thread: many small blocks keep the independent loads in flight).
 __global__ void residual_finish(const double* __restrict__ partial, int64_t stride, int splits, int M, int N,
                                 int64_t ld, double* __restrict__ out, const double* __restrict__ E,
                                 const double* __restrict__ X, const double* __restrict__ dl, unsigned long long* red,
                                 unsigned long long* colmax, int* nonfinite) {
   __shared__ double s_out[8][33], s_x[8][33];
   const int c = blockIdx.x * 32 + threadIdx.x;
-  const int r0 = blockIdx.y * 64;
+  const int r0 = blockIdx.y * 16;
   double m_out = 0.0, m_x = 0.0;
   bool bad = false;
   if (c < N) {
-    for (int r = r0 + threadIdx.y; r < min(M, r0 + 64); r += 8) {
+    for (int r = r0 + threadIdx.y; r < min(M, r0 + 16); r += 8) {
       const int64_t i = (int64_t)r * ld + c;
       double acc = 0.0;
       for (int z = 0; z < splits; ++z) acc += partial[(int64_t)z * stride + i];
@@ -223,7 +224,7 @@ rg_status gemm_residual(rg_ctx* ctx, const void* A, int64_t lda, const void* B, 
   epi.split_stride = stride;
   st = launch<BN, 6, EpiResidual, true, true>(ctx, ma, mb, args, epi, s, splits);
   if (st != RG_OK) return st;
-  dim3 grid((N + 31) / 32, (M + 63) / 64);
+  dim3 grid((N + 31) / 32, (M + 15) / 16);
   residual_finish<<<grid, dim3(32, 8), 0, s>>>(split_ws, stride, splits, M, N, ld, out, E, X, dl, red, colmax,
                                                nonfinite);
   ++ctx->launches;
