@@ -93,7 +93,7 @@ rg_status launch(rg_ctx* ctx, const CUtensorMap& ma, const CUtensorMap& mb, cons
     RG_CUDA_TRY(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     configured_device = ctx->device;
   }
-  dim3 grid((args.N + BN - 1) / BN, (args.M + BM - 1) / BM, grid_z);
+  dim3 grid(((args.N + BN - 1) / BN) * ((args.M + BM - 1) / BM), 1, grid_z);
   kern<<<grid, kThreads, smem, s>>>(ma, mb, args, epi);
   ++ctx->launches;
   RG_CUDA_TRY(ctx, cudaGetLastError());

@@ -30,6 +30,7 @@ namespace tc {
 constexpr int BM = 128;
 constexpr int BK = 64;  // one 128-byte swizzle atom of 16-bit elements
 constexpr int kThreads = 192;
+constexpr int kGroupM = 8;  // row tiles per rasterisation group
 constexpr uint64_t kWaitNs = 2000000000ull;  // a wait gives up after 2 s
 
 // ------------------------------------------------------------------ PTX wrappers
@@ -368,7 +369,16 @@ __global__ void __launch_bounds__(kThreads, 1)
   __shared__ StageT s_stage[4][32][33];  // per epilogue warp: coalescing block
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+  // grouped rasterisation of the 1-D grid: kGroupM row tiles at a time, column tiles
+  // innermost, so that the CTAs resident together share their A and B tiles in L2
+  const int tiles_m = (args.M + BM - 1) / BM, tiles_n = (args.N + BN - 1) / BN;
+  const int pid = blockIdx.x;
+  const int group = pid / (kGroupM * tiles_n);
+  const int first_m = group * kGroupM;
+  const int group_m = min(tiles_m - first_m, kGroupM);
+  const int tile_m = first_m + (pid % (kGroupM * tiles_n)) % group_m;
+  const int tile_n = (pid % (kGroupM * tiles_n)) / group_m;
+  const int m0 = tile_m * BM, n0 = tile_n * BN;
   const int kb_all = (args.K + BK - 1) / BK;
   // split K: this CTA's K blocks are kb_first .. kb_first + kb_total - 1
   const int kb_first = args.split_blocks > 0 ? blockIdx.z * args.split_blocks : 0;
