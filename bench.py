@@ -570,7 +570,8 @@ def solve_scaling(args):
         A = torch.randn(M, K, generator=g).to(torch.bfloat16).to(dev)
         B = torch.randn(N, K, generator=g).to(torch.bfloat16).to(dev)
         ms = ev(lambda: api.tc_gemm_residual(ctx, A, B, chunk_k=128), 3)
-        out["gemm"].append({"op": "refinement residual (6 slice pairs, compensated fp32 chunks)", "M": M, "N": N,
+        out["gemm"].append({"op": "rg_tc_gemm_residual: 6 slice pairs, compensated fp32 chunks of 128 K throughout "
+                                  "(the solver's own residual uses such chunks for the leading pair only)", "M": M, "N": N,
                             "K": K, "ms": round(ms, 3), "tflops": round(2 * M * N * K / ms / 1e9, 1)})
         del A, B
     torch.cuda.empty_cache()

@@ -202,7 +202,7 @@ int residual_splits(const rg_ctx* ctx, int M, int N, int K, int chunk_blocks, in
 rg_status gemm_residual(rg_ctx* ctx, const void* A, int64_t lda, const void* B, int64_t ldb, int M, int N, int K,
                         int chunk_blocks, double* out, const double* E, const double* X, const double* dl,
                         int64_t ld, cudaStream_t s, unsigned long long* red, unsigned long long* colmax,
-                        int* nonfinite, double* split_ws, int split_max) {
+                        int* nonfinite, double* split_ws, int split_max, int lead_blocks, int tail_chunk_blocks) {
   if (M <= 0 || N <= 0) return RG_OK;
   if (K <= 0) return rg::fail(ctx, RG_ERR_ARG, "gemm_residual: K = %d", K);
   constexpr int BN = 64;
@@ -213,6 +213,10 @@ rg_status gemm_residual(rg_ctx* ctx, const void* A, int64_t lda, const void* B, 
   GemmArgs args{M, N, K, chunk_blocks, ctx->d_scratch + kGemmErrorSlot};
   const int splits = split_ws ? residual_splits(ctx, M, N, K, chunk_blocks, split_max) : 1;
   if (splits <= 1) {
+    if (lead_blocks > 0 && tail_chunk_blocks > 0 && chunk_blocks > 0 && lead_blocks % chunk_blocks == 0) {
+      args.lead_blocks = lead_blocks;
+      args.tail_chunk_blocks = tail_chunk_blocks;
+    }
     EpiResidual epi{out, E, X, dl, ld, red, colmax, nonfinite};
     return launch<BN, 6, EpiResidual, true, true>(ctx, ma, mb, args, epi, s, 1);
   }

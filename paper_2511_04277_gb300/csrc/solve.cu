@@ -34,7 +34,8 @@ namespace {
 
 constexpr int NB = 128;          // panel width == GEMM tile height
 constexpr int kSlices = 6;       // slice pairs of the refinement product
-constexpr int kResidualChunk = 2;  // K blocks (of 64) per compensated fp32 chunk
+constexpr int kResidualChunk = 2;  // K blocks (of 64) per compensated fp32 chunk (leading pair)
+constexpr int kResidualTailChunk = 16;  // K blocks per chunk for the pairs after the leading one
 constexpr int kThreads = 256;
 // Below this relative residual a sweep that no longer halves it ends the refinement.
 // The residual product's own accuracy floor (fp32 accumulation inside each 128-long
@@ -384,7 +385,7 @@ struct Solver {
     RG_CUDA_TRY(ctx, cudaMemsetAsync(b.colmax, 0, (size_t)L.mp * sizeof(unsigned long long), s));
     rg_status st = tc::gemm_residual(ctx, b.Aext, (int64_t)kSlices * L.np, b.Bext, (int64_t)kSlices * L.np, L.n, L.m,
                                      pairs * L.np, kResidualChunk, b.R, b.R0, b.X, dl, L.mp, s, b.red, b.colmax,
-                                     err + 1, b.split, L.splits);
+                                     err + 1, b.split, L.splits, L.np / tc::BK, kResidualTailChunk);
     if (st != RG_OK) return st;
     // max|R|, max|X| and the error words in one pinned read-back and one wait
     int* hs = ctx->h_scratch;
@@ -822,7 +823,7 @@ rg_status rg_gebhart_adjoint(rg_ctx* ctx, int32_t n, const double* F_d, int32_t 
     RG_CUDA_TRY(ctx, cudaGetLastError());
     st = tc::gemm_residual(ctx, sv.b.Aext, (int64_t)kSlices * sv.L.np, sv.b.Bext, (int64_t)kSlices * sv.L.np, n,
                            n + 1, kSlices * sv.L.np, kResidualChunk, sv.b.R, nullptr, nullptr, nullptr, sv.L.mp, s,
-                           nullptr, nullptr, nullptr, sv.b.split, sv.L.splits);
+                           nullptr, nullptr, nullptr, sv.b.split, sv.L.splits, sv.L.np / tc::BK, kResidualTailChunk);
     if (st != RG_OK) return st;
     grad_rho<<<(n + 7) / 8, 256, 0, s>>>(B_d + off, sv.b.R, sv.L.mp, n, drho_d + (size_t)set * n);
     ++ctx->launches;

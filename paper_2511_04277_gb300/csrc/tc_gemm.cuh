@@ -341,6 +341,10 @@ struct GemmArgs {
   int chunk_blocks;  // 0: one fp32 accumulation over all of K; > 0: compensated chunks
   int* error_word;
   int split_blocks = 0;  // > 0: CTA z covers K blocks [z * split_blocks, (z + 1) * split_blocks)
+  // > 0 (compensated, unsplit): only the first lead_blocks K blocks use chunks of
+  // chunk_blocks; the rest use chunks of tail_chunk_blocks
+  int lead_blocks = 0;
+  int tail_chunk_blocks = 0;
 };
 
 template <int BN, int kStages, class Epi, bool kCompensated, bool kBF16>
@@ -384,7 +388,12 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int kb_first = args.split_blocks > 0 ? blockIdx.z * args.split_blocks : 0;
   const int kb_total = args.split_blocks > 0 ? min(args.split_blocks, kb_all - kb_first) : kb_all;
   const int chunk = (kCompensated && args.chunk_blocks > 0) ? args.chunk_blocks : kb_total;
-  const int n_chunks = (kb_total + chunk - 1) / chunk;
+  // chunk schedule: n_lead chunks of `chunk` K blocks, then chunks of `tail` blocks
+  const bool two_part = kCompensated && args.chunk_blocks > 0 && args.lead_blocks > 0 &&
+                        args.tail_chunk_blocks > 0 && args.lead_blocks < kb_total;
+  const int n_lead = two_part ? args.lead_blocks / chunk : 0;
+  const int tail = two_part ? args.tail_chunk_blocks : chunk;
+  const int n_chunks = n_lead + (kb_total - n_lead * chunk + tail - 1) / tail;
 
   if (threadIdx.x == 0) {
     s_abort = 0;
@@ -434,7 +443,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int b = c & 1;
         if (c >= 2 && !mbar_wait(&acc_empty[b], ((c >> 1) - 1) & 1)) { *abort_flag = 1; break; }
         const uint32_t d_tmem = tmem_base + (uint32_t)(b * BN);
-        const int first = kb, kb_end = min(kb_total, kb + chunk);
+        const int first = kb, kb_end = min(kb_total, kb + (c < n_lead ? chunk : tail));
         for (; kb < kb_end; ++kb) {
           const int s = kb % kStages;
           if (!mbar_wait(&full[s], (kb / kStages) & 1)) { *abort_flag = 1; break; }
@@ -543,11 +552,16 @@ rg_status gemm_f32(rg_ctx* ctx, bool bf16, const void* A, int64_t lda, const voi
 // With split_ws (room for split_max x M x ld doubles) and too few 128 x 64 tiles to fill
 // the GPU, K is split over up to split_max CTAs per tile (in whole chunks); their sums go
 // to split_ws and one more kernel adds them in a fixed order and applies the epilogue.
+//
+// lead_blocks / tail_chunk_blocks (unsplit products only): after the first lead_blocks
+// K blocks the chunks grow to tail_chunk_blocks (the refinement residual's leading slice
+// pair needs the short compensated chunks; the pairs after it are 2^8 smaller and do with
+// long ones).
 rg_status gemm_residual(rg_ctx* ctx, const void* A, int64_t lda, const void* B, int64_t ldb, int M, int N, int K,
                         int chunk_blocks, double* out, const double* E, const double* X, const double* dl,
                         int64_t ld, cudaStream_t s, unsigned long long* red = nullptr,
                         unsigned long long* colmax = nullptr, int* nonfinite = nullptr, double* split_ws = nullptr,
-                        int split_max = 0);
+                        int split_max = 0, int lead_blocks = 0, int tail_chunk_blocks = 0);
 
 // K splits gemm_residual uses for an M x N product (1: none).
 int residual_splits(const rg_ctx* ctx, int M, int N, int K, int chunk_blocks, int split_max);
