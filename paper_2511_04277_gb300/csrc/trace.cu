@@ -361,8 +361,8 @@ __device__ __forceinline__ bool visit(const DevMesh& m, Walker& w, int32_t* stac
   st.box(2);
   // the hit leaf children, tested through one loop so that lanes at different leaves
   // run the same instructions: records [r0, r0 + c0) then [r1, r1 + c1), nearer first
-  {
-    const bool ll = hl && cntL > 0, lr = hr && cntR > 0;
+  const bool ll = hl && cntL > 0, lr = hr && cntR > 0;
+  if (ll || lr) {  // skipped by whole warps on the inner levels
     const bool right_first = lr && (!ll || rmin < lmin);
     const int32_t r0 = right_first ? refR : refL, c0 = right_first ? (lr ? cntR : 0) : (ll ? cntL : 0);
     const int32_t r1 = right_first ? refL : refR, c1 = right_first ? (ll ? cntL : 0) : (lr ? cntR : 0);
