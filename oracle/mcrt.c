@@ -52,6 +52,18 @@
  * with one uniform radiosity), so the walk estimates the same B as Gebhart's method
  * for the same faces. A path still reflecting after max_bounces counts as overflow.
  *
+ * Two-sided faces (Sec. 5.2.4-5.2.5, side-resolved factors F^{X->Y}): face f has side
+ * A, the side its normal n points to, and side B. Row 2f+X of the side-resolved count
+ * matrix [2N x (2N+1)] counts the rays emitted from side X of face f: the triangle and
+ * point draws of face f, the origin lifted along n_X and the direction
+ * (x*t + y*b_X) + z*n_X, with n_A = n, b_A = b, n_B = -n, b_B = -b, and counter word
+ * 2 = f for side A, f + 2^31 for side B. Side A's rays are thus exactly face f's rays
+ * of the one-sided definition above. A hit on triangle k lies on side A of its face
+ * when det > 0 in Moller-Trumbore (the ray runs against the triangle normal e1 x e2)
+ * and on side B when det < 0; it is counted in column 2g+Y, a miss in column 2N.
+ * This needs every triangle of a face wound like the face's first triangle:
+ * dot(e1 x e2, n) > 0 for each of them (checked).
+ *
  * Build: gcc -O2 -ffp-contract=off -fopenmp -fPIC -shared (no fast-math), so
  * every float operation is one IEEE-rounded operation.
  */
@@ -145,6 +157,7 @@ typedef struct {
   v3* fn; v3* ft; v3* fb;
   double* face_area;
   float lift;
+  int wound_like_face;  /* 1: every triangle's e1 x e2 points to its face's side A */
 } omesh;
 
 static double tri_area_d(const float* verts, const int32_t* t) {
@@ -217,6 +230,9 @@ static int omesh_init(omesh* m, const float* verts, int64_t nv, const int32_t* t
     v3 t = vnormalize(m->te1[k0]);
     m->fn[f] = n; m->ft[f] = t; m->fb[f] = vcross(n, t);
   }
+  m->wound_like_face = 1;
+  for (int64_t k = 0; k < nt; ++k)
+    if (!(vdot(vcross(m->te1[k], m->te2[k]), m->fn[tri_face[k]]) > 0.0f)) m->wound_like_face = 0;
   /* origin lift from the bounding box diagonal */
   double lo[3] = {verts[0], verts[1], verts[2]}, hi[3] = {verts[0], verts[1], verts[2]};
   for (int64_t i = 0; i < nv; ++i)
@@ -255,12 +271,13 @@ static void malley(uint64_t seed, uint64_t ray, uint32_t f, uint32_t base, float
   if (used_out) *used_out = used;
 }
 
-/* Emission from face f with the draws of counters (ray, stream, base + a): a = 0 for the
-   triangle and the point, a = 1..64 for the direction. Emission proper uses stream = f
-   and base = 0; a reflection of bounce b uses stream = the path's source face and
-   base = b*128. */
-static void emit_from(const omesh* m, uint64_t seed, int32_t f, uint32_t stream, uint32_t base, uint64_t ray,
-                      v3* o, v3* d, int32_t* src_tri, int32_t* attempts_used) {
+/* Emission from side `side` (0 = A, 1 = B) of face f with the draws of counters
+   (ray, stream, base + a): a = 0 for the triangle and the point, a = 1..64 for the
+   direction. Side B uses the frame (t, -b, -n). Emission proper uses stream = f (side A)
+   or f + 2^31 (side B) and base = 0; a reflection of bounce b uses stream = the path's
+   source face and base = b*128. */
+static void emit_side(const omesh* m, uint64_t seed, int32_t f, int side, uint32_t stream, uint32_t base,
+                      uint64_t ray, v3* o, v3* d, int32_t* src_tri, int32_t* attempts_used) {
   uint32_t x[4];
   draw(seed, ray, stream, base, x);
   int64_t s = m->face_start[f], e = m->face_start[f + 1];
@@ -279,6 +296,7 @@ static void emit_from(const omesh* m, uint64_t seed, int32_t f, uint32_t stream,
   p.y = v0.y + u * e1.y; p.y = p.y + v * e2.y;
   p.z = v0.z + u * e1.z; p.z = p.z + v * e2.z;
   v3 nf = m->fn[f];
+  if (side) { nf.x = -nf.x; nf.y = -nf.y; nf.z = -nf.z; }
   p.x = p.x + m->lift * nf.x;
   p.y = p.y + m->lift * nf.y;
   p.z = p.z + m->lift * nf.z;
@@ -286,13 +304,19 @@ static void emit_from(const omesh* m, uint64_t seed, int32_t f, uint32_t stream,
   float dx, dy, dz;
   int used = 0;
   malley(seed, ray, stream, base, &dx, &dy, &dz, &used);
-  v3 t = m->ft[f], b = m->fb[f], n = m->fn[f];
+  v3 t = m->ft[f], b = m->fb[f], n = nf;
+  if (side) { b.x = -b.x; b.y = -b.y; b.z = -b.z; }
   v3 dir;
   dir.x = dx * t.x + dy * b.x; dir.x = dir.x + dz * n.x;
   dir.y = dx * t.y + dy * b.y; dir.y = dir.y + dz * n.y;
   dir.z = dx * t.z + dy * b.z; dir.z = dir.z + dz * n.z;
   *o = p; *d = dir; *src_tri = tri;
   if (attempts_used) *attempts_used = used;
+}
+
+static void emit_from(const omesh* m, uint64_t seed, int32_t f, uint32_t stream, uint32_t base, uint64_t ray,
+                      v3* o, v3* d, int32_t* src_tri, int32_t* attempts_used) {
+  emit_side(m, seed, f, 0, stream, base, ray, o, d, src_tri, attempts_used);
 }
 
 static void sample_ray(const omesh* m, uint64_t seed, int32_t f, uint64_t ray, v3* o, v3* d,
@@ -319,6 +343,12 @@ static int intersect(const omesh* m, int32_t k, v3 o, v3 d, float* t_out) {
   if (!(t > 0.0f)) return 0;
   *t_out = t;
   return 1;
+}
+
+/* Side of triangle k that a ray of direction d hits: 0 (A) when det = e1 . (d x e2) > 0,
+   1 (B) otherwise; det is computed as in intersect(), where it is non-zero for a hit. */
+static int hit_side(const omesh* m, int32_t k, v3 d) {
+  return vdot(m->te1[k], vcross(d, m->te2[k])) > 0.0f ? 0 : 1;
 }
 
 static void consider(const omesh* m, int32_t k, int32_t src, v3 o, v3 d, float* best_t, int32_t* best_k) {
@@ -545,6 +575,73 @@ int oracle_trace_counts(const float* verts, int64_t nv, const int32_t* tris, int
       if (use_bvh) closest_bvh(&m, &b, src, o, d, &bt, &bk);
       else for (int64_t k = 0; k < nt; ++k) consider(&m, (int32_t)k, src, o, d, &bt, &bk);
       row[bk < 0 ? n_faces : m.tri_face[bk]] += 1;
+    }
+  }
+  free(b.nodes); free(b.order);
+  omesh_free(&m);
+  return ORC_OK;
+}
+
+/* Origins, directions and source triangles of rays [ray0, ray0+n) of side `side` of face f. */
+int oracle_sample_rays_side(const float* verts, int64_t nv, const int32_t* tris, int64_t nt,
+                            const int32_t* tri_face, int32_t n_faces, int32_t f, int32_t side, uint64_t seed,
+                            uint64_t ray0, int64_t n, float* o_out, float* d_out, int32_t* tri_out) {
+  omesh m;
+  int st = omesh_init(&m, verts, nv, tris, nt, tri_face, n_faces);
+  if (st) return st;
+  if (f < 0 || f >= n_faces || n < 0 || (side != 0 && side != 1)) { omesh_free(&m); return ORC_ERR_ARG; }
+  const uint32_t stream = (uint32_t)f | ((uint32_t)side << 31);
+  for (int64_t r = 0; r < n; ++r) {
+    v3 o, d; int32_t tri;
+    emit_side(&m, seed, f, side, stream, 0u, ray0 + (uint64_t)r, &o, &d, &tri, NULL);
+    o_out[3 * r] = o.x; o_out[3 * r + 1] = o.y; o_out[3 * r + 2] = o.z;
+    d_out[3 * r] = d.x; d_out[3 * r + 1] = d.y; d_out[3 * r + 2] = d.z;
+    tri_out[r] = tri;
+  }
+  omesh_free(&m);
+  return ORC_OK;
+}
+
+/*
+ * Side-resolved hit counts (see the header), accumulated into
+ * counts[2 n_faces * (2 n_faces + 1)]: row 2f+X = side X of face f, column 2g+Y = side Y
+ * of face g, column 2 n_faces = environment. Side X of face f emits rays_per_side[2f+X]
+ * rays with ray indices ray_offset, ray_offset + 1, ... Returns ORC_ERR_ARG when a
+ * triangle is wound against its face.
+ */
+int oracle_trace_sided(const float* verts, int64_t nv, const int32_t* tris, int64_t nt,
+                       const int32_t* tri_face, int32_t n_faces, const int64_t* rays_per_side,
+                       uint64_t seed, uint64_t ray_offset, int use_bvh, int n_threads,
+                       const int32_t* row_subset, int32_t n_subset, int64_t* counts) {
+  omesh m;
+  int st = omesh_init(&m, verts, nv, tris, nt, tri_face, n_faces);
+  if (st) return st;
+  if (!m.wound_like_face || n_faces > (1 << 29)) { omesh_free(&m); return ORC_ERR_ARG; }
+  const int32_t n_rows = 2 * n_faces, n_cols = 2 * n_faces + 1;
+  for (int32_t q = 0; q < n_rows; ++q)
+    if (rays_per_side[q] < 0) { omesh_free(&m); return ORC_ERR_ARG; }
+  obvh b; memset(&b, 0, sizeof(b));
+  if (use_bvh) {
+    st = bvh_build(&b, &m);
+    if (st) { omesh_free(&m); return st; }
+  }
+  int32_t n_work = row_subset ? n_subset : n_rows;
+#ifdef _OPENMP
+  if (n_threads > 0) omp_set_num_threads(n_threads);
+#pragma omp parallel for schedule(dynamic, 1)
+#endif
+  for (int32_t q = 0; q < n_work; ++q) {
+    int32_t row = row_subset ? row_subset[q] : q;
+    int32_t f = row >> 1, side = row & 1;
+    const uint32_t stream = (uint32_t)f | ((uint32_t)side << 31);
+    int64_t* out = &counts[(int64_t)row * n_cols];
+    for (int64_t r = 0; r < rays_per_side[row]; ++r) {
+      v3 o, d; int32_t src;
+      emit_side(&m, seed, f, side, stream, 0u, ray_offset + (uint64_t)r, &o, &d, &src, NULL);
+      float bt = INFINITY; int32_t bk = -1;
+      if (use_bvh) closest_bvh(&m, &b, src, o, d, &bt, &bk);
+      else for (int64_t k = 0; k < nt; ++k) consider(&m, (int32_t)k, src, o, d, &bt, &bk);
+      out[bk < 0 ? n_rows : 2 * m.tri_face[bk] + hit_side(&m, bk, d)] += 1;
     }
   }
   free(b.nodes); free(b.order);

@@ -44,9 +44,13 @@ def _load():
                                             ctypes.c_int, P, i32, P]
         lib.oracle_trace_reflect.argtypes = [P, i64, P, i64, P, i32, P, P, P, i32, u64, u64, ctypes.c_int,
                                              ctypes.c_int, P, i32, P, P]
+        lib.oracle_sample_rays_side.argtypes = [P, i64, P, i64, P, i32, i32, i32, u64, u64, i64, P, P, P]
+        lib.oracle_trace_sided.argtypes = [P, i64, P, i64, P, i32, P, u64, u64, ctypes.c_int, ctypes.c_int, P,
+                                           i32, P]
         lib.oracle_max_threads.argtypes = []
         for fn in ("oracle_face_geometry", "oracle_sample_rays", "oracle_closest_hits",
-                   "oracle_trace_counts", "oracle_max_threads"):
+                   "oracle_trace_counts", "oracle_trace_reflect", "oracle_sample_rays_side",
+                   "oracle_trace_sided", "oracle_max_threads"):
             getattr(lib, fn).restype = ctypes.c_int
         _lib = lib
     return _lib
@@ -164,6 +168,38 @@ def trace_reflect(verts, tris, tri_face, n_faces, rays_per_face, eps, rho, seed,
            "trace_reflect")
     return counts, {"rays": int(stats[0]), "hits": int(stats[1]), "lost": int(stats[2]),
                     "overflow": int(stats[3])}
+
+
+def sample_rays_side(verts, tris, tri_face, n_faces, face, side, seed, ray0, n):
+    """Origins, directions and source triangles of rays [ray0, ray0+n) of side ``side``
+    (0 = A, along the face normal; 1 = B) of ``face``."""
+    lib = _load()
+    v, t, f = _mesh_arrays(verts, tris, tri_face)
+    o = np.zeros((n, 3), np.float32)
+    d = np.zeros((n, 3), np.float32)
+    tri = np.zeros(n, np.int32)
+    _check(lib.oracle_sample_rays_side(_ptr(v), len(v), _ptr(t), len(t), _ptr(f), n_faces, face, side, seed,
+                                       ray0, n, _ptr(o), _ptr(d), _ptr(tri)), "sample_rays_side")
+    return o, d, tri
+
+
+def trace_sided(verts, tris, tri_face, n_faces, rays_per_side, seed, ray_offset=0, use_bvh=True, threads=0,
+                rows=None):
+    """Side-resolved hit counts int64[2N, 2N+1] (Sec. 5.2.4-5.2.5): row 2f+X counts the rays
+    emitted from side X of face f, column 2g+Y the rays whose closest hit lies on side Y
+    of face g, column 2N the environment. ``rays_per_side[2f+X]`` rays leave side X of f;
+    ``rows`` restricts the work to a subset of rows."""
+    lib = _load()
+    v, t, f = _mesh_arrays(verts, tris, tri_face)
+    rays = np.ascontiguousarray(rays_per_side, dtype=np.int64)
+    if rays.shape != (2 * n_faces,):
+        raise ValueError("rays_per_side must have two entries per face")
+    counts = np.zeros((2 * n_faces, 2 * n_faces + 1), dtype=np.int64)
+    sub = None if rows is None else np.ascontiguousarray(rows, dtype=np.int32)
+    _check(lib.oracle_trace_sided(_ptr(v), len(v), _ptr(t), len(t), _ptr(f), n_faces, _ptr(rays), seed,
+                                  ray_offset, int(bool(use_bvh)), int(threads), _ptr(sub),
+                                  0 if sub is None else len(sub), _ptr(counts)), "trace_sided")
+    return counts
 
 
 def max_threads() -> int:
