@@ -138,6 +138,28 @@ rg_status rg_trace_stats(rg_ctx* ctx, const rg_mesh* mesh, const int64_t* rays_p
                          uint64_t ray_offset, int32_t fma_free, int64_t* counts_d, uint64_t* stats_out_h,
                          void* stream);
 
+/* Side-resolved hit counts of two-sided faces (Sec. 5.2.4-5.2.5: the factors
+ * F^{X->Y}_{n_i m_j} between the faces A and B of the nodes). Side A of face f is the
+ * side its normal n points to (n from the face's first triangle, as in rg_trace), side
+ * B the other one. Row 2f+X counts the rays emitted from side X of face f, column 2g+Y
+ * the rays whose closest hit lies on side Y of face g, column 2N the environment; F^{X->Y}
+ * = counts / rays of the row (Eq. 3.15 per side).
+ *   Side A emits exactly the rays of face f in rg_trace (counter word 2 = f), so summing
+ *   a side-A row over the target sides gives rg_trace's row bit for bit. Side B uses
+ *   counter word 2 = f + 2^31, the origin lifted along -n and Malley's direction in the
+ *   frame (t, -b, -n). A hit on a triangle is on side A when the Moller-Trumbore
+ *   determinant e1 . (d x e2) is positive (the ray runs against the triangle normal
+ *   e1 x e2), on side B otherwise; the closest-hit and tie rules are rg_trace's.
+ *   rays_per_side_h  host int64 [2N]: rays of side X of face f at index 2f+X (0 for a
+ *             face whose side B does not radiate)
+ *   counts_d  device int64 [2N][2N+1], row-major, ADDED to
+ * Errors: RG_ERR_ARG when a triangle's e1 x e2 points to its face's side B (every
+ * triangle of a face must be wound like the face's first one) or N >= 2^29;
+ * RG_ERR_UNSUPPORTED when 2N+1 tally columns exceed the shared-memory tally row
+ * (N > 24,575 on GB300); otherwise as rg_trace. */
+rg_status rg_trace_sided(rg_ctx* ctx, const rg_mesh* mesh, const int64_t* rays_per_side_h, uint64_t seed,
+                         uint64_t ray_offset, int32_t fma_free, int64_t* counts_d, void* stream);
+
 /* REFs directly from MCRT (Sec. 4.2.2): rays emitted as in rg_trace are followed
  * through diffuse reflections. At bounce b (b = 1, 2, ...) the closest hit on face j
  * is decided by word 3 of the Philox draw of counter (ray lo, ray hi, i, 128 b), i the
@@ -266,6 +288,44 @@ rg_status rg_enforce_lsq(rg_ctx* ctx, int32_t n, const double* omega_d, double* 
 rg_status rg_aggregate(rg_ctx* ctx, int32_t n_sub, const double* F_sub_d, const double* sub_area_d,
                        const int32_t* sub_group_d, int32_t n_group, double* F_group_d,
                        double* group_area_d, void* stream);
+
+/* Node view factors and view fractions of two-sided surfaces (Sec. 5.2.4-5.2.5).
+ * F2_d is a side-resolved matrix in the layout of rg_trace_sided (row 2i+X = side X of
+ * face i, column 2j+Y, column 2n = environment; leading dimension 2n+1), e.g. the view
+ * factors of the nodes' faces; node i has C_i faces.
+ *   F_node_d  device fp64 [n][n+1] (output): C_i F_ij = F^{AA}_ij + F^{AB}_ij + F^{BA}_ij
+ *             + F^{BB}_ij, C_i F_i,inf = F^{A,inf}_i + F^{B,inf}_i (Eq. 5.17 / 5.28)
+ *   frac_d    device fp64 [2n][2n+1] (output, may be NULL): the view fractions
+ *             f^{X->Y}_ij = F^{X->Y}_ij / (sum of the four) and f^{X,inf}_i =
+ *             F^{X,inf}_i / (sum of the two) (Eq. 5.27 / 5.29), 0 where the sum is 0
+ *   faces_per_node_d  device int32 [n]: C_i in {1, 2}; a one-faced node's side-B row of
+ *             F2 holds zeros (its rays are not traced)
+ * With singleton nodes of one face this is the identity. Errors: RG_ERR_ARG (bad
+ * argument, a C_i outside {1, 2}). */
+rg_status rg_node_view_factors(rg_ctx* ctx, int32_t n, const double* F2_d, const int32_t* faces_per_node_d,
+                               double* F_node_d, double* frac_d, void* stream);
+
+/* Radiative couplings of nodes whose two faces have different optical properties
+ * (App. C). B2_d holds the REFs of the system whose faces are the nodes' sides
+ * (rg_gebhart on 2n faces with per-side eps and rho), in the layout of
+ * rg_node_view_factors.
+ *   eps2_d       device fp64 [2n]: eps^X_i at 2i+X
+ *   face_area_d  device fp64 [n]: S_i, the area of each face of node i (A_i = C_i S_i)
+ *   faces_per_node_d  device int32 [n]: C_i in {1, 2}
+ *   GR_d         device fp64 [n][n+1] (output): GR_ij = S_i (eps^A_i (B^{AA}_ij +
+ *                B^{AB}_ij) + eps^B_i (B^{BA}_ij + B^{BB}_ij)) (Eq. C.3; column n the
+ *                environment, B^{X,inf}); the coupling sigma GR_ij (T_i^4 - T_j^4) of
+ *                Eq. 4.2 without sigma
+ *   B_node_d     device fp64 [n][n+1] (output, may be NULL): node REFs, C_i B_ij = sum
+ *                of the four side pairs (Eq. C.3, first line)
+ *   eps_node_d   device fp64 [n][n+1] (output, may be NULL): the node emissivity of each
+ *                pair, eps_ij = GR_ij / (C_i S_i B_ij) = eps^A_i (f^{AA} + f^{AB}) +
+ *                eps^B_i (f^{BA} + f^{BB}) with the view fractions of B (Eq. C.4); 0 where
+ *                B_ij = 0
+ * Errors: RG_ERR_ARG (bad argument, a C_i outside {1, 2}). */
+rg_status rg_node_couplings(rg_ctx* ctx, int32_t n, const double* B2_d, const double* eps2_d,
+                            const double* face_area_d, const int32_t* faces_per_node_d, double* GR_d,
+                            double* B_node_d, double* eps_node_d, void* stream);
 
 /* ---------------------------------------------------------------- Gebhart REFs (P5) */
 

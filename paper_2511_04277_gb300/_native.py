@@ -40,6 +40,7 @@ SIGNATURES = {
     "rg_face_areas": (i32, [P, P]),
     "rg_trace": (i32, [P, P, P, u64, u64, i32, P, P]),
     "rg_trace_stats": (i32, [P, P, P, u64, u64, i32, P, P, P]),
+    "rg_trace_sided": (i32, [P, P, P, u64, u64, i32, P, P]),
     "rg_counts_to_F": (i32, [P, i32, P, P, P, P]),
     "rg_enforce_iterative": (i32, [P, i32, P, P, f64, i32, P, P]),
     "rg_enforce_iterative_noalloc": (i32, [i32, P, P, f64, i32, P, P]),
@@ -50,6 +51,8 @@ SIGNATURES = {
     "rg_debug_barrier_timeout": (i32, [P, f64, P]),
     "rg_enforce_lsq": (i32, [P, i32, P, P, i32, i32, i32, P, P]),
     "rg_aggregate": (i32, [P, i32, P, P, P, i32, P, P, P]),
+    "rg_node_view_factors": (i32, [P, i32, P, P, P, P, P]),
+    "rg_node_couplings": (i32, [P, i32, P, P, P, P, P, P, P, P]),
     "rg_gebhart": (i32, [P, i32, P, i32, P, P, i32, f64, i32, P, P, P, P]),
     "rg_gebhart_adjoint": (i32, [P, i32, P, i32, P, P, P, P, i32, f64, i32, P, P, P]),
     "rg_temperatures": (i32, [P, i32, P, P, P, P, f64, f64, i32, f64, P, P]),

@@ -145,6 +145,24 @@ def trace_stats(ctx: Context, mesh: Mesh, rays_per_face, seed: int, ray_offset: 
     return counts, {"rays": int(st[0]), "box_tests": int(st[1]), "tri_tests": int(st[2])}
 
 
+def trace_sided(ctx: Context, mesh: Mesh, rays_per_side, seed: int, ray_offset: int = 0, fma_free: bool = True,
+                counts: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """Side-resolved MCRT hit counts, int64 [2N, 2N+1] on the device (rg_trace_sided): row
+    2f+X = side X of face f (0 = A, the side its normal points to; 1 = B), column 2g+Y,
+    column 2N = environment; accumulates into ``counts``."""
+    N = mesh.n_faces
+    rays = np.ascontiguousarray(rays_per_side, np.int64)
+    if rays.shape != (2 * N,):
+        raise ValueError("rays_per_side must have two entries per face")
+    if counts is None:
+        counts = torch.zeros((2 * N, 2 * N + 1), dtype=torch.int64, device=f"cuda:{ctx.device}")
+    ctx.check(ctx.lib.rg_trace_sided(ctx.handle, mesh.handle, _hptr(rays), int(seed) & (2 ** 64 - 1),
+                                     int(ray_offset), int(bool(fma_free)),
+                                     _dptr(counts, torch.int64, "counts", 2 * N * (2 * N + 1), ctx.device),
+                                     _stream(stream)), "rg_trace_sided")
+    return counts
+
+
 def trace_reflect(ctx: Context, mesh: Mesh, rays_per_face, eps, rho, seed: int, max_bounces: int = 4096,
                   ray_offset: int = 0, fma_free: bool = True, counts: torch.Tensor | None = None, stream=None):
     """REFs directly from MCRT with diffuse reflections (rg_trace_reflect): (counts int64
@@ -251,6 +269,56 @@ def aggregate(ctx: Context, F_sub: torch.Tensor, sub_area: torch.Tensor, sub_gro
                                    _dptr(Fg, torch.float64, "F_group"), _dptr(Sg, torch.float64, "group_area"),
                                    _stream(stream)), "rg_aggregate")
     return Fg, Sg
+
+
+def aggregate_sided(ctx: Context, F2: torch.Tensor, sub_area: torch.Tensor, sub_group: torch.Tensor, n_group: int,
+                    stream=None):
+    """Side-resolved group view factors F^{X->Y}_nm and F^{X,inf}_n (Eq. 5.6-5.7, the first two
+    lines of Eq. 5.28) from side-resolved sub-surface factors F2 [2n, 2n+1] (the layout of
+    trace_sided) -> (F2_group [2G, 2G+1], group areas [G]).
+
+    rg_aggregate with the sides as sub-surfaces: side X of sub-surface i (area S_i) joins
+    side X of its group, so that sum_i S_i = S_n and the weights are S_i / S_n per side."""
+    n = F2.shape[0] // 2
+    g = sub_group.to(device=F2.device, dtype=torch.int32)
+    sides = torch.stack([2 * g, 2 * g + 1], dim=1).reshape(-1).contiguous()
+    area2 = sub_area.to(device=F2.device, dtype=torch.float64).repeat_interleave(2).contiguous()
+    Fg, Sg = aggregate(ctx, F2, area2, sides, 2 * n_group, stream)
+    return Fg, Sg[0::2].contiguous()
+
+
+def node_view_factors(ctx: Context, F2: torch.Tensor, faces_per_node: torch.Tensor, fractions: bool = True,
+                      stream=None):
+    """Node view factors F [n, n+1] (Eq. 5.17) and, if asked, the view fractions f [2n, 2n+1]
+    (Eq. 5.27 / 5.29) from side-resolved factors F2 [2n, 2n+1] (rg_node_view_factors)."""
+    n = F2.shape[0] // 2
+    Fn = torch.empty((n, n + 1), dtype=torch.float64, device=F2.device)
+    fr = torch.empty_like(F2) if fractions else None
+    ctx.check(ctx.lib.rg_node_view_factors(ctx.handle, n, _dptr(F2, torch.float64, "F2", 2 * n * (2 * n + 1),
+                                                                 ctx.device),
+                                           _dptr(faces_per_node, torch.int32, "faces_per_node", n, ctx.device),
+                                           _dptr(Fn, torch.float64, "F_node"),
+                                           None if fr is None else _dptr(fr, torch.float64, "frac"),
+                                           _stream(stream)), "rg_node_view_factors")
+    return Fn, fr
+
+
+def node_couplings(ctx: Context, B2: torch.Tensor, eps2: torch.Tensor, face_area: torch.Tensor,
+                   faces_per_node: torch.Tensor, stream=None):
+    """Node couplings of two-faced nodes (App. C, rg_node_couplings) from side-resolved REFs
+    B2 [2n, 2n+1]: (GR [n, n+1] (Eq. C.3, without sigma), node REFs B [n, n+1], node
+    emissivities eps_ij [n, n+1] (Eq. C.4))."""
+    n = B2.shape[0] // 2
+    GR = torch.empty((n, n + 1), dtype=torch.float64, device=B2.device)
+    Bn = torch.empty_like(GR)
+    en = torch.empty_like(GR)
+    ctx.check(ctx.lib.rg_node_couplings(ctx.handle, n, _dptr(B2, torch.float64, "B2", 2 * n * (2 * n + 1), ctx.device),
+                                        _dptr(eps2, torch.float64, "eps2", 2 * n, ctx.device),
+                                        _dptr(face_area, torch.float64, "face_area", n, ctx.device),
+                                        _dptr(faces_per_node, torch.int32, "faces_per_node", n, ctx.device),
+                                        _dptr(GR, torch.float64, "GR"), _dptr(Bn, torch.float64, "B_node"),
+                                        _dptr(en, torch.float64, "eps_node"), _stream(stream)), "rg_node_couplings")
+    return GR, Bn, en
 
 
 def _prec(p):

@@ -270,6 +270,13 @@ rg_status rg_mesh_create(rg_ctx* ctx, const float* verts_h, int64_t nv, const in
     fr[0] = t.x; fr[1] = t.y; fr[2] = t.z; fr[3] = b.x; fr[4] = b.y; fr[5] = b.z;
     fr[6] = n.x; fr[7] = n.y; fr[8] = n.z;
   }
+  // side-resolved tracing takes the side of a hit from the triangle's own winding, so it
+  // needs every triangle's normal e1 x e2 on its face's side A
+  int32_t wound_like_face = 1;
+  for (int64_t k = 0; k < nt; ++k) {
+    const float* fr = &frames[9 * (size_t)tri_face_h[k]];
+    if (!(f3dot(f3cross(te1[k], te2[k]), F3{fr[6], fr[7], fr[8]}) > 0.0f)) wound_like_face = 0;
+  }
   // scene scale
   double lo[3], hi[3];
   for (int c = 0; c < 3; ++c) lo[c] = hi[c] = verts_h[c];
@@ -389,6 +396,7 @@ rg_status rg_mesh_create(rg_ctx* ctx, const float* verts_h, int64_t nv, const in
   d.n_faces = n_faces; d.nt = nt; d.use_bvh = use_bvh; d.n_nodes = (int32_t)nodes.size(); d.depth = depth;
   d.lift = lift; d.t_lo = -0.5f * lift; d.slack = (float)(1e-5 * diag);
   d.sah_visits = sah_visits;
+  d.wound_like_face = wound_like_face;
   // refill scheduling pays off when traversals are long; short ones run lock-step
   d.refill = schedule == 3 ? 1 : (schedule == 2 ? 0 : (depth >= kRefillDepth ? 1 : 0));
   d.nodes = d_nodes; d.tris = d_tris; d.etris = d_etris; d.ethr = d_thr; d.face_start = d_fstart;

@@ -22,6 +22,7 @@ struct DevMesh {
   float slack = 0.f;      // the window's upper end is best_t + slack
   int32_t refill = 0;     // 1: refill scheduling of the trace kernel, 0: lock-step
   float sah_visits = 0.f; // expected node visits of a random line (surface-area heuristic)
+  int32_t wound_like_face = 0;  // 1: every triangle's e1 x e2 points to its face's side A
   const float4* nodes = nullptr;
   const float4* tris = nullptr;     // nt records in leaf order (BVH) or index order
   const float4* etris = nullptr;    // nt records in face order (emission)

@@ -20,6 +20,12 @@
 // hit is the smallest (t > 0, triangle index), so the counts do not depend on the order
 // in which rays are traced.
 //
+// Side-resolved variant (two-sided faces, Sec. 5.2.4-5.2.5): work item rows are the
+// sides 2f+X of the faces (X = 0: side A, the side the face normal points to; 1: side B),
+// side B emits with the frame (t, -b, -n) and counter word 2 = f + 2^31, and a hit counts
+// for column 2g+Y with Y = 0 when the Moller-Trumbore determinant is positive (the ray
+// runs against the triangle normal) and 1 otherwise; column 2N is the environment.
+//
 // kExact = true rounds every float operation of sampling and intersection on its
 // own (no fused multiply-add), which makes the counts bit-identical to any other
 // implementation of the same ray definition that does the same.
@@ -124,7 +130,7 @@ __device__ __forceinline__ float sym24(uint32_t x) {
 // NaN or infinite u, v, t, which fail their tests.
 template <bool E>
 __device__ __forceinline__ bool moller_trumbore(const float4 r0, const float4 r1, const float4 r2, V3 o, V3 d,
-                                                float* t_out) {
+                                                float* t_out, float* det_out) {
   using A = Ar<E>;
   const float lo = -9.5367431640625e-07f, hi = 1.00000095367431640625f;  // -2^-20, 1 + 2^-20
   V3 v0{r0.x, r0.y, r0.z}, e1{r0.w, r1.x, r1.y}, e2{r1.z, r1.w, r2.x};
@@ -137,6 +143,7 @@ __device__ __forceinline__ bool moller_trumbore(const float4 r0, const float4 r1
   const float v = A::mul(dot3<E>(d, q), inv);
   const float t = A::mul(dot3<E>(e2, q), inv);
   *t_out = t;
+  *det_out = det;
   return det != 0.0f && u >= lo && u <= hi && v >= lo && A::add(u, v) <= hi && t > 0.0f;
 }
 
@@ -150,17 +157,19 @@ struct Stats {
   __device__ __forceinline__ void tri() { ++n_tri; }
 };
 
-template <bool E>
+// S (side-resolved): best_face receives the tally column 2 * face + side instead of the face.
+template <bool E, bool S>
 __device__ __forceinline__ void test_record(const float4* __restrict__ rec, int32_t src, V3 o, V3 d, float& best_t,
                                             int32_t& best_id, int32_t& best_face) {
   float4 r0 = __ldg(rec), r1 = __ldg(rec + 1), r2 = __ldg(rec + 2);
   int32_t id = __float_as_int(r2.y);
-  float t;
-  const bool hit = moller_trumbore<E>(r0, r1, r2, o, d, &t) && id != src;
+  float t, det;
+  const bool hit = moller_trumbore<E>(r0, r1, r2, o, d, &t, &det) && id != src;
   if (hit && (t < best_t || (t == best_t && id < best_id))) {
     best_t = t;
     best_id = id;
-    best_face = __float_as_int(r2.z);
+    const int32_t face = __float_as_int(r2.z);
+    best_face = S ? 2 * face + (det > 0.0f ? 0 : 1) : face;
   }
 }
 
@@ -197,15 +206,15 @@ __device__ __forceinline__ void slab_window(float x0, float x1, float y0, float 
   tmax = min3f(fmaxf(x0, x1), fmaxf(y0, y1), fminf(fmaxf(z0, z1), hi));
 }
 
-// Closest hit; returns the face index or n_faces (environment). Sets *overflow on a
-// traversal stack overflow.
-template <bool E, bool kBVH, class St>
-__device__ int32_t closest_face(const DevMesh& m, int32_t src, V3 o, V3 d, bool* overflow, St& st) {
+// Closest hit; returns the tally column of the hit (the face, or 2 face + side when S)
+// or `env`. Sets *overflow on a traversal stack overflow.
+template <bool E, bool kBVH, bool S, class St>
+__device__ int32_t closest_face(const DevMesh& m, int32_t src, V3 o, V3 d, bool* overflow, St& st, int32_t env) {
   float best_t = __int_as_float(0x7f800000);
-  int32_t best_id = INT_MAX, best_face = m.n_faces;
+  int32_t best_id = INT_MAX, best_face = env;
   if (!kBVH) {
     for (int64_t k = 0; k < m.nt; ++k) {
-      test_record<E>(m.tris + 3 * k, src, o, d, best_t, best_id, best_face);
+      test_record<E, S>(m.tris + 3 * k, src, o, d, best_t, best_id, best_face);
       st.tri();
     }
     return best_face;
@@ -232,14 +241,14 @@ __device__ int32_t closest_face(const DevMesh& m, int32_t src, V3 o, V3 d, bool*
     st.box(2);
     if (hl && cntL > 0) {
       for (int q = 0; q < cntL; ++q) {
-        test_record<E>(m.tris + 3 * (int64_t)(refL + q), src, o, d, best_t, best_id, best_face);
+        test_record<E, S>(m.tris + 3 * (int64_t)(refL + q), src, o, d, best_t, best_id, best_face);
         st.tri();
       }
       hl = false;
     }
     if (hr && cntR > 0) {
       for (int q = 0; q < cntR; ++q) {
-        test_record<E>(m.tris + 3 * (int64_t)(refR + q), src, o, d, best_t, best_id, best_face);
+        test_record<E, S>(m.tris + 3 * (int64_t)(refR + q), src, o, d, best_t, best_id, best_face);
         st.tri();
       }
       hr = false;
@@ -264,10 +273,12 @@ __device__ int32_t closest_face(const DevMesh& m, int32_t src, V3 o, V3 d, bool*
 // Emission from `face` with the draws of counters (ray lo, ray hi, stream, base + a):
 // a = 0 for the triangle and the point, a = 1..64 for Malley's direction. Emission
 // proper uses stream = face and base = 0; the reflection of bounce b of a path from
-// face i uses stream = i and base = 128 b (re-emission from the hit face).
+// face i uses stream = i and base = 128 b (re-emission from the hit face). side_b: emission
+// from side B, with the frame (t, -b, -n) (stream = face + 2^31).
 template <bool E>
 __device__ __forceinline__ void sample_ray(const DevMesh& m, uint32_t k0, uint32_t k1, uint64_t ray, int32_t face,
-                                           V3* o, V3* d, int32_t* src, uint32_t stream, uint32_t base) {
+                                           V3* o, V3* d, int32_t* src, uint32_t stream, uint32_t base,
+                                           bool side_b = false) {
   using A = Ar<E>;
   const uint32_t rlo = (uint32_t)ray, rhi = (uint32_t)(ray >> 32);
   uint4 x = philox(make_uint4(rlo, rhi, stream, base), k0, k1);
@@ -292,6 +303,10 @@ __device__ __forceinline__ void sample_ray(const DevMesh& m, uint32_t k0, uint32
   const float* fr = m.frames + 9 * (int64_t)face;
   float tx = __ldg(fr), ty = __ldg(fr + 1), tz = __ldg(fr + 2), bx = __ldg(fr + 3), by = __ldg(fr + 4),
         bz = __ldg(fr + 5), nx = __ldg(fr + 6), ny = __ldg(fr + 7), nz = __ldg(fr + 8);
+  if (side_b) {
+    bx = -bx; by = -by; bz = -bz;
+    nx = -nx; ny = -ny; nz = -nz;
+  }
   // point on the triangle, lifted off the face along its normal
   o->x = A::add(A::add(A::add(r0.x, A::mul(u, r0.w)), A::mul(v, r1.z)), A::mul(m.lift, nx));
   o->y = A::add(A::add(A::add(r0.y, A::mul(u, r1.x)), A::mul(v, r1.w)), A::mul(m.lift, ny));
@@ -335,16 +350,8 @@ struct Walker {
   int sp;
 };
 
-template <bool E, class St>
-__device__ __forceinline__ void test_leaf(const DevMesh& m, Walker& w, int32_t ref, int32_t cnt, St& st) {
-  for (int q = 0; q < cnt; ++q) {
-    test_record<E>(m.tris + 3 * (int64_t)(ref + q), w.src, w.o, w.d, w.best_t, w.best_id, w.best_face);
-    st.tri();
-  }
-}
-
 // One BVH node visit. Returns false once the ray's traversal is complete.
-template <bool E, class St>
+template <bool E, bool S, class St>
 __device__ __forceinline__ bool visit(const DevMesh& m, Walker& w, int32_t* stack, bool* overflow, St& st) {
   const float4* nd = m.nodes + 4 * w.node;
   const float4 a = __ldg(nd), b = __ldg(nd + 1), c = __ldg(nd + 2), q = __ldg(nd + 3);
@@ -368,7 +375,7 @@ __device__ __forceinline__ bool visit(const DevMesh& m, Walker& w, int32_t* stac
     const int32_t r1 = right_first ? refL : refR, c1 = right_first ? (ll ? cntL : 0) : (lr ? cntR : 0);
     for (int q = 0; q < c0 + c1; ++q) {
       const int32_t rec = q < c0 ? r0 + q : r1 + (q - c0);
-      test_record<E>(m.tris + 3 * (int64_t)rec, w.src, w.o, w.d, w.best_t, w.best_id, w.best_face);
+      test_record<E, S>(m.tris + 3 * (int64_t)rec, w.src, w.o, w.d, w.best_t, w.best_id, w.best_face);
       st.tri();
     }
     if (ll) hl = false;
@@ -405,7 +412,7 @@ __device__ __forceinline__ void start_ray(Walker& w, const Ring& r, int k, int32
 }
 
 // Refill variant (see the file comment). Best when traversals are long and uneven.
-template <bool E, bool kBVH, class St>
+template <bool E, bool kBVH, bool S, class St>
 __global__ void __launch_bounds__(kThreads, RG_REFILL_MIN_BLOCKS) trace_kernel_refill(const TraceParams p) {
   extern __shared__ __align__(16) uint32_t hist[];
   __shared__ Ring s_ring[kWarps];
@@ -429,6 +436,11 @@ __global__ void __launch_bounds__(kThreads, RG_REFILL_MIN_BLOCKS) trace_kernel_r
     const int32_t item = s_item;
     if (item >= p.n_items) break;
     const WorkItem wi = p.items[item];
+    // the item's row: a face, or side (wi.face & 1) of face (wi.face >> 1) when S
+    const int32_t face = S ? wi.face >> 1 : wi.face;
+    const bool side_b = S && (wi.face & 1);
+    const uint32_t stream = (uint32_t)face | (side_b ? 0x80000000u : 0u);
+    const int32_t env = p.n_bins - 1;
     // warp-uniform ring state: `avail` sampled rays from position `head`
     int head = 0, avail = 0;
     bool more = true;  // rays of the item left to sample
@@ -437,10 +449,10 @@ __global__ void __launch_bounds__(kThreads, RG_REFILL_MIN_BLOCKS) trace_kernel_r
     while (true) {
       if (has_ray && !done) {
         if (kBVH) {
-          done = !visit<E>(m, w, stack, &overflow, st);
+          done = !visit<E, S>(m, w, stack, &overflow, st);
         } else {
           for (int64_t t = 0; t < m.nt; ++t) {
-            test_record<E>(m.tris + 3 * t, w.src, w.o, w.d, w.best_t, w.best_id, w.best_face);
+            test_record<E, S>(m.tris + 3 * t, w.src, w.o, w.d, w.best_t, w.best_id, w.best_face);
             st.tri();
           }
           done = true;
@@ -468,8 +480,8 @@ __global__ void __launch_bounds__(kThreads, RG_REFILL_MIN_BLOCKS) trace_kernel_r
         if (valid) {
           V3 o, d;
           int32_t src;
-          sample_ray<E>(m, p.key0, p.key1, p.ray_offset + (uint64_t)(wi.begin + r), wi.face, &o, &d, &src,
-                              (uint32_t)wi.face, 0u);
+          sample_ray<E>(m, p.key0, p.key1, p.ray_offset + (uint64_t)(wi.begin + r), face, &o, &d, &src, stream, 0u,
+                        side_b);
           const int slot = (head + avail + lane) & (kRing - 1);
           ring.ox[slot] = o.x; ring.oy[slot] = o.y; ring.oz[slot] = o.z;
           ring.dx[slot] = d.x; ring.dy[slot] = d.y; ring.dz[slot] = d.z;
@@ -481,7 +493,7 @@ __global__ void __launch_bounds__(kThreads, RG_REFILL_MIN_BLOCKS) trace_kernel_r
       }
       const int rank = __popc(idle & lt_mask);
       if (!(tracing >> lane & 1u) && rank < avail) {
-        start_ray(w, ring, (head + rank) & (kRing - 1), m.n_faces);
+        start_ray(w, ring, (head + rank) & (kRing - 1), env);
         has_ray = true;
         done = false;
       }
@@ -522,7 +534,7 @@ __global__ void __launch_bounds__(kThreads, RG_REFILL_MIN_BLOCKS) trace_kernel_r
 // their traversal state, in a per-warp shared-memory queue. Whenever 32 rays are queued
 // the warp continues them to completion in step, so the long traversals run with full
 // warps instead of next to lanes that finished after one visit.
-template <bool E, bool kBVH, class St>
+template <bool E, bool kBVH, bool S, class St>
 __global__ void __launch_bounds__(kThreads, RG_LOCKSTEP_MIN_BLOCKS) trace_kernel_lockstep(const TraceParams p) {
   extern __shared__ __align__(16) uint32_t hist[];
   __shared__ Ring s_queue[kWarps];
@@ -536,6 +548,7 @@ __global__ void __launch_bounds__(kThreads, RG_LOCKSTEP_MIN_BLOCKS) trace_kernel
   unsigned long long n_rays = 0;
   int32_t stack[kTraceStack];
   const DevMesh& m = p.m;
+  const int32_t env = p.n_bins - 1;
 
   auto tally = [&](bool fin, int32_t face) {
     const unsigned fm = __ballot_sync(0xffffffffu, fin);
@@ -549,10 +562,10 @@ __global__ void __launch_bounds__(kThreads, RG_LOCKSTEP_MIN_BLOCKS) trace_kernel
   auto drain = [&](int count) {
     const bool has = lane < count;
     Walker w;
-    if (has) start_ray(w, q, lane, m.n_faces);
+    if (has) start_ray(w, q, lane, env);
     bool more = has;
     while (__any_sync(0xffffffffu, more)) {
-      if (more) more = visit<E>(m, w, stack, &overflow, st);
+      if (more) more = visit<E, S>(m, w, stack, &overflow, st);
     }
     tally(has, has ? w.best_face : 0);
   };
@@ -567,6 +580,10 @@ __global__ void __launch_bounds__(kThreads, RG_LOCKSTEP_MIN_BLOCKS) trace_kernel
     const int32_t item = s_item;
     if (item >= p.n_items) break;
     const WorkItem wi = p.items[item];
+    // the item's row: a face, or side (wi.face & 1) of face (wi.face >> 1) when S
+    const int32_t face_i = S ? wi.face >> 1 : wi.face;
+    const bool side_b = S && (wi.face & 1);
+    const uint32_t stream = (uint32_t)face_i | (side_b ? 0x80000000u : 0u);
     int queued = 0;  // warp-uniform
     while (true) {
       int base = 0;
@@ -577,10 +594,10 @@ __global__ void __launch_bounds__(kThreads, RG_LOCKSTEP_MIN_BLOCKS) trace_kernel
       const bool valid = r < wi.count;
       V3 o, d;
       int32_t src = -1;
-      if (valid) sample_ray<E>(m, p.key0, p.key1, p.ray_offset + (uint64_t)(wi.begin + r), wi.face, &o, &d, &src,
-                              (uint32_t)wi.face, 0u);
+      if (valid) sample_ray<E>(m, p.key0, p.key1, p.ray_offset + (uint64_t)(wi.begin + r), face_i, &o, &d, &src,
+                              stream, 0u, side_b);
       bool more = false;
-      int32_t face = m.n_faces;
+      int32_t face = env;
       if (valid) {
         if (kBVH) {
           // escape test: does the ray enter either child box of the root? Rays that do
@@ -597,13 +614,13 @@ __global__ void __launch_bounds__(kThreads, RG_LOCKSTEP_MIN_BLOCKS) trace_kernel
           st.box(2);
           more = lmin <= lmax || rmin <= rmax;
         } else {
-          face = closest_face<E, false>(m, src, o, d, &overflow, st);
+          face = closest_face<E, false, S>(m, src, o, d, &overflow, st, env);
         }
       }
       if (kBVH) {
         // with a BVH every ray finished here left the scene: one count for all of them
         const unsigned esc = __ballot_sync(0xffffffffu, valid && !more);
-        if (lane == 0 && esc) atomicAdd(&hist[m.n_faces], (uint32_t)__popc(esc));
+        if (lane == 0 && esc) atomicAdd(&hist[env], (uint32_t)__popc(esc));
         if (valid && !more) ++n_rays;
       } else {
         tally(valid && !more, face);
@@ -707,7 +724,7 @@ __global__ void __launch_bounds__(kThreads) trace_kernel_reflect(const TracePara
         sample_ray<E>(m, p.key0, p.key1, ray, wi.face, &o, &d, &src, stream, 0u);
         ++n_rays;
         for (int32_t bounce = 1;; ++bounce) {
-          const int32_t j = closest_face<E, kBVH>(m, src, o, d, &overflow, st);
+          const int32_t j = closest_face<E, kBVH, false>(m, src, o, d, &overflow, st, m.n_faces);
           if (j == m.n_faces) { col = j; break; }
           ++n_hits;
           const uint32_t cb = (uint32_t)bounce << 7;
@@ -751,9 +768,9 @@ __global__ void __launch_bounds__(kThreads) trace_kernel_reflect(const TracePara
 
 inline size_t trace_smem_bytes(int n_bins) { return (size_t)((n_bins + 3) & ~3) * sizeof(uint32_t); }
 
-template <bool E, bool B, class St>
+template <bool E, bool B, class St, bool S = false>
 cudaError_t launch(const TraceParams& p, int sm_count, size_t smem, cudaStream_t s) {
-  auto k = p.m.refill ? trace_kernel_refill<E, B, St> : trace_kernel_lockstep<E, B, St>;
+  auto k = p.m.refill ? trace_kernel_refill<E, B, S, St> : trace_kernel_lockstep<E, B, S, St>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int per_sm = 0;
@@ -782,28 +799,35 @@ cudaError_t launch_reflect(const TraceParams& p, int sm_count, size_t smem, cuda
   return cudaGetLastError();
 }
 
+// sided = true: side-resolved counts, rows and columns 2f + side (see the file comment).
 rg_status trace_impl(rg_ctx* ctx, const rg_mesh* mesh, const int64_t* rays_per_face_h, uint64_t seed,
-                     uint64_t ray_offset, int32_t fma_free, int64_t* counts_d, uint64_t* stats_h, void* stream) {
+                     uint64_t ray_offset, int32_t fma_free, int64_t* counts_d, uint64_t* stats_h, void* stream,
+                     bool sided = false) {
   if (!ctx) return RG_ERR_ARG;
-  RG_ARG_CHECK(ctx, mesh && rays_per_face_h && counts_d, "rg_trace: NULL argument");
+  const char* fn = sided ? "rg_trace_sided" : "rg_trace";
+  RG_ARG_CHECK(ctx, mesh && rays_per_face_h && counts_d, "%s: NULL argument", fn);
   const DevMesh& m = mesh_device_view(mesh);
-  RG_ARG_CHECK(ctx, mesh_device(mesh) == ctx->device, "rg_trace: mesh belongs to another device");
+  RG_ARG_CHECK(ctx, mesh_device(mesh) == ctx->device, "%s: mesh belongs to another device", fn);
+  RG_ARG_CHECK(ctx, !sided || m.wound_like_face,
+               "rg_trace_sided: a triangle is wound against its face (its normal e1 x e2 points to side B)");
   const int32_t N = m.n_faces;
-  const int32_t n_bins = N + 1;
+  RG_ARG_CHECK(ctx, !sided || N < (1 << 29), "rg_trace_sided: %d faces", N);
+  const int32_t n_rows = sided ? 2 * N : N;
+  const int32_t n_bins = n_rows + 1;
   const size_t smem = trace_smem_bytes(n_bins);
   if (n_bins > 49152 || (int)smem > ctx->smem_optin - 1024)
-    return rg::fail(ctx, RG_ERR_UNSUPPORTED, "rg_trace: %d faces exceed the shared-memory tally row", N);
-  // work items: chunks of at most kChunk rays of one face
+    return rg::fail(ctx, RG_ERR_UNSUPPORTED, "%s: %d tally columns exceed the shared-memory tally row", fn, n_bins);
+  // work items: chunks of at most kChunk rays of one row
   constexpr int64_t kChunk = 1 << 16;
   std::vector<WorkItem> items;
-  for (int32_t f = 0; f < N; ++f) {
+  for (int32_t f = 0; f < n_rows; ++f) {
     int64_t n = rays_per_face_h[f];
-    RG_ARG_CHECK(ctx, n >= 0, "rg_trace: negative ray count for face %d", f);
+    RG_ARG_CHECK(ctx, n >= 0, "%s: negative ray count for row %d", fn, f);
     for (int64_t b = 0; b < n; b += kChunk) items.push_back({b, f, (int32_t)std::min(kChunk, n - b)});
   }
   if (stats_h) stats_h[0] = stats_h[1] = stats_h[2] = 0;
   if (items.empty()) return RG_OK;
-  RG_ARG_CHECK(ctx, items.size() < (size_t)INT32_MAX, "rg_trace: too many rays");
+  RG_ARG_CHECK(ctx, items.size() < (size_t)INT32_MAX, "%s: too many rays", fn);
   RG_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
   cudaStream_t s = (cudaStream_t)stream;
   void* ws = nullptr;
@@ -828,7 +852,13 @@ rg_status trace_impl(rg_ctx* ctx, const rg_mesh* mesh, const int64_t* rays_per_f
   p.stats = d_stats;
   cudaError_t e;
   const int sm = ctx->sm_count;
-  if (stats_h) {
+  if (sided) {
+    if (fma_free)
+      e = m.use_bvh ? launch<true, true, NoStats, true>(p, sm, smem, s) : launch<true, false, NoStats, true>(p, sm, smem, s);
+    else
+      e = m.use_bvh ? launch<false, true, NoStats, true>(p, sm, smem, s)
+                    : launch<false, false, NoStats, true>(p, sm, smem, s);
+  } else if (stats_h) {
     if (fma_free)
       e = m.use_bvh ? launch<true, true, Stats>(p, sm, smem, s) : launch<true, false, Stats>(p, sm, smem, s);
     else
@@ -839,13 +869,13 @@ rg_status trace_impl(rg_ctx* ctx, const rg_mesh* mesh, const int64_t* rays_per_f
     else
       e = m.use_bvh ? launch<false, true, NoStats>(p, sm, smem, s) : launch<false, false, NoStats>(p, sm, smem, s);
   }
-  if (e != cudaSuccess) return rg::cuda_fail(ctx, e, "rg_trace: launch");
+  if (e != cudaSuccess) return rg::cuda_fail(ctx, e, sided ? "rg_trace_sided: launch" : "rg_trace: launch");
   ++ctx->launches;
   // the host copy of the items must outlive the async upload, and the error word is read back
   RG_CUDA_TRY(ctx, cudaMemcpyAsync(ctx->h_scratch, ctx->d_scratch + 1, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
   if (stats_h) RG_CUDA_TRY(ctx, cudaMemcpyAsync(stats_h, d_stats, 3 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
   RG_CUDA_TRY(ctx, cudaStreamSynchronize(s));
-  if (ctx->h_scratch[0]) return rg::fail(ctx, RG_ERR_STACK, "rg_trace: traversal stack overflow");
+  if (ctx->h_scratch[0]) return rg::fail(ctx, RG_ERR_STACK, "%s: traversal stack overflow", fn);
   return RG_OK;
 }
 
@@ -856,6 +886,11 @@ extern "C" {
 rg_status rg_trace(rg_ctx* ctx, const rg_mesh* mesh, const int64_t* rays_per_face_h, uint64_t seed,
                    uint64_t ray_offset, int32_t fma_free, int64_t* counts_d, void* stream) {
   return trace_impl(ctx, mesh, rays_per_face_h, seed, ray_offset, fma_free, counts_d, nullptr, stream);
+}
+
+rg_status rg_trace_sided(rg_ctx* ctx, const rg_mesh* mesh, const int64_t* rays_per_side_h, uint64_t seed,
+                         uint64_t ray_offset, int32_t fma_free, int64_t* counts_d, void* stream) {
+  return trace_impl(ctx, mesh, rays_per_side_h, seed, ray_offset, fma_free, counts_d, nullptr, stream, true);
 }
 
 rg_status rg_trace_stats(rg_ctx* ctx, const rg_mesh* mesh, const int64_t* rays_per_face_h, uint64_t seed,

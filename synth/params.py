@@ -58,6 +58,9 @@ def workload(name: str, rays_scale: float = 1.0):
     small_sat  0.3x0.3x0.6 m body + four hinged panels at 45 deg, 20,736 triangles,
                2,048 faces, 1e8 rays split by area, eps ~ U[0.05, 0.9] (seed 2).
     thermal    the plates mesh with Q ~ U[0, 50] W (seed 3) and a 3 K sink.
+    plates_sided  the plates mesh with both sides of every sub-face radiating (Sec. 5.2:
+               two-faced nodes, C_i = 2): 1e6 rays per side (1.024e9), rows 2i+X of
+               side X; eps ~ U[0.1, 0.9] per side (seed 4), rho = 1 - eps.
     spacecraft ~200k triangles, 10,240 faces, 1e9 rays split by area, 16 eps/rho sets
                eps ~ U[0.05, 0.9] (seeds 10..25).
     ``rays_scale`` multiplies the ray budget (tests use small fractions).
@@ -76,6 +79,12 @@ def workload(name: str, rays_scale: float = 1.0):
         if name == "thermal":
             d.update(Q=heat_loads(m.n_faces, seed=3), T_sink=3.0)
         return d
+    if name == "plates_sided":
+        m = meshes.plates(16)
+        rays = uniform_rays(2 * m.n_faces, max(1, int(1e6 * rays_scale)))
+        eps, rho = optical_sets(2 * m.n_faces, 1, 0.1, 0.9, seed=4)
+        return dict(mesh=m, rays=rays, seed=0, eps=eps, rho=rho, open=True,
+                    faces_per_node=np.full(m.n_faces, 2, np.int32))
     if name == "small_sat":
         m = meshes.small_sat()
         rays = rays_by_area(m, max(m.n_faces, int(1e8 * rays_scale)))
