@@ -57,6 +57,9 @@ def parse():
                          "budget (the small case the ncu captures use) and print the ray count")
     ap.add_argument("--sided", action="store_true",
                     help="with --trace-once: the side-resolved trace of the two-faced plates instead")
+    ap.add_argument("--bvh-build", action="store_true",
+                    help="instead of the bench line, print one JSON line comparing the host and device BVH "
+                         "builders (build time, tree, trace rate) on the small-satellite and spacecraft meshes")
     ap.add_argument("--solve-scaling", action="store_true",
                     help="instead of the bench line, print one JSON line with tensor-core GEMM rates and REF "
                          "solve + adjoint times against the FP64 GPU path at N = 512, 2,048 and 10,240")
@@ -672,6 +675,53 @@ def solve_scaling(args):
     return out
 
 
+def bvh_build(args):
+    """Host binned-SAH builder against the device clustering builder: build time (median
+    of 3, host wall clock around the call, uploads included) and the trace rate on each
+    tree (FMA-free, the library's schedule choice), on the small-satellite and spacecraft
+    meshes."""
+    import torch
+    import synth
+    from paper_2511_04277_gb300 import api
+    ctx = api.Context(0)
+    stream = torch.cuda.current_stream()
+    rows = []
+    for name, scale in (("small_sat", 1.0), ("spacecraft", 0.1)):
+        w = synth.workload(name, rays_scale=scale)
+        m = w["mesh"]
+        out = {"workload": name, "triangles": m.n_tris, "rays": int(w["rays"].sum())}
+        for label, kw in (("host", {}), ("device", {"gpu_bvh": 0})):
+            api.Mesh.from_synth(ctx, m, **kw).close()
+            times = []
+            for _ in range(3):
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                mesh = api.Mesh.from_synth(ctx, m, **kw)
+                torch.cuda.synchronize()
+                times.append(1e3 * (time.perf_counter() - t0))
+                if _ < 2:
+                    mesh.close()
+            counts = torch.zeros((m.n_faces, m.n_faces + 1), dtype=torch.int64, device="cuda")
+            api.trace(ctx, mesh, w["rays"], w["seed"], counts=counts)
+            t_tr = []
+            for _ in range(3):
+                counts.zero_()
+                t_tr.append(time_region(torch, lambda: api.trace(ctx, mesh, w["rays"], w["seed"], counts=counts),
+                                        stream))
+            info = mesh.info()
+            _, tst = api.trace_stats(ctx, mesh, w["rays"], w["seed"])
+            out[label] = {"build_ms": round(statistics.median(times), 2), "depth": info["bvh_depth"],
+                          "box_tests_per_ray": round(tst["box_tests"] / tst["rays"], 3),
+                          "tri_tests_per_ray": round(tst["tri_tests"] / tst["rays"], 3),
+                          "nodes": info["bvh_nodes"], "sah_visits": round(info["sah_visits"], 3),
+                          "refill": info["refill"], "trace_ms": round(statistics.median(t_tr), 3),
+                          "rays_per_s": out["rays"] / (statistics.median(t_tr) * 1e-3)}
+            mesh.close()
+        rows.append(out)
+    ctx.close()
+    return {"kind": "bvh_build", "meshes": rows}
+
+
 def trace_once(scale, sided=False):
     import torch
     import synth
@@ -694,6 +744,9 @@ def main():
         return
     if args.solve_scaling:
         print(json.dumps(solve_scaling(args)), flush=True)
+        return
+    if args.bvh_build:
+        print(json.dumps(bvh_build(args)), flush=True)
         return
     out = run_reference(args) if args.impl == "reference" else run_ours(args)
     if out is not None:

@@ -76,22 +76,41 @@ class Context:
 
 
 class Mesh:
-    """A mesh uploaded with its BVH (rg_mesh_create)."""
+    """A mesh uploaded with its BVH: built on the host (rg_mesh_create) or, with
+    ``gpu_bvh`` = the clustering's search radius (0 = its default), on the device
+    (rg_mesh_create_gpu_bvh)."""
 
-    def __init__(self, ctx: Context, verts, tris, tri_face, n_faces: int, use_bvh: int = -1):
+    def __init__(self, ctx: Context, verts, tris, tri_face, n_faces: int, use_bvh: int = -1,
+                 gpu_bvh: int | None = None):
         self.ctx = ctx
         v = np.ascontiguousarray(verts, np.float32)
         t = np.ascontiguousarray(tris, np.int32)
         f = np.ascontiguousarray(tri_face, np.int32)
         h = ctypes.c_void_p()
-        ctx.check(ctx.lib.rg_mesh_create(ctx.handle, _hptr(v), len(v), _hptr(t), len(t), _hptr(f), int(n_faces),
-                                         int(use_bvh), ctypes.byref(h)), "rg_mesh_create")
+        if gpu_bvh is None:
+            ctx.check(ctx.lib.rg_mesh_create(ctx.handle, _hptr(v), len(v), _hptr(t), len(t), _hptr(f), int(n_faces),
+                                             int(use_bvh), ctypes.byref(h)), "rg_mesh_create")
+        else:
+            ctx.check(ctx.lib.rg_mesh_create_gpu_bvh(ctx.handle, _hptr(v), len(v), _hptr(t), len(t), _hptr(f),
+                                                     int(n_faces), int(use_bvh), int(gpu_bvh), ctypes.byref(h)),
+                      "rg_mesh_create_gpu_bvh")
         self.handle = h
         self.n_faces = int(n_faces)
+        self.n_tris = len(t)
 
     @classmethod
-    def from_synth(cls, ctx, m, use_bvh=-1):
-        return cls(ctx, m.verts, m.tris, m.tri_face, m.n_faces, use_bvh)
+    def from_synth(cls, ctx, m, use_bvh=-1, gpu_bvh=None):
+        return cls(ctx, m.verts, m.tris, m.tri_face, m.n_faces, use_bvh, gpu_bvh)
+
+    def bvh(self):
+        """(nodes float32 [bvh_nodes, 16] in the traversal layout, triangle of every
+        traversal-order record int32 [n_tris]) (rg_mesh_get_bvh)."""
+        n = self.info()["bvh_nodes"]
+        nodes = np.zeros((n, 16), np.float32)
+        rec = np.zeros(self.n_tris, np.int32)
+        self.ctx.check(self.ctx.lib.rg_mesh_get_bvh(self.handle, _hptr(nodes) if n else None, _hptr(rec)),
+                       "rg_mesh_get_bvh")
+        return nodes, rec
 
     def info(self) -> dict:
         mi = _native.MeshInfo()

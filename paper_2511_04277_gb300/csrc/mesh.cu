@@ -23,6 +23,7 @@ struct rg_mesh {
   std::vector<double> face_area;
   int64_t nt = 0;
   void* d_buf = nullptr;  // one allocation holding every device array
+  void* d_bvh = nullptr;  // nodes and leaf-ordered records when the BVH was built on the device
 };
 
 const DevMesh& mesh_device_view(const rg_mesh* m) { return m->dev; }
@@ -215,10 +216,10 @@ void pack_tri(float4* dst, F3 v0, F3 e1, F3 e2, int32_t id, int32_t face) {
 
 }  // namespace
 
-extern "C" {
-
-rg_status rg_mesh_create(rg_ctx* ctx, const float* verts_h, int64_t nv, const int32_t* tris_h, int64_t nt,
-                         const int32_t* tri_face_h, int32_t n_faces, int32_t use_bvh, rg_mesh** mesh_out) {
+// gpu_radius > 0: build the BVH on the device (bvh_gpu.cu) with that search radius.
+static rg_status mesh_create(rg_ctx* ctx, const float* verts_h, int64_t nv, const int32_t* tris_h, int64_t nt,
+                      const int32_t* tri_face_h, int32_t n_faces, int32_t use_bvh, int32_t gpu_radius,
+                      rg_mesh** mesh_out) {
   if (!ctx) return RG_ERR_ARG;
   RG_ARG_CHECK(ctx, mesh_out && verts_h && tris_h && tri_face_h, "rg_mesh_create: NULL argument");
   RG_ARG_CHECK(ctx, nv > 0 && nt > 0 && n_faces > 0, "rg_mesh_create: empty mesh");
@@ -301,7 +302,20 @@ rg_status rg_mesh_create(rg_ctx* ctx, const float* verts_h, int64_t nv, const in
   std::vector<BuildNode> nodes;
   int depth = 0;
   float sah_visits = 0.f;
-  if (use_bvh) {
+  GpuBvh gb;
+  const bool on_gpu = use_bvh && gpu_radius > 0;
+  if (on_gpu) {
+    for (int64_t i = 0; i < 3 * nv; ++i)
+      RG_ARG_CHECK(ctx, std::isfinite(verts_h[i]), "rg_mesh_create_gpu_bvh: vertex %lld is not finite",
+                   (long long)(i / 3));
+    rg_status st = gpu_bvh_build(ctx, verts_h, nv, tris_h, tri_face_h, nt, diag, gpu_radius, &gb);
+    if (st != RG_OK) {
+      if (gb.buf) cudaFree(gb.buf);
+      return st;
+    }
+    depth = gb.depth;
+    sah_visits = gb.sah_visits;
+  } else if (use_bvh) {
     std::vector<Box> tbox(nt);
     std::vector<double> cent(3 * (size_t)nt);
     for (int64_t k = 0; k < nt; ++k) {
@@ -336,8 +350,8 @@ rg_status rg_mesh_create(rg_ctx* ctx, const float* verts_h, int64_t nv, const in
   // that a flat child holding the ray's own face lies behind the lifted origin and
   // falls outside the traversal window [-lift/2, best_t + slack]
   const double pad_wide = 1e-4 * diag, pad_flat = 1e-9 * diag;
-  std::vector<float4> hnodes(4 * nodes.size());
-  for (size_t i = 0; i < nodes.size(); ++i) {
+  std::vector<float4> hnodes(on_gpu ? 0 : 4 * nodes.size());
+  for (size_t i = 0; i < hnodes.size() / 4; ++i) {
     float l[2][3], h[2][3];
     for (int s = 0; s < 2; ++s)
       for (int c = 0; c < 3; ++c) {
@@ -354,17 +368,21 @@ rg_status rg_mesh_create(rg_ctx* ctx, const float* verts_h, int64_t nv, const in
     std::memcpy(fv, iv, 16);
     hnodes[4 * i + 3] = make_float4(fv[0], fv[1], fv[2], fv[3]);
   }
-  std::vector<float4> htris(3 * (size_t)nt), hetris(3 * (size_t)nt);
+  std::vector<float4> htris(on_gpu ? 0 : 3 * (size_t)nt), hetris(3 * (size_t)nt);
   for (int64_t q = 0; q < nt; ++q) {
     int32_t k = order[q];
-    pack_tri(&htris[3 * q], tv0[k], te1[k], te2[k], k, tri_face_h[k]);
+    if (!on_gpu) pack_tri(&htris[3 * q], tv0[k], te1[k], te2[k], k, tri_face_h[k]);
     int32_t kf = ftris[q];
     pack_tri(&hetris[3 * q], tv0[kf], te1[kf], te2[kf], kf, tri_face_h[kf]);
   }
 
   rg_mesh* m = new (std::nothrow) rg_mesh();
-  if (!m) return rg::fail(ctx, RG_ERR_OOM, "rg_mesh_create: host allocation");
+  if (!m) {
+    if (gb.buf) cudaFree(gb.buf);
+    return rg::fail(ctx, RG_ERR_OOM, "rg_mesh_create: host allocation");
+  }
   m->ctx = ctx;
+  m->d_bvh = gb.buf;
   m->nt = nt;
   m->face_area = farea;
   rg::Sizer sz;
@@ -372,7 +390,11 @@ rg_status rg_mesh_create(rg_ctx* ctx, const float* verts_h, int64_t nv, const in
   sz.take<uint32_t>(nt); sz.take<int64_t>(n_faces + 1); sz.take<float>(frames.size());
   cudaError_t e = cudaSetDevice(ctx->device);
   if (e == cudaSuccess) e = cudaMalloc(&m->d_buf, sz.off);
-  if (e != cudaSuccess) { delete m; return rg::cuda_fail(ctx, e, "rg_mesh_create: cudaMalloc"); }
+  if (e != cudaSuccess) {
+    if (m->d_bvh) cudaFree(m->d_bvh);
+    delete m;
+    return rg::cuda_fail(ctx, e, "rg_mesh_create: cudaMalloc");
+  }
   rg::Carver cv(m->d_buf);
   float4* d_nodes = cv.take<float4>(hnodes.size());
   float4* d_tris = cv.take<float4>(htris.size());
@@ -390,18 +412,58 @@ rg_status rg_mesh_create(rg_ctx* ctx, const float* verts_h, int64_t nv, const in
   for (auto& u : ups) {
     if (u.n == 0) continue;
     e = cudaMemcpy(u.d, u.h, u.n, cudaMemcpyHostToDevice);
-    if (e != cudaSuccess) { cudaFree(m->d_buf); delete m; return rg::cuda_fail(ctx, e, "rg_mesh_create: upload"); }
+    if (e != cudaSuccess) {
+      cudaFree(m->d_buf);
+      if (m->d_bvh) cudaFree(m->d_bvh);
+      delete m;
+      return rg::cuda_fail(ctx, e, "rg_mesh_create: upload");
+    }
   }
   DevMesh& d = m->dev;
-  d.n_faces = n_faces; d.nt = nt; d.use_bvh = use_bvh; d.n_nodes = (int32_t)nodes.size(); d.depth = depth;
+  d.n_faces = n_faces; d.nt = nt; d.use_bvh = use_bvh;
+  d.n_nodes = on_gpu ? gb.n_nodes : (int32_t)nodes.size();
+  d.depth = depth;
   d.lift = lift; d.t_lo = -0.5f * lift; d.slack = (float)(1e-5 * diag);
   d.sah_visits = sah_visits;
   d.wound_like_face = wound_like_face;
   // refill scheduling pays off when traversals are long; short ones run lock-step
   d.refill = schedule == 3 ? 1 : (schedule == 2 ? 0 : (depth >= kRefillDepth ? 1 : 0));
-  d.nodes = d_nodes; d.tris = d_tris; d.etris = d_etris; d.ethr = d_thr; d.face_start = d_fstart;
+  d.nodes = on_gpu ? gb.nodes : d_nodes;
+  d.tris = on_gpu ? gb.tris : d_tris;
+  d.etris = d_etris; d.ethr = d_thr; d.face_start = d_fstart;
   d.frames = d_frames;
   *mesh_out = m;
+  return RG_OK;
+}
+
+extern "C" {
+
+rg_status rg_mesh_create(rg_ctx* ctx, const float* verts_h, int64_t nv, const int32_t* tris_h, int64_t nt,
+                         const int32_t* tri_face_h, int32_t n_faces, int32_t use_bvh, rg_mesh** mesh_out) {
+  return mesh_create(ctx, verts_h, nv, tris_h, nt, tri_face_h, n_faces, use_bvh, 0, mesh_out);
+}
+
+rg_status rg_mesh_create_gpu_bvh(rg_ctx* ctx, const float* verts_h, int64_t nv, const int32_t* tris_h, int64_t nt,
+                                 const int32_t* tri_face_h, int32_t n_faces, int32_t use_bvh, int32_t radius,
+                                 rg_mesh** mesh_out) {
+  if (!ctx) return RG_ERR_ARG;
+  RG_ARG_CHECK(ctx, radius >= 0 && radius <= 256, "rg_mesh_create_gpu_bvh: radius %d outside [0, 256]", radius);
+  return mesh_create(ctx, verts_h, nv, tris_h, nt, tri_face_h, n_faces, use_bvh, radius ? radius : 16, mesh_out);
+}
+
+rg_status rg_mesh_get_bvh(const rg_mesh* mesh, float* nodes_h, int32_t* record_tri_h) {
+  if (!mesh) return RG_ERR_ARG;
+  const DevMesh& d = mesh->dev;
+  if (cudaSetDevice(mesh->ctx->device) != cudaSuccess) return RG_ERR_CUDA;
+  if (nodes_h && d.use_bvh && d.n_nodes > 0 &&
+      cudaMemcpy(nodes_h, d.nodes, 4 * (size_t)d.n_nodes * sizeof(float4), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return RG_ERR_CUDA;
+  if (record_tri_h) {
+    std::vector<float4> rec(3 * (size_t)d.nt);
+    if (cudaMemcpy(rec.data(), d.tris, rec.size() * sizeof(float4), cudaMemcpyDeviceToHost) != cudaSuccess)
+      return RG_ERR_CUDA;
+    for (int64_t q = 0; q < d.nt; ++q) std::memcpy(&record_tri_h[q], &rec[3 * q + 2].y, sizeof(int32_t));
+  }
   return RG_OK;
 }
 
@@ -410,6 +472,7 @@ rg_status rg_mesh_destroy(rg_mesh* mesh) {
   cudaSetDevice(mesh->ctx->device);
   cudaDeviceSynchronize();
   if (mesh->d_buf) cudaFree(mesh->d_buf);
+  if (mesh->d_bvh) cudaFree(mesh->d_bvh);
   delete mesh;
   return RG_OK;
 }

@@ -33,6 +33,19 @@ struct DevMesh {
 
 constexpr int kTraceStack = 64;
 
+// BVH built on the device (bvh_gpu.cu): n_nodes nodes in the layout above and nt
+// triangle records in leaf order, both in `buf` (cudaMalloc'd, owned by the mesh).
+struct GpuBvh {
+  int32_t n_nodes = 0;
+  int32_t depth = 0;
+  float sah_visits = 0.f;
+  void* buf = nullptr;
+  float4* nodes = nullptr;
+  float4* tris = nullptr;
+};
+rg_status gpu_bvh_build(rg_ctx* ctx, const float* verts_h, int64_t nv, const int32_t* tris_h,
+                        const int32_t* tri_face_h, int64_t nt, double diag, int32_t radius, GpuBvh* out);
+
 struct rg_mesh_impl;
 const DevMesh& mesh_device_view(const rg_mesh* m);
 int mesh_device(const rg_mesh* m);
