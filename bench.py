@@ -676,9 +676,9 @@ def solve_scaling(args):
 
 
 def bvh_build(args):
-    """Host binned-SAH builder against the device clustering builder: build time (median
-    of 3, host wall clock around the call, uploads included) and the trace rate on each
-    tree (FMA-free, the library's schedule choice), on the small-satellite and spacecraft
+    """The host and the device BVH builder (the same tree): build time (median of 3, host
+    wall clock around the call, uploads included) and the trace rate on each tree
+    (FMA-free, the library's schedule choice), on the small-satellite and spacecraft
     meshes."""
     import torch
     import synth
@@ -690,7 +690,7 @@ def bvh_build(args):
         w = synth.workload(name, rays_scale=scale)
         m = w["mesh"]
         out = {"workload": name, "triangles": m.n_tris, "rays": int(w["rays"].sum())}
-        for label, kw in (("host", {}), ("device", {"gpu_bvh": 0})):
+        for label, kw in (("host", {}), ("device", {"gpu_bvh": True})):
             api.Mesh.from_synth(ctx, m, **kw).close()
             times = []
             for _ in range(3):

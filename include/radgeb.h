@@ -95,24 +95,18 @@ rg_status rg_mesh_create(rg_ctx* ctx, const float* verts_h, int64_t nv, const in
                          int64_t nt, const int32_t* tri_face_h, int32_t n_faces, int32_t use_bvh,
                          rg_mesh** mesh_out);
 
-/* rg_mesh_create with the BVH built on the device: parallel locally-ordered clustering
- * (Meister and Bittner 2018) over the triangles sorted by 30-bit Morton codes of their
- * centroids; clusters merge with the neighbour, among `radius` on either side in the
- * list, whose union box has the smallest surface area (the cost the surface-area
- * heuristic charges for a node), ties broken by position, until one is left. Subtrees
- * of at most 4 triangles become leaves; boxes are padded as rg_mesh_create pads them.
- * Deterministic: a mesh always gets the same BVH. Any valid BVH gives bit-identical
- * counts, so the traces of both builders agree bit for bit; the tree, and with it the
- * traversal time, differs.
- *   use_bvh   as rg_mesh_create (0, or -1 with nt <= 64, traces without a BVH and builds
- *             none; nt <= 4 never builds one)
- *   radius    search radius of the clustering, 1..256 (0 = 16)
- * Everything else, including the per-face emission data (built on the host), as
+/* rg_mesh_create with the BVH built on the device: the host builder's binned
+ * surface-area heuristic (16 bins per axis, float binning and fp64 costs, leaves of at
+ * most 4 triangles, median split where no bin split separates a range) evaluated level
+ * by level, one block per range. It makes the host builder's splits, so the node array
+ * is the one rg_mesh_create builds, bit for bit; within a leaf the records may come in
+ * another order (the host partition is not stable). Counts are therefore bit-identical
+ * too. Everything else, including the per-face emission data (built on the host), as
  * rg_mesh_create. Errors: RG_ERR_ARG (also a non-finite vertex), RG_ERR_STACK (depth
- * above the traversal stack), RG_ERR_NUMERIC (the clustering stalled), RG_ERR_CUDA. */
+ * above the traversal stack), RG_ERR_NUMERIC (an inconsistent layout, a defect),
+ * RG_ERR_CUDA. */
 rg_status rg_mesh_create_gpu_bvh(rg_ctx* ctx, const float* verts_h, int64_t nv, const int32_t* tris_h, int64_t nt,
-                                 const int32_t* tri_face_h, int32_t n_faces, int32_t use_bvh, int32_t radius,
-                                 rg_mesh** mesh_out);
+                                 const int32_t* tri_face_h, int32_t n_faces, int32_t use_bvh, rg_mesh** mesh_out);
 
 /* Copy a mesh's BVH to the host for inspection (either builder):
  *   nodes_h       host float [bvh_nodes][16] (may be NULL): the traversal layout, per node

@@ -35,7 +35,7 @@ SIGNATURES = {
     "rg_version": (ctypes.c_char_p, []),
     "rg_launch_count": (i32, [P, ctypes.POINTER(i64)]),
     "rg_mesh_create": (i32, [P, P, i64, P, i64, P, i32, i32, PP]),
-    "rg_mesh_create_gpu_bvh": (i32, [P, P, i64, P, i64, P, i32, i32, i32, PP]),
+    "rg_mesh_create_gpu_bvh": (i32, [P, P, i64, P, i64, P, i32, i32, PP]),
     "rg_mesh_get_bvh": (i32, [P, P, P]),
     "rg_mesh_destroy": (i32, [P]),
     "rg_mesh_get_info": (i32, [P, ctypes.POINTER(MeshInfo)]),

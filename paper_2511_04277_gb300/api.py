@@ -77,29 +77,28 @@ class Context:
 
 class Mesh:
     """A mesh uploaded with its BVH: built on the host (rg_mesh_create) or, with
-    ``gpu_bvh`` = the clustering's search radius (0 = its default), on the device
-    (rg_mesh_create_gpu_bvh)."""
+    ``gpu_bvh``, on the device (rg_mesh_create_gpu_bvh; the same tree)."""
 
     def __init__(self, ctx: Context, verts, tris, tri_face, n_faces: int, use_bvh: int = -1,
-                 gpu_bvh: int | None = None):
+                 gpu_bvh: bool = False):
         self.ctx = ctx
         v = np.ascontiguousarray(verts, np.float32)
         t = np.ascontiguousarray(tris, np.int32)
         f = np.ascontiguousarray(tri_face, np.int32)
         h = ctypes.c_void_p()
-        if gpu_bvh is None:
+        if not gpu_bvh:
             ctx.check(ctx.lib.rg_mesh_create(ctx.handle, _hptr(v), len(v), _hptr(t), len(t), _hptr(f), int(n_faces),
                                              int(use_bvh), ctypes.byref(h)), "rg_mesh_create")
         else:
             ctx.check(ctx.lib.rg_mesh_create_gpu_bvh(ctx.handle, _hptr(v), len(v), _hptr(t), len(t), _hptr(f),
-                                                     int(n_faces), int(use_bvh), int(gpu_bvh), ctypes.byref(h)),
+                                                     int(n_faces), int(use_bvh), ctypes.byref(h)),
                       "rg_mesh_create_gpu_bvh")
         self.handle = h
         self.n_faces = int(n_faces)
         self.n_tris = len(t)
 
     @classmethod
-    def from_synth(cls, ctx, m, use_bvh=-1, gpu_bvh=None):
+    def from_synth(cls, ctx, m, use_bvh=-1, gpu_bvh=False):
         return cls(ctx, m.verts, m.tris, m.tri_face, m.n_faces, use_bvh, gpu_bvh)
 
     def bvh(self):

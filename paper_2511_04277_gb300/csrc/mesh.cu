@@ -98,13 +98,30 @@ struct BuildNode {
   int32_t count[2];
 };
 
+// Binned SAH split of a range of triangles. The binning is float arithmetic, the cost
+// fp64; bvh_gpu.cu evaluates the same expressions in the same order, so both builders
+// make the same splits and build the same tree:
+//   centroid c = 0.5f * (lo + hi) per axis (float box of the float vertices);
+//   per axis with extent x = max c - min c > 0 (float): scale = 16.0f / x and bin
+//   k = (int)((c - min c) * scale), clamped to [0, 15];
+//   cost of the split before bin k: area(left) * n_left + area(right) * n_right with
+//   area = dx dy + dy dz + dz dx of the fp64 box, bins swept from 15 down to 1, axes
+//   0..2, the first strictly smallest cost taken;
+//   the left side takes the bins below the chosen one; when no split separates the
+//   range, its (e - b) / 2 smallest (centroid on the widest axis, triangle index).
+inline float bin_scale(float ext) { return 16.0f / ext; }
+inline int bin_of(float c, float lo, float scale) {
+  int k = (int)((c - lo) * scale);
+  return std::min(std::max(k, 0), 15);
+}
+
 struct Builder {
   const std::vector<Box>& tbox;
-  const std::vector<double>& cent;  // 3 per triangle
+  const std::vector<float>& cent;  // 3 per triangle
   std::vector<int32_t>& order;
   std::vector<BuildNode> nodes;
   int max_depth = 0;
-  Builder(const std::vector<Box>& tb, const std::vector<double>& c, std::vector<int32_t>& o)
+  Builder(const std::vector<Box>& tb, const std::vector<float>& c, std::vector<int32_t>& o)
       : tbox(tb), cent(c), order(o) {}
 
   Box range_box(int32_t b, int32_t e) const {
@@ -116,19 +133,27 @@ struct Builder {
   // Split [b, e) and return the split index.
   int32_t split(int32_t b, int32_t e) {
     constexpr int kBins = 16;
-    Box cb; cb.reset();
-    for (int32_t q = b; q < e; ++q) cb.grow(&cent[3 * (size_t)order[q]]);
+    float clo[3], chi[3];
+    for (int c = 0; c < 3; ++c) { clo[c] = std::numeric_limits<float>::infinity(); chi[c] = -clo[c]; }
+    for (int32_t q = b; q < e; ++q)
+      for (int c = 0; c < 3; ++c) {
+        const float x = cent[3 * (size_t)order[q] + c];
+        clo[c] = std::min(clo[c], x); chi[c] = std::max(chi[c], x);
+      }
+    float ext[3], scale[3];
+    for (int c = 0; c < 3; ++c) {
+      ext[c] = chi[c] - clo[c];
+      scale[c] = ext[c] > 0.0f ? bin_scale(ext[c]) : 0.0f;
+    }
     double best = std::numeric_limits<double>::infinity();
     int best_axis = -1, best_bin = -1;
     for (int ax = 0; ax < 3; ++ax) {
-      double ext = cb.hi[ax] - cb.lo[ax];
-      if (!(ext > 0)) continue;
+      if (!(ext[ax] > 0.0f)) continue;
       Box bb[kBins];
       int cnt[kBins] = {0};
       for (int k = 0; k < kBins; ++k) bb[k].reset();
       for (int32_t q = b; q < e; ++q) {
-        int k = (int)((cent[3 * (size_t)order[q] + ax] - cb.lo[ax]) / ext * kBins);
-        k = std::min(std::max(k, 0), kBins - 1);
+        const int k = bin_of(cent[3 * (size_t)order[q] + ax], clo[ax], scale[ax]);
         cnt[k]++;
         bb[k].grow(tbox[order[q]]);
       }
@@ -150,11 +175,8 @@ struct Builder {
     }
     int32_t mid;
     if (best_axis >= 0) {
-      double ext = cb.hi[best_axis] - cb.lo[best_axis];
       auto it = std::partition(order.begin() + b, order.begin() + e, [&](int32_t t) {
-        int k = (int)((cent[3 * (size_t)t + best_axis] - cb.lo[best_axis]) / ext * kBins);
-        k = std::min(std::max(k, 0), kBins - 1);
-        return k < best_bin;
+        return bin_of(cent[3 * (size_t)t + best_axis], clo[best_axis], scale[best_axis]) < best_bin;
       });
       mid = (int32_t)(it - order.begin());
       if (mid > b && mid < e) return mid;
@@ -162,10 +184,10 @@ struct Builder {
     // degenerate centroids: median split along the widest axis
     int ax = 0;
     for (int c2 = 1; c2 < 3; ++c2)
-      if (cb.hi[c2] - cb.lo[c2] > cb.hi[ax] - cb.lo[ax]) ax = c2;
+      if (ext[c2] > ext[ax]) ax = c2;
     mid = b + (e - b) / 2;
     std::nth_element(order.begin() + b, order.begin() + mid, order.begin() + e, [&](int32_t x, int32_t y) {
-      double cx = cent[3 * (size_t)x + ax], cy = cent[3 * (size_t)y + ax];
+      const float cx = cent[3 * (size_t)x + ax], cy = cent[3 * (size_t)y + ax];
       return cx < cy || (cx == cy && x < y);
     });
     return mid;
@@ -216,10 +238,10 @@ void pack_tri(float4* dst, F3 v0, F3 e1, F3 e2, int32_t id, int32_t face) {
 
 }  // namespace
 
-// gpu_radius > 0: build the BVH on the device (bvh_gpu.cu) with that search radius.
+// on_device: build the BVH on the GPU (bvh_gpu.cu), the same tree as the host builder's.
 static rg_status mesh_create(rg_ctx* ctx, const float* verts_h, int64_t nv, const int32_t* tris_h, int64_t nt,
-                      const int32_t* tri_face_h, int32_t n_faces, int32_t use_bvh, int32_t gpu_radius,
-                      rg_mesh** mesh_out) {
+                             const int32_t* tri_face_h, int32_t n_faces, int32_t use_bvh, bool on_device,
+                             rg_mesh** mesh_out) {
   if (!ctx) return RG_ERR_ARG;
   RG_ARG_CHECK(ctx, mesh_out && verts_h && tris_h && tri_face_h, "rg_mesh_create: NULL argument");
   RG_ARG_CHECK(ctx, nv > 0 && nt > 0 && n_faces > 0, "rg_mesh_create: empty mesh");
@@ -303,12 +325,12 @@ static rg_status mesh_create(rg_ctx* ctx, const float* verts_h, int64_t nv, cons
   int depth = 0;
   float sah_visits = 0.f;
   GpuBvh gb;
-  const bool on_gpu = use_bvh && gpu_radius > 0;
+  const bool on_gpu = use_bvh && on_device;
   if (on_gpu) {
     for (int64_t i = 0; i < 3 * nv; ++i)
       RG_ARG_CHECK(ctx, std::isfinite(verts_h[i]), "rg_mesh_create_gpu_bvh: vertex %lld is not finite",
                    (long long)(i / 3));
-    rg_status st = gpu_bvh_build(ctx, verts_h, nv, tris_h, tri_face_h, nt, diag, gpu_radius, &gb);
+    rg_status st = gpu_bvh_build(ctx, verts_h, nv, tris_h, tri_face_h, nt, diag, &gb);
     if (st != RG_OK) {
       if (gb.buf) cudaFree(gb.buf);
       return st;
@@ -317,7 +339,7 @@ static rg_status mesh_create(rg_ctx* ctx, const float* verts_h, int64_t nv, cons
     sah_visits = gb.sah_visits;
   } else if (use_bvh) {
     std::vector<Box> tbox(nt);
-    std::vector<double> cent(3 * (size_t)nt);
+    std::vector<float> cent(3 * (size_t)nt);
     for (int64_t k = 0; k < nt; ++k) {
       tbox[k].reset();
       for (int v = 0; v < 3; ++v) {
@@ -325,7 +347,7 @@ static rg_status mesh_create(rg_ctx* ctx, const float* verts_h, int64_t nv, cons
         for (int c = 0; c < 3; ++c) p[c] = verts_h[3 * (int64_t)tris_h[3 * k + v] + c];
         tbox[k].grow(p);
       }
-      for (int c = 0; c < 3; ++c) cent[3 * k + c] = 0.5 * (tbox[k].lo[c] + tbox[k].hi[c]);
+      for (int c = 0; c < 3; ++c) cent[3 * k + c] = 0.5f * ((float)tbox[k].lo[c] + (float)tbox[k].hi[c]);
     }
     Builder bld(tbox, cent, order);
     bld.build(0, (int32_t)nt, 1);
@@ -440,15 +462,12 @@ extern "C" {
 
 rg_status rg_mesh_create(rg_ctx* ctx, const float* verts_h, int64_t nv, const int32_t* tris_h, int64_t nt,
                          const int32_t* tri_face_h, int32_t n_faces, int32_t use_bvh, rg_mesh** mesh_out) {
-  return mesh_create(ctx, verts_h, nv, tris_h, nt, tri_face_h, n_faces, use_bvh, 0, mesh_out);
+  return mesh_create(ctx, verts_h, nv, tris_h, nt, tri_face_h, n_faces, use_bvh, false, mesh_out);
 }
 
 rg_status rg_mesh_create_gpu_bvh(rg_ctx* ctx, const float* verts_h, int64_t nv, const int32_t* tris_h, int64_t nt,
-                                 const int32_t* tri_face_h, int32_t n_faces, int32_t use_bvh, int32_t radius,
-                                 rg_mesh** mesh_out) {
-  if (!ctx) return RG_ERR_ARG;
-  RG_ARG_CHECK(ctx, radius >= 0 && radius <= 256, "rg_mesh_create_gpu_bvh: radius %d outside [0, 256]", radius);
-  return mesh_create(ctx, verts_h, nv, tris_h, nt, tri_face_h, n_faces, use_bvh, radius ? radius : 16, mesh_out);
+                                 const int32_t* tri_face_h, int32_t n_faces, int32_t use_bvh, rg_mesh** mesh_out) {
+  return mesh_create(ctx, verts_h, nv, tris_h, nt, tri_face_h, n_faces, use_bvh, true, mesh_out);
 }
 
 rg_status rg_mesh_get_bvh(const rg_mesh* mesh, float* nodes_h, int32_t* record_tri_h) {

@@ -44,7 +44,7 @@ struct GpuBvh {
   float4* tris = nullptr;
 };
 rg_status gpu_bvh_build(rg_ctx* ctx, const float* verts_h, int64_t nv, const int32_t* tris_h,
-                        const int32_t* tri_face_h, int64_t nt, double diag, int32_t radius, GpuBvh* out);
+                        const int32_t* tri_face_h, int64_t nt, double diag, GpuBvh* out);
 
 struct rg_mesh_impl;
 const DevMesh& mesh_device_view(const rg_mesh* m);

@@ -1,9 +1,9 @@
-"""The device-built BVH (rg_mesh_create_gpu_bvh) against the oracle and against the
-structural rules a traversal relies on: counts bit-identical to the oracle's (any
-valid BVH gives the same closest hits), every triangle in exactly one leaf, every
-triangle inside the box of every node above it, depth within the traversal stack, the
-same tree on every build, and a tree quality (expected node visits of a random line)
-close to the host builder's."""
+"""The device-built BVH (rg_mesh_create_gpu_bvh) against the host builder, the oracle
+and the structural rules a traversal relies on: the host builder's node array bit for
+bit with the same triangles in every leaf, counts bit-identical to the oracle's, every
+triangle in exactly one leaf and inside the box of every node above it, depth within
+the traversal stack, the same tree on every build, and the median split of ranges that
+no bin split separates."""
 import time
 
 import numpy as np
@@ -54,27 +54,47 @@ def check_bvh(mesh, m):
     return depth
 
 
-@pytest.mark.parametrize("name", ["plates16", "small_sat", "spacecraft"])
-def test_structure_of_both_builders(rg_ctx, name):
-    m = synth.plates(16) if name == "plates16" else getattr(synth, name)()
+def same_tree(host, dev):
+    """The device tree is the host tree: equal node arrays, the same triangles per leaf."""
+    (nh, rh), (nd, rd) = host.bvh(), dev.bvh()
+    assert np.array_equal(nh.view(np.uint32), nd.view(np.uint32))
+    ints = nh[:, 12:16].copy().view(np.int32)
+    for s in range(2):
+        for ref, cnt in zip(ints[:, s], ints[:, 2 + s]):
+            if cnt > 0:
+                assert sorted(rh[ref:ref + cnt]) == sorted(rd[ref:ref + cnt])
+
+
+def coincident(k=40):
+    """k copies of one triangle in one face plus a square: no bin split separates the copies."""
+    verts = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0], [2, 0, 1], [3, 0, 1], [3, 1, 1], [2, 1, 1]], np.float32)
+    tris = [[0, 1, 2]] * k + [[3, 4, 5], [3, 5, 6]]
+    return synth.meshes.Mesh(name="coincident", verts=verts, tris=np.array(tris, np.int32),
+                             tri_face=np.array([0] * k + [1, 1], np.int32), n_faces=2,
+                             patch_of_face=np.arange(2, dtype=np.int32), n_patches=2)
+
+
+@pytest.mark.parametrize("name", ["plates16", "small_sat", "spacecraft", "coincident"])
+def test_device_tree_is_the_host_tree(rg_ctx, name):
+    m = {"plates16": lambda: synth.plates(16), "coincident": coincident}.get(name, getattr(synth, name, None))()
     t0 = time.perf_counter()
-    host = api.Mesh.from_synth(rg_ctx, m)
+    host = api.Mesh.from_synth(rg_ctx, m, use_bvh=1)
     t1 = time.perf_counter()
-    dev = api.Mesh.from_synth(rg_ctx, m, gpu_bvh=0)
+    dev = api.Mesh.from_synth(rg_ctx, m, use_bvh=1, gpu_bvh=True)
     t2 = time.perf_counter()
     dh, dd = check_bvh(host, m), check_bvh(dev, m)
     ih, idv = host.info(), dev.info()
-    print(f"{name}: {m.n_tris} triangles; host {1e3 * (t1 - t0):.1f} ms depth {dh} nodes {ih['bvh_nodes']} "
-          f"visits {ih['sah_visits']:.2f}; device {1e3 * (t2 - t1):.1f} ms depth {dd} nodes {idv['bvh_nodes']} "
-          f"visits {idv['sah_visits']:.2f}")
-    # tree quality: expected node visits of a random line within 30 % of the host builder's
-    assert idv["sah_visits"] <= 1.3 * ih["sah_visits"]
+    print(f"{name}: {m.n_tris} triangles; host {1e3 * (t1 - t0):.1f} ms, device {1e3 * (t2 - t1):.1f} ms; "
+          f"depth {dh}, {ih['bvh_nodes']} nodes, visits {ih['sah_visits']:.4f} / {idv['sah_visits']:.4f}")
+    assert (dd, idv["bvh_nodes"], idv["refill"]) == (dh, ih["bvh_nodes"], ih["refill"])
+    assert abs(idv["sah_visits"] - ih["sah_visits"]) <= 1e-5 * ih["sah_visits"]
+    same_tree(host, dev)
 
 
 def test_device_bvh_is_deterministic(rg_ctx):
     m = synth.spacecraft()
-    a = api.Mesh.from_synth(rg_ctx, m, gpu_bvh=16).bvh()
-    b = api.Mesh.from_synth(rg_ctx, m, gpu_bvh=16).bvh()
+    a = api.Mesh.from_synth(rg_ctx, m, gpu_bvh=True).bvh()
+    b = api.Mesh.from_synth(rg_ctx, m, gpu_bvh=True).bvh()
     assert np.array_equal(a[0].view(np.uint32), b[0].view(np.uint32)) and np.array_equal(a[1], b[1])
 
 
@@ -84,7 +104,7 @@ def test_counts_bit_exact_with_device_bvh(rg_ctx, schedule):
     rays = np.full(m.n_faces, 3000, np.int64)
     rays[5] = 0
     rays[77] = 65536 + 9
-    mesh = api.Mesh.from_synth(rg_ctx, m, use_bvh=schedule, gpu_bvh=0)
+    mesh = api.Mesh.from_synth(rg_ctx, m, use_bvh=schedule, gpu_bvh=True)
     assert mesh.info()["refill"] == (schedule == 3)
     g = api.trace(rg_ctx, mesh, rays, 4).cpu().numpy()
     o = mcrt.trace_counts(m.verts, m.tris, m.tri_face, m.n_faces, rays, 4)
@@ -99,7 +119,7 @@ def test_counts_bit_exact_with_device_bvh(rg_ctx, schedule):
 def test_device_bvh_rows_against_the_oracle(rg_ctx, name, rows):
     w = synth.workload(name, rays_scale=0.05)
     m = w["mesh"]
-    dev = api.Mesh.from_synth(rg_ctx, m, gpu_bvh=0)
+    dev = api.Mesh.from_synth(rg_ctx, m, gpu_bvh=True)
     host = api.Mesh.from_synth(rg_ctx, m)
     g = api.trace(rg_ctx, dev, w["rays"], w["seed"]).cpu().numpy()
     h = api.trace(rg_ctx, host, w["rays"], w["seed"]).cpu().numpy()
@@ -109,15 +129,21 @@ def test_device_bvh_rows_against_the_oracle(rg_ctx, name, rows):
         assert np.array_equal(g[r], o[r]), r
 
 
-def test_small_meshes_and_radius(rg_ctx):
+def test_small_meshes(rg_ctx):
     for n_sub in (2, 3, 5):                                          # 16, 36, 100 triangles
         m = synth.perpendicular_squares(n_sub)
-        mesh = api.Mesh.from_synth(rg_ctx, m, use_bvh=1, gpu_bvh=1)   # radius 1: neighbours only
+        mesh = api.Mesh.from_synth(rg_ctx, m, use_bvh=1, gpu_bvh=True)
         check_bvh(mesh, m)
+        same_tree(api.Mesh.from_synth(rg_ctx, m, use_bvh=1), mesh)
         rays = np.full(m.n_faces, 20000, np.int64)
         g = api.trace(rg_ctx, mesh, rays, 8).cpu().numpy()
         assert np.array_equal(g, mcrt.trace_counts(m.verts, m.tris, m.tri_face, m.n_faces, rays, 8, use_bvh=False))
-    cube = api.Mesh.from_synth(rg_ctx, synth.cube(), gpu_bvh=0)      # 12 triangles, -1: no BVH
+    m = coincident()
+    mesh = api.Mesh.from_synth(rg_ctx, m, use_bvh=1, gpu_bvh=True)
+    rays = np.full(2, 20000, np.int64)
+    g = api.trace(rg_ctx, mesh, rays, 8).cpu().numpy()
+    assert np.array_equal(g, mcrt.trace_counts(m.verts, m.tris, m.tri_face, 2, rays, 8, use_bvh=False))
+    cube = api.Mesh.from_synth(rg_ctx, synth.cube(), gpu_bvh=True)   # 12 triangles, -1: no BVH
     assert cube.info()["bvh_nodes"] == 0
 
 
@@ -126,7 +152,5 @@ def test_device_builder_refuses_bad_input(rg_ctx):
     v = m.verts.copy()
     v[3, 1] = np.nan
     with pytest.raises(RadgebError, match="RG_ERR_ARG"):
-        api.Mesh(rg_ctx, v, m.tris, m.tri_face, m.n_faces, use_bvh=1, gpu_bvh=0)
-    with pytest.raises(RadgebError, match="RG_ERR_ARG"):
-        api.Mesh(rg_ctx, m.verts, m.tris, m.tri_face, m.n_faces, use_bvh=1, gpu_bvh=300)
+        api.Mesh(rg_ctx, v, m.tris, m.tri_face, m.n_faces, use_bvh=1, gpu_bvh=True)
     torch.cuda.synchronize()
