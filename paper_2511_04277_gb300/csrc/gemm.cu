@@ -49,6 +49,17 @@ template <int BN, int kStages, class Epi, bool kComp, bool kBF16>
 rg_status launch(rg_ctx* ctx, const CUtensorMap& ma, const CUtensorMap& mb, const GemmArgs& args, const Epi& epi,
                  cudaStream_t s, int grid_z = 1);
 
+// Tile width: the widest of 256 / 128 / 64 that still gives every SM two tiles. A wider
+// tile reuses each A tile over more columns: a 128 x 128 x 64 step moves 32 KB for 2.1
+// MFLOP (64 FLOP/B, ~35 TB/s from L2 at the tensor peak), a 128 x 256 x 64 step 48 KB
+// for 4.2 MFLOP (87 FLOP/B).
+int tile_width(const rg_ctx* ctx, int M, int N) {
+  const int64_t tm = (M + BM - 1) / BM, want = 2 * (int64_t)ctx->sm_count;
+  if (tm * ((N + 255) / 256) >= want) return 256;
+  if (tm * ((N + 127) / 128) >= want) return 128;
+  return 64;
+}
+
 }  // namespace
 
 template <class Epi>
@@ -56,18 +67,20 @@ rg_status gemm(rg_ctx* ctx, bool bf16, const void* A, int64_t lda, const void* B
                const Epi& epi, cudaStream_t s) {
   if (M <= 0 || N <= 0) return RG_OK;
   if (K <= 0) return rg::fail(ctx, RG_ERR_ARG, "gemm: K = %d", K);
-  // 64-wide tiles when 128-wide ones would leave most SMs idle
-  const bool narrow = (int64_t)((M + BM - 1) / BM) * ((N + 127) / 128) < 2 * ctx->sm_count;
+  const int bn = tile_width(ctx, M, N);
   CUtensorMap ma, mb;
   rg_status st = encode_kmajor(ctx, &ma, A, bf16, M, K, lda, BM);
-  if (st == RG_OK) st = encode_kmajor(ctx, &mb, B, bf16, N, K, ldb, narrow ? 64 : 128);
+  if (st == RG_OK) st = encode_kmajor(ctx, &mb, B, bf16, N, K, ldb, bn);
   if (st != RG_OK) return st;
   GemmArgs args{M, N, K, 0, ctx->d_scratch + kGemmErrorSlot};
-  if (narrow)
+  if (bn == 64)
     return bf16 ? launch<64, 6, Epi, false, true>(ctx, ma, mb, args, epi, s)
                 : launch<64, 6, Epi, false, false>(ctx, ma, mb, args, epi, s);
-  return bf16 ? launch<128, 4, Epi, false, true>(ctx, ma, mb, args, epi, s)
-              : launch<128, 4, Epi, false, false>(ctx, ma, mb, args, epi, s);
+  if (bn == 128)
+    return bf16 ? launch<128, 4, Epi, false, true>(ctx, ma, mb, args, epi, s)
+                : launch<128, 4, Epi, false, false>(ctx, ma, mb, args, epi, s);
+  return bf16 ? launch<256, 4, Epi, false, true>(ctx, ma, mb, args, epi, s)
+              : launch<256, 4, Epi, false, false>(ctx, ma, mb, args, epi, s);
 }
 
 template rg_status gemm<EpiTwoIMinusT<__nv_bfloat16>>(rg_ctx*, bool, const void*, int64_t, const void*, int64_t, int,
@@ -106,15 +119,18 @@ rg_status gemm_f32(rg_ctx* ctx, bool bf16, const void* A, int64_t lda, const voi
                    int K, float* C, int64_t ldc, float alpha, float beta, cudaStream_t s) {
   if (M <= 0 || N <= 0) return RG_OK;
   if (K <= 0) return rg::fail(ctx, RG_ERR_ARG, "gemm_f32: K = %d", K);
-  constexpr int BN = 128;
+  const int bn = tile_width(ctx, M, N) == 256 ? 256 : 128;
   CUtensorMap ma, mb;
   rg_status st = encode_kmajor(ctx, &ma, A, bf16, M, K, lda, BM);
-  if (st == RG_OK) st = encode_kmajor(ctx, &mb, B, bf16, N, K, ldb, BN);
+  if (st == RG_OK) st = encode_kmajor(ctx, &mb, B, bf16, N, K, ldb, bn);
   if (st != RG_OK) return st;
   GemmArgs args{M, N, K, 0, ctx->d_scratch + kGemmErrorSlot};
   EpiF32 epi{C, ldc, alpha, beta};
-  return bf16 ? launch<BN, 4, EpiF32, false, true>(ctx, ma, mb, args, epi, s)
-              : launch<BN, 4, EpiF32, false, false>(ctx, ma, mb, args, epi, s);
+  if (bn == 256)
+    return bf16 ? launch<256, 4, EpiF32, false, true>(ctx, ma, mb, args, epi, s)
+                : launch<256, 4, EpiF32, false, false>(ctx, ma, mb, args, epi, s);
+  return bf16 ? launch<128, 4, EpiF32, false, true>(ctx, ma, mb, args, epi, s)
+              : launch<128, 4, EpiF32, false, false>(ctx, ma, mb, args, epi, s);
 }
 
 namespace {

@@ -56,6 +56,20 @@ def test_tc_gemm_matches_fp64_of_rounded_operands(rg_ctx, M, N, K, dt):
     assert err <= 2e-5 * (A.double().abs() @ B.double().abs().T).max().item()
 
 
+@pytest.mark.parametrize("dt", [torch.bfloat16, torch.float16])
+def test_tc_gemm_wide_tiles_with_ragged_edges(rg_ctx, dt):
+    """Enough tiles for the 128 x 256 tile path (two per SM), with partial tiles on both edges."""
+    M, N, K = 5000, 4931, 200
+    g = torch.Generator().manual_seed(7)
+    A = torch.randn(M, K, generator=g).to(dt)
+    B = torch.randn(N, K, generator=g).to(dt)
+    C0 = torch.randn(M, N, generator=g, dtype=torch.float32)
+    C = api.tc_gemm(rg_ctx, A.cuda(), B.cuda(), C0.clone().cuda(), alpha=-1.0, beta=1.0).cpu().double()
+    ref = C0.double() - A.double() @ B.double().T
+    scale = (A.double().abs() @ B.double().abs().T).max().item()
+    assert (C - ref).abs().max().item() <= 2e-5 * scale
+
+
 def test_tc_gemm_residual_is_fp64_accurate(rg_ctx):
     rng = np.random.default_rng(0)
     M, N, K = 256, 190, 1536
