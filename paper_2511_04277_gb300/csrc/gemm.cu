@@ -107,7 +107,7 @@ rg_status launch(rg_ctx* ctx, const CUtensorMap& ma, const CUtensorMap& mb, cons
     configured_device = ctx->device;
   }
   dim3 grid(((args.N + BN - 1) / BN) * ((args.M + BM - 1) / BM), 1, grid_z);
-  kern<<<grid, kThreads, smem, s>>>(ma, mb, args, epi);
+  kern<<<grid, cta_threads<BN, kComp>(), smem, s>>>(ma, mb, args, epi);
   ++ctx->launches;
   RG_CUDA_TRY(ctx, cudaGetLastError());
   return RG_OK;
@@ -222,18 +222,21 @@ rg_status gemm_residual(rg_ctx* ctx, const void* A, int64_t lda, const void* B, 
   if (M <= 0 || N <= 0) return RG_OK;
   if (K <= 0) return rg::fail(ctx, RG_ERR_ARG, "gemm_residual: K = %d", K);
   constexpr int BN = 64;
+  // 128-wide tiles (two epilogue groups) where they still give every SM two tiles
+  const bool wide = (int64_t)((M + BM - 1) / BM) * ((N + 127) / 128) >= 2 * (int64_t)ctx->sm_count;
   CUtensorMap ma, mb;
   rg_status st = encode_kmajor(ctx, &ma, A, true, M, K, lda, BM);
-  if (st == RG_OK) st = encode_kmajor(ctx, &mb, B, true, N, K, ldb, BN);
+  if (st == RG_OK) st = encode_kmajor(ctx, &mb, B, true, N, K, ldb, wide ? 128 : BN);
   if (st != RG_OK) return st;
   GemmArgs args{M, N, K, chunk_blocks, ctx->d_scratch + kGemmErrorSlot};
-  const int splits = split_ws ? residual_splits(ctx, M, N, K, chunk_blocks, split_max) : 1;
+  const int splits = (split_ws && !wide) ? residual_splits(ctx, M, N, K, chunk_blocks, split_max) : 1;
   if (splits <= 1) {
     if (lead_blocks > 0 && tail_chunk_blocks > 0 && chunk_blocks > 0 && lead_blocks % chunk_blocks == 0) {
       args.lead_blocks = lead_blocks;
       args.tail_chunk_blocks = tail_chunk_blocks;
     }
     EpiResidual epi{out, E, X, dl, ld, red, colmax, nonfinite};
+    if (wide) return launch<128, 4, EpiResidual, true, true>(ctx, ma, mb, args, epi, s, 1);
     return launch<BN, 6, EpiResidual, true, true>(ctx, ma, mb, args, epi, s, 1);
   }
   const int kb = (K + BK - 1) / BK;

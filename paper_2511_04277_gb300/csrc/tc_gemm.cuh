@@ -1,13 +1,17 @@
 // tcgen05 GEMM for sm_103a: D[M x N] = A[M x K] * B[N x K]^T, 16-bit operands (bf16 or
 // fp16, both K-major: row-major with K contiguous), fp32 accumulation in tensor memory.
 //
-// One CTA computes one BM x BN tile (BM = 128). Warp roles (192 threads):
+// One CTA computes one BM x BN tile (BM = 128). Warp roles (192 threads; 320 for
+// compensated 128-wide tiles):
 //   warp 0      TMA producer: 64-wide K blocks of A and B into a ring of smem stages
 //               (128-byte swizzle), completion signalled on full[s] mbarriers;
 //   warp 1      allocates TMEM, one elected thread issues tcgen05.mma (K = 16 each)
 //               and commits to empty[s] (stage free) and acc_full[b] (accumulator ready);
 //   warps 2..5  epilogue: tcgen05.ld of the accumulator (warp w reads TMEM lanes
-//               32*(w%4) .. +31, i.e. tile rows), then the Epi functor writes the result.
+//               32*(w%4) .. +31, i.e. tile rows), then the Epi functor writes the result;
+//               a compensated tile wider than 64 columns has one group of four epilogue
+//               warps per 64 columns (warps 6..9 take columns 64..127), so that a thread
+//               keeps 64 compensated sums.
 // The K loop can be cut into chunks of kChunkBlocks K blocks: each chunk is accumulated
 // in fp32 in one of two TMEM buffers and handed to the epilogue, which folds it into a
 // compensated (Kahan) fp32 sum; this keeps the long reductions of the refinement
@@ -30,6 +34,11 @@ namespace tc {
 constexpr int BM = 128;
 constexpr int BK = 64;  // one 128-byte swizzle atom of 16-bit elements
 constexpr int kThreads = 192;
+// epilogue warp groups of a tile: compensated tiles give every group 64 columns
+template <int BN, bool kCompensated>
+__host__ __device__ constexpr int epi_groups() { return (kCompensated && BN > 64) ? BN / 64 : 1; }
+template <int BN, bool kCompensated>
+__host__ __device__ constexpr int cta_threads() { return 64 + 128 * epi_groups<BN, kCompensated>(); }
 constexpr int kGroupM = 8;  // row tiles per rasterisation group
 constexpr uint64_t kWaitNs = 2000000000ull;  // a wait gives up after 2 s
 
@@ -348,11 +357,13 @@ struct GemmArgs {
 };
 
 template <int BN, int kStages, class Epi, bool kCompensated, bool kBF16>
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __launch_bounds__(cta_threads<BN, kCompensated>(), 1)
     gemm_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_b,
                 const GemmArgs args, const Epi epi) {
   static_assert(BN == 64 || BN == 128 || BN == 256, "tile width");
-  static_assert(!kCompensated || BN == 64, "the compensated epilogue keeps 2 x BN registers per thread");
+  constexpr int kGroups = epi_groups<BN, kCompensated>();
+  constexpr int kEpiCols = BN / kGroups;  // columns of one epilogue thread
+  static_assert(!kCompensated || kEpiCols == 64, "the compensated epilogue keeps 2 x 64 registers per thread");
   constexpr uint32_t kABytes = BM * BK * 2, kBBytes = BN * BK * 2;
   constexpr uint32_t kAccCols = kCompensated ? 2 * BN : BN;
   constexpr uint32_t kTmemCols = kAccCols <= 32 ? 32 : (kAccCols <= 64 ? 64 : (kAccCols <= 128 ? 128 : (kAccCols <= 256 ? 256 : 512)));
@@ -370,7 +381,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   __shared__ int s_abort;
   __shared__ int s_consumed;             // K blocks whose stage the MMA thread has taken
   using StageT = typename std::conditional<kCompensated, double, float>::type;
-  __shared__ StageT s_stage[4][32][33];  // per epilogue warp: coalescing block
+  __shared__ StageT s_stage[4 * kGroups][32][33];  // per epilogue warp: coalescing block
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   // grouped rasterisation of the 1-D grid: kGroupM row tiles at a time, column tiles
@@ -404,7 +415,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&acc_full[b], 1);
-      mbar_init(&acc_empty[b], 128);
+      mbar_init(&acc_empty[b], 128 * kGroups);
     }
     mbar_init(drain, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -464,11 +475,13 @@ __global__ void __launch_bounds__(kThreads, 1)
       mbar_wait(drain, 0);
     }
   } else {
-    // ---------------- epilogue warps 2..5
+    // ---------------- epilogue warps 2 .. 1 + 4 kGroups
+    const int ew = warp - 2;
     const int quarter = warp & 3;  // TMEM lanes 32*quarter .. +31
+    const int cbase = (ew >> 2) * kEpiCols;
     const int row0 = m0 + quarter * 32;
     const uint32_t lane_addr = (uint32_t)(quarter * 32) << 16;
-    StageT (*stage)[33] = s_stage[quarter];
+    StageT (*stage)[33] = s_stage[ew];
     if constexpr (!kCompensated) {
       if (mbar_wait(&acc_full[0], 0)) {
         tc_fence_after();
@@ -482,9 +495,9 @@ __global__ void __launch_bounds__(kThreads, 1)
         *abort_flag = 1;
       }
     } else {
-      float sum[BN], comp[BN];
+      float sum[kEpiCols], comp[kEpiCols];
 #pragma unroll
-      for (int i = 0; i < BN; ++i) {
+      for (int i = 0; i < kEpiCols; ++i) {
         sum[i] = 0.f;
         comp[i] = 0.f;
       }
@@ -494,9 +507,9 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (!mbar_wait(&acc_full[b], (c >> 1) & 1)) { *abort_flag = 1; ok = false; break; }
         tc_fence_after();
 #pragma unroll
-        for (int c0 = 0; c0 < BN; c0 += 32) {
+        for (int c0 = 0; c0 < kEpiCols; c0 += 32) {
           float v[32];
-          tmem_ld32(tmem_base + lane_addr + (uint32_t)(b * BN + c0), v);
+          tmem_ld32(tmem_base + lane_addr + (uint32_t)(b * BN + cbase + c0), v);
 #pragma unroll
           for (int i = 0; i < 32; ++i) {  // Kahan: sum + v, the lost low part kept in comp
             float y = v[i] - comp[c0 + i];
@@ -510,11 +523,11 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
       if (ok) {
 #pragma unroll
-        for (int c0 = 0; c0 < BN; c0 += 32) {
+        for (int c0 = 0; c0 < kEpiCols; c0 += 32) {
           double v[32];
 #pragma unroll
           for (int i = 0; i < 32; ++i) v[i] = (double)sum[c0 + i] - (double)comp[c0 + i];
-          epi.store(row0, lane, n0 + c0, args.M, args.N, v, stage, blockIdx.z);
+          epi.store(row0, lane, n0 + cbase + c0, args.M, args.N, v, stage, blockIdx.z);
         }
       }
     }

@@ -86,6 +86,26 @@ def test_tc_gemm_residual_is_fp64_accurate(rg_ctx):
     assert np.abs(plain - prod).max() <= 2e-7 * np.abs(prod).max()
 
 
+def test_tc_gemm_residual_wide_tiles_are_fp64_accurate(rg_ctx):
+    """Enough tiles for the 128-wide compensated path (two epilogue groups), partial tiles
+    on both edges. Within each 128-long chunk the tensor cores accumulate in fp32 rounding
+    toward zero; with all-positive operands that bias is coherent, about 1e-7 relative per
+    entry, and over 6.4 million entries its tail reaches past 2e-7 of the largest one."""
+    rng = np.random.default_rng(1)
+    M, N, K = 2593, 2483, 768
+    A = torch.from_numpy(rng.random((M, K))).to(torch.bfloat16)
+    B = torch.from_numpy(rng.random((N, K))).to(torch.bfloat16)
+    Ed = rng.random((M, N))
+    Xd = rng.random((M, N))
+    dl = rng.uniform(0.5, 1.5, M)
+    out = api.tc_gemm_residual(rg_ctx, A.cuda(), B.cuda(), _dev(Ed), _dev(Xd), _dev(dl), chunk_k=128).cpu().numpy()
+    prod = A.double().numpy() @ B.double().numpy().T
+    ref = Ed - Xd + dl[:, None] * prod
+    err = np.abs(out - ref)
+    assert err.max() <= 4e-7 * np.abs(dl[:, None] * prod).max()
+    assert np.median(err / np.abs(dl[:, None] * prod)) <= 2e-7      # a bias, not a wrong column group
+
+
 # ------------------------------------------------------------------ REFs
 def test_gebhart_plates_example(rg_ctx):
     F = load_matrix("plates_F.txt")
