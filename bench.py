@@ -299,6 +299,14 @@ def fp64_solve(torch, F, eps, rho, A, Q):
     return B.detach(), T.detach(), e.grad, r.grad
 
 
+def load_peaks():
+    """MEASURED_PEAKS.json (the machine's measured HBM copy and bf16 GEMM rates), or {}."""
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        return {}
+
+
 def l2_flusher(torch, device):
     buf = torch.empty(256 << 20, dtype=torch.uint8, device=device)
 
@@ -423,11 +431,7 @@ def run_ours(args):
                                                            counts=pipe.counts), stream))
         trace_ms = statistics.median(tr)
         ops = (st["rays"] * OPS_PER_RAY + st["box_tests"] * OPS_PER_BOX + st["tri_tests"] * OPS_PER_TRI)
-        peaks = {}
-        try:
-            peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-        except OSError:
-            pass
+        peaks = load_peaks()
         sm_count = torch.cuda.get_device_properties(device).multi_processor_count
         max_mhz = float(peaks.get("sm_max_mhz", 2070.0))
         peak_tops = sm_count * 128 * max_mhz * 1e6 / 1e12
@@ -610,7 +614,8 @@ def solve_scaling(args):
         torch.cuda.synchronize()
         return statistics.median(time_region(torch, fn, torch.cuda.current_stream()) for _ in range(reps))
 
-    out = {"kind": "solve_scaling", "precision": SOLVE_PRECISION, "gemm": [], "solves": []}
+    out = {"kind": "solve_scaling", "precision": SOLVE_PRECISION, "gemm": [], "enforce": [], "solves": []}
+    peaks = load_peaks()
     g = torch.Generator().manual_seed(0)
     for M, N, K in ((4096, 4096, 4096), (10240, 10240, 10240)):
         A = torch.randn(M, K, generator=g).to(torch.bfloat16).to(dev)
@@ -634,8 +639,28 @@ def solve_scaling(args):
         mesh = api.Mesh.from_synth(ctx, w["mesh"])
         rays = torch.as_tensor(w["rays"], device=dev)
         F = api.counts_to_F(ctx, api.trace(ctx, mesh, w["rays"], w["seed"]), rays)
-        api.enforce_iterative(ctx, F, torch.as_tensor(mesh.face_areas(), device=dev), tol=1e-12)
+        areas = torch.as_tensor(mesh.face_areas(), device=dev)
         n = F.shape[0]
+        # the iterative enforcer on this F: HBM bound above N = 2,048 (16 B per entry and
+        # iteration: eta read and written once), L2 sized below
+        F0 = F.clone()
+        t_e, iters = [], 0
+        for _ in range(4):
+            F.copy_(F0)
+            torch.cuda.synchronize()
+            box = {}
+            t = time_region(torch, lambda: box.__setitem__("it", api.enforce_iterative(ctx, F, areas, tol=1e-12)),
+                            torch.cuda.current_stream())
+            t_e.append(t)
+            iters = box["it"]
+        ms_e = statistics.median(t_e[1:])
+        gbs = 16.0 * n * (n + 1) * iters / (ms_e * 1e-3) / 1e9
+        hbm = float(peaks.get("hbm_gbs", 6800.0))
+        out["enforce"].append({"workload": name, "n": n, "iterations": iters, "ms": round(ms_e, 3),
+                               "ms_per_iteration": round(ms_e / iters, 4), "achieved_gbs": round(gbs, 1),
+                               "peak_gbs": hbm, "frac": round(gbs / hbm, 4),
+                               "bytes_per_iteration": 16 * n * (n + 1)})
+        del F0
         eps = torch.as_tensor(w["eps"][:S], device=dev)
         rho = torch.as_tensor(w["rho"][:S], device=dev)
         reps = 1 if n > 4096 else 5

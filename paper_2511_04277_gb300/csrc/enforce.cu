@@ -64,83 +64,143 @@ struct EnforceState {
   int32_t pad;
 };
 
+// 8-byte asynchronous global -> shared copy (rows of H, ld = n + 1 doubles, are only
+// 8-byte aligned, so neither 16-byte copies nor TMA apply): every thread keeps its
+// 2 T^2 / kThreads copies in flight at once.
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((uint32_t)__cvta_generic_to_shared(smem)),
+               "l"(gmem)
+               : "memory");
+}
+
 // Symmetrisation of the tile pair (I, J), I <= J (one block): T is the tile edge; kW:
 // weights from kappa [n][n] (kappa_ij multiplies eta_ij), else 1/2. Folds the block's
-// largest reciprocity defect into *d_recip.
+// largest reciprocity defect into *d_recip and writes the tiles' row sums to P.
+//
+// GB300 runs fp64 at a small fraction of its fp32 rate, and this pass is bound by it
+// unless the fp64 work per entry is small, so with equal weights a pair of entries
+// costs six fp64 operations: the tiles hold e_ij = (s_i / 2) H_ij = eta_ij / 2 exactly
+// (halving commutes with rounding; the raw tiles arrive by asynchronous copies and each
+// entry is scaled once, where the values are formed), the symmetrised value is the single sum
+// v_ij = e_ij + e_ji (= (eta_ij + eta_ji) / 2 bit for bit), the defect |e_ij - e_ji| is
+// maximised on its bit pattern, and since v_ji = e_ji + e_ij = v_ij the tile (J, I) is
+// the transpose of (I, J): its values are read transposed from shared memory. With
+// weights both tiles are computed. The values pass through registers into the tile
+// arrays, which the global writes and the row sums then read; the row sums run over a
+// rotated column order so that the 16 lanes of a half-warp read 16 different banks (the
+// row stride is T + 1 doubles: bank of (r, c) = (r + c) mod 16), in a fixed order that
+// is the same on both paths (kappa = 1/2 given as weights gives the same bits).
 template <int T, bool kW>
 __device__ __forceinline__ void sym_tile(double* __restrict__ H, const double* __restrict__ s,
                                          const double* __restrict__ kappa, int32_t n, double* __restrict__ P, int I,
                                          int J, unsigned long long* d_recip) {
+  static_assert(T == 64 || T == 32, "bank rotation for 64- and 32-wide tiles");
+  constexpr int kPer = T * T / kThreads;  // entries per thread
   __shared__ double A[T][T + 1];
   __shared__ double B[T][T + 1];
-  __shared__ double red[kThreads];
+  __shared__ double sI[T], sJ[T];  // the tiles' row scales, halved for equal weights
+  __shared__ unsigned long long red[kThreads / 32];
   const int64_t ld = n + 1;
   const int tid = threadIdx.x;
   const bool off = I != J;
+  const double h = kW ? 1.0 : 0.5;
   for (int e = tid; e < T * T; e += kThreads) {
     int r = e / T, c = e % T;
     int64_t i = (int64_t)I * T + r, j = (int64_t)J * T + c;
-    A[r][c] = (i < n && j < n) ? __ldcg(s + i) * H[i * ld + j] : 0.0;
+    if (i < n && j < n) cp_async8(&A[r][c], H + i * ld + j); else A[r][c] = 0.0;
     if (off) {
       int64_t i2 = (int64_t)J * T + r, j2 = (int64_t)I * T + c;
-      B[r][c] = (i2 < n && j2 < n) ? __ldcg(s + i2) * H[i2 * ld + j2] : 0.0;
+      if (i2 < n && j2 < n) cp_async8(&B[r][c], H + i2 * ld + j2); else B[r][c] = 0.0;
     }
   }
+  asm volatile("cp.async.commit_group;" ::: "memory");
+  if (tid < T) {
+    const int64_t i = (int64_t)I * T + tid, j = (int64_t)J * T + tid;
+    sI[tid] = i < n ? h * __ldcg(s + i) : 0.0;
+    sJ[tid] = j < n ? h * __ldcg(s + j) : 0.0;
+  }
+  asm volatile("cp.async.wait_group 0;" ::: "memory");
   __syncthreads();
+  // scaled entries: ea(r, c) = e_{I r, J c}, eb(r, c) = e_{J r, I c} (rounded products,
+  // not fused into the sums that use them)
+  auto ea = [&](int r, int c) { return __dmul_rn(sI[r], A[r][c]); };
+  auto eb = [&](int r, int c) { return off ? __dmul_rn(sJ[r], B[r][c]) : __dmul_rn(sI[r], A[r][c]); };
   auto pair = [&](double a, double b, int64_t i, int64_t j) {
     if constexpr (kW) {
       const double k = kappa[i * n + j];
       return k * a + (1.0 - k) * b;
     } else {
-      return 0.5 * (a + b);
+      return a + b;
     }
   };
-  double dmax = 0.0;
-  // tile (I, J): h(r, c) from A[r][c] and other(c, r); tile (J, I) likewise from B
-  for (int e = tid; e < T * T; e += kThreads) {
-    const int r = e / T, c = e % T;
+  double v1[kPer], v2[kW ? kPer : 1];
+  unsigned long long dmax = 0ull;  // bit pattern of the largest defect (non-negative)
+#pragma unroll
+  for (int k = 0; k < kPer; ++k) {
+    const int e = tid + k * kThreads, r = e / T, c = e % T;
     const int64_t i = (int64_t)I * T + r, j = (int64_t)J * T + c;
-    if (i < n && j < n) {
-      const double a = A[r][c], b = off ? B[c][r] : A[c][r];
-      H[i * ld + j] = pair(a, b, i, j);
-      dmax = fmax(dmax, 0.5 * fabs(a - b));
-    }
-    if (off) {
+    const double a = ea(r, c), b = eb(c, r);
+    v1[k] = (i < n && j < n) ? pair(a, b, i, j) : 0.0;
+    const double d = kW ? 0.5 * fabs(a - b) : fabs(a - b);
+    dmax = max(dmax, (unsigned long long)__double_as_longlong(d));
+    if constexpr (kW) {
       const int64_t i2 = (int64_t)J * T + r, j2 = (int64_t)I * T + c;
-      if (i2 < n && j2 < n) H[i2 * ld + j2] = pair(B[r][c], A[c][r], i2, j2);
+      v2[k] = (off && i2 < n && j2 < n) ? pair(eb(r, c), ea(c, r), i2, j2) : 0.0;
     }
   }
-  // row sums of the written values: kTpr threads per row, kCpt columns each, fixed order
+  __syncthreads();  // every read of the scaled tiles is done
+#pragma unroll
+  for (int k = 0; k < kPer; ++k) {
+    const int e = tid + k * kThreads, r = e / T, c = e % T;
+    A[r][c] = v1[k];
+    if constexpr (kW) B[r][c] = v2[k];
+    const int64_t i = (int64_t)I * T + r, j = (int64_t)J * T + c;
+    if (i < n && j < n) H[i * ld + j] = v1[k];
+  }
+  __syncthreads();
+  // value of the entry (J r, I c) of the tile (J, I)
+  auto w2 = [&](int r, int c) { return kW ? B[r][c] : A[c][r]; };
+  if (off) {
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) {
+      const int e = tid + k * kThreads, r = e / T, c = e % T;
+      const int64_t i2 = (int64_t)J * T + r, j2 = (int64_t)I * T + c;
+      if (i2 < n && j2 < n) H[i2 * ld + j2] = w2(r, c);
+    }
+  }
+  // row sums of (I, J) and (J, I); kTpr threads per row, kCpt columns each
   constexpr int kTpr = kThreads / T, kCpt = T / kTpr;
   const int row = tid / kTpr, part = tid % kTpr;
+  const int rot = T == 64 ? 4 * part : 2 * (part >> 2);
   double acc = 0.0, acc2 = 0.0;
-  const int64_t ri = (int64_t)I * T + row, rj = (int64_t)J * T + row;
-  for (int c = part * kCpt; c < part * kCpt + kCpt; ++c) {
-    const int64_t ci = (int64_t)I * T + c, cj = (int64_t)J * T + c;
-    if (ri < n && cj < n) acc += pair(A[row][c], off ? B[c][row] : A[c][row], ri, cj);
-    if (off && rj < n && ci < n) acc2 += pair(B[row][c], A[c][row], rj, ci);
+  for (int it = 0; it < kCpt; ++it) {
+    const int c = part * kCpt + ((it + rot) & (kCpt - 1));
+    acc += A[row][c];
+    if (off) acc2 += w2(row, c);
   }
 #pragma unroll
   for (int o = 1; o < kTpr; o <<= 1) {
     acc += __shfl_xor_sync(0xffffffffu, acc, o);
     acc2 += __shfl_xor_sync(0xffffffffu, acc2, o);
   }
+  const int64_t ri = (int64_t)I * T + row, rj = (int64_t)J * T + row;
   if (part == 0) {
     if (ri < n) P[(int64_t)J * n + ri] = acc;
     if (off && rj < n) P[(int64_t)I * n + rj] = acc2;
   }
-  red[tid] = dmax;
+  for (int o = 16; o > 0; o >>= 1) dmax = max(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+  if ((tid & 31) == 0) red[tid >> 5] = dmax;
   __syncthreads();
-  for (int w = kThreads / 2; w > 0; w >>= 1) {
-    if (tid < w) red[tid] = fmax(red[tid], red[tid + w]);
-    __syncthreads();
+  if (tid == 0) {
+    unsigned long long m = red[0];
+    for (int w = 1; w < kThreads / 32; ++w) m = max(m, red[w]);
+    atomicMax(d_recip, m);
   }
-  if (tid == 0) atomicMax(d_recip, (unsigned long long)__double_as_longlong(red[0]));
   __syncthreads();  // the tiles are reused by the block's next pair
 }
 
 template <int T, bool kW>
-__global__ void __launch_bounds__(kThreads) sym_pass(double* __restrict__ H, const double* __restrict__ s,
+__global__ void __launch_bounds__(kThreads, 3) sym_pass(double* __restrict__ H, const double* __restrict__ s,
                                                      const double* __restrict__ kappa, int32_t n,
                                                      double* __restrict__ P, EnforceState* st) {
   if (st->done) return;
@@ -203,7 +263,7 @@ __device__ bool grid_barrier(PersistState* st, int* s_ok, unsigned long long lim
 }
 
 template <int T, bool kW>
-__global__ void __launch_bounds__(kThreads) enforce_persistent(double* __restrict__ H, double* __restrict__ s,
+__global__ void __launch_bounds__(kThreads, 3) enforce_persistent(double* __restrict__ H, double* __restrict__ s,
                                                                const double* __restrict__ kappa,
                                                                const double* __restrict__ omega, int32_t n,
                                                                int32_t n_tiles, double* __restrict__ P,
