@@ -57,6 +57,9 @@ def parse():
                          "budget (the small case the ncu captures use) and print the ray count")
     ap.add_argument("--sided", action="store_true",
                     help="with --trace-once: the side-resolved trace of the two-faced plates instead")
+    ap.add_argument("--enforce-once", type=int, nargs=2, default=None, metavar=("N", "ITERS"),
+                    help="instead of the bench line, run the iterative enforcer once on a seeded N x (N+1) "
+                         "matrix for ITERS iterations (the small case its ncu captures use)")
     ap.add_argument("--bvh-build", action="store_true",
                     help="instead of the bench line, print one JSON line comparing the host and device BVH "
                          "builders (build time, tree, trace rate) on the small-satellite and spacecraft meshes")
@@ -659,7 +662,9 @@ def solve_scaling(args):
         out["enforce"].append({"workload": name, "n": n, "iterations": iters, "ms": round(ms_e, 3),
                                "ms_per_iteration": round(ms_e / iters, 4), "achieved_gbs": round(gbs, 1),
                                "peak_gbs": hbm, "frac": round(gbs / hbm, 4),
-                               "bytes_per_iteration": 16 * n * (n + 1)})
+                               "bytes_per_iteration": 16 * n * (n + 1),
+                               "bound": "fp64 pipe (6 fp64 operations per pair of entries); frac is of the HBM copy "
+                                        "peak, which this GPU's fp64 rate keeps out of reach"})
         del F0
         eps = torch.as_tensor(w["eps"][:S], device=dev)
         rho = torch.as_tensor(w["rho"][:S], device=dev)
@@ -747,6 +752,29 @@ def bvh_build(args):
     return {"kind": "bvh_build", "meshes": rows}
 
 
+def enforce_once(n, iters):
+    """One iterative enforcement of a seeded n x (n+1) matrix (rows summing to about 0.75,
+    areas U[0.5, 2]) stopped after `iters` iterations: the small case of the enforcer's
+    ncu captures (the tolerance is out of reach, so the call reports RG_ERR_NOT_CONVERGED
+    after `iters` iterations, which is expected here)."""
+    import torch
+    from paper_2511_04277_gb300 import api
+    from paper_2511_04277_gb300._native import RadgebError
+    ctx = api.Context(0)
+    g = torch.Generator(device="cuda").manual_seed(0)
+    F = torch.rand((n, n + 1), dtype=torch.float64, device="cuda", generator=g) * (0.5 / n)
+    F[:, n] = 0.5
+    A = torch.rand(n, dtype=torch.float64, device="cuda", generator=g) * 1.5 + 0.5
+    try:
+        api.enforce_iterative(ctx, F, A, tol=1e-300, maxit=iters)
+    except RadgebError as exc:
+        if exc.code != "RG_ERR_NOT_CONVERGED":
+            raise
+    torch.cuda.synchronize()
+    print(json.dumps({"kind": "enforce_once", "n": n, "iterations": iters}), flush=True)
+    ctx.close()
+
+
 def trace_once(scale, sided=False):
     import torch
     import synth
@@ -769,6 +797,9 @@ def main():
         return
     if args.solve_scaling:
         print(json.dumps(solve_scaling(args)), flush=True)
+        return
+    if args.enforce_once is not None:
+        enforce_once(args.enforce_once[0], args.enforce_once[1])
         return
     if args.bvh_build:
         print(json.dumps(bvh_build(args)), flush=True)
