@@ -60,6 +60,9 @@ def parse():
     ap.add_argument("--enforce-once", type=int, nargs=2, default=None, metavar=("N", "ITERS"),
                     help="instead of the bench line, run the iterative enforcer once on a seeded N x (N+1) "
                          "matrix for ITERS iterations (the small case its ncu captures use)")
+    ap.add_argument("--reflect", action="store_true",
+                    help="instead of the bench line, print one JSON line with the reflection walk's rates "
+                         "(REFs by MCRT) on the plates and the cube")
     ap.add_argument("--bvh-build", action="store_true",
                     help="instead of the bench line, print one JSON line comparing the host and device BVH "
                          "builders (build time, tree, trace rate) on the small-satellite and spacecraft meshes")
@@ -659,12 +662,28 @@ def solve_scaling(args):
         ms_e = statistics.median(t_e[1:])
         gbs = 16.0 * n * (n + 1) * iters / (ms_e * 1e-3) / 1e9
         hbm = float(peaks.get("hbm_gbs", 6800.0))
+        # the weighted enforcer (fractional-variance kappa, Eq. 3.23-3.25): kappa once, then
+        # the iterations with per-pair weights (24 B per entry per iteration)
+        K = api.kappa(ctx, rays, areas, "fractional_variance", F=F0)
+        t_k, iters_k = [], 0
+        for _ in range(3):
+            F.copy_(F0)
+            torch.cuda.synchronize()
+            box = {}
+            t_k.append(time_region(torch, lambda: box.__setitem__("it", api.enforce_iterative_kappa(
+                ctx, F, areas, api.kappa(ctx, rays, areas, "fractional_variance", F=F0, K=K), tol=1e-12)),
+                torch.cuda.current_stream()))
+            iters_k = box["it"]
+        ms_k = statistics.median(t_k[1:])
+        del K
         out["enforce"].append({"workload": name, "n": n, "iterations": iters, "ms": round(ms_e, 3),
                                "ms_per_iteration": round(ms_e / iters, 4), "achieved_gbs": round(gbs, 1),
                                "peak_gbs": hbm, "frac": round(gbs / hbm, 4),
                                "bytes_per_iteration": 16 * n * (n + 1),
                                "bound": "fp64 pipe (6 fp64 operations per pair of entries); frac is of the HBM copy "
-                                        "peak, which this GPU's fp64 rate keeps out of reach"})
+                                        "peak, which this GPU's fp64 rate keeps out of reach",
+                               "weighted": {"kappa": "fractional variance", "iterations": iters_k,
+                                            "ms": round(ms_k, 3), "ms_per_iteration": round(ms_k / iters_k, 4)}})
         del F0
         eps = torch.as_tensor(w["eps"][:S], device=dev)
         rho = torch.as_tensor(w["rho"][:S], device=dev)
@@ -775,6 +794,36 @@ def enforce_once(n, iters):
     ctx.close()
 
 
+def reflect_rates(args):
+    """REFs by the MCRT reflection walk (rg_trace_reflect): paths per second on the plates
+    (1e6 paths per sub-face, eps ~ U[0.1, 0.9], rho = 1 - eps) and the closed cube (1e6
+    per face, eps = 0.8, rho = 0.2), with the mean bounces per path."""
+    import torch
+    import synth
+    from paper_2511_04277_gb300 import api
+    ctx = api.Context(0)
+    stream = torch.cuda.current_stream()
+    rows = []
+    for name in ("plates", "cube"):
+        w = synth.workload(name, rays_scale=1.0 if name == "plates" else 10.0)
+        m = w["mesh"]
+        mesh = api.Mesh.from_synth(ctx, m)
+        eps, rho = w["eps"][0], w["rho"][0]
+        counts = torch.zeros((m.n_faces, m.n_faces + 1), dtype=torch.int64, device="cuda")
+        _, st = api.trace_reflect(ctx, mesh, w["rays"], eps, rho, w["seed"], counts=counts)
+        ts = []
+        for _ in range(3):
+            counts.zero_()
+            ts.append(time_region(torch, lambda: api.trace_reflect(ctx, mesh, w["rays"], eps, rho, w["seed"],
+                                                                   counts=counts), stream))
+        ms = statistics.median(ts)
+        rows.append({"workload": name, "paths": st["rays"], "hits_per_path": round(st["hits"] / st["rays"], 3),
+                     "ms": round(ms, 3), "paths_per_s": st["rays"] / (ms * 1e-3)})
+        mesh.close()
+    ctx.close()
+    return {"kind": "reflect", "rows": rows}
+
+
 def trace_once(scale, sided=False):
     import torch
     import synth
@@ -803,6 +852,9 @@ def main():
         return
     if args.bvh_build:
         print(json.dumps(bvh_build(args)), flush=True)
+        return
+    if args.reflect:
+        print(json.dumps(reflect_rates(args)), flush=True)
         return
     out = run_reference(args) if args.impl == "reference" else run_ours(args)
     if out is not None:
