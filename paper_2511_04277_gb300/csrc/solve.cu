@@ -57,14 +57,38 @@ template <>
 __device__ __forceinline__ __half to16<__half>(float x) { return __float2half_rn(x); }
 
 // Split x into three bf16 slices whose sum carries ~24 significant bits.
+// x rounded to bf16 (to nearest, ties to even), the rounded value also as a double. GB300
+// runs fp64 (conversions included) at a small fraction of its integer rate, so for x in
+// bf16's normal range (2^-126 <= |x| < 2^127) the rounding is done on the bit pattern:
+// keep the sign, the exponent and the 7 leading mantissa bits, rounding at bit 45 of the
+// double. Zero keeps its sign; anything else (bf16 subnormals, overflow, inf, NaN) takes
+// the conversion intrinsic. Both give the same bf16 for every input.
+__device__ __forceinline__ __nv_bfloat16 bf16_rn(double x, double* as_double) {
+  const unsigned long long t = (unsigned long long)__double_as_longlong(x);
+  const unsigned long long mag = t & 0x7fffffffffffffffull;
+  if (mag >= 0x3810000000000000ull && mag < 0x47e0000000000000ull) {
+    const unsigned long long r = (mag + 0x00000fffffffffffull + ((mag >> 45) & 1ull)) & ~0x00001fffffffffffull;
+    *as_double = __longlong_as_double((long long)(r | (t & 0x8000000000000000ull)));
+    const unsigned e = (unsigned)(r >> 52) - 1023u + 127u;  // 1 .. 254
+    return __ushort_as_bfloat16((unsigned short)(((t >> 48) & 0x8000u) | (e << 7) | ((r >> 45) & 0x7fu)));
+  }
+  if (mag == 0ull) {
+    *as_double = x;
+    return __ushort_as_bfloat16((unsigned short)((t >> 48) & 0x8000u));
+  }
+  const __nv_bfloat16 v = __double2bfloat16(x);
+  *as_double = (double)__bfloat162float(v);
+  return v;
+}
+
+// x = s0 + s1 + s2 + (remainder): three bf16 slices, each the rounding of what the ones
+// before leave (the differences are exact in fp64).
 __device__ __forceinline__ void split3(double x, __nv_bfloat16* s) {
-  __nv_bfloat16 a = __double2bfloat16(x);
-  double r = x - (double)__bfloat162float(a);
-  __nv_bfloat16 b = __double2bfloat16(r);
-  r -= (double)__bfloat162float(b);
-  s[0] = a;
-  s[1] = b;
-  s[2] = __double2bfloat16(r);
+  double a, b, c;
+  s[0] = bf16_rn(x, &a);
+  const double r = x - a;
+  s[1] = bf16_rn(r, &b);
+  s[2] = bf16_rn(r - b, &c);
 }
 // K-concatenated pair order of the refinement product: (P_a, Y_b) for
 // (0,0) (0,1) (1,0) (0,2) (1,1) (2,0).
