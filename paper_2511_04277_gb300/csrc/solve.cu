@@ -56,40 +56,96 @@ __device__ __forceinline__ __nv_bfloat16 to16<__nv_bfloat16>(float x) { return _
 template <>
 __device__ __forceinline__ __half to16<__half>(float x) { return __float2half_rn(x); }
 
-// Split x into three bf16 slices whose sum carries ~24 significant bits.
-// x rounded to bf16 (to nearest, ties to even), the rounded value also as a double. GB300
-// runs fp64 (conversions included) at a small fraction of its integer rate, so for x in
-// bf16's normal range (2^-126 <= |x| < 2^127) the rounding is done on the bit pattern:
-// keep the sign, the exponent and the 7 leading mantissa bits, rounding at bit 45 of the
-// double. Zero keeps its sign; anything else (bf16 subnormals, overflow, inf, NaN) takes
-// the conversion intrinsic. Both give the same bf16 for every input.
-__device__ __forceinline__ __nv_bfloat16 bf16_rn(double x, double* as_double) {
-  const unsigned long long t = (unsigned long long)__double_as_longlong(x);
-  const unsigned long long mag = t & 0x7fffffffffffffffull;
-  if (mag >= 0x3810000000000000ull && mag < 0x47e0000000000000ull) {
-    const unsigned long long r = (mag + 0x00000fffffffffffull + ((mag >> 45) & 1ull)) & ~0x00001fffffffffffull;
-    *as_double = __longlong_as_double((long long)(r | (t & 0x8000000000000000ull)));
-    const unsigned e = (unsigned)(r >> 52) - 1023u + 127u;  // 1 .. 254
-    return __ushort_as_bfloat16((unsigned short)(((t >> 48) & 0x8000u) | (e << 7) | ((r >> 45) & 0x7fu)));
+// Split x into three bf16 slices whose sum carries ~24 significant bits:
+// s0 = bf16(x), s1 = bf16(x - s0), s2 = bf16(x - s0 - s1), each rounding to nearest, ties to
+// even, and each difference exact. GB300 runs fp64 (conversions included) at a small
+// fraction of its integer rate, so the hot callers take the split on the bit pattern
+// (split3_bits) and fall back to the fp64 definition (split3_fp64) only where an input or
+// an intermediate leaves the ranges the integer path covers. Both give the same slices
+// for every input.
+__device__ __forceinline__ void split3_fp64(double x, __nv_bfloat16* s) {
+  s[0] = __double2bfloat16(x);
+  const double r = x - (double)__bfloat162float(s[0]);
+  s[1] = __double2bfloat16(r);
+  s[2] = __double2bfloat16(r - (double)__bfloat162float(s[1]));
+}
+
+// Bits 31..24 of the normalised magnitude h (leading one at bit 31; l holds the bits
+// below h's) rounded to nearest, ties to even, as a bf16 of sign sg (bit 31) and biased
+// exponent be; (h, l) becomes the remainder's magnitude in the same frame and sg its sign.
+__device__ __forceinline__ __nv_bfloat16 round8_bits(uint32_t& h, uint32_t& l, uint32_t& sg, int be) {
+  const uint32_t up = ((h >> 23) & 1u) & ((((h & 0x007fffffu) | l) != 0u) | ((h >> 24) & 1u));
+  const __nv_bfloat16 v =
+      __ushort_as_bfloat16((unsigned short)((sg >> 16) | (((uint32_t)be << 7) + ((h >> 24) + up - 128u))));
+  h &= 0x00ffffffu;
+  if (up) {  // the remainder is negative: 2^24 (in units of h's bit 0) minus the dropped bits
+    h = 0x01000000u - h - (l != 0u);
+    l = 0u - l;
+    sg ^= 0x80000000u;
   }
-  if (mag == 0ull) {
-    *as_double = x;
-    return __ushort_as_bfloat16((unsigned short)((t >> 48) & 0x8000u));
-  }
-  const __nv_bfloat16 v = __double2bfloat16(x);
-  *as_double = (double)__bfloat162float(v);
   return v;
 }
 
-// x = s0 + s1 + s2 + (remainder): three bf16 slices, each the rounding of what the ones
-// before leave (the differences are exact in fp64).
-__device__ __forceinline__ void split3(double x, __nv_bfloat16* s) {
-  double a, b, c;
-  s[0] = bf16_rn(x, &a);
-  const double r = x - a;
-  s[1] = bf16_rn(r, &b);
-  s[2] = bf16_rn(r - b, &c);
+// Shift the 64-bit magnitude (h, l) != 0 left until its leading one is bit 31 of h;
+// returns the leading bit's position before the shift (0 .. 63).
+__device__ __forceinline__ int normalise_bits(uint32_t& h, uint32_t& l) {
+  if (h != 0u) {
+    const int sh = __clz((int)h);
+    if (sh) {
+      h = (h << sh) | (l >> (32 - sh));
+      l <<= sh;
+    }
+    return 63 - sh;
+  }
+  const int sh = __clz((int)l);
+  h = l << sh;
+  l = 0u;
+  return 31 - sh;
 }
+
+// split3 on the two 32-bit words of x, for x zero or 2^-126 <= |x| < 2^127 with normal
+// slices; false elsewhere (the slices are then unusable). The significand M of x (53 bits,
+// unit ulp(x) = 2^(E - 1075)) is rounded to 8 bits at bit 45; the remainder, a signed
+// integer of at most 45 bits in the same unit, is normalised and rounded to 8 bits; what
+// that leaves is normalised and rounded once more.
+__device__ __forceinline__ bool split3_bits(double x, __nv_bfloat16* s) {
+  const uint32_t hi = (uint32_t)__double2hiint(x), lo = (uint32_t)__double2loint(x);
+  uint32_t sg = hi & 0x80000000u;
+  const uint32_t t = hi & 0x7fffffffu;
+  const __nv_bfloat16 zero = __ushort_as_bfloat16((unsigned short)0);
+  if ((t | lo) == 0u) {
+    s[0] = __ushort_as_bfloat16((unsigned short)(sg >> 16));
+    s[1] = s[2] = zero;
+    return true;
+  }
+  const int E = (int)(t >> 20);
+  bool ok = E >= 897 && E <= 1149;
+  // s0: the 7 leading mantissa bits, rounded at bit 12 of the high word (bit 44 of x)
+  const uint32_t up = ((t & 0x1fffu) + 0xfffu + ((lo != 0u) | ((t >> 13) & 1u))) >> 13;
+  s[0] = __ushort_as_bfloat16((unsigned short)((sg >> 16) | ((((t & ~0x1fffu) + (up << 13)) >> 13) - (896u << 7))));
+  // D = M - s0 in units of ulp(x): the dropped 45 bits, or 2^45 minus them when rounded up
+  uint32_t h = t & 0x1fffu, l = lo;
+  if (up) {
+    h = 0x2000u - h - (l != 0u);
+    l = 0u - l;
+    sg ^= 0x80000000u;
+  }
+  if ((h | l) == 0u) {
+    s[1] = s[2] = zero;
+    return ok;
+  }
+  const int p1 = normalise_bits(h, l);  // bf16 exponent of D's bit 0: E - 1075 + 127
+  const int be1 = E - 948 + p1;
+  s[1] = round8_bits(h, l, sg, be1);
+  if ((h | l) == 0u) {
+    s[2] = zero;
+    return ok && be1 >= 1;
+  }
+  const int be2 = be1 - 63 + normalise_bits(h, l);  // the frame was shifted by 63 - p1
+  s[2] = round8_bits(h, l, sg, be2);
+  return ok && be1 >= 1 && be2 >= 1;
+}
+
 // K-concatenated pair order of the refinement product: (P_a, Y_b) for
 // (0,0) (0,1) (1,0) (0,2) (1,1) (2,0).
 __constant__ int kPairA[kSlices] = {0, 0, 1, 0, 1, 2};
@@ -103,7 +159,7 @@ __global__ void build_p_slices(const double* __restrict__ P, int64_t ldp, bool t
     int i = (int)(e / np), k = (int)(e % np);
     __nv_bfloat16 s[3];
     double x = (i < n && k < n) ? p_elem(P, ldp, trans, i, k) : 0.0;
-    split3(x, s);
+    if (!split3_bits(x, s)) split3_fp64(x, s);
     __nv_bfloat16* row = Aext + (int64_t)i * (kSlices * (int64_t)np);
 #pragma unroll
     for (int q = 0; q < kSlices; ++q) row[(int64_t)q * np + k] = s[kPairA[q]];
@@ -116,11 +172,20 @@ __global__ void build_x_slices(const double* __restrict__ X, int64_t ldx, const 
                                int m, int np, int mp, __nv_bfloat16* __restrict__ Bext) {
   __shared__ __nv_bfloat16 tile[3][32][33];
   const int k0 = blockIdx.y * 32, j0 = blockIdx.x * 32;
-  for (int r = threadIdx.y; r < 32; r += 8) {
-    int k = k0 + r, j = j0 + threadIdx.x;
-    double x = (k < n && j < m) ? X[(int64_t)k * ldx + j] * (dr ? dr[k] : 1.0) : 0.0;
+  for (int r = threadIdx.y; r < 32; r += 8) {  // warp-uniform: threadIdx.y is the warp
+    const int k = k0 + r, j = j0 + threadIdx.x;
+    const bool in = k < n && j < m;
+    double xv = 0.0, dv = 1.0;
+    if (in) {
+      xv = X[(int64_t)k * ldx + j];
+      if (dr) dv = dr[k];
+    }
+    const double x = in ? xv * dv : 0.0;
     __nv_bfloat16 s[3];
-    split3(x, s);
+    const bool ok = split3_bits(x, s);
+    if (__any_sync(0xffffffffu, !ok)) {  // the fp64 definition, for the lanes that need it
+      if (!ok) split3_fp64(x, s);
+    }
     tile[0][r][threadIdx.x] = s[0];
     tile[1][r][threadIdx.x] = s[1];
     tile[2][r][threadIdx.x] = s[2];
@@ -145,6 +210,22 @@ __global__ void build_a32(const double* __restrict__ P, int64_t ldp, bool trans,
     if (i < n && k < n) v -= (dl ? dl[i] : 1.0) * p_elem(P, ldp, trans, i, k) * (dr ? dr[k] : 1.0);
     A[e] = (float)v;
   }
+}
+
+// (float)(x * 2^-e) on the two 32-bit words of x, for x zero, or normal with x 2^-e and
+// its float normal: the exponent moves by -e (exact), the 52-bit mantissa is rounded to 23
+// bits, to nearest, ties to even (a carry moves up the exponent). Clears ok elsewhere.
+__device__ __forceinline__ float scaled_bits(double x, int e, bool& ok) {
+  const uint32_t hi = (uint32_t)__double2hiint(x), lo = (uint32_t)__double2loint(x);
+  const uint32_t sign = hi & 0x80000000u, t = hi & 0x7fffffffu;
+  if ((t | lo) == 0u) return __uint_as_float(sign);
+  const int E = (int)(t >> 20);
+  const int fe = E - e - 896;  // float biased exponent: E - 1023 - e + 127
+  const uint32_t m = ((t & 0xfffffu) << 3) | (lo >> 29), rem = lo & 0x1fffffffu;
+  const uint32_t up = (rem > 0x10000000u) | ((rem == 0x10000000u) & m);
+  const uint32_t bits = ((uint32_t)fe << 23) + m + (up & 1u);
+  ok = ok && E >= 1 && E <= 2046 && fe >= 1 && fe <= 254 && bits < 0x7f800000u;
+  return __uint_as_float(sign | bits);
 }
 
 // A16 = I - Dl P Dr (16-bit, identity padding), the first Newton-Schulz iterate
@@ -203,16 +284,26 @@ __global__ void scaled_transpose16(const double* __restrict__ R, int64_t ld, int
   __shared__ float tile[32][33];
   const int i0 = blockIdx.y * 32, j0 = blockIdx.x * 32;
   const int j = j0 + threadIdx.x;
+  // e_j from the bits of max_i |R_ij| (a non-negative double): frexp's exponent, or 0
+  // when the maximum is 0 or not finite
   int e = 0;
   if (j < m) {
-    double mx = __longlong_as_double((long long)colmax[j]);
-    if (mx > 0.0 && isfinite(mx)) frexp(mx, &e);
+    const unsigned long long mb = colmax[j];
+    const int E = (int)(mb >> 52);  // 2048 and up: the sign bit is set
+    if (mb != 0ull && E < 2047) e = E >= 1 ? E - 1022 : (63 - __clzll((long long)mb)) - 1073;
   }
   const double sc = ldexp(1.0, -e);
   if (blockIdx.y == 0 && j < mp) colscale[j] = ldexpf(1.f, e);
-  for (int r = threadIdx.y; r < 32; r += 8) {
+  for (int r = threadIdx.y; r < 32; r += 8) {  // warp-uniform: threadIdx.y is the warp
     const int i = i0 + r;
-    tile[r][threadIdx.x] = (i < n && j < m) ? (float)(R[(int64_t)i * ld + j] * sc) : 0.f;
+    const bool in = i < n && j < m;
+    const double x = in ? R[(int64_t)i * ld + j] : 0.0;
+    bool ok = true;
+    float v = in ? scaled_bits(x, e, ok) : 0.f;
+    if (__any_sync(0xffffffffu, !ok)) {  // fp64, for the lanes that need it
+      if (!ok) v = (float)(x * sc);
+    }
+    tile[r][threadIdx.x] = v;
   }
   __syncthreads();
   for (int r = threadIdx.y; r < 32; r += 8) {

@@ -127,6 +127,20 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// 16 columns of fp32 accumulator for the warp's 32 TMEM lanes (the compensated drain
+// reads half-slabs, which keeps its Kahan state in registers).
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
 // Shared-memory matrix descriptor of a K-major tile with 128-byte rows, 128-byte
 // swizzle, 8-row core groups 1024 bytes apart (sm_100 descriptor version 1).
 __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
@@ -168,6 +182,40 @@ __device__ __forceinline__ void staged_rows(int row0, int lane, int c0, int M, i
     if (r < M && c < N) put(r, c, stage[rr][lane]);
   }
   __syncwarp();
+}
+
+// ------------------------------------------------------------------ fp64 on the bit pattern
+// GB300 issues conversion instructions and fp64 min/max to its fp64 pipe, at a small
+// fraction of the integer rate. The compensated epilogue widens two fp32 values per
+// element and folds two maxima per element: these integer forms do both.
+
+// (double)x, exact, for every x (a NaN keeps its payload and becomes quiet).
+__device__ __forceinline__ double f32_to_f64_bits(float x) {
+  const uint32_t b = __float_as_uint(x);
+  const uint32_t e = (b >> 23) & 0xffu, m = b & 0x7fffffu;
+  uint32_t hi = b & 0x80000000u, lo = 0u;
+  if (e == 0xffu) {  // infinity, NaN (quiet)
+    hi |= 0x7ff00000u | (m >> 3) | (m ? 0x80000u : 0u);
+    lo = m << 29;
+  } else if (e != 0u) {
+    hi |= ((e + 896u) << 20) | (m >> 3);
+    lo = m << 29;
+  } else if (m != 0u) {  // fp32 subnormal: normalise
+    const int p = 31 - __clz((int)m);
+    const uint32_t mm = m << (23 - p);
+    hi |= ((uint32_t)(p + 874) << 20) | ((mm & 0x7fffffu) >> 3);
+    lo = mm << 29;
+  }
+  return __hiloint2double((int)hi, (int)lo);
+}
+
+// |x| as its bit pattern, 0 for a NaN: the maximum of these orders like fmax of |x|.
+__device__ __forceinline__ unsigned long long abs_bits(double x) {
+  const unsigned long long a = (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffull;
+  return a > 0x7ff0000000000000ull ? 0ull : a;
+}
+__device__ __forceinline__ bool finite_bits(double x) {
+  return ((unsigned long long)__double_as_longlong(x) & 0x7ff0000000000000ull) != 0x7ff0000000000000ull;
 }
 
 template <class T16>
@@ -289,19 +337,23 @@ struct EpiResidual {
   int* nonfinite = nullptr;
   double* partial = nullptr;             // split K: CTA z writes its raw sum to partial + z * split_stride
   int64_t split_stride = 0;
-  __device__ __forceinline__ void store(int row0, int lane, int c0, int M, int N, const double* v,
-                                        double (*stage)[33], int z) const {
-    if (partial) {
-      double* dst = partial + (int64_t)z * split_stride;
-      staged_rows(row0, lane, c0, M, N, v, stage, [&](int r, int c, double x) { dst[(int64_t)r * ld + c] = x; });
-      return;
-    }
-    double m_out = 0.0, m_x = 0.0;
-    bool bad = false;
-#pragma unroll
-    for (int i = 0; i < 32; ++i) stage[lane][i] = v[i];
+  // The caller has written the warp's 32 x 32 block into stage (stage[l][i]: row
+  // row0 + l, column c0 + i), so that no register array of it stays live here.
+  __device__ __forceinline__ void store(int row0, int lane, int c0, int M, int N, double (*stage)[33], int z) const {
     __syncwarp();
     const int c = c0 + lane;
+    if (partial) {
+      double* dst = partial + (int64_t)z * split_stride;
+#pragma unroll 4
+      for (int rr = 0; rr < 32; ++rr) {
+        const int r = row0 + rr;
+        if (r < M && c < N) dst[(int64_t)r * ld + c] = stage[rr][lane];
+      }
+      __syncwarp();
+      return;
+    }
+    unsigned long long m_out = 0ull, m_x = 0ull;  // bit patterns of the maxima (abs_bits)
+    bool bad = false;
     const bool cok = c < N;
 #pragma unroll 1
     for (int rb = 0; rb < 32; rb += kRowBatch) {
@@ -322,23 +374,23 @@ struct EpiResidual {
         const double x = stage[rb + q][lane];
         const double o = E ? (e[q] - xo[q]) + s[q] * x : s[q] * x;
         out[(int64_t)r * ld + c] = o;
-        m_out = fmax(m_out, fabs(o));
-        m_x = fmax(m_x, fabs(xo[q]));
-        bad |= !isfinite(o) || !isfinite(xo[q]);
+        m_out = max(m_out, abs_bits(o));
+        m_x = max(m_x, abs_bits(xo[q]));
+        bad |= !finite_bits(o) || !finite_bits(xo[q]);
       }
     }
     __syncwarp();
     if (red) {
       // this lane saw column c0 + lane of the warp's 32 rows
-      if (colmax && c0 + lane < N) atomic_max_nonneg(&colmax[c0 + lane], m_out);
+      if (colmax && c0 + lane < N) atomicMax(&colmax[c0 + lane], m_out);
       for (int o = 16; o > 0; o >>= 1) {
-        m_out = fmax(m_out, __shfl_xor_sync(0xffffffffu, m_out, o));
-        m_x = fmax(m_x, __shfl_xor_sync(0xffffffffu, m_x, o));
+        m_out = max(m_out, __shfl_xor_sync(0xffffffffu, m_out, o));
+        m_x = max(m_x, __shfl_xor_sync(0xffffffffu, m_x, o));
       }
       bad = __any_sync(0xffffffffu, bad);
       if (lane == 0) {
-        atomic_max_nonneg(&red[0], m_out);
-        atomic_max_nonneg(&red[1], m_x);
+        atomicMax(&red[0], m_out);
+        atomicMax(&red[1], m_x);
         if (bad && nonfinite) atomicExch(nonfinite, 1);
       }
     }
@@ -507,11 +559,11 @@ __global__ void __launch_bounds__(cta_threads<BN, kCompensated>(), 1)
         if (!mbar_wait(&acc_full[b], (c >> 1) & 1)) { *abort_flag = 1; ok = false; break; }
         tc_fence_after();
 #pragma unroll
-        for (int c0 = 0; c0 < kEpiCols; c0 += 32) {
-          float v[32];
-          tmem_ld32(tmem_base + lane_addr + (uint32_t)(b * BN + cbase + c0), v);
+        for (int c0 = 0; c0 < kEpiCols; c0 += 16) {
+          float v[16];
+          tmem_ld16(tmem_base + lane_addr + (uint32_t)(b * BN + cbase + c0), v);
 #pragma unroll
-          for (int i = 0; i < 32; ++i) {  // Kahan: sum + v, the lost low part kept in comp
+          for (int i = 0; i < 16; ++i) {  // Kahan: sum + v, the lost low part kept in comp
             float y = v[i] - comp[c0 + i];
             float t = sum[c0 + i] + y;
             comp[c0 + i] = (t - sum[c0 + i]) - y;
@@ -524,10 +576,9 @@ __global__ void __launch_bounds__(cta_threads<BN, kCompensated>(), 1)
       if (ok) {
 #pragma unroll
         for (int c0 = 0; c0 < kEpiCols; c0 += 32) {
-          double v[32];
 #pragma unroll
-          for (int i = 0; i < 32; ++i) v[i] = (double)sum[c0 + i] - (double)comp[c0 + i];
-          epi.store(row0, lane, n0 + cbase + c0, args.M, args.N, v, stage, blockIdx.z);
+          for (int i = 0; i < 32; ++i) stage[lane][i] = f32_to_f64_bits(sum[c0 + i]) - f32_to_f64_bits(comp[c0 + i]);
+          epi.store(row0, lane, n0 + cbase + c0, args.M, args.N, stage, blockIdx.z);
         }
       }
     }
