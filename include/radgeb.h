@@ -395,14 +395,17 @@ rg_status rg_gebhart_adjoint(rg_ctx* ctx, int32_t n, const double* F_d, int32_t 
  * solved in u = T^4 (fp64-accurate refinement) and T = u^(1/4).
  *   B_d device fp64 [n][n+1]; eps_d, area_d, Q_d device fp64 [n]; T_d output [n]
  * Errors: RG_ERR_NUMERIC (a node with no path to the environment makes the
- * system singular), RG_ERR_NOT_CONVERGED. */
+ * system singular; a face with sigma eps_i A_i <= 0 or a B row that sums to 0 has no
+ * balance; a heat load that drives u_i = T_i^4 to 0 or below has no temperature),
+ * RG_ERR_NOT_CONVERGED. */
 rg_status rg_temperatures(rg_ctx* ctx, int32_t n, const double* B_d, const double* eps_d,
                           const double* area_d, const double* Q_d, double T_sink, double sigma,
                           int32_t precision, double tol, double* T_d, void* stream);
 
 /* Adjoint of rg_temperatures: given dT = dL/dT, writes dB = dL/dB (device fp64
  * [n][n+1]) and the direct part of dL/deps (device fp64 [n]); the part through B
- * follows from rg_gebhart_adjoint with dB. */
+ * follows from rg_gebhart_adjoint with dB. Errors as rg_temperatures (but for the heat-load
+ * case, which the adjoint does not see). */
 rg_status rg_temperatures_adjoint(rg_ctx* ctx, int32_t n, const double* B_d, const double* eps_d,
                                   const double* area_d, double T_sink, double sigma,
                                   const double* T_d, const double* dT_d, int32_t precision, double tol,

@@ -167,11 +167,18 @@ __global__ void build_p_slices(const double* __restrict__ P, int64_t ldp, bool t
 }
 
 // B_ext[j][q * Np + k] = slice kPairB[q] of (Dr X)(k, j); the refinement product's B operand.
-// Tiled transpose through shared memory: block (32 x 8) covers a 32 x 32 tile of X.
+// Tiled transpose through shared memory: block (32 x 8) covers a 32 x 32 tile of X. With
+// red / colmax set it also zeroes red[0..1] and colmax[0 .. mp) for the residual GEMM that
+// follows it on the stream (no separate memset).
 __global__ void build_x_slices(const double* __restrict__ X, int64_t ldx, const double* __restrict__ dr, int n,
-                               int m, int np, int mp, __nv_bfloat16* __restrict__ Bext) {
+                               int m, int np, int mp, __nv_bfloat16* __restrict__ Bext,
+                               unsigned long long* red = nullptr, unsigned long long* colmax = nullptr) {
   __shared__ __nv_bfloat16 tile[3][32][33];
   const int k0 = blockIdx.y * 32, j0 = blockIdx.x * 32;
+  if (blockIdx.y == 0 && threadIdx.y == 0) {
+    if (colmax && j0 + (int)threadIdx.x < mp) colmax[j0 + threadIdx.x] = 0ull;
+    if (red && blockIdx.x == 0 && threadIdx.x < 2) red[threadIdx.x] = 0ull;
+  }
   for (int r = threadIdx.y; r < 32; r += 8) {  // warp-uniform: threadIdx.y is the warp
     const int k = k0 + r, j = j0 + threadIdx.x;
     const bool in = k < n && j < m;
@@ -231,11 +238,15 @@ __device__ __forceinline__ float scaled_bits(double x, int e, bool& ok) {
 // A16 = I - Dl P Dr (16-bit, identity padding), the first Newton-Schulz iterate
 // X16 = 2I - A = I + Dl P Dr (the step from X = I, done here instead of by two GEMMs) and
 // its transpose Xt16, and the largest row sum of |Dl P Dr| (atomicMax on its bits). One
-// warp per row.
+// warp per row; the grid has at least mp threads.
 template <class T16>
 __global__ void build_ns_start(const double* __restrict__ P, int64_t ldp, bool trans, const double* __restrict__ dl,
                                const double* __restrict__ dr, int n, int np, T16* __restrict__ A16,
-                               T16* __restrict__ X16, T16* __restrict__ Xt16, unsigned long long* e0_bits) {
+                               T16* __restrict__ X16, T16* __restrict__ Xt16, unsigned long long* e0_bits,
+                               unsigned long long* colmax, int mp) {
+  // colmax[0 .. mp) = 0 for the column maxima of the first correction (no separate memset)
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+  if (tid < mp) colmax[tid] = 0ull;
   const int i = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
   const int lane = threadIdx.x & 31;
   if (i >= np) return;
@@ -341,7 +352,7 @@ struct Buffers {
   double* X;    // solution (ld = mp)
   double* R;    // residual (ld = mp)
   double* vec;  // [2][np] per-row scratch (row sums, diagonal scalings)
-  unsigned long long* red;  // [3] max|R|, max|X|, e0 bits
+  unsigned long long* red;  // [3] max|R|, max|X|, e0 bits (context status words, see Solver)
   double* split;  // [splits][np][mp] partial sums of a split residual GEMM (or null)
 };
 
@@ -357,9 +368,15 @@ void plan(const Layout& L, Take&& t) {
   t.template take<double>((size_t)L.np * L.mp);                   // X
   t.template take<double>((size_t)L.np * L.mp);                   // R
   t.template take<double>((size_t)2 * L.np);                      // vec
-  t.template take<unsigned long long>(4);                         // red
   t.template take<double>((size_t)L.splits * L.np * L.mp);        // split
 }
+
+// The solver's status words in the context scratch (ints), laid out so that one copy
+// returns everything a sweep's decision needs: [0] input error of the calling kernels,
+// [1] non-finite solution or residual, [4] the GEMM wait time-out word, [6..7] max|R|,
+// [8..9] max|X|, [10..11] e0 (doubles as bits).
+constexpr int kStatus = 12;
+static_assert(kStatus + 4 == tc::kGemmErrorSlot, "the GEMM error word sits in the status block");
 
 struct Solver {
   rg_ctx* ctx;
@@ -367,7 +384,8 @@ struct Solver {
   Buffers b;
   bool bf16;
   cudaStream_t s;
-  int* err;          // device error words: [0] unused, [1] non-finite
+  int* err;          // device status words (kStatus): [0] input error, [1] non-finite
+  const char* input_error = "invalid input to the solver";  // what err[0] means for the caller
   const double* P;
   int64_t ldp;
   bool transP;
@@ -408,11 +426,10 @@ struct Solver {
     b.X = cv.take<double>((size_t)L.np * L.mp);
     b.R = cv.take<double>((size_t)L.np * L.mp);
     b.vec = cv.take<double>((size_t)2 * L.np);
-    b.red = cv.take<unsigned long long>(4);
     b.split = L.splits ? cv.take<double>((size_t)L.splits * L.np * L.mp) : nullptr;
-    err = ctx->d_scratch + 32;
-    RG_CUDA_TRY(ctx, cudaMemsetAsync(err, 0, 2 * sizeof(int), s));
-    RG_CUDA_TRY(ctx, cudaMemsetAsync(ctx->d_scratch + tc::kGemmErrorSlot, 0, sizeof(int), s));
+    err = ctx->d_scratch + kStatus;
+    b.red = reinterpret_cast<unsigned long long*>(ctx->d_scratch + kStatus + 6);
+    RG_CUDA_TRY(ctx, cudaMemsetAsync(err, 0, 6 * sizeof(int), s));  // error words and the GEMM's
     return RG_OK;
   }
 
@@ -435,13 +452,16 @@ struct Solver {
     T16* X[2] = {static_cast<T16*>(b.X16[0]), static_cast<T16*>(b.X16[1])};
     T16* Xt = static_cast<T16*>(b.Xt16);
     T16* Zt = static_cast<T16*>(b.Zt16);
-    build_ns_start<T16><<<(L.np + 7) / 8, 256, 0, s>>>(P, ldp, transP, dl, dr, L.n, L.np, A16, X[0], Xt, b.red + 2);
+    build_ns_start<T16><<<(L.np + 7) / 8, 256, 0, s>>>(P, ldp, transP, dl, dr, L.n, L.np, A16, X[0], Xt, b.red + 2,
+                                                        b.colmax, L.mp);
     RG_CUDA_TRY(ctx, cudaGetLastError());
-    // pinned read-back: one wait on the stream
-    RG_CUDA_TRY(ctx, cudaMemcpyAsync(ctx->h_scratch, b.red + 2, 8, cudaMemcpyDeviceToHost, s));
+    // the status words and e0 in one pinned read-back: one wait on the stream
+    int* hs = ctx->h_scratch;
+    RG_CUDA_TRY(ctx, cudaMemcpyAsync(hs + kStatus, err, 12 * sizeof(int), cudaMemcpyDeviceToHost, s));
     RG_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+    if (hs[kStatus]) return rg::fail(ctx, RG_ERR_NUMERIC, "%s", input_error);
     double e0;
-    memcpy(&e0, ctx->h_scratch, sizeof(e0));
+    memcpy(&e0, hs + kStatus + 10, sizeof(e0));
     if (!std::isfinite(e0)) return rg::fail(ctx, RG_ERR_NUMERIC, "non-finite system matrix");
     const double floor16 = bf16 ? 0x1p-10 : 0x1p-13;
     int steps = kMaxNewtonSchulz;
@@ -473,8 +493,7 @@ struct Solver {
   // column maxima of src (the residual GEMM folds them in).
   template <class T16>
   rg_status apply_t(const double* src, bool first, bool have_colmax) {
-    if (!have_colmax) {
-      RG_CUDA_TRY(ctx, cudaMemsetAsync(b.colmax, 0, (size_t)L.mp * sizeof(unsigned long long), s));
+    if (!have_colmax) {  // colmax was zeroed by build_ns_start (apply(.., true) follows a factorisation)
       dim3 cg((L.m + 31) / 32, (L.n + 255) / 256);
       column_max<<<cg, dim3(32, 8), 0, s>>>(src, L.mp, L.n, L.m, b.colmax);
     }
@@ -493,40 +512,37 @@ struct Solver {
   // 6: 24-bit); returns max|R| / max|X| (synchronises the stream).
   rg_status residual(const double* dl, const double* dr, int pairs, double* rel) {
     dim3 tg((L.mp + 31) / 32, (L.np + 31) / 32);
-    build_x_slices<<<tg, dim3(32, 8), 0, s>>>(b.X, L.mp, dr, L.n, L.m, L.np, L.mp, b.Bext);
+    // also zeroes max|R|, max|X| and the column maxima that the residual GEMM folds
+    build_x_slices<<<tg, dim3(32, 8), 0, s>>>(b.X, L.mp, dr, L.n, L.m, L.np, L.mp, b.Bext, b.red, b.colmax);
     RG_CUDA_TRY(ctx, cudaGetLastError());
     // max|R|, max|X|, the column maxima of R and the non-finite flag come from the epilogue
-    RG_CUDA_TRY(ctx, cudaMemsetAsync(b.red, 0, 2 * sizeof(unsigned long long), s));
-    RG_CUDA_TRY(ctx, cudaMemsetAsync(b.colmax, 0, (size_t)L.mp * sizeof(unsigned long long), s));
     rg_status st = tc::gemm_residual(ctx, b.Aext, (int64_t)kSlices * L.np, b.Bext, (int64_t)kSlices * L.np, L.n, L.m,
                                      pairs * L.np, kResidualChunk, b.R, b.R0, b.X, dl, L.mp, s, b.red, b.colmax,
                                      err + 1, b.split, L.splits, L.np / tc::BK, kResidualTailChunk);
     if (st != RG_OK) return st;
     // max|R|, max|X| and the error words in one pinned read-back and one wait
     int* hs = ctx->h_scratch;
-    RG_CUDA_TRY(ctx, cudaMemcpyAsync(hs, b.red, 16, cudaMemcpyDeviceToHost, s));
-    RG_CUDA_TRY(ctx, cudaMemcpyAsync(hs + 4, err, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
-    RG_CUDA_TRY(ctx, cudaMemcpyAsync(hs + 6, ctx->d_scratch + tc::kGemmErrorSlot, sizeof(int), cudaMemcpyDeviceToHost,
-                                     s));
+    RG_CUDA_TRY(ctx, cudaMemcpyAsync(hs + kStatus, err, 10 * sizeof(int), cudaMemcpyDeviceToHost, s));
     RG_CUDA_TRY(ctx, cudaStreamSynchronize(s));
     double r, x;
-    memcpy(&r, hs, 8);
-    memcpy(&x, hs + 2, 8);
+    memcpy(&r, hs + kStatus + 6, 8);
+    memcpy(&x, hs + kStatus + 8, 8);
     *rel = x > 0 ? r / x : r;
-    if (hs[6]) return rg::fail(ctx, RG_ERR_CUDA, "tensor-core GEMM timed out waiting on a barrier");
-    if (hs[5]) return rg::fail(ctx, RG_ERR_NUMERIC, "non-finite value in the solution or residual");
+    return status_of(hs + kStatus);
+  }
+
+  rg_status status_of(const int* w) {
+    if (w[4]) return rg::fail(ctx, RG_ERR_CUDA, "tensor-core GEMM timed out waiting on a barrier");
+    if (w[0]) return rg::fail(ctx, RG_ERR_NUMERIC, "%s", input_error);
+    if (w[1]) return rg::fail(ctx, RG_ERR_NUMERIC, "non-finite value in the solution or residual");
     return RG_OK;
   }
 
   rg_status check_errors() {
     int* hs = ctx->h_scratch;
-    RG_CUDA_TRY(ctx, cudaMemcpyAsync(hs + 4, err, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
-    RG_CUDA_TRY(ctx, cudaMemcpyAsync(hs + 6, ctx->d_scratch + tc::kGemmErrorSlot, sizeof(int), cudaMemcpyDeviceToHost,
-                                     s));
+    RG_CUDA_TRY(ctx, cudaMemcpyAsync(hs + kStatus, err, 6 * sizeof(int), cudaMemcpyDeviceToHost, s));
     RG_CUDA_TRY(ctx, cudaStreamSynchronize(s));
-    if (hs[6]) return rg::fail(ctx, RG_ERR_CUDA, "tensor-core GEMM timed out waiting on a barrier");
-    if (hs[5]) return rg::fail(ctx, RG_ERR_NUMERIC, "non-finite value in the solution or residual");
-    return RG_OK;
+    return status_of(hs + kStatus);
   }
 
   // Factor, solve and refine one set whose right-hand side is already in b.R0.
@@ -846,9 +862,9 @@ rg_status rg_enforce_lsq(rg_ctx* ctx, int32_t n, const double* omega_d, double* 
     lsq_apply<<<g, kThreads, 0, s>>>(F0, mask, omega_d, sv.b.X, sv.L.mp, n, F_d, mask2, negs);
     ++ctx->launches;
     RG_CUDA_TRY(ctx, cudaGetLastError());
-    int h = 0;
-    RG_CUDA_TRY(ctx, cudaMemcpyAsync(&h, negs, sizeof(int), cudaMemcpyDeviceToHost, s));
+    RG_CUDA_TRY(ctx, cudaMemcpyAsync(ctx->h_scratch, negs, sizeof(int), cudaMemcpyDeviceToHost, s));  // pinned
     RG_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+    const int h = ctx->h_scratch[0];
     if (!nnr || h == 0) break;
     if (passes >= max_passes) {
       if (passes_out_h) *passes_out_h = passes;
@@ -964,14 +980,15 @@ rg_status rg_temperatures(rg_ctx* ctx, int32_t n, const double* B_d, const doubl
   double* t = sv.b.vec;
   double* dl = sv.b.vec + sv.L.np;
   const double u_sink = T_sink * T_sink * T_sink * T_sink;
+  sv.input_error = "rg_temperatures: a face with no radiative exchange, sigma eps A <= 0, or a non-positive T^4";
   balance_setup<<<(n + 7) / 8, 256, 0, s>>>(B_d, eps_d, area_d, Q_d, u_sink, sigma, n, sv.L.mp, t, dl, sv.b.R0,
                                              sv.err);
   ++ctx->launches;
   RG_CUDA_TRY(ctx, cudaGetLastError());
-  st = sv.check_errors();
+  // err[0] of balance_setup comes back with the factorisation's read-back
   int sw = 0;
   double rel = 0.0;
-  if (st == RG_OK) st = sv.run(dl, nullptr, tol, 16, &sw, &rel);
+  st = sv.run(dl, nullptr, tol, 16, &sw, &rel);
   if (st == RG_OK) {
     quartic_root<<<(n + 127) / 128, 128, 0, s>>>(sv.b.X, sv.L.mp, n, T_d, sv.err);
     ++ctx->launches;
@@ -998,16 +1015,17 @@ rg_status rg_temperatures_adjoint(rg_ctx* ctx, int32_t n, const double* B_d, con
   double* t = sv.b.vec;
   double* dl = sv.b.vec + sv.L.np;
   const double u_sink = T_sink * T_sink * T_sink * T_sink;
+  sv.input_error = "rg_temperatures_adjoint: a face with no radiative exchange or sigma eps A <= 0";
   balance_setup<<<(n + 7) / 8, 256, 0, s>>>(B_d, eps_d, area_d, eps_d, u_sink, sigma, n, sv.L.mp, t, dl, nullptr,
                                              sv.err);
   ++ctx->launches;
   balance_adj_rhs<<<(n + 127) / 128, 128, 0, s>>>(T_d, dT_d, t, n, sv.L.mp, sv.b.R0);
   ++ctx->launches;
   RG_CUDA_TRY(ctx, cudaGetLastError());
-  st = sv.check_errors();
+  // err[0] of balance_setup comes back with the factorisation's read-back
   int sw = 0;
   double rel = 0.0;
-  if (st == RG_OK) st = sv.run(dl, nullptr, tol, 16, &sw, &rel);
+  st = sv.run(dl, nullptr, tol, 16, &sw, &rel);
   if (st == RG_OK) {
     balance_adj_out<<<(n + 7) / 8, 256, 0, s>>>(B_d, eps_d, T_d, sv.b.X, sv.L.mp, u_sink, n, dB_d, deps_d);
     ++ctx->launches;

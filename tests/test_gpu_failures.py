@@ -65,3 +65,30 @@ def test_non_finite_view_factors_and_loads_are_reported(rg_ctx):
     assert err.value.code == "RG_ERR_NUMERIC"
     _context_still_works(rg_ctx)
 
+
+
+def test_invalid_radiative_balance_inputs_are_reported(rg_ctx):
+    """A face with sigma eps A = 0 or a B row that sums to 0 has no radiative balance, and a
+    heat load that drives T^4 below zero has no temperature: each is an error of the call,
+    not a NaN in its output."""
+    F, A, eps = _small_system()
+    B = G.gebhart(F, eps, 1 - eps)
+    Q = np.full(40, 10.0)
+    To = G.temperatures(B, eps, A, Q, 3.0)
+    e0 = eps.copy()
+    e0[4] = 0.0
+    B0 = B.copy()
+    B0[6] = 0.0
+    for Bx, ex in ((B, e0), (B0, eps)):
+        with pytest.raises(api.RadgebError, match="no radiative exchange") as err:
+            api.temperatures(rg_ctx, _dev(Bx), _dev(ex), _dev(A), _dev(Q), 3.0)
+        assert err.value.code == "RG_ERR_NUMERIC"
+        with pytest.raises(api.RadgebError, match="no radiative exchange") as err:
+            api.temperatures_adjoint(rg_ctx, _dev(Bx), _dev(ex), _dev(A), 3.0, _dev(To), _dev(np.ones(40)))
+        assert err.value.code == "RG_ERR_NUMERIC"
+    Qn = Q.copy()
+    Qn[9] = -1e12
+    with pytest.raises(api.RadgebError, match="non-positive T") as err:
+        api.temperatures(rg_ctx, _dev(B), _dev(eps), _dev(A), _dev(Qn), 3.0)
+    assert err.value.code == "RG_ERR_NUMERIC"
+    _context_still_works(rg_ctx)
