@@ -40,7 +40,7 @@ SOLVE_TOL = 1e-10
 # 3.42 ms for the four solves); the matrices here are bounded by 1, far from fp16's range
 SOLVE_PRECISION = "fp16"
 # algorithmic operations of the ray definition (counted in the design notes):
-OPS_PER_RAY = 236      # two Philox4x32-10 blocks, triangle choice, point, direction, tally
+OPS_PER_RAY = 193      # one Philox4x32-10 block (78), triangle choice, point, polar direction (52), tally
 OPS_PER_BOX = 23       # slab test of one child box against the traversal window
 OPS_PER_TRI = 55       # FMA-free Moller-Trumbore and the closest-hit update
 

@@ -15,16 +15,23 @@
  *
  * The paper gives no ray definition, so one is fixed here and in the library:
  *   RNG        Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11), key = (seed lo,
- *              seed hi), counter = (ray lo, ray hi, face, attempt).
+ *              seed hi), counter = (ray lo, ray hi, face, 0): one draw per ray.
  *   uniform    u = (x >> 8) * 2^-24.
  *   triangle   first k with x0 < thr[k] (uint32 area CDF of the face), else last.
  *   point      (u,v) = draws 1,2; folded to (1-u,1-v) if u+v > 1; pulled toward
  *              the centroid, u' = u*k + w with k = 1 - 2^-20 and w = float(2^-20/3),
  *              so that no origin lies on an edge; p = (v0 + u'*e1) + v'*e2, then
  *              lifted off the face: o = p + lift*n.
- *   direction  Malley's method: attempt a = 1..64 gives two candidates
- *              (x,y) = (2u-1, 2v-1) from draws (0,1) and (2,3); the first with
- *              x*x+y*y < 1 is taken; z = sqrt(1 - (x*x+y*y)); none -> (0,0,1).
+ *   direction  cosine-weighted from the same draw (one draw per ray): the point of
+ *              the unit disc at radius sqrt(s) and angle 2 pi a projects to the
+ *              direction (x, y, z) = (sqrt(s) cos, sqrt(s) sin, sqrt(1 - s)), which is
+ *              Malley's method without rejection (s and a uniform make the disc
+ *              point uniform). a = (word 3 >> 8) 2^-24; s = u-style 24 bits made of
+ *              the low bytes of words 3, 1, 2 (the point used the top 24 bits of
+ *              words 1, 2). cos and sin: a's top two bits pick the quadrant, the
+ *              rest the angle in it, folded to [0, pi/4] and evaluated by the
+ *              Taylor polynomials of degree 9 (sin) and 10 (cos) in float
+ *              (disc_direction below, the order of every operation fixed).
  *              d = (x*t + y*b) + z*n in the face frame (t, b, n).
  *   hit        Moller-Trumbore, every operation rounded to float (no FMA),
  *              u,v >= -eb, u+v <= 1+eb with eb = 2^-20, t > 0, the source
@@ -40,14 +47,14 @@
  * expectation is B_ij of Eq. 4.5, the fraction of the energy emitted by i that is
  * absorbed by j. A ray emitted from face i as above is followed through bounces
  * b = 1, 2, ...: at its closest hit on face j, word 3 of the draw of counter
- * (ray lo, ray hi, i, b*128) decides
+ * (ray lo, ray hi, i, b*128 + 1) decides
  *   x < floor(eps_j 2^32)            absorbed: counted for column j, path ends;
  *   x < floor((eps_j + rho_j) 2^32)  reflected diffusely;
  *   otherwise                        lost (neither absorbed nor reflected), path ends;
  * a miss is counted for the environment column. A reflection re-emits from face j
- * exactly as an emission of face j would, with the counter words of bounce b: the
- * same draw's words 0-2 choose the triangle and the point, counters
- * (ray lo, ray hi, i, b*128 + a), a = 1..64, Malley's direction. Re-emitting from a
+ * exactly as an emission of face j would, with the draw of counter
+ * (ray lo, ray hi, i, b*128) in place of the emission draw (triangle, point and
+ * direction). Re-emitting from a
  * uniform point of the face is the face-level model of Eq. 4.5 (each face reflects
  * with one uniform radiosity), so the walk estimates the same B as Gebhart's method
  * for the same faces. A path still reflecting after max_bounces counts as overflow.
@@ -105,9 +112,9 @@ void oracle_philox4x32_10(const uint32_t ctr_in[4], const uint32_t key_in[2],
   out[0] = c[0]; out[1] = c[1]; out[2] = c[2]; out[3] = c[3];
 }
 
-static void draw(uint64_t seed, uint64_t ray, uint32_t face, uint32_t attempt,
+static void draw(uint64_t seed, uint64_t ray, uint32_t face, uint32_t word3,
                  uint32_t out[4]) {
-  uint32_t ctr[4] = {(uint32_t)ray, (uint32_t)(ray >> 32), face, attempt};
+  uint32_t ctr[4] = {(uint32_t)ray, (uint32_t)(ray >> 32), face, word3};
   uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
   oracle_philox4x32_10(ctr, key, out);
 }
@@ -249,31 +256,52 @@ static int omesh_init(omesh* m, const float* verts, int64_t nv, const int32_t* t
 /* ------------------------------------------------------------------------ */
 /* Ray generation for ray `ray` of face `f`.                                  */
 /* ------------------------------------------------------------------------ */
-/* Malley's cosine-weighted (x, y, z) from the draws of attempts a = 1..64 of counter
-   word 3 = base + a; (0, 0, 1) when no candidate falls inside the unit disc. */
-static void malley(uint64_t seed, uint64_t ray, uint32_t f, uint32_t base, float* px, float* py, float* pz,
-                   int32_t* used_out) {
-  float dx = 0.0f, dy = 0.0f, s2 = 0.0f;
-  int used = 0;
-  for (uint32_t a = 1; a <= 64; ++a) {
-    uint32_t y[4];
-    draw(seed, ray, f, base + a, y);
-    float cx = (float)(y[0] >> 8) * 1.1920928955078125e-07f - 1.0f;
-    float cy = (float)(y[1] >> 8) * 1.1920928955078125e-07f - 1.0f;
-    float cs = cx * cx + cy * cy;
-    if (cs < 1.0f) { dx = cx; dy = cy; s2 = cs; used = (int)a; break; }
-    cx = (float)(y[2] >> 8) * 1.1920928955078125e-07f - 1.0f;
-    cy = (float)(y[3] >> 8) * 1.1920928955078125e-07f - 1.0f;
-    cs = cx * cx + cy * cy;
-    if (cs < 1.0f) { dx = cx; dy = cy; s2 = cs; used = (int)a; break; }
+/* cos and sin of 2 pi t 2^-24 for t = 0 .. 2^24 - 1. The quadrant is t >> 22; in it the
+   angle theta = (pi/2) w 2^-22, w = t mod 2^22, is folded to alpha = (pi/4) w' 2^-21 in
+   [0, pi/4] (w' = w, or 2^22 - w with cos and sin swapped, theta = pi/2 - alpha), where
+   sin alpha = alpha + alpha z (S1 + z (S2 + z (S3 + z S4))) and
+   cos alpha = 1 + z (C1 + z (C2 + z (C3 + z (C4 + z C5)))), z = alpha^2, with the Taylor
+   coefficients S_k = (-1)^k / (2k+1)!, C_k = (-1)^k / (2k)! rounded to float. */
+static void unit_circle(uint32_t t, float* pc, float* ps) {
+  uint32_t q = t >> 22, w = t & 0x3fffffu;
+  int swap = w >= 0x200000u;
+  float a = (float)(swap ? 0x400000u - w : w) * 0x1p-21f;   /* exact */
+  float al = a * 0x1.921fb6p-1f;                             /* pi/4 */
+  float z = al * al;
+  float sp = 0x1.71de3ap-19f;
+  sp = -0x1.a01a02p-13f + z * sp;
+  sp = 0x1.111112p-7f + z * sp;
+  sp = -0x1.555556p-3f + z * sp;
+  float sn = al + (al * z) * sp;
+  float cp = -0x1.27e4fcp-22f;
+  cp = 0x1.a01a02p-16f + z * cp;
+  cp = -0x1.6c16c2p-10f + z * cp;
+  cp = 0x1.555556p-5f + z * cp;
+  cp = -0.5f + z * cp;
+  float cs = 1.0f + z * cp;
+  float c = swap ? sn : cs, s = swap ? cs : sn;   /* cos, sin of theta */
+  switch (q) {
+    case 0: *pc = c; *ps = s; break;
+    case 1: *pc = -s; *ps = c; break;
+    case 2: *pc = -c; *ps = -s; break;
+    default: *pc = s; *ps = -c; break;
   }
-  *px = dx; *py = dy; *pz = sqrtf(1.0f - s2);
-  if (used_out) *used_out = used;
 }
 
-/* Emission from side `side` (0 = A, 1 = B) of face f with the draws of counters
-   (ray, stream, base + a): a = 0 for the triangle and the point, a = 1..64 for the
-   direction. Side B uses the frame (t, -b, -n). Emission proper uses stream = f (side A)
+/* Cosine-weighted (x, y, z) about +z from the emission draw x[0..3] (see the header). */
+static void disc_direction(const uint32_t x[4], float* px, float* py, float* pz) {
+  uint32_t sb = ((x[3] & 0xffu) << 24) | ((x[1] & 0xffu) << 16) | ((x[2] & 0xffu) << 8);
+  float s = unit_float(sb);
+  float c, sn;
+  unit_circle(x[3] >> 8, &c, &sn);
+  float r = sqrtf(s);
+  *px = r * c;
+  *py = r * sn;
+  *pz = sqrtf(1.0f - s);
+}
+
+/* Emission from side `side` (0 = A, 1 = B) of face f with the draw of counter
+   (ray, stream, base): triangle, point and direction. Side B uses the frame (t, -b, -n). Emission proper uses stream = f (side A)
    or f + 2^31 (side B) and base = 0; a reflection of bounce b uses stream = the path's
    source face and base = b*128. */
 static void emit_side(const omesh* m, uint64_t seed, int32_t f, int side, uint32_t stream, uint32_t base,
@@ -302,8 +330,8 @@ static void emit_side(const omesh* m, uint64_t seed, int32_t f, int side, uint32
   p.z = p.z + m->lift * nf.z;
 
   float dx, dy, dz;
-  int used = 0;
-  malley(seed, ray, stream, base, &dx, &dy, &dz, &used);
+  int used = 0;  /* draws after the emission draw: none */
+  disc_direction(x, &dx, &dy, &dz);
   v3 t = m->ft[f], b = m->fb[f], n = nf;
   if (side) { b.x = -b.x; b.y = -b.y; b.z = -b.z; }
   v3 dir;
@@ -703,7 +731,7 @@ int oracle_trace_reflect(const float* verts, int64_t nv, const int32_t* tris, in
         int32_t j = m.tri_face[bk];
         uint32_t x[4];
         const uint32_t base = (uint32_t)bounce << 7;
-        draw(seed, ray, (uint32_t)f, base, x);
+        draw(seed, ray, (uint32_t)f, base + 1u, x);  /* the decision; base itself re-emits */
         if ((uint64_t)x[3] < thr_a[j]) { row[j] += 1; break; }
         if ((uint64_t)x[3] >= thr_r[j]) { ++n_lost; break; }
         if (bounce >= max_bounces) { ++n_over; break; }

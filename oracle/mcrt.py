@@ -100,7 +100,8 @@ def face_areas(verts, tris, tri_face, n_faces):
 
 
 def sample_rays(verts, tris, tri_face, n_faces, face, seed, ray0, n):
-    """Origins, directions, source triangles and Malley attempts of rays [ray0, ray0+n) of ``face``."""
+    """Origins, directions, source triangles and extra direction draws (always 0: the
+    direction comes from the ray's one draw) of rays [ray0, ray0+n) of ``face``."""
     lib = _load()
     v, t, f = _mesh_arrays(verts, tris, tri_face)
     o = np.zeros((n, 3), np.float32)

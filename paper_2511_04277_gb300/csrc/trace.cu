@@ -13,8 +13,8 @@
 //     lanes are; then their rays go to the tally row
 // (aggregated per target face) and they take new rays from a private 64-ray ring in
 // shared memory, which the whole warp refills 32 rays at a time, in step, when it runs
-// short (Philox4x32-10 draws, area-CDF triangle choice, uniform point lifted off the
-// face, Malley cosine-weighted direction). Sampling thus stays convergent and lanes do
+// short (one Philox4x32-10 draw per ray: area-CDF triangle choice, uniform point lifted
+// off the face, cosine-weighted direction). Sampling thus stays convergent and lanes do
 // not wait for the slowest ray of their warp. At the end of an item the non-zero
 // counters are flushed to the int64 count matrix in HBM. The closest
 // hit is the smallest (t > 0, triangle index), so the counts do not depend on the order
@@ -119,8 +119,34 @@ __device__ __forceinline__ uint4 philox(uint4 c, uint32_t k0, uint32_t k1) {
 }
 
 __device__ __forceinline__ float unit24(uint32_t x) { return __uint2float_rn(x >> 8) * 5.9604644775390625e-08f; }
-__device__ __forceinline__ float sym24(uint32_t x) {
-  return __fsub_rn(__uint2float_rn(x >> 8) * 1.1920928955078125e-07f, 1.0f);  // exact: 2u - 1
+
+// cos and sin of 2 pi t 2^-24 (t < 2^24): the quadrant from t's top two bits; in it the
+// angle (pi/2) w 2^-22 folded to alpha = (pi/4) w' 2^-21 in [0, pi/4] (w' = w, or 2^22 - w
+// with cos and sin swapped) and the Taylor polynomials of degree 9 (sin) and 10 (cos) in
+// z = alpha^2, coefficients (-1)^k / (2k+1)! and (-1)^k / (2k)! rounded to float. Every
+// operation rounds on its own (A = Ar<true>) in the FMA-free mode.
+template <bool E>
+__device__ __forceinline__ void unit_circle(uint32_t t, float* pc, float* ps) {
+  using A = Ar<E>;
+  const uint32_t q = t >> 22, w = t & 0x3fffffu;
+  const bool swap = w >= 0x200000u;
+  const float a = __uint2float_rn(swap ? 0x400000u - w : w) * 0x1p-21f;  // exact
+  const float al = A::mul(a, 0x1.921fb6p-1f);                              // pi/4
+  const float z = A::mul(al, al);
+  float sp = 0x1.71de3ap-19f;
+  sp = A::add(-0x1.a01a02p-13f, A::mul(z, sp));
+  sp = A::add(0x1.111112p-7f, A::mul(z, sp));
+  sp = A::add(-0x1.555556p-3f, A::mul(z, sp));
+  const float sn = A::add(al, A::mul(A::mul(al, z), sp));
+  float cp = -0x1.27e4fcp-22f;
+  cp = A::add(0x1.a01a02p-16f, A::mul(z, cp));
+  cp = A::add(-0x1.6c16c2p-10f, A::mul(z, cp));
+  cp = A::add(0x1.555556p-5f, A::mul(z, cp));
+  cp = A::add(-0.5f, A::mul(z, cp));
+  const float cs = A::add(1.0f, A::mul(z, cp));
+  const float c = swap ? sn : cs, s = swap ? cs : sn;  // cos, sin of the angle in the quadrant
+  *pc = q == 0 ? c : (q == 1 ? -s : (q == 2 ? -c : s));
+  *ps = q == 0 ? s : (q == 1 ? c : (q == 2 ? -s : -c));
 }
 
 // Every quantity is computed whatever the outcome and the hit is one predicate at the
@@ -270,11 +296,11 @@ __device__ int32_t closest_face(const DevMesh& m, int32_t src, V3 o, V3 d, bool*
   return best_face;
 }
 
-// Emission from `face` with the draws of counters (ray lo, ray hi, stream, base + a):
-// a = 0 for the triangle and the point, a = 1..64 for Malley's direction. Emission
-// proper uses stream = face and base = 0; the reflection of bounce b of a path from
-// face i uses stream = i and base = 128 b (re-emission from the hit face). side_b: emission
-// from side B, with the frame (t, -b, -n) (stream = face + 2^31).
+// Emission from `face` with the one draw of counter (ray lo, ray hi, stream, base):
+// triangle, point and direction. Emission proper uses stream = face and base = 0; the
+// reflection of bounce b of a path from face i uses stream = i and base = 128 b
+// (re-emission from the hit face). side_b: emission from side B, with the frame
+// (t, -b, -n) (stream = face + 2^31).
 template <bool E>
 __device__ __forceinline__ void sample_ray(const DevMesh& m, uint32_t k0, uint32_t k1, uint64_t ray, int32_t face,
                                            V3* o, V3* d, int32_t* src, uint32_t stream, uint32_t base,
@@ -311,17 +337,15 @@ __device__ __forceinline__ void sample_ray(const DevMesh& m, uint32_t k0, uint32
   o->x = A::add(A::add(A::add(r0.x, A::mul(u, r0.w)), A::mul(v, r1.z)), A::mul(m.lift, nx));
   o->y = A::add(A::add(A::add(r0.y, A::mul(u, r1.x)), A::mul(v, r1.w)), A::mul(m.lift, ny));
   o->z = A::add(A::add(A::add(r0.z, A::mul(u, r1.y)), A::mul(v, r2.x)), A::mul(m.lift, nz));
-  float dx = 0.f, dy = 0.f, s2 = 0.f;
-  for (uint32_t att = 1; att <= 64; ++att) {
-    uint4 y = philox(make_uint4(rlo, rhi, stream, base + att), k0, k1);
-    float cx = sym24(y.x), cy = sym24(y.y);
-    float cs = A::add(A::mul(cx, cx), A::mul(cy, cy));
-    if (cs < 1.0f) { dx = cx; dy = cy; s2 = cs; break; }
-    cx = sym24(y.z); cy = sym24(y.w);
-    cs = A::add(A::mul(cx, cx), A::mul(cy, cy));
-    if (cs < 1.0f) { dx = cx; dy = cy; s2 = cs; break; }
-  }
-  float dz = __fsqrt_rn(A::sub(1.0f, s2));
+  // cosine-weighted direction from the same draw, no rejection: the unit-disc point at
+  // radius sqrt(s), angle 2 pi (x.w >> 8) 2^-24, lifted to the hemisphere; s takes 24
+  // bits from the low bytes of words 3, 1, 2 (the point used the top 24 bits of 1, 2)
+  const float s2 = unit24(((x.w & 0xffu) << 24) | ((x.y & 0xffu) << 16) | ((x.z & 0xffu) << 8));
+  float cph, sph;
+  unit_circle<E>(x.w >> 8, &cph, &sph);
+  const float rad = __fsqrt_rn(s2);
+  const float dx = A::mul(rad, cph), dy = A::mul(rad, sph);
+  const float dz = __fsqrt_rn(A::sub(1.0f, s2));
   d->x = A::add(A::add(A::mul(dx, tx), A::mul(dy, bx)), A::mul(dz, nx));
   d->y = A::add(A::add(A::mul(dx, ty), A::mul(dy, by)), A::mul(dz, ny));
   d->z = A::add(A::add(A::mul(dx, tz), A::mul(dy, bz)), A::mul(dz, nz));
@@ -728,7 +752,9 @@ __global__ void __launch_bounds__(kThreads) trace_kernel_reflect(const TracePara
           if (j == m.n_faces) { col = j; break; }
           ++n_hits;
           const uint32_t cb = (uint32_t)bounce << 7;
-          const uint4 x = philox(make_uint4((uint32_t)ray, (uint32_t)(ray >> 32), stream, cb), p.key0, p.key1);
+          // the decision draws counter cb + 1; cb itself is the re-emission's draw
+          const uint4 x =
+              philox(make_uint4((uint32_t)ray, (uint32_t)(ray >> 32), stream, cb + 1u), p.key0, p.key1);
           const unsigned long long dec = x.w;
           if (dec < p.thr_absorb[j]) { col = j; break; }
           if (dec >= p.thr_reflect[j]) { ++n_lost; break; }

@@ -154,16 +154,19 @@ def test_lockstep_and_refill_schedules_agree(rg_ctx, name):
 
 
 def test_rays_with_zero_direction_components(rg_ctx):
-    """Ray 2731 of face 12 (seed 0) has a direction component of exactly 0 (one ray in
-    2^24 has one): the slab tests must not cull the boxes it passes through."""
+    """Ray 564,308 of face 12 (seed 0) has a direction component of exactly 0 (about one
+    ray in 2^22 has one: the angle's 22 low bits all zero): the slab tests must not cull
+    the boxes it passes through. Traced in a 3,000-ray window through ray_offset."""
     m = synth.plates(16)
-    _, d, _, _ = mcrt.sample_rays(m.verts, m.tris, m.tri_face, m.n_faces, 12, 0, 0, 3000)
+    off = 564308 - 2731
+    _, d, _, _ = mcrt.sample_rays(m.verts, m.tris, m.tri_face, m.n_faces, 12, 0, off, 3000)
     assert d[2731, 1] == 0.0                  # the case is really exercised
     rays = np.zeros(m.n_faces, np.int64)
     rays[12] = 3000
     for sched in (2, 3):
-        g, _ = _gpu_counts(rg_ctx, m, rays, 0, use_bvh=sched)
-        o = mcrt.trace_counts(m.verts, m.tris, m.tri_face, m.n_faces, rays, 0, use_bvh=False, faces=[12])
+        g, _ = _gpu_counts(rg_ctx, m, rays, 0, ray_offset=off, use_bvh=sched)
+        o = mcrt.trace_counts(m.verts, m.tris, m.tri_face, m.n_faces, rays, 0, ray_offset=off, use_bvh=False,
+                              faces=[12])
         assert np.array_equal(g, o), sched
 
 

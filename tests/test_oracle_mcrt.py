@@ -86,9 +86,20 @@ def test_sampling_moments():
     # both triangles of the face are chosen in proportion to area (1/2 each)
     frac = np.mean(tri == tri.min())
     assert abs(frac - 0.5) < 4 * math.sqrt(0.25 / n)
-    assert att.min() >= 1 and att.max() <= 64
+    assert np.all(att == 0)                    # one draw per ray: no extra direction draws
     # |d| = 1 up to float rounding
     assert np.abs(np.linalg.norm(d.astype(np.float64), axis=1) - 1).max() < 1e-6
+    # azimuth uniform over 16 sectors (chi-square, 15 degrees of freedom, p ~ 1e-6 cut)
+    phi = np.arctan2(d[:, 1].astype(np.float64), d[:, 0].astype(np.float64))
+    hist = np.bincount(((phi + math.pi) / (2 * math.pi) * 16).astype(int) % 16, minlength=16)
+    assert ((hist - n / 16) ** 2 / (n / 16)).sum() < 55.0
+    # E[cos^2] = 1/2 for a cosine-weighted hemisphere (the radius is sqrt of a uniform)
+    assert abs((cz ** 2).mean() - 0.5) < 4 * math.sqrt((1 / 3 - 1 / 4) / n)
+    # the direction uses other bits of the draw than the point: no correlation between
+    # the origin and the direction components
+    for a_ in (o[:, 0], o[:, 1]):
+        for b_ in (d[:, 0], d[:, 1], cz):
+            assert abs(np.corrcoef(a_.astype(np.float64), b_.astype(np.float64))[0, 1]) < 4 / math.sqrt(n)
 
 
 def test_face_geometry():
