@@ -184,30 +184,9 @@ __device__ __forceinline__ void staged_rows(int row0, int lane, int c0, int M, i
   __syncwarp();
 }
 
-// ------------------------------------------------------------------ fp64 on the bit pattern
-// GB300 issues conversion instructions and fp64 min/max to its fp64 pipe, at a small
-// fraction of the integer rate. The compensated epilogue widens two fp32 values per
-// element and folds two maxima per element: these integer forms do both.
-
-// (double)x, exact, for every x (a NaN keeps its payload and becomes quiet).
-__device__ __forceinline__ double f32_to_f64_bits(float x) {
-  const uint32_t b = __float_as_uint(x);
-  const uint32_t e = (b >> 23) & 0xffu, m = b & 0x7fffffu;
-  uint32_t hi = b & 0x80000000u, lo = 0u;
-  if (e == 0xffu) {  // infinity, NaN (quiet)
-    hi |= 0x7ff00000u | (m >> 3) | (m ? 0x80000u : 0u);
-    lo = m << 29;
-  } else if (e != 0u) {
-    hi |= ((e + 896u) << 20) | (m >> 3);
-    lo = m << 29;
-  } else if (m != 0u) {  // fp32 subnormal: normalise
-    const int p = 31 - __clz((int)m);
-    const uint32_t mm = m << (23 - p);
-    hi |= ((uint32_t)(p + 874) << 20) | ((mm & 0x7fffffu) >> 3);
-    lo = mm << 29;
-  }
-  return __hiloint2double((int)hi, (int)lo);
-}
+// ------------------------------------------------------------------ fp64 maxima on the bit pattern
+// GB300 runs fp64 min/max on a pipe far slower than its integer ALU; the compensated
+// epilogue folds two maxima per element, as the bit patterns of |x|.
 
 // |x| as its bit pattern, 0 for a NaN: the maximum of these orders like fmax of |x|.
 __device__ __forceinline__ unsigned long long abs_bits(double x) {
@@ -558,12 +537,18 @@ __global__ void __launch_bounds__(cta_threads<BN, kCompensated>(), 1)
         const int b = c & 1;
         if (!mbar_wait(&acc_full[b], (c >> 1) & 1)) { *abort_flag = 1; ok = false; break; }
         tc_fence_after();
+        // drain in 32-column loads, or 16-column ones where the CTA's 10 warps leave each
+        // thread 168 registers (wide tiles): there half a load less keeps the state in registers
+        constexpr int kDrain = BN > 64 ? 16 : 32;
 #pragma unroll
-        for (int c0 = 0; c0 < kEpiCols; c0 += 16) {
-          float v[16];
-          tmem_ld16(tmem_base + lane_addr + (uint32_t)(b * BN + cbase + c0), v);
+        for (int c0 = 0; c0 < kEpiCols; c0 += kDrain) {
+          float v[kDrain];
+          if constexpr (kDrain == 16)
+            tmem_ld16(tmem_base + lane_addr + (uint32_t)(b * BN + cbase + c0), v);
+          else
+            tmem_ld32(tmem_base + lane_addr + (uint32_t)(b * BN + cbase + c0), v);
 #pragma unroll
-          for (int i = 0; i < 16; ++i) {  // Kahan: sum + v, the lost low part kept in comp
+          for (int i = 0; i < kDrain; ++i) {  // Kahan: sum + v, the lost low part kept in comp
             float y = v[i] - comp[c0 + i];
             float t = sum[c0 + i] + y;
             comp[c0 + i] = (t - sum[c0 + i]) - y;
@@ -577,7 +562,7 @@ __global__ void __launch_bounds__(cta_threads<BN, kCompensated>(), 1)
 #pragma unroll
         for (int c0 = 0; c0 < kEpiCols; c0 += 32) {
 #pragma unroll
-          for (int i = 0; i < 32; ++i) stage[lane][i] = f32_to_f64_bits(sum[c0 + i]) - f32_to_f64_bits(comp[c0 + i]);
+          for (int i = 0; i < 32; ++i) stage[lane][i] = (double)sum[c0 + i] - (double)comp[c0 + i];
           epi.store(row0, lane, n0 + cbase + c0, args.M, args.N, stage, blockIdx.z);
         }
       }
