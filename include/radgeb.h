@@ -434,6 +434,17 @@ rg_status rg_tc_gemm_residual(rg_ctx* ctx, int32_t M, int32_t N, int32_t K, cons
                               const double* E_d, const double* X_d, const double* dl_d, int64_t ld,
                               void* stream);
 
+/* The split the refinement product uses (App. B.2 mixed precision: the fp64 operands of
+ * the residual R = E - K B enter the bf16 tensor-core GEMM as three slices each):
+ *   s0 = bf16(x), s1 = bf16(x - s0), s2 = bf16(x - s0 - s1), each bf16() rounding to
+ *   nearest, ties to even, and each difference taken in fp64 (it is exact).
+ * The kernel forms the slices from the bit pattern of x and falls back to that fp64
+ * definition where x or a slice leaves bf16's normal range; the two agree for every x.
+ *   x_d       device fp64 [n]
+ *   slices_d  device bf16 bits (uint16) [n][3] (output)
+ * Errors: RG_ERR_ARG (n < 0 or a null pointer with n > 0). */
+rg_status rg_refinement_slices(rg_ctx* ctx, int64_t n, const double* x_d, uint16_t* slices_d, void* stream);
+
 /* ---------------------------------------------------------------- failure-detection checks */
 
 /* Test support with no counterpart in the thesis: each runs one of the library's bounded

@@ -410,6 +410,17 @@ def temperatures_adjoint(ctx: Context, B, eps, area, T_sink: float, T, dT, sigma
     return dB, deps
 
 
+def refinement_slices(ctx: Context, x: torch.Tensor, stream=None) -> torch.Tensor:
+    """The three bf16 slices s0 + s1 + s2 ~ x of each entry of the fp64 vector x, as the
+    refinement product uses them (rg_refinement_slices): int16 bit patterns [n, 3]."""
+    x = x.reshape(-1)
+    out = torch.empty((x.numel(), 3), dtype=torch.int16, device=x.device)
+    ctx.check(ctx.lib.rg_refinement_slices(ctx.handle, x.numel(), _dptr(x, torch.float64, "x"),
+                                           _dptr(out, torch.int16, "slices"), _stream(stream)),
+              "rg_refinement_slices")
+    return out
+
+
 def debug_wait_timeout(ctx: Context, kind: str, limit_s: float = 0.01, stream=None):
     """Run one bounded device wait against a flag nothing sets (rg_debug_*_timeout);
     raises RadgebError(RG_ERR_CUDA) when the wait runs out, as it should."""

@@ -146,6 +146,26 @@ __device__ __forceinline__ bool split3_bits(double x, __nv_bfloat16* s) {
   return ok && be1 >= 1 && be2 >= 1;
 }
 
+// The split of x_d[i] into slices_d[3 i .. 3 i + 2] (rg_refinement_slices). The loop's
+// trip count is the same for every thread of a block, so the vote sees whole warps.
+__global__ void split_slices(const double* __restrict__ x, int64_t n, __nv_bfloat16* __restrict__ out) {
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = base + threadIdx.x;
+    const bool in = i < n;
+    const double v = in ? x[i] : 0.0;
+    __nv_bfloat16 s[3];
+    const bool ok = split3_bits(v, s);
+    if (__any_sync(0xffffffffu, !ok)) {
+      if (!ok) split3_fp64(v, s);
+    }
+    if (in) {
+      out[3 * i] = s[0];
+      out[3 * i + 1] = s[1];
+      out[3 * i + 2] = s[2];
+    }
+  }
+}
+
 // K-concatenated pair order of the refinement product: (P_a, Y_b) for
 // (0,0) (0,1) (1,0) (0,2) (1,1) (2,0).
 __constant__ int kPairA[kSlices] = {0, 0, 1, 0, 1, 2};
@@ -873,6 +893,19 @@ rg_status rg_enforce_lsq(rg_ctx* ctx, int32_t n, const double* omega_d, double* 
     std::swap(mask, mask2);
   }
   if (passes_out_h) *passes_out_h = passes;
+  return RG_OK;
+}
+
+rg_status rg_refinement_slices(rg_ctx* ctx, int64_t n, const double* x_d, uint16_t* slices_d, void* stream) {
+  if (!ctx) return RG_ERR_ARG;
+  RG_ARG_CHECK(ctx, n >= 0 && (n == 0 || (x_d && slices_d)), "rg_refinement_slices: bad argument");
+  if (n == 0) return RG_OK;
+  RG_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+  cudaStream_t s = (cudaStream_t)stream;
+  const int64_t blocks = std::min<int64_t>((n + 255) / 256, (int64_t)ctx->sm_count * 8);
+  split_slices<<<(int)blocks, 256, 0, s>>>(x_d, n, reinterpret_cast<__nv_bfloat16*>(slices_d));
+  ++ctx->launches;
+  RG_CUDA_TRY(ctx, cudaGetLastError());
   return RG_OK;
 }
 

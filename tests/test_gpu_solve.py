@@ -266,3 +266,57 @@ def test_lsq_plates_config(rg_ctx):
     assert np.abs(got.sum(axis=1) - 1).max() <= 1e-7
     eta = A[:, None] * got[:, :512]
     assert np.abs(eta - eta.T).max() <= 1e-7 * np.abs(eta).max()
+
+
+# ------------------------------------------------------------------ refinement slices
+def _bf16_rne(x):
+    """bf16 bit patterns of fp64 x, rounding to nearest, ties to even: the quantum is
+    2^(e-8) for |x| in [2^(e-1), 2^e) within bf16's normal range and 2^-133 below it;
+    results at 2^128 and above overflow to infinity (the float32 conversion of r)."""
+    with np.errstate(all="ignore"):
+        _, e = np.frexp(x)
+        q = np.where(np.abs(x) >= 2.0 ** -126, e - 8, -133)
+        r = np.ldexp(np.rint(np.ldexp(x, -q)), q)
+        return (r.astype(np.float32).view(np.uint32) >> 16).astype(np.uint16)
+
+
+def _bf16_value(bits):
+    return (bits.astype(np.uint32) << 16).view(np.float32).astype(np.float64)
+
+
+def test_refinement_slices_match_their_definition(rg_ctx):
+    """The bit-pattern split of the refinement product against its definition
+    s0 = bf16(x), s1 = bf16(x - s0), s2 = bf16(x - s0 - s1) in fp64, on random doubles
+    across the exponent range and on the edges: zeros, ties at every slice, bf16
+    subnormals, fp64 subnormals, values that overflow bf16, infinities."""
+    rng = np.random.default_rng(5)
+    n = 1 << 20
+    x = rng.standard_normal(n) * np.exp2(rng.integers(-140, 130, n).astype(np.float64))
+    u = x.view(np.uint64)
+    tie = rng.random(n) < 0.2                          # a tie in s0: bit 44 set, bits below 0
+    u[tie] = (u[tie] & ~np.uint64((1 << 45) - 1)) | np.uint64(1 << 44)
+    tie1 = rng.random(n) < 0.1                         # ties deeper down
+    k = rng.integers(0, 44, n).astype(np.uint64)
+    u[tie1] = (u[tie1] & ~((np.uint64(1) << (k[tie1] + np.uint64(1))) - np.uint64(1))) | (np.uint64(1) << k[tie1])
+    x = u.view(np.float64)
+    edges = np.array([0.0, -0.0, 5e-324, -5e-324, 2.2e-308, 1e-40, -1e-39, 2.0 ** -133, 2.0 ** -126, 3.38e38,
+                      3.3895313892515355e38, 3.4e38, -1e39, 1e300, np.inf, -np.inf, 1.0, -1.0, 1.0 + 2.0 ** -8,
+                      1.0 + 2.0 ** -9, 1.0 + 2.0 ** -9 + 2.0 ** -30])
+    x = np.concatenate([x, edges])
+    got = api.refinement_slices(rg_ctx, _dev(x)).cpu().numpy().view(np.uint16)
+    with np.errstate(all="ignore"):
+        s0 = _bf16_rne(x)
+        r = x - _bf16_value(s0)
+        s1 = _bf16_rne(r)
+        s2 = _bf16_rne(r - _bf16_value(s1))
+    want = np.stack([s0, s1, s2], axis=1)
+    nan_want = np.isnan(_bf16_value(want))
+    nan_got = np.isnan(_bf16_value(got))
+    assert np.array_equal(nan_want, nan_got)
+    assert np.array_equal(got[~nan_want], want[~nan_want])
+    # for doubles in bf16's range the slices carry 24 bits: |x - sum| <= 2^-24 |x| roughly
+    fin = np.isfinite(x) & (np.abs(x) > 2.0 ** -100) & (np.abs(x) < 2.0 ** 120)
+    g = got[fin]
+    tot = _bf16_value(g[:, 0]) + _bf16_value(g[:, 1]) + _bf16_value(g[:, 2])
+    assert np.all(np.abs(x[fin] - tot) <= 2.0 ** -24 * np.abs(x[fin]))
+    assert api.refinement_slices(rg_ctx, _dev(np.zeros(0))).shape == (0, 3)
