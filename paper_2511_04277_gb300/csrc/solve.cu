@@ -257,8 +257,9 @@ __device__ __forceinline__ float scaled_bits(double x, int e, bool& ok) {
 
 // A16 = I - Dl P Dr (16-bit, identity padding), the first Newton-Schulz iterate
 // X16 = 2I - A = I + Dl P Dr (the step from X = I, done here instead of by two GEMMs) and
-// its transpose Xt16, and the largest row sum of |Dl P Dr| (atomicMax on its bits). One
-// warp per row; the grid has at least mp threads.
+// its transpose Xt16, and the largest row and column sums of |Dl P Dr| (||E||_inf into
+// e0_bits[0], ||E||_1 into e0_bits[1], atomicMax on their bits). One warp per row; the grid
+// has at least mp threads.
 template <class T16>
 __global__ void build_ns_start(const double* __restrict__ P, int64_t ldp, bool trans, const double* __restrict__ dl,
                                const double* __restrict__ dr, int n, int np, T16* __restrict__ A16,
@@ -270,7 +271,7 @@ __global__ void build_ns_start(const double* __restrict__ P, int64_t ldp, bool t
   const int i = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
   const int lane = threadIdx.x & 31;
   if (i >= np) return;
-  double rs = 0.0;
+  double rs = 0.0, cs = 0.0;  // row i and column i of |E|
   const double li = (i < n && dl) ? dl[i] : 1.0;
   const double ri = (i < n && dr) ? dr[i] : 1.0;
   for (int k = lane; k < np; k += 32) {
@@ -280,6 +281,7 @@ __global__ void build_ns_start(const double* __restrict__ P, int64_t ldp, bool t
       et = (dl ? dl[k] : 1.0) * p_elem(P, ldp, trans, k, i) * ri;
     }
     rs += fabs(e);
+    cs += fabs(et);
     const double one = (i == k) ? 1.0 : 0.0;
     const int64_t o = (int64_t)i * np + k;
     A16[o] = to16<T16>((float)(one - e));
@@ -287,7 +289,11 @@ __global__ void build_ns_start(const double* __restrict__ P, int64_t ldp, bool t
     Xt16[o] = to16<T16>((float)(one + et));
   }
   for (int o = 16; o > 0; o >>= 1) rs += __shfl_xor_sync(0xffffffffu, rs, o);
-  if (lane == 0) atomicMax(e0_bits, (unsigned long long)__double_as_longlong(rs));
+  for (int o = 16; o > 0; o >>= 1) cs += __shfl_xor_sync(0xffffffffu, cs, o);
+  if (lane == 0) {
+    atomicMax(e0_bits, (unsigned long long)__double_as_longlong(rs));
+    atomicMax(e0_bits + 1, (unsigned long long)__double_as_longlong(cs));
+  }
 }
 
 // Largest |R_ij| of each column j < m (bits, atomicMax); block (32 x 8) per 32 columns x 256 rows.
@@ -372,7 +378,7 @@ struct Buffers {
   double* X;    // solution (ld = mp)
   double* R;    // residual (ld = mp)
   double* vec;  // [2][np] per-row scratch (row sums, diagonal scalings)
-  unsigned long long* red;  // [3] max|R|, max|X|, e0 bits (context status words, see Solver)
+  unsigned long long* red;  // [4] max|R|, max|X|, ||E||_inf, ||E||_1 bits (context status words, see Solver)
   double* split;  // [splits][np][mp] partial sums of a split residual GEMM (or null)
 };
 
@@ -394,7 +400,8 @@ void plan(const Layout& L, Take&& t) {
 // The solver's status words in the context scratch (ints), laid out so that one copy
 // returns everything a sweep's decision needs: [0] input error of the calling kernels,
 // [1] non-finite solution or residual, [4] the GEMM wait time-out word, [6..7] max|R|,
-// [8..9] max|X|, [10..11] e0 (doubles as bits).
+// [8..9] max|X|, [10..11] ||E||_inf and [12..13] ||E||_1 of the first Newton-Schulz
+// iterate's E (doubles as bits).
 constexpr int kStatus = 12;
 static_assert(kStatus + 4 == tc::kGemmErrorSlot, "the GEMM error word sits in the status block");
 
@@ -467,7 +474,7 @@ struct Solver {
   // Newton-Schulz approximate inverse of A = I - Dl P Dr into b.X16[cur].
   template <class T16>
   rg_status factor_t(const double* dl, const double* dr) {
-    RG_CUDA_TRY(ctx, cudaMemsetAsync(b.red + 2, 0, sizeof(unsigned long long), s));
+    RG_CUDA_TRY(ctx, cudaMemsetAsync(b.red + 2, 0, 2 * sizeof(unsigned long long), s));
     T16* A16 = static_cast<T16*>(b.A16);
     T16* X[2] = {static_cast<T16*>(b.X16[0]), static_cast<T16*>(b.X16[1])};
     T16* Xt = static_cast<T16*>(b.Xt16);
@@ -477,12 +484,19 @@ struct Solver {
     RG_CUDA_TRY(ctx, cudaGetLastError());
     // the status words and e0 in one pinned read-back: one wait on the stream
     int* hs = ctx->h_scratch;
-    RG_CUDA_TRY(ctx, cudaMemcpyAsync(hs + kStatus, err, 12 * sizeof(int), cudaMemcpyDeviceToHost, s));
+    RG_CUDA_TRY(ctx, cudaMemcpyAsync(hs + kStatus, err, 14 * sizeof(int), cudaMemcpyDeviceToHost, s));
     RG_CUDA_TRY(ctx, cudaStreamSynchronize(s));
     if (hs[kStatus]) return rg::fail(ctx, RG_ERR_NUMERIC, "%s", input_error);
-    double e0;
-    memcpy(&e0, hs + kStatus + 10, sizeof(e0));
-    if (!std::isfinite(e0)) return rg::fail(ctx, RG_ERR_NUMERIC, "non-finite system matrix");
+    double e_inf, e_one;
+    memcpy(&e_inf, hs + kStatus + 10, sizeof(e_inf));
+    memcpy(&e_one, hs + kStatus + 12, sizeof(e_one));
+    if (!std::isfinite(e_inf) || !std::isfinite(e_one)) return rg::fail(ctx, RG_ERR_NUMERIC, "non-finite system matrix");
+    // The residual of the Newton-Schulz iterate X_k is I - A X_k = E^(2^(k-1)), so any
+    // norm of E with ||E|| < 1 bounds it. ||E||_inf (row sums) suits the Gebhart matrix
+    // K = I - F diag(rho); its transpose, solved by the adjoint, has ||E||_1 < 1 instead
+    // while its row sums (the column sums of F) can exceed 1: the smaller bound sets the
+    // step count.
+    const double e0 = std::min(e_inf, e_one);
     const double floor16 = bf16 ? 0x1p-10 : 0x1p-13;
     int steps = kMaxNewtonSchulz;
     if (e0 < 1.0) {

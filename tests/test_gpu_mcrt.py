@@ -248,3 +248,28 @@ def test_reflect_estimates_the_refs_at_1e7_paths_per_face(rg_ctx):
         sig = np.sqrt(np.maximum(B * (1 - B), 1e-14) / rays[:, None])
         assert np.all(np.abs(Bh - B) <= 5 * sig + 1e-6), m.name
         assert st["lost"] == 0 and st["overflow"] == 0
+
+
+def test_empty_launches_and_a_single_face(rg_ctx):
+    """No rays at all (one-sided, side-resolved and reflection walks) gives all-zero
+    counts; a mesh of one triangle sends every ray to the environment, as the oracle
+    does."""
+    m = synth.plates(4)
+    mesh = api.Mesh.from_synth(rg_ctx, m)
+    n = m.n_faces
+    z = api.trace(rg_ctx, mesh, np.zeros(n, np.int64), 3).cpu().numpy()
+    assert z.shape == (n, n + 1) and not z.any()
+    zs = api.trace_sided(rg_ctx, mesh, np.zeros(2 * n, np.int64), 3).cpu().numpy()
+    assert zs.shape == (2 * n, 2 * n + 1) and not zs.any()
+    zr, st = api.trace_reflect(rg_ctx, mesh, np.zeros(n, np.int64), np.full(n, 0.5), np.full(n, 0.5), 3)
+    assert not zr.cpu().numpy().any()
+    verts = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0]], np.float32)
+    tris = np.array([[0, 1, 2]], np.int32)
+    tf = np.array([0], np.int32)
+    one = api.Mesh(rg_ctx, verts, tris, tf, 1)
+    rays = np.array([10000], np.int64)
+    c = api.trace(rg_ctx, one, rays, 0).cpu().numpy()
+    assert c.tolist() == [[0, 10000]]
+    assert np.array_equal(c, mcrt.trace_counts(verts, tris, tf, 1, rays, 0, use_bvh=False))
+    cs = api.trace_sided(rg_ctx, one, np.array([300, 200], np.int64), 0).cpu().numpy()
+    assert cs.tolist() == [[0, 0, 300], [0, 0, 200]]
