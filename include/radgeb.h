@@ -138,8 +138,8 @@ rg_status rg_face_areas(const rg_mesh* mesh, double* areas_out_h);
 
 /* Hit counts N_ij of the MCRT estimator F_ij = N_ij / N_i (Sec. 3.5.1, Eq. 3.15).
  *   rays_per_face_h  host int64 [N]: rays emitted from face i (N_i >= 0)
- *   seed             Philox4x32-10 key; ray r of face i uses the counter
- *                    (ray_offset + r, i, attempt), so disjoint ray ranges of
+ *   seed             Philox4x32-10 key; ray r of face i is made from the one draw
+ *                    of counter (ray_offset + r, i, 0), so disjoint ray ranges of
  *                    separate calls are independent and their counts add up
  *   fma_free         1: every float operation of sampling and intersection is
  *                    individually rounded (bit-exact with the reference ray
@@ -170,8 +170,8 @@ rg_status rg_trace_stats(rg_ctx* ctx, const rg_mesh* mesh, const int64_t* rays_p
  * = counts / rays of the row (Eq. 3.15 per side).
  *   Side A emits exactly the rays of face f in rg_trace (counter word 2 = f), so summing
  *   a side-A row over the target sides gives rg_trace's row bit for bit. Side B uses
- *   counter word 2 = f + 2^31, the origin lifted along -n and Malley's direction in the
- *   frame (t, -b, -n). A hit on a triangle is on side A when the Moller-Trumbore
+ *   counter word 2 = f + 2^31, the origin lifted along -n and the cosine-weighted
+ *   direction in the frame (t, -b, -n). A hit on a triangle is on side A when the Moller-Trumbore
  *   determinant e1 . (d x e2) is positive (the ray runs against the triangle normal
  *   e1 x e2), on side B otherwise; the closest-hit and tie rules are rg_trace's.
  *   rays_per_side_h  host int64 [2N]: rays of side X of face f at index 2f+X (0 for a
@@ -186,12 +186,11 @@ rg_status rg_trace_sided(rg_ctx* ctx, const rg_mesh* mesh, const int64_t* rays_p
 
 /* REFs directly from MCRT (Sec. 4.2.2): rays emitted as in rg_trace are followed
  * through diffuse reflections. At bounce b (b = 1, 2, ...) the closest hit on face j
- * is decided by word 3 of the Philox draw of counter (ray lo, ray hi, i, 128 b), i the
- * path's source face: below floor(eps_j 2^32) the ray is absorbed and counted for
+ * is decided by word 3 of the Philox draw of counter (ray lo, ray hi, i, 128 b + 1), i
+ * the path's source face: below floor(eps_j 2^32) the ray is absorbed and counted for
  * column j; below floor((eps_j + rho_j) 2^32) it is reflected, i.e. re-emitted from
- * face j exactly as an emission of face j (triangle and point from words 0-2 of that
- * draw, Malley's direction from counters (ray lo, ray hi, i, 128 b + a), a = 1..64);
- * otherwise it is lost. A miss is counted for the environment column. Re-emission
+ * face j exactly as an emission of face j, with the draw of counter
+ * (ray lo, ray hi, i, 128 b) in place of the emission draw; otherwise it is lost. A miss is counted for the environment column. Re-emission
  * from a uniform point of the hit face is the face-level model of Eq. 4.5, so
  * counts_ij / N_i estimates the B_ij that rg_gebhart solves for from the exact view
  * factors of the same faces.
