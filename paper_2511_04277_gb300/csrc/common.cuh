@@ -23,6 +23,9 @@ struct rg_ctx {
   int* d_scratch = nullptr;
   // pinned host scratch for scalar read-backs
   int* h_scratch = nullptr;
+  // recorded after a read-back copy, so that the host can wait for it while later
+  // launches on the stream keep the GPU busy
+  cudaEvent_t ev_read = nullptr;
   // kernels this context has launched (rg_launch_count)
   int64_t launches = 0;
 };

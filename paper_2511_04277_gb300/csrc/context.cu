@@ -72,6 +72,12 @@ rg_status rg_create(rg_ctx** ctx_out, int device) {
     delete ctx;
     return RG_ERR_OOM;
   }
+  if (cudaEventCreateWithFlags(&ctx->ev_read, cudaEventDisableTiming) != cudaSuccess) {
+    cudaFree(ctx->d_scratch);
+    cudaFreeHost(ctx->h_scratch);
+    delete ctx;
+    return RG_ERR_CUDA;
+  }
   *ctx_out = ctx;
   return RG_OK;
 }
@@ -83,6 +89,7 @@ void rg_destroy(rg_ctx* ctx) {
   if (ctx->ws) cudaFree(ctx->ws);
   if (ctx->d_scratch) cudaFree(ctx->d_scratch);
   if (ctx->h_scratch) cudaFreeHost(ctx->h_scratch);
+  if (ctx->ev_read) cudaEventDestroy(ctx->ev_read);
   delete ctx;
 }
 

@@ -64,7 +64,7 @@ int tile_width(const rg_ctx* ctx, int M, int N) {
 
 template <class Epi>
 rg_status gemm(rg_ctx* ctx, bool bf16, const void* A, int64_t lda, const void* B, int64_t ldb, int M, int N, int K,
-               const Epi& epi, cudaStream_t s) {
+               const Epi& epi, cudaStream_t s, const int* skip) {
   if (M <= 0 || N <= 0) return RG_OK;
   if (K <= 0) return rg::fail(ctx, RG_ERR_ARG, "gemm: K = %d", K);
   const int bn = tile_width(ctx, M, N);
@@ -73,6 +73,7 @@ rg_status gemm(rg_ctx* ctx, bool bf16, const void* A, int64_t lda, const void* B
   if (st == RG_OK) st = encode_kmajor(ctx, &mb, B, bf16, N, K, ldb, bn);
   if (st != RG_OK) return st;
   GemmArgs args{M, N, K, 0, ctx->d_scratch + kGemmErrorSlot};
+  args.skip = skip;
   if (bn == 64)
     return bf16 ? launch<64, 6, Epi, false, true>(ctx, ma, mb, args, epi, s)
                 : launch<64, 6, Epi, false, false>(ctx, ma, mb, args, epi, s);
@@ -84,15 +85,15 @@ rg_status gemm(rg_ctx* ctx, bool bf16, const void* A, int64_t lda, const void* B
 }
 
 template rg_status gemm<EpiTwoIMinusT<__nv_bfloat16>>(rg_ctx*, bool, const void*, int64_t, const void*, int64_t, int,
-                                                      int, int, const EpiTwoIMinusT<__nv_bfloat16>&, cudaStream_t);
+                                                      int, int, const EpiTwoIMinusT<__nv_bfloat16>&, cudaStream_t, const int*);
 template rg_status gemm<EpiTwoIMinusT<__half>>(rg_ctx*, bool, const void*, int64_t, const void*, int64_t, int, int,
-                                               int, const EpiTwoIMinusT<__half>&, cudaStream_t);
+                                               int, const EpiTwoIMinusT<__half>&, cudaStream_t, const int*);
 template rg_status gemm<EpiStore16Both<__nv_bfloat16>>(rg_ctx*, bool, const void*, int64_t, const void*, int64_t, int,
-                                                       int, int, const EpiStore16Both<__nv_bfloat16>&, cudaStream_t);
+                                                       int, int, const EpiStore16Both<__nv_bfloat16>&, cudaStream_t, const int*);
 template rg_status gemm<EpiStore16Both<__half>>(rg_ctx*, bool, const void*, int64_t, const void*, int64_t, int, int,
-                                                int, const EpiStore16Both<__half>&, cudaStream_t);
+                                                int, const EpiStore16Both<__half>&, cudaStream_t, const int*);
 template rg_status gemm<EpiAddF64>(rg_ctx*, bool, const void*, int64_t, const void*, int64_t, int, int, int,
-                                   const EpiAddF64&, cudaStream_t);
+                                   const EpiAddF64&, cudaStream_t, const int*);
 
 namespace {
 

@@ -312,13 +312,42 @@ __global__ void column_max(const double* __restrict__ R, int64_t ld, int n, int 
   }
 }
 
+// The refinement's stopping rule evaluated on the device, for a correction launched
+// before the host has read the residual it corrects: status = the solver's status words
+// (null: no guard), tol / prev / coarse as the host's loop has them. When the sweep ends
+// the refinement (converged or stalled) or reported an error, the correction is skipped:
+// the transposition returns at once and sets *skip, which its GEMM reads.
+struct SweepGuard {
+  const int* status = nullptr;
+  double tol = 0.0, prev = 0.0;
+  int coarse = 0;
+  int* skip = nullptr;
+};
+
+__device__ __forceinline__ bool sweep_ends(const SweepGuard& g) {
+  const volatile int* w = g.status;
+  const double r = __hiloint2double(w[7], w[6]), x = __hiloint2double(w[9], w[8]);
+  const double rel = x > 0 ? r / x : r;
+  const bool done = !g.coarse && (rel <= g.tol || (rel <= kStallFloor && rel > 0.5 * g.prev));
+  return done || w[0] || w[1] || w[4];
+}
+
 // Rt16[j][i] = 16-bit (R_ij * 2^-e_j) with max_i |R_ij| 2^-e_j in [0.5, 1), zero padding;
 // colscale[j] = 2^e_j. Tiled transpose through shared memory, block (32 x 8).
 template <class T16>
 __global__ void scaled_transpose16(const double* __restrict__ R, int64_t ld, int n, int m, int np, int mp,
                                    const unsigned long long* __restrict__ colmax, T16* __restrict__ Rt,
-                                   float* __restrict__ colscale) {
+                                   float* __restrict__ colscale, const SweepGuard guard) {
   __shared__ float tile[32][33];
+  if (guard.status) {  // one thread per block evaluates the rule (an fp64 division), the block follows
+    __shared__ int s_end;
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+      s_end = sweep_ends(guard) ? 1 : 0;
+      if (blockIdx.x == 0 && blockIdx.y == 0) *guard.skip = s_end;
+    }
+    __syncthreads();
+    if (s_end) return;
+  }
   const int i0 = blockIdx.y * 32, j0 = blockIdx.x * 32;
   const int j = j0 + threadIdx.x;
   // e_j from the bits of max_i |R_ij| (a non-negative double): frexp's exponent, or 0
@@ -399,7 +428,8 @@ void plan(const Layout& L, Take&& t) {
 
 // The solver's status words in the context scratch (ints), laid out so that one copy
 // returns everything a sweep's decision needs: [0] input error of the calling kernels,
-// [1] non-finite solution or residual, [4] the GEMM wait time-out word, [6..7] max|R|,
+// [1] non-finite solution or residual, [4] the GEMM wait time-out word, [5] the skip word
+// of a speculatively launched correction (SweepGuard), [6..7] max|R|,
 // [8..9] max|X|, [10..11] ||E||_inf and [12..13] ||E||_1 of the first Newton-Schulz
 // iterate's E (doubles as bits).
 constexpr int kStatus = 12;
@@ -526,25 +556,28 @@ struct Solver {
   // src scaled column by column into 16 bits. `have_colmax`: b.colmax already holds the
   // column maxima of src (the residual GEMM folds them in).
   template <class T16>
-  rg_status apply_t(const double* src, bool first, bool have_colmax) {
+  rg_status apply_t(const double* src, bool first, bool have_colmax, const SweepGuard& guard) {
     if (!have_colmax) {  // colmax was zeroed by build_ns_start (apply(.., true) follows a factorisation)
       dim3 cg((L.m + 31) / 32, (L.n + 255) / 256);
       column_max<<<cg, dim3(32, 8), 0, s>>>(src, L.mp, L.n, L.m, b.colmax);
     }
     dim3 tg(L.mp / 32, L.np / 32);
     T16* Rt = static_cast<T16*>(b.Rt16);
-    scaled_transpose16<T16><<<tg, dim3(32, 8), 0, s>>>(src, L.mp, L.n, L.m, L.np, L.mp, b.colmax, Rt, b.colscale);
+    scaled_transpose16<T16><<<tg, dim3(32, 8), 0, s>>>(src, L.mp, L.n, L.m, L.np, L.mp, b.colmax, Rt, b.colscale,
+                                                        guard);
     RG_CUDA_TRY(ctx, cudaGetLastError());
     return tc::gemm(ctx, bf16, b.X16[cur], L.np, Rt, L.np, L.n, L.m, L.np,
-                    tc::EpiAddF64{b.X, L.mp, b.colscale, first ? 1 : 0}, s);
+                    tc::EpiAddF64{b.X, L.mp, b.colscale, first ? 1 : 0}, s, guard.status ? guard.skip : nullptr);
   }
-  rg_status apply(const double* src, bool first, bool have_colmax = false) {
-    return bf16 ? apply_t<__nv_bfloat16>(src, first, have_colmax) : apply_t<__half>(src, first, have_colmax);
+  rg_status apply(const double* src, bool first, bool have_colmax = false, const SweepGuard& guard = SweepGuard{}) {
+    return bf16 ? apply_t<__nv_bfloat16>(src, first, have_colmax, guard)
+                : apply_t<__half>(src, first, have_colmax, guard);
   }
 
   // R = R0 - X + Dl (P (Dr X)) from the first `pairs` slice pairs (3: 16-bit operands,
-  // 6: 24-bit); returns max|R| / max|X| (synchronises the stream).
-  rg_status residual(const double* dl, const double* dr, int pairs, double* rel) {
+  // 6: 24-bit), and the copy of max|R|, max|X| and the error words to the pinned scratch,
+  // after which ctx->ev_read is recorded (read_residual waits for it).
+  rg_status launch_residual(const double* dl, const double* dr, int pairs) {
     dim3 tg((L.mp + 31) / 32, (L.np + 31) / 32);
     // also zeroes max|R|, max|X| and the column maxima that the residual GEMM folds
     build_x_slices<<<tg, dim3(32, 8), 0, s>>>(b.X, L.mp, dr, L.n, L.m, L.np, L.mp, b.Bext, b.red, b.colmax);
@@ -554,15 +587,20 @@ struct Solver {
                                      pairs * L.np, kResidualChunk, b.R, b.R0, b.X, dl, L.mp, s, b.red, b.colmax,
                                      err + 1, b.split, L.splits, L.np / tc::BK, kResidualTailChunk);
     if (st != RG_OK) return st;
-    // max|R|, max|X| and the error words in one pinned read-back and one wait
-    int* hs = ctx->h_scratch;
-    RG_CUDA_TRY(ctx, cudaMemcpyAsync(hs + kStatus, err, 10 * sizeof(int), cudaMemcpyDeviceToHost, s));
-    RG_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+    RG_CUDA_TRY(ctx, cudaMemcpyAsync(ctx->h_scratch + kStatus, err, 10 * sizeof(int), cudaMemcpyDeviceToHost, s));
+    RG_CUDA_TRY(ctx, cudaEventRecord(ctx->ev_read, s));
+    return RG_OK;
+  }
+
+  // Waits for the read-back of launch_residual (not for later launches); max|R| / max|X|.
+  rg_status read_residual(double* rel) {
+    RG_CUDA_TRY(ctx, cudaEventSynchronize(ctx->ev_read));
+    const int* hs = ctx->h_scratch + kStatus;
     double r, x;
-    memcpy(&r, hs + kStatus + 6, 8);
-    memcpy(&x, hs + kStatus + 8, 8);
+    memcpy(&r, hs + 6, 8);
+    memcpy(&x, hs + 8, 8);
     *rel = x > 0 ? r / x : r;
-    return status_of(hs + kStatus);
+    return status_of(hs);
   }
 
   rg_status status_of(const int* w) {
@@ -591,13 +629,25 @@ struct Solver {
       // while the residual is large, the three leading slice pairs (16-bit operands,
       // error ~2^-16 max|X|) resolve it; those sweeps correct but never stop
       const bool coarse = prev > kCoarseAbove && tol < kCoarseAbove;
-      st = residual(dl, dr, coarse ? 3 : kSlices, &rel);
+      st = launch_residual(dl, dr, coarse ? 3 : kSlices);
+      if (st != RG_OK) return st;
+      // the correction goes in behind the residual before the host has read it, so the GPU
+      // works while the read-back travels; it evaluates the stopping rule below on the
+      // device and does nothing when this sweep ends the refinement (X then stays as the
+      // residual saw it, as if it had not been launched)
+      SweepGuard g;
+      g.status = err;
+      g.tol = tol;
+      g.prev = prev;
+      g.coarse = coarse ? 1 : 0;
+      g.skip = err + 5;
+      st = apply(b.R, false, true, g);
+      if (st != RG_OK) return st;
+      st = read_residual(&rel);
       if (st != RG_OK) return st;
       // converged, or stalled at the accuracy floor of the fp32-chunked residual product
       if (!coarse && (rel <= tol || (rel <= kStallFloor && rel > 0.5 * prev))) { done = true; break; }
       prev = rel;
-      st = apply(b.R, false, true);
-      if (st != RG_OK) return st;
     }
     *sweeps = sw + (done ? 1 : 0);
     *rel_out = rel;

@@ -385,6 +385,9 @@ struct GemmArgs {
   // chunk_blocks; the rest use chunks of tail_chunk_blocks
   int lead_blocks = 0;
   int tail_chunk_blocks = 0;
+  // non-null: the kernel does nothing when *skip != 0 (written by an earlier kernel on
+  // the stream; a speculatively launched product the host's decision made unnecessary)
+  const int* skip = nullptr;
 };
 
 template <int BN, int kStages, class Epi, bool kCompensated, bool kBF16>
@@ -414,6 +417,7 @@ __global__ void __launch_bounds__(cta_threads<BN, kCompensated>(), 1)
   using StageT = typename std::conditional<kCompensated, double, float>::type;
   __shared__ StageT s_stage[4 * kGroups][32][33];  // per epilogue warp: coalescing block
 
+  if (args.skip && *(volatile const int*)args.skip) return;  // uniform: before any barrier or allocation
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   // grouped rasterisation of the 1-D grid: kGroupM row tiles at a time, column tiles
   // innermost, so that the CTAs resident together share their A and B tiles in L2
@@ -587,7 +591,7 @@ constexpr size_t smem_bytes() {
 // instantiated in gemm.cu for the epilogues above (bf16 selects the operand type).
 template <class Epi>
 rg_status gemm(rg_ctx* ctx, bool bf16, const void* A, int64_t lda, const void* B, int64_t ldb, int M, int N, int K,
-               const Epi& epi, cudaStream_t s);
+               const Epi& epi, cudaStream_t s, const int* skip = nullptr);
 
 // C (fp32, ldc) = alpha * A B^T + beta * C with A [M x K] (lda), B [N x K] (ldb), 16-bit
 // K-major operands (bf16 when `bf16`, else fp16). lda, ldb: multiples of 8 elements;
