@@ -288,6 +288,14 @@ static void unit_circle(uint32_t t, float* pc, float* ps) {
   }
 }
 
+/* cos and sin of 2 pi t 2^-24 for t = t0 .. t0 + n - 1 (the sampling's unit circle, for
+   its accuracy pin). */
+int oracle_unit_circle(uint32_t t0, int64_t n, float* c_out, float* s_out) {
+  if (n < 0 || (uint64_t)t0 + (uint64_t)n > (1ull << 24)) return ORC_ERR_ARG;
+  for (int64_t k = 0; k < n; ++k) unit_circle(t0 + (uint32_t)k, &c_out[k], &s_out[k]);
+  return ORC_OK;
+}
+
 /* Cosine-weighted (x, y, z) about +z from the emission draw x[0..3] (see the header). */
 static void disc_direction(const uint32_t x[4], float* px, float* py, float* pz) {
   uint32_t sb = ((x[3] & 0xffu) << 24) | ((x[1] & 0xffu) << 16) | ((x[2] & 0xffu) << 8);

@@ -48,9 +48,10 @@ def _load():
         lib.oracle_trace_sided.argtypes = [P, i64, P, i64, P, i32, P, u64, u64, ctypes.c_int, ctypes.c_int, P,
                                            i32, P]
         lib.oracle_max_threads.argtypes = []
+        lib.oracle_unit_circle.argtypes = [ctypes.c_uint32, i64, P, P]
         for fn in ("oracle_face_geometry", "oracle_sample_rays", "oracle_closest_hits",
                    "oracle_trace_counts", "oracle_trace_reflect", "oracle_sample_rays_side",
-                   "oracle_trace_sided", "oracle_max_threads"):
+                   "oracle_trace_sided", "oracle_max_threads", "oracle_unit_circle"):
             getattr(lib, fn).restype = ctypes.c_int
         _lib = lib
     return _lib
@@ -80,6 +81,15 @@ def philox4x32_10(counter, key):
     out = np.zeros(4, dtype=np.uint32)
     lib.oracle_philox4x32_10(_ptr(c), _ptr(k), _ptr(out))
     return out
+
+
+def unit_circle(t0, n):
+    """cos and sin (float32) of 2 pi t 2^-24, t = t0 .. t0+n-1, as the ray sampling forms them."""
+    lib = _load()
+    c = np.zeros(n, np.float32)
+    s = np.zeros(n, np.float32)
+    _check(lib.oracle_unit_circle(ctypes.c_uint32(t0), ctypes.c_int64(n), _ptr(c), _ptr(s)), "unit_circle")
+    return c, s
 
 
 def face_geometry(verts, tris, tri_face, n_faces):

@@ -270,3 +270,20 @@ def test_reflections_reproduce_the_printed_parallel_plate_refs():
     sig = np.sqrt(np.maximum(Bp * (1 - Bp), 1e-12) / rays[:, None])
     assert np.all(np.abs(Bh - Bp) <= 5 * sig + 1e-6)
     assert np.all(c[[0, 3], :4] == 0)           # the outer sides only see the environment
+
+
+def test_unit_circle_of_the_sampling():
+    """The direction's cos and sin of 2 pi t 2^-24 (quadrant, fold to [0, pi/4], Taylor
+    polynomials in float) against the fp64 library functions, for every one of the 2^24
+    angles: within a few float ulps, on the unit circle, and exact at the quadrant
+    boundaries."""
+    n = 1 << 24
+    c, s = mcrt.unit_circle(0, n)
+    phi = 2 * np.pi * np.arange(n, dtype=np.float64) / n
+    assert np.abs(c - np.cos(phi)).max() < 3e-7
+    assert np.abs(s - np.sin(phi)).max() < 3e-7
+    assert np.abs(c.astype(np.float64) ** 2 + s.astype(np.float64) ** 2 - 1).max() < 6e-7
+    q = np.arange(4) << 22
+    assert c[q].tolist() == [1.0, 0.0, -1.0, 0.0] and s[q].tolist() == [0.0, 1.0, 0.0, -1.0]
+    with pytest.raises(ValueError):
+        mcrt.unit_circle(n - 1, 2)
