@@ -127,8 +127,8 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-// 16 columns of fp32 accumulator for the warp's 32 TMEM lanes (the compensated drain
-// reads half-slabs, which keeps its Kahan state in registers).
+// 16 columns of fp32 accumulator for the warp's 32 TMEM lanes (the compensated drain of
+// wide tiles reads half-slabs: 16 fewer registers in flight next to its Kahan state).
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
   uint32_t r[16];
   asm volatile(
@@ -542,7 +542,7 @@ __global__ void __launch_bounds__(cta_threads<BN, kCompensated>(), 1)
         if (!mbar_wait(&acc_full[b], (c >> 1) & 1)) { *abort_flag = 1; ok = false; break; }
         tc_fence_after();
         // drain in 32-column loads, or 16-column ones where the CTA's 10 warps leave each
-        // thread 168 registers (wide tiles): there half a load less keeps the state in registers
+        // thread 168 registers (wide tiles) and the Kahan state of 64 columns needs 128
         constexpr int kDrain = BN > 64 ? 16 : 32;
 #pragma unroll
         for (int c0 = 0; c0 < kEpiCols; c0 += kDrain) {
