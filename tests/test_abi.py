@@ -55,3 +55,47 @@ def test_create_reports_no_device_without_gpu(lib):
     lib.rg_create.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int]
     st = lib.rg_create(ctypes.byref(h), 0)
     assert st != 0 and not h.value
+
+
+def _declarations():
+    """name -> list of parameter type strings, from the header's prototypes."""
+    text = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    text = re.sub(r"#.*", "", text)
+    out = {}
+    for m in re.finditer(r"\b(rg_[A-Za-z_0-9]+)\s*\(([^;{()]*)\)\s*;", text):
+        params = [p.strip() for p in m.group(2).split(",") if p.strip()]
+        if params == ["void"]:
+            params = []
+        out[m.group(1)] = params
+    return out
+
+
+def _kind_of_c(param):
+    """The calling-convention class of a C parameter: pointer, 64-bit or 32-bit integer,
+    double or float."""
+    if "*" in param:
+        return "ptr"
+    t = param.rsplit(None, 1)[0].replace("const", "").strip()
+    return {"int64_t": "i64", "uint64_t": "i64", "int32_t": "i32", "uint32_t": "i32", "int": "i32",
+            "double": "f64", "float": "f32"}[t]
+
+
+def _kind_of_ctypes(t):
+    if t in (ctypes.c_void_p, ctypes.c_char_p) or (isinstance(t, type) and issubclass(t, ctypes._Pointer)):
+        return "ptr"
+    return {ctypes.c_int64: "i64", ctypes.c_uint64: "i64", ctypes.c_int32: "i32", ctypes.c_uint32: "i32",
+            ctypes.c_double: "f64", ctypes.c_float: "f32"}[t]
+
+
+def test_binding_argument_types_match_the_header():
+    """Every ctypes signature has the header prototype's parameter count and, parameter
+    by parameter, its class (pointer / 64-bit / 32-bit integer / double / float): a
+    mismatch would pass a wrong-sized argument without any error."""
+    from paper_2511_04277_gb300 import _native
+    decl = _declarations()
+    assert sorted(decl) == sorted(_native.SIGNATURES)
+    for name, params in decl.items():
+        argtypes = _native.SIGNATURES[name][1]
+        assert len(argtypes) == len(params), (name, params, argtypes)
+        for p, a in zip(params, argtypes):
+            assert _kind_of_c(p) == _kind_of_ctypes(a), (name, p, a)
