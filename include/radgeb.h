@@ -72,6 +72,27 @@ const char* rg_version(void);
 /* Number of kernels this context has launched so far (host counter, for accounting). */
 rg_status rg_launch_count(const rg_ctx* ctx, int64_t* launches_out_h);
 
+/* Kernel timer, for measurement (no counterpart in the thesis). While it is on, the
+ * context records a CUDA event pair on the launching stream around every launch of
+ * these kernel classes:
+ *   RG_TIME_TRACE     the MCRT trace kernel of rg_trace, rg_trace_stats, rg_trace_sided;
+ *   RG_TIME_RESIDUAL  the refinement-residual GEMM of the dense solves (and of
+ *                     rg_tc_gemm_residual);
+ *   RG_TIME_GEMM      the other tensor-core GEMMs (Newton-Schulz steps, corrections);
+ *   RG_TIME_ENFORCE   the persistent iterative enforcer.
+ * rg_kernel_timer(ctx, 1) clears the records and starts recording, rg_kernel_timer(ctx, 0)
+ * stops. rg_kernel_timer_read synchronises on the recorded events of `kind` and returns
+ * their number, the sum of their durations (ms) and, for the GEMM classes, the tensor-core
+ * flops the launches executed (2 M N K each) and the algorithmic flops of the products
+ * they stand for (for the refinement residual, 2 n m n of the fp64 product R = E - K X that
+ * the sliced bf16 product emulates; otherwise equal to the executed flops). The two flop
+ * outputs may be NULL. The records grow by one event pair per timed launch until the next
+ * rg_kernel_timer(ctx, 1). Errors: RG_ERR_ARG, RG_ERR_CUDA. */
+typedef enum { RG_TIME_TRACE = 0, RG_TIME_RESIDUAL = 1, RG_TIME_GEMM = 2, RG_TIME_ENFORCE = 3 } rg_kernel_class;
+rg_status rg_kernel_timer(rg_ctx* ctx, int32_t enable);
+rg_status rg_kernel_timer_read(rg_ctx* ctx, int32_t kind, int64_t* launches_out_h, double* ms_out_h,
+                               double* flops_out_h, double* alg_flops_out_h);
+
 /* ---------------------------------------------------------------- mesh (P1) */
 
 /* Upload a triangle mesh and build its bounding-volume hierarchy (host binned
@@ -269,11 +290,15 @@ rg_status rg_enforce_iterative_kappa(rg_ctx* ctx, int32_t n, const double* omega
  *     no cudaFree, no allocating library call). Its scratch is a file-scope device
  *     array of about 2.1 MB that every GPU loading the library holds until exit.
  *   - Limit: n <= 4096; larger n returns RG_ERR_UNSUPPORTED.
- *   - The first call on a device looks up the array's device address
- *     (cudaGetSymbolAddress); make that first call before any stream capture.
+ *   - Every call looks up the array's device address on the current device
+ *     (cudaGetSymbolAddress).
  *   - Every call shares the one array and clears the part that must start at zero;
  *     calls that overlap on the GPU (other streams, other host threads) race.
- *   - It synchronises `stream` to read its iteration state back.
+ *   - It synchronises `stream` to read its iteration state back, so it must not be
+ *     called while `stream` is being captured into a CUDA graph.
+ *   - A CUDA error already pending on the calling thread when it is called (left by the
+ *     caller's own earlier work) makes it return RG_ERR_CUDA at once, without running
+ *     and without clearing that error.
  * Arguments, results and other errors as rg_enforce_iterative (no rg_last_error:
  * the status code is the whole report). */
 rg_status rg_enforce_iterative_noalloc(int32_t n, const double* omega_d, double* F_d, double tol,

@@ -34,6 +34,9 @@ SIGNATURES = {
     "rg_last_error": (ctypes.c_char_p, [P]),
     "rg_version": (ctypes.c_char_p, []),
     "rg_launch_count": (i32, [P, ctypes.POINTER(i64)]),
+    "rg_kernel_timer": (i32, [P, i32]),
+    "rg_kernel_timer_read": (i32, [P, i32, ctypes.POINTER(i64), ctypes.POINTER(f64), ctypes.POINTER(f64),
+                                    ctypes.POINTER(f64)]),
     "rg_mesh_create": (i32, [P, P, i64, P, i64, P, i32, i32, PP]),
     "rg_mesh_create_gpu_bvh": (i32, [P, P, i64, P, i64, P, i32, i32, PP]),
     "rg_mesh_get_bvh": (i32, [P, P, P]),

@@ -209,6 +209,27 @@ def launch_count(ctx: Context) -> int:
     return n.value
 
 
+KERNEL_CLASSES = {"trace": 0, "residual_gemm": 1, "gemm": 2, "enforce": 3}
+
+
+def kernel_timer(ctx: Context, enable: bool):
+    """Start (clearing earlier records) or stop the context's kernel timer (rg_kernel_timer)."""
+    ctx.check(ctx.lib.rg_kernel_timer(ctx.handle, int(bool(enable))), "rg_kernel_timer")
+
+
+def kernel_timer_read(ctx: Context, kind: str) -> dict:
+    """Launches, summed CUDA-event duration (ms), executed tensor-core flops and algorithmic
+    flops of the timed launches of one kernel class since the timer was started
+    (rg_kernel_timer_read)."""
+    n = ctypes.c_int64(0)
+    ms = ctypes.c_double(0.0)
+    fl = ctypes.c_double(0.0)
+    alg = ctypes.c_double(0.0)
+    ctx.check(ctx.lib.rg_kernel_timer_read(ctx.handle, KERNEL_CLASSES[kind], ctypes.byref(n), ctypes.byref(ms),
+                                           ctypes.byref(fl), ctypes.byref(alg)), "rg_kernel_timer_read")
+    return {"launches": n.value, "ms": ms.value, "flops": fl.value, "alg_flops": alg.value}
+
+
 def counts_to_F(ctx: Context, counts: torch.Tensor, rays: torch.Tensor, F: torch.Tensor | None = None,
                 stream=None) -> torch.Tensor:
     """F_ij = N_ij / N_i (rg_counts_to_F)."""
@@ -380,32 +401,36 @@ def gebhart_adjoint(ctx: Context, F, eps, rho, B, dB, precision="bf16", tol: flo
 
 
 def temperatures(ctx: Context, B, eps, area, Q, T_sink: float, sigma: float = 5.67e-8, precision="bf16",
-                 tol: float = 1e-13, stream=None) -> torch.Tensor:
-    """Steady node temperatures (rg_temperatures)."""
+                 tol: float = 1e-13, stream=None, T=None) -> torch.Tensor:
+    """Steady node temperatures (rg_temperatures); T (optional) receives them."""
     n = B.shape[-2]
-    T = torch.empty(n, dtype=torch.float64, device=B.device)
+    if T is None:
+        T = torch.empty(n, dtype=torch.float64, device=B.device)
     ctx.check(ctx.lib.rg_temperatures(ctx.handle, n, _dptr(B, torch.float64, "B", n * (n + 1), ctx.device),
                                       _dptr(eps, torch.float64, "eps", n, ctx.device),
                                       _dptr(area, torch.float64, "area", n, ctx.device),
                                       _dptr(Q, torch.float64, "Q", n, ctx.device), float(T_sink), float(sigma),
-                                      _prec(precision), float(tol), _dptr(T, torch.float64, "T"), _stream(stream)),
+                                      _prec(precision), float(tol), _dptr(T, torch.float64, "T", n, ctx.device), _stream(stream)),
               "rg_temperatures")
     return T
 
 
 def temperatures_adjoint(ctx: Context, B, eps, area, T_sink: float, T, dT, sigma: float = 5.67e-8,
-                         precision="bf16", tol: float = 1e-13, stream=None):
-    """(dL/dB [N, N+1], direct dL/deps [N]) from dT = dL/dT (rg_temperatures_adjoint)."""
+                         precision="bf16", tol: float = 1e-13, stream=None, dB=None, deps=None):
+    """(dL/dB [N, N+1], direct dL/deps [N]) from dT = dL/dT (rg_temperatures_adjoint);
+    dB and deps (optional) receive them."""
     n = B.shape[-2]
-    dB = torch.empty((n, n + 1), dtype=torch.float64, device=B.device)
-    deps = torch.empty(n, dtype=torch.float64, device=B.device)
+    if dB is None:
+        dB = torch.empty((n, n + 1), dtype=torch.float64, device=B.device)
+    if deps is None:
+        deps = torch.empty(n, dtype=torch.float64, device=B.device)
     ctx.check(ctx.lib.rg_temperatures_adjoint(ctx.handle, n, _dptr(B, torch.float64, "B", n * (n + 1), ctx.device),
                                               _dptr(eps, torch.float64, "eps", n, ctx.device),
                                               _dptr(area, torch.float64, "area", n, ctx.device), float(T_sink),
                                               float(sigma), _dptr(T, torch.float64, "T", n, ctx.device),
                                               _dptr(dT, torch.float64, "dT", n, ctx.device), _prec(precision),
-                                              float(tol), _dptr(dB, torch.float64, "dB"),
-                                              _dptr(deps, torch.float64, "deps"), _stream(stream)),
+                                              float(tol), _dptr(dB, torch.float64, "dB", n * (n + 1), ctx.device),
+                                              _dptr(deps, torch.float64, "deps", n, ctx.device), _stream(stream)),
               "rg_temperatures_adjoint")
     return dB, deps
 

@@ -28,6 +28,19 @@ struct rg_ctx {
   cudaEvent_t ev_read = nullptr;
   // kernels this context has launched (rg_launch_count)
   int64_t launches = 0;
+  // kernel timer (rg_kernel_timer): while on, an event pair is recorded on the launching
+  // stream around every launch of the timed kernel classes
+  struct TimedLaunch {
+    int kind;
+    int a, b;      // indices into timer_events
+    double flops;  // tensor-core flops the launch executes (2 M N K), 0 for non-GEMM kernels
+    double alg;    // algorithmic flops of the product it stands for (the fp64 residual for the
+                   // sliced refinement product), 0 for non-GEMM kernels
+  };
+  bool timer_on = false;
+  std::vector<cudaEvent_t> timer_events;
+  size_t timer_used = 0;
+  std::vector<TimedLaunch> timed;
 };
 
 namespace rg {
@@ -41,6 +54,13 @@ rg_status cuda_fail(rg_ctx* ctx, cudaError_t e, const char* what);
 rg_status workspace(rg_ctx* ctx, size_t bytes, void** out);
 
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// Kernel classes of the kernel timer (values of rg_kernel_class in radgeb.h).
+enum KernelClass { kTimeTrace = 0, kTimeResidualGemm = 1, kTimeGemm = 2, kTimeEnforce = 3, kTimeClasses = 4 };
+// Records the start event of a launch of class `kind` on stream s when the timer is on;
+// returns the token timer_end takes (-1: not recorded).
+int timer_begin(rg_ctx* ctx, int kind, cudaStream_t s, double flops = 0.0, double alg = 0.0);
+void timer_end(rg_ctx* ctx, int token, cudaStream_t s);
 
 // Carves consecutive 256-byte aligned sub-buffers out of one allocation.
 struct Carver {

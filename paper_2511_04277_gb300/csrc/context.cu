@@ -37,9 +37,71 @@ rg_status workspace(rg_ctx* ctx, size_t bytes, void** out) {
   return RG_OK;
 }
 
+namespace {
+int timer_event(rg_ctx* ctx) {
+  if (ctx->timer_used == ctx->timer_events.size()) {
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return -1;
+    ctx->timer_events.push_back(e);
+  }
+  return (int)ctx->timer_used++;
+}
+}  // namespace
+
+int timer_begin(rg_ctx* ctx, int kind, cudaStream_t s, double flops, double alg) {
+  if (!ctx->timer_on) return -1;
+  const int a = timer_event(ctx), b = timer_event(ctx);
+  if (a < 0 || b < 0 || cudaEventRecord(ctx->timer_events[a], s) != cudaSuccess) return -1;
+  ctx->timed.push_back({kind, a, b, flops, alg});
+  return (int)ctx->timed.size() - 1;
+}
+
+void timer_end(rg_ctx* ctx, int token, cudaStream_t s) {
+  if (token < 0) return;
+  if (cudaEventRecord(ctx->timer_events[ctx->timed[token].b], s) != cudaSuccess) ctx->timed[token].b = -1;
+}
+
 }  // namespace rg
 
 extern "C" {
+
+rg_status rg_kernel_timer(rg_ctx* ctx, int32_t enable) {
+  if (!ctx) return RG_ERR_ARG;
+  RG_ARG_CHECK(ctx, enable == 0 || enable == 1, "rg_kernel_timer: enable = %d", enable);
+  if (enable) {
+    ctx->timed.clear();
+    ctx->timer_used = 0;
+  }
+  ctx->timer_on = enable != 0;
+  return RG_OK;
+}
+
+rg_status rg_kernel_timer_read(rg_ctx* ctx, int32_t kind, int64_t* launches_out_h, double* ms_out_h,
+                               double* flops_out_h, double* alg_flops_out_h) {
+  if (!ctx) return RG_ERR_ARG;
+  RG_ARG_CHECK(ctx, kind >= 0 && kind < rg::kTimeClasses && launches_out_h && ms_out_h,
+               "rg_kernel_timer_read: bad argument");
+  RG_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+  int64_t n = 0;
+  double ms = 0.0, flops = 0.0, alg = 0.0;
+  for (const auto& t : ctx->timed) {
+    if (t.kind != kind) continue;
+    if (t.b < 0) return rg::fail(ctx, RG_ERR_CUDA, "rg_kernel_timer_read: an end event was not recorded");
+    RG_CUDA_TRY(ctx, cudaEventSynchronize(ctx->timer_events[t.b]));
+    float e = 0.f;
+    RG_CUDA_TRY(ctx, cudaEventElapsedTime(&e, ctx->timer_events[t.a], ctx->timer_events[t.b]));
+    ++n;
+    ms += e;
+    flops += t.flops;
+    alg += t.alg;
+  }
+  *launches_out_h = n;
+  *ms_out_h = ms;
+  if (flops_out_h) *flops_out_h = flops;
+  if (alg_flops_out_h) *alg_flops_out_h = alg;
+  return RG_OK;
+}
+
 
 const char* rg_version(void) { return "radgeb 0.1 (sm_103a)"; }
 
@@ -90,6 +152,7 @@ void rg_destroy(rg_ctx* ctx) {
   if (ctx->d_scratch) cudaFree(ctx->d_scratch);
   if (ctx->h_scratch) cudaFreeHost(ctx->h_scratch);
   if (ctx->ev_read) cudaEventDestroy(ctx->ev_read);
+  for (cudaEvent_t e : ctx->timer_events) cudaEventDestroy(e);
   delete ctx;
 }
 

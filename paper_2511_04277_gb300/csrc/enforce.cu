@@ -17,7 +17,6 @@
 #include <cfloat>
 #include <cmath>
 #include <cstring>
-#include <mutex>
 
 #include "common.cuh"
 
@@ -563,7 +562,9 @@ rg_status enforce_iterative(rg_ctx* ctx, int32_t n, const double* omega_d, const
     const double* kp = kappa_d;
     const double* op = omega_d;
     void* args[] = {&Fp, &sc, &kp, &op, &nn, &nt, &P, &pst, &ta, &mi};
+    const int tok = rg::timer_begin(ctx, rg::kTimeEnforce, s);
     RG_CUDA_TRY(ctx, cudaLaunchCooperativeKernel((const void*)kern, dim3(grid), dim3(kThreads), args, 0, s));
+    rg::timer_end(ctx, tok, s);
     ++ctx->launches;
     PersistState hp{};
     RG_CUDA_TRY(ctx, cudaMemcpyAsync(&hp, pst, sizeof(PersistState), cudaMemcpyDeviceToHost, s));
@@ -709,22 +710,10 @@ constexpr size_t kNoallocBytes = kNoallocScaleBytes + kNoallocRowSumBytes + 256 
 //         [EnforceState, 256 B][tolerance scale max|Omega|, 256 B]
 static __device__ __align__(256) unsigned char g_enforce_scratch[kNoallocBytes];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_scratch_mutex;
-void* g_scratch_ptr[kMaxDevices] = {};
-
-// Device address of g_enforce_scratch on the current device (looked up once per device).
-cudaError_t scratch_address(int device, void** out) {
-  std::lock_guard<std::mutex> lock(g_scratch_mutex);
-  if (!g_scratch_ptr[device]) {
-    void* p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, g_enforce_scratch);
-    if (e != cudaSuccess) return e;
-    g_scratch_ptr[device] = p;
-  }
-  *out = g_scratch_ptr[device];
-  return cudaSuccess;
-}
+// Device address of g_enforce_scratch on the current device. Looked up on every call (the
+// lookup is cheap next to the call's synchronisations), so that no address outlives the
+// context it was taken in.
+cudaError_t scratch_address(void** out) { return cudaGetSymbolAddress(out, g_enforce_scratch); }
 
 }  // namespace
 
@@ -732,10 +721,13 @@ extern "C" rg_status rg_enforce_iterative_noalloc(int32_t n, const double* omega
                                                   int32_t maxit, int32_t* iters_out_h, void* stream) {
   if (n <= 0 || !omega_d || !F_d || maxit <= 0 || !(tol >= 0.0)) return RG_ERR_ARG;
   if (n > kNoallocMaxN) return RG_ERR_UNSUPPORTED;  // the static scratch holds N <= 4096
+  // an error the caller's own earlier work left pending is reported, not consumed: the
+  // checks below would otherwise take it for one of this call's launches
+  if (cudaPeekAtLastError() != cudaSuccess) return RG_ERR_CUDA;
   int device = 0;
-  if (cudaGetDevice(&device) != cudaSuccess || device < 0 || device >= kMaxDevices) return RG_ERR_CUDA;
+  if (cudaGetDevice(&device) != cudaSuccess) return RG_ERR_CUDA;
   void* base = nullptr;
-  if (scratch_address(device, &base) != cudaSuccess) return RG_ERR_CUDA;
+  if (scratch_address(&base) != cudaSuccess) return RG_ERR_CUDA;
   cudaStream_t s = (cudaStream_t)stream;
   char* b = static_cast<char*>(base);
   double* sc = reinterpret_cast<double*>(b);

@@ -108,7 +108,11 @@ rg_status launch(rg_ctx* ctx, const CUtensorMap& ma, const CUtensorMap& mb, cons
     configured_device = ctx->device;
   }
   dim3 grid(((args.N + BN - 1) / BN) * ((args.M + BM - 1) / BM), 1, grid_z);
+  const double executed = 2.0 * args.M * (double)args.N * args.K;
+  const int tok = rg::timer_begin(ctx, kComp ? rg::kTimeResidualGemm : rg::kTimeGemm, s, executed,
+                                  args.alg_k > 0 ? 2.0 * args.M * (double)args.N * args.alg_k : executed);
   kern<<<grid, cta_threads<BN, kComp>(), smem, s>>>(ma, mb, args, epi);
+  rg::timer_end(ctx, tok, s);
   ++ctx->launches;
   RG_CUDA_TRY(ctx, cudaGetLastError());
   return RG_OK;
@@ -219,7 +223,8 @@ int residual_splits(const rg_ctx* ctx, int M, int N, int K, int chunk_blocks, in
 rg_status gemm_residual(rg_ctx* ctx, const void* A, int64_t lda, const void* B, int64_t ldb, int M, int N, int K,
                         int chunk_blocks, double* out, const double* E, const double* X, const double* dl,
                         int64_t ld, cudaStream_t s, unsigned long long* red, unsigned long long* colmax,
-                        int* nonfinite, double* split_ws, int split_max, int lead_blocks, int tail_chunk_blocks) {
+                        int* nonfinite, double* split_ws, int split_max, int lead_blocks, int tail_chunk_blocks,
+                        int alg_k) {
   if (M <= 0 || N <= 0) return RG_OK;
   if (K <= 0) return rg::fail(ctx, RG_ERR_ARG, "gemm_residual: K = %d", K);
   constexpr int BN = 64;
@@ -230,6 +235,7 @@ rg_status gemm_residual(rg_ctx* ctx, const void* A, int64_t lda, const void* B, 
   if (st == RG_OK) st = encode_kmajor(ctx, &mb, B, true, N, K, ldb, wide ? 128 : BN);
   if (st != RG_OK) return st;
   GemmArgs args{M, N, K, chunk_blocks, ctx->d_scratch + kGemmErrorSlot};
+  args.alg_k = alg_k;
   const int splits = (split_ws && !wide) ? residual_splits(ctx, M, N, K, chunk_blocks, split_max) : 1;
   if (splits <= 1) {
     if (lead_blocks > 0 && tail_chunk_blocks > 0 && chunk_blocks > 0 && lead_blocks % chunk_blocks == 0) {

@@ -585,7 +585,7 @@ struct Solver {
     // max|R|, max|X|, the column maxima of R and the non-finite flag come from the epilogue
     rg_status st = tc::gemm_residual(ctx, b.Aext, (int64_t)kSlices * L.np, b.Bext, (int64_t)kSlices * L.np, L.n, L.m,
                                      pairs * L.np, kResidualChunk, b.R, b.R0, b.X, dl, L.mp, s, b.red, b.colmax,
-                                     err + 1, b.split, L.splits, L.np / tc::BK, kResidualTailChunk);
+                                     err + 1, b.split, L.splits, L.np / tc::BK, kResidualTailChunk, L.n);
     if (st != RG_OK) return st;
     RG_CUDA_TRY(ctx, cudaMemcpyAsync(ctx->h_scratch + kStatus, err, 10 * sizeof(int), cudaMemcpyDeviceToHost, s));
     RG_CUDA_TRY(ctx, cudaEventRecord(ctx->ev_read, s));
@@ -1051,7 +1051,8 @@ rg_status rg_gebhart_adjoint(rg_ctx* ctx, int32_t n, const double* F_d, int32_t 
     RG_CUDA_TRY(ctx, cudaGetLastError());
     st = tc::gemm_residual(ctx, sv.b.Aext, (int64_t)kSlices * sv.L.np, sv.b.Bext, (int64_t)kSlices * sv.L.np, n,
                            n + 1, kSlices * sv.L.np, kResidualChunk, sv.b.R, nullptr, nullptr, nullptr, sv.L.mp, s,
-                           nullptr, nullptr, nullptr, sv.b.split, sv.L.splits, sv.L.np / tc::BK, kResidualTailChunk);
+                           nullptr, nullptr, nullptr, sv.b.split, sv.L.splits, sv.L.np / tc::BK, kResidualTailChunk,
+                           n);
     if (st != RG_OK) return st;
     grad_rho<<<(n + 7) / 8, 256, 0, s>>>(B_d + off, sv.b.R, sv.L.mp, n, drho_d + (size_t)set * n);
     ++ctx->launches;

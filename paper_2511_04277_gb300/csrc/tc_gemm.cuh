@@ -388,6 +388,8 @@ struct GemmArgs {
   // non-null: the kernel does nothing when *skip != 0 (written by an earlier kernel on
   // the stream; a speculatively launched product the host's decision made unnecessary)
   const int* skip = nullptr;
+  // > 0: the inner dimension of the product the launch stands for (kernel timer accounting)
+  int alg_k = 0;
 };
 
 template <int BN, int kStages, class Epi, bool kCompensated, bool kBF16>
@@ -614,7 +616,7 @@ rg_status gemm_residual(rg_ctx* ctx, const void* A, int64_t lda, const void* B, 
                         int chunk_blocks, double* out, const double* E, const double* X, const double* dl,
                         int64_t ld, cudaStream_t s, unsigned long long* red = nullptr,
                         unsigned long long* colmax = nullptr, int* nonfinite = nullptr, double* split_ws = nullptr,
-                        int split_max = 0, int lead_blocks = 0, int tail_chunk_blocks = 0);
+                        int split_max = 0, int lead_blocks = 0, int tail_chunk_blocks = 0, int alg_k = 0);
 
 // K splits gemm_residual uses for an M x N product (1: none).
 int residual_splits(const rg_ctx* ctx, int M, int N, int K, int chunk_blocks, int split_max);

@@ -887,6 +887,7 @@ rg_status trace_impl(rg_ctx* ctx, const rg_mesh* mesh, const int64_t* rays_per_f
   p.stats = d_stats;
   cudaError_t e;
   const int sm = ctx->sm_count;
+  const int tok = rg::timer_begin(ctx, rg::kTimeTrace, s);
   if (sided) {
     if (fma_free)
       e = m.use_bvh ? launch<true, true, NoStats, true>(p, sm, smem, s) : launch<true, false, NoStats, true>(p, sm, smem, s);
@@ -904,6 +905,7 @@ rg_status trace_impl(rg_ctx* ctx, const rg_mesh* mesh, const int64_t* rays_per_f
     else
       e = m.use_bvh ? launch<false, true, NoStats>(p, sm, smem, s) : launch<false, false, NoStats>(p, sm, smem, s);
   }
+  rg::timer_end(ctx, tok, s);
   if (e != cudaSuccess) return rg::cuda_fail(ctx, e, sided ? "rg_trace_sided: launch" : "rg_trace: launch");
   ++ctx->launches;
   // the host copy of the items must outlive the async upload, and the error word is read back

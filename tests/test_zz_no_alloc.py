@@ -37,9 +37,14 @@ def _noalloc(F, A):
     return st, it.value
 
 
-def test_noalloc_enforcer_matches_allocating_entry_point_on_two_calls(rg_ctx):
+# Two calls in a row per case. The first order fills the scratch's per-tile row sums
+# completely (n = 4096 takes 64-wide tiles: 64 tiles x 4096 rows is the whole region) and
+# then checks that a small call is unaffected by what that call left behind; the second
+# starts just above the tile-width switch (n = 2049, 64-wide tiles) before a 32-wide one.
+@pytest.mark.parametrize("sizes", [(4096, 300), (2049, 1000)], ids=["4096-then-300", "2049-then-1000"])
+def test_noalloc_enforcer_matches_allocating_entry_point_on_two_calls(rg_ctx, sizes):
     rng = np.random.default_rng(42)
-    for N in (300, 1000):
+    for N in sizes:
         F = _random_F(N, rng)
         A = rng.uniform(0.5, 2.0, N)
         A_d = torch.as_tensor(A, device="cuda")
