@@ -51,10 +51,11 @@ WORKLOADS = {
 }
 SIGMA = 5.67e-8
 T_SINK = 3.0
-# Refinement tolerance of the dense solves (relative residual). The product the
-# refinement residual is built on is accurate to about 1e-10 relative, and a residual of
-# 1e-10 leaves B about 1e-8 from the fp64 solution (row-normwise), inside the 1e-6 target.
-SOLVE_TOL = 1e-10
+# Refinement tolerance of the dense solves (relative residual). On the spacecraft the
+# REFs' error against the fp64 solution is the same (2.0e-7 row-normwise) for every
+# tolerance from 1e-8 to 1e-11: it is set by the accuracy of the residual product, not
+# by the sweep count, so the bench stops at 1e-9 (three sweeps instead of five).
+SOLVE_TOL = 1e-9
 # 16-bit type of the tensor-core factorisations: fp16 keeps three more mantissa bits than
 # bf16, so its approximate inverses need fewer refinement sweeps (N = 512: 2.95 against
 # 3.42 ms for the four solves); the matrices here are bounded by 1, far from fp16's range
@@ -96,6 +97,9 @@ def parse():
     ap.add_argument("--solve-once", type=int, default=None, metavar="SETS",
                     help="instead of the bench line, run the spacecraft solves (REFs, temperatures, both adjoints) "
                          "for SETS eps/rho sets once on a 1e7-ray F (the case the solver's ncu captures use)")
+    ap.add_argument("--solve-n", type=int, default=None, metavar="N",
+                    help="with --solve-once: a seeded random N-face system (F_ij ~ U[0, 1.5/N] off the diagonal, "
+                         "the rest of each row to the environment, areas U[0.5, 2]) instead of the spacecraft")
     ap.add_argument("--reflect", action="store_true",
                     help="instead of the bench line, print one JSON line with the reflection walk's rates "
                          "(REFs by MCRT) on the plates and the cube")
@@ -535,9 +539,11 @@ def fp64_comparison(torch, pipe):
     """The plain FP64 GPU path on set 0 (timed once, scaled to the sets of the step) and the
     errors of our set-0 outputs against it."""
     try:
-        n_small = 64  # cuSOLVER's handle and workspace, outside the timing
-        fp64_solve(torch, pipe.F_it[:n_small, :n_small + 1].contiguous(), pipe.eps[0, :n_small],
-                   pipe.rho[0, :n_small], pipe.areas[:n_small], pipe.Q[:n_small])
+        # cuSOLVER's handle and workspace outside the timing: one small well-posed solve
+        g = torch.Generator(device=pipe.F_it.device).manual_seed(0)
+        Kw = torch.eye(64, dtype=torch.float64, device=pipe.F_it.device) + 0.01 * torch.rand(
+            (64, 64), dtype=torch.float64, device=pipe.F_it.device, generator=g)
+        torch.linalg.solve(Kw, torch.ones((64, 2), dtype=torch.float64, device=pipe.F_it.device))
         torch.cuda.synchronize()
         box = [None]
         ms = time_region(torch, lambda: box.__setitem__(0, fp64_solve(torch, pipe.F_it, pipe.eps[0], pipe.rho[0],
@@ -1090,23 +1096,60 @@ def trace_once(scale, mesh_name="plates", sided=False):
     ctx.close()
 
 
-def solve_once(n_sets):
-    """The spacecraft solves once for `n_sets` eps / rho sets on an enforced 1e7-ray F:
-    REFs, steady temperatures and their adjoint per set, the REF adjoint (the case the
-    solver's ncu launch lists use)."""
+class _RandomSystem:
+    """A seeded random open system of n faces with the attributes of Pipeline that the
+    solve stages use (no mesh)."""
+
+    def __init__(self, ctx, n, n_sets, device):
+        import torch
+        import synth
+        from paper_2511_04277_gb300 import api
+        self.api, self.ctx, self.N, self.S = api, ctx, n, n_sets
+        g = torch.Generator(device=device).manual_seed(0)
+        F = torch.rand((n, n + 1), dtype=torch.float64, device=device, generator=g) * (1.5 / n)
+        F.diagonal()[:] = 0.0
+        F[:, n] = 0.0
+        F[:, n] = 1.0 - F.sum(dim=1)
+        self.areas = torch.rand(n, dtype=torch.float64, device=device, generator=g) * 1.5 + 0.5
+        self.F_it = F
+        api.enforce_iterative(ctx, self.F_it, self.areas, tol=1e-12)
+        eps, rho = synth.optical_sets(n, n_sets, 0.05, 0.9, seed=10)
+        self.eps = torch.as_tensor(eps, device=device)
+        self.rho = torch.as_tensor(rho, device=device)
+        self.Q = torch.as_tensor(synth.heat_loads(n, seed=3), device=device)
+        self.ones = torch.ones(n, dtype=torch.float64, device=device)
+        f64 = dict(dtype=torch.float64, device=device)
+        self.B = torch.empty((n_sets, n, n + 1), **f64)
+        self.dB = torch.empty((n_sets, n, n + 1), **f64)
+        self.T = torch.empty((n_sets, n), **f64)
+        self.deps_T = torch.empty((n_sets, n), **f64)
+
+    refs = Pipeline.refs
+    thermal = Pipeline.thermal
+    adjoint = Pipeline.adjoint
+
+
+def solve_once(n_sets, n=None):
+    """The spacecraft solves once for `n_sets` eps / rho sets on an enforced 1e7-ray F (or
+    on a seeded random n-face system): REFs, steady temperatures and their adjoint per
+    set, the REF adjoint (the case the solver's ncu captures use)."""
     import torch
     from paper_2511_04277_gb300 import api
     ctx = api.Context(0)
-    w = load_workload("spacecraft", rays_scale=0.01)
-    w["eps"], w["rho"] = w["eps"][:n_sets], w["rho"][:n_sets]
-    p = Pipeline(ctx, w, torch.device("cuda:0"))
-    p.mcrt()
-    p.enforce()
+    if n is None:
+        w = load_workload("spacecraft", rays_scale=0.01)
+        w["eps"], w["rho"] = w["eps"][:n_sets], w["rho"][:n_sets]
+        p = Pipeline(ctx, w, torch.device("cuda:0"))
+        p.mcrt()
+        p.enforce()
+    else:
+        p = _RandomSystem(ctx, n, n_sets, torch.device("cuda:0"))
     torch.cuda.synchronize()
     t = time_region(torch, lambda: (p.refs(), p.thermal(), p.adjoint()), torch.cuda.current_stream())
     print(json.dumps({"kind": "solve_once", "n": p.N, "sets": n_sets, "ms": round(t, 2), "sweeps": p.sweeps,
                       "residual": p.resid, "closure_B": float((p.B.sum(dim=-1) - 1.0).abs().max())}), flush=True)
-    p.mesh.close()
+    if n is None:
+        p.mesh.close()
     ctx.close()
 
 
@@ -1116,7 +1159,7 @@ def main():
         trace_once(args.trace_once, args.mesh, args.sided)
         return
     if args.solve_once is not None:
-        solve_once(args.solve_once)
+        solve_once(args.solve_once, args.solve_n)
         return
     if args.solve_scaling:
         print(json.dumps(solve_scaling(args)), flush=True)
