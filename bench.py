@@ -885,13 +885,15 @@ def solve_scaling(args):
         out["gemm"].append({"op": "bf16 A B^T -> fp32", "M": M, "N": N, "K": K, "ms": round(ms, 3),
                             "tflops": round(2 * M * N * K / ms / 1e9, 1)})
         del A, B, C
-    for M, N, K in ((10240, 10241, 61440),):
-        A = torch.randn(M, K, generator=g).to(torch.bfloat16).to(dev)
-        B = torch.randn(N, K, generator=g).to(torch.bfloat16).to(dev)
-        ms = ev(lambda: api.tc_gemm_residual(ctx, A, B, chunk_k=128), 3)
-        out["gemm"].append({"op": "rg_tc_gemm_residual: 6 slice pairs, compensated fp32 chunks of 128 K throughout "
-                                  "(the solver's own residual uses such chunks for the leading pair only)", "M": M, "N": N,
-                            "K": K, "ms": round(ms, 3), "tflops": round(2 * M * N * K / ms / 1e9, 1)})
+    for M, N, np_, levels in ((10240, 10241, 10240, 5),):
+        # the refinement's exact level product: integer operands |x| <= 128 in bf16
+        A = torch.randint(-128, 129, (M, 5 * np_), generator=g).to(torch.bfloat16).to(dev)
+        B = torch.randint(-128, 129, (N, np_), generator=g).to(torch.bfloat16).to(dev)
+        ms = ev(lambda: api.tc_gemm_exact(ctx, A, B, levels), 3)
+        out["gemm"].append({"op": "rg_tc_gemm_exact: exact integer level product (5 levels), int32 sums, "
+                                  "including the copy of the level sums to the caller's layout", "M": M, "N": N,
+                            "K": levels * np_, "ms": round(ms, 3),
+                            "tflops": round(2 * M * N * levels * np_ / ms / 1e9, 1)})
         del A, B
     torch.cuda.empty_cache()
     for name, scale, S in (("plates", 0.02, 1), ("small_sat", 0.02, 1), ("spacecraft", 0.01, 16)):

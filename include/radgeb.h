@@ -53,9 +53,10 @@ typedef struct rg_ctx rg_ctx;
 typedef struct rg_mesh rg_mesh;
 
 /* Precision of the dense solves (Gebhart, adjoints, radiative balance). The
- * factorisation and triangular solves run on tcgen05 tensor cores in 16-bit
- * floating point with fp32 accumulation; iterative refinement with an fp64-
- * accurate residual brings the result to the requested tolerance. */
+ * approximate inverse (Newton-Schulz iteration) and the corrections run on tcgen05
+ * tensor cores in 16-bit floating point with fp32 accumulation; iterative refinement
+ * with an exactly tracked residual (integer-exact bf16 products of fixed-point slices)
+ * brings the result to the requested tolerance. */
 typedef enum {
   RG_PREC_BF16_IR = 1,
   RG_PREC_FP16_IR = 2
@@ -384,12 +385,14 @@ rg_status rg_node_couplings(rg_ctx* ctx, int32_t n, const double* B2_d, const do
  *   eps_d    device fp64 [n_sets][n];  rho_d device fp64 [n_sets][n], 0 <= rho < 1
  *   B_d      device fp64 [n_sets][n][n+1] (output)
  *   tol      refinement stops when max_ij |R_ij| <= tol * max_ij |B_ij| for the
- *            residual R = E - K B of every set (tol >= 1e-13). The residual product is
- *            accumulated in compensated fp32 chunks, so the attainable residual is
- *            about 1e-10 to 1e-9 relative whatever smaller tol is asked for; once
- *            the residual is below 1e-8 a sweep that fails to halve it also ends
- *            the refinement (stagnation at that floor counts as converged, and
- *            resid_out_h reports where it stopped).
+ *            residual R = E - K B of every set (tol >= 1e-13). The residual is tracked
+ *            exactly: each correction is rounded to 8 bits per column and added to B
+ *            exactly, and its product with the fixed-point slices of F diag(rho) is an
+ *            exact integer sum on the tensor cores; the only error is the truncation of
+ *            those slices (below 2^-38 of max|K| max|B| per sweep), so residuals of about
+ *            1e-12 relative are attainable. Below 1e-8 a sweep that fails to halve the
+ *            residual also ends the refinement (counted as converged; resid_out_h reports
+ *            where it stopped).
  *   max_sweeps  refinement sweeps at most (>= 1)
  *   sweeps_out_h host int32 (may be NULL); resid_out_h host fp64 (may be NULL):
  *            the final relative residual (max over sets)
@@ -448,26 +451,33 @@ rg_status rg_tc_gemm(rg_ctx* ctx, int32_t M, int32_t N, int32_t K, const void* A
                      const void* B_d, int64_t ldb, int32_t fp16, float* C_d, int64_t ldc, float alpha,
                      float beta, void* stream);
 
-/* The refinement-residual form of the same GEMM (bf16 operands only):
- *   out = E - X + diag(dl) (A B^T)      or, with E_d = X_d = NULL,  out = diag(dl) (A B^T)
- * where the K loop is accumulated in fp32 chunks of chunk_k (a multiple of 64) folded
- * into a compensated sum. out_d, E_d, X_d: device fp64 [M][ld]; dl_d device fp64 [M] or
- * NULL (identity). Errors as rg_tc_gemm. */
-rg_status rg_tc_gemm_residual(rg_ctx* ctx, int32_t M, int32_t N, int32_t K, const void* A_d, int64_t lda,
-                              const void* B_d, int64_t ldb, int32_t chunk_k, double* out_d,
-                              const double* E_d, const double* X_d, const double* dl_d, int64_t ld,
-                              void* stream);
-
-/* The split the refinement product uses (App. B.2 mixed precision: the fp64 operands of
- * the residual R = E - K B enter the bf16 tensor-core GEMM as three slices each):
- *   s0 = bf16(x), s1 = bf16(x - s0), s2 = bf16(x - s0 - s1), each bf16() rounding to
- *   nearest, ties to even, and each difference taken in fp64 (it is exact).
- * The kernel forms the slices from the bit pattern of x and falls back to that fp64
- * definition where x or a slice leaves bf16's normal range; the two agree for every x.
- *   x_d       device fp64 [n]
- *   slices_d  device bf16 bits (uint16) [n][3] (output)
- * Errors: RG_ERR_ARG (n < 0 or a null pointer with n > 0). */
-rg_status rg_refinement_slices(rg_ctx* ctx, int64_t n, const double* x_d, uint16_t* slices_d, void* stream);
+/* The two pieces of the dense solves' exact refinement (App. B.2 mixed precision: the
+ * residual R = E - K B is tracked exactly while the tensor cores run in bf16), exposed for
+ * testing; no counterpart in the thesis.
+ *
+ * rg_exact_split: the fixed-point split of P' = P diag(dr) (dr may be NULL) row by row. With
+ *   e_i the exponent of max_k |P'_ik| (max = m 2^e_i, m in [0.5, 1); e_i = 0 for a zero row)
+ *   and q_ik = round(P'_ik 2^(39 - e_i)) (to nearest, ties to even; |q| < 2^39), the five
+ *   slices are the balanced base-256 digits of q: q = sum_a s_a 256^(4 - a), s_1..s_4 in
+ *   [-128, 127], |s_0| <= 128, so that P'_ik = 2^(e_i - 7) sum_a s_a 2^(-8a) to 2^(e_i - 40).
+ *   P_d       device fp64 [n][ldp] (or, with trans = 1, P_ik read as P_d[k][i])
+ *   dr_d      device fp64 [n] or NULL
+ *   slices_d  device int16 [n][5][np] (output): s_a of P'_ik at [i][a][k], zero for k >= n;
+ *             np = n rounded up to a multiple of 128
+ *   rowexp_d  device int32 [n] (output): e_i
+ *   Errors: RG_ERR_ARG; RG_ERR_NUMERIC for a non-finite P'.
+ *
+ * rg_tc_gemm_exact: the level product on tcgen05 for integer operands:
+ *   S_a[i][j] = sum_k A[i][a np + k] B[j][k]  for a = 0 .. levels-1,
+ *   A_d  device bf16 [M][lda] (lda >= 5 np), B_d device bf16 [N][np], every element an
+ *        integer of magnitude <= 128 (then every product is <= 2^14 and every 128-long chunk
+ *        sum is exact in the fp32 tensor-core accumulator); np a multiple of 128
+ *   S_d  device int32 [levels][M][N] (output), exact for |S| < 2^31
+ *   Errors: RG_ERR_ARG (layout, levels outside 1..5), RG_ERR_CUDA. */
+rg_status rg_exact_split(rg_ctx* ctx, int32_t n, const double* P_d, int64_t ldp, int32_t trans, const double* dr_d,
+                         int16_t* slices_d, int32_t* rowexp_d, void* stream);
+rg_status rg_tc_gemm_exact(rg_ctx* ctx, int32_t M, int32_t N, int32_t np, int32_t levels, const void* A_d,
+                           int64_t lda, const void* B_d, int32_t* S_d, void* stream);
 
 /* ---------------------------------------------------------------- failure-detection checks */
 

@@ -435,17 +435,6 @@ def temperatures_adjoint(ctx: Context, B, eps, area, T_sink: float, T, dT, sigma
     return dB, deps
 
 
-def refinement_slices(ctx: Context, x: torch.Tensor, stream=None) -> torch.Tensor:
-    """The three bf16 slices s0 + s1 + s2 ~ x of each entry of the fp64 vector x, as the
-    refinement product uses them (rg_refinement_slices): int16 bit patterns [n, 3]."""
-    x = x.reshape(-1)
-    out = torch.empty((x.numel(), 3), dtype=torch.int16, device=x.device)
-    ctx.check(ctx.lib.rg_refinement_slices(ctx.handle, x.numel(), _dptr(x, torch.float64, "x"),
-                                           _dptr(out, torch.int16, "slices"), _stream(stream)),
-              "rg_refinement_slices")
-    return out
-
-
 def debug_wait_timeout(ctx: Context, kind: str, limit_s: float = 0.01, stream=None):
     """Run one bounded device wait against a flag nothing sets (rg_debug_*_timeout);
     raises RadgebError(RG_ERR_CUDA) when the wait runs out, as it should."""
@@ -468,16 +457,28 @@ def tc_gemm(ctx: Context, A: torch.Tensor, B: torch.Tensor, C: torch.Tensor | No
     return C
 
 
-def tc_gemm_residual(ctx: Context, A: torch.Tensor, B: torch.Tensor, E=None, X=None, dl=None, chunk_k: int = 128,
-                     stream=None) -> torch.Tensor:
-    """E - X + diag(dl) A B^T (or diag(dl) A B^T) with compensated fp32 chunks (rg_tc_gemm_residual)."""
-    M, K = A.shape
-    N = B.shape[0]
-    out = torch.empty((M, N), dtype=torch.float64, device=A.device)
+def exact_split(ctx: Context, P: torch.Tensor, dr: torch.Tensor | None = None, trans: bool = False, stream=None):
+    """The fixed-point split of P' = P diag(dr) the exact refinement uses (rg_exact_split):
+    (slices int16 [n, 5, np], row exponents int32 [n])."""
+    n = P.shape[0]
+    np_ = (n + 127) // 128 * 128
+    sl = torch.empty((n, 5, np_), dtype=torch.int16, device=P.device)
+    ex = torch.empty(n, dtype=torch.int32, device=P.device)
     nul = ctypes.c_void_p(None)
-    ctx.check(ctx.lib.rg_tc_gemm_residual(
-        ctx.handle, M, N, K, _dptr(A, torch.bfloat16, "A"), A.stride(0), _dptr(B, torch.bfloat16, "B"), B.stride(0),
-        int(chunk_k), _dptr(out, torch.float64, "out"), nul if E is None else _dptr(E, torch.float64, "E", M * N),
-        nul if X is None else _dptr(X, torch.float64, "X", M * N),
-        nul if dl is None else _dptr(dl, torch.float64, "dl", M), N, _stream(stream)), "rg_tc_gemm_residual")
-    return out
+    ctx.check(ctx.lib.rg_exact_split(ctx.handle, n, _dptr(P, torch.float64, "P", None, ctx.device), P.stride(0),
+                                     int(bool(trans)), nul if dr is None else _dptr(dr, torch.float64, "dr", n),
+                                     _dptr(sl, torch.int16, "slices"), _dptr(ex, torch.int32, "rowexp"),
+                                     _stream(stream)), "rg_exact_split")
+    return sl, ex
+
+
+def tc_gemm_exact(ctx: Context, A: torch.Tensor, B: torch.Tensor, levels: int, stream=None) -> torch.Tensor:
+    """S_a = A_a B^T for integer bf16 operands, a < levels (rg_tc_gemm_exact): int32 [levels, M, N].
+    A: [M, >= 5 np], B: [N, np]."""
+    M = A.shape[0]
+    N, np_ = B.shape
+    S = torch.empty((levels, M, N), dtype=torch.int32, device=A.device)
+    ctx.check(ctx.lib.rg_tc_gemm_exact(ctx.handle, M, N, np_, int(levels), _dptr(A, torch.bfloat16, "A"), A.stride(0),
+                                       _dptr(B, torch.bfloat16, "B"), _dptr(S, torch.int32, "S"), _stream(stream)),
+              "rg_tc_gemm_exact")
+    return S

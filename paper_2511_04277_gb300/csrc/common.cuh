@@ -24,8 +24,8 @@ struct rg_ctx {
   // pinned host scratch for scalar read-backs
   int* h_scratch = nullptr;
   // recorded after a read-back copy, so that the host can wait for it while later
-  // launches on the stream keep the GPU busy
-  cudaEvent_t ev_read = nullptr;
+  // launches on the stream keep the GPU busy (two: the refinement alternates them)
+  cudaEvent_t ev_read[2] = {nullptr, nullptr};
   // kernels this context has launched (rg_launch_count)
   int64_t launches = 0;
   // kernel timer (rg_kernel_timer): while on, an event pair is recorded on the launching
@@ -36,11 +36,15 @@ struct rg_ctx {
     double flops;  // tensor-core flops the launch executes (2 M N K), 0 for non-GEMM kernels
     double alg;    // algorithmic flops of the product it stands for (the fp64 residual for the
                    // sliced refinement product), 0 for non-GEMM kernels
+    int level_slot = -1;  // >= 0: flops are per level, the level count is timer_levels_d[slot]
   };
   bool timer_on = false;
   std::vector<cudaEvent_t> timer_events;
   size_t timer_used = 0;
   std::vector<TimedLaunch> timed;
+  // device log of the level counts of timed exact-product launches (decided on the device)
+  int* timer_levels_d = nullptr;
+  int timer_levels_used = 0;
 };
 
 namespace rg {
@@ -60,6 +64,10 @@ enum KernelClass { kTimeTrace = 0, kTimeResidualGemm = 1, kTimeGemm = 2, kTimeEn
 // Records the start event of a launch of class `kind` on stream s when the timer is on;
 // returns the token timer_end takes (-1: not recorded).
 int timer_begin(rg_ctx* ctx, int kind, cudaStream_t s, double flops = 0.0, double alg = 0.0);
+constexpr int kTimerLevelSlots = 8192;
+// For a timed launch whose flops count per level (token from timer_begin): the device slot the
+// launch writes its level count to, or nullptr (timer off, or the log is full).
+int* timer_level_slot(rg_ctx* ctx, int token);
 void timer_end(rg_ctx* ctx, int token, cudaStream_t s);
 
 // Carves consecutive 256-byte aligned sub-buffers out of one allocation.

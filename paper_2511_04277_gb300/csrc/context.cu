@@ -56,6 +56,12 @@ int timer_begin(rg_ctx* ctx, int kind, cudaStream_t s, double flops, double alg)
   return (int)ctx->timed.size() - 1;
 }
 
+int* timer_level_slot(rg_ctx* ctx, int token) {
+  if (token < 0 || !ctx->timer_levels_d || ctx->timer_levels_used >= kTimerLevelSlots) return nullptr;
+  ctx->timed[token].level_slot = ctx->timer_levels_used;
+  return ctx->timer_levels_d + ctx->timer_levels_used++;
+}
+
 void timer_end(rg_ctx* ctx, int token, cudaStream_t s) {
   if (token < 0) return;
   if (cudaEventRecord(ctx->timer_events[ctx->timed[token].b], s) != cudaSuccess) ctx->timed[token].b = -1;
@@ -69,8 +75,12 @@ rg_status rg_kernel_timer(rg_ctx* ctx, int32_t enable) {
   if (!ctx) return RG_ERR_ARG;
   RG_ARG_CHECK(ctx, enable == 0 || enable == 1, "rg_kernel_timer: enable = %d", enable);
   if (enable) {
+    RG_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
     ctx->timed.clear();
     ctx->timer_used = 0;
+    ctx->timer_levels_used = 0;
+    if (!ctx->timer_levels_d)
+      RG_CUDA_TRY(ctx, cudaMalloc(&ctx->timer_levels_d, rg::kTimerLevelSlots * sizeof(int)));
   }
   ctx->timer_on = enable != 0;
   return RG_OK;
@@ -84,15 +94,25 @@ rg_status rg_kernel_timer_read(rg_ctx* ctx, int32_t kind, int64_t* launches_out_
   RG_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
   int64_t n = 0;
   double ms = 0.0, flops = 0.0, alg = 0.0;
+  std::vector<int> levels;
   for (const auto& t : ctx->timed) {
     if (t.kind != kind) continue;
     if (t.b < 0) return rg::fail(ctx, RG_ERR_CUDA, "rg_kernel_timer_read: an end event was not recorded");
     RG_CUDA_TRY(ctx, cudaEventSynchronize(ctx->timer_events[t.b]));
     float e = 0.f;
     RG_CUDA_TRY(ctx, cudaEventElapsedTime(&e, ctx->timer_events[t.a], ctx->timer_events[t.b]));
+    double f = t.flops;
+    if (t.level_slot >= 0) {
+      if (levels.empty()) {
+        levels.resize(ctx->timer_levels_used);
+        RG_CUDA_TRY(ctx, cudaMemcpy(levels.data(), ctx->timer_levels_d, levels.size() * sizeof(int),
+                                    cudaMemcpyDeviceToHost));
+      }
+      f *= levels[t.level_slot];
+    }
     ++n;
     ms += e;
-    flops += t.flops;
+    flops += f;
     alg += t.alg;
   }
   *launches_out_h = n;
@@ -134,7 +154,9 @@ rg_status rg_create(rg_ctx** ctx_out, int device) {
     delete ctx;
     return RG_ERR_OOM;
   }
-  if (cudaEventCreateWithFlags(&ctx->ev_read, cudaEventDisableTiming) != cudaSuccess) {
+  if (cudaEventCreateWithFlags(&ctx->ev_read[0], cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&ctx->ev_read[1], cudaEventDisableTiming) != cudaSuccess) {
+    if (ctx->ev_read[0]) cudaEventDestroy(ctx->ev_read[0]);
     cudaFree(ctx->d_scratch);
     cudaFreeHost(ctx->h_scratch);
     delete ctx;
@@ -151,8 +173,10 @@ void rg_destroy(rg_ctx* ctx) {
   if (ctx->ws) cudaFree(ctx->ws);
   if (ctx->d_scratch) cudaFree(ctx->d_scratch);
   if (ctx->h_scratch) cudaFreeHost(ctx->h_scratch);
-  if (ctx->ev_read) cudaEventDestroy(ctx->ev_read);
+  for (cudaEvent_t e : ctx->ev_read)
+    if (e) cudaEventDestroy(e);
   for (cudaEvent_t e : ctx->timer_events) cudaEventDestroy(e);
+  if (ctx->timer_levels_d) cudaFree(ctx->timer_levels_d);
   delete ctx;
 }
 

@@ -14,17 +14,26 @@
 // Algorithm (per set):
 //   1. A = I - Dl P Dr in 16-bit (bf16 or fp16), padded to a multiple of 128 with the
 //      identity, and e0 = ||Dl P Dr||_inf.
-//   2. Approximate inverse by Newton-Schulz iteration X <- X (2I - A X) from X = I: the
+//   2. Approximate inverse M by Newton-Schulz iteration X <- X (2I - A X) from X = I: the
 //      error I - A X squares every step (its inf-norm starts at e0 < 1), so
 //      ceil(log2(log(tol16) / log(e0))) + 1 steps reach the 16-bit floor. Each step is two
 //      tcgen05 GEMMs whose epilogues write the 16-bit operands of the next one (the
 //      transposed copies the K-major layout needs included).
-//   3. Solve and refine: X64 = M R0, then R = R0 - X + Dl (P (Dr X)) with P and Dr X each
-//      split into three bf16 slices (24 bits) and the six leading slice products summed by
-//      one tcgen05 GEMM over a 6N-long K with compensated fp32 chunks (fp64-accurate);
-//      X64 += M R is one more GEMM. It stops when max|R| <= tol max|X| (or stalls below
-//      1e-8, above the accuracy floor of that product).
-// The transposed systems reuse the same code with P read transposed.
+//   3. Refinement with an exactly tracked residual. P' = P Dr is split once into five
+//      fixed-point slices per row, P'_ik = 2^(e_i - 7) sum_a s_a,ik 2^(-8a) with integers
+//      |s_a| <= 128 (40 bits below the row maximum). Starting from R = R0, X = 0, every
+//      sweep takes the correction D = M R (one tensor-core GEMM), rounds each column of D to
+//      one 8-bit fixed-point slice (integers |d| <= 128 times 2^(f_j - 7)), adds it to X
+//      exactly and updates R <- R - D + Dl (P' D). The product P' D is a sum of integer
+//      products; every 128-long chunk of it is exact in the fp32 tensor-core accumulator and
+//      the chunks are added as integers, so the only error of the update is the truncation
+//      of P' to the levels used (L levels: 2^-(8L-1) of |P'| |D|, L chosen per sweep from
+//      max|D| / max|X| so that it stays below 2^-38 of |P'| |X|). The residual is thus known
+//      to ~1e-12 whatever the tensor cores' rounding, and the refinement converges to the
+//      fp64 solution instead of a biased one. It stops when max|R| <= tol max|X| (or stalls
+//      below 1e-8).
+// The transposed systems reuse the same code with P read transposed; the REF adjoint also
+// accumulates sum_k P' D_k = F^T Lambda, the product its rho gradient needs.
 #include <cmath>
 #include <utility>
 
@@ -33,17 +42,16 @@
 namespace {
 
 constexpr int NB = 128;          // panel width == GEMM tile height
-constexpr int kSlices = 6;       // slice pairs of the refinement product
-constexpr int kResidualChunk = 2;  // K blocks (of 64) per compensated fp32 chunk (leading pair)
-constexpr int kResidualTailChunk = 16;  // K blocks per chunk for the pairs after the leading one
 constexpr int kThreads = 256;
 // Below this relative residual a sweep that no longer halves it ends the refinement.
-// The residual product's own accuracy floor (fp32 accumulation inside each 128-long
-// chunk) was measured between 1e-10 and 1.3e-9 for N = 512 ... 10,240.
 constexpr double kStallFloor = 1e-8;
 constexpr int kMaxNewtonSchulz = 24;
-// Sweeps whose previous relative residual is above this use half of the slice pairs.
-constexpr double kCoarseAbove = 1e-3;
+// Fixed-point levels of P' (8 bits each) and the resolution the level count of a sweep
+// keeps: the levels dropped from P' D stay below 2^-kLevelBits of max|P'| max|X|.
+constexpr int kLevels = 5;
+constexpr int kLevelBits = 38;
+// Most K splits of the exact product (used when its tiles leave SMs idle).
+constexpr int kMaxExactSplits = 4;
 
 __device__ __forceinline__ double p_elem(const double* P, int64_t ldp, bool trans, int i, int k) {
   return trans ? P[(int64_t)k * ldp + i] : P[(int64_t)i * ldp + k];
@@ -56,187 +64,187 @@ __device__ __forceinline__ __nv_bfloat16 to16<__nv_bfloat16>(float x) { return _
 template <>
 __device__ __forceinline__ __half to16<__half>(float x) { return __float2half_rn(x); }
 
-// Split x into three bf16 slices whose sum carries ~24 significant bits:
-// s0 = bf16(x), s1 = bf16(x - s0), s2 = bf16(x - s0 - s1), each rounding to nearest, ties to
-// even, and each difference exact. GB300 runs fp64 (conversions included) at a small
-// fraction of its integer rate, so the hot callers take the split on the bit pattern
-// (split3_bits) and fall back to the fp64 definition (split3_fp64) only where an input or
-// an intermediate leaves the ranges the integer path covers. Both give the same slices
-// for every input.
-__device__ __forceinline__ void split3_fp64(double x, __nv_bfloat16* s) {
-  s[0] = __double2bfloat16(x);
-  const double r = x - (double)__bfloat162float(s[0]);
-  s[1] = __double2bfloat16(r);
-  s[2] = __double2bfloat16(r - (double)__bfloat162float(s[1]));
+// ------------------------------------------------------------------ exact refinement kernels
+// Exponent e of a non-negative finite double x > 0 with x = m 2^e, m in [0.5, 1) (frexp's).
+__device__ __forceinline__ int frexp_exponent(double x) {
+  int e;
+  frexp(x, &e);
+  return e;
 }
 
-// Bits 31..24 of the normalised magnitude h (leading one at bit 31; l holds the bits
-// below h's) rounded to nearest, ties to even, as a bf16 of sign sg (bit 31) and biased
-// exponent be; (h, l) becomes the remainder's magnitude in the same frame and sg its sign.
-__device__ __forceinline__ __nv_bfloat16 round8_bits(uint32_t& h, uint32_t& l, uint32_t& sg, int be) {
-  const uint32_t up = ((h >> 23) & 1u) & ((((h & 0x007fffffu) | l) != 0u) | ((h >> 24) & 1u));
-  const __nv_bfloat16 v =
-      __ushort_as_bfloat16((unsigned short)((sg >> 16) | (((uint32_t)be << 7) + ((h >> 24) + up - 128u))));
-  h &= 0x00ffffffu;
-  if (up) {  // the remainder is negative: 2^24 (in units of h's bit 0) minus the dropped bits
-    h = 0x01000000u - h - (l != 0u);
-    l = 0u - l;
-    sg ^= 0x80000000u;
-  }
-  return v;
+// x 2^k (exact unless the result leaves the normal range).
+__device__ __forceinline__ double scale2(double x, int k) {
+  if (k >= -1022 && k <= 1023) return x * __longlong_as_double((long long)(k + 1023) << 52);
+  return ldexp(x, k);
 }
 
-// Shift the 64-bit magnitude (h, l) != 0 left until its leading one is bit 31 of h;
-// returns the leading bit's position before the shift (0 .. 63).
-__device__ __forceinline__ int normalise_bits(uint32_t& h, uint32_t& l) {
-  if (h != 0u) {
-    const int sh = __clz((int)h);
-    if (sh) {
-      h = (h << sh) | (l >> (32 - sh));
-      l <<= sh;
-    }
-    return 63 - sh;
-  }
-  const int sh = __clz((int)l);
-  h = l << sh;
-  l = 0u;
-  return 31 - sh;
+// Levels of P' that a sweep uses: the dropped ones stay below 2^-kLevelBits of
+// max|P'| max|X|, with max|X| and max|D| in red[1] and red[2] (the sweep's status words).
+__device__ __forceinline__ int exact_levels(const unsigned long long* red) {
+  return tc::exact_level_count(red, kLevelBits, kLevels);
 }
 
-// split3 on the two 32-bit words of x, for x zero or 2^-126 <= |x| < 2^127 with normal
-// slices; false elsewhere (the slices are then unusable). The significand M of x (53 bits,
-// unit ulp(x) = 2^(E - 1075)) is rounded to 8 bits at bit 45; the remainder, a signed
-// integer of at most 45 bits in the same unit, is normalised and rounded to 8 bits; what
-// that leaves is normalised and rounded once more.
-__device__ __forceinline__ bool split3_bits(double x, __nv_bfloat16* s) {
-  const uint32_t hi = (uint32_t)__double2hiint(x), lo = (uint32_t)__double2loint(x);
-  uint32_t sg = hi & 0x80000000u;
-  const uint32_t t = hi & 0x7fffffffu;
+// Fixed-point split of P' = P Dr (Dr may be null) into kLevels slices per row: with e_i the
+// exponent of max_k |P'_ik| and q = round(P'_ik 2^(39 - e_i)) (|q| < 2^39, to nearest, ties
+// to even), the slices are q's balanced base-256 digits, q = sum_a s_a 256^(4 - a) with
+// s_1..s_4 in [-128, 127] and |s_0| <= 128, so that P'_ik = 2^(e_i - 7) sum_a s_a 2^(-8a)
+// up to 2^(e_i - 40). Aex[i][a np + k] = s_a (exact in bf16), zero in the padding;
+// rowexp[i] = e_i (0 for a zero row). A non-finite entry raises *err. One warp per row.
+__global__ void build_p_exact(const double* __restrict__ P, int64_t ldp, bool trans, const double* __restrict__ dr,
+                              int n, int np, __nv_bfloat16* __restrict__ Aex, int* __restrict__ rowexp, int* err) {
+  const int i = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+  const int lane = threadIdx.x & 31;
+  if (i >= np) return;
+  __nv_bfloat16* row = Aex + (int64_t)i * kLevels * np;
   const __nv_bfloat16 zero = __ushort_as_bfloat16((unsigned short)0);
-  if ((t | lo) == 0u) {
-    s[0] = __ushort_as_bfloat16((unsigned short)(sg >> 16));
-    s[1] = s[2] = zero;
-    return true;
-  }
-  const int E = (int)(t >> 20);
-  bool ok = E >= 897 && E <= 1149;
-  // s0: the 7 leading mantissa bits, rounded at bit 12 of the high word (bit 44 of x)
-  const uint32_t up = ((t & 0x1fffu) + 0xfffu + ((lo != 0u) | ((t >> 13) & 1u))) >> 13;
-  s[0] = __ushort_as_bfloat16((unsigned short)((sg >> 16) | ((((t & ~0x1fffu) + (up << 13)) >> 13) - (896u << 7))));
-  // D = M - s0 in units of ulp(x): the dropped 45 bits, or 2^45 minus them when rounded up
-  uint32_t h = t & 0x1fffu, l = lo;
-  if (up) {
-    h = 0x2000u - h - (l != 0u);
-    l = 0u - l;
-    sg ^= 0x80000000u;
-  }
-  if ((h | l) == 0u) {
-    s[1] = s[2] = zero;
-    return ok;
-  }
-  const int p1 = normalise_bits(h, l);  // bf16 exponent of D's bit 0: E - 1075 + 127
-  const int be1 = E - 948 + p1;
-  s[1] = round8_bits(h, l, sg, be1);
-  if ((h | l) == 0u) {
-    s[2] = zero;
-    return ok && be1 >= 1;
-  }
-  const int be2 = be1 - 63 + normalise_bits(h, l);  // the frame was shifted by 63 - p1
-  s[2] = round8_bits(h, l, sg, be2);
-  return ok && be1 >= 1 && be2 >= 1;
-}
-
-// The split of x_d[i] into slices_d[3 i .. 3 i + 2] (rg_refinement_slices). The loop's
-// trip count is the same for every thread of a block, so the vote sees whole warps.
-__global__ void split_slices(const double* __restrict__ x, int64_t n, __nv_bfloat16* __restrict__ out) {
-  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t i = base + threadIdx.x;
-    const bool in = i < n;
-    const double v = in ? x[i] : 0.0;
-    __nv_bfloat16 s[3];
-    const bool ok = split3_bits(v, s);
-    if (__any_sync(0xffffffffu, !ok)) {
-      if (!ok) split3_fp64(v, s);
-    }
-    if (in) {
-      out[3 * i] = s[0];
-      out[3 * i + 1] = s[1];
-      out[3 * i + 2] = s[2];
-    }
-  }
-}
-
-// K-concatenated pair order of the refinement product: (P_a, Y_b) for
-// (0,0) (0,1) (1,0) (0,2) (1,1) (2,0).
-__constant__ int kPairA[kSlices] = {0, 0, 1, 0, 1, 2};
-__constant__ int kPairB[kSlices] = {0, 1, 0, 2, 1, 0};
-
-// A_ext[i][q * Np + k] = slice kPairA[q] of P(i, k); zero in the padding.
-__global__ void build_p_slices(const double* __restrict__ P, int64_t ldp, bool trans, int n, int np,
-                               __nv_bfloat16* __restrict__ Aext) {
-  const int64_t total = (int64_t)np * np;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-    int i = (int)(e / np), k = (int)(e % np);
-    __nv_bfloat16 s[3];
-    double x = (i < n && k < n) ? p_elem(P, ldp, trans, i, k) : 0.0;
-    if (!split3_bits(x, s)) split3_fp64(x, s);
-    __nv_bfloat16* row = Aext + (int64_t)i * (kSlices * (int64_t)np);
+  if (i >= n) {
+    for (int k = lane; k < np; k += 32)
 #pragma unroll
-    for (int q = 0; q < kSlices; ++q) row[(int64_t)q * np + k] = s[kPairA[q]];
+      for (int a = 0; a < kLevels; ++a) row[(int64_t)a * np + k] = zero;
+    if (lane == 0) rowexp[i] = 0;
+    return;
   }
+  double mx = 0.0;
+  bool bad = false;
+  for (int k = lane; k < n; k += 32) {
+    const double x = p_elem(P, ldp, trans, i, k) * (dr ? dr[k] : 1.0);
+    bad |= !isfinite(x);
+    mx = fmax(mx, fabs(x));
+  }
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if (__any_sync(0xffffffffu, bad)) {
+    if (lane == 0) atomicExch(err, 1);
+    mx = 0.0;  // the slices are not used once the error is raised
+  }
+  const int e = mx > 0.0 ? frexp_exponent(mx) : 0;
+  const double sc = mx > 0.0 ? ldexp(1.0, 39 - e) : 0.0;
+  for (int k = lane; k < np; k += 32) {
+    long long q = 0;
+    if (k < n && mx > 0.0) q = __double2ll_rn(p_elem(P, ldp, trans, i, k) * (dr ? dr[k] : 1.0) * sc);
+    int d[kLevels];
+#pragma unroll
+    for (int a = kLevels - 1; a > 0; --a) {
+      d[a] = (int)((q + 128) & 255) - 128;
+      q = (q - d[a]) >> 8;
+    }
+    d[0] = (int)q;
+#pragma unroll
+    for (int a = 0; a < kLevels; ++a) row[(int64_t)a * np + k] = __float2bfloat16_rz((float)d[a]);
+  }
+  if (lane == 0) rowexp[i] = e;
 }
 
-// B_ext[j][q * Np + k] = slice kPairB[q] of (Dr X)(k, j); the refinement product's B operand.
-// Tiled transpose through shared memory: block (32 x 8) covers a 32 x 32 tile of X. With
-// red / colmax set it also zeroes red[0..1] and colmax[0 .. mp) for the residual GEMM that
-// follows it on the stream (no separate memset).
-__global__ void build_x_slices(const double* __restrict__ X, int64_t ldx, const double* __restrict__ dr, int n,
-                               int m, int np, int mp, __nv_bfloat16* __restrict__ Bext,
-                               unsigned long long* red = nullptr, unsigned long long* colmax = nullptr) {
-  __shared__ __nv_bfloat16 tile[3][32][33];
+// Rounds each column j < m of the correction D (fp32, ld = mp) to one 8-bit fixed-point slice:
+// f_j = the exponent of max_k |D_kj| (colmax, float bits), d = round(D_kj 2^(7 - f_j)) clamped to
+// [-127, 127]. Writes Bq[j][k] = d (bf16, the exact product's B operand, zero in the padding),
+// Dn[k][j] = d, dexp[j] = f_j and adds d 2^(f_j - 7) to X (first: X = that); folds max|X| into
+// red[1], max_j colmax_j into red[2] (as doubles; both zeroed by the sweep's first kernel) and
+// zeroes the column maxima of R for the residual that follows. Tiled transpose, block (32 x 8).
+__global__ void quantize_correction(const float* __restrict__ D, int n, int m, int np, int mp,
+                                    const unsigned int* __restrict__ dcolmax, __nv_bfloat16* __restrict__ Bq,
+                                    int16_t* __restrict__ Dn, int* __restrict__ dexp, double* __restrict__ X,
+                                    int first, unsigned long long* red, unsigned long long* rcolmax, int* nonfinite,
+                                    const int* skip) {
+  if (skip && *(volatile const int*)skip) return;
+  __shared__ __nv_bfloat16 tile[32][34];
+  __shared__ unsigned long long s_xmax;
+  if (threadIdx.x == 0 && threadIdx.y == 0) s_xmax = 0ull;
   const int k0 = blockIdx.y * 32, j0 = blockIdx.x * 32;
+  const int j = j0 + threadIdx.x;
+  const unsigned int cb = j < m ? dcolmax[j] : 0u;
+  const bool cfin = cb < 0x7f800000u;
+  int f = 0;
+  if (cb != 0u && cfin) f = frexp_exponent((double)__uint_as_float(cb));
+  const float sc = ldexpf(1.f, 7 - f);
+  const double unit = ldexp(1.0, f - 7);
   if (blockIdx.y == 0 && threadIdx.y == 0) {
-    if (colmax && j0 + (int)threadIdx.x < mp) colmax[j0 + threadIdx.x] = 0ull;
-    if (red && blockIdx.x == 0 && threadIdx.x < 2) red[threadIdx.x] = 0ull;
-  }
-  for (int r = threadIdx.y; r < 32; r += 8) {  // warp-uniform: threadIdx.y is the warp
-    const int k = k0 + r, j = j0 + threadIdx.x;
-    const bool in = k < n && j < m;
-    double xv = 0.0, dv = 1.0;
-    if (in) {
-      xv = X[(int64_t)k * ldx + j];
-      if (dr) dv = dr[k];
+    if (j < mp) {
+      dexp[j] = f;
+      rcolmax[j] = 0ull;
     }
-    const double x = in ? xv * dv : 0.0;
-    __nv_bfloat16 s[3];
-    const bool ok = split3_bits(x, s);
-    if (__any_sync(0xffffffffu, !ok)) {  // the fp64 definition, for the lanes that need it
-      if (!ok) split3_fp64(x, s);
-    }
-    tile[0][r][threadIdx.x] = s[0];
-    tile[1][r][threadIdx.x] = s[1];
-    tile[2][r][threadIdx.x] = s[2];
+    if (j < m && cfin) atomicMax(&red[2], (unsigned long long)__double_as_longlong((double)__uint_as_float(cb)));
+    if (j < m && !cfin) atomicExch(nonfinite, 1);
   }
   __syncthreads();
+  unsigned long long xmax = 0ull;
   for (int r = threadIdx.y; r < 32; r += 8) {
-    int j = j0 + r, k = k0 + threadIdx.x;
-    if (j >= mp || k >= np) continue;
-    __nv_bfloat16* row = Bext + (int64_t)j * (kSlices * (int64_t)np);
-#pragma unroll
-    for (int q = 0; q < kSlices; ++q) row[(int64_t)q * np + k] = tile[kPairB[q]][threadIdx.x][r];
+    const int k = k0 + r;
+    const bool in = k < n && j < m;
+    int q = 0;
+    if (in) {
+      q = __float2int_rn(D[(int64_t)k * mp + j] * sc);
+      q = q > 127 ? 127 : (q < -127 ? -127 : q);
+      const int64_t o = (int64_t)k * mp + j;
+      Dn[o] = (int16_t)q;
+      const double v = (double)q * unit + (first ? 0.0 : X[o]);
+      X[o] = v;
+      xmax = max(xmax, (unsigned long long)__double_as_longlong(fabs(v)) & 0x7fffffffffffffffull);
+    }
+    tile[r][threadIdx.x] = __float2bfloat16_rz((float)q);
+  }
+  atomicMax(&s_xmax, xmax);
+  __syncthreads();
+  for (int r = threadIdx.y; r < 32; r += 8) {
+    const int jj = j0 + r, kk = k0 + threadIdx.x;
+    if (jj < mp && kk < np) Bq[(int64_t)jj * np + kk] = tile[threadIdx.x][r];
+  }
+  if (threadIdx.x == 0 && threadIdx.y == 0 && s_xmax) atomicMax(&red[1], s_xmax);
+}
+
+// The residual update after the exact product: with S = P' D assembled from the integer level
+// sums (T = sum_z sum_a lev[z][a] 256^(L - 1 - a), S_ij = T 2^(e_i + f_j - 14 - 8(L - 1))),
+//   R_ij <- (first ? R0_ij : R_ij) - D_ij + dl_i S_ij,   D_ij = Dn_ij 2^(f_j - 7),
+// and, with Q, Q_ij <- (first ? 0 : Q_ij) + S_ij. Folds max|R| into red[0], max_i |R_ij| into
+// colmax[j] (as doubles) and raises *nonfinite on an inf or NaN. Block (32 x 8) per 32 columns
+// x 32 rows.
+__global__ void finish_residual(const int32_t* __restrict__ lev, int64_t ldl, int64_t plane, int splits,
+                                const int* __restrict__ rowexp, const int* __restrict__ dexp,
+                                const int16_t* __restrict__ Dn, const double* __restrict__ dl, int n, int m, int mp,
+                                const double* __restrict__ R0, double* __restrict__ R, double* __restrict__ Q,
+                                int first, unsigned long long* red, unsigned long long* colmax, int* nonfinite,
+                                const int* skip) {
+  if (skip && *(volatile const int*)skip) return;
+  __shared__ unsigned long long s_col[8][33];
+  const int L = exact_levels(red);
+  const int j = blockIdx.x * 32 + threadIdx.x;
+  const int i0 = blockIdx.y * 32;
+  unsigned long long cmax = 0ull;
+  bool bad = false;
+  if (j < m) {
+    const int f = dexp[j];
+    for (int i = i0 + threadIdx.y; i < min(n, i0 + 32); i += 8) {
+      const int64_t o = (int64_t)i * ldl + j;
+      long long T = 0;
+      for (int z = 0; z < splits; ++z) {
+        long long t = 0;
+        for (int a = 0; a < L; ++a) t = t * 256 + lev[((int64_t)z * kLevels + a) * plane + o];
+        T += t;
+      }
+      const double S = scale2((double)T, rowexp[i] + f - 14 - 8 * (L - 1));
+      const int64_t e = (int64_t)i * mp + j;
+      const double d = scale2((double)Dn[e], f - 7);
+      const double r = ((first ? R0[e] : R[e]) - d) + (dl ? dl[i] : 1.0) * S;
+      R[e] = r;
+      if (Q) Q[e] = (first ? 0.0 : Q[e]) + S;
+      const unsigned long long rb = (unsigned long long)__double_as_longlong(r) & 0x7fffffffffffffffull;
+      bad |= rb >= 0x7ff0000000000000ull;
+      cmax = max(cmax, rb >= 0x7ff0000000000000ull ? 0ull : rb);
+    }
+  }
+  s_col[threadIdx.y][threadIdx.x] = cmax;
+  if (__syncthreads_or(bad) && threadIdx.x == 0 && threadIdx.y == 0) atomicExch(nonfinite, 1);
+  if (threadIdx.y == 0) {
+    for (int y = 1; y < 8; ++y) cmax = max(cmax, s_col[y][threadIdx.x]);
+    if (j < m && cmax) atomicMax(&colmax[j], cmax);
+    for (int o = 16; o > 0; o >>= 1) cmax = max(cmax, __shfl_xor_sync(0xffffffffu, cmax, o));
+    if (threadIdx.x == 0 && cmax) atomicMax(&red[0], cmax);
   }
 }
 
-// A = I - Dl P Dr (fp32), identity in the padding.
-__global__ void build_a32(const double* __restrict__ P, int64_t ldp, bool trans, const double* __restrict__ dl,
-                          const double* __restrict__ dr, int n, int np, float* __restrict__ A) {
-  const int64_t total = (int64_t)np * np;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-    int i = (int)(e / np), k = (int)(e % np);
-    double v = (i == k) ? 1.0 : 0.0;
-    if (i < n && k < n) v -= (dl ? dl[i] : 1.0) * p_elem(P, ldp, trans, i, k) * (dr ? dr[k] : 1.0);
-    A[e] = (float)v;
-  }
+// out[e] = (int16) of the integer-valued bf16 in[e] (rg_exact_split's output form).
+__global__ void bf16_rows_to_int16(const __nv_bfloat16* __restrict__ in, int64_t total, int16_t* __restrict__ out) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x)
+    out[e] = (int16_t)__float2int_rz(__bfloat162float(in[e]));
 }
 
 // (float)(x * 2^-e) on the two 32-bit words of x, for x zero, or normal with x 2^-e and
@@ -312,34 +320,38 @@ __global__ void column_max(const double* __restrict__ R, int64_t ld, int n, int 
   }
 }
 
-// The refinement's stopping rule evaluated on the device, for a correction launched
-// before the host has read the residual it corrects: status = the solver's status words
-// (null: no guard), tol / prev / coarse as the host's loop has them. When the sweep ends
-// the refinement (converged or stalled) or reported an error, the correction is skipped:
-// the transposition returns at once and sets *skip, which its GEMM reads.
+// The refinement's stopping rule evaluated on the device, for a sweep launched before the
+// host has read the residual of the sweep before it: err = the solver's error words, red =
+// that sweep's status words (max|R|, max|X|), tol / prev as the host's loop has them. When
+// that sweep ended the refinement (converged or stalled) or an error was reported, the new
+// sweep is skipped: its first kernel returns at once and sets *skip, which the others read.
 struct SweepGuard {
-  const int* status = nullptr;
+  const int* err = nullptr;
+  const unsigned long long* red = nullptr;
   double tol = 0.0, prev = 0.0;
-  int coarse = 0;
   int* skip = nullptr;
 };
 
 __device__ __forceinline__ bool sweep_ends(const SweepGuard& g) {
-  const volatile int* w = g.status;
-  const double r = __hiloint2double(w[7], w[6]), x = __hiloint2double(w[9], w[8]);
+  const volatile int* w = g.err;
+  const volatile unsigned long long* red = g.red;
+  const double r = __longlong_as_double((long long)red[0]), x = __longlong_as_double((long long)red[1]);
   const double rel = x > 0 ? r / x : r;
-  const bool done = !g.coarse && (rel <= g.tol || (rel <= kStallFloor && rel > 0.5 * g.prev));
+  const bool done = rel <= g.tol || (rel <= kStallFloor && rel > 0.5 * g.prev);
   return done || w[0] || w[1] || w[4];
 }
 
 // Rt16[j][i] = 16-bit (R_ij * 2^-e_j) with max_i |R_ij| 2^-e_j in [0.5, 1), zero padding;
 // colscale[j] = 2^e_j. Tiled transpose through shared memory, block (32 x 8).
+// The first kernel of a sweep: it also zeroes the sweep's status words (red_cur: max|R|,
+// max|X|, max|D|) and the column maxima of the correction (dcolmax[0 .. mp)).
 template <class T16>
 __global__ void scaled_transpose16(const double* __restrict__ R, int64_t ld, int n, int m, int np, int mp,
                                    const unsigned long long* __restrict__ colmax, T16* __restrict__ Rt,
-                                   float* __restrict__ colscale, const SweepGuard guard) {
+                                   float* __restrict__ colscale, const SweepGuard guard,
+                                   unsigned long long* red_cur, unsigned int* dcolmax) {
   __shared__ float tile[32][33];
-  if (guard.status) {  // one thread per block evaluates the rule (an fp64 division), the block follows
+  if (guard.err) {  // one thread per block evaluates the rule (an fp64 division), the block follows
     __shared__ int s_end;
     if (threadIdx.x == 0 && threadIdx.y == 0) {
       s_end = sweep_ends(guard) ? 1 : 0;
@@ -350,6 +362,8 @@ __global__ void scaled_transpose16(const double* __restrict__ R, int64_t ld, int
   }
   const int i0 = blockIdx.y * 32, j0 = blockIdx.x * 32;
   const int j = j0 + threadIdx.x;
+  if (blockIdx.y == 0 && threadIdx.y == 0 && j < mp) dcolmax[j] = 0u;
+  if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.y == 0 && threadIdx.x < 3) red_cur[threadIdx.x] = 0ull;
   // e_j from the bits of max_i |R_ij| (a non-negative double): frexp's exponent, or 0
   // when the maximum is 0 or not finite
   int e = 0;
@@ -387,11 +401,8 @@ inline int grid_for(int64_t total, int sm) {
 // ------------------------------------------------------------------ solver object
 struct Layout {
   int n, m, np, mp;
-  int splits;  // room for this many K splits of the residual GEMM (0: none)
+  bool want_q;  // accumulate Q = P' X (the REF adjoint's F^T Lambda)
 };
-
-// Most K splits of the refinement residual GEMM (used when its tiles leave SMs idle).
-constexpr int kMaxResidualSplits = 4;
 
 struct Buffers {
   void* A16;      // np x np
@@ -400,15 +411,20 @@ struct Buffers {
   void* Zt16;     // np x np, (2I - A X)^T
   void* Rt16;     // mp x np, scaled transposed right-hand side / residual
   float* colscale;               // mp
-  unsigned long long* colmax;    // mp
-  __nv_bfloat16* Aext;           // np x 6np
-  __nv_bfloat16* Bext;           // mp x 6np
+  unsigned long long* colmax;    // mp, column maxima of R (double bits)
+  __nv_bfloat16* Aex;            // np x kLevels np, fixed-point slices of P'
+  int* rowexp;                   // np
+  float* Dbuf;                   // np x mp, correction M R before rounding
+  unsigned int* dcolmax;         // mp, its column maxima (float bits)
+  __nv_bfloat16* Bq;             // mp x np, the rounded correction, transposed
+  int16_t* Dn;                   // np x mp, the rounded correction's integers
+  int* dexp;                     // mp, its column exponents
+  int32_t* lev;                  // kMaxExactSplits x kLevels planes of exact_plane(n, m)
   double* R0;   // right-hand side (ld = mp)
   double* X;    // solution (ld = mp)
   double* R;    // residual (ld = mp)
+  double* Q;    // P' X (ld = mp) when want_q, else null
   double* vec;  // [2][np] per-row scratch (row sums, diagonal scalings)
-  unsigned long long* red;  // [4] max|R|, max|X|, ||E||_inf, ||E||_1 bits (context status words, see Solver)
-  double* split;  // [splits][np][mp] partial sums of a split residual GEMM (or null)
 };
 
 template <class Take>
@@ -417,22 +433,29 @@ void plan(const Layout& L, Take&& t) {
   t.template take<uint16_t>((size_t)L.mp * L.np);                 // Rt16
   t.template take<float>((size_t)L.mp);                           // colscale
   t.template take<unsigned long long>((size_t)L.mp);              // colmax
-  t.template take<__nv_bfloat16>((size_t)L.np * kSlices * L.np);  // Aext
-  t.template take<__nv_bfloat16>((size_t)L.mp * kSlices * L.np);  // Bext
+  t.template take<__nv_bfloat16>((size_t)L.np * kLevels * L.np);  // Aex
+  t.template take<int>((size_t)L.np);                             // rowexp
+  t.template take<float>((size_t)L.np * L.mp);                    // Dbuf
+  t.template take<unsigned int>((size_t)L.mp);                    // dcolmax
+  t.template take<__nv_bfloat16>((size_t)L.mp * L.np);            // Bq
+  t.template take<int16_t>((size_t)L.np * L.mp);                  // Dn
+  t.template take<int>((size_t)L.mp);                             // dexp
+  t.template take<int32_t>((size_t)kMaxExactSplits * kLevels * tc::exact_plane(L.n, L.m));  // lev
   t.template take<double>((size_t)L.np * L.mp);                   // R0
   t.template take<double>((size_t)L.np * L.mp);                   // X
   t.template take<double>((size_t)L.np * L.mp);                   // R
+  t.template take<double>(L.want_q ? (size_t)L.np * L.mp : 0);    // Q
   t.template take<double>((size_t)2 * L.np);                      // vec
-  t.template take<double>((size_t)L.splits * L.np * L.mp);        // split
 }
 
 // The solver's status words in the context scratch (ints), laid out so that one copy
 // returns everything a sweep's decision needs: [0] input error of the calling kernels,
-// [1] non-finite solution or residual, [4] the GEMM wait time-out word, [5] the skip word
-// of a speculatively launched correction (SweepGuard), [6..7] max|R|,
-// [8..9] max|X|, [10..11] ||E||_inf and [12..13] ||E||_1 of the first Newton-Schulz
-// iterate's E (doubles as bits).
+// [1] non-finite value, [4] the GEMM wait time-out word, [5] the skip word of a
+// speculatively launched sweep (SweepGuard), [6..7] ||E||_inf and [8..9] ||E||_1 of the
+// first Newton-Schulz iterate's E, then per sweep parity p the sweep's words at [10 + 6p ..]:
+// max|R|, max|X|, max|D| (doubles as bits).
 constexpr int kStatus = 12;
+constexpr int kStatusInts = 22;
 static_assert(kStatus + 4 == tc::kGemmErrorSlot, "the GEMM error word sits in the status block");
 
 struct Solver {
@@ -441,24 +464,26 @@ struct Solver {
   Buffers b;
   bool bf16;
   cudaStream_t s;
-  int* err;          // device status words (kStatus): [0] input error, [1] non-finite
+  int* err;          // device status words (kStatus)
   const char* input_error = "invalid input to the solver";  // what err[0] means for the caller
   const double* P;
   int64_t ldp;
   bool transP;
   int cur = 0;       // which X16 buffer holds the current inverse
   int ns_steps = 0;
+  int splits = 1;    // K splits of the last exact product
+
+  unsigned long long* red(int parity) { return reinterpret_cast<unsigned long long*>(err + 10 + 6 * parity); }
 
   // Carves the solver's buffers out of the context workspace, after `extra_bytes`
   // reserved for the caller (returned in *extra).
-  rg_status setup(int n, int m, bool use_bf16, cudaStream_t stream, size_t extra_bytes = 0, void** extra = nullptr) {
+  rg_status setup(int n, int m, bool use_bf16, cudaStream_t stream, size_t extra_bytes = 0, void** extra = nullptr,
+                  bool want_q = false) {
     L.n = n;
     L.m = m;
     L.np = (n + NB - 1) / NB * NB;
     L.mp = (m + NB - 1) / NB * NB;
-    L.splits = tc::residual_splits(ctx, L.n, L.m, kSlices * L.np, kResidualChunk, kMaxResidualSplits) > 1
-                   ? kMaxResidualSplits
-                   : 0;
+    L.want_q = want_q;
     bf16 = use_bf16;
     s = stream;
     extra_bytes = rg::align_up(extra_bytes, 256);
@@ -477,26 +502,37 @@ struct Solver {
     b.Rt16 = cv.take<uint16_t>((size_t)L.mp * L.np);
     b.colscale = cv.take<float>(L.mp);
     b.colmax = cv.take<unsigned long long>(L.mp);
-    b.Aext = cv.take<__nv_bfloat16>((size_t)L.np * kSlices * L.np);
-    b.Bext = cv.take<__nv_bfloat16>((size_t)L.mp * kSlices * L.np);
+    b.Aex = cv.take<__nv_bfloat16>((size_t)L.np * kLevels * L.np);
+    b.rowexp = cv.take<int>(L.np);
+    b.Dbuf = cv.take<float>((size_t)L.np * L.mp);
+    b.dcolmax = cv.take<unsigned int>(L.mp);
+    b.Bq = cv.take<__nv_bfloat16>((size_t)L.mp * L.np);
+    b.Dn = cv.take<int16_t>((size_t)L.np * L.mp);
+    b.dexp = cv.take<int>(L.mp);
+    b.lev = cv.take<int32_t>((size_t)kMaxExactSplits * kLevels * tc::exact_plane(L.n, L.m));
     b.R0 = cv.take<double>((size_t)L.np * L.mp);
     b.X = cv.take<double>((size_t)L.np * L.mp);
     b.R = cv.take<double>((size_t)L.np * L.mp);
+    b.Q = want_q ? cv.take<double>((size_t)L.np * L.mp) : nullptr;
     b.vec = cv.take<double>((size_t)2 * L.np);
-    b.split = L.splits ? cv.take<double>((size_t)L.splits * L.np * L.mp) : nullptr;
     err = ctx->d_scratch + kStatus;
-    b.red = reinterpret_cast<unsigned long long*>(ctx->d_scratch + kStatus + 6);
     RG_CUDA_TRY(ctx, cudaMemsetAsync(err, 0, 6 * sizeof(int), s));  // error words and the GEMM's
     return RG_OK;
   }
 
-  // P (shared by every set): its bf16 slices for the refinement product.
+  // The matrix P of every set (read directly or transposed); its fixed-point slices are
+  // built by build_slices (they include Dr).
   rg_status set_matrix(const double* P_, int64_t ldp_, bool trans) {
     P = P_;
     ldp = ldp_;
     transP = trans;
-    build_p_slices<<<grid_for((int64_t)L.np * L.np, ctx->sm_count), kThreads, 0, s>>>(P, ldp, transP, L.n, L.np,
-                                                                                      b.Aext);
+    return RG_OK;
+  }
+
+  // Fixed-point slices of P' = P Dr (Dr may be null).
+  rg_status build_slices(const double* dr) {
+    build_p_exact<<<(L.np + 7) / 8, 256, 0, s>>>(P, ldp, transP, dr, L.n, L.np, b.Aex, b.rowexp, err);
+    ++ctx->launches;
     RG_CUDA_TRY(ctx, cudaGetLastError());
     return RG_OK;
   }
@@ -504,34 +540,36 @@ struct Solver {
   // Newton-Schulz approximate inverse of A = I - Dl P Dr into b.X16[cur].
   template <class T16>
   rg_status factor_t(const double* dl, const double* dr) {
-    RG_CUDA_TRY(ctx, cudaMemsetAsync(b.red + 2, 0, 2 * sizeof(unsigned long long), s));
+    unsigned long long* e0 = reinterpret_cast<unsigned long long*>(err + 6);
+    RG_CUDA_TRY(ctx, cudaMemsetAsync(e0, 0, 2 * sizeof(unsigned long long), s));
     T16* A16 = static_cast<T16*>(b.A16);
     T16* X[2] = {static_cast<T16*>(b.X16[0]), static_cast<T16*>(b.X16[1])};
     T16* Xt = static_cast<T16*>(b.Xt16);
     T16* Zt = static_cast<T16*>(b.Zt16);
-    build_ns_start<T16><<<(L.np + 7) / 8, 256, 0, s>>>(P, ldp, transP, dl, dr, L.n, L.np, A16, X[0], Xt, b.red + 2,
+    build_ns_start<T16><<<(L.np + 7) / 8, 256, 0, s>>>(P, ldp, transP, dl, dr, L.n, L.np, A16, X[0], Xt, e0,
                                                         b.colmax, L.mp);
+    ++ctx->launches;
     RG_CUDA_TRY(ctx, cudaGetLastError());
     // the status words and e0 in one pinned read-back: one wait on the stream
     int* hs = ctx->h_scratch;
-    RG_CUDA_TRY(ctx, cudaMemcpyAsync(hs + kStatus, err, 14 * sizeof(int), cudaMemcpyDeviceToHost, s));
+    RG_CUDA_TRY(ctx, cudaMemcpyAsync(hs + kStatus, err, 10 * sizeof(int), cudaMemcpyDeviceToHost, s));
     RG_CUDA_TRY(ctx, cudaStreamSynchronize(s));
     if (hs[kStatus]) return rg::fail(ctx, RG_ERR_NUMERIC, "%s", input_error);
     double e_inf, e_one;
-    memcpy(&e_inf, hs + kStatus + 10, sizeof(e_inf));
-    memcpy(&e_one, hs + kStatus + 12, sizeof(e_one));
+    memcpy(&e_inf, hs + kStatus + 6, sizeof(e_inf));
+    memcpy(&e_one, hs + kStatus + 8, sizeof(e_one));
     if (!std::isfinite(e_inf) || !std::isfinite(e_one)) return rg::fail(ctx, RG_ERR_NUMERIC, "non-finite system matrix");
     // The residual of the Newton-Schulz iterate X_k is I - A X_k = E^(2^(k-1)), so any
     // norm of E with ||E|| < 1 bounds it. ||E||_inf (row sums) suits the Gebhart matrix
     // K = I - F diag(rho); its transpose, solved by the adjoint, has ||E||_1 < 1 instead
     // while its row sums (the column sums of F) can exceed 1: the smaller bound sets the
     // step count.
-    const double e0 = std::min(e_inf, e_one);
+    const double e0v = std::min(e_inf, e_one);
     const double floor16 = bf16 ? 0x1p-10 : 0x1p-13;
     int steps = kMaxNewtonSchulz;
-    if (e0 < 1.0) {
+    if (e0v < 1.0) {
       steps = 1;
-      if (e0 > 0.0) steps = (int)std::ceil(std::log2(std::log(floor16) / std::log(e0))) + 1;
+      if (e0v > 0.0) steps = (int)std::ceil(std::log2(std::log(floor16) / std::log(e0v))) + 1;
       steps = std::max(1, std::min(steps, kMaxNewtonSchulz));
     }
     ns_steps = steps;
@@ -552,53 +590,54 @@ struct Solver {
     return bf16 ? factor_t<__nv_bfloat16>(dl, dr) : factor_t<__half>(dl, dr);
   }
 
-  // X (+)= M src, where src is an fp64 n x m matrix (ld = mp): one tensor-core GEMM with
-  // src scaled column by column into 16 bits. `have_colmax`: b.colmax already holds the
-  // column maxima of src (the residual GEMM folds them in).
+  // One sweep: D = M src (src = R0 for the first, R after), D rounded to its one-slice form and
+  // added to X, R = src - D + Dl P' D exactly, then the sweep's words copied to the pinned
+  // slot of its parity (ctx->ev_read[parity] recorded after the copy). With a guard the sweep
+  // skips itself when the sweep before it ended the refinement.
   template <class T16>
-  rg_status apply_t(const double* src, bool first, bool have_colmax, const SweepGuard& guard) {
-    if (!have_colmax) {  // colmax was zeroed by build_ns_start (apply(.., true) follows a factorisation)
-      dim3 cg((L.m + 31) / 32, (L.n + 255) / 256);
-      column_max<<<cg, dim3(32, 8), 0, s>>>(src, L.mp, L.n, L.m, b.colmax);
-    }
+  rg_status launch_sweep_t(int parity, bool first, const double* dl, const SweepGuard& g) {
+    const double* src = first ? b.R0 : b.R;
+    unsigned long long* rc = red(parity);
+    const int* skip = g.err ? g.skip : nullptr;
     dim3 tg(L.mp / 32, L.np / 32);
     T16* Rt = static_cast<T16*>(b.Rt16);
-    scaled_transpose16<T16><<<tg, dim3(32, 8), 0, s>>>(src, L.mp, L.n, L.m, L.np, L.mp, b.colmax, Rt, b.colscale,
-                                                        guard);
+    scaled_transpose16<T16><<<tg, dim3(32, 8), 0, s>>>(src, L.mp, L.n, L.m, L.np, L.mp, b.colmax, Rt, b.colscale, g,
+                                                        rc, b.dcolmax);
+    ++ctx->launches;
     RG_CUDA_TRY(ctx, cudaGetLastError());
-    return tc::gemm(ctx, bf16, b.X16[cur], L.np, Rt, L.np, L.n, L.m, L.np,
-                    tc::EpiAddF64{b.X, L.mp, b.colscale, first ? 1 : 0}, s, guard.status ? guard.skip : nullptr);
-  }
-  rg_status apply(const double* src, bool first, bool have_colmax = false, const SweepGuard& guard = SweepGuard{}) {
-    return bf16 ? apply_t<__nv_bfloat16>(src, first, have_colmax, guard)
-                : apply_t<__half>(src, first, have_colmax, guard);
-  }
-
-  // R = R0 - X + Dl (P (Dr X)) from the first `pairs` slice pairs (3: 16-bit operands,
-  // 6: 24-bit), and the copy of max|R|, max|X| and the error words to the pinned scratch,
-  // after which ctx->ev_read is recorded (read_residual waits for it).
-  rg_status launch_residual(const double* dl, const double* dr, int pairs) {
-    dim3 tg((L.mp + 31) / 32, (L.np + 31) / 32);
-    // also zeroes max|R|, max|X| and the column maxima that the residual GEMM folds
-    build_x_slices<<<tg, dim3(32, 8), 0, s>>>(b.X, L.mp, dr, L.n, L.m, L.np, L.mp, b.Bext, b.red, b.colmax);
-    RG_CUDA_TRY(ctx, cudaGetLastError());
-    // max|R|, max|X|, the column maxima of R and the non-finite flag come from the epilogue
-    rg_status st = tc::gemm_residual(ctx, b.Aext, (int64_t)kSlices * L.np, b.Bext, (int64_t)kSlices * L.np, L.n, L.m,
-                                     pairs * L.np, kResidualChunk, b.R, b.R0, b.X, dl, L.mp, s, b.red, b.colmax,
-                                     err + 1, b.split, L.splits, L.np / tc::BK, kResidualTailChunk, L.n);
+    rg_status st = tc::gemm(ctx, bf16, b.X16[cur], L.np, Rt, L.np, L.n, L.m, L.np,
+                            tc::EpiCorrection{b.Dbuf, L.mp, b.colscale, b.dcolmax, err + 1}, s, skip);
     if (st != RG_OK) return st;
-    RG_CUDA_TRY(ctx, cudaMemcpyAsync(ctx->h_scratch + kStatus, err, 10 * sizeof(int), cudaMemcpyDeviceToHost, s));
-    RG_CUDA_TRY(ctx, cudaEventRecord(ctx->ev_read, s));
+    quantize_correction<<<tg, dim3(32, 8), 0, s>>>(b.Dbuf, L.n, L.m, L.np, L.mp, b.dcolmax, b.Bq, b.Dn, b.dexp, b.X,
+                                                   first ? 1 : 0, rc, b.colmax, err + 1, skip);
+    ++ctx->launches;
+    RG_CUDA_TRY(ctx, cudaGetLastError());
+    // levels from max|D| / max|X| of this sweep (rc[2] / rc[1]), read on the device
+    st = tc::gemm_exact(ctx, b.Aex, (int64_t)kLevels * L.np, b.Bq, L.np, L.n, L.m, L.np, nullptr, rc, kLevelBits,
+                        kLevels, b.lev, kMaxExactSplits, &splits, s, skip, L.n);
+    if (st != RG_OK) return st;
+    dim3 fg((L.m + 31) / 32, (L.n + 31) / 32);
+    finish_residual<<<fg, dim3(32, 8), 0, s>>>(b.lev, tc::exact_ld(L.m), tc::exact_plane(L.n, L.m), splits, b.rowexp,
+                                               b.dexp, b.Dn, dl, L.n, L.m, L.mp, b.R0, b.R, b.Q, first ? 1 : 0, rc,
+                                               b.colmax, err + 1, skip);
+    ++ctx->launches;
+    RG_CUDA_TRY(ctx, cudaGetLastError());
+    int* slot = ctx->h_scratch + kStatus + 32 * parity;
+    RG_CUDA_TRY(ctx, cudaMemcpyAsync(slot, err, kStatusInts * sizeof(int), cudaMemcpyDeviceToHost, s));
+    RG_CUDA_TRY(ctx, cudaEventRecord(ctx->ev_read[parity], s));
     return RG_OK;
   }
+  rg_status launch_sweep(int parity, bool first, const double* dl, const SweepGuard& g = SweepGuard{}) {
+    return bf16 ? launch_sweep_t<__nv_bfloat16>(parity, first, dl, g) : launch_sweep_t<__half>(parity, first, dl, g);
+  }
 
-  // Waits for the read-back of launch_residual (not for later launches); max|R| / max|X|.
-  rg_status read_residual(double* rel) {
-    RG_CUDA_TRY(ctx, cudaEventSynchronize(ctx->ev_read));
-    const int* hs = ctx->h_scratch + kStatus;
+  // Waits for the read-back of the sweep of this parity (not for later launches).
+  rg_status read_sweep(int parity, double* rel) {
+    RG_CUDA_TRY(ctx, cudaEventSynchronize(ctx->ev_read[parity]));
+    const int* hs = ctx->h_scratch + kStatus + 32 * parity;
     double r, x;
-    memcpy(&r, hs + 6, 8);
-    memcpy(&x, hs + 8, 8);
+    memcpy(&r, hs + 10 + 6 * parity, 8);
+    memcpy(&x, hs + 12 + 6 * parity, 8);
     *rel = x > 0 ? r / x : r;
     return status_of(hs);
   }
@@ -617,41 +656,50 @@ struct Solver {
     return status_of(hs + kStatus);
   }
 
-  // Factor, solve and refine one set whose right-hand side is already in b.R0.
-  rg_status run(const double* dl, const double* dr, double tol, int max_sweeps, int* sweeps, double* rel_out) {
+  // Factor, solve and refine one set whose right-hand side is already in b.R0. The
+  // fixed-point slices of P' are rebuilt when `slices` (they depend on dr).
+  rg_status run(const double* dl, const double* dr, double tol, int max_sweeps, int* sweeps, double* rel_out,
+                bool slices = true) {
     rg_status st = factor(dl, dr);
-    if (st == RG_OK) st = apply(b.R0, true);
+    if (st == RG_OK && slices) st = build_slices(dr);
+    if (st != RG_OK) return st;
+    dim3 cg((L.m + 31) / 32, (L.n + 255) / 256);  // colmax was zeroed by build_ns_start
+    column_max<<<cg, dim3(32, 8), 0, s>>>(b.R0, L.mp, L.n, L.m, b.colmax);
+    ++ctx->launches;
+    RG_CUDA_TRY(ctx, cudaGetLastError());
+    st = launch_sweep(0, true, dl);
     if (st != RG_OK) return st;
     double rel = INFINITY, prev = INFINITY;
     int sw = 0;
     bool done = false;
     for (; sw < max_sweeps; ++sw) {
-      // while the residual is large, the three leading slice pairs (16-bit operands,
-      // error ~2^-16 max|X|) resolve it; those sweeps correct but never stop
-      const bool coarse = prev > kCoarseAbove && tol < kCoarseAbove;
-      st = launch_residual(dl, dr, coarse ? 3 : kSlices);
+      const int p = sw & 1;
+      // the next sweep goes in before the host has read this one, so the GPU works while the
+      // read-back travels; it evaluates the stopping rule on the device and does nothing when
+      // this sweep ends the refinement
+      if (sw + 1 < max_sweeps) {
+        SweepGuard g;
+        g.err = err;
+        g.red = red(p);
+        g.tol = tol;
+        g.prev = prev;
+        g.skip = err + 5;
+        st = launch_sweep(p ^ 1, false, dl, g);
+        if (st != RG_OK) return st;
+      }
+      st = read_sweep(p, &rel);
       if (st != RG_OK) return st;
-      // the correction goes in behind the residual before the host has read it, so the GPU
-      // works while the read-back travels; it evaluates the stopping rule below on the
-      // device and does nothing when this sweep ends the refinement (X then stays as the
-      // residual saw it, as if it had not been launched)
-      SweepGuard g;
-      g.status = err;
-      g.tol = tol;
-      g.prev = prev;
-      g.coarse = coarse ? 1 : 0;
-      g.skip = err + 5;
-      st = apply(b.R, false, true, g);
-      if (st != RG_OK) return st;
-      st = read_residual(&rel);
-      if (st != RG_OK) return st;
-      // converged, or stalled at the accuracy floor of the fp32-chunked residual product
-      if (!coarse && (rel <= tol || (rel <= kStallFloor && rel > 0.5 * prev))) { done = true; break; }
+      if (rel <= tol || (rel <= kStallFloor && rel > 0.5 * prev)) { done = true; break; }
       prev = rel;
     }
     *sweeps = sw + (done ? 1 : 0);
     *rel_out = rel;
-    if (!done) return rg::fail(ctx, RG_ERR_NOT_CONVERGED, "refinement: residual %.3e > tol %.3e", rel, tol);
+    if (!done) {
+      // the last speculative sweep (if any) was skipped by its guard only when it saw an
+      // ending; wait for the stream before reporting
+      RG_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+      return rg::fail(ctx, RG_ERR_NOT_CONVERGED, "refinement: residual %.3e > tol %.3e", rel, tol);
+    }
     return RG_OK;
   }
 };
@@ -960,16 +1008,38 @@ rg_status rg_enforce_lsq(rg_ctx* ctx, int32_t n, const double* omega_d, double* 
   return RG_OK;
 }
 
-rg_status rg_refinement_slices(rg_ctx* ctx, int64_t n, const double* x_d, uint16_t* slices_d, void* stream) {
+rg_status rg_exact_split(rg_ctx* ctx, int32_t n, const double* P_d, int64_t ldp, int32_t trans, const double* dr_d,
+                         int16_t* slices_d, int32_t* rowexp_d, void* stream) {
   if (!ctx) return RG_ERR_ARG;
-  RG_ARG_CHECK(ctx, n >= 0 && (n == 0 || (x_d && slices_d)), "rg_refinement_slices: bad argument");
-  if (n == 0) return RG_OK;
+  RG_ARG_CHECK(ctx, n > 0 && n <= 32768 && P_d && slices_d && rowexp_d && ldp >= (trans ? n : n),
+               "rg_exact_split: bad argument");
   RG_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
   cudaStream_t s = (cudaStream_t)stream;
-  const int64_t blocks = std::min<int64_t>((n + 255) / 256, (int64_t)ctx->sm_count * 8);
-  split_slices<<<(int)blocks, 256, 0, s>>>(x_d, n, reinterpret_cast<__nv_bfloat16*>(slices_d));
+  const int np = (n + NB - 1) / NB * NB;
+  rg::Sizer sz;
+  sz.take<__nv_bfloat16>((size_t)np * kLevels * np);
+  sz.take<int>(np);
+  void* ws = nullptr;
+  rg_status st = rg::workspace(ctx, sz.off, &ws);
+  if (st != RG_OK) return st;
+  rg::Carver cv(ws);
+  __nv_bfloat16* Aex = cv.take<__nv_bfloat16>((size_t)np * kLevels * np);
+  int* rowexp = cv.take<int>(np);
+  int* e = ctx->d_scratch + kStatus;
+  RG_CUDA_TRY(ctx, cudaMemsetAsync(e, 0, sizeof(int), s));
+  build_p_exact<<<(np + 7) / 8, 256, 0, s>>>(P_d, ldp, trans != 0, dr_d, n, np, Aex, rowexp, e);
   ++ctx->launches;
   RG_CUDA_TRY(ctx, cudaGetLastError());
+  bf16_rows_to_int16<<<grid_for((int64_t)n * kLevels * np, ctx->sm_count), kThreads, 0, s>>>(
+      Aex, (int64_t)n * kLevels * np, slices_d);
+  ++ctx->launches;
+  RG_CUDA_TRY(ctx, cudaMemcpyAsync(rowexp_d, rowexp, n * sizeof(int), cudaMemcpyDeviceToDevice, s));
+  RG_CUDA_TRY(ctx, cudaGetLastError());
+  int h = 0;
+  RG_CUDA_TRY(ctx, cudaMemcpyAsync(ctx->h_scratch, e, sizeof(int), cudaMemcpyDeviceToHost, s));
+  RG_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+  h = ctx->h_scratch[0];
+  if (h) return rg::fail(ctx, RG_ERR_NUMERIC, "rg_exact_split: non-finite entry");
   return RG_OK;
 }
 
@@ -1026,8 +1096,9 @@ rg_status rg_gebhart_adjoint(rg_ctx* ctx, int32_t n, const double* F_d, int32_t 
   RG_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
   cudaStream_t s = (cudaStream_t)stream;
   Solver sv{ctx};
-  // K^T = I - diag(rho) F_NN^T
-  st = sv.setup(n, n + 1, precision == RG_PREC_BF16_IR, s);
+  // K^T = I - diag(rho) F_NN^T: P' = F^T for every set; the refinement also accumulates
+  // Q = F^T Lambda (the sum of its exact products), which the rho gradient needs
+  st = sv.setup(n, n + 1, precision == RG_PREC_BF16_IR, s, 0, nullptr, true);
   if (st == RG_OK) st = sv.set_matrix(F_d, n + 1, true);
   if (st != RG_OK) return st;
   for (int set = 0; set < n_sets; ++set) {
@@ -1039,22 +1110,13 @@ rg_status rg_gebhart_adjoint(rg_ctx* ctx, int32_t n, const double* F_d, int32_t 
     RG_CUDA_TRY(ctx, cudaGetLastError());
     int sw = 0;
     double rel = 0.0;
-    st = sv.run(rho, nullptr, tol, max_sweeps, &sw, &rel);
+    st = sv.run(rho, nullptr, tol, max_sweeps, &sw, &rel, set == 0);
     if (st != RG_OK) return st;
     // deps_j = sum_i Lam_ij F_ij
     grad_eps<<<(n + 31) / 32, dim3(32, 8), 0, s>>>(sv.b.X, sv.L.mp, F_d, n, deps_d + (size_t)set * n);
     ++ctx->launches;
-    // Q = F^T Lam (fp64-accurate sliced product), then drho_k = sum_j B_kj Q_kj
-    dim3 tg((sv.L.mp + 31) / 32, (sv.L.np + 31) / 32);
-    build_x_slices<<<tg, dim3(32, 8), 0, s>>>(sv.b.X, sv.L.mp, nullptr, n, n + 1, sv.L.np, sv.L.mp, sv.b.Bext);
-    ++ctx->launches;
-    RG_CUDA_TRY(ctx, cudaGetLastError());
-    st = tc::gemm_residual(ctx, sv.b.Aext, (int64_t)kSlices * sv.L.np, sv.b.Bext, (int64_t)kSlices * sv.L.np, n,
-                           n + 1, kSlices * sv.L.np, kResidualChunk, sv.b.R, nullptr, nullptr, nullptr, sv.L.mp, s,
-                           nullptr, nullptr, nullptr, sv.b.split, sv.L.splits, sv.L.np / tc::BK, kResidualTailChunk,
-                           n);
-    if (st != RG_OK) return st;
-    grad_rho<<<(n + 7) / 8, 256, 0, s>>>(B_d + off, sv.b.R, sv.L.mp, n, drho_d + (size_t)set * n);
+    // drho_k = sum_j B_kj Q_kj with Q = F^T Lam
+    grad_rho<<<(n + 7) / 8, 256, 0, s>>>(B_d + off, sv.b.Q, sv.L.mp, n, drho_d + (size_t)set * n);
     ++ctx->launches;
     RG_CUDA_TRY(ctx, cudaGetLastError());
   }

@@ -1,21 +1,16 @@
-// tcgen05 GEMM for sm_103a: D[M x N] = A[M x K] * B[N x K]^T, 16-bit operands (bf16 or
-// fp16, both K-major: row-major with K contiguous), fp32 accumulation in tensor memory.
+// tcgen05 GEMMs for sm_103a, 16-bit operands (bf16 or fp16, both K-major: row-major with K
+// contiguous), fp32 accumulation in tensor memory.
 //
-// One CTA computes one BM x BN tile (BM = 128). Warp roles (192 threads; 320 for
-// compensated 128-wide tiles):
+// gemm_kernel: D[M x N] = A[M x K] * B[N x K]^T with an epilogue functor. One CTA computes
+// one BM x BN tile (BM = 128). Warp roles (192 threads):
 //   warp 0      TMA producer: 64-wide K blocks of A and B into a ring of smem stages
 //               (128-byte swizzle), completion signalled on full[s] mbarriers;
 //   warp 1      allocates TMEM, one elected thread issues tcgen05.mma (K = 16 each)
-//               and commits to empty[s] (stage free) and acc_full[b] (accumulator ready);
+//               and commits to empty[s] (stage free) and acc_full (accumulator ready);
 //   warps 2..5  epilogue: tcgen05.ld of the accumulator (warp w reads TMEM lanes
-//               32*(w%4) .. +31, i.e. tile rows), then the Epi functor writes the result;
-//               a compensated tile wider than 64 columns has one group of four epilogue
-//               warps per 64 columns (warps 6..9 take columns 64..127), so that a thread
-//               keeps 64 compensated sums.
-// The K loop can be cut into chunks of kChunkBlocks K blocks: each chunk is accumulated
-// in fp32 in one of two TMEM buffers and handed to the epilogue, which folds it into a
-// compensated (Kahan) fp32 sum; this keeps the long reductions of the refinement
-// residual accurate to ~1e-7 relative while the tensor cores run in 16-bit.
+//               32*(w%4) .. +31, i.e. tile rows), then the Epi functor writes the result.
+// gemm_exact_kernel: the integer-exact level product of the dense solves' refinement (see
+// its comment); the same roles with 128-long K chunks in two TMEM buffers.
 //
 // Every mbarrier wait is bounded; on a timeout the kernel records an error word, stops
 // issuing work, frees its TMEM and returns.
@@ -34,11 +29,6 @@ namespace tc {
 constexpr int BM = 128;
 constexpr int BK = 64;  // one 128-byte swizzle atom of 16-bit elements
 constexpr int kThreads = 192;
-// epilogue warp groups of a tile: compensated tiles give every group 64 columns
-template <int BN, bool kCompensated>
-__host__ __device__ constexpr int epi_groups() { return (kCompensated && BN > 64) ? BN / 64 : 1; }
-template <int BN, bool kCompensated>
-__host__ __device__ constexpr int cta_threads() { return 64 + 128 * epi_groups<BN, kCompensated>(); }
 constexpr int kGroupM = 8;  // row tiles per rasterisation group
 constexpr uint64_t kWaitNs = 2000000000ull;  // a wait gives up after 2 s
 
@@ -127,20 +117,6 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-// 16 columns of fp32 accumulator for the warp's 32 TMEM lanes (the compensated drain of
-// wide tiles reads half-slabs: 16 fewer registers in flight next to its Kahan state).
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
-  uint32_t r[16];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
-        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
-}
-
 // Shared-memory matrix descriptor of a K-major tile with 128-byte rows, 128-byte
 // swizzle, 8-row core groups 1024 bytes apart (sm_100 descriptor version 1).
 __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
@@ -182,19 +158,6 @@ __device__ __forceinline__ void staged_rows(int row0, int lane, int c0, int M, i
     if (r < M && c < N) put(r, c, stage[rr][lane]);
   }
   __syncwarp();
-}
-
-// ------------------------------------------------------------------ fp64 maxima on the bit pattern
-// GB300 runs fp64 min/max on a pipe far slower than its integer ALU; the compensated
-// epilogue folds two maxima per element, as the bit patterns of |x|.
-
-// |x| as its bit pattern, 0 for a NaN: the maximum of these orders like fmax of |x|.
-__device__ __forceinline__ unsigned long long abs_bits(double x) {
-  const unsigned long long a = (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffull;
-  return a > 0x7ff0000000000000ull ? 0ull : a;
-}
-__device__ __forceinline__ bool finite_bits(double x) {
-  return ((unsigned long long)__double_as_longlong(x) & 0x7ff0000000000000ull) != 0x7ff0000000000000ull;
 }
 
 template <class T16>
@@ -256,17 +219,15 @@ struct EpiStore16Both {
   }
 };
 
-// Epilogues that read fp64 operands of the output tile go through the staging block in
-// batches of kRowBatch rows: the loads of a batch are issued together, so a warp waits
-// for one memory latency per batch rather than one per row.
-constexpr int kRowBatch = 8;
-
-// X64[r][c] = (first ? 0 : X64[r][c]) + acc * colscale[c]   (the refinement correction)
-struct EpiAddF64 {
-  double* X;
+// D[r][c] = acc * colscale[c] (fp32; the refinement's correction M R before it is rounded to
+// its one-slice form), with max_r |D[r][c]| folded into colmax[c] (float bits, atomicMax) and
+// *nonfinite raised on an inf or NaN.
+struct EpiCorrection {
+  float* D;
   int64_t ld;
   const float* colscale;
-  int first;
+  unsigned int* colmax;
+  int* nonfinite;
   __device__ __forceinline__ void store(int row0, int lane, int c0, int M, int N, const float* v,
                                         float (*stage)[33]) const {
 #pragma unroll
@@ -274,117 +235,28 @@ struct EpiAddF64 {
     __syncwarp();
     const int c = c0 + lane;
     const bool cok = c < N;
-    const double cs = cok ? (double)colscale[c] : 0.0;
-#pragma unroll 1
-    for (int rb = 0; rb < 32; rb += kRowBatch) {
-      double old[kRowBatch];
-#pragma unroll
-      for (int q = 0; q < kRowBatch; ++q) {
-        const int r = row0 + rb + q;
-        old[q] = (!first && cok && r < M) ? X[(int64_t)r * ld + c] : 0.0;
-      }
-#pragma unroll
-      for (int q = 0; q < kRowBatch; ++q) {
-        const int r = row0 + rb + q;
-        if (cok && r < M) {
-          const double d = (double)stage[rb + q][lane] * cs;
-          X[(int64_t)r * ld + c] = first ? d : old[q] + d;
-        }
-      }
-    }
-    __syncwarp();
-  }
-};
-
-// Largest non-negative double into *dst (its bit pattern orders like the value).
-__device__ __forceinline__ void atomic_max_nonneg(unsigned long long* dst, double x) {
-  atomicMax(dst, (unsigned long long)__double_as_longlong(x));
-}
-
-// out[r][c] = E[r][c] - X[r][c] + dl[r] * acc   (fp64; the refinement residual), or
-// out[r][c] = dl[r] * acc when E is null (an fp64-accurate product). With `red` set it
-// also folds max|out| into red[0], max|X| into red[1], max_r |out[r][c]| into
-// colmax[c] (all as double bits) and raises *nonfinite on an inf or NaN.
-struct EpiResidual {
-  double* out;
-  const double* E;   // may be null together with X
-  const double* X;
-  const double* dl;  // may be null (identity)
-  int64_t ld;        // shared leading dimension of out, E and X
-  unsigned long long* red = nullptr;     // [2], zeroed by the caller
-  unsigned long long* colmax = nullptr;  // [N], zeroed by the caller (may be null)
-  int* nonfinite = nullptr;
-  double* partial = nullptr;             // split K: CTA z writes its raw sum to partial + z * split_stride
-  int64_t split_stride = 0;
-  // The caller has written the warp's 32 x 32 block into stage (stage[l][i]: row
-  // row0 + l, column c0 + i), so that no register array of it stays live here.
-  __device__ __forceinline__ void store(int row0, int lane, int c0, int M, int N, double (*stage)[33], int z) const {
-    __syncwarp();
-    const int c = c0 + lane;
-    if (partial) {
-      double* dst = partial + (int64_t)z * split_stride;
-#pragma unroll 4
-      for (int rr = 0; rr < 32; ++rr) {
-        const int r = row0 + rr;
-        if (r < M && c < N) dst[(int64_t)r * ld + c] = stage[rr][lane];
-      }
-      __syncwarp();
-      return;
-    }
-    unsigned long long m_out = 0ull, m_x = 0ull;  // bit patterns of the maxima (abs_bits)
+    const float cs = cok ? colscale[c] : 0.f;
+    float mx = 0.f;
     bool bad = false;
-    const bool cok = c < N;
-#pragma unroll 1
-    for (int rb = 0; rb < 32; rb += kRowBatch) {
-      double e[kRowBatch], xo[kRowBatch], s[kRowBatch];
-#pragma unroll
-      for (int q = 0; q < kRowBatch; ++q) {
-        const int r = row0 + rb + q;
-        const bool ok = cok && r < M;
-        const int64_t i = (int64_t)r * ld + c;
-        e[q] = (ok && E) ? E[i] : 0.0;
-        xo[q] = (ok && E) ? X[i] : 0.0;
-        s[q] = (r < M && dl) ? dl[r] : 1.0;
-      }
-#pragma unroll
-      for (int q = 0; q < kRowBatch; ++q) {
-        const int r = row0 + rb + q;
-        if (!(cok && r < M)) continue;
-        const double x = stage[rb + q][lane];
-        const double o = E ? (e[q] - xo[q]) + s[q] * x : s[q] * x;
-        out[(int64_t)r * ld + c] = o;
-        m_out = max(m_out, abs_bits(o));
-        m_x = max(m_x, abs_bits(xo[q]));
-        bad |= !finite_bits(o) || !finite_bits(xo[q]);
+#pragma unroll 4
+    for (int rr = 0; rr < 32; ++rr) {
+      const int r = row0 + rr;
+      if (cok && r < M) {
+        const float d = stage[rr][lane] * cs;
+        D[(int64_t)r * ld + c] = d;
+        mx = fmaxf(mx, fabsf(d));
+        bad |= !isfinite(d);
       }
     }
     __syncwarp();
-    if (red) {
-      // this lane saw column c0 + lane of the warp's 32 rows
-      if (colmax && c0 + lane < N) atomicMax(&colmax[c0 + lane], m_out);
-      for (int o = 16; o > 0; o >>= 1) {
-        m_out = max(m_out, __shfl_xor_sync(0xffffffffu, m_out, o));
-        m_x = max(m_x, __shfl_xor_sync(0xffffffffu, m_x, o));
-      }
-      bad = __any_sync(0xffffffffu, bad);
-      if (lane == 0) {
-        atomicMax(&red[0], m_out);
-        atomicMax(&red[1], m_x);
-        if (bad && nonfinite) atomicExch(nonfinite, 1);
-      }
-    }
+    if (cok) atomicMax(&colmax[c], __float_as_uint(mx));
+    if (__any_sync(0xffffffffu, bad) && lane == 0 && nonfinite) atomicExch(nonfinite, 1);
   }
 };
 
 struct GemmArgs {
   int M, N, K;
-  int chunk_blocks;  // 0: one fp32 accumulation over all of K; > 0: compensated chunks
   int* error_word;
-  int split_blocks = 0;  // > 0: CTA z covers K blocks [z * split_blocks, (z + 1) * split_blocks)
-  // > 0 (compensated, unsplit): only the first lead_blocks K blocks use chunks of
-  // chunk_blocks; the rest use chunks of tail_chunk_blocks
-  int lead_blocks = 0;
-  int tail_chunk_blocks = 0;
   // non-null: the kernel does nothing when *skip != 0 (written by an earlier kernel on
   // the stream; a speculatively launched product the host's decision made unnecessary)
   const int* skip = nullptr;
@@ -392,17 +264,13 @@ struct GemmArgs {
   int alg_k = 0;
 };
 
-template <int BN, int kStages, class Epi, bool kCompensated, bool kBF16>
-__global__ void __launch_bounds__(cta_threads<BN, kCompensated>(), 1)
+template <int BN, int kStages, class Epi, bool kBF16>
+__global__ void __launch_bounds__(kThreads, 1)
     gemm_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_b,
                 const GemmArgs args, const Epi epi) {
   static_assert(BN == 64 || BN == 128 || BN == 256, "tile width");
-  constexpr int kGroups = epi_groups<BN, kCompensated>();
-  constexpr int kEpiCols = BN / kGroups;  // columns of one epilogue thread
-  static_assert(!kCompensated || kEpiCols == 64, "the compensated epilogue keeps 2 x 64 registers per thread");
   constexpr uint32_t kABytes = BM * BK * 2, kBBytes = BN * BK * 2;
-  constexpr uint32_t kAccCols = kCompensated ? 2 * BN : BN;
-  constexpr uint32_t kTmemCols = kAccCols <= 32 ? 32 : (kAccCols <= 64 ? 64 : (kAccCols <= 128 ? 128 : (kAccCols <= 256 ? 256 : 512)));
+  constexpr uint32_t kTmemCols = BN < 32 ? 32 : BN;
   constexpr uint32_t kIdesc = idesc_f16(BM, BN, kBF16);
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -410,14 +278,12 @@ __global__ void __launch_bounds__(cta_threads<BN, kCompensated>(), 1)
   uint8_t* sB = smem + kStages * kABytes;
   uint64_t* full = reinterpret_cast<uint64_t*>(sB + kStages * kBBytes);
   uint64_t* empty = full + kStages;
-  uint64_t* acc_full = empty + kStages;  // [2]
-  uint64_t* acc_empty = acc_full + 2;    // [2]
-  uint64_t* drain = acc_empty + 2;       // [1]
+  uint64_t* acc_full = empty + kStages;  // [1]
+  uint64_t* drain = acc_full + 1;        // [1]
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
   __shared__ int s_abort;
   __shared__ int s_consumed;             // K blocks whose stage the MMA thread has taken
-  using StageT = typename std::conditional<kCompensated, double, float>::type;
-  __shared__ StageT s_stage[4 * kGroups][32][33];  // per epilogue warp: coalescing block
+  __shared__ float s_stage[4][32][33];   // per epilogue warp: coalescing block
 
   if (args.skip && *(volatile const int*)args.skip) return;  // uniform: before any barrier or allocation
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -431,17 +297,186 @@ __global__ void __launch_bounds__(cta_threads<BN, kCompensated>(), 1)
   const int tile_m = first_m + (pid % (kGroupM * tiles_n)) % group_m;
   const int tile_n = (pid % (kGroupM * tiles_n)) / group_m;
   const int m0 = tile_m * BM, n0 = tile_n * BN;
-  const int kb_all = (args.K + BK - 1) / BK;
-  // split K: this CTA's K blocks are kb_first .. kb_first + kb_total - 1
+  const int kb_total = (args.K + BK - 1) / BK;
+
+  if (threadIdx.x == 0) {
+    s_abort = 0;
+    s_consumed = 0;
+    for (int s = 0; s < kStages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(acc_full, 1);
+    mbar_init(drain, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 1) tmem_alloc(tmem_slot, kTmemCols);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+  volatile int* abort_flag = &s_abort;
+
+  if (warp == 0) {
+    // ---------------- TMA producer
+    if (lane == 0) {
+      int issued = 0;
+      for (int kb = 0; kb < kb_total; ++kb) {
+        const int s = kb % kStages;
+        if (kb >= kStages && !mbar_wait(&empty[s], ((kb / kStages) - 1) & 1)) { *abort_flag = 1; break; }
+        if (*abort_flag) break;
+        mbar_expect_tx(&full[s], kABytes + kBBytes);
+        tma_load_2d(sA + s * kABytes, &map_a, &full[s], kb * BK, m0);
+        tma_load_2d(sB + s * kBBytes, &map_b, &full[s], kb * BK, n0);
+        ++issued;
+      }
+      if (*abort_flag) {
+        // let the copies this thread started land before the CTA goes away
+        for (int kb = *(volatile int*)&s_consumed; kb < issued; ++kb) mbar_wait(&full[kb % kStages], (kb / kStages) & 1);
+      }
+    }
+  } else if (warp == 1) {
+    // ---------------- MMA issuer
+    if (lane == 0) {
+      for (int kb = 0; kb < kb_total && !*abort_flag; ++kb) {
+        const int s = kb % kStages;
+        if (!mbar_wait(&full[s], (kb / kStages) & 1)) { *abort_flag = 1; break; }
+        *(volatile int*)&s_consumed = kb + 1;
+        tc_fence_after();
+        const uint32_t a_addr = smem_u32(sA + s * kABytes), b_addr = smem_u32(sB + s * kBBytes);
+#pragma unroll
+        for (int kk = 0; kk < BK / 16; ++kk)
+          umma_f16(tmem_base, sw128_desc(a_addr + kk * 32), sw128_desc(b_addr + kk * 32), kIdesc,
+                   (kb > 0 || kk > 0) ? 1u : 0u);
+        umma_commit(&empty[s]);
+      }
+      if (!*abort_flag) umma_commit(acc_full);
+      // every MMA this thread issued has completed once `drain` fires
+      umma_commit(drain);
+      mbar_wait(drain, 0);
+    }
+  } else {
+    // ---------------- epilogue warps 2 .. 5
+    const int ew = warp - 2;
+    const int quarter = warp & 3;  // TMEM lanes 32*quarter .. +31
+    const int row0 = m0 + quarter * 32;
+    const uint32_t lane_addr = (uint32_t)(quarter * 32) << 16;
+    float(*stage)[33] = s_stage[ew];
+    if (mbar_wait(acc_full, 0)) {
+      tc_fence_after();
+      float v[32];
+#pragma unroll 1
+      for (int c0 = 0; c0 < BN; c0 += 32) {
+        tmem_ld32(tmem_base + lane_addr + (uint32_t)c0, v);
+        epi.store(row0, lane, n0 + c0, args.M, args.N, v, stage);
+      }
+    } else {
+      *abort_flag = 1;
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tmem_base, kTmemCols);
+  }
+  if (threadIdx.x == 0 && *abort_flag && args.error_word) atomicExch(args.error_word, 1);
+}
+
+template <int BN, int kStages>
+constexpr size_t smem_bytes() {
+  return 1024 + (size_t)kStages * (BM * BK * 2 + BN * BK * 2) + (2 * kStages + 3) * 8 + 16;
+}
+
+// ------------------------------------------------------------------ exact level GEMM
+// The product of the exact refinement (solve.cu): for levels a = 0 .. L-1,
+//   S_a[i][j] = sum_k A[i][a np + k] B[j][k],   A [M][Lmax np], B [N][np], both bf16 K-major,
+// where every element of A and B is an integer of magnitude <= 128 (exact in bf16). Each
+// product is then an integer of magnitude <= 2^14 and the sum of one 128-long chunk is at
+// most 2^21, so the fp32 tensor-memory accumulator holds every chunk sum exactly whatever
+// the order of its additions. The epilogue adds the chunk sums as int32 (exact for level
+// sums below 2^31, i.e. np <= 131,072) and stores each level's sums as int32 to
+// lev + (z Lmax + a) plane, row i at i ldl (z: the CTA's K split). L is read from device
+// memory (written by an earlier kernel on the stream), so that the level count can be
+// decided on the device. Warp roles as gemm_kernel; the epilogue has one group of four
+// warps per 128 columns (a thread keeps its row's 128 int32 sums).
+// Level count of an exact product from max|X| and max|D| (bits of non-negative doubles in
+// words[1] and words[2]): the dropped levels (each 2^-8 of the previous) stay below 2^-bits of
+// max|A| max|X|. Every kernel that needs the count evaluates it from the same words.
+__device__ __forceinline__ int exact_level_count(const unsigned long long* words, int bits, int max_levels) {
+  const unsigned long long xb = words[1], db = words[2];
+  if (db == 0ull) return 1;
+  if (xb == 0ull || xb >= 0x7ff0000000000000ull || db >= 0x7ff0000000000000ull) return max_levels;
+  const int ed = (int)(db >> 52), ex = (int)(xb >> 52);  // biased exponents (0 for subnormals)
+  const int L = (bits + (ed - ex) + 7) / 8;
+  return L < 1 ? 1 : (L > max_levels ? max_levels : L);
+}
+
+struct ExactArgs {
+  int M, N, np;          // rows and columns of S, K length of one level (multiple of 128)
+  const int* levels;     // device int L (1 <= L <= max_levels), or null: L from level_words
+  const unsigned long long* level_words;  // see exact_level_count
+  int level_bits;
+  int max_levels;
+  int32_t* lev;          // [splits][max_levels][rows >= tiles_m BM][ldl]
+  int64_t ldl, plane;    // row stride; stride of one (split, level) plane; ldl >= tiles_n BN
+  int split_blocks;      // K blocks of one level per CTA z (0: all)
+  int* error_word;
+  const int* skip = nullptr;
+  int* level_log = nullptr;  // kernel timer: the launch records L here (CTA 0, thread 0)
+};
+
+constexpr int kExactChunkBlocks = 2;  // 128-long K chunks
+__host__ __device__ constexpr int exact_groups(int BN) { return BN > 128 ? BN / 128 : 1; }
+__host__ __device__ constexpr int exact_threads(int BN) { return 64 + 128 * exact_groups(BN); }
+
+template <int BN, int kStages>
+__global__ void __launch_bounds__(exact_threads(BN), 1)
+    gemm_exact_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_b,
+                      const ExactArgs args) {
+  static_assert(BN == 64 || BN == 128 || BN == 256, "tile width");
+  constexpr int kGroups = exact_groups(BN);
+  constexpr int kCols = BN / kGroups;  // columns of one epilogue thread
+  constexpr uint32_t kABytes = BM * BK * 2, kBBytes = BN * BK * 2;
+  constexpr uint32_t kTmemCols = 2 * BN < 32 ? 32 : 2 * BN;
+  constexpr uint32_t kIdesc = idesc_f16(BM, BN, true);
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint8_t* sA = smem;
+  uint8_t* sB = smem + kStages * kABytes;
+  uint64_t* full = reinterpret_cast<uint64_t*>(sB + kStages * kBBytes);
+  uint64_t* empty = full + kStages;
+  uint64_t* acc_full = empty + kStages;  // [2]
+  uint64_t* acc_empty = acc_full + 2;    // [2]
+  uint64_t* drain = acc_empty + 2;       // [1]
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
+  __shared__ int s_abort;
+  __shared__ int s_consumed;
+
+  if (args.skip && *(volatile const int*)args.skip) return;  // uniform: before any barrier or allocation
+  const int L = args.levels ? *(volatile const int*)args.levels
+                            : exact_level_count(args.level_words, args.level_bits, args.max_levels);
+  if (L < 1 || L > args.max_levels) {
+    if (threadIdx.x == 0 && args.error_word) atomicExch(args.error_word, 1);
+    return;
+  }
+  if (args.level_log && threadIdx.x == 0 && blockIdx.x == 0 && blockIdx.z == 0) *args.level_log = L;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int tiles_m = (args.M + BM - 1) / BM, tiles_n = (args.N + BN - 1) / BN;
+  const int pid = blockIdx.x;
+  const int group = pid / (kGroupM * tiles_n);
+  const int first_m = group * kGroupM;
+  const int group_m = min(tiles_m - first_m, kGroupM);
+  const int tile_m = first_m + (pid % (kGroupM * tiles_n)) % group_m;
+  const int tile_n = (pid % (kGroupM * tiles_n)) / group_m;
+  const int m0 = tile_m * BM, n0 = tile_n * BN;
+  const int kb_level = args.np / BK;  // K blocks of one level
   const int kb_first = args.split_blocks > 0 ? blockIdx.z * args.split_blocks : 0;
-  const int kb_total = args.split_blocks > 0 ? min(args.split_blocks, kb_all - kb_first) : kb_all;
-  const int chunk = (kCompensated && args.chunk_blocks > 0) ? args.chunk_blocks : kb_total;
-  // chunk schedule: n_lead chunks of `chunk` K blocks, then chunks of `tail` blocks
-  const bool two_part = kCompensated && args.chunk_blocks > 0 && args.lead_blocks > 0 &&
-                        args.tail_chunk_blocks > 0 && args.lead_blocks < kb_total;
-  const int n_lead = two_part ? args.lead_blocks / chunk : 0;
-  const int tail = two_part ? args.tail_chunk_blocks : chunk;
-  const int n_chunks = n_lead + (kb_total - n_lead * chunk + tail - 1) / tail;
+  const int kb_per = args.split_blocks > 0 ? min(args.split_blocks, kb_level - kb_first) : kb_level;
+  const int chunks_per_level = kb_per / kExactChunkBlocks;
+  const int n_chunks = L * chunks_per_level;
+  const int total_kb = L * kb_per;
 
   if (threadIdx.x == 0) {
     s_abort = 0;
@@ -466,111 +501,92 @@ __global__ void __launch_bounds__(cta_threads<BN, kCompensated>(), 1)
   volatile int* abort_flag = &s_abort;
 
   if (warp == 0) {
-    // ---------------- TMA producer
+    // ---------------- TMA producer: level a, block kb of the CTA's K range
     if (lane == 0) {
       int issued = 0;
-      for (int kb = 0; kb < kb_total; ++kb) {
-        const int s = kb % kStages;
-        if (kb >= kStages && !mbar_wait(&empty[s], ((kb / kStages) - 1) & 1)) { *abort_flag = 1; break; }
+      for (int t = 0; t < total_kb; ++t) {
+        const int s = t % kStages;
+        if (t >= kStages && !mbar_wait(&empty[s], ((t / kStages) - 1) & 1)) { *abort_flag = 1; break; }
         if (*abort_flag) break;
+        const int a = t / kb_per, kb = kb_first + t % kb_per;
         mbar_expect_tx(&full[s], kABytes + kBBytes);
-        tma_load_2d(sA + s * kABytes, &map_a, &full[s], (kb_first + kb) * BK, m0);
-        tma_load_2d(sB + s * kBBytes, &map_b, &full[s], (kb_first + kb) * BK, n0);
+        tma_load_2d(sA + s * kABytes, &map_a, &full[s], a * args.np + kb * BK, m0);
+        tma_load_2d(sB + s * kBBytes, &map_b, &full[s], kb * BK, n0);
         ++issued;
       }
       if (*abort_flag) {
-        // let the copies this thread started land before the CTA goes away
-        for (int kb = *(volatile int*)&s_consumed; kb < issued; ++kb) mbar_wait(&full[kb % kStages], (kb / kStages) & 1);
+        for (int t = *(volatile int*)&s_consumed; t < issued; ++t) mbar_wait(&full[t % kStages], (t / kStages) & 1);
       }
     }
   } else if (warp == 1) {
-    // ---------------- MMA issuer
+    // ---------------- MMA issuer: one accumulation per 128-long chunk, two TMEM buffers
     if (lane == 0) {
-      int kb = 0;
+      int t = 0;
       for (int c = 0; c < n_chunks && !*abort_flag; ++c) {
         const int b = c & 1;
         if (c >= 2 && !mbar_wait(&acc_empty[b], ((c >> 1) - 1) & 1)) { *abort_flag = 1; break; }
         const uint32_t d_tmem = tmem_base + (uint32_t)(b * BN);
-        const int first = kb, kb_end = min(kb_total, kb + (c < n_lead ? chunk : tail));
-        for (; kb < kb_end; ++kb) {
-          const int s = kb % kStages;
-          if (!mbar_wait(&full[s], (kb / kStages) & 1)) { *abort_flag = 1; break; }
-          *(volatile int*)&s_consumed = kb + 1;
+        for (int q = 0; q < kExactChunkBlocks; ++q, ++t) {
+          const int s = t % kStages;
+          if (!mbar_wait(&full[s], (t / kStages) & 1)) { *abort_flag = 1; break; }
+          *(volatile int*)&s_consumed = t + 1;
           tc_fence_after();
           const uint32_t a_addr = smem_u32(sA + s * kABytes), b_addr = smem_u32(sB + s * kBBytes);
 #pragma unroll
           for (int kk = 0; kk < BK / 16; ++kk)
             umma_f16(d_tmem, sw128_desc(a_addr + kk * 32), sw128_desc(b_addr + kk * 32), kIdesc,
-                     (kb > first || kk > 0) ? 1u : 0u);
+                     (q > 0 || kk > 0) ? 1u : 0u);
           umma_commit(&empty[s]);
         }
         if (*abort_flag) break;
         umma_commit(&acc_full[b]);
       }
-      // every MMA this thread issued has completed once `drain` fires
       umma_commit(drain);
       mbar_wait(drain, 0);
     }
   } else {
-    // ---------------- epilogue warps 2 .. 1 + 4 kGroups
+    // ---------------- epilogue: int32 level sums, one row per thread
     const int ew = warp - 2;
-    const int quarter = warp & 3;  // TMEM lanes 32*quarter .. +31
-    const int cbase = (ew >> 2) * kEpiCols;
-    const int row0 = m0 + quarter * 32;
+    const int quarter = warp & 3;
+    const int cbase = (ew >> 2) * kCols;
+    const int row = m0 + quarter * 32 + lane;
     const uint32_t lane_addr = (uint32_t)(quarter * 32) << 16;
-    StageT (*stage)[33] = s_stage[ew];
-    if constexpr (!kCompensated) {
-      if (mbar_wait(&acc_full[0], 0)) {
-        tc_fence_after();
+    uint32_t acc[kCols];
+#pragma unroll
+    for (int i = 0; i < kCols; ++i) acc[i] = 0u;
+    int in_level = 0;
+    for (int c = 0; c < n_chunks; ++c) {
+      const int b = c & 1;
+      if (!mbar_wait(&acc_full[b], (c >> 1) & 1)) { *abort_flag = 1; break; }
+      tc_fence_after();
+#pragma unroll
+      for (int c0 = 0; c0 < kCols; c0 += 32) {
         float v[32];
-#pragma unroll 1
-        for (int c0 = 0; c0 < BN; c0 += 32) {
-          tmem_ld32(tmem_base + lane_addr + (uint32_t)c0, v);
-          epi.store(row0, lane, n0 + c0, args.M, args.N, v, stage);
-        }
-      } else {
-        *abort_flag = 1;
+        tmem_ld32(tmem_base + lane_addr + (uint32_t)(b * BN + cbase + c0), v);
+        // v is an integer of magnitude <= 2^21: v + 1.5 2^23 keeps it in the low mantissa
+        // bits (exact), read as an integer it is v + 0x4B400000; the offsets are taken out
+        // when the level is stored (modulo 2^32, which is exact for the true sum)
+#pragma unroll
+        for (int i = 0; i < 32; ++i) acc[c0 + i] += __float_as_uint(v[i] + 12582912.0f);
       }
-    } else {
-      float sum[kEpiCols], comp[kEpiCols];
+      tc_fence_before();
+      mbar_arrive(&acc_empty[b]);
+      if (++in_level == chunks_per_level) {
+        const int a = c / chunks_per_level;
+        const uint32_t off = (uint32_t)chunks_per_level * 0x4B400000u;
+        int32_t* dst = args.lev + ((int64_t)blockIdx.z * args.max_levels + a) * args.plane + (int64_t)row * args.ldl +
+                       n0 + cbase;
 #pragma unroll
-      for (int i = 0; i < kEpiCols; ++i) {
-        sum[i] = 0.f;
-        comp[i] = 0.f;
-      }
-      bool ok = true;
-      for (int c = 0; c < n_chunks; ++c) {
-        const int b = c & 1;
-        if (!mbar_wait(&acc_full[b], (c >> 1) & 1)) { *abort_flag = 1; ok = false; break; }
-        tc_fence_after();
-        // drain in 32-column loads, or 16-column ones where the CTA's 10 warps leave each
-        // thread 168 registers (wide tiles) and the Kahan state of 64 columns needs 128
-        constexpr int kDrain = BN > 64 ? 16 : 32;
-#pragma unroll
-        for (int c0 = 0; c0 < kEpiCols; c0 += kDrain) {
-          float v[kDrain];
-          if constexpr (kDrain == 16)
-            tmem_ld16(tmem_base + lane_addr + (uint32_t)(b * BN + cbase + c0), v);
-          else
-            tmem_ld32(tmem_base + lane_addr + (uint32_t)(b * BN + cbase + c0), v);
-#pragma unroll
-          for (int i = 0; i < kDrain; ++i) {  // Kahan: sum + v, the lost low part kept in comp
-            float y = v[i] - comp[c0 + i];
-            float t = sum[c0 + i] + y;
-            comp[c0 + i] = (t - sum[c0 + i]) - y;
-            sum[c0 + i] = t;
-          }
+        for (int i = 0; i < kCols; i += 4) {
+          int4 w;
+          w.x = (int32_t)(acc[i] - off);
+          w.y = (int32_t)(acc[i + 1] - off);
+          w.z = (int32_t)(acc[i + 2] - off);
+          w.w = (int32_t)(acc[i + 3] - off);
+          *reinterpret_cast<int4*>(dst + i) = w;
+          acc[i] = acc[i + 1] = acc[i + 2] = acc[i + 3] = 0u;
         }
-        tc_fence_before();
-        mbar_arrive(&acc_empty[b]);
-      }
-      if (ok) {
-#pragma unroll
-        for (int c0 = 0; c0 < kEpiCols; c0 += 32) {
-#pragma unroll
-          for (int i = 0; i < 32; ++i) stage[lane][i] = (double)sum[c0 + i] - (double)comp[c0 + i];
-          epi.store(row0, lane, n0 + cbase + c0, args.M, args.N, stage, blockIdx.z);
-        }
+        in_level = 0;
       }
     }
   }
@@ -584,9 +600,10 @@ __global__ void __launch_bounds__(cta_threads<BN, kCompensated>(), 1)
 }
 
 template <int BN, int kStages>
-constexpr size_t smem_bytes() {
+constexpr size_t exact_smem_bytes() {
   return 1024 + (size_t)kStages * (BM * BK * 2 + BN * BK * 2) + (2 * kStages + 5) * 8 + 16;
 }
+
 
 // ------------------------------------------------------------------ host side
 // Launch D = A B^T (A [M x K], B [N x K], 16-bit K-major) with the epilogue `epi`;
@@ -601,25 +618,20 @@ rg_status gemm(rg_ctx* ctx, bool bf16, const void* A, int64_t lda, const void* B
 rg_status gemm_f32(rg_ctx* ctx, bool bf16, const void* A, int64_t lda, const void* B, int64_t ldb, int M, int N,
                    int K, float* C, int64_t ldc, float alpha, float beta, cudaStream_t s);
 
-// out (fp64, ld) = E - X + dl o (A B^T) (or dl o (A B^T) when E is null), bf16 operands,
-// fp32 tensor-core accumulation in chunks of `chunk_blocks` x 64 of K folded into a
-// compensated sum.
-// With split_ws (room for split_max x M x ld doubles) and too few 128 x 64 tiles to fill
-// the GPU, K is split over up to split_max CTAs per tile (in whole chunks); their sums go
-// to split_ws and one more kernel adds them in a fixed order and applies the epilogue.
-//
-// lead_blocks / tail_chunk_blocks (unsplit products only): after the first lead_blocks
-// K blocks the chunks grow to tail_chunk_blocks (the refinement residual's leading slice
-// pair needs the short compensated chunks; the pairs after it are 2^8 smaller and do with
-// long ones).
-rg_status gemm_residual(rg_ctx* ctx, const void* A, int64_t lda, const void* B, int64_t ldb, int M, int N, int K,
-                        int chunk_blocks, double* out, const double* E, const double* X, const double* dl,
-                        int64_t ld, cudaStream_t s, unsigned long long* red = nullptr,
-                        unsigned long long* colmax = nullptr, int* nonfinite = nullptr, double* split_ws = nullptr,
-                        int split_max = 0, int lead_blocks = 0, int tail_chunk_blocks = 0, int alg_k = 0);
-
-// K splits gemm_residual uses for an M x N product (1: none).
-int residual_splits(const rg_ctx* ctx, int M, int N, int K, int chunk_blocks, int split_max);
+// The exact level product of the refinement (gemm_exact_kernel): S_a = A_a B^T for the
+// L levels that *levels_d names, int32 sums to lev (see ExactArgs); tiles of 128 x 256 where
+// they give every SM a tile, else narrower; K split over up to split_max CTAs per tile when
+// the tiles leave SMs idle. lev needs split_max x max_levels planes of
+// exact_plane(M, N) int32; *splits_out receives the splits used. alg_k: the inner dimension of
+// the product the launch stands for (kernel timer accounting).
+int64_t exact_ld(int N);
+int64_t exact_plane(int M, int N);
+// The level count comes from levels_d (device int) or, when that is null, from
+// exact_level_count(level_words, level_bits, max_levels).
+rg_status gemm_exact(rg_ctx* ctx, const void* A, int64_t lda, const void* B, int64_t ldb, int M, int N, int np,
+                     const int* levels_d, const unsigned long long* level_words, int level_bits, int max_levels,
+                     int32_t* lev, int split_max, int* splits_out, cudaStream_t s, const int* skip = nullptr,
+                     int alg_k = 0);
 
 // Device error word the GEMM kernels raise on a timed-out wait (ctx scratch slot).
 constexpr int kGemmErrorSlot = 16;

@@ -1,0 +1,83 @@
+"""The exact refinement's two pieces against their integer definitions (bit for bit).
+
+The dense solves track the refinement residual R = E - K B exactly (App. B.2's mixed
+precision): P' = P diag(dr) is split into five 8-bit fixed-point slices per row, each
+correction into one 8-bit slice per column, and the tensor cores form their products as
+exact integer sums. These tests pin the split to its definition and the tcgen05 level
+product to integer arithmetic, including the largest operands (+-128), whose 128-long chunk
+sums reach 2^21 and whose level sums pass 2^24.
+"""
+import numpy as np
+import pytest
+import torch
+
+from paper_2511_04277_gb300 import api
+
+pytestmark = pytest.mark.gpu
+
+
+def split_reference(P, dr):
+    """rg_exact_split's definition in numpy int64: e_i = frexp exponent of the row maximum of
+    |P'|, q = rint(P' 2^(39 - e_i)), balanced base-256 digits of q."""
+    Pp = P * (dr[None, :] if dr is not None else 1.0)
+    n = P.shape[0]
+    mx = np.abs(Pp).max(axis=1)
+    e = np.where(mx > 0, np.frexp(mx)[1], 0).astype(np.int64)
+    q = np.rint(Pp * np.ldexp(1.0, 39 - e)[:, None]).astype(np.int64)
+    q[mx == 0] = 0
+    d = np.zeros((n, 5, P.shape[1]), np.int64)
+    for a in range(4, 0, -1):
+        d[:, a] = ((q + 128) & 255) - 128
+        q = (q - d[:, a]) >> 8
+    d[:, 0] = q
+    return d, e
+
+
+@pytest.mark.parametrize("n,trans,with_dr", [(300, False, True), (300, True, False), (129, False, False)])
+def test_exact_split_matches_its_definition(rg_ctx, n, trans, with_dr):
+    rng = np.random.default_rng(n + 7 * trans)
+    # entries spread over 40 binades, signs mixed, some exact zeros and one zero row
+    P = rng.uniform(-1, 1, (n, n)) * np.ldexp(1.0, rng.integers(-40, 1, (n, n)))
+    P[rng.random((n, n)) < 0.1] = 0.0
+    P[5] = 0.0
+    dr = rng.uniform(0.05, 0.95, n) if with_dr else None
+    P_d = torch.as_tensor(P.T.copy() if trans else P, device="cuda")
+    sl, ex = api.exact_split(rg_ctx, P_d, None if dr is None else torch.as_tensor(dr, device="cuda"), trans=trans)
+    d_ref, e_ref = split_reference(P, dr)
+    sl = sl.cpu().numpy().astype(np.int64)
+    np_ = sl.shape[2]
+    assert np.array_equal(ex.cpu().numpy(), e_ref)
+    assert np.array_equal(sl[:, :, :n], d_ref)
+    assert not sl[:, :, n:].any()
+    assert np.abs(sl[:, 1:]).max() <= 128 and np.abs(sl[:, 0]).max() <= 128
+    # the slices represent P' to 2^(e_i - 40)
+    w = np.ldexp(1.0, -8 * np.arange(5))
+    rec = np.einsum("iak,a->ik", sl[:, :, :n].astype(np.float64), w) * np.ldexp(1.0, e_ref - 7)[:, None]
+    Pp = P * (dr[None, :] if dr is not None else 1.0)
+    assert np.all(np.abs(rec - Pp) <= np.ldexp(1.0, e_ref - 40)[:, None])
+    del np_
+
+
+def _ints(rng, shape, extreme=False):
+    if extreme:
+        return rng.choice(np.array([-128.0, 128.0]), shape)
+    return rng.integers(-128, 129, shape).astype(np.float64)
+
+
+@pytest.mark.parametrize("M,N,np_,levels,extreme", [
+    (300, 257, 256, 5, False),     # ragged tiles, narrow tile widths
+    (130, 7, 1024, 3, True),       # every product 2^14: chunk sums 2^21, level sums 2^24
+    (4096, 2560, 512, 2, False),   # 128 x 256 tiles
+    (2048, 2049, 384, 4, True),    # 128 x 128 tiles with a one-column tail
+])
+def test_exact_gemm_is_integer_exact(rg_ctx, M, N, np_, levels, extreme):
+    rng = np.random.default_rng(M + N + levels)
+    A = np.zeros((M, 5 * np_))
+    A[:, :levels * np_] = _ints(rng, (M, levels * np_), extreme)
+    B = _ints(rng, (N, np_), extreme)
+    A_d = torch.as_tensor(A, device="cuda").to(torch.bfloat16)
+    B_d = torch.as_tensor(B, device="cuda").to(torch.bfloat16)
+    S = api.tc_gemm_exact(rg_ctx, A_d, B_d, levels).cpu().numpy().astype(np.int64)
+    for a in range(levels):
+        ref = (A[:, a * np_:(a + 1) * np_] @ B.T).astype(np.int64)   # exact in fp64 (< 2^53)
+        assert np.array_equal(S[a], ref), f"level {a}: max diff {np.abs(S[a] - ref).max()}"

@@ -70,42 +70,6 @@ def test_tc_gemm_wide_tiles_with_ragged_edges(rg_ctx, dt):
     assert (C - ref).abs().max().item() <= 2e-5 * scale
 
 
-def test_tc_gemm_residual_is_fp64_accurate(rg_ctx):
-    rng = np.random.default_rng(0)
-    M, N, K = 256, 190, 1536
-    A = torch.from_numpy(rng.random((M, K))).to(torch.bfloat16)
-    B = torch.from_numpy(rng.random((N, K))).to(torch.bfloat16)
-    Ed = rng.random((M, N))
-    Xd = rng.random((M, N))
-    dl = rng.uniform(0.5, 1.5, M)
-    out = api.tc_gemm_residual(rg_ctx, A.cuda(), B.cuda(), _dev(Ed), _dev(Xd), _dev(dl), chunk_k=128).cpu().numpy()
-    prod = A.double().numpy() @ B.double().numpy().T
-    ref = Ed - Xd + dl[:, None] * prod
-    assert np.abs(out - ref).max() <= 2e-7 * np.abs(dl[:, None] * prod).max()
-    plain = api.tc_gemm_residual(rg_ctx, A.cuda(), B.cuda(), chunk_k=64).cpu().numpy()
-    assert np.abs(plain - prod).max() <= 2e-7 * np.abs(prod).max()
-
-
-def test_tc_gemm_residual_wide_tiles_are_fp64_accurate(rg_ctx):
-    """Enough tiles for the 128-wide compensated path (two epilogue groups), partial tiles
-    on both edges. Within each 128-long chunk the tensor cores accumulate in fp32 rounding
-    toward zero; with all-positive operands that bias is coherent, about 1e-7 relative per
-    entry, and over 6.4 million entries its tail reaches past 2e-7 of the largest one."""
-    rng = np.random.default_rng(1)
-    M, N, K = 2593, 2483, 768
-    A = torch.from_numpy(rng.random((M, K))).to(torch.bfloat16)
-    B = torch.from_numpy(rng.random((N, K))).to(torch.bfloat16)
-    Ed = rng.random((M, N))
-    Xd = rng.random((M, N))
-    dl = rng.uniform(0.5, 1.5, M)
-    out = api.tc_gemm_residual(rg_ctx, A.cuda(), B.cuda(), _dev(Ed), _dev(Xd), _dev(dl), chunk_k=128).cpu().numpy()
-    prod = A.double().numpy() @ B.double().numpy().T
-    ref = Ed - Xd + dl[:, None] * prod
-    err = np.abs(out - ref)
-    assert err.max() <= 4e-7 * np.abs(dl[:, None] * prod).max()
-    assert np.median(err / np.abs(dl[:, None] * prod)) <= 2e-7      # a bias, not a wrong column group
-
-
 # ------------------------------------------------------------------ REFs
 def test_gebhart_plates_example(rg_ctx):
     F = load_matrix("plates_F.txt")
@@ -124,8 +88,9 @@ def test_gebhart_random_sizes(rg_ctx, N, prec):
     B, sw, res = api.gebhart(rg_ctx, _dev(F), _dev(eps), _dev(1 - eps), precision=prec, tol=1e-12)
     Bo = G.gebhart(F, eps, 1 - eps)
     assert _rownorm_err(B[0].cpu().numpy(), Bo) <= REL
-    # converged to tol, or stalled below 1e-8 (above the residual product's accuracy floor)
-    assert res <= 1e-8 and sw >= 1
+    assert _rownorm_err(B[0].cpu().numpy(), Bo) <= 1e-10
+    # converged to tol (the residual is tracked exactly, so 1e-12 is reachable)
+    assert res <= 1e-12 and sw >= 1
 
 
 def test_gebhart_batched_sets_and_identities(rg_ctx):
@@ -139,11 +104,11 @@ def test_gebhart_batched_sets_and_identities(rg_ctx):
     for s in range(S):
         Bo = G.gebhart(F, eps[s], rho[s])
         assert _rownorm_err(Bg[s], Bo) <= REL
-        # identities hold to the refinement's accuracy floor (~1e-8: the residual product
-        # is accumulated in compensated fp32 chunks of 128)
-        assert np.abs(Bg[s].sum(axis=1) - 1).max() <= 1e-7                   # Eq. 4.3
+        # the identities hold to the refinement's exactly tracked residual (tol 1e-12)
+        assert _rownorm_err(Bg[s], Bo) <= 1e-10
+        assert np.abs(Bg[s].sum(axis=1) - 1).max() <= 1e-10                  # Eq. 4.3
         R = (eps[s] * A)[:, None] * Bg[s][:, :N]
-        assert np.abs(R - R.T).max() <= 1e-7 * np.abs(R).max()                # Eq. 4.4
+        assert np.abs(R - R.T).max() <= 1e-10 * np.abs(R).max()               # Eq. 4.4
 
 
 def test_gebhart_black_surfaces(rg_ctx):
@@ -266,57 +231,3 @@ def test_lsq_plates_config(rg_ctx):
     assert np.abs(got.sum(axis=1) - 1).max() <= 1e-7
     eta = A[:, None] * got[:, :512]
     assert np.abs(eta - eta.T).max() <= 1e-7 * np.abs(eta).max()
-
-
-# ------------------------------------------------------------------ refinement slices
-def _bf16_rne(x):
-    """bf16 bit patterns of fp64 x, rounding to nearest, ties to even: the quantum is
-    2^(e-8) for |x| in [2^(e-1), 2^e) within bf16's normal range and 2^-133 below it;
-    results at 2^128 and above overflow to infinity (the float32 conversion of r)."""
-    with np.errstate(all="ignore"):
-        _, e = np.frexp(x)
-        q = np.where(np.abs(x) >= 2.0 ** -126, e - 8, -133)
-        r = np.ldexp(np.rint(np.ldexp(x, -q)), q)
-        return (r.astype(np.float32).view(np.uint32) >> 16).astype(np.uint16)
-
-
-def _bf16_value(bits):
-    return (bits.astype(np.uint32) << 16).view(np.float32).astype(np.float64)
-
-
-def test_refinement_slices_match_their_definition(rg_ctx):
-    """The bit-pattern split of the refinement product against its definition
-    s0 = bf16(x), s1 = bf16(x - s0), s2 = bf16(x - s0 - s1) in fp64, on random doubles
-    across the exponent range and on the edges: zeros, ties at every slice, bf16
-    subnormals, fp64 subnormals, values that overflow bf16, infinities."""
-    rng = np.random.default_rng(5)
-    n = 1 << 20
-    x = rng.standard_normal(n) * np.exp2(rng.integers(-140, 130, n).astype(np.float64))
-    u = x.view(np.uint64)
-    tie = rng.random(n) < 0.2                          # a tie in s0: bit 44 set, bits below 0
-    u[tie] = (u[tie] & ~np.uint64((1 << 45) - 1)) | np.uint64(1 << 44)
-    tie1 = rng.random(n) < 0.1                         # ties deeper down
-    k = rng.integers(0, 44, n).astype(np.uint64)
-    u[tie1] = (u[tie1] & ~((np.uint64(1) << (k[tie1] + np.uint64(1))) - np.uint64(1))) | (np.uint64(1) << k[tie1])
-    x = u.view(np.float64)
-    edges = np.array([0.0, -0.0, 5e-324, -5e-324, 2.2e-308, 1e-40, -1e-39, 2.0 ** -133, 2.0 ** -126, 3.38e38,
-                      3.3895313892515355e38, 3.4e38, -1e39, 1e300, np.inf, -np.inf, 1.0, -1.0, 1.0 + 2.0 ** -8,
-                      1.0 + 2.0 ** -9, 1.0 + 2.0 ** -9 + 2.0 ** -30])
-    x = np.concatenate([x, edges])
-    got = api.refinement_slices(rg_ctx, _dev(x)).cpu().numpy().view(np.uint16)
-    with np.errstate(all="ignore"):
-        s0 = _bf16_rne(x)
-        r = x - _bf16_value(s0)
-        s1 = _bf16_rne(r)
-        s2 = _bf16_rne(r - _bf16_value(s1))
-    want = np.stack([s0, s1, s2], axis=1)
-    nan_want = np.isnan(_bf16_value(want))
-    nan_got = np.isnan(_bf16_value(got))
-    assert np.array_equal(nan_want, nan_got)
-    assert np.array_equal(got[~nan_want], want[~nan_want])
-    # for doubles in bf16's range the slices carry 24 bits: |x - sum| <= 2^-24 |x| roughly
-    fin = np.isfinite(x) & (np.abs(x) > 2.0 ** -100) & (np.abs(x) < 2.0 ** 120)
-    g = got[fin]
-    tot = _bf16_value(g[:, 0]) + _bf16_value(g[:, 1]) + _bf16_value(g[:, 2])
-    assert np.all(np.abs(x[fin] - tot) <= 2.0 ** -24 * np.abs(x[fin]))
-    assert api.refinement_slices(rg_ctx, _dev(np.zeros(0))).shape == (0, 3)
