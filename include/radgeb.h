@@ -438,6 +438,28 @@ rg_status rg_temperatures_adjoint(rg_ctx* ctx, int32_t n, const double* B_d, con
                                   const double* T_d, const double* dT_d, int32_t precision, double tol,
                                   double* dB_d, double* deps_d, void* stream);
 
+/* rg_temperatures and rg_temperatures_adjoint for n_sets (eps, rho) sets sharing F, in one
+ * call: the same equations and results (each set's balance is refined to tol against its own
+ * exact residual), solved faster. For opaque faces (rho = 1 - eps) whose REFs close, the
+ * balance matrix of every set is K^-1 (I - F_NN) up to diagonal scalings (K = I - F_NN
+ * diag(rho), Eq. B.9), so one 16-bit approximate inverse of I - F_NN, built once per call,
+ * preconditions the refinement of all sets; F and rho enter only this preconditioner (with
+ * other properties the refinement converges more slowly, and RG_ERR_NOT_CONVERGED reports a
+ * failure to reach tol in 24 sweeps).
+ *   F_d       device fp64 [n][n+1], the view factors the REFs were solved from
+ *   B_d       device fp64 [n_sets][n][n+1]; eps_d, rho_d device fp64 [n_sets][n]
+ *   area_d    device fp64 [n];  Q_d device fp64 [n_sets][n];  T_d device fp64 [n_sets][n] (output)
+ * adjoint:  T_d, dT_d device fp64 [n_sets][n] in; dB_d [n_sets][n][n+1], deps_d [n_sets][n] out.
+ * Errors as rg_temperatures / rg_temperatures_adjoint. */
+rg_status rg_temperatures_sets(rg_ctx* ctx, int32_t n, const double* F_d, int32_t n_sets, const double* B_d,
+                               const double* eps_d, const double* rho_d, const double* area_d, const double* Q_d,
+                               double T_sink, double sigma, int32_t precision, double tol, double* T_d, void* stream);
+rg_status rg_temperatures_adjoint_sets(rg_ctx* ctx, int32_t n, const double* F_d, int32_t n_sets,
+                                       const double* B_d, const double* eps_d, const double* rho_d,
+                                       const double* area_d, double T_sink, double sigma, const double* T_d,
+                                       const double* dT_d, int32_t precision, double tol, double* dB_d,
+                                       double* deps_d, void* stream);
+
 /* ---------------------------------------------------------------- tensor-core GEMM */
 
 /* The tcgen05 GEMM the dense solves are built on (no counterpart in the thesis; it

@@ -435,6 +435,46 @@ def temperatures_adjoint(ctx: Context, B, eps, area, T_sink: float, T, dT, sigma
     return dB, deps
 
 
+def temperatures_sets(ctx: Context, F, B, eps, rho, area, Q, T_sink: float, sigma: float = 5.67e-8,
+                      precision="bf16", tol: float = 1e-13, stream=None, T=None) -> torch.Tensor:
+    """Steady temperatures of every (eps, rho) set [S, N] (rg_temperatures_sets; F and rho
+    precondition the refinement)."""
+    n = F.shape[0]
+    S = B.numel() // (n * (n + 1))
+    if T is None:
+        T = torch.empty((S, n), dtype=torch.float64, device=B.device)
+    ctx.check(ctx.lib.rg_temperatures_sets(ctx.handle, n, _dptr(F, torch.float64, "F", n * (n + 1), ctx.device), S,
+                                           _dptr(B, torch.float64, "B", S * n * (n + 1), ctx.device),
+                                           _dptr(eps, torch.float64, "eps", S * n, ctx.device),
+                                           _dptr(rho, torch.float64, "rho", S * n, ctx.device),
+                                           _dptr(area, torch.float64, "area", n, ctx.device),
+                                           _dptr(Q, torch.float64, "Q", S * n, ctx.device), float(T_sink),
+                                           float(sigma), _prec(precision), float(tol),
+                                           _dptr(T, torch.float64, "T", S * n, ctx.device), _stream(stream)),
+              "rg_temperatures_sets")
+    return T
+
+
+def temperatures_adjoint_sets(ctx: Context, F, B, eps, rho, area, T_sink: float, T, dT, sigma: float = 5.67e-8,
+                              precision="bf16", tol: float = 1e-13, stream=None, dB=None, deps=None):
+    """(dL/dB [S, N, N+1], direct dL/deps [S, N]) of every set (rg_temperatures_adjoint_sets)."""
+    n = F.shape[0]
+    S = B.numel() // (n * (n + 1))
+    if dB is None:
+        dB = torch.empty((S, n, n + 1), dtype=torch.float64, device=B.device)
+    if deps is None:
+        deps = torch.empty((S, n), dtype=torch.float64, device=B.device)
+    ctx.check(ctx.lib.rg_temperatures_adjoint_sets(
+        ctx.handle, n, _dptr(F, torch.float64, "F", n * (n + 1), ctx.device), S,
+        _dptr(B, torch.float64, "B", S * n * (n + 1), ctx.device), _dptr(eps, torch.float64, "eps", S * n, ctx.device),
+        _dptr(rho, torch.float64, "rho", S * n, ctx.device), _dptr(area, torch.float64, "area", n, ctx.device),
+        float(T_sink), float(sigma), _dptr(T, torch.float64, "T", S * n, ctx.device),
+        _dptr(dT, torch.float64, "dT", S * n, ctx.device), _prec(precision), float(tol),
+        _dptr(dB, torch.float64, "dB", S * n * (n + 1), ctx.device),
+        _dptr(deps, torch.float64, "deps", S * n, ctx.device), _stream(stream)), "rg_temperatures_adjoint_sets")
+    return dB, deps
+
+
 def debug_wait_timeout(ctx: Context, kind: str, limit_s: float = 0.01, stream=None):
     """Run one bounded device wait against a flag nothing sets (rg_debug_*_timeout);
     raises RadgebError(RG_ERR_CUDA) when the wait runs out, as it should."""

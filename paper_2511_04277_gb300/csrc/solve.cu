@@ -398,6 +398,112 @@ inline int grid_for(int64_t total, int sm) {
   return (int)(b < 1 ? 1 : (b > cap ? cap : b));
 }
 
+// ------------------------------------------------------------------ shared balance preconditioner
+// For the steady balance of opaque faces (rho = 1 - eps) with REFs that close (t = 1),
+// diag(t) - B_NN = K^-1 (I - F_NN) with K = I - F_NN diag(rho), so one approximate inverse W of
+// I - F_NN, shared by every (eps, rho) set, gives each set's correction as
+//   forward  D = W K diag(t) R,          adjoint  D = K^T W^T diag(t) R
+// (two matrix-vector products; the balance has one right-hand side). The residual stays the
+// exact residual of the set's own balance, so W only sets the convergence rate.
+struct BalancePre {
+  const void* W = nullptr;    // 16-bit np x np, row-major (the Newton-Schulz iterate)
+  const void* Wt = nullptr;   // its transpose
+  const double* F = nullptr;  // N x (N+1)
+  const double* rho = nullptr;
+  const double* t = nullptr;  // row sums of the set's B
+  bool trans = false;         // the adjoint (transposed) balance
+  bool fp16 = true;
+  double* y = nullptr;        // [np] scratch vectors
+  double* z = nullptr;
+};
+
+template <class T16>
+__device__ __forceinline__ float w16(const void* W, int64_t o) { return (float)reinterpret_cast<const T16*>(W)[o]; }
+
+// First kernel of a preconditioned sweep: the guard (as scaled_transpose16), the zeroing of
+// the sweep's words and of dcolmax[0], then y = t o src (column 0) and, forward, yr = rho o y.
+__global__ void pre_first(const double* __restrict__ src, int64_t ld, const double* __restrict__ t,
+                          const double* __restrict__ rho, int n, bool trans, double* __restrict__ y,
+                          double* __restrict__ yr, const SweepGuard guard, unsigned long long* red_cur,
+                          unsigned int* dcolmax) {
+  if (guard.err) {
+    __shared__ int s_end;
+    if (threadIdx.x == 0) {
+      s_end = sweep_ends(guard) ? 1 : 0;
+      if (blockIdx.x == 0) *guard.skip = s_end;
+    }
+    __syncthreads();
+    if (s_end) return;
+  }
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (blockIdx.x == 0 && threadIdx.x < 3) red_cur[threadIdx.x] = 0ull;
+  if (blockIdx.x == 0 && threadIdx.x == 0) dcolmax[0] = 0u;
+  if (i < n) {
+    const double v = t[i] * src[(int64_t)i * ld];
+    y[i] = v;
+    if (!trans) yr[i] = rho[i] * v;
+  }
+}
+
+// Forward: z_i = y_i - sum_j F_ij yr_j (one warp per row).
+__global__ void pre_k_apply(const double* __restrict__ F, int n, const double* __restrict__ y,
+                            const double* __restrict__ yr, double* __restrict__ z, const int* skip) {
+  if (skip && *(volatile const int*)skip) return;
+  const int i = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+  const int lane = threadIdx.x & 31;
+  if (i >= n) return;
+  double acc = 0.0;
+  for (int j = lane; j < n; j += 32) acc += F[(int64_t)i * (n + 1) + j] * yr[j];
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (lane == 0) z[i] = y[i] - acc;
+}
+
+// out_k = sum_i W[k][i] v_i (one warp per row of W, 16-bit W, fp32 products summed in fp64);
+// with D set, out goes to D[k][0] (fp32) and max_k |out_k| to dcolmax[0].
+template <class T16>
+__global__ void pre_w_apply(const void* __restrict__ W, int np, int n, const double* __restrict__ v,
+                            double* __restrict__ out, float* __restrict__ D, int64_t ldd, unsigned int* dcolmax,
+                            int* nonfinite, const int* skip) {
+  if (skip && *(volatile const int*)skip) return;
+  const int k = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+  const int lane = threadIdx.x & 31;
+  if (k >= n) return;
+  double acc = 0.0;
+  for (int i = lane; i < n; i += 32) acc += (double)(w16<T16>(W, (int64_t)k * np + i) * (float)v[i]);
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (lane == 0) {
+    if (out) out[k] = acc;
+    if (D) {
+      const float d = (float)acc;
+      D[(int64_t)k * ldd] = d;
+      if (!isfinite(d)) atomicExch(nonfinite, 1);
+      else atomicMax(dcolmax, __float_as_uint(fabsf(d)));
+    }
+  }
+}
+
+// Adjoint: D_k = w_k - rho_k sum_i F_ik w_i (K^T w), D[k][0] fp32 and max |D| into dcolmax[0].
+// Block (32 x 8) per 32 columns k: thread (x, y) sums rows i = y, y + 8, ... (coalesced in x).
+__global__ void pre_kt_apply(const double* __restrict__ F, int n, const double* __restrict__ rho,
+                             const double* __restrict__ w, float* __restrict__ D, int64_t ldd, unsigned int* dcolmax,
+                             int* nonfinite, const int* skip) {
+  if (skip && *(volatile const int*)skip) return;
+  __shared__ double part[8][33];
+  const int k = blockIdx.x * 32 + threadIdx.x;
+  double acc = 0.0;
+  if (k < n)
+    for (int i = threadIdx.y; i < n; i += 8) acc += F[(int64_t)i * (n + 1) + k] * w[i];
+  part[threadIdx.y][threadIdx.x] = acc;
+  __syncthreads();
+  if (threadIdx.y == 0 && k < n) {
+    for (int yy = 1; yy < 8; ++yy) acc += part[yy][threadIdx.x];
+    const float d = (float)(w[k] - rho[k] * acc);
+    D[(int64_t)k * ldd] = d;
+    if (!isfinite(d)) atomicExch(nonfinite, 1);
+    else atomicMax(dcolmax, __float_as_uint(fabsf(d)));
+  }
+}
+
 // ------------------------------------------------------------------ solver object
 struct Layout {
   int n, m, np, mp;
@@ -472,6 +578,7 @@ struct Solver {
   int cur = 0;       // which X16 buffer holds the current inverse
   int ns_steps = 0;
   int splits = 1;    // K splits of the last exact product
+  const BalancePre* pre = nullptr;  // set: corrections from the shared balance preconditioner
 
   unsigned long long* red(int parity) { return reinterpret_cast<unsigned long long*>(err + 10 + 6 * parity); }
 
@@ -600,14 +707,35 @@ struct Solver {
     unsigned long long* rc = red(parity);
     const int* skip = g.err ? g.skip : nullptr;
     dim3 tg(L.mp / 32, L.np / 32);
-    T16* Rt = static_cast<T16*>(b.Rt16);
-    scaled_transpose16<T16><<<tg, dim3(32, 8), 0, s>>>(src, L.mp, L.n, L.m, L.np, L.mp, b.colmax, Rt, b.colscale, g,
-                                                        rc, b.dcolmax);
-    ++ctx->launches;
-    RG_CUDA_TRY(ctx, cudaGetLastError());
-    rg_status st = tc::gemm(ctx, bf16, b.X16[cur], L.np, Rt, L.np, L.n, L.m, L.np,
-                            tc::EpiCorrection{b.Dbuf, L.mp, b.colscale, b.dcolmax, err + 1}, s, skip);
-    if (st != RG_OK) return st;
+    rg_status st = RG_OK;
+    if (pre) {
+      // D = W K diag(t) R (forward) or K^T W^T diag(t) R (adjoint), one column
+      const int rb = (L.n + 255) / 256, wb = (L.n + 7) / 8;
+      pre_first<<<rb, 256, 0, s>>>(src, L.mp, pre->t, pre->rho, L.n, pre->trans, pre->y, pre->z, g, rc, b.dcolmax);
+      ++ctx->launches;
+      auto wapply = pre->fp16 ? pre_w_apply<__half> : pre_w_apply<__nv_bfloat16>;
+      if (!pre->trans) {
+        // y -> z = K y (in pre->y, reading yr from pre->z), then D = W z
+        pre_k_apply<<<wb, 256, 0, s>>>(pre->F, L.n, pre->y, pre->z, pre->y, skip);
+        wapply<<<wb, 256, 0, s>>>(pre->W, L.np, L.n, pre->y, nullptr, b.Dbuf, L.mp, b.dcolmax, err + 1, skip);
+      } else {
+        // w = W^T y (rows of the transposed copy), then D = K^T w
+        wapply<<<wb, 256, 0, s>>>(pre->Wt, L.np, L.n, pre->y, pre->z, nullptr, 0, nullptr, err + 1, skip);
+        pre_kt_apply<<<(L.n + 31) / 32, dim3(32, 8), 0, s>>>(pre->F, L.n, pre->rho, pre->z, b.Dbuf, L.mp, b.dcolmax,
+                                                              err + 1, skip);
+      }
+      ctx->launches += 2;
+      RG_CUDA_TRY(ctx, cudaGetLastError());
+    } else {
+      T16* Rt = static_cast<T16*>(b.Rt16);
+      scaled_transpose16<T16><<<tg, dim3(32, 8), 0, s>>>(src, L.mp, L.n, L.m, L.np, L.mp, b.colmax, Rt, b.colscale,
+                                                          g, rc, b.dcolmax);
+      ++ctx->launches;
+      RG_CUDA_TRY(ctx, cudaGetLastError());
+      st = tc::gemm(ctx, bf16, b.X16[cur], L.np, Rt, L.np, L.n, L.m, L.np,
+                    tc::EpiCorrection{b.Dbuf, L.mp, b.colscale, b.dcolmax, err + 1}, s, skip);
+      if (st != RG_OK) return st;
+    }
     quantize_correction<<<tg, dim3(32, 8), 0, s>>>(b.Dbuf, L.n, L.m, L.np, L.mp, b.dcolmax, b.Bq, b.Dn, b.dexp, b.X,
                                                    first ? 1 : 0, rc, b.colmax, err + 1, skip);
     ++ctx->launches;
@@ -663,10 +791,18 @@ struct Solver {
     rg_status st = factor(dl, dr);
     if (st == RG_OK && slices) st = build_slices(dr);
     if (st != RG_OK) return st;
-    dim3 cg((L.m + 31) / 32, (L.n + 255) / 256);  // colmax was zeroed by build_ns_start
-    column_max<<<cg, dim3(32, 8), 0, s>>>(b.R0, L.mp, L.n, L.m, b.colmax);
-    ++ctx->launches;
-    RG_CUDA_TRY(ctx, cudaGetLastError());
+    return refine(dl, tol, max_sweeps, sweeps, rel_out);
+  }
+
+  // The refinement of run(), with the inverse (or the preconditioner) and the slices in place.
+  rg_status refine(const double* dl, double tol, int max_sweeps, int* sweeps, double* rel_out) {
+    rg_status st = RG_OK;
+    if (!pre) {
+      dim3 cg((L.m + 31) / 32, (L.n + 255) / 256);  // colmax was zeroed by build_ns_start
+      column_max<<<cg, dim3(32, 8), 0, s>>>(b.R0, L.mp, L.n, L.m, b.colmax);
+      ++ctx->launches;
+      RG_CUDA_TRY(ctx, cudaGetLastError());
+    }
     st = launch_sweep(0, true, dl);
     if (st != RG_OK) return st;
     double rel = INFINITY, prev = INFINITY;
@@ -1193,6 +1329,99 @@ rg_status rg_temperatures_adjoint(rg_ctx* ctx, int32_t n, const double* B_d, con
     st = sv.check_errors();
   }
   return st;
+}
+
+// Steady temperatures of n_sets (eps, rho) sets through the shared preconditioner
+// (BalancePre): one factorisation of I - F_NN for all sets, then per set the refinement of its
+// own balance. adjoint: the transposed balance and its outputs (rg_temperatures_adjoint).
+static rg_status temperatures_sets(rg_ctx* ctx, int32_t n, const double* F_d, int32_t n_sets, const double* B_d,
+                                   const double* eps_d, const double* rho_d, const double* area_d, const double* Q_d,
+                                   double T_sink, double sigma, int32_t precision, double tol, const double* T_in,
+                                   const double* dT_d, double* T_d, double* dB_d, double* deps_d, void* stream,
+                                   bool adjoint) {
+  const char* fn = adjoint ? "rg_temperatures_adjoint_sets" : "rg_temperatures_sets";
+  rg_status st = check_common(ctx, n, precision, tol, 1);
+  if (st != RG_OK) return st;
+  RG_ARG_CHECK(ctx, F_d && B_d && eps_d && rho_d && area_d && n_sets > 0 && sigma > 0.0 && T_sink >= 0.0 &&
+                        (adjoint ? (T_in && dT_d && dB_d && deps_d) : (Q_d && T_d)),
+               "%s: bad argument", fn);
+  RG_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+  cudaStream_t s = (cudaStream_t)stream;
+  rg::Sizer ex;
+  ex.take<double>((size_t)2 * ((n + NB - 1) / NB * NB));  // preconditioner vectors
+  Solver sv{ctx};
+  void* extra = nullptr;
+  st = sv.setup(n, 1, precision == RG_PREC_BF16_IR, s, ex.off, &extra);
+  if (st != RG_OK) return st;
+  rg::Carver cv(extra);
+  BalancePre pre;
+  pre.y = cv.take<double>(sv.L.np);
+  pre.z = cv.take<double>(sv.L.np);
+  // W ~ (I - F_NN)^-1, shared by every set
+  st = sv.set_matrix(F_d, n + 1, false);
+  if (st == RG_OK) st = sv.factor(nullptr, nullptr);
+  if (st != RG_OK) return st;
+  pre.W = sv.b.X16[sv.cur];
+  pre.Wt = sv.b.Xt16;
+  pre.F = F_d;
+  pre.trans = adjoint;
+  pre.fp16 = precision == RG_PREC_FP16_IR;
+  sv.pre = &pre;
+  double* t = sv.b.vec;
+  double* dl = sv.b.vec + sv.L.np;
+  pre.t = t;
+  const double u_sink = T_sink * T_sink * T_sink * T_sink;
+  sv.input_error = adjoint ? "rg_temperatures_adjoint_sets: a face with no radiative exchange or sigma eps A <= 0"
+                           : "rg_temperatures_sets: a face with no radiative exchange, sigma eps A <= 0, or a "
+                             "non-positive T^4";
+  for (int set = 0; set < n_sets; ++set) {
+    const double* B = B_d + (size_t)set * n * (n + 1);
+    const double* eps = eps_d + (size_t)set * n;
+    pre.rho = rho_d + (size_t)set * n;
+    st = sv.set_matrix(B, n + 1, adjoint);
+    if (st == RG_OK) st = sv.build_slices(nullptr);
+    if (st != RG_OK) return st;
+    balance_setup<<<(n + 7) / 8, 256, 0, s>>>(B, eps, area_d, adjoint ? eps : Q_d + (size_t)set * n, u_sink, sigma, n,
+                                               sv.L.mp, t, dl, adjoint ? nullptr : sv.b.R0, sv.err);
+    ++ctx->launches;
+    if (adjoint) {
+      balance_adj_rhs<<<(n + 127) / 128, 128, 0, s>>>(T_in + (size_t)set * n, dT_d + (size_t)set * n, t, n, sv.L.mp,
+                                                      sv.b.R0);
+      ++ctx->launches;
+    }
+    RG_CUDA_TRY(ctx, cudaGetLastError());
+    int sw = 0;
+    double rel = 0.0;
+    st = sv.refine(dl, tol, 24, &sw, &rel);
+    if (st != RG_OK) return st;
+    if (adjoint) {
+      balance_adj_out<<<(n + 7) / 8, 256, 0, s>>>(B, eps, T_in + (size_t)set * n, sv.b.X, sv.L.mp, u_sink, n,
+                                                   dB_d + (size_t)set * n * (n + 1), deps_d + (size_t)set * n);
+    } else {
+      quartic_root<<<(n + 127) / 128, 128, 0, s>>>(sv.b.X, sv.L.mp, n, T_d + (size_t)set * n, sv.err);
+    }
+    ++ctx->launches;
+    RG_CUDA_TRY(ctx, cudaGetLastError());
+  }
+  return sv.check_errors();
+}
+
+rg_status rg_temperatures_sets(rg_ctx* ctx, int32_t n, const double* F_d, int32_t n_sets, const double* B_d,
+                               const double* eps_d, const double* rho_d, const double* area_d, const double* Q_d,
+                               double T_sink, double sigma, int32_t precision, double tol, double* T_d, void* stream) {
+  if (!ctx) return RG_ERR_ARG;
+  return temperatures_sets(ctx, n, F_d, n_sets, B_d, eps_d, rho_d, area_d, Q_d, T_sink, sigma, precision, tol,
+                           nullptr, nullptr, T_d, nullptr, nullptr, stream, false);
+}
+
+rg_status rg_temperatures_adjoint_sets(rg_ctx* ctx, int32_t n, const double* F_d, int32_t n_sets,
+                                       const double* B_d, const double* eps_d, const double* rho_d,
+                                       const double* area_d, double T_sink, double sigma, const double* T_d,
+                                       const double* dT_d, int32_t precision, double tol, double* dB_d,
+                                       double* deps_d, void* stream) {
+  if (!ctx) return RG_ERR_ARG;
+  return temperatures_sets(ctx, n, F_d, n_sets, B_d, eps_d, rho_d, area_d, nullptr, T_sink, sigma, precision, tol,
+                           T_d, dT_d, nullptr, dB_d, deps_d, stream, true);
 }
 
 }  // extern "C"

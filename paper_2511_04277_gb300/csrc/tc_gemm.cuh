@@ -454,14 +454,17 @@ __global__ void __launch_bounds__(exact_threads(BN), 1)
   __shared__ int s_abort;
   __shared__ int s_consumed;
 
-  if (args.skip && *(volatile const int*)args.skip) return;  // uniform: before any barrier or allocation
-  const int L = args.levels ? *(volatile const int*)args.levels
-                            : exact_level_count(args.level_words, args.level_bits, args.max_levels);
+  const bool skipped = args.skip && *(volatile const int*)args.skip;
+  const int L = skipped ? 0
+                        : (args.levels ? *(volatile const int*)args.levels
+                                       : exact_level_count(args.level_words, args.level_bits, args.max_levels));
+  // the kernel timer's record of the levels this launch ran (0 when it skipped itself)
+  if (args.level_log && threadIdx.x == 0 && blockIdx.x == 0 && blockIdx.z == 0) *args.level_log = L;
+  if (skipped) return;  // uniform: before any barrier or allocation
   if (L < 1 || L > args.max_levels) {
     if (threadIdx.x == 0 && args.error_word) atomicExch(args.error_word, 1);
     return;
   }
-  if (args.level_log && threadIdx.x == 0 && blockIdx.x == 0 && blockIdx.z == 0) *args.level_log = L;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int tiles_m = (args.M + BM - 1) / BM, tiles_n = (args.N + BN - 1) / BN;
   const int pid = blockIdx.x;

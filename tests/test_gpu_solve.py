@@ -200,6 +200,53 @@ def test_temperatures_adjoint_vs_oracle(rg_ctx):
     assert np.abs(deps.cpu().numpy() - depso).max() <= REL * np.abs(depso).max()
 
 
+@pytest.mark.parametrize("prec", ["fp16", "bf16"])
+def test_temperature_sets_vs_oracle_and_per_set_calls(rg_ctx, prec):
+    """rg_temperatures_sets / rg_temperatures_adjoint_sets (one shared preconditioner for all
+    sets) against the oracle's balance and adjoint of each set (Eq. 3.13, 4.2), and against
+    the per-set entry points: the same equations, refined to the same tolerance."""
+    rng = np.random.default_rng(33)
+    N, S = 300, 3
+    F, A = _consistent_F(N, rng)
+    eps = rng.uniform(0.05, 0.9, (S, N))
+    rho = 1 - eps
+    Q = rng.uniform(0, 50, (S, N))
+    B, _, _ = api.gebhart(rg_ctx, _dev(F), _dev(eps), _dev(rho), tol=1e-12)
+    T = api.temperatures_sets(rg_ctx, _dev(F), B, _dev(eps), _dev(rho), _dev(A), _dev(Q), 3.0, precision=prec,
+                              tol=1e-13)
+    wT = rng.standard_normal((S, N))
+    dB, deps = api.temperatures_adjoint_sets(rg_ctx, _dev(F), B, _dev(eps), _dev(rho), _dev(A), 3.0, T, _dev(wT),
+                                             precision=prec, tol=1e-13)
+    Bh = B.cpu().numpy()
+    for s in range(S):
+        To = G.temperatures(Bh[s], eps[s], A, Q[s], 3.0)
+        assert np.abs(T[s].cpu().numpy() - To).max() <= 1e-10 * To.max()
+        dBo, depso = G.temperatures_adjoint(Bh[s], eps[s], A, Q[s], 3.0, T[s].cpu().numpy(), wT[s])
+        assert np.abs(dB[s].cpu().numpy() - dBo).max() <= 1e-9 * np.abs(dBo).max()
+        assert np.abs(deps[s].cpu().numpy() - depso).max() <= 1e-9 * np.abs(depso).max()
+        T1 = api.temperatures(rg_ctx, B[s].contiguous(), _dev(eps[s]), _dev(A), _dev(Q[s]), 3.0, precision=prec,
+                              tol=1e-13)
+        assert np.abs(T1.cpu().numpy() - T[s].cpu().numpy()).max() <= 1e-10 * To.max()
+
+
+def test_temperature_sets_small_sat(rg_ctx):
+    """The 2,048-face small satellite, two sets: the batched balance against the oracle."""
+    w = synth.workload("small_sat", rays_scale=0.02)
+    mesh = api.Mesh.from_synth(rg_ctx, w["mesh"])
+    F = api.counts_to_F(rg_ctx, api.trace(rg_ctx, mesh, w["rays"], 0), _dev(w["rays"], torch.int64))
+    A = mesh.face_areas()
+    api.enforce_iterative(rg_ctx, F, _dev(A), tol=1e-12)
+    N = F.shape[0]
+    eps, rho = synth.optical_sets(N, 2, 0.05, 0.9, seed=40)
+    Q = np.stack([synth.heat_loads(N, seed=3), synth.heat_loads(N, seed=4)])
+    B, _, _ = api.gebhart(rg_ctx, F, _dev(eps), _dev(rho), tol=1e-12)
+    T = api.temperatures_sets(rg_ctx, F, B, _dev(eps), _dev(rho), _dev(A), _dev(Q), 3.0, tol=1e-13)
+    Bh = B.cpu().numpy()
+    for s in range(2):
+        To = G.temperatures(Bh[s], eps[s], A, Q[s], 3.0)
+        assert np.abs(T[s].cpu().numpy() - To).max() <= 1e-10 * To.max()
+
+
 # ------------------------------------------------------------------ least-squares optimum
 def test_lsq_disc_example(rg_ctx):
     F1 = load_matrix("disc_F1_mcrt.txt")
