@@ -491,9 +491,10 @@ rg_status rg_tc_gemm(rg_ctx* ctx, int32_t M, int32_t N, int32_t K, const void* A
  *
  * rg_tc_gemm_exact: the level product on tcgen05 for integer operands:
  *   S_a[i][j] = sum_k A[i][a np + k] B[j][k]  for a = 0 .. levels-1,
- *   A_d  device bf16 [M][lda] (lda >= 5 np), B_d device bf16 [N][np], every element an
- *        integer of magnitude <= 128 (then every product is <= 2^14 and every 128-long chunk
- *        sum is exact in the fp32 tensor-core accumulator); np a multiple of 128
+ *   A_d  device bf16 [M][lda] (lda >= 5 np), every element an integer of magnitude <= 128;
+ *   B_d  device bf16 [N][np], every element an integer of magnitude <= 127 (then every
+ *        product is below 2^14 and every 256-long chunk sum is exact in the fp32
+ *        tensor-core accumulator); np a multiple of 128
  *   S_d  device int32 [levels][M][N] (output), exact for |S| < 2^31
  *   Errors: RG_ERR_ARG (layout, levels outside 1..5), RG_ERR_CUDA. */
 rg_status rg_exact_split(rg_ctx* ctx, int32_t n, const double* P_d, int64_t ldp, int32_t trans, const double* dr_d,

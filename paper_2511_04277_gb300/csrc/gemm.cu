@@ -168,7 +168,7 @@ rg_status gemm_exact(rg_ctx* ctx, const void* A, int64_t lda, const void* B, int
                      const int* levels_d, const unsigned long long* level_words, int level_bits, int max_levels,
                      int32_t* lev, int split_max, int* splits_out, cudaStream_t s, const int* skip, int alg_k) {
   if (M <= 0 || N <= 0) return RG_OK;
-  if (np <= 0 || np % (BK * kExactChunkBlocks) || max_levels < 1)
+  if (np <= 0 || np % (2 * BK) || max_levels < 1)
     return rg::fail(ctx, RG_ERR_ARG, "gemm_exact: level length %d, %d levels", np, max_levels);
   // the widest tile that still gives every SM a tile
   const int64_t tm = (M + BM - 1) / BM;
@@ -179,7 +179,7 @@ rg_status gemm_exact(rg_ctx* ctx, const void* A, int64_t lda, const void* B, int
   int splits = 1;
   for (int z = 2; z <= split_max; ++z) {
     if ((int64_t)tiles * (z - 1) >= ctx->sm_count) break;
-    if (kb_level % (kExactChunkBlocks * z) == 0) splits = z;
+    if (kb_level % (2 * z) == 0) splits = z;
   }
   if (splits_out) *splits_out = splits;
   CUtensorMap ma, mb;

@@ -78,6 +78,29 @@ __device__ __forceinline__ double scale2(double x, int k) {
   return ldexp(x, k);
 }
 
+// q 2^k for an integer q (|q| < 2^63), rounded to nearest, ties to even, when q needs more
+// than 53 bits: the same double as scale2((double)q, k), formed with integer operations
+// (GB300 runs fp64 arithmetic and conversions on a pipe far slower than its integer ALU).
+__device__ __forceinline__ double int_scale2(long long q, int k) {
+  if (q == 0) return 0.0;
+  const unsigned long long sgn = q < 0 ? 0x8000000000000000ull : 0ull;
+  const unsigned long long a = q < 0 ? 0ull - (unsigned long long)q : (unsigned long long)q;
+  const int lz = __clzll((long long)a);
+  int e = 63 - lz + k;                       // exponent of the leading bit
+  const unsigned long long m = a << lz;      // leading bit at 63
+  unsigned long long mant = m >> 11;         // 53 bits
+  const unsigned long long rem = m & 0x7ffull;
+  if (rem > 0x400ull || (rem == 0x400ull && (mant & 1ull))) {
+    ++mant;
+    if (mant >> 53) {
+      mant >>= 1;
+      ++e;
+    }
+  }
+  if (e < -1022 || e > 1023) return scale2((double)q, k);
+  return __longlong_as_double((long long)(sgn | ((unsigned long long)(e + 1023) << 52) | (mant & 0xfffffffffffffull)));
+}
+
 // Levels of P' that a sweep uses: the dropped ones stay below 2^-kLevelBits of
 // max|P'| max|X|, with max|X| and max|D| in red[1] and red[2] (the sweep's status words).
 __device__ __forceinline__ int exact_levels(const unsigned long long* red) {
@@ -156,7 +179,6 @@ __global__ void quantize_correction(const float* __restrict__ D, int n, int m, i
   int f = 0;
   if (cb != 0u && cfin) f = frexp_exponent((double)__uint_as_float(cb));
   const float sc = ldexpf(1.f, 7 - f);
-  const double unit = ldexp(1.0, f - 7);
   if (blockIdx.y == 0 && threadIdx.y == 0) {
     if (j < mp) {
       dexp[j] = f;
@@ -176,7 +198,8 @@ __global__ void quantize_correction(const float* __restrict__ D, int n, int m, i
       q = q > 127 ? 127 : (q < -127 ? -127 : q);
       const int64_t o = (int64_t)k * mp + j;
       Dn[o] = (int16_t)q;
-      const double v = (double)q * unit + (first ? 0.0 : X[o]);
+      const double dv = int_scale2(q, f - 7);
+      const double v = first ? dv : X[o] + dv;
       X[o] = v;
       xmax = max(xmax, (unsigned long long)__double_as_longlong(fabs(v)) & 0x7fffffffffffffffull);
     }
@@ -220,9 +243,9 @@ __global__ void finish_residual(const int32_t* __restrict__ lev, int64_t ldl, in
         for (int a = 0; a < L; ++a) t = t * 256 + lev[((int64_t)z * kLevels + a) * plane + o];
         T += t;
       }
-      const double S = scale2((double)T, rowexp[i] + f - 14 - 8 * (L - 1));
+      const double S = int_scale2(T, rowexp[i] + f - 14 - 8 * (L - 1));
       const int64_t e = (int64_t)i * mp + j;
-      const double d = scale2((double)Dn[e], f - 7);
+      const double d = int_scale2(Dn[e], f - 7);
       const double r = ((first ? R0[e] : R[e]) - d) + (dl ? dl[i] : 1.0) * S;
       R[e] = r;
       if (Q) Q[e] = (first ? 0.0 : Q[e]) + S;

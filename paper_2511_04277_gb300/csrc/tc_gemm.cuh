@@ -392,11 +392,12 @@ constexpr size_t smem_bytes() {
 // ------------------------------------------------------------------ exact level GEMM
 // The product of the exact refinement (solve.cu): for levels a = 0 .. L-1,
 //   S_a[i][j] = sum_k A[i][a np + k] B[j][k],   A [M][Lmax np], B [N][np], both bf16 K-major,
-// where every element of A and B is an integer of magnitude <= 128 (exact in bf16). Each
-// product is then an integer of magnitude <= 2^14 and the sum of one 128-long chunk is at
-// most 2^21, so the fp32 tensor-memory accumulator holds every chunk sum exactly whatever
-// the order of its additions. The epilogue adds the chunk sums as int32 (exact for level
-// sums below 2^31, i.e. np <= 131,072) and stores each level's sums as int32 to
+// where every element of A is an integer of magnitude <= 128 and every element of B one of
+// magnitude <= 127 (exact in bf16). Each product is then an integer of magnitude below 2^14
+// and the sum of one 256-long chunk stays below 2^22, so the fp32 tensor-memory accumulator
+// holds every chunk sum exactly whatever the order of its additions. The epilogue adds the
+// chunk sums as int32 (exact for level sums below 2^31, i.e. np <= 131,072) and stores each
+// level's sums as int32 to
 // lev + (z Lmax + a) plane, row i at i ldl (z: the CTA's K split). L is read from device
 // memory (written by an earlier kernel on the stream), so that the level count can be
 // decided on the device. Warp roles as gemm_kernel; the epilogue has one group of four
@@ -427,7 +428,7 @@ struct ExactArgs {
   int* level_log = nullptr;  // kernel timer: the launch records L here (CTA 0, thread 0)
 };
 
-constexpr int kExactChunkBlocks = 2;  // 128-long K chunks
+constexpr int kExactChunkBlocks = 4;  // 256-long K chunks (the last one of a level may be shorter)
 __host__ __device__ constexpr int exact_groups(int BN) { return BN > 128 ? BN / 128 : 1; }
 __host__ __device__ constexpr int exact_threads(int BN) { return 64 + 128 * exact_groups(BN); }
 
@@ -477,7 +478,7 @@ __global__ void __launch_bounds__(exact_threads(BN), 1)
   const int kb_level = args.np / BK;  // K blocks of one level
   const int kb_first = args.split_blocks > 0 ? blockIdx.z * args.split_blocks : 0;
   const int kb_per = args.split_blocks > 0 ? min(args.split_blocks, kb_level - kb_first) : kb_level;
-  const int chunks_per_level = kb_per / kExactChunkBlocks;
+  const int chunks_per_level = (kb_per + kExactChunkBlocks - 1) / kExactChunkBlocks;
   const int n_chunks = L * chunks_per_level;
   const int total_kb = L * kb_per;
 
@@ -529,7 +530,9 @@ __global__ void __launch_bounds__(exact_threads(BN), 1)
         const int b = c & 1;
         if (c >= 2 && !mbar_wait(&acc_empty[b], ((c >> 1) - 1) & 1)) { *abort_flag = 1; break; }
         const uint32_t d_tmem = tmem_base + (uint32_t)(b * BN);
-        for (int q = 0; q < kExactChunkBlocks; ++q, ++t) {
+        const int c_in = c % chunks_per_level;
+        const int nq = min(kExactChunkBlocks, kb_per - c_in * kExactChunkBlocks);
+        for (int q = 0; q < nq; ++q, ++t) {
           const int s = t % kStages;
           if (!mbar_wait(&full[s], (t / kStages) & 1)) { *abort_flag = 1; break; }
           *(volatile int*)&s_consumed = t + 1;
@@ -566,7 +569,7 @@ __global__ void __launch_bounds__(exact_threads(BN), 1)
       for (int c0 = 0; c0 < kCols; c0 += 32) {
         float v[32];
         tmem_ld32(tmem_base + lane_addr + (uint32_t)(b * BN + cbase + c0), v);
-        // v is an integer of magnitude <= 2^21: v + 1.5 2^23 keeps it in the low mantissa
+        // v is an integer of magnitude below 2^22: v + 1.5 2^23 keeps it in the low mantissa
         // bits (exact), read as an integer it is v + 0x4B400000; the offsets are taken out
         // when the level is stored (modulo 2^32, which is exact for the true sum)
 #pragma unroll

@@ -2,10 +2,11 @@
 
 The dense solves track the refinement residual R = E - K B exactly (App. B.2's mixed
 precision): P' = P diag(dr) is split into five 8-bit fixed-point slices per row, each
-correction into one 8-bit slice per column, and the tensor cores form their products as
-exact integer sums. These tests pin the split to its definition and the tcgen05 level
-product to integer arithmetic, including the largest operands (+-128), whose 128-long chunk
-sums reach 2^21 and whose level sums pass 2^24.
+correction into one 8-bit slice per column (integers up to 127), and the tensor cores form
+their products as exact integer sums. These tests pin the split to its definition and the
+tcgen05 level product to integer arithmetic, including the largest operands (+-128 times
++-127), whose 256-long chunk sums reach 4,161,536 (just below 2^22) and whose level sums
+pass 2^24.
 """
 import numpy as np
 import pytest
@@ -58,15 +59,16 @@ def test_exact_split_matches_its_definition(rg_ctx, n, trans, with_dr):
     del np_
 
 
-def _ints(rng, shape, extreme=False):
+def _ints(rng, shape, extreme=False, top=128):
     if extreme:
-        return rng.choice(np.array([-128.0, 128.0]), shape)
-    return rng.integers(-128, 129, shape).astype(np.float64)
+        return rng.choice(np.array([-float(top), float(top)]), shape)
+    return rng.integers(-top, top + 1, shape).astype(np.float64)
 
 
 @pytest.mark.parametrize("M,N,np_,levels,extreme", [
     (300, 257, 256, 5, False),     # ragged tiles, narrow tile widths
-    (130, 7, 1024, 3, True),       # every product 2^14: chunk sums 2^21, level sums 2^24
+    (130, 7, 1024, 3, True),       # every product 16,256: chunk sums just below 2^22
+    (257, 300, 384, 5, True),      # a level of 1.5 chunks: a short last chunk
     (4096, 2560, 512, 2, False),   # 128 x 256 tiles
     (2048, 2049, 384, 4, True),    # 128 x 128 tiles with a one-column tail
 ])
@@ -74,7 +76,7 @@ def test_exact_gemm_is_integer_exact(rg_ctx, M, N, np_, levels, extreme):
     rng = np.random.default_rng(M + N + levels)
     A = np.zeros((M, 5 * np_))
     A[:, :levels * np_] = _ints(rng, (M, levels * np_), extreme)
-    B = _ints(rng, (N, np_), extreme)
+    B = _ints(rng, (N, np_), extreme, top=127)
     A_d = torch.as_tensor(A, device="cuda").to(torch.bfloat16)
     B_d = torch.as_tensor(B, device="cuda").to(torch.bfloat16)
     S = api.tc_gemm_exact(rg_ctx, A_d, B_d, levels).cpu().numpy().astype(np.int64)
