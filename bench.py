@@ -5,9 +5,11 @@ One step is the whole path on the spacecraft workload, the large model: a proced
 spacecraft (1 x 1 x 1.5 m body, two wings of three tilted 1 m panels, two radiators, a
 32-facet boom), 204,512 triangles grouped into N = 10,240 faces, 1e9 rays split by area:
   MCRT counts -> F -> iterative closure/reciprocity enforcer (fp64) -> REFs of 16
-  (eps, rho) sets (eps ~ U[0.05, 0.9], rho = 1 - eps; fp16 tensor-core inverse + fp64-
-  accurate refinement) -> steady temperatures of every set (Q ~ U[0, 50] W, 3 K sink) ->
-  their adjoint -> the adjoint of the REFs (dL/deps, dL/drho of L = sum of all T).
+  (eps, rho) sets (eps ~ U[0.05, 0.9], rho = 1 - eps; fp16 tensor-core inverse + a
+  refinement whose residual is tracked exactly) -> steady temperatures of every set
+  (Q ~ U[0, 50] W, 3 K sink) -> their adjoint -> the adjoint of the REFs (dL/deps,
+  dL/drho of L = sum of all T; the balance's cotangent dL/dB is rank 2, so K^T is solved
+  for two right-hand sides per set).
 value = rays traced per second of whole steps (all ranks' rays / the slowest rank).
 
 The plates (N = 512, with the least-squares enforcer and sub-face aggregation) and the
@@ -39,9 +41,9 @@ HEADLINE = "spacecraft"
 WORKLOADS = {
     "spacecraft": ("spacecraft: body + 6 tilted panels + 2 radiators + boom, 204,512 triangles grouped into "
                    "N=10,240 faces, 1e9 rays split by area per step; iterative fp64 enforcement; REFs of 16 eps/rho "
-                   "sets (fp16 tensor-core inverse + fp64-accurate refinement); steady temperatures of every set "
-                   "(Q ~ U[0,50] W, 3 K sink) and their adjoints; REF adjoints of every set (dL/deps, dL/drho of "
-                   "L = sum T)"),
+                   "sets (fp16 tensor-core inverse + refinement with an exactly tracked residual); steady "
+                   "temperatures of every set (Q ~ U[0,50] W, 3 K sink) and their adjoints; REF adjoints of every "
+                   "set (dL/deps, dL/drho of L = sum T, the balance's rank-2 cotangent)"),
     "plates": ("plates: 2 x (16 x 16) sub-faces, N=512, 1,024 triangles, 1e6 rays/sub-face (5.12e8 per step); "
                "iterative + least-squares (NNR+SPVA) enforcement; sub-face->plate aggregation; REFs (N=512, fp16 "
                "tensor-core inverse + fp64-accurate refinement); steady temperatures + adjoints"),
@@ -204,7 +206,8 @@ class Pipeline:
         self.F_it = torch.empty_like(self.F)
         self.F_ls = torch.empty_like(self.F) if lsq else None
         self.B = torch.empty((S, N, N + 1), **f64)
-        self.dB = torch.empty((S, N, N + 1), **f64)
+        self.dB_a = torch.empty((S, 2, N), **f64)      # dL/dB of the balance, factored: sum_r a_r b_r^T
+        self.dB_b = torch.empty((S, 2, N + 1), **f64)
         self.T = torch.empty((S, N), **f64)
         self.deps_T = torch.empty((S, N), **f64)
         self.Qs = self.Q.expand(S, N).contiguous()
@@ -249,11 +252,15 @@ class Pipeline:
         api.temperatures_sets(self.ctx, self.F_it, self.B, self.eps, self.rho, self.areas, self.Qs, T_SINK, SIGMA,
                               precision=p, tol=SOLVE_TOL, T=self.T)
         api.temperatures_adjoint_sets(self.ctx, self.F_it, self.B, self.eps, self.rho, self.areas, T_SINK, self.T,
-                                      self.dT, SIGMA, precision=p, tol=SOLVE_TOL, dB=self.dB, deps=self.deps_T)
+                                      self.dT, SIGMA, precision=p, tol=SOLVE_TOL, deps=self.deps_T, factored=True,
+                                      dB_a=self.dB_a, dB_b=self.dB_b)
 
     def adjoint(self):
-        self.deps_B, self.drho = self.api.gebhart_adjoint(self.ctx, self.F_it, self.eps, self.rho, self.B, self.dB,
-                                                          precision=SOLVE_PRECISION, tol=SOLVE_TOL)
+        """The REF adjoint of every set for the balance's cotangent dL/dB = sum_r a_r b_r^T
+        (rank 2): K^T solved for the two left factors of each set."""
+        self.deps_B, self.drho = self.api.gebhart_adjoint_factored(self.ctx, self.F_it, self.eps, self.rho, self.B,
+                                                                   self.dB_a, self.dB_b, precision=SOLVE_PRECISION,
+                                                                   tol=SOLVE_TOL)
 
     def step(self, marks=None, stream=None):
         """One pass of the path; with `marks` (one CUDA event per stage) each stage's end is
@@ -1128,7 +1135,8 @@ class _RandomSystem:
         self.ones = torch.ones(n, dtype=torch.float64, device=device)
         f64 = dict(dtype=torch.float64, device=device)
         self.B = torch.empty((n_sets, n, n + 1), **f64)
-        self.dB = torch.empty((n_sets, n, n + 1), **f64)
+        self.dB_a = torch.empty((n_sets, 2, n), **f64)
+        self.dB_b = torch.empty((n_sets, 2, n + 1), **f64)
         self.T = torch.empty((n_sets, n), **f64)
         self.deps_T = torch.empty((n_sets, n), **f64)
 

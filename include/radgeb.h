@@ -449,7 +449,11 @@ rg_status rg_temperatures_adjoint(rg_ctx* ctx, int32_t n, const double* B_d, con
  *   F_d       device fp64 [n][n+1], the view factors the REFs were solved from
  *   B_d       device fp64 [n_sets][n][n+1]; eps_d, rho_d device fp64 [n_sets][n]
  *   area_d    device fp64 [n];  Q_d device fp64 [n_sets][n];  T_d device fp64 [n_sets][n] (output)
- * adjoint:  T_d, dT_d device fp64 [n_sets][n] in; dB_d [n_sets][n][n+1], deps_d [n_sets][n] out.
+ * adjoint:  T_d, dT_d device fp64 [n_sets][n] in; deps_d [n_sets][n] out (the direct part of
+ *           dL/deps) and dL/dB, in full in dB_d [n_sets][n][n+1] and/or in its factored form
+ *           dL/dB_ij = -nu_i (u_i - u_j) = sum_r a_r,i b_r,j (r = 0, 1; u = T^4, u_n = T_sink^4):
+ *           dB_a_d [n_sets][2][n] = (-nu o u, nu), dB_b_d [n_sets][2][n+1] = (1, u); dB_d may
+ *           be NULL when dB_a_d and dB_b_d are given, and those two may be NULL when dB_d is.
  * Errors as rg_temperatures / rg_temperatures_adjoint. */
 rg_status rg_temperatures_sets(rg_ctx* ctx, int32_t n, const double* F_d, int32_t n_sets, const double* B_d,
                                const double* eps_d, const double* rho_d, const double* area_d, const double* Q_d,
@@ -458,7 +462,20 @@ rg_status rg_temperatures_adjoint_sets(rg_ctx* ctx, int32_t n, const double* F_d
                                        const double* B_d, const double* eps_d, const double* rho_d,
                                        const double* area_d, double T_sink, double sigma, const double* T_d,
                                        const double* dT_d, int32_t precision, double tol, double* dB_d,
-                                       double* deps_d, void* stream);
+                                       double* dB_a_d, double* dB_b_d, double* deps_d, void* stream);
+
+/* rg_gebhart_adjoint for a cotangent given in factored form, dB = sum_r a_r b_r^T (for
+ * instance the one rg_temperatures_adjoint_sets writes: rank 2). Lambda = K^-T dB =
+ * sum_r x_r b_r^T with K^T x_r = a_r, so the transposed system (a fresh factorisation of K^T,
+ * no stored factors, as rg_gebhart_adjoint) is solved for `rank` right-hand sides instead of
+ * N+1, and (derived from Eq. B.11)
+ *   dL/deps_j = sum_r b_r,j (F^T x_r)_j,    dL/drho_k = sum_r (F^T x_r)_k (B b_r)_k.
+ *   a_d  device fp64 [n_sets][rank][n];  b_d device fp64 [n_sets][rank][n+1];  1 <= rank <= 64
+ * The other arguments and the errors as rg_gebhart_adjoint. */
+rg_status rg_gebhart_adjoint_factored(rg_ctx* ctx, int32_t n, const double* F_d, int32_t n_sets,
+                                      const double* eps_d, const double* rho_d, const double* B_d, int32_t rank,
+                                      const double* a_d, const double* b_d, int32_t precision, double tol,
+                                      int32_t max_sweeps, double* deps_d, double* drho_d, void* stream);
 
 /* ---------------------------------------------------------------- tensor-core GEMM */
 

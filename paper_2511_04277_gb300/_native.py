@@ -63,7 +63,8 @@ SIGNATURES = {
     "rg_temperatures": (i32, [P, i32, P, P, P, P, f64, f64, i32, f64, P, P]),
     "rg_temperatures_adjoint": (i32, [P, i32, P, P, P, f64, f64, P, P, i32, f64, P, P, P]),
     "rg_temperatures_sets": (i32, [P, i32, P, i32, P, P, P, P, P, f64, f64, i32, f64, P, P]),
-    "rg_temperatures_adjoint_sets": (i32, [P, i32, P, i32, P, P, P, P, f64, f64, P, P, i32, f64, P, P, P]),
+    "rg_temperatures_adjoint_sets": (i32, [P, i32, P, i32, P, P, P, P, f64, f64, P, P, i32, f64, P, P, P, P, P]),
+    "rg_gebhart_adjoint_factored": (i32, [P, i32, P, i32, P, P, P, i32, P, P, i32, f64, i32, P, P, P]),
     "rg_tc_gemm": (i32, [P, i32, i32, i32, P, i64, P, i64, i32, P, i64, ctypes.c_float, ctypes.c_float, P]),
     "rg_exact_split": (i32, [P, i32, P, i64, i32, P, P, P, P]),
     "rg_tc_gemm_exact": (i32, [P, i32, i32, i32, i32, P, i64, P, P, P]),

@@ -456,23 +456,55 @@ def temperatures_sets(ctx: Context, F, B, eps, rho, area, Q, T_sink: float, sigm
 
 
 def temperatures_adjoint_sets(ctx: Context, F, B, eps, rho, area, T_sink: float, T, dT, sigma: float = 5.67e-8,
-                              precision="bf16", tol: float = 1e-13, stream=None, dB=None, deps=None):
-    """(dL/dB [S, N, N+1], direct dL/deps [S, N]) of every set (rg_temperatures_adjoint_sets)."""
+                              precision="bf16", tol: float = 1e-13, stream=None, dB=None, deps=None,
+                              factored: bool = False, dB_a=None, dB_b=None):
+    """Direct dL/deps [S, N] and dL/dB of every set (rg_temperatures_adjoint_sets): dL/dB in
+    full [S, N, N+1], or with factored=True as (a [S, 2, N], b [S, 2, N+1]) with
+    dL/dB = sum_r a_r b_r^T. Returns (dB or (a, b), deps)."""
     n = F.shape[0]
     S = B.numel() // (n * (n + 1))
-    if dB is None:
-        dB = torch.empty((S, n, n + 1), dtype=torch.float64, device=B.device)
+    dev = B.device
+    nul = ctypes.c_void_p(None)
+    if factored:
+        dB_a = torch.empty((S, 2, n), dtype=torch.float64, device=dev) if dB_a is None else dB_a
+        dB_b = torch.empty((S, 2, n + 1), dtype=torch.float64, device=dev) if dB_b is None else dB_b
+    elif dB is None:
+        dB = torch.empty((S, n, n + 1), dtype=torch.float64, device=dev)
     if deps is None:
-        deps = torch.empty((S, n), dtype=torch.float64, device=B.device)
+        deps = torch.empty((S, n), dtype=torch.float64, device=dev)
     ctx.check(ctx.lib.rg_temperatures_adjoint_sets(
         ctx.handle, n, _dptr(F, torch.float64, "F", n * (n + 1), ctx.device), S,
         _dptr(B, torch.float64, "B", S * n * (n + 1), ctx.device), _dptr(eps, torch.float64, "eps", S * n, ctx.device),
         _dptr(rho, torch.float64, "rho", S * n, ctx.device), _dptr(area, torch.float64, "area", n, ctx.device),
         float(T_sink), float(sigma), _dptr(T, torch.float64, "T", S * n, ctx.device),
         _dptr(dT, torch.float64, "dT", S * n, ctx.device), _prec(precision), float(tol),
-        _dptr(dB, torch.float64, "dB", S * n * (n + 1), ctx.device),
+        nul if factored else _dptr(dB, torch.float64, "dB", S * n * (n + 1), ctx.device),
+        _dptr(dB_a, torch.float64, "dB_a", S * 2 * n, ctx.device) if factored else nul,
+        _dptr(dB_b, torch.float64, "dB_b", S * 2 * (n + 1), ctx.device) if factored else nul,
         _dptr(deps, torch.float64, "deps", S * n, ctx.device), _stream(stream)), "rg_temperatures_adjoint_sets")
-    return dB, deps
+    return ((dB_a, dB_b) if factored else dB), deps
+
+
+def gebhart_adjoint_factored(ctx: Context, F, eps, rho, B, a, b, precision="bf16", tol: float = 1e-12,
+                             max_sweeps: int = 12, stream=None, deps=None, drho=None):
+    """(dL/deps, dL/drho) [S, N] for dL/dB = sum_r a_r b_r^T, a [S, r, N], b [S, r, N+1]
+    (rg_gebhart_adjoint_factored)."""
+    n = F.shape[0]
+    S = eps.numel() // n
+    rank = a.shape[-2]
+    if deps is None:
+        deps = torch.empty((S, n), dtype=torch.float64, device=F.device)
+    if drho is None:
+        drho = torch.empty((S, n), dtype=torch.float64, device=F.device)
+    ctx.check(ctx.lib.rg_gebhart_adjoint_factored(
+        ctx.handle, n, _dptr(F, torch.float64, "F", n * (n + 1), ctx.device), S,
+        _dptr(eps, torch.float64, "eps", S * n, ctx.device), _dptr(rho, torch.float64, "rho", S * n, ctx.device),
+        _dptr(B, torch.float64, "B", S * n * (n + 1), ctx.device), int(rank),
+        _dptr(a, torch.float64, "a", S * rank * n, ctx.device),
+        _dptr(b, torch.float64, "b", S * rank * (n + 1), ctx.device), _prec(precision), float(tol), int(max_sweeps),
+        _dptr(deps, torch.float64, "deps", S * n, ctx.device), _dptr(drho, torch.float64, "drho", S * n, ctx.device),
+        _stream(stream)), "rg_gebhart_adjoint_factored")
+    return deps, drho
 
 
 def debug_wait_timeout(ctx: Context, kind: str, limit_s: float = 0.01, stream=None):

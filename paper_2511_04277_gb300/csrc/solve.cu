@@ -953,9 +953,12 @@ __global__ void balance_adj_rhs(const double* __restrict__ T, const double* __re
 
 // dB_ij = -nu_i (u_i - u_j) (u_{n} = T_sink^4), deps_i = -(nu_i / eps_i) sum_j B_ij (u_i - u_j)
 // with nu = g o mu the solution of the transposed balance. One warp per row.
+// dB may be null; with fa / fb set, dB = fa_0 fb_0^T + fa_1 fb_1^T is also written in that
+// factored form: fa_0 = -nu o u, fb_0 = 1; fa_1 = nu, fb_1 = (u, u_sink) (fa [2][n], fb [2][n+1]).
 __global__ void balance_adj_out(const double* __restrict__ B, const double* __restrict__ eps,
                                 const double* __restrict__ T, const double* __restrict__ nu, int64_t ldnu,
-                                double u_sink, int n, double* __restrict__ dB, double* __restrict__ deps) {
+                                double u_sink, int n, double* __restrict__ dB, double* __restrict__ deps,
+                                double* __restrict__ fa, double* __restrict__ fb) {
   const int i = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
   const int lane = threadIdx.x & 31;
   if (i >= n) return;
@@ -971,11 +974,54 @@ __global__ void balance_adj_out(const double* __restrict__ B, const double* __re
     } else {
       uj = u_sink;
     }
-    dB[(int64_t)i * (n + 1) + j] = -v * (ui - uj);
+    if (dB) dB[(int64_t)i * (n + 1) + j] = -v * (ui - uj);
     s += B[(int64_t)i * (n + 1) + j] * (ui - uj);
   }
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  if (lane == 0) deps[i] = -(v / eps[i]) * s;
+  if (lane == 0) {
+    deps[i] = -(v / eps[i]) * s;
+    if (fa) {
+      fa[i] = -v * ui;
+      fa[n + i] = v;
+      fb[i] = 1.0;
+      fb[(n + 1) + i] = ui;
+      if (i == 0) {
+        fb[n] = 1.0;
+        fb[(n + 1) + n] = u_sink;
+      }
+    }
+  }
+}
+
+// Factored REF adjoint outputs (rg_gebhart_adjoint_factored), one warp per row k:
+//   deps_k = sum_r b_r,k Q_kr,   drho_k = sum_r Q_kr (B b_r)_k,   Q = F^T X (ld = ldq).
+__global__ void factored_grads(const double* __restrict__ B, const double* __restrict__ Q, int64_t ldq,
+                               const double* __restrict__ b, int rank, int n, double* __restrict__ deps,
+                               double* __restrict__ drho) {
+  const int k = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+  const int lane = threadIdx.x & 31;
+  if (k >= n) return;
+  double de = 0.0, dr = 0.0;
+  for (int r = 0; r < rank; ++r) {
+    const double* br = b + (int64_t)r * (n + 1);
+    double bb = 0.0;
+    for (int j = lane; j <= n; j += 32) bb += B[(int64_t)k * (n + 1) + j] * br[j];
+    for (int o = 16; o > 0; o >>= 1) bb += __shfl_xor_sync(0xffffffffu, bb, o);
+    const double q = Q[(int64_t)k * ldq + r];
+    de += br[k] * q;
+    dr += q * bb;
+  }
+  if (lane == 0) {
+    deps[k] = de;
+    drho[k] = dr;
+  }
+}
+
+// R0[i][r] = a_r,i (the factored cotangent's left factors as right-hand sides).
+__global__ void factors_in(const double* __restrict__ a, int rank, int n, double* __restrict__ R0, int64_t ld) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  for (int r = 0; r < rank; ++r) R0[(int64_t)i * ld + r] = a[(int64_t)r * n + i];
 }
 
 
@@ -1346,7 +1392,8 @@ rg_status rg_temperatures_adjoint(rg_ctx* ctx, int32_t n, const double* B_d, con
   double rel = 0.0;
   st = sv.run(dl, nullptr, tol, 16, &sw, &rel);
   if (st == RG_OK) {
-    balance_adj_out<<<(n + 7) / 8, 256, 0, s>>>(B_d, eps_d, T_d, sv.b.X, sv.L.mp, u_sink, n, dB_d, deps_d);
+    balance_adj_out<<<(n + 7) / 8, 256, 0, s>>>(B_d, eps_d, T_d, sv.b.X, sv.L.mp, u_sink, n, dB_d, deps_d, nullptr,
+                                                 nullptr);
     ++ctx->launches;
     RG_CUDA_TRY(ctx, cudaGetLastError());
     st = sv.check_errors();
@@ -1360,13 +1407,13 @@ rg_status rg_temperatures_adjoint(rg_ctx* ctx, int32_t n, const double* B_d, con
 static rg_status temperatures_sets(rg_ctx* ctx, int32_t n, const double* F_d, int32_t n_sets, const double* B_d,
                                    const double* eps_d, const double* rho_d, const double* area_d, const double* Q_d,
                                    double T_sink, double sigma, int32_t precision, double tol, const double* T_in,
-                                   const double* dT_d, double* T_d, double* dB_d, double* deps_d, void* stream,
-                                   bool adjoint) {
+                                   const double* dT_d, double* T_d, double* dB_d, double* deps_d, double* fa_d,
+                                   double* fb_d, void* stream, bool adjoint) {
   const char* fn = adjoint ? "rg_temperatures_adjoint_sets" : "rg_temperatures_sets";
   rg_status st = check_common(ctx, n, precision, tol, 1);
   if (st != RG_OK) return st;
   RG_ARG_CHECK(ctx, F_d && B_d && eps_d && rho_d && area_d && n_sets > 0 && sigma > 0.0 && T_sink >= 0.0 &&
-                        (adjoint ? (T_in && dT_d && dB_d && deps_d) : (Q_d && T_d)),
+                        (adjoint ? (T_in && dT_d && (dB_d || (fa_d && fb_d)) && deps_d) : (Q_d && T_d)),
                "%s: bad argument", fn);
   RG_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
   cudaStream_t s = (cudaStream_t)stream;
@@ -1418,8 +1465,10 @@ static rg_status temperatures_sets(rg_ctx* ctx, int32_t n, const double* F_d, in
     st = sv.refine(dl, tol, 24, &sw, &rel);
     if (st != RG_OK) return st;
     if (adjoint) {
-      balance_adj_out<<<(n + 7) / 8, 256, 0, s>>>(B, eps, T_in + (size_t)set * n, sv.b.X, sv.L.mp, u_sink, n,
-                                                   dB_d + (size_t)set * n * (n + 1), deps_d + (size_t)set * n);
+      balance_adj_out<<<(n + 7) / 8, 256, 0, s>>>(
+          B, eps, T_in + (size_t)set * n, sv.b.X, sv.L.mp, u_sink, n, dB_d ? dB_d + (size_t)set * n * (n + 1) : nullptr,
+          deps_d + (size_t)set * n, fa_d ? fa_d + (size_t)set * 2 * n : nullptr,
+          fb_d ? fb_d + (size_t)set * 2 * (n + 1) : nullptr);
     } else {
       quartic_root<<<(n + 127) / 128, 128, 0, s>>>(sv.b.X, sv.L.mp, n, T_d + (size_t)set * n, sv.err);
     }
@@ -1434,17 +1483,52 @@ rg_status rg_temperatures_sets(rg_ctx* ctx, int32_t n, const double* F_d, int32_
                                double T_sink, double sigma, int32_t precision, double tol, double* T_d, void* stream) {
   if (!ctx) return RG_ERR_ARG;
   return temperatures_sets(ctx, n, F_d, n_sets, B_d, eps_d, rho_d, area_d, Q_d, T_sink, sigma, precision, tol,
-                           nullptr, nullptr, T_d, nullptr, nullptr, stream, false);
+                           nullptr, nullptr, T_d, nullptr, nullptr, nullptr, nullptr, stream, false);
 }
 
 rg_status rg_temperatures_adjoint_sets(rg_ctx* ctx, int32_t n, const double* F_d, int32_t n_sets,
                                        const double* B_d, const double* eps_d, const double* rho_d,
                                        const double* area_d, double T_sink, double sigma, const double* T_d,
                                        const double* dT_d, int32_t precision, double tol, double* dB_d,
-                                       double* deps_d, void* stream) {
+                                       double* dB_a_d, double* dB_b_d, double* deps_d, void* stream) {
   if (!ctx) return RG_ERR_ARG;
   return temperatures_sets(ctx, n, F_d, n_sets, B_d, eps_d, rho_d, area_d, nullptr, T_sink, sigma, precision, tol,
-                           T_d, dT_d, nullptr, dB_d, deps_d, stream, true);
+                           T_d, dT_d, nullptr, dB_d, deps_d, dB_a_d, dB_b_d, stream, true);
+}
+
+rg_status rg_gebhart_adjoint_factored(rg_ctx* ctx, int32_t n, const double* F_d, int32_t n_sets,
+                                      const double* eps_d, const double* rho_d, const double* B_d, int32_t rank,
+                                      const double* a_d, const double* b_d, int32_t precision, double tol,
+                                      int32_t max_sweeps, double* deps_d, double* drho_d, void* stream) {
+  if (!ctx) return RG_ERR_ARG;
+  rg_status st = check_common(ctx, n, precision, tol, max_sweeps);
+  if (st != RG_OK) return st;
+  RG_ARG_CHECK(ctx, F_d && eps_d && rho_d && B_d && a_d && b_d && deps_d && drho_d && n_sets > 0 && rank >= 1 &&
+                        rank <= 64,
+               "rg_gebhart_adjoint_factored: bad argument");
+  RG_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+  cudaStream_t s = (cudaStream_t)stream;
+  Solver sv{ctx};
+  // K^T X = A (rank right-hand sides), P' = F^T for every set, Q = F^T X accumulated
+  st = sv.setup(n, rank, precision == RG_PREC_BF16_IR, s, 0, nullptr, true);
+  if (st == RG_OK) st = sv.set_matrix(F_d, n + 1, true);
+  if (st != RG_OK) return st;
+  for (int set = 0; set < n_sets; ++set) {
+    const double* rho = rho_d + (size_t)set * n;
+    factors_in<<<(n + 255) / 256, 256, 0, s>>>(a_d + (size_t)set * rank * n, rank, n, sv.b.R0, sv.L.mp);
+    ++ctx->launches;
+    RG_CUDA_TRY(ctx, cudaGetLastError());
+    int sw = 0;
+    double rel = 0.0;
+    st = sv.run(rho, nullptr, tol, max_sweeps, &sw, &rel, set == 0);
+    if (st != RG_OK) return st;
+    factored_grads<<<(n + 7) / 8, 256, 0, s>>>(B_d + (size_t)set * n * (n + 1), sv.b.Q, sv.L.mp,
+                                                b_d + (size_t)set * rank * (n + 1), rank, n, deps_d + (size_t)set * n,
+                                                drho_d + (size_t)set * n);
+    ++ctx->launches;
+    RG_CUDA_TRY(ctx, cudaGetLastError());
+  }
+  return sv.check_errors();
 }
 
 }  // extern "C"

@@ -229,6 +229,39 @@ def test_temperature_sets_vs_oracle_and_per_set_calls(rg_ctx, prec):
         assert np.abs(T1.cpu().numpy() - T[s].cpu().numpy()).max() <= 1e-10 * To.max()
 
 
+def test_factored_thermal_adjoint_vs_full_and_oracle(rg_ctx):
+    """The calibration chain with the temperature cotangent in factored form: dL/dB of the
+    balance is -nu_i (u_i - u_j), rank 2, and rg_gebhart_adjoint_factored solves K^T for its
+    two left factors only. Against the full-dB chain (rg_temperatures_adjoint_sets ->
+    rg_gebhart_adjoint) and the oracle's fp64 gradients of L = sum w o T."""
+    rng = np.random.default_rng(44)
+    N, S = 300, 3
+    F, A = _consistent_F(N, rng)
+    eps = rng.uniform(0.05, 0.9, (S, N))
+    rho = 1 - eps
+    Q = rng.uniform(0, 50, (S, N))
+    wT = rng.standard_normal((S, N))
+    Fd, ed, rd, Ad = _dev(F), _dev(eps), _dev(rho), _dev(A)
+    B, _, _ = api.gebhart(rg_ctx, Fd, ed, rd, tol=1e-12)
+    T = api.temperatures_sets(rg_ctx, Fd, B, ed, rd, Ad, _dev(Q), 3.0, tol=1e-13)
+    (fa, fb), deps_T = api.temperatures_adjoint_sets(rg_ctx, Fd, B, ed, rd, Ad, 3.0, T, _dev(wT), tol=1e-13,
+                                                      factored=True)
+    dB, deps_T2 = api.temperatures_adjoint_sets(rg_ctx, Fd, B, ed, rd, Ad, 3.0, T, _dev(wT), tol=1e-13)
+    # the factors reproduce the full cotangent
+    full = torch.einsum("srn,srm->snm", fa, fb)
+    assert (full - dB).abs().max().item() <= 1e-14 * dB.abs().max().item()
+    assert torch.equal(deps_T, deps_T2)
+    de_f, dr_f = api.gebhart_adjoint_factored(rg_ctx, Fd, ed, rd, B, fa, fb, tol=1e-12)
+    de_full, dr_full = api.gebhart_adjoint(rg_ctx, Fd, ed, rd, B, dB, tol=1e-12)
+    assert (de_f - de_full).abs().max().item() <= 1e-9 * de_full.abs().max().item()
+    assert (dr_f - dr_full).abs().max().item() <= 1e-9 * dr_full.abs().max().item()
+    for s in range(S):
+        geo, gro = G.thermal_gradients(F, eps[s], rho[s], A, Q[s], 3.0, wT[s])
+        g = (de_f[s] + deps_T[s]).cpu().numpy()
+        assert np.abs(g - geo).max() <= 1e-8 * np.abs(geo).max()
+        assert np.abs(dr_f[s].cpu().numpy() - gro).max() <= 1e-8 * np.abs(gro).max()
+
+
 def test_temperature_sets_small_sat(rg_ctx):
     """The 2,048-face small satellite, two sets: the batched balance against the oracle."""
     w = synth.workload("small_sat", rays_scale=0.02)
