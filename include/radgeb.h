@@ -15,7 +15,12 @@
  *   on that context (never NULL).
  * - Ownership: the caller owns every buffer it passes (host or device, as each
  *   argument says). The library owns only the opaque rg_ctx and rg_mesh objects
- *   and the device workspace held by a context.
+ *   and the device workspace held by a context. Every dense-solve call (REFs,
+ *   balances, adjoints, least-squares enforcement) also takes an optional
+ *   caller-owned workspace (workspace_d, workspace_bytes): device memory, 256-byte
+ *   aligned, at least the size rg_solver_workspace / rg_gebhart_workspace report, used
+ *   for the call's duration only; with workspace_d = NULL the call uses (and grows on
+ *   demand) the context's workspace. A workspace smaller than needed is RG_ERR_ARG.
  * - Layout: matrices are dense, row-major, fp64 unless stated. A view-factor or
  *   REF matrix of N faces is N x (N+1): column N is the environment (deep space),
  *   Sec. 2.4.12. Batched data of S sets is set-major ([S][...]).
@@ -72,6 +77,29 @@ const char* rg_last_error(const rg_ctx* ctx);
 const char* rg_version(void);
 /* Number of kernels this context has launched so far (host counter, for accounting). */
 rg_status rg_launch_count(const rg_ctx* ctx, int64_t* launches_out_h);
+/* Bytes of device workspace the context holds (grown on demand by calls made without a
+ * caller-owned workspace; never shrunk before rg_destroy). */
+rg_status rg_workspace_bytes(const rg_ctx* ctx, size_t* bytes_out);
+
+/* Device workspace a dense-solve call needs when the caller provides it (no device, no
+ * context: sizes only). kind: which call; n the number of faces; rank the number of
+ * cotangent factors for RG_WS_GEBHART_ADJOINT_FACTORED (ignored otherwise). The sets of a
+ * batched call are solved one after another in the same workspace, so the size does not
+ * depend on n_sets. Errors: RG_ERR_ARG (unknown kind, n outside the call's limits). */
+typedef enum {
+  RG_WS_GEBHART = 1,                  /* rg_gebhart */
+  RG_WS_GEBHART_ADJOINT = 2,          /* rg_gebhart_adjoint */
+  RG_WS_GEBHART_ADJOINT_FACTORED = 3, /* rg_gebhart_adjoint_factored */
+  RG_WS_TEMPERATURES = 4,             /* rg_temperatures, rg_temperatures_adjoint */
+  RG_WS_TEMPERATURES_SETS = 5,        /* rg_temperatures_sets, rg_temperatures_adjoint_sets */
+  RG_WS_ENFORCE_LSQ = 6               /* rg_enforce_lsq */
+} rg_solver_kind;
+rg_status rg_solver_workspace(int32_t kind, int32_t n, int32_t rank, size_t* bytes_out);
+/* The REF solve's workspace (App. B, Eq. B.8-B.11) for n faces and n_sets sets in
+ * `precision`: rg_solver_workspace(RG_WS_GEBHART, n, 0, ...). keep_factors must be 0: no
+ * factors are kept between calls (the adjoint factorises K^T afresh);
+ * keep_factors != 0 is RG_ERR_UNSUPPORTED. */
+rg_status rg_gebhart_workspace(int32_t n, int32_t n_sets, int32_t precision, int32_t keep_factors, size_t* bytes_out);
 
 /* Kernel timer, for measurement (no counterpart in the thesis). While it is on, the
  * context records a CUDA event pair on the launching stream around every launch of
@@ -319,7 +347,8 @@ rg_status rg_enforce_iterative_noalloc(int32_t n, const double* omega_d, double*
  * Limit: n <= 4096 (one dense n x n Schur complement is factorised).
  * Errors: RG_ERR_NUMERIC (singular restriction system), RG_ERR_NOT_CONVERGED. */
 rg_status rg_enforce_lsq(rg_ctx* ctx, int32_t n, const double* omega_d, double* F_d, int32_t nnr,
-                         int32_t spva, int32_t max_passes, int32_t* passes_out_h, void* stream);
+                         int32_t spva, int32_t max_passes, int32_t* passes_out_h, void* workspace_d,
+                         size_t workspace_bytes, void* stream);
 
 /* ---------------------------------------------------------------- multi-node (P4) */
 
@@ -401,7 +430,8 @@ rg_status rg_node_couplings(rg_ctx* ctx, int32_t n, const double* B2_d, const do
  * Limit: n <= 32768. Errors: RG_ERR_NOT_CONVERGED, RG_ERR_NUMERIC, RG_ERR_OOM. */
 rg_status rg_gebhart(rg_ctx* ctx, int32_t n, const double* F_d, int32_t n_sets, const double* eps_d,
                      const double* rho_d, int32_t precision, double tol, int32_t max_sweeps,
-                     double* B_d, int32_t* sweeps_out_h, double* resid_out_h, void* stream);
+                     double* B_d, int32_t* sweeps_out_h, double* resid_out_h, void* workspace_d,
+                     size_t workspace_bytes, void* stream);
 
 /* Adjoint of rg_gebhart: given dB = dL/dB, the gradients of L with respect to eps
  * and rho. It solves K^T Lambda = dB (a fresh factorisation of K^T, no stored
@@ -412,7 +442,8 @@ rg_status rg_gebhart(rg_ctx* ctx, int32_t n, const double* F_d, int32_t n_sets, 
 rg_status rg_gebhart_adjoint(rg_ctx* ctx, int32_t n, const double* F_d, int32_t n_sets,
                              const double* eps_d, const double* rho_d, const double* B_d,
                              const double* dB_d, int32_t precision, double tol, int32_t max_sweeps,
-                             double* deps_d, double* drho_d, void* stream);
+                             double* deps_d, double* drho_d, void* workspace_d, size_t workspace_bytes,
+                             void* stream);
 
 /* ---------------------------------------------------------------- radiative balance (P6) */
 
@@ -427,7 +458,8 @@ rg_status rg_gebhart_adjoint(rg_ctx* ctx, int32_t n, const double* F_d, int32_t 
  * RG_ERR_NOT_CONVERGED. */
 rg_status rg_temperatures(rg_ctx* ctx, int32_t n, const double* B_d, const double* eps_d,
                           const double* area_d, const double* Q_d, double T_sink, double sigma,
-                          int32_t precision, double tol, double* T_d, void* stream);
+                          int32_t precision, double tol, double* T_d, void* workspace_d, size_t workspace_bytes,
+                          void* stream);
 
 /* Adjoint of rg_temperatures: given dT = dL/dT, writes dB = dL/dB (device fp64
  * [n][n+1]) and the direct part of dL/deps (device fp64 [n]); the part through B
@@ -436,7 +468,8 @@ rg_status rg_temperatures(rg_ctx* ctx, int32_t n, const double* B_d, const doubl
 rg_status rg_temperatures_adjoint(rg_ctx* ctx, int32_t n, const double* B_d, const double* eps_d,
                                   const double* area_d, double T_sink, double sigma,
                                   const double* T_d, const double* dT_d, int32_t precision, double tol,
-                                  double* dB_d, double* deps_d, void* stream);
+                                  double* dB_d, double* deps_d, void* workspace_d, size_t workspace_bytes,
+                                  void* stream);
 
 /* rg_temperatures and rg_temperatures_adjoint for n_sets (eps, rho) sets sharing F, in one
  * call: the same equations and results (each set's balance is refined to tol against its own
@@ -457,12 +490,14 @@ rg_status rg_temperatures_adjoint(rg_ctx* ctx, int32_t n, const double* B_d, con
  * Errors as rg_temperatures / rg_temperatures_adjoint. */
 rg_status rg_temperatures_sets(rg_ctx* ctx, int32_t n, const double* F_d, int32_t n_sets, const double* B_d,
                                const double* eps_d, const double* rho_d, const double* area_d, const double* Q_d,
-                               double T_sink, double sigma, int32_t precision, double tol, double* T_d, void* stream);
+                               double T_sink, double sigma, int32_t precision, double tol, double* T_d,
+                               void* workspace_d, size_t workspace_bytes, void* stream);
 rg_status rg_temperatures_adjoint_sets(rg_ctx* ctx, int32_t n, const double* F_d, int32_t n_sets,
                                        const double* B_d, const double* eps_d, const double* rho_d,
                                        const double* area_d, double T_sink, double sigma, const double* T_d,
                                        const double* dT_d, int32_t precision, double tol, double* dB_d,
-                                       double* dB_a_d, double* dB_b_d, double* deps_d, void* stream);
+                                       double* dB_a_d, double* dB_b_d, double* deps_d, void* workspace_d,
+                                       size_t workspace_bytes, void* stream);
 
 /* rg_gebhart_adjoint for a cotangent given in factored form, dB = sum_r a_r b_r^T (for
  * instance the one rg_temperatures_adjoint_sets writes: rank 2). Lambda = K^-T dB =
@@ -475,7 +510,8 @@ rg_status rg_temperatures_adjoint_sets(rg_ctx* ctx, int32_t n, const double* F_d
 rg_status rg_gebhart_adjoint_factored(rg_ctx* ctx, int32_t n, const double* F_d, int32_t n_sets,
                                       const double* eps_d, const double* rho_d, const double* B_d, int32_t rank,
                                       const double* a_d, const double* b_d, int32_t precision, double tol,
-                                      int32_t max_sweeps, double* deps_d, double* drho_d, void* stream);
+                                      int32_t max_sweeps, double* deps_d, double* drho_d, void* workspace_d,
+                                      size_t workspace_bytes, void* stream);
 
 /* ---------------------------------------------------------------- tensor-core GEMM */
 

@@ -13,12 +13,15 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libradgeb.so")
 
 P = ctypes.c_void_p
 i32, i64, u64, f64 = ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64, ctypes.c_double
+sz = ctypes.c_size_t
 PP = ctypes.POINTER(ctypes.c_void_p)
 
 RG_OK = 0
 STATUS = {0: "RG_OK", -1: "RG_ERR_ARG", -2: "RG_ERR_CUDA", -3: "RG_ERR_OOM", -4: "RG_ERR_NOT_CONVERGED",
           -5: "RG_ERR_STACK", -6: "RG_ERR_NUMERIC", -7: "RG_ERR_UNSUPPORTED"}
 PREC = {"bf16": 1, "fp16": 2}
+WS_KIND = {"gebhart": 1, "gebhart_adjoint": 2, "gebhart_adjoint_factored": 3, "temperatures": 4,
+           "temperatures_sets": 5, "enforce_lsq": 6}
 KAPPA = {"triangulation": 1, "fractional_variance": 2}
 
 
@@ -34,6 +37,9 @@ SIGNATURES = {
     "rg_last_error": (ctypes.c_char_p, [P]),
     "rg_version": (ctypes.c_char_p, []),
     "rg_launch_count": (i32, [P, ctypes.POINTER(i64)]),
+    "rg_workspace_bytes": (i32, [P, ctypes.POINTER(sz)]),
+    "rg_solver_workspace": (i32, [i32, i32, i32, ctypes.POINTER(sz)]),
+    "rg_gebhart_workspace": (i32, [i32, i32, i32, i32, ctypes.POINTER(sz)]),
     "rg_kernel_timer": (i32, [P, i32]),
     "rg_kernel_timer_read": (i32, [P, i32, ctypes.POINTER(i64), ctypes.POINTER(f64), ctypes.POINTER(f64),
                                     ctypes.POINTER(f64)]),
@@ -54,17 +60,17 @@ SIGNATURES = {
     "rg_trace_reflect": (i32, [P, P, P, P, P, i32, u64, u64, i32, P, P, P]),
     "rg_debug_mbarrier_timeout": (i32, [P, f64, P]),
     "rg_debug_barrier_timeout": (i32, [P, f64, P]),
-    "rg_enforce_lsq": (i32, [P, i32, P, P, i32, i32, i32, P, P]),
+    "rg_enforce_lsq": (i32, [P, i32, P, P, i32, i32, i32, P, P, sz, P]),
     "rg_aggregate": (i32, [P, i32, P, P, P, i32, P, P, P]),
     "rg_node_view_factors": (i32, [P, i32, P, P, P, P, P]),
     "rg_node_couplings": (i32, [P, i32, P, P, P, P, P, P, P, P]),
-    "rg_gebhart": (i32, [P, i32, P, i32, P, P, i32, f64, i32, P, P, P, P]),
-    "rg_gebhart_adjoint": (i32, [P, i32, P, i32, P, P, P, P, i32, f64, i32, P, P, P]),
-    "rg_temperatures": (i32, [P, i32, P, P, P, P, f64, f64, i32, f64, P, P]),
-    "rg_temperatures_adjoint": (i32, [P, i32, P, P, P, f64, f64, P, P, i32, f64, P, P, P]),
-    "rg_temperatures_sets": (i32, [P, i32, P, i32, P, P, P, P, P, f64, f64, i32, f64, P, P]),
-    "rg_temperatures_adjoint_sets": (i32, [P, i32, P, i32, P, P, P, P, f64, f64, P, P, i32, f64, P, P, P, P, P]),
-    "rg_gebhart_adjoint_factored": (i32, [P, i32, P, i32, P, P, P, i32, P, P, i32, f64, i32, P, P, P]),
+    "rg_gebhart": (i32, [P, i32, P, i32, P, P, i32, f64, i32, P, P, P, P, sz, P]),
+    "rg_gebhart_adjoint": (i32, [P, i32, P, i32, P, P, P, P, i32, f64, i32, P, P, P, sz, P]),
+    "rg_temperatures": (i32, [P, i32, P, P, P, P, f64, f64, i32, f64, P, P, sz, P]),
+    "rg_temperatures_adjoint": (i32, [P, i32, P, P, P, f64, f64, P, P, i32, f64, P, P, P, sz, P]),
+    "rg_temperatures_sets": (i32, [P, i32, P, i32, P, P, P, P, P, f64, f64, i32, f64, P, P, sz, P]),
+    "rg_temperatures_adjoint_sets": (i32, [P, i32, P, i32, P, P, P, P, f64, f64, P, P, i32, f64, P, P, P, P, P, sz, P]),
+    "rg_gebhart_adjoint_factored": (i32, [P, i32, P, i32, P, P, P, i32, P, P, i32, f64, i32, P, P, P, sz, P]),
     "rg_tc_gemm": (i32, [P, i32, i32, i32, P, i64, P, i64, i32, P, i64, ctypes.c_float, ctypes.c_float, P]),
     "rg_exact_split": (i32, [P, i32, P, i64, i32, P, P, P, P]),
     "rg_tc_gemm_exact": (i32, [P, i32, i32, i32, i32, P, i64, P, P, P]),

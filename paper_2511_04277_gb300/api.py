@@ -40,6 +40,17 @@ def _hptr(a: np.ndarray):
     return a.ctypes.data_as(ctypes.c_void_p)
 
 
+def _ws(ws, device=None):
+    """(pointer, bytes) of an optional caller-owned workspace (a CUDA tensor), or (NULL, 0)."""
+    if ws is None:
+        return ctypes.c_void_p(None), ctypes.c_size_t(0)
+    if not isinstance(ws, torch.Tensor) or not ws.is_cuda or not ws.is_contiguous():
+        raise TypeError("ws must be a contiguous CUDA tensor")
+    if device is not None and ws.device.index != device:
+        raise ValueError(f"ws is on cuda:{ws.device.index}, the context on cuda:{device}")
+    return ctypes.c_void_p(ws.data_ptr()), ctypes.c_size_t(ws.numel() * ws.element_size())
+
+
 class Context:
     """A library context bound to one CUDA device (rg_create / rg_destroy)."""
 
@@ -212,6 +223,34 @@ def launch_count(ctx: Context) -> int:
 KERNEL_CLASSES = {"trace": 0, "residual_gemm": 1, "gemm": 2, "enforce": 3}
 
 
+def workspace_bytes(ctx: Context) -> int:
+    """Device workspace the context holds (rg_workspace_bytes)."""
+    n = ctypes.c_size_t(0)
+    ctx.check(ctx.lib.rg_workspace_bytes(ctx.handle, ctypes.byref(n)), "rg_workspace_bytes")
+    return n.value
+
+
+def solver_workspace(kind: str, n: int, rank: int = 0) -> int:
+    """Bytes of caller-owned workspace a dense-solve call of n faces needs (rg_solver_workspace);
+    kind one of gebhart, gebhart_adjoint, gebhart_adjoint_factored, temperatures,
+    temperatures_sets, enforce_lsq."""
+    out = ctypes.c_size_t(0)
+    st = _native.load().rg_solver_workspace(_native.WS_KIND[kind], int(n), int(rank), ctypes.byref(out))
+    if st != 0:
+        raise RadgebError(st, f"rg_solver_workspace({kind}, {n}, {rank})")
+    return out.value
+
+
+def gebhart_workspace(n: int, n_sets: int = 1, precision="bf16", keep_factors: bool = False) -> int:
+    """Bytes of caller-owned workspace rg_gebhart needs (rg_gebhart_workspace)."""
+    out = ctypes.c_size_t(0)
+    st = _native.load().rg_gebhart_workspace(int(n), int(n_sets), _prec(precision), int(bool(keep_factors)),
+                                             ctypes.byref(out))
+    if st != 0:
+        raise RadgebError(st, f"rg_gebhart_workspace({n}, {n_sets})")
+    return out.value
+
+
 def kernel_timer(ctx: Context, enable: bool):
     """Start (clearing earlier records) or stop the context's kernel timer (rg_kernel_timer)."""
     ctx.check(ctx.lib.rg_kernel_timer(ctx.handle, int(bool(enable))), "rg_kernel_timer")
@@ -285,13 +324,13 @@ def enforce_iterative_kappa(ctx: Context, F: torch.Tensor, omega: torch.Tensor, 
 
 
 def enforce_lsq(ctx: Context, F: torch.Tensor, omega: torch.Tensor, nnr: bool = True, spva: bool = True,
-                max_passes: int = 1000, stream=None) -> int:
+                max_passes: int = 1000, stream=None, ws=None) -> int:
     """In-place least-squares optimum with NNR / SPVA (rg_enforce_lsq); returns projections."""
     n = F.shape[0]
     p = ctypes.c_int32(0)
     ctx.check(ctx.lib.rg_enforce_lsq(ctx.handle, n, _dptr(omega, torch.float64, "omega", n, ctx.device),
                                      _dptr(F, torch.float64, "F", n * (n + 1), ctx.device), int(bool(nnr)),
-                                     int(bool(spva)), int(max_passes), ctypes.byref(p), _stream(stream)),
+                                     int(bool(spva)), int(max_passes), ctypes.byref(p), *_ws(ws, ctx.device), _stream(stream)),
               "rg_enforce_lsq")
     return p.value
 
@@ -365,7 +404,7 @@ def _prec(p):
 
 
 def gebhart(ctx: Context, F: torch.Tensor, eps: torch.Tensor, rho: torch.Tensor, precision="bf16",
-            tol: float = 1e-12, max_sweeps: int = 12, B: torch.Tensor | None = None, stream=None):
+            tol: float = 1e-12, max_sweeps: int = 12, B: torch.Tensor | None = None, stream=None, ws=None):
     """REFs of every (eps, rho) set (rg_gebhart) -> (B [S, N, N+1], sweeps, relative residual)."""
     n = F.shape[0]
     eps2 = eps.reshape(-1, n)
@@ -378,12 +417,12 @@ def gebhart(ctx: Context, F: torch.Tensor, eps: torch.Tensor, rho: torch.Tensor,
                                  _dptr(eps2, torch.float64, "eps", S * n, ctx.device),
                                  _dptr(rho, torch.float64, "rho", S * n, ctx.device), _prec(precision), float(tol),
                                  int(max_sweeps), _dptr(B, torch.float64, "B", S * n * (n + 1), ctx.device),
-                                 ctypes.byref(sw), ctypes.byref(res), _stream(stream)), "rg_gebhart")
+                                 ctypes.byref(sw), ctypes.byref(res), *_ws(ws, ctx.device), _stream(stream)), "rg_gebhart")
     return B, sw.value, res.value
 
 
 def gebhart_adjoint(ctx: Context, F, eps, rho, B, dB, precision="bf16", tol: float = 1e-12, max_sweeps: int = 12,
-                    stream=None):
+                    stream=None, ws=None):
     """(dL/deps, dL/drho) [S, N] from dB = dL/dB (rg_gebhart_adjoint)."""
     n = F.shape[0]
     S = eps.numel() // n
@@ -396,12 +435,12 @@ def gebhart_adjoint(ctx: Context, F, eps, rho, B, dB, precision="bf16", tol: flo
                                          _dptr(dB, torch.float64, "dB", S * n * (n + 1), ctx.device),
                                          _prec(precision), float(tol), int(max_sweeps),
                                          _dptr(deps, torch.float64, "deps"), _dptr(drho, torch.float64, "drho"),
-                                         _stream(stream)), "rg_gebhart_adjoint")
+                                         *_ws(ws, ctx.device), _stream(stream)), "rg_gebhart_adjoint")
     return deps, drho
 
 
 def temperatures(ctx: Context, B, eps, area, Q, T_sink: float, sigma: float = 5.67e-8, precision="bf16",
-                 tol: float = 1e-13, stream=None, T=None) -> torch.Tensor:
+                 tol: float = 1e-13, stream=None, ws=None, T=None) -> torch.Tensor:
     """Steady node temperatures (rg_temperatures); T (optional) receives them."""
     n = B.shape[-2]
     if T is None:
@@ -410,13 +449,13 @@ def temperatures(ctx: Context, B, eps, area, Q, T_sink: float, sigma: float = 5.
                                       _dptr(eps, torch.float64, "eps", n, ctx.device),
                                       _dptr(area, torch.float64, "area", n, ctx.device),
                                       _dptr(Q, torch.float64, "Q", n, ctx.device), float(T_sink), float(sigma),
-                                      _prec(precision), float(tol), _dptr(T, torch.float64, "T", n, ctx.device), _stream(stream)),
+                                      _prec(precision), float(tol), _dptr(T, torch.float64, "T", n, ctx.device), *_ws(ws, ctx.device), _stream(stream)),
               "rg_temperatures")
     return T
 
 
 def temperatures_adjoint(ctx: Context, B, eps, area, T_sink: float, T, dT, sigma: float = 5.67e-8,
-                         precision="bf16", tol: float = 1e-13, stream=None, dB=None, deps=None):
+                         precision="bf16", tol: float = 1e-13, stream=None, ws=None, dB=None, deps=None):
     """(dL/dB [N, N+1], direct dL/deps [N]) from dT = dL/dT (rg_temperatures_adjoint);
     dB and deps (optional) receive them."""
     n = B.shape[-2]
@@ -430,13 +469,13 @@ def temperatures_adjoint(ctx: Context, B, eps, area, T_sink: float, T, dT, sigma
                                               float(sigma), _dptr(T, torch.float64, "T", n, ctx.device),
                                               _dptr(dT, torch.float64, "dT", n, ctx.device), _prec(precision),
                                               float(tol), _dptr(dB, torch.float64, "dB", n * (n + 1), ctx.device),
-                                              _dptr(deps, torch.float64, "deps", n, ctx.device), _stream(stream)),
+                                              _dptr(deps, torch.float64, "deps", n, ctx.device), *_ws(ws, ctx.device), _stream(stream)),
               "rg_temperatures_adjoint")
     return dB, deps
 
 
 def temperatures_sets(ctx: Context, F, B, eps, rho, area, Q, T_sink: float, sigma: float = 5.67e-8,
-                      precision="bf16", tol: float = 1e-13, stream=None, T=None) -> torch.Tensor:
+                      precision="bf16", tol: float = 1e-13, stream=None, ws=None, T=None) -> torch.Tensor:
     """Steady temperatures of every (eps, rho) set [S, N] (rg_temperatures_sets; F and rho
     precondition the refinement)."""
     n = F.shape[0]
@@ -450,13 +489,13 @@ def temperatures_sets(ctx: Context, F, B, eps, rho, area, Q, T_sink: float, sigm
                                            _dptr(area, torch.float64, "area", n, ctx.device),
                                            _dptr(Q, torch.float64, "Q", S * n, ctx.device), float(T_sink),
                                            float(sigma), _prec(precision), float(tol),
-                                           _dptr(T, torch.float64, "T", S * n, ctx.device), _stream(stream)),
+                                           _dptr(T, torch.float64, "T", S * n, ctx.device), *_ws(ws, ctx.device), _stream(stream)),
               "rg_temperatures_sets")
     return T
 
 
 def temperatures_adjoint_sets(ctx: Context, F, B, eps, rho, area, T_sink: float, T, dT, sigma: float = 5.67e-8,
-                              precision="bf16", tol: float = 1e-13, stream=None, dB=None, deps=None,
+                              precision="bf16", tol: float = 1e-13, stream=None, ws=None, dB=None, deps=None,
                               factored: bool = False, dB_a=None, dB_b=None):
     """Direct dL/deps [S, N] and dL/dB of every set (rg_temperatures_adjoint_sets): dL/dB in
     full [S, N, N+1], or with factored=True as (a [S, 2, N], b [S, 2, N+1]) with
@@ -481,12 +520,12 @@ def temperatures_adjoint_sets(ctx: Context, F, B, eps, rho, area, T_sink: float,
         nul if factored else _dptr(dB, torch.float64, "dB", S * n * (n + 1), ctx.device),
         _dptr(dB_a, torch.float64, "dB_a", S * 2 * n, ctx.device) if factored else nul,
         _dptr(dB_b, torch.float64, "dB_b", S * 2 * (n + 1), ctx.device) if factored else nul,
-        _dptr(deps, torch.float64, "deps", S * n, ctx.device), _stream(stream)), "rg_temperatures_adjoint_sets")
+        _dptr(deps, torch.float64, "deps", S * n, ctx.device), *_ws(ws, ctx.device), _stream(stream)), "rg_temperatures_adjoint_sets")
     return ((dB_a, dB_b) if factored else dB), deps
 
 
 def gebhart_adjoint_factored(ctx: Context, F, eps, rho, B, a, b, precision="bf16", tol: float = 1e-12,
-                             max_sweeps: int = 12, stream=None, deps=None, drho=None):
+                             max_sweeps: int = 12, stream=None, ws=None, deps=None, drho=None):
     """(dL/deps, dL/drho) [S, N] for dL/dB = sum_r a_r b_r^T, a [S, r, N], b [S, r, N+1]
     (rg_gebhart_adjoint_factored)."""
     n = F.shape[0]
@@ -503,7 +542,7 @@ def gebhart_adjoint_factored(ctx: Context, F, eps, rho, B, a, b, precision="bf16
         _dptr(a, torch.float64, "a", S * rank * n, ctx.device),
         _dptr(b, torch.float64, "b", S * rank * (n + 1), ctx.device), _prec(precision), float(tol), int(max_sweeps),
         _dptr(deps, torch.float64, "deps", S * n, ctx.device), _dptr(drho, torch.float64, "drho", S * n, ctx.device),
-        _stream(stream)), "rg_gebhart_adjoint_factored")
+        *_ws(ws, ctx.device), _stream(stream)), "rg_gebhart_adjoint_factored")
     return deps, drho
 
 

@@ -56,6 +56,9 @@ rg_status cuda_fail(rg_ctx* ctx, cudaError_t e, const char* what);
 
 // Device workspace of at least `bytes` (256-byte aligned), owned by ctx.
 rg_status workspace(rg_ctx* ctx, size_t bytes, void** out);
+// The caller's workspace (user, user_bytes) when user is not null -- 256-byte aligned and at
+// least `bytes` long, else RG_ERR_ARG naming `fn` and the size needed -- or the context's.
+rg_status workspace_or(rg_ctx* ctx, void* user, size_t user_bytes, size_t bytes, void** out, const char* fn);
 
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 

@@ -67,9 +67,26 @@ void timer_end(rg_ctx* ctx, int token, cudaStream_t s) {
   if (cudaEventRecord(ctx->timer_events[ctx->timed[token].b], s) != cudaSuccess) ctx->timed[token].b = -1;
 }
 
+rg_status workspace_or(rg_ctx* ctx, void* user, size_t user_bytes, size_t bytes, void** out, const char* fn) {
+  if (!user) return workspace(ctx, bytes, out);
+  if (reinterpret_cast<uintptr_t>(user) & 255)
+    return fail(ctx, RG_ERR_ARG, "%s: the caller's workspace must be 256-byte aligned", fn);
+  if (user_bytes < bytes)
+    return fail(ctx, RG_ERR_ARG, "%s: the caller's workspace holds %zu bytes, the call needs %zu", fn, user_bytes,
+                bytes);
+  *out = user;
+  return RG_OK;
+}
+
 }  // namespace rg
 
 extern "C" {
+
+rg_status rg_workspace_bytes(const rg_ctx* ctx, size_t* bytes_out) {
+  if (!ctx || !bytes_out) return RG_ERR_ARG;
+  *bytes_out = ctx->ws_bytes;
+  return RG_OK;
+}
 
 rg_status rg_kernel_timer(rg_ctx* ctx, int32_t enable) {
   if (!ctx) return RG_ERR_ARG;

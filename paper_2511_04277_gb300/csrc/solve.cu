@@ -605,10 +605,19 @@ struct Solver {
 
   unsigned long long* red(int parity) { return reinterpret_cast<unsigned long long*>(err + 10 + 6 * parity); }
 
-  // Carves the solver's buffers out of the context workspace, after `extra_bytes`
-  // reserved for the caller (returned in *extra).
+  // Workspace bytes of a solver of n unknowns and m right-hand sides after `extra_bytes`
+  // reserved for the calling entry point (the sizes every call and the size queries use).
+  static size_t bytes(int n, int m, bool want_q, size_t extra_bytes) {
+    Layout L{n, m, (n + NB - 1) / NB * NB, (m + NB - 1) / NB * NB, want_q};
+    rg::Sizer sz;
+    plan(L, sz);
+    return rg::align_up(extra_bytes, 256) + sz.off;
+  }
+
+  // Carves the solver's buffers out of the caller's workspace (user, user_bytes) or the
+  // context's, after `extra_bytes` reserved for the calling entry point (returned in *extra).
   rg_status setup(int n, int m, bool use_bf16, cudaStream_t stream, size_t extra_bytes = 0, void** extra = nullptr,
-                  bool want_q = false) {
+                  bool want_q = false, void* user = nullptr, size_t user_bytes = 0, const char* fn = "solver") {
     L.n = n;
     L.m = m;
     L.np = (n + NB - 1) / NB * NB;
@@ -617,10 +626,8 @@ struct Solver {
     bf16 = use_bf16;
     s = stream;
     extra_bytes = rg::align_up(extra_bytes, 256);
-    rg::Sizer sz;
-    plan(L, sz);
     void* ws = nullptr;
-    rg_status st = rg::workspace(ctx, extra_bytes + sz.off, &ws);
+    rg_status st = rg::workspace_or(ctx, user, user_bytes, bytes(n, m, want_q, extra_bytes), &ws, fn);
     if (st != RG_OK) return st;
     if (extra) *extra = ws;
     rg::Carver cv(static_cast<char*>(ws) + extra_bytes);
@@ -1149,16 +1156,8 @@ rg_status check_common(rg_ctx* ctx, int32_t n, int32_t precision, double tol, in
   return RG_OK;
 }
 
-}  // namespace
-
-extern "C" {
-
-rg_status rg_enforce_lsq(rg_ctx* ctx, int32_t n, const double* omega_d, double* F_d, int32_t nnr, int32_t spva,
-                         int32_t max_passes, int32_t* passes_out_h, void* stream) {
-  if (!ctx) return RG_ERR_ARG;
-  RG_ARG_CHECK(ctx, n > 0 && n <= 4096 && omega_d && F_d && max_passes >= 1, "rg_enforce_lsq: bad argument");
-  RG_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
-  cudaStream_t s = (cudaStream_t)stream;
+// Bytes rg_enforce_lsq reserves ahead of its solver.
+size_t lsq_extra_bytes(int n) {
   const size_t nn1 = (size_t)n * (n + 1);
   rg::Sizer ex;
   ex.take<double>(nn1);            // F0
@@ -1167,9 +1166,32 @@ rg_status rg_enforce_lsq(rg_ctx* ctx, int32_t n, const double* omega_d, double* 
   ex.take<double>((size_t)n * n);  // P
   ex.take<double>(n);              // dl
   ex.take<int>(4);                 // negative counter
+  return ex.off;
+}
+
+// Bytes rg_temperatures_sets reserves ahead of its solver (the preconditioner's vectors).
+size_t balance_sets_extra_bytes(int n) {
+  rg::Sizer ex;
+  ex.take<double>((size_t)2 * ((n + NB - 1) / NB * NB));
+  return ex.off;
+}
+
+}  // namespace
+
+extern "C" {
+
+rg_status rg_enforce_lsq(rg_ctx* ctx, int32_t n, const double* omega_d, double* F_d, int32_t nnr, int32_t spva,
+                         int32_t max_passes, int32_t* passes_out_h, void* workspace_d, size_t workspace_bytes,
+                         void* stream) {
+  if (!ctx) return RG_ERR_ARG;
+  RG_ARG_CHECK(ctx, n > 0 && n <= 4096 && omega_d && F_d && max_passes >= 1, "rg_enforce_lsq: bad argument");
+  RG_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t nn1 = (size_t)n * (n + 1);
   Solver sv{ctx};
   void* extra = nullptr;
-  rg_status st = sv.setup(n, 1, false, s, ex.off, &extra);
+  rg_status st = sv.setup(n, 1, false, s, lsq_extra_bytes(n), &extra, false, workspace_d, workspace_bytes,
+                          "rg_enforce_lsq");
   if (st != RG_OK) return st;
   rg::Carver cv(extra);
   double* F0 = cv.take<double>(nn1);
@@ -1250,7 +1272,8 @@ rg_status rg_exact_split(rg_ctx* ctx, int32_t n, const double* P_d, int64_t ldp,
 
 rg_status rg_gebhart(rg_ctx* ctx, int32_t n, const double* F_d, int32_t n_sets, const double* eps_d,
                      const double* rho_d, int32_t precision, double tol, int32_t max_sweeps, double* B_d,
-                     int32_t* sweeps_out_h, double* resid_out_h, void* stream) {
+                     int32_t* sweeps_out_h, double* resid_out_h, void* workspace_d, size_t workspace_bytes,
+                     void* stream) {
   if (!ctx) return RG_ERR_ARG;
   rg_status st = check_common(ctx, n, precision, tol, max_sweeps);
   if (st != RG_OK) return st;
@@ -1258,7 +1281,8 @@ rg_status rg_gebhart(rg_ctx* ctx, int32_t n, const double* F_d, int32_t n_sets, 
   RG_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
   cudaStream_t s = (cudaStream_t)stream;
   Solver sv{ctx};
-  st = sv.setup(n, n + 1, precision == RG_PREC_BF16_IR, s);
+  st = sv.setup(n, n + 1, precision == RG_PREC_BF16_IR, s, 0, nullptr, false, workspace_d, workspace_bytes,
+                "rg_gebhart");
   if (st == RG_OK) st = sv.set_matrix(F_d, n + 1, false);
   if (st != RG_OK) return st;
   int max_sw = 0;
@@ -1292,7 +1316,8 @@ rg_status rg_gebhart(rg_ctx* ctx, int32_t n, const double* F_d, int32_t n_sets, 
 
 rg_status rg_gebhart_adjoint(rg_ctx* ctx, int32_t n, const double* F_d, int32_t n_sets, const double* eps_d,
                              const double* rho_d, const double* B_d, const double* dB_d, int32_t precision,
-                             double tol, int32_t max_sweeps, double* deps_d, double* drho_d, void* stream) {
+                             double tol, int32_t max_sweeps, double* deps_d, double* drho_d, void* workspace_d,
+                             size_t workspace_bytes, void* stream) {
   if (!ctx) return RG_ERR_ARG;
   rg_status st = check_common(ctx, n, precision, tol, max_sweeps);
   if (st != RG_OK) return st;
@@ -1303,7 +1328,8 @@ rg_status rg_gebhart_adjoint(rg_ctx* ctx, int32_t n, const double* F_d, int32_t 
   Solver sv{ctx};
   // K^T = I - diag(rho) F_NN^T: P' = F^T for every set; the refinement also accumulates
   // Q = F^T Lambda (the sum of its exact products), which the rho gradient needs
-  st = sv.setup(n, n + 1, precision == RG_PREC_BF16_IR, s, 0, nullptr, true);
+  st = sv.setup(n, n + 1, precision == RG_PREC_BF16_IR, s, 0, nullptr, true, workspace_d, workspace_bytes,
+                "rg_gebhart_adjoint");
   if (st == RG_OK) st = sv.set_matrix(F_d, n + 1, true);
   if (st != RG_OK) return st;
   for (int set = 0; set < n_sets; ++set) {
@@ -1330,7 +1356,7 @@ rg_status rg_gebhart_adjoint(rg_ctx* ctx, int32_t n, const double* F_d, int32_t 
 
 rg_status rg_temperatures(rg_ctx* ctx, int32_t n, const double* B_d, const double* eps_d, const double* area_d,
                           const double* Q_d, double T_sink, double sigma, int32_t precision, double tol, double* T_d,
-                          void* stream) {
+                          void* workspace_d, size_t workspace_bytes, void* stream) {
   if (!ctx) return RG_ERR_ARG;
   rg_status st = check_common(ctx, n, precision, tol, 1);
   if (st != RG_OK) return st;
@@ -1339,7 +1365,8 @@ rg_status rg_temperatures(rg_ctx* ctx, int32_t n, const double* B_d, const doubl
   RG_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
   cudaStream_t s = (cudaStream_t)stream;
   Solver sv{ctx};
-  st = sv.setup(n, 1, precision == RG_PREC_BF16_IR, s);
+  st = sv.setup(n, 1, precision == RG_PREC_BF16_IR, s, 0, nullptr, false, workspace_d, workspace_bytes,
+                "rg_temperatures");
   if (st == RG_OK) st = sv.set_matrix(B_d, n + 1, false);
   if (st != RG_OK) return st;
   double* t = sv.b.vec;
@@ -1365,7 +1392,7 @@ rg_status rg_temperatures(rg_ctx* ctx, int32_t n, const double* B_d, const doubl
 rg_status rg_temperatures_adjoint(rg_ctx* ctx, int32_t n, const double* B_d, const double* eps_d,
                                   const double* area_d, double T_sink, double sigma, const double* T_d,
                                   const double* dT_d, int32_t precision, double tol, double* dB_d, double* deps_d,
-                                  void* stream) {
+                                  void* workspace_d, size_t workspace_bytes, void* stream) {
   if (!ctx) return RG_ERR_ARG;
   rg_status st = check_common(ctx, n, precision, tol, 1);
   if (st != RG_OK) return st;
@@ -1374,7 +1401,8 @@ rg_status rg_temperatures_adjoint(rg_ctx* ctx, int32_t n, const double* B_d, con
   RG_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
   cudaStream_t s = (cudaStream_t)stream;
   Solver sv{ctx};
-  st = sv.setup(n, 1, precision == RG_PREC_BF16_IR, s);
+  st = sv.setup(n, 1, precision == RG_PREC_BF16_IR, s, 0, nullptr, false, workspace_d, workspace_bytes,
+                "rg_temperatures_adjoint");
   if (st == RG_OK) st = sv.set_matrix(B_d, n + 1, true);
   if (st != RG_OK) return st;
   double* t = sv.b.vec;
@@ -1408,7 +1436,8 @@ static rg_status temperatures_sets(rg_ctx* ctx, int32_t n, const double* F_d, in
                                    const double* eps_d, const double* rho_d, const double* area_d, const double* Q_d,
                                    double T_sink, double sigma, int32_t precision, double tol, const double* T_in,
                                    const double* dT_d, double* T_d, double* dB_d, double* deps_d, double* fa_d,
-                                   double* fb_d, void* stream, bool adjoint) {
+                                   double* fb_d, void* workspace_d, size_t workspace_bytes, void* stream,
+                                   bool adjoint) {
   const char* fn = adjoint ? "rg_temperatures_adjoint_sets" : "rg_temperatures_sets";
   rg_status st = check_common(ctx, n, precision, tol, 1);
   if (st != RG_OK) return st;
@@ -1417,11 +1446,10 @@ static rg_status temperatures_sets(rg_ctx* ctx, int32_t n, const double* F_d, in
                "%s: bad argument", fn);
   RG_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
   cudaStream_t s = (cudaStream_t)stream;
-  rg::Sizer ex;
-  ex.take<double>((size_t)2 * ((n + NB - 1) / NB * NB));  // preconditioner vectors
   Solver sv{ctx};
   void* extra = nullptr;
-  st = sv.setup(n, 1, precision == RG_PREC_BF16_IR, s, ex.off, &extra);
+  st = sv.setup(n, 1, precision == RG_PREC_BF16_IR, s, balance_sets_extra_bytes(n), &extra, false, workspace_d,
+                workspace_bytes, fn);
   if (st != RG_OK) return st;
   rg::Carver cv(extra);
   BalancePre pre;
@@ -1480,26 +1508,31 @@ static rg_status temperatures_sets(rg_ctx* ctx, int32_t n, const double* F_d, in
 
 rg_status rg_temperatures_sets(rg_ctx* ctx, int32_t n, const double* F_d, int32_t n_sets, const double* B_d,
                                const double* eps_d, const double* rho_d, const double* area_d, const double* Q_d,
-                               double T_sink, double sigma, int32_t precision, double tol, double* T_d, void* stream) {
+                               double T_sink, double sigma, int32_t precision, double tol, double* T_d,
+                               void* workspace_d, size_t workspace_bytes, void* stream) {
   if (!ctx) return RG_ERR_ARG;
   return temperatures_sets(ctx, n, F_d, n_sets, B_d, eps_d, rho_d, area_d, Q_d, T_sink, sigma, precision, tol,
-                           nullptr, nullptr, T_d, nullptr, nullptr, nullptr, nullptr, stream, false);
+                           nullptr, nullptr, T_d, nullptr, nullptr, nullptr, nullptr, workspace_d, workspace_bytes,
+                           stream, false);
 }
 
 rg_status rg_temperatures_adjoint_sets(rg_ctx* ctx, int32_t n, const double* F_d, int32_t n_sets,
                                        const double* B_d, const double* eps_d, const double* rho_d,
                                        const double* area_d, double T_sink, double sigma, const double* T_d,
                                        const double* dT_d, int32_t precision, double tol, double* dB_d,
-                                       double* dB_a_d, double* dB_b_d, double* deps_d, void* stream) {
+                                       double* dB_a_d, double* dB_b_d, double* deps_d, void* workspace_d,
+                                       size_t workspace_bytes, void* stream) {
   if (!ctx) return RG_ERR_ARG;
   return temperatures_sets(ctx, n, F_d, n_sets, B_d, eps_d, rho_d, area_d, nullptr, T_sink, sigma, precision, tol,
-                           T_d, dT_d, nullptr, dB_d, deps_d, dB_a_d, dB_b_d, stream, true);
+                           T_d, dT_d, nullptr, dB_d, deps_d, dB_a_d, dB_b_d, workspace_d, workspace_bytes, stream,
+                           true);
 }
 
 rg_status rg_gebhart_adjoint_factored(rg_ctx* ctx, int32_t n, const double* F_d, int32_t n_sets,
                                       const double* eps_d, const double* rho_d, const double* B_d, int32_t rank,
                                       const double* a_d, const double* b_d, int32_t precision, double tol,
-                                      int32_t max_sweeps, double* deps_d, double* drho_d, void* stream) {
+                                      int32_t max_sweeps, double* deps_d, double* drho_d, void* workspace_d,
+                                      size_t workspace_bytes, void* stream) {
   if (!ctx) return RG_ERR_ARG;
   rg_status st = check_common(ctx, n, precision, tol, max_sweeps);
   if (st != RG_OK) return st;
@@ -1510,7 +1543,8 @@ rg_status rg_gebhart_adjoint_factored(rg_ctx* ctx, int32_t n, const double* F_d,
   cudaStream_t s = (cudaStream_t)stream;
   Solver sv{ctx};
   // K^T X = A (rank right-hand sides), P' = F^T for every set, Q = F^T X accumulated
-  st = sv.setup(n, rank, precision == RG_PREC_BF16_IR, s, 0, nullptr, true);
+  st = sv.setup(n, rank, precision == RG_PREC_BF16_IR, s, 0, nullptr, true, workspace_d, workspace_bytes,
+                "rg_gebhart_adjoint_factored");
   if (st == RG_OK) st = sv.set_matrix(F_d, n + 1, true);
   if (st != RG_OK) return st;
   for (int set = 0; set < n_sets; ++set) {
@@ -1529,6 +1563,31 @@ rg_status rg_gebhart_adjoint_factored(rg_ctx* ctx, int32_t n, const double* F_d,
     RG_CUDA_TRY(ctx, cudaGetLastError());
   }
   return sv.check_errors();
+}
+
+rg_status rg_solver_workspace(int32_t kind, int32_t n, int32_t rank, size_t* bytes_out) {
+  if (!bytes_out || n <= 0 || n > 32768) return RG_ERR_ARG;
+  switch (kind) {
+    case RG_WS_GEBHART: *bytes_out = Solver::bytes(n, n + 1, false, 0); return RG_OK;
+    case RG_WS_GEBHART_ADJOINT: *bytes_out = Solver::bytes(n, n + 1, true, 0); return RG_OK;
+    case RG_WS_GEBHART_ADJOINT_FACTORED:
+      if (rank < 1 || rank > 64) return RG_ERR_ARG;
+      *bytes_out = Solver::bytes(n, rank, true, 0);
+      return RG_OK;
+    case RG_WS_TEMPERATURES: *bytes_out = Solver::bytes(n, 1, false, 0); return RG_OK;
+    case RG_WS_TEMPERATURES_SETS: *bytes_out = Solver::bytes(n, 1, false, balance_sets_extra_bytes(n)); return RG_OK;
+    case RG_WS_ENFORCE_LSQ:
+      if (n > 4096) return RG_ERR_ARG;
+      *bytes_out = Solver::bytes(n, 1, false, lsq_extra_bytes(n));
+      return RG_OK;
+    default: return RG_ERR_ARG;
+  }
+}
+
+rg_status rg_gebhart_workspace(int32_t n, int32_t n_sets, int32_t precision, int32_t keep_factors, size_t* bytes_out) {
+  if (!bytes_out || n_sets <= 0 || (precision != RG_PREC_BF16_IR && precision != RG_PREC_FP16_IR)) return RG_ERR_ARG;
+  if (keep_factors) return RG_ERR_UNSUPPORTED;  // the solves never keep factors between calls
+  return rg_solver_workspace(RG_WS_GEBHART, n, 0, bytes_out);
 }
 
 }  // extern "C"

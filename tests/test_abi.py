@@ -76,7 +76,7 @@ def _kind_of_c(param):
     if "*" in param:
         return "ptr"
     t = param.rsplit(None, 1)[0].replace("const", "").strip()
-    return {"int64_t": "i64", "uint64_t": "i64", "int32_t": "i32", "uint32_t": "i32", "int": "i32",
+    return {"int64_t": "i64", "uint64_t": "i64", "size_t": "i64", "int32_t": "i32", "uint32_t": "i32", "int": "i32",
             "double": "f64", "float": "f32"}[t]
 
 
@@ -99,3 +99,21 @@ def test_binding_argument_types_match_the_header():
         assert len(argtypes) == len(params), (name, params, argtypes)
         for p, a in zip(params, argtypes):
             assert _kind_of_c(p) == _kind_of_ctypes(a), (name, p, a)
+
+
+def test_solver_workspace_sizes_without_a_gpu():
+    """The caller-owned workspace sizes are pure host arithmetic: positive, growing with n,
+    the REF query equal to rg_solver_workspace's, keep_factors refused."""
+    from paper_2511_04277_gb300 import api
+    from paper_2511_04277_gb300._native import RadgebError
+    for kind in ("gebhart", "gebhart_adjoint", "temperatures", "temperatures_sets", "enforce_lsq"):
+        a, b = api.solver_workspace(kind, 300), api.solver_workspace(kind, 1000)
+        assert 0 < a < b, kind
+    assert api.solver_workspace("gebhart_adjoint_factored", 500, 2) > 0
+    assert api.gebhart_workspace(700, 3, "fp16") == api.solver_workspace("gebhart", 700)
+    # the adjoint keeps F^T Lambda as well: more than the forward solve
+    assert api.solver_workspace("gebhart_adjoint", 700) > api.solver_workspace("gebhart", 700)
+    with pytest.raises(RadgebError):
+        api.gebhart_workspace(700, 1, "bf16", keep_factors=True)
+    with pytest.raises(RadgebError):
+        api.solver_workspace("enforce_lsq", 5000)
