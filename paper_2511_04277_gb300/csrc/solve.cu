@@ -239,8 +239,13 @@ __global__ void finish_residual(const int32_t* __restrict__ lev, int64_t ldl, in
       const int64_t o = (int64_t)i * ldl + j;
       long long T = 0;
       for (int z = 0; z < splits; ++z) {
+        int32_t lv[kLevels];
+#pragma unroll
+        for (int a = 0; a < kLevels; ++a) lv[a] = a < L ? lev[((int64_t)z * kLevels + a) * plane + o] : 0;
         long long t = 0;
-        for (int a = 0; a < L; ++a) t = t * 256 + lev[((int64_t)z * kLevels + a) * plane + o];
+#pragma unroll
+        for (int a = 0; a < kLevels; ++a)
+          if (a < L) t = t * 256 + lv[a];
         T += t;
       }
       const double S = int_scale2(T, rowexp[i] + f - 14 - 8 * (L - 1));
@@ -287,43 +292,74 @@ __device__ __forceinline__ float scaled_bits(double x, int e, bool& ok) {
 }
 
 // A16 = I - Dl P Dr (16-bit, identity padding), the first Newton-Schulz iterate
-// X16 = 2I - A = I + Dl P Dr (the step from X = I, done here instead of by two GEMMs) and
-// its transpose Xt16, and the largest row and column sums of |Dl P Dr| (||E||_inf into
-// e0_bits[0], ||E||_1 into e0_bits[1], atomicMax on their bits). One warp per row; the grid
-// has at least mp threads.
+// X16 = 2I - A = I + Dl P Dr (the step from X = I, done here instead of by two GEMMs) and its
+// transpose Xt16, with the row and column sums of |Dl P Dr| added into rowsum / colsum (zeroed
+// by the caller). One block (32 x 8) per 32 x 32 tile: P's tile is read coalesced in its own
+// layout (directly or transposed) through shared memory, and Xt16's tile is written from a
+// transposed copy.
 template <class T16>
 __global__ void build_ns_start(const double* __restrict__ P, int64_t ldp, bool trans, const double* __restrict__ dl,
                                const double* __restrict__ dr, int n, int np, T16* __restrict__ A16,
-                               T16* __restrict__ X16, T16* __restrict__ Xt16, unsigned long long* e0_bits,
-                               unsigned long long* colmax, int mp) {
-  // colmax[0 .. mp) = 0 for the column maxima of the first correction (no separate memset)
-  const int tid = blockIdx.x * blockDim.x + threadIdx.x;
-  if (tid < mp) colmax[tid] = 0ull;
-  const int i = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
-  const int lane = threadIdx.x & 31;
-  if (i >= np) return;
-  double rs = 0.0, cs = 0.0;  // row i and column i of |E|
-  const double li = (i < n && dl) ? dl[i] : 1.0;
-  const double ri = (i < n && dr) ? dr[i] : 1.0;
-  for (int k = lane; k < np; k += 32) {
-    double e = 0.0, et = 0.0;  // (Dl P Dr)_ik and (Dl P Dr)_ki
-    if (i < n && k < n) {
-      e = li * p_elem(P, ldp, trans, i, k) * (dr ? dr[k] : 1.0);
-      et = (dl ? dl[k] : 1.0) * p_elem(P, ldp, trans, k, i) * ri;
-    }
-    rs += fabs(e);
-    cs += fabs(et);
+                               T16* __restrict__ X16, T16* __restrict__ Xt16, double* __restrict__ rowsum,
+                               double* __restrict__ colsum) {
+  __shared__ double raw[32][33];
+  __shared__ float xs[32][33];
+  __shared__ double cpart[8][33];
+  const int i0 = blockIdx.y * 32, k0 = blockIdx.x * 32;
+  const int r0 = trans ? k0 : i0, c0 = trans ? i0 : k0;  // tile origin in P's own layout
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  for (int a = ty; a < 32; a += 8) {
+    const int r = r0 + a, c = c0 + tx;
+    raw[a][tx] = (r < n && c < n) ? P[(int64_t)r * ldp + c] : 0.0;
+  }
+  __syncthreads();
+  const int k = k0 + tx;
+  const double rk = (k < n && dr) ? dr[k] : 1.0;
+  double cs = 0.0;
+  for (int a = ty; a < 32; a += 8) {
+    const int i = i0 + a;
+    const double p = trans ? raw[tx][a] : raw[a][tx];
+    double e = 0.0;
+    if (i < n && k < n) e = (dl ? dl[i] : 1.0) * p * rk;
     const double one = (i == k) ? 1.0 : 0.0;
     const int64_t o = (int64_t)i * np + k;
     A16[o] = to16<T16>((float)(one - e));
     X16[o] = to16<T16>((float)(one + e));
-    Xt16[o] = to16<T16>((float)(one + et));
+    xs[a][tx] = (float)(one + e);
+    const double ae = fabs(e);
+    cs += ae;
+    double rs = ae;
+    for (int q = 16; q > 0; q >>= 1) rs += __shfl_xor_sync(0xffffffffu, rs, q);
+    if (tx == 0 && rs != 0.0) atomicAdd(&rowsum[i], rs);
   }
-  for (int o = 16; o > 0; o >>= 1) rs += __shfl_xor_sync(0xffffffffu, rs, o);
-  for (int o = 16; o > 0; o >>= 1) cs += __shfl_xor_sync(0xffffffffu, cs, o);
-  if (lane == 0) {
-    atomicMax(e0_bits, (unsigned long long)__double_as_longlong(rs));
-    atomicMax(e0_bits + 1, (unsigned long long)__double_as_longlong(cs));
+  cpart[ty][tx] = cs;
+  __syncthreads();
+  if (ty == 0) {
+    for (int y = 1; y < 8; ++y) cs += cpart[y][tx];
+    if (cs != 0.0) atomicAdd(&colsum[k], cs);
+  }
+  for (int a = ty; a < 32; a += 8) Xt16[(int64_t)(k0 + a) * np + i0 + tx] = to16<T16>(xs[tx][a]);
+}
+
+// ||E||_inf = max_i rowsum_i into e0_bits[0], ||E||_1 = max_k colsum_k into e0_bits[1] (bits,
+// atomicMax; zeroed by the caller), and colmax[0 .. mp) = 0 for the first correction.
+__global__ void ns_norms(const double* __restrict__ rowsum, const double* __restrict__ colsum, int np,
+                         unsigned long long* e0_bits, unsigned long long* colmax, int mp) {
+  unsigned long long r = 0ull, c = 0ull;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < max(np, mp); i += gridDim.x * blockDim.x) {
+    if (i < np) {
+      r = max(r, (unsigned long long)__double_as_longlong(rowsum[i]));
+      c = max(c, (unsigned long long)__double_as_longlong(colsum[i]));
+    }
+    if (i < mp) colmax[i] = 0ull;
+  }
+  for (int q = 16; q > 0; q >>= 1) {
+    r = max(r, __shfl_xor_sync(0xffffffffu, r, q));
+    c = max(c, __shfl_xor_sync(0xffffffffu, c, q));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicMax(e0_bits, r);
+    atomicMax(e0_bits + 1, c);
   }
 }
 
@@ -481,8 +517,10 @@ __global__ void pre_k_apply(const double* __restrict__ F, int n, const double* _
   if (lane == 0) z[i] = y[i] - acc;
 }
 
-// out_k = sum_i W[k][i] v_i (one warp per row of W, 16-bit W, fp32 products summed in fp64);
-// with D set, out goes to D[k][0] (fp32) and max_k |out_k| to dcolmax[0].
+// out_k = sum_i W[k][i] v_i (one warp per row of W, 16-bit W read eight elements at a time,
+// summed in fp32: W is a 16-bit approximate inverse, so fp32 sums are far more accurate than
+// needed); with D set, out goes to D[k][0] (fp32) and max_k |out_k| to dcolmax[0]. v is
+// zero beyond n, so the rows' padding (np is a multiple of 128) adds nothing.
 template <class T16>
 __global__ void pre_w_apply(const void* __restrict__ W, int np, int n, const double* __restrict__ v,
                             double* __restrict__ out, float* __restrict__ D, int64_t ldd, unsigned int* dcolmax,
@@ -491,16 +529,22 @@ __global__ void pre_w_apply(const void* __restrict__ W, int np, int n, const dou
   const int k = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
   const int lane = threadIdx.x & 31;
   if (k >= n) return;
-  double acc = 0.0;
-  for (int i = lane; i < n; i += 32) acc += (double)(w16<T16>(W, (int64_t)k * np + i) * (float)v[i]);
+  const uint4* row = reinterpret_cast<const uint4*>(reinterpret_cast<const T16*>(W) + (int64_t)k * np);
+  float acc = 0.f;
+  for (int g = lane; g < np / 8; g += 32) {
+    const uint4 w = row[g];
+    const T16* h = reinterpret_cast<const T16*>(&w);
+    const double* vv = v + 8 * g;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) acc = fmaf((float)h[q], (float)vv[q], acc);
+  }
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
   if (lane == 0) {
-    if (out) out[k] = acc;
+    if (out) out[k] = (double)acc;
     if (D) {
-      const float d = (float)acc;
-      D[(int64_t)k * ldd] = d;
-      if (!isfinite(d)) atomicExch(nonfinite, 1);
-      else atomicMax(dcolmax, __float_as_uint(fabsf(d)));
+      D[(int64_t)k * ldd] = acc;
+      if (!isfinite(acc)) atomicExch(nonfinite, 1);
+      else atomicMax(dcolmax, __float_as_uint(fabsf(acc)));
     }
   }
 }
@@ -554,6 +598,7 @@ struct Buffers {
   double* R;    // residual (ld = mp)
   double* Q;    // P' X (ld = mp) when want_q, else null
   double* vec;  // [2][np] per-row scratch (row sums, diagonal scalings)
+  double* nsum; // [2][np] row and column sums of |Dl P Dr| (Newton-Schulz start)
 };
 
 template <class Take>
@@ -575,6 +620,7 @@ void plan(const Layout& L, Take&& t) {
   t.template take<double>((size_t)L.np * L.mp);                   // R
   t.template take<double>(L.want_q ? (size_t)L.np * L.mp : 0);    // Q
   t.template take<double>((size_t)2 * L.np);                      // vec
+  t.template take<double>((size_t)2 * L.np);                      // nsum
 }
 
 // The solver's status words in the context scratch (ints), laid out so that one copy
@@ -652,6 +698,7 @@ struct Solver {
     b.R = cv.take<double>((size_t)L.np * L.mp);
     b.Q = want_q ? cv.take<double>((size_t)L.np * L.mp) : nullptr;
     b.vec = cv.take<double>((size_t)2 * L.np);
+    b.nsum = cv.take<double>((size_t)2 * L.np);
     err = ctx->d_scratch + kStatus;
     RG_CUDA_TRY(ctx, cudaMemsetAsync(err, 0, 6 * sizeof(int), s));  // error words and the GEMM's
     return RG_OK;
@@ -683,9 +730,12 @@ struct Solver {
     T16* X[2] = {static_cast<T16*>(b.X16[0]), static_cast<T16*>(b.X16[1])};
     T16* Xt = static_cast<T16*>(b.Xt16);
     T16* Zt = static_cast<T16*>(b.Zt16);
-    build_ns_start<T16><<<(L.np + 7) / 8, 256, 0, s>>>(P, ldp, transP, dl, dr, L.n, L.np, A16, X[0], Xt, e0,
-                                                        b.colmax, L.mp);
-    ++ctx->launches;
+    RG_CUDA_TRY(ctx, cudaMemsetAsync(b.nsum, 0, 2 * L.np * sizeof(double), s));
+    build_ns_start<T16><<<dim3(L.np / 32, L.np / 32), dim3(32, 8), 0, s>>>(P, ldp, transP, dl, dr, L.n, L.np, A16,
+                                                                           X[0], Xt, b.nsum, b.nsum + L.np);
+    ns_norms<<<std::max(1, std::min(ctx->sm_count, (std::max(L.np, L.mp) + 255) / 256)), 256, 0, s>>>(
+        b.nsum, b.nsum + L.np, L.np, e0, b.colmax, L.mp);
+    ctx->launches += 2;
     RG_CUDA_TRY(ctx, cudaGetLastError());
     // the status words and e0 in one pinned read-back: one wait on the stream
     int* hs = ctx->h_scratch;
@@ -1455,6 +1505,9 @@ static rg_status temperatures_sets(rg_ctx* ctx, int32_t n, const double* F_d, in
   BalancePre pre;
   pre.y = cv.take<double>(sv.L.np);
   pre.z = cv.take<double>(sv.L.np);
+  // only entries below n are ever written: the padding stays zero for the row products
+  RG_CUDA_TRY(ctx, cudaMemsetAsync(pre.y, 0, sv.L.np * sizeof(double), s));
+  RG_CUDA_TRY(ctx, cudaMemsetAsync(pre.z, 0, sv.L.np * sizeof(double), s));
   // W ~ (I - F_NN)^-1, shared by every set
   st = sv.set_matrix(F_d, n + 1, false);
   if (st == RG_OK) st = sv.factor(nullptr, nullptr);
