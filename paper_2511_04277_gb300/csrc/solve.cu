@@ -52,6 +52,12 @@ constexpr int kLevels = 5;
 constexpr int kLevelBits = 38;
 // Most K splits of the exact product (used when its tiles leave SMs idle).
 constexpr int kMaxExactSplits = 4;
+// K splits the workspace makes room for: a product whose level planes are small has few
+// tiles and may split; a large one has tiles for every SM and never does (its int32 level
+// sums then take one set of planes, not four).
+inline int exact_splits(int n, int m) {
+  return tc::exact_plane(n, m) * (int64_t)sizeof(int32_t) <= (64ll << 20) ? kMaxExactSplits : 1;
+}
 
 __device__ __forceinline__ double p_elem(const double* P, int64_t ldp, bool trans, int i, int k) {
   return trans ? P[(int64_t)k * ldp + i] : P[(int64_t)i * ldp + k];
@@ -107,6 +113,27 @@ __device__ __forceinline__ int exact_levels(const unsigned long long* red) {
   return tc::exact_level_count(red, kLevelBits, kLevels);
 }
 
+// round(x 2^s) to the nearest integer, ties to even, for |x 2^s| < 2^62, on the bit pattern of x
+// (the value llrint(ldexp(x, s)) gives, without the fp64 pipe).
+__device__ __forceinline__ long long round_scaled(double x, int s) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int E = (int)((b >> 52) & 0x7ff);
+  if (E == 0) return 0;  // zero or subnormal: |x 2^s| < 2^-1022 2^s, below 1/2 here
+  const unsigned long long m = (b & 0xfffffffffffffull) | 0x10000000000000ull;  // 53-bit significand
+  const int sh = E - 1075 + s;  // x 2^s = m 2^sh
+  long long q;
+  if (sh >= 0) {
+    q = (long long)(m << sh);
+  } else if (sh <= -54) {
+    q = 0;  // below 1/2
+  } else {
+    const int r = -sh;
+    const unsigned long long keep = m >> r, rem = m & ((1ull << r) - 1ull), half = 1ull << (r - 1);
+    q = (long long)(keep + ((rem > half || (rem == half && (keep & 1ull))) ? 1ull : 0ull));
+  }
+  return (b >> 63) ? -q : q;
+}
+
 // Fixed-point split of P' = P Dr (Dr may be null) into kLevels slices per row: with e_i the
 // exponent of max_k |P'_ik| and q = round(P'_ik 2^(39 - e_i)) (|q| < 2^39, to nearest, ties
 // to even), the slices are q's balanced base-256 digits, q = sum_a s_a 256^(4 - a) with
@@ -140,10 +167,9 @@ __global__ void build_p_exact(const double* __restrict__ P, int64_t ldp, bool tr
     mx = 0.0;  // the slices are not used once the error is raised
   }
   const int e = mx > 0.0 ? frexp_exponent(mx) : 0;
-  const double sc = mx > 0.0 ? ldexp(1.0, 39 - e) : 0.0;
   for (int k = lane; k < np; k += 32) {
     long long q = 0;
-    if (k < n && mx > 0.0) q = __double2ll_rn(p_elem(P, ldp, trans, i, k) * (dr ? dr[k] : 1.0) * sc);
+    if (k < n && mx > 0.0) q = round_scaled(p_elem(P, ldp, trans, i, k) * (dr ? dr[k] : 1.0), 39 - e);
     int d[kLevels];
 #pragma unroll
     for (int a = kLevels - 1; a > 0; --a) {
@@ -293,8 +319,8 @@ __device__ __forceinline__ float scaled_bits(double x, int e, bool& ok) {
 
 // A16 = I - Dl P Dr (16-bit, identity padding), the first Newton-Schulz iterate
 // X16 = 2I - A = I + Dl P Dr (the step from X = I, done here instead of by two GEMMs) and its
-// transpose Xt16, with the row and column sums of |Dl P Dr| added into rowsum / colsum (zeroed
-// by the caller). One block (32 x 8) per 32 x 32 tile: P's tile is read coalesced in its own
+// transpose Xt16, with the row and column sums of |Dl P Dr| (in fp32) added into rowsum /
+// colsum (zeroed by the caller). One block (32 x 8) per 32 x 32 tile: P's tile is read coalesced in its own
 // layout (directly or transposed) through shared memory, and Xt16's tile is written from a
 // transposed copy.
 template <class T16>
@@ -304,7 +330,7 @@ __global__ void build_ns_start(const double* __restrict__ P, int64_t ldp, bool t
                                double* __restrict__ colsum) {
   __shared__ double raw[32][33];
   __shared__ float xs[32][33];
-  __shared__ double cpart[8][33];
+  __shared__ float cpart[8][33];
   const int i0 = blockIdx.y * 32, k0 = blockIdx.x * 32;
   const int r0 = trans ? k0 : i0, c0 = trans ? i0 : k0;  // tile origin in P's own layout
   const int tx = threadIdx.x, ty = threadIdx.y;
@@ -313,30 +339,32 @@ __global__ void build_ns_start(const double* __restrict__ P, int64_t ldp, bool t
     raw[a][tx] = (r < n && c < n) ? P[(int64_t)r * ldp + c] : 0.0;
   }
   __syncthreads();
+  // fp32 arithmetic from here: A16 and X16 are 16-bit, and the norms only set the step count
+  // (GB300's fp64 pipe, conversions included, is far slower than its fp32 one)
   const int k = k0 + tx;
-  const double rk = (k < n && dr) ? dr[k] : 1.0;
-  double cs = 0.0;
+  const float rk = (k < n && dr) ? (float)dr[k] : 1.f;
+  float cs = 0.f;
   for (int a = ty; a < 32; a += 8) {
     const int i = i0 + a;
-    const double p = trans ? raw[tx][a] : raw[a][tx];
-    double e = 0.0;
-    if (i < n && k < n) e = (dl ? dl[i] : 1.0) * p * rk;
-    const double one = (i == k) ? 1.0 : 0.0;
+    const float p = (float)(trans ? raw[tx][a] : raw[a][tx]);
+    float e = 0.f;
+    if (i < n && k < n) e = (dl ? (float)dl[i] : 1.f) * p * rk;
+    const float one = (i == k) ? 1.f : 0.f;
     const int64_t o = (int64_t)i * np + k;
-    A16[o] = to16<T16>((float)(one - e));
-    X16[o] = to16<T16>((float)(one + e));
-    xs[a][tx] = (float)(one + e);
-    const double ae = fabs(e);
+    A16[o] = to16<T16>(one - e);
+    X16[o] = to16<T16>(one + e);
+    xs[a][tx] = one + e;
+    const float ae = fabsf(e);
     cs += ae;
-    double rs = ae;
+    float rs = ae;
     for (int q = 16; q > 0; q >>= 1) rs += __shfl_xor_sync(0xffffffffu, rs, q);
-    if (tx == 0 && rs != 0.0) atomicAdd(&rowsum[i], rs);
+    if (tx == 0 && rs != 0.f) atomicAdd(&rowsum[i], (double)rs);
   }
   cpart[ty][tx] = cs;
   __syncthreads();
   if (ty == 0) {
     for (int y = 1; y < 8; ++y) cs += cpart[y][tx];
-    if (cs != 0.0) atomicAdd(&colsum[k], cs);
+    if (cs != 0.f) atomicAdd(&colsum[k], (double)cs);
   }
   for (int a = ty; a < 32; a += 8) Xt16[(int64_t)(k0 + a) * np + i0 + tx] = to16<T16>(xs[tx][a]);
 }
@@ -592,7 +620,7 @@ struct Buffers {
   __nv_bfloat16* Bq;             // mp x np, the rounded correction, transposed
   int16_t* Dn;                   // np x mp, the rounded correction's integers
   int* dexp;                     // mp, its column exponents
-  int32_t* lev;                  // kMaxExactSplits x kLevels planes of exact_plane(n, m)
+  int32_t* lev;                  // exact_splits(n, m) x kLevels planes of exact_plane(n, m)
   double* R0;   // right-hand side (ld = mp)
   double* X;    // solution (ld = mp)
   double* R;    // residual (ld = mp)
@@ -614,7 +642,7 @@ void plan(const Layout& L, Take&& t) {
   t.template take<__nv_bfloat16>((size_t)L.mp * L.np);            // Bq
   t.template take<int16_t>((size_t)L.np * L.mp);                  // Dn
   t.template take<int>((size_t)L.mp);                             // dexp
-  t.template take<int32_t>((size_t)kMaxExactSplits * kLevels * tc::exact_plane(L.n, L.m));  // lev
+  t.template take<int32_t>((size_t)exact_splits(L.n, L.m) * kLevels * tc::exact_plane(L.n, L.m));  // lev
   t.template take<double>((size_t)L.np * L.mp);                   // R0
   t.template take<double>((size_t)L.np * L.mp);                   // X
   t.template take<double>((size_t)L.np * L.mp);                   // R
@@ -692,7 +720,7 @@ struct Solver {
     b.Bq = cv.take<__nv_bfloat16>((size_t)L.mp * L.np);
     b.Dn = cv.take<int16_t>((size_t)L.np * L.mp);
     b.dexp = cv.take<int>(L.mp);
-    b.lev = cv.take<int32_t>((size_t)kMaxExactSplits * kLevels * tc::exact_plane(L.n, L.m));
+    b.lev = cv.take<int32_t>((size_t)exact_splits(L.n, L.m) * kLevels * tc::exact_plane(L.n, L.m));
     b.R0 = cv.take<double>((size_t)L.np * L.mp);
     b.X = cv.take<double>((size_t)L.np * L.mp);
     b.R = cv.take<double>((size_t)L.np * L.mp);
@@ -822,7 +850,7 @@ struct Solver {
     RG_CUDA_TRY(ctx, cudaGetLastError());
     // levels from max|D| / max|X| of this sweep (rc[2] / rc[1]), read on the device
     st = tc::gemm_exact(ctx, b.Aex, (int64_t)kLevels * L.np, b.Bq, L.np, L.n, L.m, L.np, nullptr, rc, kLevelBits,
-                        kLevels, b.lev, kMaxExactSplits, &splits, s, skip, L.n);
+                        kLevels, b.lev, exact_splits(L.n, L.m), &splits, s, skip, L.n);
     if (st != RG_OK) return st;
     dim3 fg((L.m + 31) / 32, (L.n + 31) / 32);
     finish_residual<<<fg, dim3(32, 8), 0, s>>>(b.lev, tc::exact_ld(L.m), tc::exact_plane(L.n, L.m), splits, b.rowexp,
