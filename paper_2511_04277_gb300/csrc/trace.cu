@@ -1,7 +1,7 @@
 // Monte Carlo ray tracing of view factors (Sec. 3.5.1, Eq. 3.15) on sm_103a.
 //
 // One persistent kernel: each block repeatedly takes a work item (one face, a range
-// of its rays) and keeps a shared-memory tally row of N+1 counters for that face. The
+// of its rays) and keeps a shared-memory tally row of N+1 16-bit counters for that face. The
 // warps of the block share the item's rays through a counter. Two schedules (chosen per
 // mesh, identical counts):
 //   lock-step (shallow BVHs): the warp samples 32 rays in step, gives each one root
@@ -435,6 +435,26 @@ __device__ __forceinline__ void start_ray(Walker& w, const Ring& r, int k, int32
   w.sp = 0;
 }
 
+// The block's tally row in shared memory: two 16-bit counters per 32-bit word (bin b in the
+// low half of word b / 2 when b is even, the high half when odd). A work item holds at most
+// kMaxItemRays rays (paths), so no counter can pass 65,535 and spill into its neighbour.
+// Halving the row leaves more of the SM's unified L1 / shared memory to the per-thread
+// traversal stacks.
+constexpr int64_t kMaxItemRays = 1 << 15;
+__device__ __forceinline__ void tally_clear(uint32_t* hist, int n_bins) {
+  for (int w = threadIdx.x; w < (n_bins + 1) / 2; w += kThreads) hist[w] = 0u;
+}
+__device__ __forceinline__ void tally_add(uint32_t* hist, int b, uint32_t c) {
+  atomicAdd(&hist[b >> 1], c << ((b & 1) * 16));
+}
+__device__ __forceinline__ void tally_flush(const uint32_t* hist, int n_bins, unsigned long long* row) {
+  for (int w = threadIdx.x; w < (n_bins + 1) / 2; w += kThreads) {
+    const uint32_t v = hist[w];
+    if (v & 0xffffu) atomicAdd(row + 2 * w, (unsigned long long)(v & 0xffffu));
+    if ((v >> 16) && 2 * w + 1 < n_bins) atomicAdd(row + 2 * w + 1, (unsigned long long)(v >> 16));
+  }
+}
+
 // Refill variant (see the file comment). Best when traversals are long and uneven.
 template <bool E, bool kBVH, bool S, class St>
 __global__ void __launch_bounds__(kThreads, RG_REFILL_MIN_BLOCKS) trace_kernel_refill(const TraceParams p) {
@@ -455,7 +475,7 @@ __global__ void __launch_bounds__(kThreads, RG_REFILL_MIN_BLOCKS) trace_kernel_r
       s_item = atomicAdd(p.item_counter, 1);
       s_next = 0;
     }
-    for (int b = threadIdx.x; b < p.n_bins; b += kThreads) hist[b] = 0u;
+    tally_clear(hist, p.n_bins);
     __syncthreads();
     const int32_t item = s_item;
     if (item >= p.n_items) break;
@@ -489,7 +509,7 @@ __global__ void __launch_bounds__(kThreads, RG_REFILL_MIN_BLOCKS) trace_kernel_r
       const unsigned fin = __ballot_sync(0xffffffffu, has_ray && done);
       if (has_ray && done) {
         const unsigned peers = __match_any_sync(fin, w.best_face);
-        if (lane == __ffs(peers) - 1) atomicAdd(&hist[w.best_face], (uint32_t)__popc(peers));
+        if (lane == __ffs(peers) - 1) tally_add(hist, w.best_face, (uint32_t)__popc(peers));
         ++n_rays;
         has_ray = false;
       }
@@ -528,11 +548,7 @@ __global__ void __launch_bounds__(kThreads, RG_REFILL_MIN_BLOCKS) trace_kernel_r
       if (!__any_sync(0xffffffffu, has_ray)) break;  // ring empty and nothing left to sample
     }
     __syncthreads();
-    unsigned long long* row = p.counts + (int64_t)wi.face * p.n_bins;
-    for (int b = threadIdx.x; b < p.n_bins; b += kThreads) {
-      uint32_t c = hist[b];
-      if (c) atomicAdd(row + b, (unsigned long long)c);
-    }
+    tally_flush(hist, p.n_bins, p.counts + (int64_t)wi.face * p.n_bins);
     __syncthreads();
   }
   if (overflow) atomicExch(p.error_word, 1);
@@ -578,7 +594,7 @@ __global__ void __launch_bounds__(kThreads, RG_LOCKSTEP_MIN_BLOCKS) trace_kernel
     const unsigned fm = __ballot_sync(0xffffffffu, fin);
     if (fin) {
       const unsigned peers = __match_any_sync(fm, face);
-      if (lane == __ffs(peers) - 1) atomicAdd(&hist[face], (uint32_t)__popc(peers));
+      if (lane == __ffs(peers) - 1) tally_add(hist, face, (uint32_t)__popc(peers));
       ++n_rays;
     }
   };
@@ -599,7 +615,7 @@ __global__ void __launch_bounds__(kThreads, RG_LOCKSTEP_MIN_BLOCKS) trace_kernel
       s_item = atomicAdd(p.item_counter, 1);
       s_next = 0;
     }
-    for (int b = threadIdx.x; b < p.n_bins; b += kThreads) hist[b] = 0u;
+    tally_clear(hist, p.n_bins);
     __syncthreads();
     const int32_t item = s_item;
     if (item >= p.n_items) break;
@@ -644,7 +660,7 @@ __global__ void __launch_bounds__(kThreads, RG_LOCKSTEP_MIN_BLOCKS) trace_kernel
       if (kBVH) {
         // with a BVH every ray finished here left the scene: one count for all of them
         const unsigned esc = __ballot_sync(0xffffffffu, valid && !more);
-        if (lane == 0 && esc) atomicAdd(&hist[env], (uint32_t)__popc(esc));
+        if (lane == 0 && esc) tally_add(hist, env, (uint32_t)__popc(esc));
         if (valid && !more) ++n_rays;
       } else {
         tally(valid && !more, face);
@@ -685,11 +701,7 @@ __global__ void __launch_bounds__(kThreads, RG_LOCKSTEP_MIN_BLOCKS) trace_kernel
       __syncwarp();
     }
     __syncthreads();
-    unsigned long long* row = p.counts + (int64_t)wi.face * p.n_bins;
-    for (int b = threadIdx.x; b < p.n_bins; b += kThreads) {
-      uint32_t c = hist[b];
-      if (c) atomicAdd(row + b, (unsigned long long)c);
-    }
+    tally_flush(hist, p.n_bins, p.counts + (int64_t)wi.face * p.n_bins);
     __syncthreads();
   }
   if (overflow) atomicExch(p.error_word, 1);
@@ -728,7 +740,7 @@ __global__ void __launch_bounds__(kThreads) trace_kernel_reflect(const TracePara
       s_item = atomicAdd(p.item_counter, 1);
       s_next = 0;
     }
-    for (int b = threadIdx.x; b < p.n_bins; b += kThreads) hist[b] = 0u;
+    tally_clear(hist, p.n_bins);
     __syncthreads();
     const int32_t item = s_item;
     if (item >= p.n_items) break;
@@ -766,15 +778,11 @@ __global__ void __launch_bounds__(kThreads) trace_kernel_reflect(const TracePara
       const unsigned fm = __ballot_sync(0xffffffffu, fin);
       if (fin) {
         const unsigned peers = __match_any_sync(fm, col);
-        if (lane == __ffs(peers) - 1) atomicAdd(&hist[col], (uint32_t)__popc(peers));
+        if (lane == __ffs(peers) - 1) tally_add(hist, col, (uint32_t)__popc(peers));
       }
     }
     __syncthreads();
-    unsigned long long* row = p.counts + (int64_t)wi.face * p.n_bins;
-    for (int b = threadIdx.x; b < p.n_bins; b += kThreads) {
-      uint32_t c = hist[b];
-      if (c) atomicAdd(row + b, (unsigned long long)c);
-    }
+    tally_flush(hist, p.n_bins, p.counts + (int64_t)wi.face * p.n_bins);
     __syncthreads();
   }
   if (overflow) atomicExch(p.error_word, 1);
@@ -792,7 +800,8 @@ __global__ void __launch_bounds__(kThreads) trace_kernel_reflect(const TracePara
   }
 }
 
-inline size_t trace_smem_bytes(int n_bins) { return (size_t)((n_bins + 3) & ~3) * sizeof(uint32_t); }
+// Shared memory of the tally row: (n_bins + 1) / 2 words, rounded up to 16 bytes.
+inline size_t trace_smem_bytes(int n_bins) { return (size_t)((((n_bins + 1) / 2) + 3) & ~3) * sizeof(uint32_t); }
 
 template <bool E, bool B, class St, bool S = false>
 cudaError_t launch(const TraceParams& p, int sm_count, size_t smem, cudaStream_t s) {
@@ -844,15 +853,15 @@ rg_status trace_impl(rg_ctx* ctx, const rg_mesh* mesh, const int64_t* rays_per_f
   if (n_bins > 49152 || (int)smem > ctx->smem_optin - 1024)
     return rg::fail(ctx, RG_ERR_UNSUPPORTED, "%s: %d tally columns exceed the shared-memory tally row", fn, n_bins);
   // work items: chunks of at most `chunk` rays of one row. Blocks take items dynamically,
-  // so the last ones set the tail of the launch: the chunk halves from 65,536 rays while
-  // the launch would give its resident blocks fewer than 32 items each, down to 16,384
-  // (measured on GB300: the 1e8-ray small-satellite trace 4.20 -> 4.75 G rays/s, the
-  // plates unchanged; below that the per-item clearing and flushing of the tally row
-  // starts to show)
+  // so the last ones set the tail of the launch: the chunk halves from 32,768 rays (the
+  // most a 16-bit tally counter can take) while the launch would give its resident blocks
+  // fewer than 32 items each, down to 16,384 (measured on GB300: the 1e8-ray small-
+  // satellite trace 4.20 -> 4.75 G rays/s; below that the per-item clearing and flushing
+  // of the tally row starts to show)
   int64_t total = 0;
   for (int32_t f = 0; f < n_rows; ++f) total += std::max<int64_t>(rays_per_face_h[f], 0);
   const int64_t resident = (int64_t)ctx->sm_count * (m.refill ? RG_REFILL_MIN_BLOCKS : RG_LOCKSTEP_MIN_BLOCKS);
-  int64_t kChunk = 1 << 16;
+  int64_t kChunk = kMaxItemRays;
   while (kChunk > (1 << 14) && total / kChunk < 32 * resident) kChunk /= 2;
   std::vector<WorkItem> items;
   for (int32_t f = 0; f < n_rows; ++f) {
@@ -961,6 +970,7 @@ rg_status rg_trace_reflect(rg_ctx* ctx, const rg_mesh* mesh, const int64_t* rays
     thr[N + f] = (unsigned long long)std::floor((a + r) * 4294967296.0);
   }
   constexpr int64_t kChunk = 1 << 14;  // paths are long and uneven: smaller items balance the blocks
+  static_assert(kChunk <= kMaxItemRays, "an item's tally counters are 16-bit");
   std::vector<WorkItem> items;
   for (int32_t f = 0; f < N; ++f) {
     int64_t n = rays_per_face_h[f];
