@@ -870,6 +870,54 @@ def run_reference(args):
             "e2e": {"value": value, "unit": "rays/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+def factorisation_comparison(torch, api, ctx, ev, name, F, eps, rho):
+    """The factorisation the REF solve makes (the Newton-Schulz inverse M of K on tcgen05,
+    fp16) and the per-sweep application of it (one correction product D = M R, n x n x (n+1)),
+    beside an LU of the same K (cuSOLVER getrf through torch.linalg.lu_factor) and its
+    per-sweep application (getrs with the n+1 right-hand sides, torch.linalg.lu_solve), in
+    fp32 and fp64. Every figure is measured with CUDA events; the two totals are
+    factorisation + sweeps x application, the sweeps being the ones the solve took."""
+    n = F.shape[0]
+    dev = F.device
+    api.kernel_timer(ctx, True)
+    _, sweeps, _ = api.gebhart(ctx, F, eps[:1], rho[:1], SOLVE_PRECISION, tol=SOLVE_TOL)
+    api.kernel_timer(ctx, False)
+    fa = api.kernel_timer_read(ctx, "factor")
+    np_ = (n + 127) // 128 * 128
+    dt16 = torch.float16 if SOLVE_PRECISION == "fp16" else torch.bfloat16
+    Mi = torch.randn(np_, np_, device=dev).to(dt16)
+    Rt = torch.randn(n + 1, np_, device=dev).to(dt16)
+    C = torch.empty(np_, n + 1, dtype=torch.float32, device=dev)
+    ms_corr = ev(lambda: api.tc_gemm(ctx, Mi, Rt, C), 5)
+    del Mi, Rt, C
+    res = {"workload": name, "n": n, "sweeps": int(sweeps),
+           "newton_schulz": {"factor_ms": round(fa["ms"], 3), "apply_ms": round(ms_corr, 3),
+                             "total_ms": round(fa["ms"] + sweeps * ms_corr, 3)}}
+    Kd = torch.eye(n, dtype=torch.float64, device=dev) - F[:, :n] * rho[0][None, :]
+    Ed = F.clone()
+    Ed[:, :n] *= eps[0][None, :]
+    prev = torch.backends.cuda.preferred_linalg_library()
+    torch.backends.cuda.preferred_linalg_library("cusolver")
+    try:
+        for dt, key in ((torch.float32, "cusolver_lu_fp32"), (torch.float64, "cusolver_lu_fp64")):
+            Kt, Et = Kd.to(dt), Ed.to(dt)
+            try:
+                box = {}
+                ms_f = ev(lambda: box.__setitem__("lu", torch.linalg.lu_factor(Kt)), 3)
+                LU, piv = box["lu"]
+                ms_s = ev(lambda: torch.linalg.lu_solve(LU, piv, Et), 3)
+                res[key] = {"factor_ms": round(ms_f, 3), "apply_ms": round(ms_s, 3),
+                            "total_ms": round(ms_f + sweeps * ms_s, 3)}
+                del LU, piv, box
+            except RuntimeError as exc:
+                res[key] = str(exc).splitlines()[0][:100]
+            del Kt, Et
+    finally:
+        torch.backends.cuda.preferred_linalg_library(prev)
+    del Kd, Ed
+    return res
+
+
 def solve_scaling(args):
     """REF solve + adjoint at the three solve sizes of the workloads (enforced MCRT F at a
     reduced ray budget), ours against torch.linalg.solve float64, and the tcgen05 GEMM
@@ -885,7 +933,8 @@ def solve_scaling(args):
         torch.cuda.synchronize()
         return statistics.median(time_region(torch, fn, torch.cuda.current_stream()) for _ in range(reps))
 
-    out = {"kind": "solve_scaling", "precision": SOLVE_PRECISION, "gemm": [], "enforce": [], "solves": []}
+    out = {"kind": "solve_scaling", "precision": SOLVE_PRECISION, "gemm": [], "enforce": [], "solves": [],
+           "factorisations": []}
     peaks = load_peaks()
     g = torch.Generator().manual_seed(0)
     for M, N, K in ((4096, 4096, 4096), (10240, 10240, 10240)):
@@ -979,6 +1028,7 @@ def solve_scaling(args):
             del Kd, Ed, B64
         except RuntimeError as exc:
             ms64, err = None, str(exc).splitlines()[0][:120]
+        out["factorisations"].append(factorisation_comparison(torch, api, ctx, ev, name, F, eps, rho))
         out["solves"].append({"workload": name, "n": n, "sets": S, "ours_ms": round(ms_f + ms_a, 2),
                               "refs_ms": round(ms_f, 2), "adjoint_ms": round(ms_a, 2), "sweeps": sweeps,
                               "residual": res, "fp64_ms": None if ms64 is None else round(ms64, 2),

@@ -105,19 +105,29 @@ rg_status rg_gebhart_workspace(int32_t n, int32_t n_sets, int32_t precision, int
  * context records a CUDA event pair on the launching stream around every launch of
  * these kernel classes:
  *   RG_TIME_TRACE     the MCRT trace kernel of rg_trace, rg_trace_stats, rg_trace_sided;
- *   RG_TIME_RESIDUAL  the refinement-residual GEMM of the dense solves (and of
- *                     rg_tc_gemm_residual);
+ *   RG_TIME_RESIDUAL  the exact level products of the dense solves' refinement (and of
+ *                     rg_tc_gemm_exact);
  *   RG_TIME_GEMM      the other tensor-core GEMMs (Newton-Schulz steps, corrections);
- *   RG_TIME_ENFORCE   the persistent iterative enforcer.
+ *   RG_TIME_ENFORCE   the persistent iterative enforcer;
+ *   RG_TIME_FACTOR    one region per factorisation of a dense solve: the Newton-Schulz
+ *                     inverse from its start iterate through its last step, including the
+ *                     read-back of the start norms that fixes the step count (its GEMMs
+ *                     are also counted under RG_TIME_GEMM).
  * rg_kernel_timer(ctx, 1) clears the records and starts recording, rg_kernel_timer(ctx, 0)
  * stops. rg_kernel_timer_read synchronises on the recorded events of `kind` and returns
  * their number, the sum of their durations (ms) and, for the GEMM classes, the tensor-core
- * flops the launches executed (2 M N K each) and the algorithmic flops of the products
- * they stand for (for the refinement residual, 2 n m n of the fp64 product R = E - K X that
- * the sliced bf16 product emulates; otherwise equal to the executed flops). The two flop
- * outputs may be NULL. The records grow by one event pair per timed launch until the next
+ * flops the launches executed (2 M N K each, times the levels an exact product ran) and the
+ * algorithmic flops of the products they stand for (for the refinement's level product,
+ * 2 n n m of the one-slice product P' D it computes exactly; otherwise equal to the executed
+ * flops); both are 0 for the other classes. The two flop outputs may be NULL. The records grow by one event pair per timed launch until the next
  * rg_kernel_timer(ctx, 1). Errors: RG_ERR_ARG, RG_ERR_CUDA. */
-typedef enum { RG_TIME_TRACE = 0, RG_TIME_RESIDUAL = 1, RG_TIME_GEMM = 2, RG_TIME_ENFORCE = 3 } rg_kernel_class;
+typedef enum {
+  RG_TIME_TRACE = 0,
+  RG_TIME_RESIDUAL = 1,
+  RG_TIME_GEMM = 2,
+  RG_TIME_ENFORCE = 3,
+  RG_TIME_FACTOR = 4
+} rg_kernel_class;
 rg_status rg_kernel_timer(rg_ctx* ctx, int32_t enable);
 rg_status rg_kernel_timer_read(rg_ctx* ctx, int32_t kind, int64_t* launches_out_h, double* ms_out_h,
                                double* flops_out_h, double* alg_flops_out_h);

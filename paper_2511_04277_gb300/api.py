@@ -220,7 +220,7 @@ def launch_count(ctx: Context) -> int:
     return n.value
 
 
-KERNEL_CLASSES = {"trace": 0, "residual_gemm": 1, "gemm": 2, "enforce": 3}
+KERNEL_CLASSES = {"trace": 0, "residual_gemm": 1, "gemm": 2, "enforce": 3, "factor": 4}
 
 
 def workspace_bytes(ctx: Context) -> int:

@@ -63,7 +63,14 @@ rg_status workspace_or(rg_ctx* ctx, void* user, size_t user_bytes, size_t bytes,
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 // Kernel classes of the kernel timer (values of rg_kernel_class in radgeb.h).
-enum KernelClass { kTimeTrace = 0, kTimeResidualGemm = 1, kTimeGemm = 2, kTimeEnforce = 3, kTimeClasses = 4 };
+enum KernelClass {
+  kTimeTrace = 0,
+  kTimeResidualGemm = 1,
+  kTimeGemm = 2,
+  kTimeEnforce = 3,
+  kTimeFactor = 4,
+  kTimeClasses = 5
+};
 // Records the start event of a launch of class `kind` on stream s when the timer is on;
 // returns the token timer_end takes (-1: not recorded).
 int timer_begin(rg_ctx* ctx, int kind, cudaStream_t s, double flops = 0.0, double alg = 0.0);

@@ -802,7 +802,10 @@ struct Solver {
     return RG_OK;
   }
   rg_status factor(const double* dl, const double* dr) {
-    return bf16 ? factor_t<__nv_bfloat16>(dl, dr) : factor_t<__half>(dl, dr);
+    const int tok = rg::timer_begin(ctx, rg::kTimeFactor, s);
+    const rg_status st = bf16 ? factor_t<__nv_bfloat16>(dl, dr) : factor_t<__half>(dl, dr);
+    rg::timer_end(ctx, tok, s);
+    return st;
   }
 
   // One sweep: D = M src (src = R0 for the first, R after), D rounded to its one-slice form and
