@@ -206,6 +206,8 @@ class Pipeline:
         self.F_it = torch.empty_like(self.F)
         self.F_ls = torch.empty_like(self.F) if lsq else None
         self.B = torch.empty((S, N, N + 1), **f64)
+        # the REF solve keeps each set's 16-bit inverse here; the REF adjoint reads it
+        self.factors = api.gebhart_factor_store(N, S, SOLVE_PRECISION, device=torch.device(device).index or 0)
         self.dB_a = torch.empty((S, 2, N), **f64)      # dL/dB of the balance, factored: sum_r a_r b_r^T
         self.dB_b = torch.empty((S, 2, N + 1), **f64)
         self.T = torch.empty((S, N), **f64)
@@ -243,7 +245,7 @@ class Pipeline:
 
     def refs(self):
         _, self.sweeps, self.resid = self.api.gebhart(self.ctx, self.F_it, self.eps, self.rho, SOLVE_PRECISION,
-                                                      tol=SOLVE_TOL, B=self.B)
+                                                      tol=SOLVE_TOL, B=self.B, factors=self.factors)
 
     def thermal(self):
         """Steady temperatures of every set and their adjoint (dL/dB, direct dL/deps of
@@ -257,10 +259,11 @@ class Pipeline:
 
     def adjoint(self):
         """The REF adjoint of every set for the balance's cotangent dL/dB = sum_r a_r b_r^T
-        (rank 2): K^T solved for the two left factors of each set."""
+        (rank 2): K^T solved for the two left factors of each set, with the inverses the
+        REF solve kept (no second factorisation)."""
         self.deps_B, self.drho = self.api.gebhart_adjoint_factored(self.ctx, self.F_it, self.eps, self.rho, self.B,
                                                                    self.dB_a, self.dB_b, precision=SOLVE_PRECISION,
-                                                                   tol=SOLVE_TOL)
+                                                                   tol=SOLVE_TOL, factors=self.factors)
 
     def step(self, marks=None, stream=None):
         """One pass of the path; with `marks` (one CUDA event per stage) each stage's end is
@@ -1005,11 +1008,14 @@ def solve_scaling(args):
         rho = torch.as_tensor(w["rho"][:S], device=dev)
         reps = 1 if n > 4096 else 5
         box = {}
-        ms_f = ev(lambda: box.__setitem__("B", api.gebhart(ctx, F, eps, rho, SOLVE_PRECISION, tol=SOLVE_TOL)), reps)
+        store = api.gebhart_factor_store(n, S, SOLVE_PRECISION)
+        ms_f = ev(lambda: box.__setitem__("B", api.gebhart(ctx, F, eps, rho, SOLVE_PRECISION, tol=SOLVE_TOL,
+                                                           factors=store)), reps)
         B, sweeps, res = box["B"]
         dB = torch.ones_like(B)
-        ms_a = ev(lambda: api.gebhart_adjoint(ctx, F, eps, rho, B, dB, SOLVE_PRECISION, tol=SOLVE_TOL), reps)
-        del dB
+        ms_a = ev(lambda: api.gebhart_adjoint(ctx, F, eps, rho, B, dB, SOLVE_PRECISION, tol=SOLVE_TOL,
+                                              factors=store), reps)
+        del dB, store
         Fn = F[:, :n]
 
         def fp64_pair():

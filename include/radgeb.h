@@ -95,10 +95,12 @@ typedef enum {
   RG_WS_ENFORCE_LSQ = 6               /* rg_enforce_lsq */
 } rg_solver_kind;
 rg_status rg_solver_workspace(int32_t kind, int32_t n, int32_t rank, size_t* bytes_out);
-/* The REF solve's workspace (App. B, Eq. B.8-B.11) for n faces and n_sets sets in
- * `precision`: rg_solver_workspace(RG_WS_GEBHART, n, 0, ...). keep_factors must be 0: no
- * factors are kept between calls (the adjoint factorises K^T afresh);
- * keep_factors != 0 is RG_ERR_UNSUPPORTED. */
+/* The REF solve's memory (App. B, Eq. B.8-B.11) for n faces and n_sets sets in `precision`.
+ * keep_factors = 0: the workspace of one rg_gebhart call, as
+ * rg_solver_workspace(RG_WS_GEBHART, n, 0, ...). keep_factors != 0: the size of the factor
+ * store (factors_d) that rg_gebhart fills and rg_gebhart_adjoint / rg_gebhart_adjoint_factored
+ * read: a 256-byte header and one 16-bit np x np inverse per set (np = n rounded up to 128),
+ * about 2 n^2 n_sets bytes. Errors: RG_ERR_ARG. */
 rg_status rg_gebhart_workspace(int32_t n, int32_t n_sets, int32_t precision, int32_t keep_factors, size_t* bytes_out);
 
 /* Kernel timer, for measurement (no counterpart in the thesis). While it is on, the
@@ -435,25 +437,42 @@ rg_status rg_node_couplings(rg_ctx* ctx, int32_t n, const double* B2_d, const do
  *   max_sweeps  refinement sweeps at most (>= 1)
  *   sweeps_out_h host int32 (may be NULL); resid_out_h host fp64 (may be NULL):
  *            the final relative residual (max over sets)
+ *   factors_d   device buffer of factors_bytes (may be NULL: nothing kept), 256-byte
+ *            aligned, at least rg_gebhart_workspace(n, n_sets, precision, 1) bytes: the
+ *            call stores there, per set, the transpose of its 16-bit approximate inverse of
+ *            K, which is an approximate inverse of K^T, so that the adjoint calls need not
+ *            factorise K^T again (the thesis has no adjoint; this is the usual reuse of a
+ *            forward factorisation by a backward pass). Owned by the caller; the store is
+ *            marked complete only when every set has been solved, and an adjoint given an
+ *            incomplete store fails with RG_ERR_ARG.
  * K must be strictly diagonally dominant (rows of F_NN sum to <= 1 and rho < 1), which
  * is what makes the factorisation without pivoting stable.
- * Limit: n <= 32768. Errors: RG_ERR_NOT_CONVERGED, RG_ERR_NUMERIC, RG_ERR_OOM. */
+ * Limit: n <= 32768. Errors: RG_ERR_ARG (also a factor store that is short or misaligned),
+ * RG_ERR_NOT_CONVERGED, RG_ERR_NUMERIC, RG_ERR_OOM. */
 rg_status rg_gebhart(rg_ctx* ctx, int32_t n, const double* F_d, int32_t n_sets, const double* eps_d,
                      const double* rho_d, int32_t precision, double tol, int32_t max_sweeps,
-                     double* B_d, int32_t* sweeps_out_h, double* resid_out_h, void* workspace_d,
-                     size_t workspace_bytes, void* stream);
+                     double* B_d, int32_t* sweeps_out_h, double* resid_out_h, void* factors_d,
+                     size_t factors_bytes, void* workspace_d, size_t workspace_bytes, void* stream);
 
 /* Adjoint of rg_gebhart: given dB = dL/dB, the gradients of L with respect to eps
- * and rho. It solves K^T Lambda = dB (a fresh factorisation of K^T, no stored
- * factors) and forms dL/deps_j = sum_i Lambda_ij F_ij and
+ * and rho. It solves K^T Lambda = dB and forms dL/deps_j = sum_i Lambda_ij F_ij and
  * dL/drho_k = sum_i F_ik (Lambda B^T)_ik.
  *   B_d, dB_d  device fp64 [n_sets][n][n+1];  deps_d, drho_d device fp64 [n_sets][n]
- * Errors as rg_gebhart. */
+ *   factors_d  NULL: K^T is factorised afresh for every set. Otherwise the factor store a
+ *              completed rg_gebhart call filled (factors_bytes its size) for the same n,
+ *              precision and at least n_sets sets, whose set s then stands in for the
+ *              factorisation of set s. Its header is read on the host (the call waits for
+ *              the stream once), so a store written on another stream must be ordered before
+ *              this call. The residual is refined exactly against this call's F and rho, so
+ *              the results do not depend on the store; factors of another system only slow
+ *              the sweeps (RG_ERR_NOT_CONVERGED when they no longer converge).
+ * Errors as rg_gebhart; RG_ERR_ARG for a store of another n, precision or fewer sets, or one
+ * that is short, misaligned or not filled. */
 rg_status rg_gebhart_adjoint(rg_ctx* ctx, int32_t n, const double* F_d, int32_t n_sets,
                              const double* eps_d, const double* rho_d, const double* B_d,
                              const double* dB_d, int32_t precision, double tol, int32_t max_sweeps,
-                             double* deps_d, double* drho_d, void* workspace_d, size_t workspace_bytes,
-                             void* stream);
+                             double* deps_d, double* drho_d, const void* factors_d, size_t factors_bytes,
+                             void* workspace_d, size_t workspace_bytes, void* stream);
 
 /* ---------------------------------------------------------------- radiative balance (P6) */
 
@@ -511,17 +530,18 @@ rg_status rg_temperatures_adjoint_sets(rg_ctx* ctx, int32_t n, const double* F_d
 
 /* rg_gebhart_adjoint for a cotangent given in factored form, dB = sum_r a_r b_r^T (for
  * instance the one rg_temperatures_adjoint_sets writes: rank 2). Lambda = K^-T dB =
- * sum_r x_r b_r^T with K^T x_r = a_r, so the transposed system (a fresh factorisation of K^T,
- * no stored factors, as rg_gebhart_adjoint) is solved for `rank` right-hand sides instead of
- * N+1, and (derived from Eq. B.11)
+ * sum_r x_r b_r^T with K^T x_r = a_r, so the transposed system (factorised afresh, or with the
+ * stored factors of rg_gebhart, as in rg_gebhart_adjoint) is solved for `rank` right-hand
+ * sides instead of N+1, and (derived from Eq. B.11)
  *   dL/deps_j = sum_r b_r,j (F^T x_r)_j,    dL/drho_k = sum_r (F^T x_r)_k (B b_r)_k.
  *   a_d  device fp64 [n_sets][rank][n];  b_d device fp64 [n_sets][rank][n+1];  1 <= rank <= 64
  * The other arguments and the errors as rg_gebhart_adjoint. */
 rg_status rg_gebhart_adjoint_factored(rg_ctx* ctx, int32_t n, const double* F_d, int32_t n_sets,
                                       const double* eps_d, const double* rho_d, const double* B_d, int32_t rank,
                                       const double* a_d, const double* b_d, int32_t precision, double tol,
-                                      int32_t max_sweeps, double* deps_d, double* drho_d, void* workspace_d,
-                                      size_t workspace_bytes, void* stream);
+                                      int32_t max_sweeps, double* deps_d, double* drho_d, const void* factors_d,
+                                      size_t factors_bytes, void* workspace_d, size_t workspace_bytes,
+                                      void* stream);
 
 /* ---------------------------------------------------------------- tensor-core GEMM */
 

@@ -242,13 +242,20 @@ def solver_workspace(kind: str, n: int, rank: int = 0) -> int:
 
 
 def gebhart_workspace(n: int, n_sets: int = 1, precision="bf16", keep_factors: bool = False) -> int:
-    """Bytes of caller-owned workspace rg_gebhart needs (rg_gebhart_workspace)."""
+    """Bytes of caller-owned workspace rg_gebhart needs, or with keep_factors the bytes of the
+    factor store it fills for the adjoints (rg_gebhart_workspace)."""
     out = ctypes.c_size_t(0)
     st = _native.load().rg_gebhart_workspace(int(n), int(n_sets), _prec(precision), int(bool(keep_factors)),
                                              ctypes.byref(out))
     if st != 0:
         raise RadgebError(st, f"rg_gebhart_workspace({n}, {n_sets})")
     return out.value
+
+
+def gebhart_factor_store(n: int, n_sets: int, precision="bf16", device=0) -> torch.Tensor:
+    """A device buffer (uint8) for the factors rg_gebhart keeps for the REF adjoints."""
+    nbytes = gebhart_workspace(n, n_sets, precision, keep_factors=True)
+    return torch.empty(nbytes, dtype=torch.uint8, device=torch.device("cuda", int(device)))
 
 
 def kernel_timer(ctx: Context, enable: bool):
@@ -404,8 +411,10 @@ def _prec(p):
 
 
 def gebhart(ctx: Context, F: torch.Tensor, eps: torch.Tensor, rho: torch.Tensor, precision="bf16",
-            tol: float = 1e-12, max_sweeps: int = 12, B: torch.Tensor | None = None, stream=None, ws=None):
-    """REFs of every (eps, rho) set (rg_gebhart) -> (B [S, N, N+1], sweeps, relative residual)."""
+            tol: float = 1e-12, max_sweeps: int = 12, B: torch.Tensor | None = None, stream=None, ws=None,
+            factors=None):
+    """REFs of every (eps, rho) set (rg_gebhart) -> (B [S, N, N+1], sweeps, relative residual).
+    factors: a store from gebhart_factor_store, filled for the adjoints (or None)."""
     n = F.shape[0]
     eps2 = eps.reshape(-1, n)
     S = eps2.shape[0]
@@ -417,13 +426,15 @@ def gebhart(ctx: Context, F: torch.Tensor, eps: torch.Tensor, rho: torch.Tensor,
                                  _dptr(eps2, torch.float64, "eps", S * n, ctx.device),
                                  _dptr(rho, torch.float64, "rho", S * n, ctx.device), _prec(precision), float(tol),
                                  int(max_sweeps), _dptr(B, torch.float64, "B", S * n * (n + 1), ctx.device),
-                                 ctypes.byref(sw), ctypes.byref(res), *_ws(ws, ctx.device), _stream(stream)), "rg_gebhart")
+                                 ctypes.byref(sw), ctypes.byref(res), *_ws(factors, ctx.device),
+                                 *_ws(ws, ctx.device), _stream(stream)), "rg_gebhart")
     return B, sw.value, res.value
 
 
 def gebhart_adjoint(ctx: Context, F, eps, rho, B, dB, precision="bf16", tol: float = 1e-12, max_sweeps: int = 12,
-                    stream=None, ws=None):
-    """(dL/deps, dL/drho) [S, N] from dB = dL/dB (rg_gebhart_adjoint)."""
+                    stream=None, ws=None, factors=None):
+    """(dL/deps, dL/drho) [S, N] from dB = dL/dB (rg_gebhart_adjoint); factors: the store a
+    gebhart call filled (or None: K^T is factorised afresh)."""
     n = F.shape[0]
     S = eps.numel() // n
     deps = torch.empty((S, n), dtype=torch.float64, device=F.device)
@@ -435,7 +446,8 @@ def gebhart_adjoint(ctx: Context, F, eps, rho, B, dB, precision="bf16", tol: flo
                                          _dptr(dB, torch.float64, "dB", S * n * (n + 1), ctx.device),
                                          _prec(precision), float(tol), int(max_sweeps),
                                          _dptr(deps, torch.float64, "deps"), _dptr(drho, torch.float64, "drho"),
-                                         *_ws(ws, ctx.device), _stream(stream)), "rg_gebhart_adjoint")
+                                         *_ws(factors, ctx.device), *_ws(ws, ctx.device), _stream(stream)),
+              "rg_gebhart_adjoint")
     return deps, drho
 
 
@@ -525,9 +537,9 @@ def temperatures_adjoint_sets(ctx: Context, F, B, eps, rho, area, T_sink: float,
 
 
 def gebhart_adjoint_factored(ctx: Context, F, eps, rho, B, a, b, precision="bf16", tol: float = 1e-12,
-                             max_sweeps: int = 12, stream=None, ws=None, deps=None, drho=None):
+                             max_sweeps: int = 12, stream=None, ws=None, deps=None, drho=None, factors=None):
     """(dL/deps, dL/drho) [S, N] for dL/dB = sum_r a_r b_r^T, a [S, r, N], b [S, r, N+1]
-    (rg_gebhart_adjoint_factored)."""
+    (rg_gebhart_adjoint_factored); factors as in gebhart_adjoint."""
     n = F.shape[0]
     S = eps.numel() // n
     rank = a.shape[-2]
@@ -542,7 +554,7 @@ def gebhart_adjoint_factored(ctx: Context, F, eps, rho, B, a, b, precision="bf16
         _dptr(a, torch.float64, "a", S * rank * n, ctx.device),
         _dptr(b, torch.float64, "b", S * rank * (n + 1), ctx.device), _prec(precision), float(tol), int(max_sweeps),
         _dptr(deps, torch.float64, "deps", S * n, ctx.device), _dptr(drho, torch.float64, "drho", S * n, ctx.device),
-        *_ws(ws, ctx.device), _stream(stream)), "rg_gebhart_adjoint_factored")
+        *_ws(factors, ctx.device), *_ws(ws, ctx.device), _stream(stream)), "rg_gebhart_adjoint_factored")
     return deps, drho
 
 

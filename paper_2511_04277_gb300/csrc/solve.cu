@@ -676,6 +676,7 @@ struct Solver {
   int ns_steps = 0;
   int splits = 1;    // K splits of the last exact product
   const BalancePre* pre = nullptr;  // set: corrections from the shared balance preconditioner
+  const void* minv = nullptr;       // set: a stored inverse (16-bit np x np, row-major) replaces factor()
 
   unsigned long long* red(int parity) { return reinterpret_cast<unsigned long long*>(err + 10 + 6 * parity); }
 
@@ -843,7 +844,7 @@ struct Solver {
                                                           g, rc, b.dcolmax);
       ++ctx->launches;
       RG_CUDA_TRY(ctx, cudaGetLastError());
-      st = tc::gemm(ctx, bf16, b.X16[cur], L.np, Rt, L.np, L.n, L.m, L.np,
+      st = tc::gemm(ctx, bf16, minv ? minv : b.X16[cur], L.np, Rt, L.np, L.n, L.m, L.np,
                     tc::EpiCorrection{b.Dbuf, L.mp, b.colscale, b.dcolmax, err + 1}, s, skip);
       if (st != RG_OK) return st;
     }
@@ -899,7 +900,14 @@ struct Solver {
   // fixed-point slices of P' are rebuilt when `slices` (they depend on dr).
   rg_status run(const double* dl, const double* dr, double tol, int max_sweeps, int* sweeps, double* rel_out,
                 bool slices = true) {
-    rg_status st = factor(dl, dr);
+    rg_status st = RG_OK;
+    if (minv) {
+      // the stored inverse stands in for the factorisation; refine() wants the column maxima
+      // zeroed, which the factorisation's norm kernel does otherwise
+      RG_CUDA_TRY(ctx, cudaMemsetAsync(b.colmax, 0, L.mp * sizeof(unsigned long long), s));
+    } else {
+      st = factor(dl, dr);
+    }
     if (st == RG_OK && slices) st = build_slices(dr);
     if (st != RG_OK) return st;
     return refine(dl, tol, max_sweeps, sweeps, rel_out);
@@ -950,6 +958,63 @@ struct Solver {
     return RG_OK;
   }
 };
+
+// ------------------------------------------------------------------ stored factors
+// The factor store rg_gebhart fills for the REF adjoints: a header, then per set the
+// transpose of that set's Newton-Schulz inverse M of K = I - F diag(rho) (16-bit np x np,
+// row-major). K^T = I - diag(rho) F^T is K transposed, and M is a polynomial in K, so M^T is
+// as good an inverse of K^T as M is of K; stored transposed it is the correction GEMM's
+// operand as it stands. The refinement computes its residual exactly, so a stored inverse
+// decides only how fast the sweeps converge, never what they converge to.
+constexpr uint32_t kFactorMagic = 0x31464752u;  // "RGF1"
+constexpr size_t kFactorHeader = 256;
+struct FactorHeader {
+  uint32_t magic;
+  int32_t n, n_sets, precision, np, filled;
+};
+
+size_t factor_store_bytes(int n, int n_sets) {
+  const size_t np = (size_t)(n + NB - 1) / NB * NB;
+  return kFactorHeader + (size_t)n_sets * np * np * sizeof(uint16_t);
+}
+
+void* factor_slice(const void* store, int n, int set) {
+  const size_t np = (size_t)(n + NB - 1) / NB * NB;
+  return static_cast<char*>(const_cast<void*>(store)) + kFactorHeader + (size_t)set * np * np * sizeof(uint16_t);
+}
+
+__global__ void write_factor_header(FactorHeader* h, FactorHeader v) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) *h = v;
+}
+
+rg_status check_store_layout(rg_ctx* ctx, const void* store, size_t bytes, int n, int n_sets, const char* fn) {
+  if (reinterpret_cast<uintptr_t>(store) & 255)
+    return rg::fail(ctx, RG_ERR_ARG, "%s: the factor store must be 256-byte aligned", fn);
+  if (bytes < factor_store_bytes(n, n_sets))
+    return rg::fail(ctx, RG_ERR_ARG, "%s: the factor store holds %zu bytes, %d sets of n = %d need %zu", fn, bytes,
+                    n_sets, n, factor_store_bytes(n, n_sets));
+  return RG_OK;
+}
+
+// Reads the store's header and checks that it holds factors of n unknowns, in `precision`
+// (the inverse is an operand of a GEMM whose other operand has that type), for n_sets sets.
+rg_status check_stored_factors(rg_ctx* ctx, const void* store, size_t bytes, int n, int n_sets, int precision,
+                               cudaStream_t s, const char* fn) {
+  rg_status st = check_store_layout(ctx, store, bytes, n, n_sets, fn);
+  if (st != RG_OK) return st;
+  FactorHeader h;
+  RG_CUDA_TRY(ctx, cudaMemcpyAsync(ctx->h_scratch, store, sizeof(h), cudaMemcpyDeviceToHost, s));
+  RG_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+  memcpy(&h, ctx->h_scratch, sizeof(h));
+  if (h.magic != kFactorMagic || h.n != n || h.np != (n + NB - 1) / NB * NB)
+    return rg::fail(ctx, RG_ERR_ARG, "%s: the factor store holds no factors of an n = %d system", fn, n);
+  if (h.precision != precision)
+    return rg::fail(ctx, RG_ERR_ARG, "%s: the factors were made in precision %d, the call asks for %d", fn,
+                    h.precision, precision);
+  if (h.filled < n_sets)
+    return rg::fail(ctx, RG_ERR_ARG, "%s: the factor store holds %d sets, the call has %d", fn, h.filled, n_sets);
+  return RG_OK;
+}
 
 // ------------------------------------------------------------------ problem-specific kernels
 // R0 = [F_NN diag(eps) | F_inf] (ld = mp), zero padding rows are never read.
@@ -1353,12 +1418,16 @@ rg_status rg_exact_split(rg_ctx* ctx, int32_t n, const double* P_d, int64_t ldp,
 
 rg_status rg_gebhart(rg_ctx* ctx, int32_t n, const double* F_d, int32_t n_sets, const double* eps_d,
                      const double* rho_d, int32_t precision, double tol, int32_t max_sweeps, double* B_d,
-                     int32_t* sweeps_out_h, double* resid_out_h, void* workspace_d, size_t workspace_bytes,
-                     void* stream) {
+                     int32_t* sweeps_out_h, double* resid_out_h, void* factors_d, size_t factors_bytes,
+                     void* workspace_d, size_t workspace_bytes, void* stream) {
   if (!ctx) return RG_ERR_ARG;
   rg_status st = check_common(ctx, n, precision, tol, max_sweeps);
   if (st != RG_OK) return st;
   RG_ARG_CHECK(ctx, F_d && eps_d && rho_d && B_d && n_sets > 0, "rg_gebhart: bad argument");
+  if (factors_d) {
+    st = check_store_layout(ctx, factors_d, factors_bytes, n, n_sets, "rg_gebhart");
+    if (st != RG_OK) return st;
+  }
   RG_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
   cudaStream_t s = (cudaStream_t)stream;
   Solver sv{ctx};
@@ -1368,12 +1437,26 @@ rg_status rg_gebhart(rg_ctx* ctx, int32_t n, const double* F_d, int32_t n_sets, 
   if (st != RG_OK) return st;
   int max_sw = 0;
   double max_rel = 0.0;
+  // the header says "no sets" until every set has been factorised
+  auto header = [&](int filled) -> rg_status {
+    if (!factors_d) return RG_OK;
+    const FactorHeader h{kFactorMagic, n, n_sets, precision, sv.L.np, filled};
+    write_factor_header<<<1, 32, 0, s>>>(static_cast<FactorHeader*>(factors_d), h);
+    ++ctx->launches;
+    RG_CUDA_TRY(ctx, cudaGetLastError());
+    return RG_OK;
+  };
+  st = header(0);
+  if (st != RG_OK) return st;
   for (int set = 0; set < n_sets; ++set) {
     const double* eps = eps_d + (size_t)set * n;
     const double* rho = rho_d + (size_t)set * n;
     gebhart_rhs<<<grid_for((int64_t)n * (n + 1), ctx->sm_count), kThreads, 0, s>>>(F_d, eps, n, sv.L.mp, sv.b.R0);
     ++ctx->launches;
     RG_CUDA_TRY(ctx, cudaGetLastError());
+    // the factorisation keeps the transpose of its iterate in b.Xt16: with a store, that is
+    // the set's slice of the store, which then holds M^T when the set is done
+    if (factors_d) sv.b.Xt16 = factor_slice(factors_d, n, set);
     int sw = 0;
     double rel = 0.0;
     st = sv.run(nullptr, rho, tol, max_sweeps, &sw, &rel);
@@ -1392,13 +1475,13 @@ rg_status rg_gebhart(rg_ctx* ctx, int32_t n, const double* F_d, int32_t n_sets, 
   }
   if (sweeps_out_h) *sweeps_out_h = max_sw;
   if (resid_out_h) *resid_out_h = max_rel;
-  return RG_OK;
+  return header(n_sets);
 }
 
 rg_status rg_gebhart_adjoint(rg_ctx* ctx, int32_t n, const double* F_d, int32_t n_sets, const double* eps_d,
                              const double* rho_d, const double* B_d, const double* dB_d, int32_t precision,
-                             double tol, int32_t max_sweeps, double* deps_d, double* drho_d, void* workspace_d,
-                             size_t workspace_bytes, void* stream) {
+                             double tol, int32_t max_sweeps, double* deps_d, double* drho_d, const void* factors_d,
+                             size_t factors_bytes, void* workspace_d, size_t workspace_bytes, void* stream) {
   if (!ctx) return RG_ERR_ARG;
   rg_status st = check_common(ctx, n, precision, tol, max_sweeps);
   if (st != RG_OK) return st;
@@ -1406,6 +1489,10 @@ rg_status rg_gebhart_adjoint(rg_ctx* ctx, int32_t n, const double* F_d, int32_t 
                "rg_gebhart_adjoint: bad argument");
   RG_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
   cudaStream_t s = (cudaStream_t)stream;
+  if (factors_d) {
+    st = check_stored_factors(ctx, factors_d, factors_bytes, n, n_sets, precision, s, "rg_gebhart_adjoint");
+    if (st != RG_OK) return st;
+  }
   Solver sv{ctx};
   // K^T = I - diag(rho) F_NN^T: P' = F^T for every set; the refinement also accumulates
   // Q = F^T Lambda (the sum of its exact products), which the rho gradient needs
@@ -1420,6 +1507,7 @@ rg_status rg_gebhart_adjoint(rg_ctx* ctx, int32_t n, const double* F_d, int32_t 
                                                                                 sv.b.R0, sv.L.mp);
     ++ctx->launches;
     RG_CUDA_TRY(ctx, cudaGetLastError());
+    if (factors_d) sv.minv = factor_slice(factors_d, n, set);
     int sw = 0;
     double rel = 0.0;
     st = sv.run(rho, nullptr, tol, max_sweeps, &sw, &rel, set == 0);
@@ -1615,8 +1703,8 @@ rg_status rg_temperatures_adjoint_sets(rg_ctx* ctx, int32_t n, const double* F_d
 rg_status rg_gebhart_adjoint_factored(rg_ctx* ctx, int32_t n, const double* F_d, int32_t n_sets,
                                       const double* eps_d, const double* rho_d, const double* B_d, int32_t rank,
                                       const double* a_d, const double* b_d, int32_t precision, double tol,
-                                      int32_t max_sweeps, double* deps_d, double* drho_d, void* workspace_d,
-                                      size_t workspace_bytes, void* stream) {
+                                      int32_t max_sweeps, double* deps_d, double* drho_d, const void* factors_d,
+                                      size_t factors_bytes, void* workspace_d, size_t workspace_bytes, void* stream) {
   if (!ctx) return RG_ERR_ARG;
   rg_status st = check_common(ctx, n, precision, tol, max_sweeps);
   if (st != RG_OK) return st;
@@ -1625,6 +1713,10 @@ rg_status rg_gebhart_adjoint_factored(rg_ctx* ctx, int32_t n, const double* F_d,
                "rg_gebhart_adjoint_factored: bad argument");
   RG_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
   cudaStream_t s = (cudaStream_t)stream;
+  if (factors_d) {
+    st = check_stored_factors(ctx, factors_d, factors_bytes, n, n_sets, precision, s, "rg_gebhart_adjoint_factored");
+    if (st != RG_OK) return st;
+  }
   Solver sv{ctx};
   // K^T X = A (rank right-hand sides), P' = F^T for every set, Q = F^T X accumulated
   st = sv.setup(n, rank, precision == RG_PREC_BF16_IR, s, 0, nullptr, true, workspace_d, workspace_bytes,
@@ -1636,6 +1728,7 @@ rg_status rg_gebhart_adjoint_factored(rg_ctx* ctx, int32_t n, const double* F_d,
     factors_in<<<(n + 255) / 256, 256, 0, s>>>(a_d + (size_t)set * rank * n, rank, n, sv.b.R0, sv.L.mp);
     ++ctx->launches;
     RG_CUDA_TRY(ctx, cudaGetLastError());
+    if (factors_d) sv.minv = factor_slice(factors_d, n, set);
     int sw = 0;
     double rel = 0.0;
     st = sv.run(rho, nullptr, tol, max_sweeps, &sw, &rel, set == 0);
@@ -1670,7 +1763,11 @@ rg_status rg_solver_workspace(int32_t kind, int32_t n, int32_t rank, size_t* byt
 
 rg_status rg_gebhart_workspace(int32_t n, int32_t n_sets, int32_t precision, int32_t keep_factors, size_t* bytes_out) {
   if (!bytes_out || n_sets <= 0 || (precision != RG_PREC_BF16_IR && precision != RG_PREC_FP16_IR)) return RG_ERR_ARG;
-  if (keep_factors) return RG_ERR_UNSUPPORTED;  // the solves never keep factors between calls
+  if (n <= 0 || n > 32768) return RG_ERR_ARG;
+  if (keep_factors) {
+    *bytes_out = factor_store_bytes(n, n_sets);
+    return RG_OK;
+  }
   return rg_solver_workspace(RG_WS_GEBHART, n, 0, bytes_out);
 }
 

@@ -1,7 +1,7 @@
 """Dense solves in a caller-owned workspace (the boundary's ownership rule: the caller owns
 every device buffer). On a fresh context, every dense-solve call run with a workspace of
 the queried size gives the same bits as the context-workspace call and leaves the context
-holding no workspace; a short or misaligned workspace and keep_factors are refused."""
+holding no workspace; a short or misaligned workspace is refused."""
 import numpy as np
 import pytest
 import torch
