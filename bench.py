@@ -1191,6 +1191,7 @@ class _RandomSystem:
         self.ones = torch.ones(n, dtype=torch.float64, device=device)
         f64 = dict(dtype=torch.float64, device=device)
         self.B = torch.empty((n_sets, n, n + 1), **f64)
+        self.factors = api.gebhart_factor_store(n, n_sets, SOLVE_PRECISION, device=torch.device(device).index or 0)
         self.dB_a = torch.empty((n_sets, 2, n), **f64)
         self.dB_b = torch.empty((n_sets, 2, n + 1), **f64)
         self.T = torch.empty((n_sets, n), **f64)

@@ -84,6 +84,10 @@ __device__ __forceinline__ double scale2(double x, int k) {
   return ldexp(x, k);
 }
 
+// int_scale2 for results outside the normal range, out of line so that its fp64 arithmetic
+// stays off the common path.
+__device__ __noinline__ double int_scale2_outside(long long q, int k) { return scale2((double)q, k); }
+
 // q 2^k for an integer q (|q| < 2^63), rounded to nearest, ties to even, when q needs more
 // than 53 bits: the same double as scale2((double)q, k), formed with integer operations
 // (GB300 runs fp64 arithmetic and conversions on a pipe far slower than its integer ALU).
@@ -103,7 +107,7 @@ __device__ __forceinline__ double int_scale2(long long q, int k) {
       ++e;
     }
   }
-  if (e < -1022 || e > 1023) return scale2((double)q, k);
+  if (e < -1022 || e > 1023) return int_scale2_outside(q, k);
   return __longlong_as_double((long long)(sgn | ((unsigned long long)(e + 1023) << 52) | (mant & 0xfffffffffffffull)));
 }
 
@@ -188,54 +192,88 @@ __global__ void build_p_exact(const double* __restrict__ P, int64_t ldp, bool tr
 // [-127, 127]. Writes Bq[j][k] = d (bf16, the exact product's B operand, zero in the padding),
 // Dn[k][j] = d, dexp[j] = f_j and adds d 2^(f_j - 7) to X (first: X = that); folds max|X| into
 // red[1], max_j colmax_j into red[2] (as doubles; both zeroed by the sweep's first kernel) and
-// zeroes the column maxima of R for the residual that follows. Tiled transpose, block (32 x 8).
+// zeroes the column maxima of R for the residual that follows. Block (32 x 8) per 64 rows x 64
+// columns, two columns per lane (8- and 16-byte loads), the transposed rows written as bf16
+// pairs through shared memory; the one fp64 operation per entry is the addition to X.
 __global__ void quantize_correction(const float* __restrict__ D, int n, int m, int np, int mp,
                                     const unsigned int* __restrict__ dcolmax, __nv_bfloat16* __restrict__ Bq,
                                     int16_t* __restrict__ Dn, int* __restrict__ dexp, double* __restrict__ X,
                                     int first, unsigned long long* red, unsigned long long* rcolmax, int* nonfinite,
                                     const int* skip) {
   if (skip && *(volatile const int*)skip) return;
-  __shared__ __nv_bfloat16 tile[32][34];
+  __shared__ __align__(16) __nv_bfloat16 tile[64][66];  // [column][row]
   __shared__ unsigned long long s_xmax;
   if (threadIdx.x == 0 && threadIdx.y == 0) s_xmax = 0ull;
-  const int k0 = blockIdx.y * 32, j0 = blockIdx.x * 32;
-  const int j = j0 + threadIdx.x;
-  const unsigned int cb = j < m ? dcolmax[j] : 0u;
-  const bool cfin = cb < 0x7f800000u;
-  int f = 0;
-  if (cb != 0u && cfin) f = frexp_exponent((double)__uint_as_float(cb));
-  const float sc = ldexpf(1.f, 7 - f);
-  if (blockIdx.y == 0 && threadIdx.y == 0) {
-    if (j < mp) {
-      dexp[j] = f;
-      rcolmax[j] = 0ull;
+  const int k0 = blockIdx.y * 64, j0 = blockIdx.x * 64;
+  const int jl = 2 * threadIdx.x, j = j0 + jl;  // this lane's columns j, j + 1
+  int f[2];
+  float sc[2];
+#pragma unroll
+  for (int c = 0; c < 2; ++c) {
+    const unsigned int cb = j + c < m ? dcolmax[j + c] : 0u;
+    const bool cfin = cb < 0x7f800000u;
+    f[c] = 0;
+    if (cb != 0u && cfin) f[c] = (int)(cb >> 23) != 0 ? (int)(cb >> 23) - 126 : (31 - __clz((int)cb)) - 148;
+    sc[c] = ldexpf(1.f, 7 - f[c]);
+    if (blockIdx.y == 0 && threadIdx.y == 0) {
+      if (j + c < mp) {
+        dexp[j + c] = f[c];
+        rcolmax[j + c] = 0ull;
+      }
+      if (j + c < m && cfin && cb) atomicMax(&red[2], (unsigned long long)__double_as_longlong((double)__uint_as_float(cb)));
+      if (j + c < m && !cfin) atomicExch(nonfinite, 1);
     }
-    if (j < m && cfin) atomicMax(&red[2], (unsigned long long)__double_as_longlong((double)__uint_as_float(cb)));
-    if (j < m && !cfin) atomicExch(nonfinite, 1);
   }
   __syncthreads();
   unsigned long long xmax = 0ull;
-  for (int r = threadIdx.y; r < 32; r += 8) {
-    const int k = k0 + r;
-    const bool in = k < n && j < m;
-    int q = 0;
-    if (in) {
-      q = __float2int_rn(D[(int64_t)k * mp + j] * sc);
-      q = q > 127 ? 127 : (q < -127 ? -127 : q);
+  const bool c1 = j + 1 < m;
+  if (j < m) {
+#pragma unroll 4
+    for (int r = 0; r < 8; ++r) {
+      const int k = k0 + threadIdx.y + 8 * r;
+      if (k >= n) break;
       const int64_t o = (int64_t)k * mp + j;
-      Dn[o] = (int16_t)q;
-      const double dv = int_scale2(q, f - 7);
-      const double v = first ? dv : X[o] + dv;
-      X[o] = v;
-      xmax = max(xmax, (unsigned long long)__double_as_longlong(fabs(v)) & 0x7fffffffffffffffull);
+      const float2 dv = *reinterpret_cast<const float2*>(D + o);
+      int q0 = __float2int_rn(dv.x * sc[0]), q1 = c1 ? __float2int_rn(dv.y * sc[1]) : 0;
+      q0 = q0 > 127 ? 127 : (q0 < -127 ? -127 : q0);
+      q1 = q1 > 127 ? 127 : (q1 < -127 ? -127 : q1);
+      *reinterpret_cast<uint32_t*>(Dn + o) = (uint32_t)(uint16_t)(int16_t)q0 | ((uint32_t)(uint16_t)(int16_t)q1 << 16);
+      double2 xv = first ? make_double2(0.0, 0.0) : *reinterpret_cast<const double2*>(X + o);
+      if (!c1) xv.y = 0.0;  // column m is padding
+      xv.x += int_scale2(q0, f[0] - 7);
+      xv.y += int_scale2(q1, f[1] - 7);
+      if (c1) {
+        *reinterpret_cast<double2*>(X + o) = xv;
+      } else {
+        X[o] = xv.x;
+      }
+      xmax = max(xmax, (unsigned long long)__double_as_longlong(xv.x) & 0x7fffffffffffffffull);
+      xmax = max(xmax, (unsigned long long)__double_as_longlong(xv.y) & 0x7fffffffffffffffull);
+      tile[jl][threadIdx.y + 8 * r] = __float2bfloat16_rz((float)q0);
+      tile[jl + 1][threadIdx.y + 8 * r] = __float2bfloat16_rz((float)q1);
     }
-    tile[r][threadIdx.x] = __float2bfloat16_rz((float)q);
   }
-  atomicMax(&s_xmax, xmax);
+  // rows k >= n and columns j >= m are zero in Bq
+#pragma unroll
+  for (int r = 0; r < 8; ++r) {
+    const int kl = threadIdx.y + 8 * r;
+    if (j >= m || k0 + kl >= n) {
+      tile[jl][kl] = __float2bfloat16_rz(0.f);
+      tile[jl + 1][kl] = __float2bfloat16_rz(0.f);
+    } else if (!c1) {
+      tile[jl + 1][kl] = __float2bfloat16_rz(0.f);
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) xmax = max(xmax, __shfl_xor_sync(0xffffffffu, xmax, o));
+  if (threadIdx.x == 0 && xmax) atomicMax(&s_xmax, xmax);
   __syncthreads();
-  for (int r = threadIdx.y; r < 32; r += 8) {
-    const int jj = j0 + r, kk = k0 + threadIdx.x;
-    if (jj < mp && kk < np) Bq[(int64_t)jj * np + kk] = tile[threadIdx.x][r];
+  // warp w writes columns j0 + w + 8 c, lane l the rows k0 + 2 l, k0 + 2 l + 1
+  const int kk = k0 + 2 * threadIdx.x;
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    const int cl = threadIdx.y + 8 * c, jj = j0 + cl;
+    if (jj < mp && kk < np)
+      *reinterpret_cast<uint32_t*>(Bq + (int64_t)jj * np + kk) = *reinterpret_cast<const uint32_t*>(&tile[cl][2 * threadIdx.x]);
   }
   if (threadIdx.x == 0 && threadIdx.y == 0 && s_xmax) atomicMax(&red[1], s_xmax);
 }
@@ -243,25 +281,181 @@ __global__ void quantize_correction(const float* __restrict__ D, int n, int m, i
 // The residual update after the exact product: with S = P' D assembled from the integer level
 // sums (T = sum_z sum_a lev[z][a] 256^(L - 1 - a), S_ij = T 2^(e_i + f_j - 14 - 8(L - 1))),
 //   R_ij <- (first ? R0_ij : R_ij) - D_ij + dl_i S_ij,   D_ij = Dn_ij 2^(f_j - 7),
-// and, with Q, Q_ij <- (first ? 0 : Q_ij) + S_ij. Folds max|R| into red[0], max_i |R_ij| into
-// colmax[j] (as doubles) and raises *nonfinite on an inf or NaN. Block (32 x 8) per 32 columns
-// x 32 rows.
-__global__ void finish_residual(const int32_t* __restrict__ lev, int64_t ldl, int64_t plane, int splits,
-                                const int* __restrict__ rowexp, const int* __restrict__ dexp,
-                                const int16_t* __restrict__ Dn, const double* __restrict__ dl, int n, int m, int mp,
-                                const double* __restrict__ R0, double* __restrict__ R, double* __restrict__ Q,
-                                int first, unsigned long long* red, unsigned long long* colmax, int* nonfinite,
-                                const int* skip) {
+// and, with Q, Q_ij <- (first ? 0 : Q_ij) + S_ij. Without dl and Q, S - D = (T - Dn 2^sh) 2^a
+// with sh = 7 - e_i + 8(L - 1) is formed exactly in int64 (|T| < 2^61.01 and |Dn 2^sh| < 2^60
+// for e_i >= -14, so the difference fits) and rounded once, leaving one fp64 addition per
+// entry (GB300's fp64 pipe issues about 2 lanes per clock per SM). Folds max|R| into red[0],
+// max_i |R_ij| into colmax[j] (as doubles) and raises *nonfinite on an inf or NaN.
+// Block (32 x 8) per 128 columns x 128 rows: lane l owns the block's columns 4 l .. 4 l + 3
+// (16-byte loads of the level sums, the residual and Dn), warp w the rows w, w + 8, ...
+__global__ void __launch_bounds__(256, 3) finish_residual(
+    const int32_t* __restrict__ lev, int64_t ldl, int64_t plane, int splits, const int* __restrict__ rowexp,
+    const int* __restrict__ dexp, const int16_t* __restrict__ Dn, const double* __restrict__ dl, int n, int m, int mp,
+    const double* __restrict__ R0, double* __restrict__ R, double* __restrict__ Q, int first, unsigned long long* red,
+    unsigned long long* colmax, int* nonfinite, const int* skip) {
   if (skip && *(volatile const int*)skip) return;
-  __shared__ unsigned long long s_col[8][33];
+  __shared__ unsigned long long s_col[8][128];
   const int L = exact_levels(red);
-  const int j = blockIdx.x * 32 + threadIdx.x;
-  const int i0 = blockIdx.y * 32;
-  unsigned long long cmax = 0ull;
+  const int jb = blockIdx.x * 128, j = jb + 4 * threadIdx.x;
+  const int i0 = blockIdx.y * 128;
+  const double* src = first ? R0 : R;
+  const bool plain = !dl && !Q;
+  unsigned long long cmax[4] = {0ull, 0ull, 0ull, 0ull};
   bool bad = false;
   if (j < m) {
-    const int f = dexp[j];
-    for (int i = i0 + threadIdx.y; i < min(n, i0 + 32); i += 8) {
+    const int4 fv = *reinterpret_cast<const int4*>(dexp + j);  // dexp holds mp >= j + 4 entries
+    const int f[4] = {fv.x, fv.y, fv.z, fv.w};
+    const int nc = min(4, m - j);  // valid columns of this lane
+#pragma unroll 1
+    for (int i = i0 + threadIdx.y; i < min(n, i0 + 128); i += 8) {
+      const int64_t o = (int64_t)i * ldl + j;
+      long long T[4] = {0ll, 0ll, 0ll, 0ll};
+      for (int z = 0; z < splits; ++z) {
+        int4 lv[kLevels];
+#pragma unroll
+        for (int a = 0; a < kLevels; ++a)
+          lv[a] = a < L ? *reinterpret_cast<const int4*>(lev + ((int64_t)z * kLevels + a) * plane + o)
+                        : make_int4(0, 0, 0, 0);
+        long long t[4] = {0ll, 0ll, 0ll, 0ll};
+#pragma unroll
+        for (int a = 0; a < kLevels; ++a)
+          if (a < L) {
+            t[0] = t[0] * 256 + lv[a].x;
+            t[1] = t[1] * 256 + lv[a].y;
+            t[2] = t[2] * 256 + lv[a].z;
+            t[3] = t[3] * 256 + lv[a].w;
+          }
+#pragma unroll
+        for (int c = 0; c < 4; ++c) T[c] += t[c];
+      }
+      const int64_t e = (int64_t)i * mp + j;
+      const double2 s01 = *reinterpret_cast<const double2*>(src + e);
+      const double2 s23 = *reinterpret_cast<const double2*>(src + e + 2);
+      const uint2 dnv = *reinterpret_cast<const uint2*>(Dn + e);
+      const double sv[4] = {s01.x, s01.y, s23.x, s23.y};
+      const int dn[4] = {(int)(int16_t)(dnv.x & 0xffffu), (int)(int16_t)(dnv.x >> 16), (int)(int16_t)(dnv.y & 0xffffu),
+                         (int)(int16_t)(dnv.y >> 16)};
+      const int re = rowexp[i];
+      const int sh = 7 - re + 8 * (L - 1);
+      double r[4];
+      if (plain && re >= -14 && sh >= 0) {  // warp-uniform: the warp shares row i
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          const long long U = T[c] - (long long)((unsigned long long)(long long)dn[c] << sh);
+          r[c] = sv[c] + int_scale2(U, re + f[c] - 14 - 8 * (L - 1));
+        }
+      } else {
+        const double w = dl ? dl[i] : 1.0;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          const double S = int_scale2(T[c], re + f[c] - 14 - 8 * (L - 1));
+          r[c] = (sv[c] - int_scale2(dn[c], f[c] - 7)) + w * S;
+          if (Q && c < nc) Q[e + c] = (first ? 0.0 : Q[e + c]) + S;
+        }
+      }
+      if (nc == 4) {
+        *reinterpret_cast<double2*>(R + e) = make_double2(r[0], r[1]);
+        *reinterpret_cast<double2*>(R + e + 2) = make_double2(r[2], r[3]);
+      } else {
+        for (int c = 0; c < nc; ++c) R[e + c] = r[c];
+      }
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const unsigned long long rb = (unsigned long long)__double_as_longlong(r[c]) & 0x7fffffffffffffffull;
+        const bool fin = rb < 0x7ff0000000000000ull;
+        if (c < nc) {
+          bad |= !fin;
+          cmax[c] = max(cmax[c], fin ? rb : 0ull);
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < 4; ++c) s_col[threadIdx.y][4 * threadIdx.x + c] = cmax[c];
+  if (__syncthreads_or(bad) && threadIdx.x == 0 && threadIdx.y == 0) atomicExch(nonfinite, 1);
+  const int tid = threadIdx.y * 32 + threadIdx.x;
+  if (tid < 128) {  // warps 0 .. 3: one column each
+    unsigned long long cm = s_col[0][tid];
+#pragma unroll
+    for (int y = 1; y < 8; ++y) cm = max(cm, s_col[y][tid]);
+    if (jb + tid < m && cm) atomicMax(&colmax[jb + tid], cm);
+    for (int o = 16; o > 0; o >>= 1) cm = max(cm, __shfl_xor_sync(0xffffffffu, cm, o));
+    if (threadIdx.x == 0 && cm) atomicMax(&red[0], cm);
+  }
+}
+
+// ------------------------------------------------------------------ narrow systems
+// quantize_correction and finish_residual for m <= kNarrow right-hand sides (the balance's one
+// column, a factored cotangent's few): one thread per row and a loop over the columns, so
+// that no lane idles on a column that does not exist; the same arithmetic and status words.
+// The B operands' rows j >= m (Bq, Rt16) are left unwritten: the GEMMs read N = m rows.
+constexpr int kNarrow = 8;
+
+__global__ void __launch_bounds__(256) quantize_correction_narrow(
+    const float* __restrict__ D, int n, int m, int np, int mp, const unsigned int* __restrict__ dcolmax,
+    __nv_bfloat16* __restrict__ Bq, int16_t* __restrict__ Dn, int* __restrict__ dexp, double* __restrict__ X,
+    int first, unsigned long long* red, unsigned long long* rcolmax, int* nonfinite, const int* skip) {
+  if (skip && *(volatile const int*)skip) return;
+  __shared__ unsigned long long s_xmax;
+  if (threadIdx.x == 0) s_xmax = 0ull;
+  const int k = blockIdx.x * 256 + threadIdx.x;
+  if (blockIdx.x == 0 && threadIdx.x < mp) {
+    rcolmax[threadIdx.x] = 0ull;
+    if (threadIdx.x >= m) dexp[threadIdx.x] = 0;
+  }
+  unsigned long long xmax = 0ull;
+#pragma unroll
+  for (int j = 0; j < kNarrow; ++j) {
+    if (j >= m) break;
+    const unsigned int cb = dcolmax[j];
+    const bool cfin = cb < 0x7f800000u;
+    int f = 0;
+    if (cb != 0u && cfin) f = (int)(cb >> 23) != 0 ? (int)(cb >> 23) - 126 : (31 - __clz((int)cb)) - 148;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      dexp[j] = f;
+      if (cfin && cb) atomicMax(&red[2], (unsigned long long)__double_as_longlong((double)__uint_as_float(cb)));
+      if (!cfin) atomicExch(nonfinite, 1);
+    }
+    int q = 0;
+    if (k < n) {
+      const int64_t o = (int64_t)k * mp + j;
+      q = __float2int_rn(D[o] * ldexpf(1.f, 7 - f));
+      q = q > 127 ? 127 : (q < -127 ? -127 : q);
+      Dn[o] = (int16_t)q;
+      const double v = (first ? 0.0 : X[o]) + int_scale2(q, f - 7);
+      X[o] = v;
+      xmax = max(xmax, (unsigned long long)__double_as_longlong(v) & 0x7fffffffffffffffull);
+    }
+    if (k < np) Bq[(int64_t)j * np + k] = __float2bfloat16_rz((float)q);
+  }
+  for (int o = 16; o > 0; o >>= 1) xmax = max(xmax, __shfl_xor_sync(0xffffffffu, xmax, o));
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0 && xmax) atomicMax(&s_xmax, xmax);
+  __syncthreads();
+  if (threadIdx.x == 0 && s_xmax) atomicMax(&red[1], s_xmax);
+}
+
+__global__ void __launch_bounds__(256) finish_residual_narrow(
+    const int32_t* __restrict__ lev, int64_t ldl, int64_t plane, int splits, const int* __restrict__ rowexp,
+    const int* __restrict__ dexp, const int16_t* __restrict__ Dn, const double* __restrict__ dl, int n, int m, int mp,
+    const double* __restrict__ R0, double* __restrict__ R, double* __restrict__ Q, int first, unsigned long long* red,
+    unsigned long long* colmax, int* nonfinite, const int* skip) {
+  if (skip && *(volatile const int*)skip) return;
+  __shared__ unsigned long long s_col[8][kNarrow];
+  const int L = exact_levels(red);
+  const int i = blockIdx.x * 256 + threadIdx.x;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const double* src = first ? R0 : R;
+  unsigned long long cmax[kNarrow];
+  bool bad = false;
+  const int re = i < n ? rowexp[i] : 0;
+  const int sh = 7 - re + 8 * (L - 1);
+  const bool fast = !dl && !Q && re >= -14 && sh >= 0;
+  const double w = (dl && i < n) ? dl[i] : 1.0;
+#pragma unroll
+  for (int j = 0; j < kNarrow; ++j) {
+    cmax[j] = 0ull;
+    if (j < m && i < n) {
       const int64_t o = (int64_t)i * ldl + j;
       long long T = 0;
       for (int z = 0; z < splits; ++z) {
@@ -274,47 +468,46 @@ __global__ void finish_residual(const int32_t* __restrict__ lev, int64_t ldl, in
           if (a < L) t = t * 256 + lv[a];
         T += t;
       }
-      const double S = int_scale2(T, rowexp[i] + f - 14 - 8 * (L - 1));
       const int64_t e = (int64_t)i * mp + j;
-      const double d = int_scale2(Dn[e], f - 7);
-      const double r = ((first ? R0[e] : R[e]) - d) + (dl ? dl[i] : 1.0) * S;
+      const int f = dexp[j], dn = Dn[e];
+      const int ex = re + f - 14 - 8 * (L - 1);
+      double r;
+      if (fast) {
+        r = src[e] + int_scale2(T - (long long)((unsigned long long)(long long)dn << sh), ex);
+      } else {
+        const double S = int_scale2(T, ex);
+        r = (src[e] - int_scale2(dn, f - 7)) + w * S;
+        if (Q) Q[e] = (first ? 0.0 : Q[e]) + S;
+      }
       R[e] = r;
-      if (Q) Q[e] = (first ? 0.0 : Q[e]) + S;
       const unsigned long long rb = (unsigned long long)__double_as_longlong(r) & 0x7fffffffffffffffull;
-      bad |= rb >= 0x7ff0000000000000ull;
-      cmax = max(cmax, rb >= 0x7ff0000000000000ull ? 0ull : rb);
+      const bool fin = rb < 0x7ff0000000000000ull;
+      bad |= !fin;
+      cmax[j] = fin ? rb : 0ull;
     }
   }
-  s_col[threadIdx.y][threadIdx.x] = cmax;
-  if (__syncthreads_or(bad) && threadIdx.x == 0 && threadIdx.y == 0) atomicExch(nonfinite, 1);
-  if (threadIdx.y == 0) {
-    for (int y = 1; y < 8; ++y) cmax = max(cmax, s_col[y][threadIdx.x]);
-    if (j < m && cmax) atomicMax(&colmax[j], cmax);
-    for (int o = 16; o > 0; o >>= 1) cmax = max(cmax, __shfl_xor_sync(0xffffffffu, cmax, o));
-    if (threadIdx.x == 0 && cmax) atomicMax(&red[0], cmax);
+  unsigned long long all = 0ull;
+#pragma unroll
+  for (int j = 0; j < kNarrow; ++j) {
+    unsigned long long c = cmax[j];
+    for (int o = 16; o > 0; o >>= 1) c = max(c, __shfl_xor_sync(0xffffffffu, c, o));
+    if (lane == 0) s_col[warp][j] = c;
+    all = max(all, c);
   }
+  if (__syncthreads_or(bad) && threadIdx.x == 0) atomicExch(nonfinite, 1);
+  if (threadIdx.x < kNarrow && threadIdx.x < m) {
+    unsigned long long c = s_col[0][threadIdx.x];
+#pragma unroll
+    for (int y = 1; y < 8; ++y) c = max(c, s_col[y][threadIdx.x]);
+    if (c) atomicMax(&colmax[threadIdx.x], c);
+  }
+  if (lane == 0 && all) atomicMax(&red[0], all);
 }
 
 // out[e] = (int16) of the integer-valued bf16 in[e] (rg_exact_split's output form).
 __global__ void bf16_rows_to_int16(const __nv_bfloat16* __restrict__ in, int64_t total, int16_t* __restrict__ out) {
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x)
     out[e] = (int16_t)__float2int_rz(__bfloat162float(in[e]));
-}
-
-// (float)(x * 2^-e) on the two 32-bit words of x, for x zero, or normal with x 2^-e and
-// its float normal: the exponent moves by -e (exact), the 52-bit mantissa is rounded to 23
-// bits, to nearest, ties to even (a carry moves up the exponent). Clears ok elsewhere.
-__device__ __forceinline__ float scaled_bits(double x, int e, bool& ok) {
-  const uint32_t hi = (uint32_t)__double2hiint(x), lo = (uint32_t)__double2loint(x);
-  const uint32_t sign = hi & 0x80000000u, t = hi & 0x7fffffffu;
-  if ((t | lo) == 0u) return __uint_as_float(sign);
-  const int E = (int)(t >> 20);
-  const int fe = E - e - 896;  // float biased exponent: E - 1023 - e + 127
-  const uint32_t m = ((t & 0xfffffu) << 3) | (lo >> 29), rem = lo & 0x1fffffffu;
-  const uint32_t up = (rem > 0x10000000u) | ((rem == 0x10000000u) & m);
-  const uint32_t bits = ((uint32_t)fe << 23) + m + (up & 1u);
-  ok = ok && E >= 1 && E <= 2046 && fe >= 1 && fe <= 254 && bits < 0x7f800000u;
-  return __uint_as_float(sign | bits);
 }
 
 // A16 = I - Dl P Dr (16-bit, identity padding), the first Newton-Schulz iterate
@@ -428,8 +621,44 @@ __device__ __forceinline__ bool sweep_ends(const SweepGuard& g) {
   return done || w[0] || w[1] || w[4];
 }
 
-// Rt16[j][i] = 16-bit (R_ij * 2^-e_j) with max_i |R_ij| 2^-e_j in [0.5, 1), zero padding;
-// colscale[j] = 2^e_j. Tiled transpose through shared memory, block (32 x 8).
+// 16-bit pair (lo, hi) as one 32-bit word, lo in the lower half.
+template <class T16>
+__device__ __forceinline__ uint32_t pack16(float lo, float hi);
+template <>
+__device__ __forceinline__ uint32_t pack16<__nv_bfloat16>(float lo, float hi) {
+  const __nv_bfloat162 p = __floats2bfloat162_rn(lo, hi);
+  return *reinterpret_cast<const uint32_t*>(&p);
+}
+template <>
+__device__ __forceinline__ uint32_t pack16<__half>(float lo, float hi) {
+  const __half2 p = __floats2half2_rn(lo, hi);
+  return *reinterpret_cast<const uint32_t*>(&p);
+}
+
+// (float)(x 2^-e) for |x 2^-e| < 2^128, on the two 32-bit words of x (no fp64 arithmetic):
+// the exponent moves by -e, the 52-bit mantissa is rounded to 23 bits to nearest, ties to
+// even (a carry moves up the exponent). Results below 2^-126 in magnitude, and subnormal x,
+// give a signed zero (the value is bound for a 16-bit operand scaled to [0.5, 1), whose
+// resolution is far coarser); inf and NaN stay inf and NaN.
+__device__ __forceinline__ float scaled_float(double x, int e) {
+  const uint32_t hi = (uint32_t)__double2hiint(x), lo = (uint32_t)__double2loint(x);
+  const uint32_t sign = hi & 0x80000000u, t = hi & 0x7fffffffu;
+  const int E = (int)(t >> 20);
+  if (E == 2047) return __uint_as_float(sign | 0x7f800000u | (((t & 0xfffffu) | lo) ? 0x400000u : 0u));
+  const int fe = E - e - 896;  // float biased exponent: E - 1023 - e + 127
+  if (E == 0 || fe < 1) return __uint_as_float(sign);
+  if (fe > 254) return __uint_as_float(sign | 0x7f800000u);
+  const uint32_t m = ((t & 0xfffffu) << 3) | (lo >> 29), rem = lo & 0x1fffffffu;
+  const uint32_t up = (rem > 0x10000000u) | ((rem == 0x10000000u) & m);
+  const uint32_t bits = ((uint32_t)fe << 23) + m + (up & 1u);
+  return __uint_as_float(sign | (bits < 0x7f800000u ? bits : 0x7f800000u));
+}
+
+// Rt16[j][i] = 16-bit (R_ij * 2^-e_j) with max_i |R_ij| 2^-e_j in [0.5, 1), zero padding
+// (values below 2^-126 of the column maximum flushed to zero); colscale[j] = 2^e_j. Block
+// (32 x 8) per 64 rows x 32 columns: eight row loads in flight per thread, the transposed
+// rows written as 16-bit pairs (128 bytes per warp) through shared memory; integer
+// arithmetic only (GB300's fp64 pipe is far narrower than its integer ALU).
 // The first kernel of a sweep: it also zeroes the sweep's status words (red_cur: max|R|,
 // max|X|, max|D|) and the column maxima of the correction (dcolmax[0 .. mp)).
 template <class T16>
@@ -437,7 +666,7 @@ __global__ void scaled_transpose16(const double* __restrict__ R, int64_t ld, int
                                    const unsigned long long* __restrict__ colmax, T16* __restrict__ Rt,
                                    float* __restrict__ colscale, const SweepGuard guard,
                                    unsigned long long* red_cur, unsigned int* dcolmax) {
-  __shared__ float tile[32][33];
+  __shared__ __align__(16) float tile[32][66];  // [column][row]: a row pair is one 8-byte read
   if (guard.err) {  // one thread per block evaluates the rule (an fp64 division), the block follows
     __shared__ int s_end;
     if (threadIdx.x == 0 && threadIdx.y == 0) {
@@ -447,7 +676,7 @@ __global__ void scaled_transpose16(const double* __restrict__ R, int64_t ld, int
     __syncthreads();
     if (s_end) return;
   }
-  const int i0 = blockIdx.y * 32, j0 = blockIdx.x * 32;
+  const int i0 = blockIdx.y * 64, j0 = blockIdx.x * 32;
   const int j = j0 + threadIdx.x;
   if (blockIdx.y == 0 && threadIdx.y == 0 && j < mp) dcolmax[j] = 0u;
   if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.y == 0 && threadIdx.x < 3) red_cur[threadIdx.x] = 0ull;
@@ -459,23 +688,58 @@ __global__ void scaled_transpose16(const double* __restrict__ R, int64_t ld, int
     const int E = (int)(mb >> 52);  // 2048 and up: the sign bit is set
     if (mb != 0ull && E < 2047) e = E >= 1 ? E - 1022 : (63 - __clzll((long long)mb)) - 1073;
   }
-  const double sc = ldexp(1.0, -e);
-  if (blockIdx.y == 0 && j < mp) colscale[j] = ldexpf(1.f, e);
-  for (int r = threadIdx.y; r < 32; r += 8) {  // warp-uniform: threadIdx.y is the warp
-    const int i = i0 + r;
-    const bool in = i < n && j < m;
-    const double x = in ? R[(int64_t)i * ld + j] : 0.0;
-    bool ok = true;
-    float v = in ? scaled_bits(x, e, ok) : 0.f;
-    if (__any_sync(0xffffffffu, !ok)) {  // fp64, for the lanes that need it
-      if (!ok) v = (float)(x * sc);
-    }
-    tile[r][threadIdx.x] = v;
+  if (blockIdx.y == 0 && threadIdx.y == 0 && j < mp) colscale[j] = ldexpf(1.f, e);
+  double x[8];
+#pragma unroll
+  for (int r = 0; r < 8; ++r) {  // warp-uniform rows: threadIdx.y is the warp
+    const int i = i0 + threadIdx.y + 8 * r;
+    x[r] = (i < n && j < m) ? R[(int64_t)i * ld + j] : 0.0;
   }
+#pragma unroll
+  for (int r = 0; r < 8; ++r) tile[threadIdx.x][threadIdx.y + 8 * r] = scaled_float(x[r], e);
   __syncthreads();
-  for (int r = threadIdx.y; r < 32; r += 8) {
-    const int jj = j0 + r, ii = i0 + threadIdx.x;
-    if (jj < mp && ii < np) Rt[(int64_t)jj * np + ii] = to16<T16>(tile[threadIdx.x][r]);
+  // warp w writes columns j0 + w + 8 c, lane l the rows i0 + 2 l, i0 + 2 l + 1
+  const int ii = i0 + 2 * threadIdx.x;
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    const int jl = threadIdx.y + 8 * c, jj = j0 + jl;
+    const float2 p = *reinterpret_cast<const float2*>(&tile[jl][2 * threadIdx.x]);
+    if (jj < mp && ii < np) *reinterpret_cast<uint32_t*>(Rt + (int64_t)jj * np + ii) = pack16<T16>(p.x, p.y);
+  }
+}
+
+// scaled_transpose16 for m <= kNarrow columns: one thread per row i (the writes Rt16[j][i]
+// are consecutive along i); the same outputs and status words, rows j >= m of Rt16 left
+// unwritten (the GEMM reads N = m rows).
+template <class T16>
+__global__ void __launch_bounds__(256) scaled_transpose16_narrow(
+    const double* __restrict__ R, int64_t ld, int n, int m, int np, int mp,
+    const unsigned long long* __restrict__ colmax, T16* __restrict__ Rt, float* __restrict__ colscale,
+    const SweepGuard guard, unsigned long long* red_cur, unsigned int* dcolmax) {
+  if (guard.err) {
+    __shared__ int s_end;
+    if (threadIdx.x == 0) {
+      s_end = sweep_ends(guard) ? 1 : 0;
+      if (blockIdx.x == 0) *guard.skip = s_end;
+    }
+    __syncthreads();
+    if (s_end) return;
+  }
+  const int i = blockIdx.x * 256 + threadIdx.x;
+  if (blockIdx.x == 0 && threadIdx.x < 3) red_cur[threadIdx.x] = 0ull;
+  if (blockIdx.x == 0 && threadIdx.x < mp) {
+    dcolmax[threadIdx.x] = 0u;
+    if (threadIdx.x >= m) colscale[threadIdx.x] = 1.f;
+  }
+#pragma unroll
+  for (int j = 0; j < kNarrow; ++j) {
+    if (j >= m) break;
+    const unsigned long long mb = colmax[j];
+    const int E = (int)(mb >> 52);
+    int e = 0;
+    if (mb != 0ull && E < 2047) e = E >= 1 ? E - 1022 : (63 - __clzll((long long)mb)) - 1073;
+    if (blockIdx.x == 0 && threadIdx.x == 0) colscale[j] = ldexpf(1.f, e);
+    if (i < np) Rt[(int64_t)j * np + i] = to16<T16>(i < n ? scaled_float(R[(int64_t)i * ld + j], e) : 0.f);
   }
 }
 
@@ -818,7 +1082,8 @@ struct Solver {
     const double* src = first ? b.R0 : b.R;
     unsigned long long* rc = red(parity);
     const int* skip = g.err ? g.skip : nullptr;
-    dim3 tg(L.mp / 32, L.np / 32);
+    dim3 tg(L.mp / 32, L.np / 64), qg(L.mp / 64, L.np / 64);
+    const int nb = L.np / 256 + (L.np % 256 ? 1 : 0);  // narrow kernels: one thread per row < np
     rg_status st = RG_OK;
     if (pre) {
       // D = W K diag(t) R (forward) or K^T W^T diag(t) R (adjoint), one column
@@ -840,26 +1105,39 @@ struct Solver {
       RG_CUDA_TRY(ctx, cudaGetLastError());
     } else {
       T16* Rt = static_cast<T16*>(b.Rt16);
-      scaled_transpose16<T16><<<tg, dim3(32, 8), 0, s>>>(src, L.mp, L.n, L.m, L.np, L.mp, b.colmax, Rt, b.colscale,
+      if (L.m <= kNarrow)
+        scaled_transpose16_narrow<T16><<<nb, 256, 0, s>>>(src, L.mp, L.n, L.m, L.np, L.mp, b.colmax, Rt, b.colscale,
                                                           g, rc, b.dcolmax);
+      else
+        scaled_transpose16<T16><<<tg, dim3(32, 8), 0, s>>>(src, L.mp, L.n, L.m, L.np, L.mp, b.colmax, Rt,
+                                                            b.colscale, g, rc, b.dcolmax);
       ++ctx->launches;
       RG_CUDA_TRY(ctx, cudaGetLastError());
       st = tc::gemm(ctx, bf16, minv ? minv : b.X16[cur], L.np, Rt, L.np, L.n, L.m, L.np,
                     tc::EpiCorrection{b.Dbuf, L.mp, b.colscale, b.dcolmax, err + 1}, s, skip);
       if (st != RG_OK) return st;
     }
-    quantize_correction<<<tg, dim3(32, 8), 0, s>>>(b.Dbuf, L.n, L.m, L.np, L.mp, b.dcolmax, b.Bq, b.Dn, b.dexp, b.X,
-                                                   first ? 1 : 0, rc, b.colmax, err + 1, skip);
+    if (L.m <= kNarrow)
+      quantize_correction_narrow<<<nb, 256, 0, s>>>(b.Dbuf, L.n, L.m, L.np, L.mp, b.dcolmax, b.Bq, b.Dn, b.dexp,
+                                                     b.X, first ? 1 : 0, rc, b.colmax, err + 1, skip);
+    else
+      quantize_correction<<<qg, dim3(32, 8), 0, s>>>(b.Dbuf, L.n, L.m, L.np, L.mp, b.dcolmax, b.Bq, b.Dn, b.dexp,
+                                                     b.X, first ? 1 : 0, rc, b.colmax, err + 1, skip);
     ++ctx->launches;
     RG_CUDA_TRY(ctx, cudaGetLastError());
     // levels from max|D| / max|X| of this sweep (rc[2] / rc[1]), read on the device
     st = tc::gemm_exact(ctx, b.Aex, (int64_t)kLevels * L.np, b.Bq, L.np, L.n, L.m, L.np, nullptr, rc, kLevelBits,
                         kLevels, b.lev, exact_splits(L.n, L.m), &splits, s, skip, L.n);
     if (st != RG_OK) return st;
-    dim3 fg((L.m + 31) / 32, (L.n + 31) / 32);
-    finish_residual<<<fg, dim3(32, 8), 0, s>>>(b.lev, tc::exact_ld(L.m), tc::exact_plane(L.n, L.m), splits, b.rowexp,
-                                               b.dexp, b.Dn, dl, L.n, L.m, L.mp, b.R0, b.R, b.Q, first ? 1 : 0, rc,
-                                               b.colmax, err + 1, skip);
+    dim3 fg((L.m + 127) / 128, (L.n + 127) / 128);
+    if (L.m <= kNarrow)
+      finish_residual_narrow<<<nb, 256, 0, s>>>(b.lev, tc::exact_ld(L.m), tc::exact_plane(L.n, L.m), splits,
+                                                 b.rowexp, b.dexp, b.Dn, dl, L.n, L.m, L.mp, b.R0, b.R, b.Q,
+                                                 first ? 1 : 0, rc, b.colmax, err + 1, skip);
+    else
+      finish_residual<<<fg, dim3(32, 8), 0, s>>>(b.lev, tc::exact_ld(L.m), tc::exact_plane(L.n, L.m), splits,
+                                                 b.rowexp, b.dexp, b.Dn, dl, L.n, L.m, L.mp, b.R0, b.R, b.Q,
+                                                 first ? 1 : 0, rc, b.colmax, err + 1, skip);
     ++ctx->launches;
     RG_CUDA_TRY(ctx, cudaGetLastError());
     int* slot = ctx->h_scratch + kStatus + 32 * parity;

@@ -140,3 +140,26 @@ def test_stores_that_do_not_fit_the_call_are_refused(rg_ctx):
     de, _ = adj()
     de0, _ = api.gebhart_adjoint(rg_ctx, Fd, ed, rd, B, W, "fp16", tol=1e-12)
     assert (de - de0).abs().max().item() <= 1e-10 * de0.abs().max().item()
+
+
+@pytest.mark.parametrize("rank", [3, 8, 9, 64])
+def test_factored_adjoint_ranks_across_the_narrow_and_wide_kernels(rg_ctx, rank):
+    """Up to 8 right-hand sides the sweeps run one thread per row; from 9 on, four columns
+    per lane with a ragged last lane (9 = 4 + 4 + 1). Both against the oracle's adjoint of
+    dB = sum_r a_r b_r^T, with and without stored factors."""
+    N, S = 333, 2
+    F, eps, rho, rng = _system(N, S, 200 + rank)
+    Fd, ed, rd = _dev(F), _dev(eps), _dev(rho)
+    store = api.gebhart_factor_store(N, S, "fp16")
+    B, _, _ = api.gebhart(rg_ctx, Fd, ed, rd, "fp16", tol=1e-12, factors=store)
+    a = _dev(rng.standard_normal((S, rank, N)))
+    b = _dev(rng.standard_normal((S, rank, N + 1)))
+    de, dr = api.gebhart_adjoint_factored(rg_ctx, Fd, ed, rd, B, a, b, "fp16", tol=1e-12, factors=store)
+    de0, dr0 = api.gebhart_adjoint_factored(rg_ctx, Fd, ed, rd, B, a, b, "fp16", tol=1e-12)
+    assert (de - de0).abs().max().item() <= 1e-10 * de0.abs().max().item()
+    assert (dr - dr0).abs().max().item() <= 1e-10 * dr0.abs().max().item()
+    Bh, ah, bh = B.cpu().numpy(), a.cpu().numpy(), b.cpu().numpy()
+    for s in range(S):
+        deo, dro = G.gebhart_adjoint(F, eps[s], rho[s], Bh[s], ah[s].T @ bh[s])
+        assert np.abs(de[s].cpu().numpy() - deo).max() <= 1e-9 * np.abs(deo).max()
+        assert np.abs(dr[s].cpu().numpy() - dro).max() <= 1e-9 * np.abs(dro).max()
