@@ -417,15 +417,15 @@ def kernel_rooflines(api, ctx, pipe, steps, step_ms, peaks, trace_roof):
         elif kind in ("residual_gemm", "gemm"):
             alg = r["alg_flops"] / r["ms"] / 1e9
             exe = r["flops"] / r["ms"] / 1e9
-            row.update({"kernel": "tc::gemm_kernel (tcgen05, compensated residual epilogue)" if kind == "residual_gemm"
-                        else "tc::gemm_kernel (tcgen05: Newton-Schulz steps, corrections)",
+            row.update({"kernel": "tc::gemm_exact_kernel (tcgen05, exact integer level products)"
+                        if kind == "residual_gemm" else "tc::gemm_kernel (tcgen05: Newton-Schulz steps, corrections)",
                         "bound": "tensor", "achieved": round(alg, 2), "peak": tc, "unit": "TFLOP/s",
                         "frac": round(alg / tc, 4), "traffic": None,
                         "executed_tflops": round(exe, 2), "executed_frac": round(exe / tc, 4),
                         "peak_basis": "bf16_tflops_sustained of MEASURED_PEAKS.json (kernel timed inside a long "
                                       "step); fp16 has the bf16 rate",
-                        "note": "achieved counts the fp64 product each launch stands for (2 n m n per refinement "
-                                "residual); executed counts the bf16 slice products it runs (2 M N K)"
+                        "note": "achieved counts the one-slice product P' D each launch stands for (2 n m n per "
+                                "sweep); executed counts the level products it runs (2 M N K per level)"
                         if kind == "residual_gemm" else "achieved = executed tensor flops (2 M N K)"})
         else:
             it = getattr(pipe, "iters", 0)
@@ -435,6 +435,12 @@ def kernel_rooflines(api, ctx, pipe, steps, step_ms, peaks, trace_roof):
                         "note": f"16 B per matrix entry per iteration, {it} iterations per launch; the fp64 pipe "
                                 "(6 fp64 operations per pair of entries) is the limit on this GPU"})
         out[kind] = row
+    r = api.kernel_timer_read(ctx, "factor")
+    if r["launches"]:
+        out["factor"] = {"regions_per_step": r["launches"] / steps, "ms_per_step": round(r["ms"] / steps, 3),
+                         "share_of_step": round(r["ms"] / steps / step_ms, 4),
+                         "ms_per_factorisation": round(r["ms"] / r["launches"], 4),
+                         "note": "Newton-Schulz inverses, start iterate to last step (their GEMMs are also in gemm)"}
     return out
 
 

@@ -576,8 +576,8 @@ rg_status rg_tc_gemm(rg_ctx* ctx, int32_t M, int32_t N, int32_t K, const void* A
  *   S_a[i][j] = sum_k A[i][a np + k] B[j][k]  for a = 0 .. levels-1,
  *   A_d  device bf16 [M][lda] (lda >= 5 np), every element an integer of magnitude <= 128;
  *   B_d  device bf16 [N][np], every element an integer of magnitude <= 127 (then every
- *        product is below 2^14 and every 256-long chunk sum is exact in the fp32
- *        tensor-core accumulator); np a multiple of 128
+ *        product is at most 16,256 and every partial sum of a 1,024-long chunk is an integer
+ *        below 2^24, exact in the fp32 tensor-core accumulator); np a multiple of 128
  *   S_d  device int32 [levels][M][N] (output), exact for |S| < 2^31
  *   Errors: RG_ERR_ARG (layout, levels outside 1..5), RG_ERR_CUDA. */
 rg_status rg_exact_split(rg_ctx* ctx, int32_t n, const double* P_d, int64_t ldp, int32_t trans, const double* dr_d,

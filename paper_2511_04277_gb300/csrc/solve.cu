@@ -23,9 +23,9 @@
 //      fixed-point slices per row, P'_ik = 2^(e_i - 7) sum_a s_a,ik 2^(-8a) with integers
 //      |s_a| <= 128 (40 bits below the row maximum). Starting from R = R0, X = 0, every
 //      sweep takes the correction D = M R (one tensor-core GEMM), rounds each column of D to
-//      one 8-bit fixed-point slice (integers |d| <= 128 times 2^(f_j - 7)), adds it to X
+//      one 8-bit fixed-point slice (integers |d| <= 127 times 2^(f_j - 7)), adds it to X
 //      exactly and updates R <- R - D + Dl (P' D). The product P' D is a sum of integer
-//      products; every 128-long chunk of it is exact in the fp32 tensor-core accumulator and
+//      products; every 1,024-long chunk of it is exact in the fp32 tensor-core accumulator and
 //      the chunks are added as integers, so the only error of the update is the truncation
 //      of P' to the levels used (L levels: 2^-(8L-1) of |P'| |D|, L chosen per sweep from
 //      max|D| / max|X| so that it stays below 2^-38 of |P'| |X|). The residual is thus known

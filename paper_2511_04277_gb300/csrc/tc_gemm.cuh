@@ -428,7 +428,11 @@ struct ExactArgs {
   int* level_log = nullptr;  // kernel timer: the launch records L here (CTA 0, thread 0)
 };
 
-constexpr int kExactChunkBlocks = 4;  // 256-long K chunks (the last one of a level may be shorter)
+// 1,024-long K chunks (the last one of a level may be shorter): with operands |a| <= 128 and
+// |b| <= 127 every partial sum of a chunk is an integer below 1,024 x 16,256 = 16,646,144 < 2^24,
+// so the fp32 accumulation in tensor memory is exact, and the epilogue drains each chunk while
+// the MMAs of the next one run.
+constexpr int kExactChunkBlocks = 16;
 __host__ __device__ constexpr int exact_groups(int BN) { return BN > 128 ? BN / 128 : 1; }
 __host__ __device__ constexpr int exact_threads(int BN) { return 64 + 128 * exact_groups(BN); }
 
@@ -523,7 +527,7 @@ __global__ void __launch_bounds__(exact_threads(BN), 1)
       }
     }
   } else if (warp == 1) {
-    // ---------------- MMA issuer: one accumulation per 128-long chunk, two TMEM buffers
+    // ---------------- MMA issuer: one accumulation per chunk, two TMEM buffers
     if (lane == 0) {
       int t = 0;
       for (int c = 0; c < n_chunks && !*abort_flag; ++c) {
@@ -569,26 +573,23 @@ __global__ void __launch_bounds__(exact_threads(BN), 1)
       for (int c0 = 0; c0 < kCols; c0 += 32) {
         float v[32];
         tmem_ld32(tmem_base + lane_addr + (uint32_t)(b * BN + cbase + c0), v);
-        // v is an integer of magnitude below 2^22: v + 1.5 2^23 keeps it in the low mantissa
-        // bits (exact), read as an integer it is v + 0x4B400000; the offsets are taken out
-        // when the level is stored (modulo 2^32, which is exact for the true sum)
+        // v is an integer of magnitude below 2^24, exact in fp32: converted exactly
 #pragma unroll
-        for (int i = 0; i < 32; ++i) acc[c0 + i] += __float_as_uint(v[i] + 12582912.0f);
+        for (int i = 0; i < 32; ++i) acc[c0 + i] += (uint32_t)__float2int_rn(v[i]);
       }
       tc_fence_before();
       mbar_arrive(&acc_empty[b]);
       if (++in_level == chunks_per_level) {
         const int a = c / chunks_per_level;
-        const uint32_t off = (uint32_t)chunks_per_level * 0x4B400000u;
         int32_t* dst = args.lev + ((int64_t)blockIdx.z * args.max_levels + a) * args.plane + (int64_t)row * args.ldl +
                        n0 + cbase;
 #pragma unroll
         for (int i = 0; i < kCols; i += 4) {
           int4 w;
-          w.x = (int32_t)(acc[i] - off);
-          w.y = (int32_t)(acc[i + 1] - off);
-          w.z = (int32_t)(acc[i + 2] - off);
-          w.w = (int32_t)(acc[i + 3] - off);
+          w.x = (int32_t)acc[i];
+          w.y = (int32_t)acc[i + 1];
+          w.z = (int32_t)acc[i + 2];
+          w.w = (int32_t)acc[i + 3];
           *reinterpret_cast<int4*>(dst + i) = w;
           acc[i] = acc[i + 1] = acc[i + 2] = acc[i + 3] = 0u;
         }

@@ -5,8 +5,9 @@ precision): P' = P diag(dr) is split into five 8-bit fixed-point slices per row,
 correction into one 8-bit slice per column (integers up to 127), and the tensor cores form
 their products as exact integer sums. These tests pin the split to its definition and the
 tcgen05 level product to integer arithmetic, including the largest operands (+-128 times
-+-127), whose 256-long chunk sums reach 4,161,536 (just below 2^22) and whose level sums
-pass 2^24.
++-127) with signs aligned so that every product of an output entry has one sign: the
+1,024-long chunk sums then reach 16,646,144 (the largest the operand bounds allow, below
+2^24) and the level sums pass 2^24.
 """
 import numpy as np
 import pytest
@@ -59,7 +60,13 @@ def test_exact_split_matches_its_definition(rg_ctx, n, trans, with_dr):
     del np_
 
 
-def _ints(rng, shape, extreme=False, top=128):
+def _ints(rng, shape, extreme=False, top=128, col_signs=None):
+    """Random integers in [-top, top]; extreme: +-top; col_signs: +-top with the sign of
+    column k from col_signs[k] times a random sign per row (products of two such operands
+    share one sign along k)."""
+    if col_signs is not None:
+        rows = rng.choice(np.array([-1.0, 1.0]), (shape[0], 1))
+        return top * rows * col_signs[None, :shape[1]]
     if extreme:
         return rng.choice(np.array([-float(top), float(top)]), shape)
     return rng.integers(-top, top + 1, shape).astype(np.float64)
@@ -67,16 +74,22 @@ def _ints(rng, shape, extreme=False, top=128):
 
 @pytest.mark.parametrize("M,N,np_,levels,extreme", [
     (300, 257, 256, 5, False),     # ragged tiles, narrow tile widths
-    (130, 7, 1024, 3, True),       # every product 16,256: chunk sums just below 2^22
-    (257, 300, 384, 5, True),      # a level of 1.5 chunks: a short last chunk
+    (130, 7, 1024, 3, True),       # every product +-16,256
+    (200, 140, 2304, 5, "aligned"),  # full chunks of one sign: sums 16,646,144, two chunks and a short one
+    (257, 300, 384, 5, True),      # a level shorter than one chunk
     (4096, 2560, 512, 2, False),   # 128 x 256 tiles
     (2048, 2049, 384, 4, True),    # 128 x 128 tiles with a one-column tail
 ])
 def test_exact_gemm_is_integer_exact(rg_ctx, M, N, np_, levels, extreme):
     rng = np.random.default_rng(M + N + levels)
     A = np.zeros((M, 5 * np_))
-    A[:, :levels * np_] = _ints(rng, (M, levels * np_), extreme)
-    B = _ints(rng, (N, np_), extreme, top=127)
+    if extreme == "aligned":
+        sk = rng.choice(np.array([-1.0, 1.0]), np_)
+        A[:, :levels * np_] = np.concatenate([_ints(rng, (M, np_), col_signs=sk) for _ in range(levels)], axis=1)
+        B = _ints(rng, (N, np_), top=127, col_signs=sk)
+    else:
+        A[:, :levels * np_] = _ints(rng, (M, levels * np_), extreme)
+        B = _ints(rng, (N, np_), extreme, top=127)
     A_d = torch.as_tensor(A, device="cuda").to(torch.bfloat16)
     B_d = torch.as_tensor(B, device="cuda").to(torch.bfloat16)
     S = api.tc_gemm_exact(rg_ctx, A_d, B_d, levels).cpu().numpy().astype(np.int64)
