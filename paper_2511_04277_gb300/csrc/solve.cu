@@ -59,10 +59,6 @@ inline int exact_splits(int n, int m) {
   return tc::exact_plane(n, m) * (int64_t)sizeof(int32_t) <= (64ll << 20) ? kMaxExactSplits : 1;
 }
 
-__device__ __forceinline__ double p_elem(const double* P, int64_t ldp, bool trans, int i, int k) {
-  return trans ? P[(int64_t)k * ldp + i] : P[(int64_t)i * ldp + k];
-}
-
 template <class T>
 __device__ __forceinline__ T to16(float x);
 template <>
@@ -71,13 +67,6 @@ template <>
 __device__ __forceinline__ __half to16<__half>(float x) { return __float2half_rn(x); }
 
 // ------------------------------------------------------------------ exact refinement kernels
-// Exponent e of a non-negative finite double x > 0 with x = m 2^e, m in [0.5, 1) (frexp's).
-__device__ __forceinline__ int frexp_exponent(double x) {
-  int e;
-  frexp(x, &e);
-  return e;
-}
-
 // x 2^k (exact unless the result leaves the normal range).
 __device__ __forceinline__ double scale2(double x, int k) {
   if (k >= -1022 && k <= 1023) return x * __longlong_as_double((long long)(k + 1023) << 52);
@@ -138,53 +127,152 @@ __device__ __forceinline__ long long round_scaled(double x, int s) {
   return (b >> 63) ? -q : q;
 }
 
+// bf16 bit pattern of an integer |d| <= 255 (exact): the float is formed by the magic-number
+// subtraction (fp32, exact) and its upper half is the bf16 value.
+__device__ __forceinline__ uint32_t bf16_bits_of_int(int d) {
+  return __float_as_uint(__int_as_float(0x4B400000 + d) - 12582912.0f) >> 16;
+}
+
+// frexp's exponent of the double whose bit pattern (sign cleared) is b > 0, finite.
+__device__ __forceinline__ int frexp_exponent_bits(unsigned long long b) {
+  const int E = (int)(b >> 52);
+  return E >= 1 ? E - 1022 : (63 - __clzll((long long)b)) - 1073;
+}
+
+// The split of one entry: q = round(x 2^s) (to nearest, ties to even) and its balanced
+// base-256 digits s_0 .. s_4 (q = sum_a s_a 256^(4 - a)) as bf16 bit patterns.
+__device__ __forceinline__ void split_digits(double x, int s, bool nonzero, uint32_t (&dbits)[kLevels]) {
+  long long q = nonzero ? round_scaled(x, s) : 0;
+#pragma unroll
+  for (int a = kLevels - 1; a > 0; --a) {
+    const int d = (int)((q + 128) & 255) - 128;
+    dbits[a] = bf16_bits_of_int(d);
+    q = (q - d) >> 8;
+  }
+  dbits[0] = bf16_bits_of_int((int)q);
+}
+
 // Fixed-point split of P' = P Dr (Dr may be null) into kLevels slices per row: with e_i the
 // exponent of max_k |P'_ik| and q = round(P'_ik 2^(39 - e_i)) (|q| < 2^39, to nearest, ties
 // to even), the slices are q's balanced base-256 digits, q = sum_a s_a 256^(4 - a) with
 // s_1..s_4 in [-128, 127] and |s_0| <= 128, so that P'_ik = 2^(e_i - 7) sum_a s_a 2^(-8a)
 // up to 2^(e_i - 40). Aex[i][a np + k] = s_a (exact in bf16), zero in the padding;
-// rowexp[i] = e_i (0 for a zero row). A non-finite entry raises *err. One warp per row.
-__global__ void build_p_exact(const double* __restrict__ P, int64_t ldp, bool trans, const double* __restrict__ dr,
-                              int n, int np, __nv_bfloat16* __restrict__ Aex, int* __restrict__ rowexp, int* err) {
+// rowexp[i] = e_i (0 for a zero row). A non-finite entry raises *err. One warp per row, two
+// adjacent columns per lane (the slices written as bf16 pairs); the row maximum is taken on
+// the bit patterns and the only fp64 arithmetic is the product with Dr (GB300's fp64 pipe is
+// narrow).
+__global__ void build_p_exact(const double* __restrict__ P, int64_t ldp, const double* __restrict__ dr, int n,
+                              int np, __nv_bfloat16* __restrict__ Aex, int* __restrict__ rowexp, int* err) {
   const int i = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
   const int lane = threadIdx.x & 31;
   if (i >= np) return;
-  __nv_bfloat16* row = Aex + (int64_t)i * kLevels * np;
-  const __nv_bfloat16 zero = __ushort_as_bfloat16((unsigned short)0);
+  uint32_t* row = reinterpret_cast<uint32_t*>(Aex + (int64_t)i * kLevels * np);  // bf16 pairs
+  const int half = np / 2;
   if (i >= n) {
-    for (int k = lane; k < np; k += 32)
+    for (int k2 = lane; k2 < half; k2 += 32)
 #pragma unroll
-      for (int a = 0; a < kLevels; ++a) row[(int64_t)a * np + k] = zero;
+      for (int a = 0; a < kLevels; ++a) row[(int64_t)a * half + k2] = 0u;
     if (lane == 0) rowexp[i] = 0;
     return;
   }
-  double mx = 0.0;
+  const double* prow = P + (int64_t)i * ldp;
+  unsigned long long mx = 0ull;
   bool bad = false;
   for (int k = lane; k < n; k += 32) {
-    const double x = p_elem(P, ldp, trans, i, k) * (dr ? dr[k] : 1.0);
-    bad |= !isfinite(x);
-    mx = fmax(mx, fabs(x));
+    const double x = dr ? prow[k] * dr[k] : prow[k];
+    const unsigned long long bx = (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffull;
+    bad |= bx >= 0x7ff0000000000000ull;
+    mx = max(mx, bx);
   }
-  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
   if (__any_sync(0xffffffffu, bad)) {
     if (lane == 0) atomicExch(err, 1);
-    mx = 0.0;  // the slices are not used once the error is raised
+    mx = 0ull;  // the slices are not used once the error is raised
   }
-  const int e = mx > 0.0 ? frexp_exponent(mx) : 0;
-  for (int k = lane; k < np; k += 32) {
-    long long q = 0;
-    if (k < n && mx > 0.0) q = round_scaled(p_elem(P, ldp, trans, i, k) * (dr ? dr[k] : 1.0), 39 - e);
-    int d[kLevels];
+  const int e = mx ? frexp_exponent_bits(mx) : 0;
+  for (int k2 = lane; k2 < half; k2 += 32) {
+    const int k = 2 * k2;
+    uint32_t d0[kLevels], d1[kLevels];
+    split_digits(k < n ? (dr ? prow[k] * dr[k] : prow[k]) : 0.0, 39 - e, k < n && mx, d0);
+    split_digits(k + 1 < n ? (dr ? prow[k + 1] * dr[k + 1] : prow[k + 1]) : 0.0, 39 - e, k + 1 < n && mx, d1);
 #pragma unroll
-    for (int a = kLevels - 1; a > 0; --a) {
-      d[a] = (int)((q + 128) & 255) - 128;
-      q = (q - d[a]) >> 8;
-    }
-    d[0] = (int)q;
-#pragma unroll
-    for (int a = 0; a < kLevels; ++a) row[(int64_t)a * np + k] = __float2bfloat16_rz((float)d[a]);
+    for (int a = 0; a < kLevels; ++a) row[(int64_t)a * half + k2] = d0[a] | (d1[a] << 16);
   }
   if (lane == 0) rowexp[i] = e;
+}
+
+// build_p_exact for P read transposed (P'_ik = P_ki Dr_k): block (32 x 8) per 32 rows i of P',
+// so that every read of P is a coalesced segment of one of its rows. Pass 1: the row maxima
+// (eight loads in flight per thread, shared-memory reduction). Pass 2: per 64 columns k, the
+// digits go through shared memory and are written along k (64-byte rows per slice).
+__global__ void __launch_bounds__(256) build_p_exact_t(const double* __restrict__ P, int64_t ldp,
+                                                       const double* __restrict__ dr, int n, int np,
+                                                       __nv_bfloat16* __restrict__ Aex, int* __restrict__ rowexp,
+                                                       int* err) {
+  __shared__ unsigned long long s_mx[8][32];
+  __shared__ int s_bad;
+  __shared__ __align__(16) uint16_t tile[kLevels][32][66];  // [a][row of P'][column k]
+  const int x = threadIdx.x, y = threadIdx.y;
+  const int i0 = blockIdx.x * 32, i = i0 + x;
+  if (x == 0 && y == 0) s_bad = 0;
+  unsigned long long mx = 0ull;
+  bool bad = false;
+  if (i < n) {
+    for (int k0 = y; k0 < n; k0 += 64) {
+      double v[8];
+#pragma unroll
+      for (int r = 0; r < 8; ++r) {
+        const int k = k0 + 8 * r;
+        v[r] = k < n ? P[(int64_t)k * ldp + i] : 0.0;
+      }
+#pragma unroll
+      for (int r = 0; r < 8; ++r) {
+        const int k = k0 + 8 * r;
+        const double xv = (dr && k < n) ? v[r] * dr[k] : v[r];
+        const unsigned long long bx = (unsigned long long)__double_as_longlong(xv) & 0x7fffffffffffffffull;
+        bad |= bx >= 0x7ff0000000000000ull;
+        mx = max(mx, bx);
+      }
+    }
+  }
+  s_mx[y][x] = mx;
+  if (__syncthreads_or(bad) && x == 0 && y == 0) {
+    s_bad = 1;
+    atomicExch(err, 1);
+  }
+  __syncthreads();
+  unsigned long long m = s_mx[0][x];
+#pragma unroll
+  for (int yy = 1; yy < 8; ++yy) m = max(m, s_mx[yy][x]);
+  if (s_bad) m = 0ull;  // the slices are not used once the error is raised
+  const int e = m ? frexp_exponent_bits(m) : 0;
+  if (y == 0 && i < np) rowexp[i] = e;
+  for (int k0 = 0; k0 < np; k0 += 64) {
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      const int kl = y + 8 * r, k = k0 + kl;
+      const bool in = i < n && k < n;
+      double xv = in ? P[(int64_t)k * ldp + i] : 0.0;
+      if (dr && in) xv *= dr[k];
+      uint32_t d[kLevels];
+      split_digits(xv, 39 - e, in && m, d);
+#pragma unroll
+      for (int a = 0; a < kLevels; ++a) tile[a][x][kl] = (uint16_t)d[a];
+    }
+    __syncthreads();
+    // warp y writes rows i0 + y + 8 c, lane x the columns k0 + 2 x, k0 + 2 x + 1
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int il = y + 8 * c, ii = i0 + il;
+      if (ii < np) {
+        uint32_t* row = reinterpret_cast<uint32_t*>(Aex + (int64_t)ii * kLevels * np + k0);
+#pragma unroll
+        for (int a = 0; a < kLevels; ++a)
+          row[(int64_t)a * (np / 2) + x] = *reinterpret_cast<const uint32_t*>(&tile[a][il][2 * x]);
+      }
+    }
+    __syncthreads();
+  }
 }
 
 // Rounds each column j < m of the correction D (fp32, ld = mp) to one 8-bit fixed-point slice:
@@ -764,18 +852,27 @@ struct BalancePre {
   const double* t = nullptr;  // row sums of the set's B
   bool trans = false;         // the adjoint (transposed) balance
   bool fp16 = true;
-  double* y = nullptr;        // [np] scratch vectors
-  double* z = nullptr;
+  float* y = nullptr;         // [np] scratch vectors, zero beyond n
+  float* z = nullptr;
 };
 
-template <class T16>
-__device__ __forceinline__ float w16(const void* W, int64_t o) { return (float)reinterpret_cast<const T16*>(W)[o]; }
+// (float)x rounded toward zero on the bit pattern of x (no fp64 pipe): magnitudes below 2^-126
+// give zero, above the float range infinity (NaN too, which the caller's finiteness check
+// then reports). The preconditioner's products only need a correction good to a few bits.
+__device__ __forceinline__ float narrow_rz(double x) {
+  const uint32_t hi = (uint32_t)__double2hiint(x), lo = (uint32_t)__double2loint(x);
+  const uint32_t sign = hi & 0x80000000u, t = hi & 0x7fffffffu;
+  if (t < 0x38100000u) return __uint_as_float(sign);                // below 2^-126
+  if (t >= 0x47f00000u) return __uint_as_float(sign | 0x7f800000u);  // 2^128 and up, inf, NaN
+  return __uint_as_float(sign | ((t - 0x38000000u) << 3) | (lo >> 29));
+}
 
-// First kernel of a preconditioned sweep: the guard (as scaled_transpose16), the zeroing of
-// the sweep's words and of dcolmax[0], then y = t o src (column 0) and, forward, yr = rho o y.
+// The first kernel of a preconditioned sweep: y = diag(t) src (the residual column) and, for
+// the forward balance, yr = rho o y, in fp32; also zeroes the sweep's status words and the
+// correction's column maximum.
 __global__ void pre_first(const double* __restrict__ src, int64_t ld, const double* __restrict__ t,
-                          const double* __restrict__ rho, int n, bool trans, double* __restrict__ y,
-                          double* __restrict__ yr, const SweepGuard guard, unsigned long long* red_cur,
+                          const double* __restrict__ rho, int n, bool trans, float* __restrict__ y,
+                          float* __restrict__ yr, const SweepGuard guard, unsigned long long* red_cur,
                           unsigned int* dcolmax) {
   if (guard.err) {
     __shared__ int s_end;
@@ -791,48 +888,62 @@ __global__ void pre_first(const double* __restrict__ src, int64_t ld, const doub
   if (blockIdx.x == 0 && threadIdx.x == 0) dcolmax[0] = 0u;
   if (i < n) {
     const double v = t[i] * src[(int64_t)i * ld];
-    y[i] = v;
-    if (!trans) yr[i] = rho[i] * v;
+    y[i] = (float)v;
+    if (!trans) yr[i] = (float)(rho[i] * v);
   }
 }
 
-// Forward: z_i = y_i - sum_j F_ij yr_j (one warp per row).
-__global__ void pre_k_apply(const double* __restrict__ F, int n, const double* __restrict__ y,
-                            const double* __restrict__ yr, double* __restrict__ z, const int* skip) {
+// Forward: z_i = y_i - sum_j F_ij yr_j in fp32 (one warp per row, F narrowed on its bits).
+__global__ void pre_k_apply(const double* __restrict__ F, int n, const float* __restrict__ y,
+                            const float* __restrict__ yr, float* __restrict__ z, const int* skip) {
   if (skip && *(volatile const int*)skip) return;
   const int i = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
   const int lane = threadIdx.x & 31;
   if (i >= n) return;
-  double acc = 0.0;
-  for (int j = lane; j < n; j += 32) acc += F[(int64_t)i * (n + 1) + j] * yr[j];
+  const double* row = F + (int64_t)i * (n + 1);
+  float acc = 0.f, acc2 = 0.f;
+  int j = lane;
+  for (; j + 32 < n; j += 64) {
+    acc = fmaf(narrow_rz(row[j]), yr[j], acc);
+    acc2 = fmaf(narrow_rz(row[j + 32]), yr[j + 32], acc2);
+  }
+  if (j < n) acc = fmaf(narrow_rz(row[j]), yr[j], acc);
+  acc += acc2;
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
   if (lane == 0) z[i] = y[i] - acc;
 }
 
 // out_k = sum_i W[k][i] v_i (one warp per row of W, 16-bit W read eight elements at a time,
-// summed in fp32: W is a 16-bit approximate inverse, so fp32 sums are far more accurate than
+// fp32 v and sums: W is a 16-bit approximate inverse, so fp32 sums are far more accurate than
 // needed); with D set, out goes to D[k][0] (fp32) and max_k |out_k| to dcolmax[0]. v is
 // zero beyond n, so the rows' padding (np is a multiple of 128) adds nothing.
 template <class T16>
-__global__ void pre_w_apply(const void* __restrict__ W, int np, int n, const double* __restrict__ v,
-                            double* __restrict__ out, float* __restrict__ D, int64_t ldd, unsigned int* dcolmax,
+__global__ void pre_w_apply(const void* __restrict__ W, int np, int n, const float* __restrict__ v,
+                            float* __restrict__ out, float* __restrict__ D, int64_t ldd, unsigned int* dcolmax,
                             int* nonfinite, const int* skip) {
   if (skip && *(volatile const int*)skip) return;
   const int k = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
   const int lane = threadIdx.x & 31;
   if (k >= n) return;
   const uint4* row = reinterpret_cast<const uint4*>(reinterpret_cast<const T16*>(W) + (int64_t)k * np);
+  const float4* v4 = reinterpret_cast<const float4*>(v);
   float acc = 0.f;
   for (int g = lane; g < np / 8; g += 32) {
     const uint4 w = row[g];
     const T16* h = reinterpret_cast<const T16*>(&w);
-    const double* vv = v + 8 * g;
-#pragma unroll
-    for (int q = 0; q < 8; ++q) acc = fmaf((float)h[q], (float)vv[q], acc);
+    const float4 a = v4[2 * g], b = v4[2 * g + 1];
+    acc = fmaf((float)h[0], a.x, acc);
+    acc = fmaf((float)h[1], a.y, acc);
+    acc = fmaf((float)h[2], a.z, acc);
+    acc = fmaf((float)h[3], a.w, acc);
+    acc = fmaf((float)h[4], b.x, acc);
+    acc = fmaf((float)h[5], b.y, acc);
+    acc = fmaf((float)h[6], b.z, acc);
+    acc = fmaf((float)h[7], b.w, acc);
   }
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
   if (lane == 0) {
-    if (out) out[k] = (double)acc;
+    if (out) out[k] = acc;
     if (D) {
       D[(int64_t)k * ldd] = acc;
       if (!isfinite(acc)) atomicExch(nonfinite, 1);
@@ -841,22 +952,30 @@ __global__ void pre_w_apply(const void* __restrict__ W, int np, int n, const dou
   }
 }
 
-// Adjoint: D_k = w_k - rho_k sum_i F_ik w_i (K^T w), D[k][0] fp32 and max |D| into dcolmax[0].
-// Block (32 x 8) per 32 columns k: thread (x, y) sums rows i = y, y + 8, ... (coalesced in x).
+// Adjoint: D_k = w_k - rho_k sum_i F_ik w_i (K^T w) in fp32, D[k][0] and max |D| into
+// dcolmax[0]. Block (32 x 8) per 32 columns k: thread (x, y) sums rows i = y, y + 8, ...
+// (coalesced in x), F narrowed on its bits.
 __global__ void pre_kt_apply(const double* __restrict__ F, int n, const double* __restrict__ rho,
-                             const double* __restrict__ w, float* __restrict__ D, int64_t ldd, unsigned int* dcolmax,
+                             const float* __restrict__ w, float* __restrict__ D, int64_t ldd, unsigned int* dcolmax,
                              int* nonfinite, const int* skip) {
   if (skip && *(volatile const int*)skip) return;
-  __shared__ double part[8][33];
+  __shared__ float part[8][33];
   const int k = blockIdx.x * 32 + threadIdx.x;
-  double acc = 0.0;
-  if (k < n)
-    for (int i = threadIdx.y; i < n; i += 8) acc += F[(int64_t)i * (n + 1) + k] * w[i];
-  part[threadIdx.y][threadIdx.x] = acc;
+  float acc = 0.f, acc2 = 0.f;
+  if (k < n) {
+    int i = threadIdx.y;
+    for (; i + 8 < n; i += 16) {
+      acc = fmaf(narrow_rz(F[(int64_t)i * (n + 1) + k]), w[i], acc);
+      acc2 = fmaf(narrow_rz(F[(int64_t)(i + 8) * (n + 1) + k]), w[i + 8], acc2);
+    }
+    if (i < n) acc = fmaf(narrow_rz(F[(int64_t)i * (n + 1) + k]), w[i], acc);
+  }
+  part[threadIdx.y][threadIdx.x] = acc + acc2;
   __syncthreads();
   if (threadIdx.y == 0 && k < n) {
-    for (int yy = 1; yy < 8; ++yy) acc += part[yy][threadIdx.x];
-    const float d = (float)(w[k] - rho[k] * acc);
+    float sum = part[0][threadIdx.x];
+    for (int yy = 1; yy < 8; ++yy) sum += part[yy][threadIdx.x];
+    const float d = w[k] - (float)rho[k] * sum;
     D[(int64_t)k * ldd] = d;
     if (!isfinite(d)) atomicExch(nonfinite, 1);
     else atomicMax(dcolmax, __float_as_uint(fabsf(d)));
@@ -1008,7 +1127,10 @@ struct Solver {
 
   // Fixed-point slices of P' = P Dr (Dr may be null).
   rg_status build_slices(const double* dr) {
-    build_p_exact<<<(L.np + 7) / 8, 256, 0, s>>>(P, ldp, transP, dr, L.n, L.np, b.Aex, b.rowexp, err);
+    if (transP)
+      build_p_exact_t<<<L.np / 32, dim3(32, 8), 0, s>>>(P, ldp, dr, L.n, L.np, b.Aex, b.rowexp, err);
+    else
+      build_p_exact<<<(L.np + 7) / 8, 256, 0, s>>>(P, ldp, dr, L.n, L.np, b.Aex, b.rowexp, err);
     ++ctx->launches;
     RG_CUDA_TRY(ctx, cudaGetLastError());
     return RG_OK;
@@ -1382,29 +1504,32 @@ __global__ void balance_adj_rhs(const double* __restrict__ T, const double* __re
   R0[(int64_t)i * mp] = dT[i] / (4.0 * Ti * Ti * Ti) / t[i];
 }
 
+// u_i = T_i^4 (once per set, so that the adjoint's row pass reads it instead of recomputing it
+// per entry on the fp64 pipe).
+__global__ void quartic_powers(const double* __restrict__ T, int n, double* __restrict__ u) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double Ti = T[i];
+  u[i] = Ti * Ti * Ti * Ti;
+}
+
 // dB_ij = -nu_i (u_i - u_j) (u_{n} = T_sink^4), deps_i = -(nu_i / eps_i) sum_j B_ij (u_i - u_j)
-// with nu = g o mu the solution of the transposed balance. One warp per row.
+// with nu = g o mu the solution of the transposed balance and u = T^4 (quartic_powers). One
+// warp per row.
 // dB may be null; with fa / fb set, dB = fa_0 fb_0^T + fa_1 fb_1^T is also written in that
 // factored form: fa_0 = -nu o u, fb_0 = 1; fa_1 = nu, fb_1 = (u, u_sink) (fa [2][n], fb [2][n+1]).
 __global__ void balance_adj_out(const double* __restrict__ B, const double* __restrict__ eps,
-                                const double* __restrict__ T, const double* __restrict__ nu, int64_t ldnu,
+                                const double* __restrict__ u, const double* __restrict__ nu, int64_t ldnu,
                                 double u_sink, int n, double* __restrict__ dB, double* __restrict__ deps,
                                 double* __restrict__ fa, double* __restrict__ fb) {
   const int i = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
   const int lane = threadIdx.x & 31;
   if (i >= n) return;
-  const double Ti = T[i];
-  const double ui = Ti * Ti * Ti * Ti;
+  const double ui = u[i];
   const double v = nu[(int64_t)i * ldnu];
   double s = 0.0;
   for (int j = lane; j <= n; j += 32) {
-    double uj;
-    if (j < n) {
-      double Tj = T[j];
-      uj = Tj * Tj * Tj * Tj;
-    } else {
-      uj = u_sink;
-    }
+    const double uj = j < n ? u[j] : u_sink;
     if (dB) dB[(int64_t)i * (n + 1) + j] = -v * (ui - uj);
     s += B[(int64_t)i * (n + 1) + j] * (ui - uj);
   }
@@ -1595,8 +1720,11 @@ size_t lsq_extra_bytes(int n) {
 
 // Bytes rg_temperatures_sets reserves ahead of its solver (the preconditioner's vectors).
 size_t balance_sets_extra_bytes(int n) {
+  const size_t np = (size_t)(n + NB - 1) / NB * NB;
   rg::Sizer ex;
-  ex.take<double>((size_t)2 * ((n + NB - 1) / NB * NB));
+  ex.take<float>(np);   // y
+  ex.take<float>(np);   // z
+  ex.take<double>(np);  // u = T^4 (adjoint)
   return ex.off;
 }
 
@@ -1678,7 +1806,10 @@ rg_status rg_exact_split(rg_ctx* ctx, int32_t n, const double* P_d, int64_t ldp,
   int* rowexp = cv.take<int>(np);
   int* e = ctx->d_scratch + kStatus;
   RG_CUDA_TRY(ctx, cudaMemsetAsync(e, 0, sizeof(int), s));
-  build_p_exact<<<(np + 7) / 8, 256, 0, s>>>(P_d, ldp, trans != 0, dr_d, n, np, Aex, rowexp, e);
+  if (trans)
+    build_p_exact_t<<<np / 32, dim3(32, 8), 0, s>>>(P_d, ldp, dr_d, n, np, Aex, rowexp, e);
+  else
+    build_p_exact<<<(np + 7) / 8, 256, 0, s>>>(P_d, ldp, dr_d, n, np, Aex, rowexp, e);
   ++ctx->launches;
   RG_CUDA_TRY(ctx, cudaGetLastError());
   bf16_rows_to_int16<<<grid_for((int64_t)n * kLevels * np, ctx->sm_count), kThreads, 0, s>>>(
@@ -1867,9 +1998,12 @@ rg_status rg_temperatures_adjoint(rg_ctx* ctx, int32_t n, const double* B_d, con
   double rel = 0.0;
   st = sv.run(dl, nullptr, tol, 16, &sw, &rel);
   if (st == RG_OK) {
-    balance_adj_out<<<(n + 7) / 8, 256, 0, s>>>(B_d, eps_d, T_d, sv.b.X, sv.L.mp, u_sink, n, dB_d, deps_d, nullptr,
+    // u = T^4 in the right-hand side's buffer, which the finished solve no longer reads
+    double* u4 = sv.b.R0;
+    quartic_powers<<<(n + 255) / 256, 256, 0, s>>>(T_d, n, u4);
+    balance_adj_out<<<(n + 7) / 8, 256, 0, s>>>(B_d, eps_d, u4, sv.b.X, sv.L.mp, u_sink, n, dB_d, deps_d, nullptr,
                                                  nullptr);
-    ++ctx->launches;
+    ctx->launches += 2;
     RG_CUDA_TRY(ctx, cudaGetLastError());
     st = sv.check_errors();
   }
@@ -1900,11 +2034,12 @@ static rg_status temperatures_sets(rg_ctx* ctx, int32_t n, const double* F_d, in
   if (st != RG_OK) return st;
   rg::Carver cv(extra);
   BalancePre pre;
-  pre.y = cv.take<double>(sv.L.np);
-  pre.z = cv.take<double>(sv.L.np);
+  pre.y = cv.take<float>(sv.L.np);
+  pre.z = cv.take<float>(sv.L.np);
+  double* u4 = cv.take<double>(sv.L.np);
   // only entries below n are ever written: the padding stays zero for the row products
-  RG_CUDA_TRY(ctx, cudaMemsetAsync(pre.y, 0, sv.L.np * sizeof(double), s));
-  RG_CUDA_TRY(ctx, cudaMemsetAsync(pre.z, 0, sv.L.np * sizeof(double), s));
+  RG_CUDA_TRY(ctx, cudaMemsetAsync(pre.y, 0, sv.L.np * sizeof(float), s));
+  RG_CUDA_TRY(ctx, cudaMemsetAsync(pre.z, 0, sv.L.np * sizeof(float), s));
   // W ~ (I - F_NN)^-1, shared by every set
   st = sv.set_matrix(F_d, n + 1, false);
   if (st == RG_OK) st = sv.factor(nullptr, nullptr);
@@ -1943,8 +2078,10 @@ static rg_status temperatures_sets(rg_ctx* ctx, int32_t n, const double* F_d, in
     st = sv.refine(dl, tol, 24, &sw, &rel);
     if (st != RG_OK) return st;
     if (adjoint) {
+      quartic_powers<<<(n + 255) / 256, 256, 0, s>>>(T_in + (size_t)set * n, n, u4);
+      ++ctx->launches;
       balance_adj_out<<<(n + 7) / 8, 256, 0, s>>>(
-          B, eps, T_in + (size_t)set * n, sv.b.X, sv.L.mp, u_sink, n, dB_d ? dB_d + (size_t)set * n * (n + 1) : nullptr,
+          B, eps, u4, sv.b.X, sv.L.mp, u_sink, n, dB_d ? dB_d + (size_t)set * n * (n + 1) : nullptr,
           deps_d + (size_t)set * n, fa_d ? fa_d + (size_t)set * 2 * n : nullptr,
           fb_d ? fb_d + (size_t)set * 2 * (n + 1) : nullptr);
     } else {

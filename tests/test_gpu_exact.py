@@ -35,7 +35,8 @@ def split_reference(P, dr):
     return d, e
 
 
-@pytest.mark.parametrize("n,trans,with_dr", [(300, False, True), (300, True, False), (129, False, False)])
+@pytest.mark.parametrize("n,trans,with_dr", [(300, False, True), (300, True, False), (129, False, False),
+                                             (517, True, True), (1000, False, True), (70, True, False)])
 def test_exact_split_matches_its_definition(rg_ctx, n, trans, with_dr):
     rng = np.random.default_rng(n + 7 * trans)
     # entries spread over 40 binades, signs mixed, some exact zeros and one zero row
