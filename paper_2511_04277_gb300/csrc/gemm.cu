@@ -48,6 +48,9 @@ rg_status encode_kmajor(rg_ctx* ctx, CUtensorMap* map, const void* base, bool bf
 template <int BN, int kStages, class Epi, bool kBF16>
 rg_status launch(rg_ctx* ctx, const CUtensorMap& ma, const CUtensorMap& mb, const GemmArgs& args, const Epi& epi,
                  cudaStream_t s);
+template <class Epi, bool kBF16>
+rg_status launch_pair(rg_ctx* ctx, const CUtensorMap& ma, const CUtensorMap& mb, const GemmArgs& args,
+                      const Epi& epi, cudaStream_t s);
 
 // Tile width: the widest of 256 / 128 / 64 that still gives every SM two tiles. A wider
 // tile reuses each A tile over more columns: a 128 x 128 x 64 step moves 32 KB for 2.1
@@ -69,18 +72,18 @@ rg_status gemm(rg_ctx* ctx, bool bf16, const void* A, int64_t lda, const void* B
   if (K <= 0) return rg::fail(ctx, RG_ERR_ARG, "gemm: K = %d", K);
   const int bn = tile_width(ctx, M, N);
   CUtensorMap ma, mb;
+  // 256-wide tiles go to CTA pairs (gemm_pair_kernel): each CTA loads 128 of B's rows
   rg_status st = encode_kmajor(ctx, &ma, A, bf16, M, K, lda, BM);
-  if (st == RG_OK) st = encode_kmajor(ctx, &mb, B, bf16, N, K, ldb, bn);
+  if (st == RG_OK) st = encode_kmajor(ctx, &mb, B, bf16, N, K, ldb, bn == 256 ? 128 : bn);
   if (st != RG_OK) return st;
   GemmArgs args{M, N, K, ctx->d_scratch + kGemmErrorSlot};
   args.skip = skip;
+  if (bn == 256)
+    return bf16 ? launch_pair<Epi, true>(ctx, ma, mb, args, epi, s) : launch_pair<Epi, false>(ctx, ma, mb, args, epi, s);
   if (bn == 64)
     return bf16 ? launch<64, 6, Epi, true>(ctx, ma, mb, args, epi, s) : launch<64, 6, Epi, false>(ctx, ma, mb, args, epi, s);
-  if (bn == 128)
-    return bf16 ? launch<128, 4, Epi, true>(ctx, ma, mb, args, epi, s)
-                : launch<128, 4, Epi, false>(ctx, ma, mb, args, epi, s);
-  return bf16 ? launch<256, 4, Epi, true>(ctx, ma, mb, args, epi, s)
-              : launch<256, 4, Epi, false>(ctx, ma, mb, args, epi, s);
+  return bf16 ? launch<128, 4, Epi, true>(ctx, ma, mb, args, epi, s)
+              : launch<128, 4, Epi, false>(ctx, ma, mb, args, epi, s);
 }
 
 template rg_status gemm<EpiTwoIMinusT<__nv_bfloat16>>(rg_ctx*, bool, const void*, int64_t, const void*, int64_t, int,
@@ -117,6 +120,28 @@ rg_status launch(rg_ctx* ctx, const CUtensorMap& ma, const CUtensorMap& mb, cons
   return RG_OK;
 }
 
+template <class Epi, bool kBF16>
+rg_status launch_pair(rg_ctx* ctx, const CUtensorMap& ma, const CUtensorMap& mb, const GemmArgs& args,
+                      const Epi& epi, cudaStream_t s) {
+  auto kern = gemm_pair_kernel<kPairStages, Epi, kBF16>;
+  constexpr size_t smem = pair_smem_bytes<kPairStages>();
+  static thread_local int configured_device = -1;
+  if (configured_device != ctx->device) {
+    RG_CUDA_TRY(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    configured_device = ctx->device;
+  }
+  // two CTAs (one cluster) per 256 x 256 tile
+  dim3 grid(2 * ((args.N + 255) / 256) * ((args.M + 2 * BM - 1) / (2 * BM)));
+  const double executed = 2.0 * args.M * (double)args.N * args.K;
+  const int tok = rg::timer_begin(ctx, rg::kTimeGemm, s, executed,
+                                  args.alg_k > 0 ? 2.0 * args.M * (double)args.N * args.alg_k : executed);
+  kern<<<grid, kThreads, smem, s>>>(ma, mb, args, epi);
+  rg::timer_end(ctx, tok, s);
+  ++ctx->launches;
+  RG_CUDA_TRY(ctx, cudaGetLastError());
+  return RG_OK;
+}
+
 }  // namespace
 
 rg_status gemm_f32(rg_ctx* ctx, bool bf16, const void* A, int64_t lda, const void* B, int64_t ldb, int M, int N,
@@ -126,13 +151,13 @@ rg_status gemm_f32(rg_ctx* ctx, bool bf16, const void* A, int64_t lda, const voi
   const int bn = tile_width(ctx, M, N) == 256 ? 256 : 128;
   CUtensorMap ma, mb;
   rg_status st = encode_kmajor(ctx, &ma, A, bf16, M, K, lda, BM);
-  if (st == RG_OK) st = encode_kmajor(ctx, &mb, B, bf16, N, K, ldb, bn);
+  if (st == RG_OK) st = encode_kmajor(ctx, &mb, B, bf16, N, K, ldb, 128);
   if (st != RG_OK) return st;
   GemmArgs args{M, N, K, ctx->d_scratch + kGemmErrorSlot};
   EpiF32 epi{C, ldc, alpha, beta};
   if (bn == 256)
-    return bf16 ? launch<256, 4, EpiF32, true>(ctx, ma, mb, args, epi, s)
-                : launch<256, 4, EpiF32, false>(ctx, ma, mb, args, epi, s);
+    return bf16 ? launch_pair<EpiF32, true>(ctx, ma, mb, args, epi, s)
+                : launch_pair<EpiF32, false>(ctx, ma, mb, args, epi, s);
   return bf16 ? launch<128, 4, EpiF32, true>(ctx, ma, mb, args, epi, s)
               : launch<128, 4, EpiF32, false>(ctx, ma, mb, args, epi, s);
 }

@@ -523,6 +523,64 @@ __global__ void __launch_bounds__(256) quantize_correction_narrow(
   if (threadIdx.x == 0 && s_xmax) atomicMax(&red[1], s_xmax);
 }
 
+// The exact level product for m <= kNarrow right-hand sides, on the CUDA cores: a matrix-vector
+// product is bound by reading the slices, which a tensor-core tile of 64 columns would read
+// no faster. lev[a][i][j] = sum_k Aex[i][a np + k] Bq[j][k] for a < L (the level count from
+// the sweep's words), the layout of gemm_exact with one split. Exact: lane l sums the np / 32
+// products of its k (|s| <= 128, |d| <= 127, so |sum| <= 1,024 x 16,256 < 2^24 for np <= 32,768)
+// in fp32, and the lanes' sums are added as int32. One warp per row i, eight k per 16-byte
+// load and eight loads of the slices in flight per lane; bf16 widens to fp32 by a shift.
+// M = m (1 .. kNarrow).
+template <int M>
+__global__ void __launch_bounds__(256) exact_gemv_narrow(const __nv_bfloat16* __restrict__ Aex,
+                                                         const __nv_bfloat16* __restrict__ Bq, int n, int np,
+                                                         int32_t* __restrict__ lev, int64_t ldl, int64_t plane,
+                                                         const unsigned long long* red, const int* skip) {
+  if (skip && *(volatile const int*)skip) return;
+  constexpr int kU = 8;  // loads in flight per lane
+  const int i = blockIdx.x * 8 + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (i >= n) return;
+  const int L = exact_levels(red);
+  const int groups = np / 8;  // uint4 groups of a row
+  for (int a = 0; a < L; ++a) {
+    const uint4* arow = reinterpret_cast<const uint4*>(Aex + ((int64_t)i * kLevels + a) * np);
+    float acc[M];
+#pragma unroll
+    for (int j = 0; j < M; ++j) acc[j] = 0.f;
+    for (int g0 = lane; g0 < groups; g0 += 32 * kU) {
+      uint4 av[kU];
+#pragma unroll
+      for (int u = 0; u < kU; ++u) {
+        const int g = g0 + 32 * u;
+        av[u] = g < groups ? __ldcs(arow + g) : make_uint4(0u, 0u, 0u, 0u);
+      }
+#pragma unroll
+      for (int u = 0; u < kU; ++u) {
+        const int g = g0 + 32 * u;
+        if (g >= groups) break;
+        const uint32_t aw[4] = {av[u].x, av[u].y, av[u].z, av[u].w};
+#pragma unroll
+        for (int j = 0; j < M; ++j) {
+          const uint4 bv = reinterpret_cast<const uint4*>(Bq + (int64_t)j * np)[g];
+          const uint32_t bw[4] = {bv.x, bv.y, bv.z, bv.w};
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            acc[j] = fmaf(__uint_as_float(aw[q] << 16), __uint_as_float(bw[q] << 16), acc[j]);
+            acc[j] = fmaf(__uint_as_float(aw[q] & 0xffff0000u), __uint_as_float(bw[q] & 0xffff0000u), acc[j]);
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < M; ++j) {
+      int v = __float2int_rn(acc[j]);
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (lane == 0) lev[(int64_t)a * plane + (int64_t)i * ldl + j] = v;
+    }
+  }
+}
+
 __global__ void __launch_bounds__(256) finish_residual_narrow(
     const int32_t* __restrict__ lev, int64_t ldl, int64_t plane, int splits, const int* __restrict__ rowexp,
     const int* __restrict__ dexp, const int16_t* __restrict__ Dn, const double* __restrict__ dl, int n, int m, int mp,
@@ -1248,9 +1306,22 @@ struct Solver {
     ++ctx->launches;
     RG_CUDA_TRY(ctx, cudaGetLastError());
     // levels from max|D| / max|X| of this sweep (rc[2] / rc[1]), read on the device
-    st = tc::gemm_exact(ctx, b.Aex, (int64_t)kLevels * L.np, b.Bq, L.np, L.n, L.m, L.np, nullptr, rc, kLevelBits,
-                        kLevels, b.lev, exact_splits(L.n, L.m), &splits, s, skip, L.n);
-    if (st != RG_OK) return st;
+    if (L.m <= kNarrow) {
+      using Gemv = void (*)(const __nv_bfloat16*, const __nv_bfloat16*, int, int, int32_t*, int64_t, int64_t,
+                            const unsigned long long*, const int*);
+      static constexpr Gemv kGemv[kNarrow] = {exact_gemv_narrow<1>, exact_gemv_narrow<2>, exact_gemv_narrow<3>,
+                                              exact_gemv_narrow<4>, exact_gemv_narrow<5>, exact_gemv_narrow<6>,
+                                              exact_gemv_narrow<7>, exact_gemv_narrow<8>};
+      kGemv[L.m - 1]<<<(L.n + 7) / 8, 256, 0, s>>>(b.Aex, b.Bq, L.n, L.np, b.lev, tc::exact_ld(L.m),
+                                                    tc::exact_plane(L.n, L.m), rc, skip);
+      ++ctx->launches;
+      RG_CUDA_TRY(ctx, cudaGetLastError());
+      splits = 1;
+    } else {
+      st = tc::gemm_exact(ctx, b.Aex, (int64_t)kLevels * L.np, b.Bq, L.np, L.n, L.m, L.np, nullptr, rc, kLevelBits,
+                          kLevels, b.lev, exact_splits(L.n, L.m), &splits, s, skip, L.n);
+      if (st != RG_OK) return st;
+    }
     dim3 fg((L.m + 127) / 128, (L.n + 127) / 128);
     if (L.m <= kNarrow)
       finish_residual_narrow<<<nb, 256, 0, s>>>(b.lev, tc::exact_ld(L.m), tc::exact_plane(L.n, L.m), splits,

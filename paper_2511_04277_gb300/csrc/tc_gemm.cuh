@@ -101,6 +101,81 @@ __device__ __forceinline__ void umma_commit(uint64_t* bar) {
                : "memory");
 }
 
+// ---- CTA pairs (cta_group::2): a cluster of two CTAs computes one 256-row tile, each CTA
+// holding its 128 rows of A and half of the tile's columns of B in shared memory at the same
+// offsets; one thread of the even CTA issues the MMAs, and each CTA's tensor memory receives
+// its 128 rows of the product.
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+// shared::cluster address of the same shared location in CTA `rank` of the cluster
+__device__ __forceinline__ uint32_t mapa_shared(uint32_t saddr, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(saddr), "r"(rank));
+  return r;
+}
+__device__ __forceinline__ void cluster_sync() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\nbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+// one arrival on an mbarrier of another CTA of the cluster (no memory ordering: the data the
+// arrival announces is already in place, in shared memory or tensor memory)
+__device__ __forceinline__ void mbar_arrive_remote(uint32_t cluster_addr) {
+  asm volatile("mbarrier.arrive.relaxed.cluster.shared::cluster.b64 _, [%0];" ::"r"(cluster_addr) : "memory");
+}
+// mbar_wait with cluster-scope acquire, for phases completed by the other CTA of the pair
+__device__ __forceinline__ bool mbar_wait_cluster(uint64_t* bar, uint32_t parity, uint64_t limit_ns = kWaitNs) {
+  uint32_t addr = smem_u32(bar);
+  uint64_t t0 = 0;
+  for (uint32_t i = 1;; ++i) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(addr), "r"(parity)
+        : "memory");
+    if (ok) return true;
+    if ((i & 255u) == 0) {
+      uint64_t now = global_ns();
+      if (t0 == 0) t0 = now;
+      else if (now - t0 > limit_ns) return false;
+    }
+  }
+}
+// tensor memory of both CTAs of the pair: one warp of each CTA takes part (the same columns
+// in both)
+__device__ __forceinline__ void tmem_alloc_pair(uint32_t* dst_smem, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst_smem)),
+               "r"(ncols));
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;");
+}
+__device__ __forceinline__ void tmem_dealloc_pair(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols));
+}
+__device__ __forceinline__ void umma_f16_pair(uint32_t tmem_d, uint64_t a_desc, uint64_t b_desc, uint32_t idesc,
+                                              uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+      "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+// one arrival on the barrier at this offset in both CTAs once this thread's prior tcgen05
+// operations have completed
+__device__ __forceinline__ void umma_commit_pair_both(uint64_t* bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+          smem_u32(bar)),
+      "h"((uint16_t)3)
+      : "memory");
+}
+__device__ __forceinline__ void umma_commit_pair_local(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+
 // 32 consecutive fp32 columns of this thread's TMEM lane.
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
   uint32_t r[32];
@@ -388,6 +463,150 @@ template <int BN, int kStages>
 constexpr size_t smem_bytes() {
   return 1024 + (size_t)kStages * (BM * BK * 2 + BN * BK * 2) + (2 * kStages + 3) * 8 + 16;
 }
+
+// gemm_kernel on CTA pairs (cluster of 2, cta_group::2): the pair computes a 256 x 256 tile;
+// each CTA loads its 128 rows of A and 128 of the tile's 256 rows of B per K block (32 KB a
+// stage instead of 48 KB, so kStages = 6 fit where the one-CTA kernel holds 4: the deeper
+// ring hides more of the L2 latency, and the pair reads B once for both row halves). Warp
+// roles as gemm_kernel, with:
+//   warp 0 (both CTAs)   TMA into its own stage ring, completion on its own full[s];
+//   warp 1, even CTA     the MMAs of the pair (M = 256, N = 256) once full[s] has both its
+//                        own bytes and the odd CTA's arrival, committing to empty[s] and
+//                        acc_full of both CTAs;
+//   warp 1, odd CTA      relays each of its full stages to the even CTA's full[s];
+//   warps 2..5           the epilogue of the CTA's own 128 rows (tensor memory of its own).
+// Grid: two CTAs per tile, grouped rasterisation over the tiles as gemm_kernel.
+template <int kStages, class Epi, bool kBF16>
+__global__ void __launch_bounds__(kThreads, 1) __cluster_dims__(2, 1, 1)
+    gemm_pair_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_b,
+                     const GemmArgs args, const Epi epi) {
+  constexpr int PN = 256;  // columns of the pair's tile
+  constexpr uint32_t kABytes = BM * BK * 2, kBBytes = (PN / 2) * BK * 2;
+  constexpr uint32_t kTmemCols = PN;
+  constexpr uint32_t kIdesc = idesc_f16(2 * BM, PN, kBF16);
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint8_t* sA = smem;
+  uint8_t* sB = smem + kStages * kABytes;
+  uint64_t* full = reinterpret_cast<uint64_t*>(sB + kStages * kBBytes);
+  uint64_t* empty = full + kStages;
+  uint64_t* acc_full = empty + kStages;  // [1]
+  uint64_t* drain = acc_full + 1;        // [1]
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
+  __shared__ int s_abort;
+  __shared__ float s_stage[4][32][33];
+
+  // uniform over the pair (both read the same word): before any barrier or allocation
+  if (args.skip && *(volatile const int*)args.skip) return;
+  const uint32_t rank = cluster_rank();
+  const bool leader = rank == 0;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int tiles_m = (args.M + 2 * BM - 1) / (2 * BM), tiles_n = (args.N + PN - 1) / PN;
+  const int pid = blockIdx.x >> 1;
+  const int group = pid / (kGroupM * tiles_n);
+  const int first_m = group * kGroupM;
+  const int group_m = min(tiles_m - first_m, kGroupM);
+  const int tile_m = first_m + (pid % (kGroupM * tiles_n)) % group_m;
+  const int tile_n = (pid % (kGroupM * tiles_n)) / group_m;
+  const int m0 = tile_m * 2 * BM + (int)rank * BM;         // this CTA's rows
+  const int nb0 = tile_n * PN + (int)rank * (PN / 2);      // this CTA's half of B's rows
+  const int n0 = tile_n * PN;                              // the tile's columns
+  const int kb_total = (args.K + BK - 1) / BK;
+
+  if (threadIdx.x == 0) {
+    s_abort = 0;
+    for (int s = 0; s < kStages; ++s) {
+      mbar_init(&full[s], leader ? 2 : 1);  // even CTA: its own expect_tx and the odd CTA's relay
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(acc_full, 1);
+    mbar_init(drain, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 1) tmem_alloc_pair(tmem_slot, kTmemCols);
+  tc_fence_before();
+  __syncthreads();
+  cluster_sync();  // both CTAs' barriers exist before any arrival from the other
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+  volatile int* abort_flag = &s_abort;
+
+  if (warp == 0) {
+    // ---------------- TMA producer (both CTAs)
+    if (lane == 0) {
+      for (int kb = 0; kb < kb_total; ++kb) {
+        const int s = kb % kStages;
+        if (kb >= kStages && !mbar_wait_cluster(&empty[s], ((kb / kStages) - 1) & 1)) { *abort_flag = 1; break; }
+        if (*abort_flag) break;
+        mbar_expect_tx(&full[s], kABytes + kBBytes);
+        tma_load_2d(sA + s * kABytes, &map_a, &full[s], kb * BK, m0);
+        tma_load_2d(sB + s * kBBytes, &map_b, &full[s], kb * BK, nb0);
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      if (leader) {
+        // ---------------- MMA issuer of the pair
+        for (int kb = 0; kb < kb_total && !*abort_flag; ++kb) {
+          const int s = kb % kStages;
+          if (!mbar_wait_cluster(&full[s], (kb / kStages) & 1)) { *abort_flag = 1; break; }
+          tc_fence_after();
+          const uint32_t a_addr = smem_u32(sA + s * kABytes), b_addr = smem_u32(sB + s * kBBytes);
+#pragma unroll
+          for (int kk = 0; kk < BK / 16; ++kk)
+            umma_f16_pair(tmem_base, sw128_desc(a_addr + kk * 32), sw128_desc(b_addr + kk * 32), kIdesc,
+                          (kb > 0 || kk > 0) ? 1u : 0u);
+          umma_commit_pair_both(&empty[s]);
+        }
+        if (!*abort_flag) umma_commit_pair_both(acc_full);
+        // every MMA this thread issued has completed once `drain` fires
+        umma_commit_pair_local(drain);
+        mbar_wait(drain, 0);
+      } else {
+        // ---------------- relay: this CTA's stage s is full -> one arrival on the even CTA's full[s]
+        const uint32_t leader_full = mapa_shared(smem_u32(full), 0);
+        for (int kb = 0; kb < kb_total; ++kb) {
+          const int s = kb % kStages;
+          if (!mbar_wait(&full[s], (kb / kStages) & 1)) { *abort_flag = 1; break; }
+          mbar_arrive_remote(leader_full + 8u * (uint32_t)s);
+        }
+      }
+    }
+  } else {
+    // ---------------- epilogue warps 2 .. 5: this CTA's 128 rows
+    const int ew = warp - 2;
+    const int quarter = warp & 3;
+    const int row0 = m0 + quarter * 32;
+    const uint32_t lane_addr = (uint32_t)(quarter * 32) << 16;
+    float(*stage)[33] = s_stage[ew];
+    if (mbar_wait_cluster(acc_full, 0)) {
+      tc_fence_after();
+      float v[32];
+#pragma unroll 1
+      for (int c0 = 0; c0 < PN; c0 += 32) {
+        tmem_ld32(tmem_base + lane_addr + (uint32_t)c0, v);
+        epi.store(row0, lane, n0 + c0, args.M, args.N, v, stage);
+      }
+    } else {
+      *abort_flag = 1;
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  cluster_sync();  // the pair's MMAs and relays no longer touch either CTA's shared memory
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc_pair(tmem_base, kTmemCols);
+  }
+  if (threadIdx.x == 0 && *abort_flag && args.error_word) atomicExch(args.error_word, 1);
+}
+
+template <int kStages>
+constexpr size_t pair_smem_bytes() {
+  return 1024 + (size_t)kStages * (BM * BK * 2 + 128 * BK * 2) + (2 * kStages + 2) * 8 + 16;
+}
+constexpr int kPairStages = 6;
 
 // ------------------------------------------------------------------ exact level GEMM
 // The product of the exact refinement (solve.cu): for levels a = 0 .. L-1,

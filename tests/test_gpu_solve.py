@@ -57,9 +57,13 @@ def test_tc_gemm_matches_fp64_of_rounded_operands(rg_ctx, M, N, K, dt):
 
 
 @pytest.mark.parametrize("dt", [torch.bfloat16, torch.float16])
-def test_tc_gemm_wide_tiles_with_ragged_edges(rg_ctx, dt):
-    """Enough tiles for the 128 x 256 tile path (two per SM), with partial tiles on both edges."""
-    M, N, K = 5000, 4931, 200
+@pytest.mark.parametrize("M", [5000, 4900])
+def test_tc_gemm_wide_tiles_with_ragged_edges(rg_ctx, dt, M):
+    """Enough tiles for the CTA-pair path (256 x 256 tiles, two CTAs each), with partial tiles on
+    both edges: at N = 4,931 the odd CTA's half of B in the last column tile lies wholly
+    beyond N, at M = 4,900 its rows in the last row tile lie wholly beyond M, and K = 200 ends
+    in a partial K block."""
+    N, K = 4931, 200
     g = torch.Generator().manual_seed(7)
     A = torch.randn(M, K, generator=g).to(dt)
     B = torch.randn(N, K, generator=g).to(dt)
