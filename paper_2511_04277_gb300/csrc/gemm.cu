@@ -163,7 +163,8 @@ rg_status gemm_f32(rg_ctx* ctx, bool bf16, const void* A, int64_t lda, const voi
 }
 
 int64_t exact_ld(int N) { return ((int64_t)N + 255) / 256 * 256; }
-int64_t exact_plane(int M, int N) { return ((int64_t)M + BM - 1) / BM * BM * exact_ld(N); }
+// rows rounded up to 256: a CTA pair's tile reaches that far
+int64_t exact_plane(int M, int N) { return ((int64_t)M + 2 * BM - 1) / (2 * BM) * (2 * BM) * exact_ld(N); }
 
 namespace {
 
@@ -187,6 +188,26 @@ rg_status launch_exact(rg_ctx* ctx, const CUtensorMap& ma, const CUtensorMap& mb
   return RG_OK;
 }
 
+rg_status launch_exact_pair(rg_ctx* ctx, const CUtensorMap& ma, const CUtensorMap& mb, ExactArgs args, cudaStream_t s,
+                            double flops_per_level, double alg) {
+  auto kern = gemm_exact_pair_kernel<kPairStages>;
+  constexpr size_t smem = exact_pair_smem_bytes<kPairStages>();
+  static thread_local int configured_device = -1;
+  if (configured_device != ctx->device) {
+    RG_CUDA_TRY(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    configured_device = ctx->device;
+  }
+  // two CTAs (one cluster) per 256 x 256 tile, no K splits
+  dim3 grid(2 * ((args.N + 255) / 256) * ((args.M + 2 * BM - 1) / (2 * BM)), 1, 1);
+  const int tok = rg::timer_begin(ctx, rg::kTimeResidualGemm, s, flops_per_level, alg);
+  args.level_log = rg::timer_level_slot(ctx, tok);
+  kern<<<grid, exact_threads(256), smem, s>>>(ma, mb, args);
+  rg::timer_end(ctx, tok, s);
+  ++ctx->launches;
+  RG_CUDA_TRY(ctx, cudaGetLastError());
+  return RG_OK;
+}
+
 }  // namespace
 
 rg_status gemm_exact(rg_ctx* ctx, const void* A, int64_t lda, const void* B, int64_t ldb, int M, int N, int np,
@@ -199,22 +220,25 @@ rg_status gemm_exact(rg_ctx* ctx, const void* A, int64_t lda, const void* B, int
   const int64_t tm = (M + BM - 1) / BM;
   const int bn = tm * ((N + 255) / 256) >= ctx->sm_count ? 256 : (tm * ((N + 127) / 128) >= ctx->sm_count ? 128 : 64);
   const int tiles = (int)(tm * ((N + bn - 1) / bn));
+  // CTA pairs (256 x 256 tiles) when the 256-wide tiles fill the GPU twice over
+  const bool pair = bn == 256 && tiles >= 2 * ctx->sm_count;
   // K splits (whole chunks per CTA and level) while the tiles leave SMs idle
   const int kb_level = np / BK;
   int splits = 1;
-  for (int z = 2; z <= split_max; ++z) {
+  for (int z = 2; z <= split_max && !pair; ++z) {
     if ((int64_t)tiles * (z - 1) >= ctx->sm_count) break;
     if (kb_level % (2 * z) == 0) splits = z;
   }
   if (splits_out) *splits_out = splits;
   CUtensorMap ma, mb;
   rg_status st = encode_kmajor(ctx, &ma, A, true, M, (int64_t)max_levels * np, lda, BM);
-  if (st == RG_OK) st = encode_kmajor(ctx, &mb, B, true, N, np, ldb, bn);
+  if (st == RG_OK) st = encode_kmajor(ctx, &mb, B, true, N, np, ldb, pair ? 128 : bn);
   if (st != RG_OK) return st;
   ExactArgs args{M,   N,        np, levels_d, level_words, level_bits, max_levels, lev, exact_ld(N), exact_plane(M, N),
                  splits > 1 ? kb_level / splits : 0, ctx->d_scratch + kGemmErrorSlot, skip};
   const double per_level = 2.0 * M * (double)N * np;
   const double alg = 2.0 * M * (double)N * (alg_k > 0 ? alg_k : np);
+  if (pair) return launch_exact_pair(ctx, ma, mb, args, s, per_level, alg);
   if (bn == 256) return launch_exact<256, 4>(ctx, ma, mb, args, splits, s, per_level, alg);
   if (bn == 128) return launch_exact<128, 4>(ctx, ma, mb, args, splits, s, per_level, alg);
   return launch_exact<64, 6>(ctx, ma, mb, args, splits, s, per_level, alg);

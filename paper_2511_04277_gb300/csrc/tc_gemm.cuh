@@ -830,6 +830,200 @@ constexpr size_t exact_smem_bytes() {
   return 1024 + (size_t)kStages * (BM * BK * 2 + BN * BK * 2) + (2 * kStages + 5) * 8 + 16;
 }
 
+// gemm_exact_kernel on CTA pairs (cluster of 2, cta_group::2), 256 x 256 tiles: each CTA
+// loads its 128 rows of the slices and 128 of the tile's 256 rows of B per K block (32 KB a
+// stage, kPairStages of them), the even CTA's thread issues the MMAs of the pair into both
+// CTAs' two chunk accumulators (512 tensor-memory columns in each), and each CTA's epilogue
+// adds and stores the level sums of its own 128 rows. A chunk buffer is free again once all
+// eight epilogue warps of the pair have drained it (one arrival per warp on the even CTA's
+// acc_empty; the odd CTA's warps arrive remotely). Level count, chunking, splits and stores
+// as gemm_exact_kernel.
+template <int kStages>
+__global__ void __launch_bounds__(exact_threads(256), 1) __cluster_dims__(2, 1, 1)
+    gemm_exact_pair_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_b,
+                           const ExactArgs args) {
+  constexpr int PN = 256;
+  constexpr int kGroups = exact_groups(PN);  // 2 epilogue groups of four warps (128 columns each)
+  constexpr int kCols = PN / kGroups;
+  constexpr int kEpiWarps = 4 * kGroups;
+  constexpr uint32_t kABytes = BM * BK * 2, kBBytes = (PN / 2) * BK * 2;
+  constexpr uint32_t kTmemCols = 2 * PN;
+  constexpr uint32_t kIdesc = idesc_f16(2 * BM, PN, true);
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint8_t* sA = smem;
+  uint8_t* sB = smem + kStages * kABytes;
+  uint64_t* full = reinterpret_cast<uint64_t*>(sB + kStages * kBBytes);
+  uint64_t* empty = full + kStages;
+  uint64_t* acc_full = empty + kStages;  // [2]
+  uint64_t* acc_empty = acc_full + 2;    // [2] (even CTA)
+  uint64_t* drain = acc_empty + 2;       // [1]
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
+  __shared__ int s_abort;
+
+  const bool skipped = args.skip && *(volatile const int*)args.skip;
+  const int L = skipped ? 0
+                        : (args.levels ? *(volatile const int*)args.levels
+                                       : exact_level_count(args.level_words, args.level_bits, args.max_levels));
+  if (args.level_log && threadIdx.x == 0 && blockIdx.x == 0 && blockIdx.z == 0) *args.level_log = L;
+  if (skipped) return;  // uniform over the pair: before any barrier or allocation
+  if (L < 1 || L > args.max_levels) {
+    if (threadIdx.x == 0 && args.error_word) atomicExch(args.error_word, 1);
+    return;
+  }
+  const uint32_t rank = cluster_rank();
+  const bool leader = rank == 0;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int tiles_m = (args.M + 2 * BM - 1) / (2 * BM), tiles_n = (args.N + PN - 1) / PN;
+  const int pid = blockIdx.x >> 1;
+  const int group = pid / (kGroupM * tiles_n);
+  const int first_m = group * kGroupM;
+  const int group_m = min(tiles_m - first_m, kGroupM);
+  const int tile_m = first_m + (pid % (kGroupM * tiles_n)) % group_m;
+  const int tile_n = (pid % (kGroupM * tiles_n)) / group_m;
+  const int m0 = tile_m * 2 * BM + (int)rank * BM;
+  const int nb0 = tile_n * PN + (int)rank * (PN / 2);
+  const int n0 = tile_n * PN;
+  const int kb_level = args.np / BK;
+  const int kb_first = args.split_blocks > 0 ? blockIdx.z * args.split_blocks : 0;
+  const int kb_per = args.split_blocks > 0 ? min(args.split_blocks, kb_level - kb_first) : kb_level;
+  const int chunks_per_level = (kb_per + kExactChunkBlocks - 1) / kExactChunkBlocks;
+  const int n_chunks = L * chunks_per_level;
+  const int total_kb = L * kb_per;
+
+  if (threadIdx.x == 0) {
+    s_abort = 0;
+    for (int s = 0; s < kStages; ++s) {
+      mbar_init(&full[s], leader ? 2 : 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&acc_full[b], 1);
+      mbar_init(&acc_empty[b], 2 * kEpiWarps);
+    }
+    mbar_init(drain, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 1) tmem_alloc_pair(tmem_slot, kTmemCols);
+  tc_fence_before();
+  __syncthreads();
+  cluster_sync();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+  volatile int* abort_flag = &s_abort;
+
+  if (warp == 0) {
+    // ---------------- TMA producer (both CTAs): level a, block kb of the CTA's K range
+    if (lane == 0) {
+      for (int t = 0; t < total_kb; ++t) {
+        const int s = t % kStages;
+        if (t >= kStages && !mbar_wait_cluster(&empty[s], ((t / kStages) - 1) & 1)) { *abort_flag = 1; break; }
+        if (*abort_flag) break;
+        const int a = t / kb_per, kb = kb_first + t % kb_per;
+        mbar_expect_tx(&full[s], kABytes + kBBytes);
+        tma_load_2d(sA + s * kABytes, &map_a, &full[s], a * args.np + kb * BK, m0);
+        tma_load_2d(sB + s * kBBytes, &map_b, &full[s], kb * BK, nb0);
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      if (leader) {
+        // ---------------- MMA issuer of the pair: one accumulation per chunk, two buffers
+        int t = 0;
+        for (int c = 0; c < n_chunks && !*abort_flag; ++c) {
+          const int b = c & 1;
+          if (c >= 2 && !mbar_wait_cluster(&acc_empty[b], ((c >> 1) - 1) & 1)) { *abort_flag = 1; break; }
+          const uint32_t d_tmem = tmem_base + (uint32_t)(b * PN);
+          const int c_in = c % chunks_per_level;
+          const int nq = min(kExactChunkBlocks, kb_per - c_in * kExactChunkBlocks);
+          for (int q = 0; q < nq; ++q, ++t) {
+            const int s = t % kStages;
+            if (!mbar_wait_cluster(&full[s], (t / kStages) & 1)) { *abort_flag = 1; break; }
+            tc_fence_after();
+            const uint32_t a_addr = smem_u32(sA + s * kABytes), b_addr = smem_u32(sB + s * kBBytes);
+#pragma unroll
+            for (int kk = 0; kk < BK / 16; ++kk)
+              umma_f16_pair(d_tmem, sw128_desc(a_addr + kk * 32), sw128_desc(b_addr + kk * 32), kIdesc,
+                            (q > 0 || kk > 0) ? 1u : 0u);
+            umma_commit_pair_both(&empty[s]);
+          }
+          if (*abort_flag) break;
+          umma_commit_pair_both(&acc_full[b]);
+        }
+        umma_commit_pair_local(drain);
+        mbar_wait(drain, 0);
+      } else {
+        // ---------------- relay of this CTA's full stages to the even CTA
+        const uint32_t leader_full = mapa_shared(smem_u32(full), 0);
+        for (int t = 0; t < total_kb; ++t) {
+          const int s = t % kStages;
+          if (!mbar_wait(&full[s], (t / kStages) & 1)) { *abort_flag = 1; break; }
+          mbar_arrive_remote(leader_full + 8u * (uint32_t)s);
+        }
+      }
+    }
+  } else {
+    // ---------------- epilogue: int32 level sums of this CTA's rows, one row per thread
+    const int ew = warp - 2;
+    const int quarter = warp & 3;
+    const int cbase = (ew >> 2) * kCols;
+    const int row = m0 + quarter * 32 + lane;
+    const uint32_t lane_addr = (uint32_t)(quarter * 32) << 16;
+    const uint32_t empty_addr = mapa_shared(smem_u32(acc_empty), 0);  // the even CTA's, from either CTA
+    uint32_t acc[kCols];
+#pragma unroll
+    for (int i = 0; i < kCols; ++i) acc[i] = 0u;
+    int in_level = 0;
+    for (int c = 0; c < n_chunks; ++c) {
+      const int b = c & 1;
+      if (!mbar_wait_cluster(&acc_full[b], (c >> 1) & 1)) { *abort_flag = 1; break; }
+      tc_fence_after();
+#pragma unroll
+      for (int c0 = 0; c0 < kCols; c0 += 32) {
+        float v[32];
+        tmem_ld32(tmem_base + lane_addr + (uint32_t)(b * PN + cbase + c0), v);
+        // v is an integer of magnitude below 2^24, exact in fp32: converted exactly
+#pragma unroll
+        for (int i = 0; i < 32; ++i) acc[c0 + i] += (uint32_t)__float2int_rn(v[i]);
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive_remote(empty_addr + 8u * (uint32_t)b);
+      if (++in_level == chunks_per_level) {
+        // rows at and beyond M land in the plane's padding (exact_plane rounds M up to 256)
+        const int a = c / chunks_per_level;
+        int32_t* dst = args.lev + ((int64_t)blockIdx.z * args.max_levels + a) * args.plane + (int64_t)row * args.ldl +
+                       n0 + cbase;
+#pragma unroll
+        for (int i = 0; i < kCols; i += 4) {
+          int4 w;
+          w.x = (int32_t)acc[i];
+          w.y = (int32_t)acc[i + 1];
+          w.z = (int32_t)acc[i + 2];
+          w.w = (int32_t)acc[i + 3];
+          *reinterpret_cast<int4*>(dst + i) = w;
+          acc[i] = acc[i + 1] = acc[i + 2] = acc[i + 3] = 0u;
+        }
+        in_level = 0;
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  cluster_sync();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc_pair(tmem_base, kTmemCols);
+  }
+  if (threadIdx.x == 0 && *abort_flag && args.error_word) atomicExch(args.error_word, 1);
+}
+
+template <int kStages>
+constexpr size_t exact_pair_smem_bytes() {
+  return 1024 + (size_t)kStages * (BM * BK * 2 + 128 * BK * 2) + (2 * kStages + 5) * 8 + 16;
+}
+
 
 // ------------------------------------------------------------------ host side
 // Launch D = A B^T (A [M x K], B [N x K], 16-bit K-major) with the epilogue `epi`;
@@ -848,7 +1042,7 @@ rg_status gemm_f32(rg_ctx* ctx, bool bf16, const void* A, int64_t lda, const voi
 // L levels that *levels_d names, int32 sums to lev (see ExactArgs); tiles of 128 x 256 where
 // they give every SM a tile, else narrower; K split over up to split_max CTAs per tile when
 // the tiles leave SMs idle. lev needs split_max x max_levels planes of
-// exact_plane(M, N) int32; *splits_out receives the splits used. alg_k: the inner dimension of
+// exact_plane(M, N) int32 (rows rounded up to 256); *splits_out receives the splits used. alg_k: the inner dimension of
 // the product the launch stands for (kernel timer accounting).
 int64_t exact_ld(int N);
 int64_t exact_plane(int M, int N);

@@ -80,6 +80,8 @@ def _ints(rng, shape, extreme=False, top=128, col_signs=None):
     (257, 300, 384, 5, True),      # a level shorter than one chunk
     (4096, 2560, 512, 2, False),   # 128 x 256 tiles
     (2048, 2049, 384, 4, True),    # 128 x 128 tiles with a one-column tail
+    (4097, 2600, 512, 3, True),    # CTA pairs (256 x 256): the last pair's odd CTA lies beyond M
+    (4000, 2600, 1152, 2, "aligned"),  # CTA pairs, a full chunk of one sign and a short one
 ])
 def test_exact_gemm_is_integer_exact(rg_ctx, M, N, np_, levels, extreme):
     rng = np.random.default_rng(M + N + levels)
