@@ -417,10 +417,17 @@ def kernel_rooflines(api, ctx, pipe, steps, step_ms, peaks, trace_roof):
         elif kind in ("residual_gemm", "gemm"):
             alg = r["alg_flops"] / r["ms"] / 1e9
             exe = r["flops"] / r["ms"] / 1e9
+            traffic = None
+            if kind == "residual_gemm":
+                # DRAM bytes per output entry and level from the committed capture, times the
+                # entries x levels of a mean launch (executed flops / (2 N_p))
+                np_ = (pipe.N + 127) // 128 * 128
+                traffic = profiled_traffic("exact_gemm_n4096.md", "tc_gemm.cuh",
+                                           r["flops"] / r["launches"] / (2.0 * np_))
             row.update({"kernel": "tc::gemm_exact_kernel (tcgen05, exact integer level products)"
                         if kind == "residual_gemm" else "tc::gemm_kernel (tcgen05: Newton-Schulz steps, corrections)",
                         "bound": "tensor", "achieved": round(alg, 2), "peak": tc, "unit": "TFLOP/s",
-                        "frac": round(alg / tc, 4), "traffic": None,
+                        "frac": round(alg / tc, 4), "traffic": None if traffic is None else round(traffic),
                         "executed_tflops": round(exe, 2), "executed_frac": round(exe / tc, 4),
                         "peak_basis": "bf16_tflops_sustained of MEASURED_PEAKS.json (kernel timed inside a long "
                                       "step); fp16 has the bf16 rate",
