@@ -905,33 +905,22 @@ inline int grid_for(int64_t total, int sm) {
 struct BalancePre {
   const void* W = nullptr;    // 16-bit np x np, row-major (the Newton-Schulz iterate)
   const void* Wt = nullptr;   // its transpose
-  const double* F = nullptr;  // N x (N+1)
   const double* rho = nullptr;
   const double* t = nullptr;  // row sums of the set's B
   bool trans = false;         // the adjoint (transposed) balance
   bool fp16 = true;
   float* y = nullptr;         // [np] scratch vectors, zero beyond n
+  float* yr = nullptr;
   float* z = nullptr;
 };
 
-// (float)x rounded toward zero on the bit pattern of x (no fp64 pipe): magnitudes below 2^-126
-// give zero, above the float range infinity (NaN too, which the caller's finiteness check
-// then reports). The preconditioner's products only need a correction good to a few bits.
-__device__ __forceinline__ float narrow_rz(double x) {
-  const uint32_t hi = (uint32_t)__double2hiint(x), lo = (uint32_t)__double2loint(x);
-  const uint32_t sign = hi & 0x80000000u, t = hi & 0x7fffffffu;
-  if (t < 0x38100000u) return __uint_as_float(sign);                // below 2^-126
-  if (t >= 0x47f00000u) return __uint_as_float(sign | 0x7f800000u);  // 2^128 and up, inf, NaN
-  return __uint_as_float(sign | ((t - 0x38000000u) << 3) | (lo >> 29));
-}
-
-// The first kernel of a preconditioned sweep: y = diag(t) src (the residual column) and, for
-// the forward balance, yr = rho o y, in fp32; also zeroes the sweep's status words and the
-// correction's column maximum.
+// The first kernel of a preconditioned sweep, in fp32: y = diag(t) src (the residual column),
+// z = rho o y and, for the forward balance, yr = (1 - rho) o y; also zeroes the sweep's status
+// words and the correction's column maximum.
 __global__ void pre_first(const double* __restrict__ src, int64_t ld, const double* __restrict__ t,
                           const double* __restrict__ rho, int n, bool trans, float* __restrict__ y,
-                          float* __restrict__ yr, const SweepGuard guard, unsigned long long* red_cur,
-                          unsigned int* dcolmax) {
+                          float* __restrict__ yr, float* __restrict__ z, const SweepGuard guard,
+                          unsigned long long* red_cur, unsigned int* dcolmax) {
   if (guard.err) {
     __shared__ int s_end;
     if (threadIdx.x == 0) {
@@ -946,47 +935,55 @@ __global__ void pre_first(const double* __restrict__ src, int64_t ld, const doub
   if (blockIdx.x == 0 && threadIdx.x == 0) dcolmax[0] = 0u;
   if (i < n) {
     const double v = t[i] * src[(int64_t)i * ld];
+    const double r = rho[i];
     y[i] = (float)v;
-    if (!trans) yr[i] = (float)(rho[i] * v);
+    z[i] = (float)(r * v);
+    if (!trans) yr[i] = (float)((1.0 - r) * v);
   }
 }
 
-// Forward: z_i = y_i - sum_j F_ij yr_j in fp32 (one warp per row, F narrowed on its bits).
-__global__ void pre_k_apply(const double* __restrict__ F, int n, const float* __restrict__ y,
-                            const float* __restrict__ yr, float* __restrict__ z, const int* skip) {
-  if (skip && *(volatile const int*)skip) return;
-  const int i = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
-  const int lane = threadIdx.x & 31;
-  if (i >= n) return;
-  const double* row = F + (int64_t)i * (n + 1);
-  float acc = 0.f, acc2 = 0.f;
-  int j = lane;
-  for (; j + 32 < n; j += 64) {
-    acc = fmaf(narrow_rz(row[j]), yr[j], acc);
-    acc2 = fmaf(narrow_rz(row[j + 32]), yr[j + 32], acc2);
-  }
-  if (j < n) acc = fmaf(narrow_rz(row[j]), yr[j], acc);
-  acc += acc2;
-  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-  if (lane == 0) z[i] = y[i] - acc;
-}
-
-// out_k = sum_i W[k][i] v_i (one warp per row of W, 16-bit W read eight elements at a time,
-// fp32 v and sums: W is a 16-bit approximate inverse, so fp32 sums are far more accurate than
-// needed); with D set, out goes to D[k][0] (fp32) and max_k |out_k| to dcolmax[0]. v is
-// zero beyond n, so the rows' padding (np is a multiple of 128) adds nothing.
+// D_k = (rho ? 1 - rho_k : 1) sum_i W[k][i] v_i + z_k, to D[k][0] (fp32), max_k |D_k| to
+// dcolmax[0]: the balance correction W K y = W ((1 - rho) o y) + rho o y (forward: v = yr, no
+// scale) or its transpose (1 - rho) o (W^T y) + rho o y (adjoint: W^T's rows, v = y, scale
+// 1 - rho), which hold because W (I - F_NN) = I for the exact inverse W of I - F_NN. One warp
+// per row of W, the 16-bit W read eight elements at a time, fp32 sums (W is a 16-bit
+// approximate inverse, so fp32 is far more accurate than needed). v is zero beyond n, so the
+// rows' padding (np is a multiple of 128) adds nothing.
 template <class T16>
 __global__ void pre_w_apply(const void* __restrict__ W, int np, int n, const float* __restrict__ v,
-                            float* __restrict__ out, float* __restrict__ D, int64_t ldd, unsigned int* dcolmax,
-                            int* nonfinite, const int* skip) {
+                            const double* __restrict__ rho, const float* __restrict__ z, float* __restrict__ D,
+                            int64_t ldd, unsigned int* dcolmax, int* nonfinite, const int* skip) {
   if (skip && *(volatile const int*)skip) return;
   const int k = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
   const int lane = threadIdx.x & 31;
   if (k >= n) return;
   const uint4* row = reinterpret_cast<const uint4*>(reinterpret_cast<const T16*>(W) + (int64_t)k * np);
   const float4* v4 = reinterpret_cast<const float4*>(v);
-  float acc = 0.f;
-  for (int g = lane; g < np / 8; g += 32) {
+  float acc = 0.f, acc2 = 0.f;
+  int g = lane;
+  for (; g + 32 < np / 8; g += 64) {
+    const uint4 w = row[g], w2 = row[g + 32];
+    const T16* h = reinterpret_cast<const T16*>(&w);
+    const T16* h2 = reinterpret_cast<const T16*>(&w2);
+    const float4 a = v4[2 * g], b = v4[2 * g + 1], a2 = v4[2 * (g + 32)], b2 = v4[2 * (g + 32) + 1];
+    acc = fmaf((float)h[0], a.x, acc);
+    acc = fmaf((float)h[1], a.y, acc);
+    acc = fmaf((float)h[2], a.z, acc);
+    acc = fmaf((float)h[3], a.w, acc);
+    acc = fmaf((float)h[4], b.x, acc);
+    acc = fmaf((float)h[5], b.y, acc);
+    acc = fmaf((float)h[6], b.z, acc);
+    acc = fmaf((float)h[7], b.w, acc);
+    acc2 = fmaf((float)h2[0], a2.x, acc2);
+    acc2 = fmaf((float)h2[1], a2.y, acc2);
+    acc2 = fmaf((float)h2[2], a2.z, acc2);
+    acc2 = fmaf((float)h2[3], a2.w, acc2);
+    acc2 = fmaf((float)h2[4], b2.x, acc2);
+    acc2 = fmaf((float)h2[5], b2.y, acc2);
+    acc2 = fmaf((float)h2[6], b2.z, acc2);
+    acc2 = fmaf((float)h2[7], b2.w, acc2);
+  }
+  if (g < np / 8) {
     const uint4 w = row[g];
     const T16* h = reinterpret_cast<const T16*>(&w);
     const float4 a = v4[2 * g], b = v4[2 * g + 1];
@@ -999,41 +996,10 @@ __global__ void pre_w_apply(const void* __restrict__ W, int np, int n, const flo
     acc = fmaf((float)h[6], b.z, acc);
     acc = fmaf((float)h[7], b.w, acc);
   }
+  acc += acc2;
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
   if (lane == 0) {
-    if (out) out[k] = acc;
-    if (D) {
-      D[(int64_t)k * ldd] = acc;
-      if (!isfinite(acc)) atomicExch(nonfinite, 1);
-      else atomicMax(dcolmax, __float_as_uint(fabsf(acc)));
-    }
-  }
-}
-
-// Adjoint: D_k = w_k - rho_k sum_i F_ik w_i (K^T w) in fp32, D[k][0] and max |D| into
-// dcolmax[0]. Block (32 x 8) per 32 columns k: thread (x, y) sums rows i = y, y + 8, ...
-// (coalesced in x), F narrowed on its bits.
-__global__ void pre_kt_apply(const double* __restrict__ F, int n, const double* __restrict__ rho,
-                             const float* __restrict__ w, float* __restrict__ D, int64_t ldd, unsigned int* dcolmax,
-                             int* nonfinite, const int* skip) {
-  if (skip && *(volatile const int*)skip) return;
-  __shared__ float part[8][33];
-  const int k = blockIdx.x * 32 + threadIdx.x;
-  float acc = 0.f, acc2 = 0.f;
-  if (k < n) {
-    int i = threadIdx.y;
-    for (; i + 8 < n; i += 16) {
-      acc = fmaf(narrow_rz(F[(int64_t)i * (n + 1) + k]), w[i], acc);
-      acc2 = fmaf(narrow_rz(F[(int64_t)(i + 8) * (n + 1) + k]), w[i + 8], acc2);
-    }
-    if (i < n) acc = fmaf(narrow_rz(F[(int64_t)i * (n + 1) + k]), w[i], acc);
-  }
-  part[threadIdx.y][threadIdx.x] = acc + acc2;
-  __syncthreads();
-  if (threadIdx.y == 0 && k < n) {
-    float sum = part[0][threadIdx.x];
-    for (int yy = 1; yy < 8; ++yy) sum += part[yy][threadIdx.x];
-    const float d = w[k] - (float)rho[k] * sum;
+    const float d = (rho ? (float)(1.0 - rho[k]) : 1.f) * acc + z[k];
     D[(int64_t)k * ldd] = d;
     if (!isfinite(d)) atomicExch(nonfinite, 1);
     else atomicMax(dcolmax, __float_as_uint(fabsf(d)));
@@ -1266,21 +1232,17 @@ struct Solver {
     const int nb = L.np / 256 + (L.np % 256 ? 1 : 0);  // narrow kernels: one thread per row < np
     rg_status st = RG_OK;
     if (pre) {
-      // D = W K diag(t) R (forward) or K^T W^T diag(t) R (adjoint), one column
+      // D = W K diag(t) R (forward) or K^T W^T diag(t) R (adjoint), one column, as
+      // W ((1 - rho) o y) + rho o y or (1 - rho) o (W^T y) + rho o y with y = diag(t) R
       const int rb = (L.n + 255) / 256, wb = (L.n + 7) / 8;
-      pre_first<<<rb, 256, 0, s>>>(src, L.mp, pre->t, pre->rho, L.n, pre->trans, pre->y, pre->z, g, rc, b.dcolmax);
-      ++ctx->launches;
+      pre_first<<<rb, 256, 0, s>>>(src, L.mp, pre->t, pre->rho, L.n, pre->trans, pre->y, pre->yr, pre->z, g, rc,
+                                   b.dcolmax);
       auto wapply = pre->fp16 ? pre_w_apply<__half> : pre_w_apply<__nv_bfloat16>;
-      if (!pre->trans) {
-        // y -> z = K y (in pre->y, reading yr from pre->z), then D = W z
-        pre_k_apply<<<wb, 256, 0, s>>>(pre->F, L.n, pre->y, pre->z, pre->y, skip);
-        wapply<<<wb, 256, 0, s>>>(pre->W, L.np, L.n, pre->y, nullptr, b.Dbuf, L.mp, b.dcolmax, err + 1, skip);
-      } else {
-        // w = W^T y (rows of the transposed copy), then D = K^T w
-        wapply<<<wb, 256, 0, s>>>(pre->Wt, L.np, L.n, pre->y, pre->z, nullptr, 0, nullptr, err + 1, skip);
-        pre_kt_apply<<<(L.n + 31) / 32, dim3(32, 8), 0, s>>>(pre->F, L.n, pre->rho, pre->z, b.Dbuf, L.mp, b.dcolmax,
-                                                              err + 1, skip);
-      }
+      if (!pre->trans)
+        wapply<<<wb, 256, 0, s>>>(pre->W, L.np, L.n, pre->yr, nullptr, pre->z, b.Dbuf, L.mp, b.dcolmax, err + 1, skip);
+      else
+        wapply<<<wb, 256, 0, s>>>(pre->Wt, L.np, L.n, pre->y, pre->rho, pre->z, b.Dbuf, L.mp, b.dcolmax, err + 1,
+                                  skip);
       ctx->launches += 2;
       RG_CUDA_TRY(ctx, cudaGetLastError());
     } else {
@@ -1794,6 +1756,7 @@ size_t balance_sets_extra_bytes(int n) {
   const size_t np = (size_t)(n + NB - 1) / NB * NB;
   rg::Sizer ex;
   ex.take<float>(np);   // y
+  ex.take<float>(np);   // yr
   ex.take<float>(np);   // z
   ex.take<double>(np);  // u = T^4 (adjoint)
   return ex.off;
@@ -2106,18 +2069,18 @@ static rg_status temperatures_sets(rg_ctx* ctx, int32_t n, const double* F_d, in
   rg::Carver cv(extra);
   BalancePre pre;
   pre.y = cv.take<float>(sv.L.np);
+  pre.yr = cv.take<float>(sv.L.np);
   pre.z = cv.take<float>(sv.L.np);
   double* u4 = cv.take<double>(sv.L.np);
   // only entries below n are ever written: the padding stays zero for the row products
   RG_CUDA_TRY(ctx, cudaMemsetAsync(pre.y, 0, sv.L.np * sizeof(float), s));
-  RG_CUDA_TRY(ctx, cudaMemsetAsync(pre.z, 0, sv.L.np * sizeof(float), s));
+  RG_CUDA_TRY(ctx, cudaMemsetAsync(pre.yr, 0, sv.L.np * sizeof(float), s));
   // W ~ (I - F_NN)^-1, shared by every set
   st = sv.set_matrix(F_d, n + 1, false);
   if (st == RG_OK) st = sv.factor(nullptr, nullptr);
   if (st != RG_OK) return st;
   pre.W = sv.b.X16[sv.cur];
   pre.Wt = sv.b.Xt16;
-  pre.F = F_d;
   pre.trans = adjoint;
   pre.fp16 = precision == RG_PREC_FP16_IR;
   sv.pre = &pre;
