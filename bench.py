@@ -279,19 +279,18 @@ def profiled_traffic(summary, source, units):
     'source_sha256: <hash of csrc/<source> when captured>' and 'dram_bytes_per_unit: <x>'.
     None when the summary is missing or the kernel source has changed since the capture."""
     import hashlib
+    import re
     path = os.path.join(ROOT, "profiles", summary)
     src = os.path.join(ROOT, "paper_2511_04277_gb300", "csrc", source)
     if not os.path.exists(path):
         return None
-    fields = {}
-    for line in open(path):
-        if ":" in line:
-            k, v = line.split(":", 1)
-            fields[k.strip().lstrip("-* ").strip("`")] = v.strip().strip("`")
+    text = open(path).read()
+    m_sha = re.search(r"source_sha256:\s*`?([0-9a-f]{64})", text)
+    m_per = re.search(r"dram_bytes_per_unit:\s*([0-9.eE+-]+)", text)
     sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
-    if fields.get("source_sha256") != sha or "dram_bytes_per_unit" not in fields:
+    if not m_sha or not m_per or m_sha.group(1) != sha:
         return None
-    return float(fields["dram_bytes_per_unit"]) * units
+    return float(m_per.group(1)) * units
 
 
 def lu_equivalent_flops(N, S, sweeps_refs, with_thermal=True):
@@ -417,13 +416,15 @@ def kernel_rooflines(api, ctx, pipe, steps, step_ms, peaks, trace_roof):
         elif kind in ("residual_gemm", "gemm"):
             alg = r["alg_flops"] / r["ms"] / 1e9
             exe = r["flops"] / r["ms"] / 1e9
-            traffic = None
             if kind == "residual_gemm":
-                # DRAM bytes per output entry and level from the committed capture, times the
-                # entries x levels of a mean launch (executed flops / (2 N_p))
+                # DRAM bytes per output entry and level from the committed full-size capture,
+                # times the entries x levels of a mean launch (executed flops / (2 N_p))
                 np_ = (pipe.N + 127) // 128 * 128
                 traffic = profiled_traffic("exact_gemm_n4096.md", "tc_gemm.cuh",
                                            r["flops"] / r["launches"] / (2.0 * np_))
+            else:
+                # DRAM bytes per executed flop from the committed full-size capture
+                traffic = profiled_traffic("gemm_pair_n4096.md", "tc_gemm.cuh", r["flops"] / r["launches"])
             row.update({"kernel": "tc::gemm_exact_kernel (tcgen05, exact integer level products)"
                         if kind == "residual_gemm" else "tc::gemm_kernel (tcgen05: Newton-Schulz steps, corrections)",
                         "bound": "tensor", "achieved": round(alg, 2), "peak": tc, "unit": "TFLOP/s",
