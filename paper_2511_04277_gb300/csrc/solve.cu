@@ -1185,17 +1185,18 @@ struct Solver {
     memcpy(&e_inf, hs + kStatus + 6, sizeof(e_inf));
     memcpy(&e_one, hs + kStatus + 8, sizeof(e_one));
     if (!std::isfinite(e_inf) || !std::isfinite(e_one)) return rg::fail(ctx, RG_ERR_NUMERIC, "non-finite system matrix");
-    // The residual of the Newton-Schulz iterate X_k is I - A X_k = E^(2^(k-1)), so any
-    // norm of E with ||E|| < 1 bounds it. ||E||_inf (row sums) suits the Gebhart matrix
+    // build_ns_start writes X_1 = I + E (E = Dl P Dr), whose residual is I - A X_1 = E^2, and
+    // each step X <- X (2I - A X) squares the residual: X_k has residual E^(2^k), bounded by
+    // ||E||^(2^k) in any norm with ||E|| < 1. ||E||_inf (row sums) suits the Gebhart matrix
     // K = I - F diag(rho); its transpose, solved by the adjoint, has ||E||_1 < 1 instead
     // while its row sums (the column sums of F) can exceed 1: the smaller bound sets the
-    // step count.
+    // step count, the least k with ||E||^(2^k) <= the 16-bit floor.
     const double e0v = std::min(e_inf, e_one);
     const double floor16 = bf16 ? 0x1p-10 : 0x1p-13;
     int steps = kMaxNewtonSchulz;
     if (e0v < 1.0) {
       steps = 1;
-      if (e0v > 0.0) steps = (int)std::ceil(std::log2(std::log(floor16) / std::log(e0v))) + 1;
+      if (e0v > 0.0) steps = (int)std::ceil(std::log2(std::log(floor16) / std::log(e0v)));
       steps = std::max(1, std::min(steps, kMaxNewtonSchulz));
     }
     ns_steps = steps;
