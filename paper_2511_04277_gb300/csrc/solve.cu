@@ -201,78 +201,180 @@ __global__ void build_p_exact(const double* __restrict__ P, int64_t ldp, const d
   if (lane == 0) rowexp[i] = e;
 }
 
-// build_p_exact for P read transposed (P'_ik = P_ki Dr_k): block (32 x 8) per 32 rows i of P',
-// so that every read of P is a coalesced segment of one of its rows. Pass 1: the row maxima
-// (eight loads in flight per thread, shared-memory reduction). Pass 2: per 64 columns k, the
-// digits go through shared memory and are written along k (64-byte rows per slice).
-__global__ void __launch_bounds__(256) build_p_exact_t(const double* __restrict__ P, int64_t ldp,
-                                                       const double* __restrict__ dr, int n, int np,
-                                                       __nv_bfloat16* __restrict__ Aex, int* __restrict__ rowexp,
-                                                       int* err) {
-  __shared__ unsigned long long s_mx[8][32];
-  __shared__ int s_bad;
-  __shared__ __align__(16) uint16_t tile[kLevels][32][66];  // [a][row of P'][column k]
-  const int x = threadIdx.x, y = threadIdx.y;
-  const int i0 = blockIdx.x * 32, i = i0 + x;
-  if (x == 0 && y == 0) s_bad = 0;
+// build_p_exact with the row in shared memory (n <= kRowSmem): one block of 512 threads per
+// row of P', which is read from HBM once (the warp-per-row form reads it twice, the second
+// time from HBM again when thousands of rows are in flight).
+constexpr int kRowSmem = 12288;
+__global__ void __launch_bounds__(512) build_p_exact_row(const double* __restrict__ P, int64_t ldp,
+                                                         const double* __restrict__ dr, int n, int np,
+                                                         __nv_bfloat16* __restrict__ Aex, int* __restrict__ rowexp,
+                                                         int* err) {
+  extern __shared__ double xs[];  // [n]: the row of P'
+  __shared__ unsigned long long s_mx[16];
+  const int i = blockIdx.x, t = threadIdx.x;
+  uint32_t* row = reinterpret_cast<uint32_t*>(Aex + (int64_t)i * kLevels * np);  // bf16 pairs
+  const int half = np / 2;
+  if (i >= n) {  // uniform over the block
+    for (int k2 = t; k2 < half; k2 += 512)
+#pragma unroll
+      for (int a = 0; a < kLevels; ++a) row[(int64_t)a * half + k2] = 0u;
+    if (t == 0) rowexp[i] = 0;
+    return;
+  }
+  const double* prow = P + (int64_t)i * ldp;
   unsigned long long mx = 0ull;
   bool bad = false;
-  if (i < n) {
-    for (int k0 = y; k0 < n; k0 += 64) {
-      double v[8];
+  for (int k0 = t; k0 < n; k0 += 4 * 512) {
+    double v[4];
 #pragma unroll
-      for (int r = 0; r < 8; ++r) {
-        const int k = k0 + 8 * r;
-        v[r] = k < n ? P[(int64_t)k * ldp + i] : 0.0;
-      }
+    for (int u = 0; u < 4; ++u) {
+      const int k = k0 + 512 * u;
+      v[u] = k < n ? (dr ? prow[k] * dr[k] : prow[k]) : 0.0;
+    }
 #pragma unroll
-      for (int r = 0; r < 8; ++r) {
-        const int k = k0 + 8 * r;
-        const double xv = (dr && k < n) ? v[r] * dr[k] : v[r];
-        const unsigned long long bx = (unsigned long long)__double_as_longlong(xv) & 0x7fffffffffffffffull;
+    for (int u = 0; u < 4; ++u) {
+      const int k = k0 + 512 * u;
+      if (k < n) {
+        xs[k] = v[u];
+        const unsigned long long bx = (unsigned long long)__double_as_longlong(v[u]) & 0x7fffffffffffffffull;
         bad |= bx >= 0x7ff0000000000000ull;
         mx = max(mx, bx);
       }
     }
   }
-  s_mx[y][x] = mx;
-  if (__syncthreads_or(bad) && x == 0 && y == 0) {
-    s_bad = 1;
-    atomicExch(err, 1);
+  for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((t & 31) == 0) s_mx[t >> 5] = mx;
+  if (__syncthreads_or(bad)) {
+    if (t == 0) atomicExch(err, 1);
+    for (int w = 0; w < 16; ++w) s_mx[w] = 0ull;  // every thread writes the same: no race on the value
   }
   __syncthreads();
-  unsigned long long m = s_mx[0][x];
+  unsigned long long m = s_mx[0];
 #pragma unroll
-  for (int yy = 1; yy < 8; ++yy) m = max(m, s_mx[yy][x]);
-  if (s_bad) m = 0ull;  // the slices are not used once the error is raised
+  for (int w = 1; w < 16; ++w) m = max(m, s_mx[w]);
   const int e = m ? frexp_exponent_bits(m) : 0;
-  if (y == 0 && i < np) rowexp[i] = e;
-  for (int k0 = 0; k0 < np; k0 += 64) {
+  for (int k2 = t; k2 < half; k2 += 512) {
+    const int k = 2 * k2;
+    uint32_t d0[kLevels], d1[kLevels];
+    split_digits(k < n ? xs[k] : 0.0, 39 - e, k < n && m, d0);
+    split_digits(k + 1 < n ? xs[k + 1] : 0.0, 39 - e, k + 1 < n && m, d1);
 #pragma unroll
-    for (int r = 0; r < 8; ++r) {
-      const int kl = y + 8 * r, k = k0 + kl;
-      const bool in = i < n && k < n;
-      double xv = in ? P[(int64_t)k * ldp + i] : 0.0;
-      if (dr && in) xv *= dr[k];
-      uint32_t d[kLevels];
-      split_digits(xv, 39 - e, in && m, d);
+    for (int a = 0; a < kLevels; ++a) row[(int64_t)a * half + k2] = d0[a] | (d1[a] << 16);
+  }
+  if (t == 0) rowexp[i] = e;
+}
+
+// Row maxima of P' for P read transposed (P'_ik = P_ki Dr_k), from P's rows (coalesced): block
+// (32 x 8) per 32 columns i of P and 256 of its rows k, the bit patterns of |P'_ik| folded into
+// colmax[i] by atomicMax (zeroed by the caller); a non-finite entry raises *err.
+__global__ void __launch_bounds__(256) p_colmax_t(const double* __restrict__ P, int64_t ldp,
+                                                  const double* __restrict__ dr, int n,
+                                                  unsigned long long* __restrict__ colmax, int* err) {
+  __shared__ unsigned long long s_mx[8][32];
+  const int x = threadIdx.x, y = threadIdx.y;
+  const int i = blockIdx.x * 32 + x;
+  const int k0 = blockIdx.y * 256;
+  unsigned long long mx = 0ull;
+  bool bad = false;
+  if (i < n) {
 #pragma unroll
-      for (int a = 0; a < kLevels; ++a) tile[a][x][kl] = (uint16_t)d[a];
-    }
-    __syncthreads();
-    // warp y writes rows i0 + y + 8 c, lane x the columns k0 + 2 x, k0 + 2 x + 1
+    for (int j0 = 0; j0 < 32; j0 += 8) {
+      double v[8];
 #pragma unroll
-    for (int c = 0; c < 4; ++c) {
-      const int il = y + 8 * c, ii = i0 + il;
-      if (ii < np) {
-        uint32_t* row = reinterpret_cast<uint32_t*>(Aex + (int64_t)ii * kLevels * np + k0);
+      for (int r = 0; r < 8; ++r) {
+        const int k = k0 + y + 8 * (j0 + r);
+        v[r] = k < n ? P[(int64_t)k * ldp + i] : 0.0;
+      }
 #pragma unroll
-        for (int a = 0; a < kLevels; ++a)
-          row[(int64_t)a * (np / 2) + x] = *reinterpret_cast<const uint32_t*>(&tile[a][il][2 * x]);
+      for (int r = 0; r < 8; ++r) {
+        const int k = k0 + y + 8 * (j0 + r);
+        const double xv = (dr && k < n) ? v[r] * dr[k] : v[r];
+        const unsigned long long bx = (unsigned long long)__double_as_longlong(xv) & 0x7fffffffffffffffull;
+        const bool fin = bx < 0x7ff0000000000000ull;
+        bad |= !fin;
+        mx = max(mx, fin ? bx : 0ull);
       }
     }
-    __syncthreads();
   }
+  s_mx[y][x] = mx;
+  if (__syncthreads_or(bad) && x == 0 && y == 0) atomicExch(err, 1);
+  if (y == 0 && i < n) {
+    unsigned long long m = s_mx[0][x];
+#pragma unroll
+    for (int yy = 1; yy < 8; ++yy) m = max(m, s_mx[yy][x]);
+    if (m) atomicMax(&colmax[i], m);
+  }
+}
+
+// The transposed split's digits: block (32 x 8) per 32 rows i of P' and 64 columns k, the
+// exponents from p_colmax_t's maxima; reads of P along its rows (coalesced), the digits
+// through shared memory and written along k (64-byte rows per slice).
+__global__ void __launch_bounds__(256) build_p_exact_t(const double* __restrict__ P, int64_t ldp,
+                                                       const double* __restrict__ dr, int n, int np,
+                                                       const unsigned long long* __restrict__ colmax,
+                                                       __nv_bfloat16* __restrict__ Aex, int* __restrict__ rowexp) {
+  __shared__ __align__(16) uint16_t tile[kLevels][32][66];  // [a][row of P'][column k]
+  const int x = threadIdx.x, y = threadIdx.y;
+  const int i0 = blockIdx.x * 32, i = i0 + x;
+  const int k0 = blockIdx.y * 64;
+  const unsigned long long m = i < n ? colmax[i] : 0ull;
+  const int e = m ? frexp_exponent_bits(m) : 0;
+  if (blockIdx.y == 0 && y == 0 && i < np) rowexp[i] = e;
+  double v[8];
+#pragma unroll
+  for (int r = 0; r < 8; ++r) {
+    const int k = k0 + y + 8 * r;
+    v[r] = (i < n && k < n) ? P[(int64_t)k * ldp + i] : 0.0;
+  }
+#pragma unroll
+  for (int r = 0; r < 8; ++r) {
+    const int kl = y + 8 * r, k = k0 + kl;
+    const bool in = i < n && k < n;
+    const double xv = (dr && in) ? v[r] * dr[k] : v[r];
+    uint32_t d[kLevels];
+    split_digits(xv, 39 - e, in && m, d);
+#pragma unroll
+    for (int a = 0; a < kLevels; ++a) tile[a][x][kl] = (uint16_t)d[a];
+  }
+  __syncthreads();
+  // warp y writes rows i0 + y + 8 c, lane x the columns k0 + 2 x, k0 + 2 x + 1
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    const int il = y + 8 * c, ii = i0 + il;
+    if (ii < np) {
+      uint32_t* row = reinterpret_cast<uint32_t*>(Aex + (int64_t)ii * kLevels * np + k0);
+#pragma unroll
+      for (int a = 0; a < kLevels; ++a)
+        row[(int64_t)a * (np / 2) + x] = *reinterpret_cast<const uint32_t*>(&tile[a][il][2 * x]);
+    }
+  }
+}
+
+// The fixed-point split of P' = P Dr (P^T Dr with trans) into Aex / rowexp (build_p_exact's
+// definition): the transposed form as a column-maximum pass and a tiled digit pass (colmax:
+// np words of scratch), the row form with the row in shared memory up to kRowSmem columns.
+rg_status launch_build_p(rg_ctx* ctx, const double* P, int64_t ldp, bool trans, const double* dr, int n, int np,
+                         __nv_bfloat16* Aex, int* rowexp, int* err, unsigned long long* colmax, cudaStream_t s) {
+  if (trans) {
+    RG_CUDA_TRY(ctx, cudaMemsetAsync(colmax, 0, (size_t)np * sizeof(unsigned long long), s));
+    p_colmax_t<<<dim3((n + 31) / 32, (n + 255) / 256), dim3(32, 8), 0, s>>>(P, ldp, dr, n, colmax, err);
+    build_p_exact_t<<<dim3(np / 32, np / 64), dim3(32, 8), 0, s>>>(P, ldp, dr, n, np, colmax, Aex, rowexp);
+    ctx->launches += 2;
+  } else if (n <= kRowSmem) {
+    static thread_local int configured_device = -1;
+    if (configured_device != ctx->device) {
+      RG_CUDA_TRY(ctx, cudaFuncSetAttribute(build_p_exact_row, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)(kRowSmem * sizeof(double))));
+      configured_device = ctx->device;
+    }
+    build_p_exact_row<<<np, 512, (size_t)n * sizeof(double), s>>>(P, ldp, dr, n, np, Aex, rowexp, err);
+    ++ctx->launches;
+  } else {
+    build_p_exact<<<(np + 7) / 8, 256, 0, s>>>(P, ldp, dr, n, np, Aex, rowexp, err);
+    ++ctx->launches;
+  }
+  RG_CUDA_TRY(ctx, cudaGetLastError());
+  return RG_OK;
 }
 
 // Rounds each column j < m of the correction D (fp32, ld = mp) to one 8-bit fixed-point slice:
@@ -1151,13 +1253,9 @@ struct Solver {
 
   // Fixed-point slices of P' = P Dr (Dr may be null).
   rg_status build_slices(const double* dr) {
-    if (transP)
-      build_p_exact_t<<<L.np / 32, dim3(32, 8), 0, s>>>(P, ldp, dr, L.n, L.np, b.Aex, b.rowexp, err);
-    else
-      build_p_exact<<<(L.np + 7) / 8, 256, 0, s>>>(P, ldp, dr, L.n, L.np, b.Aex, b.rowexp, err);
-    ++ctx->launches;
-    RG_CUDA_TRY(ctx, cudaGetLastError());
-    return RG_OK;
+    // nsum (the Newton-Schulz start's sums, read before this) serves as the column maxima
+    return launch_build_p(ctx, P, ldp, transP, dr, L.n, L.np, b.Aex, b.rowexp, err,
+                          reinterpret_cast<unsigned long long*>(b.nsum), s);
   }
 
   // Newton-Schulz approximate inverse of A = I - Dl P Dr into b.X16[cur].
@@ -1833,20 +1931,18 @@ rg_status rg_exact_split(rg_ctx* ctx, int32_t n, const double* P_d, int64_t ldp,
   rg::Sizer sz;
   sz.take<__nv_bfloat16>((size_t)np * kLevels * np);
   sz.take<int>(np);
+  sz.take<unsigned long long>(np);
   void* ws = nullptr;
   rg_status st = rg::workspace(ctx, sz.off, &ws);
   if (st != RG_OK) return st;
   rg::Carver cv(ws);
   __nv_bfloat16* Aex = cv.take<__nv_bfloat16>((size_t)np * kLevels * np);
   int* rowexp = cv.take<int>(np);
+  unsigned long long* colmax = cv.take<unsigned long long>(np);
   int* e = ctx->d_scratch + kStatus;
   RG_CUDA_TRY(ctx, cudaMemsetAsync(e, 0, sizeof(int), s));
-  if (trans)
-    build_p_exact_t<<<np / 32, dim3(32, 8), 0, s>>>(P_d, ldp, dr_d, n, np, Aex, rowexp, e);
-  else
-    build_p_exact<<<(np + 7) / 8, 256, 0, s>>>(P_d, ldp, dr_d, n, np, Aex, rowexp, e);
-  ++ctx->launches;
-  RG_CUDA_TRY(ctx, cudaGetLastError());
+  st = launch_build_p(ctx, P_d, ldp, trans != 0, dr_d, n, np, Aex, rowexp, e, colmax, s);
+  if (st != RG_OK) return st;
   bf16_rows_to_int16<<<grid_for((int64_t)n * kLevels * np, ctx->sm_count), kThreads, 0, s>>>(
       Aex, (int64_t)n * kLevels * np, slices_d);
   ++ctx->launches;

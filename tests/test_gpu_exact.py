@@ -61,6 +61,23 @@ def test_exact_split_matches_its_definition(rg_ctx, n, trans, with_dr):
     del np_
 
 
+@pytest.mark.parametrize("trans", [False, True])
+def test_exact_split_beyond_the_shared_memory_row(rg_ctx, trans):
+    """n = 12,300: rows longer than the shared-memory form holds take the two-pass warp form
+    (and the transposed form its tiled passes); sampled rows against the definition."""
+    n = 12300
+    rng = np.random.default_rng(11 + trans)
+    P = (rng.uniform(-1, 1, (n, n)) * np.ldexp(1.0, rng.integers(-30, 1, (n, n)))).astype(np.float64)
+    dr = rng.uniform(0.05, 0.95, n)
+    P_d = torch.as_tensor(P.T.copy() if trans else P, device="cuda")
+    sl, ex = api.exact_split(rg_ctx, P_d, torch.as_tensor(dr, device="cuda"), trans=trans)
+    rows = np.array([0, 1, 4095, 6150, 12299])
+    d_ref, e_ref = split_reference(P[rows], dr)
+    assert np.array_equal(ex.cpu().numpy()[rows], e_ref)
+    assert np.array_equal(sl[rows].cpu().numpy().astype(np.int64)[:, :, :n], d_ref)
+    del P_d, sl
+
+
 def _ints(rng, shape, extreme=False, top=128, col_signs=None):
     """Random integers in [-top, top]; extreme: +-top; col_signs: +-top with the sign of
     column k from col_signs[k] times a random sign per row (products of two such operands
