@@ -245,7 +245,8 @@ class Pipeline:
 
     def refs(self):
         _, self.sweeps, self.resid = self.api.gebhart(self.ctx, self.F_it, self.eps, self.rho, SOLVE_PRECISION,
-                                                      tol=SOLVE_TOL, B=self.B, factors=self.factors)
+                                                      tol=SOLVE_TOL, B=self.B, factors=self.factors,
+                                                      areas=self.areas)
 
     def thermal(self):
         """Steady temperatures of every set and their adjoint (dL/dB, direct dL/deps of

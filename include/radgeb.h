@@ -99,7 +99,8 @@ rg_status rg_solver_workspace(int32_t kind, int32_t n, int32_t rank, size_t* byt
  * keep_factors = 0: the workspace of one rg_gebhart call, as
  * rg_solver_workspace(RG_WS_GEBHART, n, 0, ...). keep_factors != 0: the size of the factor
  * store (factors_d) that rg_gebhart fills and rg_gebhart_adjoint / rg_gebhart_adjoint_factored
- * read: a 256-byte header and one 16-bit np x np inverse per set (np = n rounded up to 128),
+ * read: a 256-byte header, one 16-bit np x np inverse per set (np = n rounded up to 128) and
+ * one fp64 scale vector of np per set (the symmetric form's D, zeros for a general inverse),
  * about 2 n^2 n_sets bytes. Errors: RG_ERR_ARG. */
 rg_status rg_gebhart_workspace(int32_t n, int32_t n_sets, int32_t precision, int32_t keep_factors, size_t* bytes_out);
 
@@ -424,6 +425,14 @@ rg_status rg_node_couplings(rg_ctx* ctx, int32_t n, const double* B2_d, const do
  * for n_sets independent (eps, rho) sets sharing F.
  *   F_d      device fp64 [n][n+1]
  *   eps_d    device fp64 [n_sets][n];  rho_d device fp64 [n_sets][n], 0 <= rho < 1
+ *   area_d   device fp64 [n] face areas, or NULL. Given, and with F reciprocal (A_i F_ij =
+ *            A_j F_ji, as the enforcers leave it), the 16-bit inverse is built in the
+ *            symmetric form of K, D K D^-1 with D = diag(sqrt(A rho)), whose Newton-Schulz
+ *            steps compute the second of their two products, X (2I - A X) (symmetric), on
+ *            the tiles on and above the diagonal only; a set with a non-positive A_i rho_i, or one
+ *            below 2^-20 of the largest, takes the general factorisation. The refinement's
+ *            residual is exact for the F given either way: areas of a non-reciprocal F only
+ *            make the inverse a poorer preconditioner (more sweeps).
  *   B_d      device fp64 [n_sets][n][n+1] (output)
  *   tol      refinement stops when max_ij |R_ij| <= tol * max_ij |B_ij| for the
  *            residual R = E - K B of every set (tol >= 1e-13). The residual is tracked
@@ -450,7 +459,7 @@ rg_status rg_node_couplings(rg_ctx* ctx, int32_t n, const double* B2_d, const do
  * Limit: n <= 32768. Errors: RG_ERR_ARG (also a factor store that is short or misaligned),
  * RG_ERR_NOT_CONVERGED, RG_ERR_NUMERIC, RG_ERR_OOM. */
 rg_status rg_gebhart(rg_ctx* ctx, int32_t n, const double* F_d, int32_t n_sets, const double* eps_d,
-                     const double* rho_d, int32_t precision, double tol, int32_t max_sweeps,
+                     const double* rho_d, const double* area_d, int32_t precision, double tol, int32_t max_sweeps,
                      double* B_d, int32_t* sweeps_out_h, double* resid_out_h, void* factors_d,
                      size_t factors_bytes, void* workspace_d, size_t workspace_bytes, void* stream);
 

@@ -64,7 +64,7 @@ SIGNATURES = {
     "rg_aggregate": (i32, [P, i32, P, P, P, i32, P, P, P]),
     "rg_node_view_factors": (i32, [P, i32, P, P, P, P, P]),
     "rg_node_couplings": (i32, [P, i32, P, P, P, P, P, P, P, P]),
-    "rg_gebhart": (i32, [P, i32, P, i32, P, P, i32, f64, i32, P, P, P, P, sz, P, sz, P]),
+    "rg_gebhart": (i32, [P, i32, P, i32, P, P, P, i32, f64, i32, P, P, P, P, sz, P, sz, P]),
     "rg_gebhart_adjoint": (i32, [P, i32, P, i32, P, P, P, P, i32, f64, i32, P, P, P, sz, P, sz, P]),
     "rg_temperatures": (i32, [P, i32, P, P, P, P, f64, f64, i32, f64, P, P, sz, P]),
     "rg_temperatures_adjoint": (i32, [P, i32, P, P, P, f64, f64, P, P, i32, f64, P, P, P, sz, P]),

@@ -412,9 +412,10 @@ def _prec(p):
 
 def gebhart(ctx: Context, F: torch.Tensor, eps: torch.Tensor, rho: torch.Tensor, precision="bf16",
             tol: float = 1e-12, max_sweeps: int = 12, B: torch.Tensor | None = None, stream=None, ws=None,
-            factors=None):
+            factors=None, areas=None):
     """REFs of every (eps, rho) set (rg_gebhart) -> (B [S, N, N+1], sweeps, relative residual).
-    factors: a store from gebhart_factor_store, filled for the adjoints (or None)."""
+    factors: a store from gebhart_factor_store, filled for the adjoints (or None); areas: the
+    face areas of a reciprocal F (the symmetric factorisation), or None."""
     n = F.shape[0]
     eps2 = eps.reshape(-1, n)
     S = eps2.shape[0]
@@ -424,7 +425,10 @@ def gebhart(ctx: Context, F: torch.Tensor, eps: torch.Tensor, rho: torch.Tensor,
     res = ctypes.c_double(0.0)
     ctx.check(ctx.lib.rg_gebhart(ctx.handle, n, _dptr(F, torch.float64, "F", n * (n + 1), ctx.device), S,
                                  _dptr(eps2, torch.float64, "eps", S * n, ctx.device),
-                                 _dptr(rho, torch.float64, "rho", S * n, ctx.device), _prec(precision), float(tol),
+                                 _dptr(rho, torch.float64, "rho", S * n, ctx.device),
+                                 ctypes.c_void_p(None) if areas is None else _dptr(areas, torch.float64, "areas", n,
+                                                                                   ctx.device),
+                                 _prec(precision), float(tol),
                                  int(max_sweeps), _dptr(B, torch.float64, "B", S * n * (n + 1), ctx.device),
                                  ctypes.byref(sw), ctypes.byref(res), *_ws(factors, ctx.device),
                                  *_ws(ws, ctx.device), _stream(stream)), "rg_gebhart")

@@ -67,7 +67,7 @@ int tile_width(const rg_ctx* ctx, int M, int N) {
 
 template <class Epi>
 rg_status gemm(rg_ctx* ctx, bool bf16, const void* A, int64_t lda, const void* B, int64_t ldb, int M, int N, int K,
-               const Epi& epi, cudaStream_t s, const int* skip) {
+               const Epi& epi, cudaStream_t s, const int* skip, bool sym) {
   if (M <= 0 || N <= 0) return RG_OK;
   if (K <= 0) return rg::fail(ctx, RG_ERR_ARG, "gemm: K = %d", K);
   const int bn = tile_width(ctx, M, N);
@@ -78,6 +78,8 @@ rg_status gemm(rg_ctx* ctx, bool bf16, const void* A, int64_t lda, const void* B
   if (st != RG_OK) return st;
   GemmArgs args{M, N, K, ctx->d_scratch + kGemmErrorSlot};
   args.skip = skip;
+  // a symmetric product computes the upper tiles only where the tiles are square
+  args.sym = (sym && M == N && (bn == 256 || bn == 128)) ? 1 : 0;
   if (bn == 256)
     return bf16 ? launch_pair<Epi, true>(ctx, ma, mb, args, epi, s) : launch_pair<Epi, false>(ctx, ma, mb, args, epi, s);
   if (bn == 64)
@@ -87,15 +89,15 @@ rg_status gemm(rg_ctx* ctx, bool bf16, const void* A, int64_t lda, const void* B
 }
 
 template rg_status gemm<EpiTwoIMinusT<__nv_bfloat16>>(rg_ctx*, bool, const void*, int64_t, const void*, int64_t, int,
-                                                      int, int, const EpiTwoIMinusT<__nv_bfloat16>&, cudaStream_t, const int*);
+                                                      int, int, const EpiTwoIMinusT<__nv_bfloat16>&, cudaStream_t, const int*, bool);
 template rg_status gemm<EpiTwoIMinusT<__half>>(rg_ctx*, bool, const void*, int64_t, const void*, int64_t, int, int,
-                                               int, const EpiTwoIMinusT<__half>&, cudaStream_t, const int*);
+                                               int, const EpiTwoIMinusT<__half>&, cudaStream_t, const int*, bool);
 template rg_status gemm<EpiStore16Both<__nv_bfloat16>>(rg_ctx*, bool, const void*, int64_t, const void*, int64_t, int,
-                                                       int, int, const EpiStore16Both<__nv_bfloat16>&, cudaStream_t, const int*);
+                                                       int, int, const EpiStore16Both<__nv_bfloat16>&, cudaStream_t, const int*, bool);
 template rg_status gemm<EpiStore16Both<__half>>(rg_ctx*, bool, const void*, int64_t, const void*, int64_t, int, int,
-                                                int, const EpiStore16Both<__half>&, cudaStream_t, const int*);
+                                                int, const EpiStore16Both<__half>&, cudaStream_t, const int*, bool);
 template rg_status gemm<EpiCorrection>(rg_ctx*, bool, const void*, int64_t, const void*, int64_t, int, int, int,
-                                       const EpiCorrection&, cudaStream_t, const int*);
+                                       const EpiCorrection&, cudaStream_t, const int*, bool);
 
 namespace {
 
@@ -109,8 +111,10 @@ rg_status launch(rg_ctx* ctx, const CUtensorMap& ma, const CUtensorMap& mb, cons
     RG_CUDA_TRY(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     configured_device = ctx->device;
   }
-  dim3 grid(((args.N + BN - 1) / BN) * ((args.M + BM - 1) / BM));
-  const double executed = 2.0 * args.M * (double)args.N * args.K;
+  const int64_t tiles_m = (args.M + BM - 1) / BM;
+  const int64_t tiles = args.sym ? tiles_m * (tiles_m + 1) / 2 : ((args.N + BN - 1) / BN) * tiles_m;
+  dim3 grid((unsigned)tiles);
+  const double executed = args.sym ? 2.0 * (double)tiles * BM * BN * args.K : 2.0 * args.M * (double)args.N * args.K;
   const int tok = rg::timer_begin(ctx, rg::kTimeGemm, s, executed,
                                   args.alg_k > 0 ? 2.0 * args.M * (double)args.N * args.alg_k : executed);
   kern<<<grid, kThreads, smem, s>>>(ma, mb, args, epi);
@@ -131,8 +135,11 @@ rg_status launch_pair(rg_ctx* ctx, const CUtensorMap& ma, const CUtensorMap& mb,
     configured_device = ctx->device;
   }
   // two CTAs (one cluster) per 256 x 256 tile
-  dim3 grid(2 * ((args.N + 255) / 256) * ((args.M + 2 * BM - 1) / (2 * BM)));
-  const double executed = 2.0 * args.M * (double)args.N * args.K;
+  const int64_t tiles_m = (args.M + 2 * BM - 1) / (2 * BM);
+  const int64_t tiles = args.sym ? tiles_m * (tiles_m + 1) / 2 : ((args.N + 255) / 256) * tiles_m;
+  dim3 grid((unsigned)(2 * tiles));
+  const double executed =
+      args.sym ? 2.0 * (double)tiles * 256 * 256 * args.K : 2.0 * args.M * (double)args.N * args.K;
   const int tok = rg::timer_begin(ctx, rg::kTimeGemm, s, executed,
                                   args.alg_k > 0 ? 2.0 * args.M * (double)args.N * args.alg_k : executed);
   kern<<<grid, kThreads, smem, s>>>(ma, mb, args, epi);

@@ -761,14 +761,15 @@ __global__ void bf16_rows_to_int16(const __nv_bfloat16* __restrict__ in, int64_t
 // A16 = I - Dl P Dr (16-bit, identity padding), the first Newton-Schulz iterate
 // X16 = 2I - A = I + Dl P Dr (the step from X = I, done here instead of by two GEMMs) and its
 // transpose Xt16, with the row and column sums of |Dl P Dr| (in fp32) added into rowsum /
-// colsum (zeroed by the caller). One block (32 x 8) per 32 x 32 tile: P's tile is read coalesced in its own
+// colsum (zeroed by the caller); with gen, those of |P diag(gdr)| instead (gdr null: 1), the
+// unscaled matrix whose residual the refinement sees when Dl P Dr is its symmetric form. One block (32 x 8) per 32 x 32 tile: P's tile is read coalesced in its own
 // layout (directly or transposed) through shared memory, and Xt16's tile is written from a
 // transposed copy.
 template <class T16>
 __global__ void build_ns_start(const double* __restrict__ P, int64_t ldp, bool trans, const double* __restrict__ dl,
                                const double* __restrict__ dr, int n, int np, T16* __restrict__ A16,
                                T16* __restrict__ X16, T16* __restrict__ Xt16, double* __restrict__ rowsum,
-                               double* __restrict__ colsum) {
+                               double* __restrict__ colsum, bool gen, const double* __restrict__ gdr) {
   __shared__ double raw[32][33];
   __shared__ float xs[32][33];
   __shared__ float cpart[8][33];
@@ -784,6 +785,7 @@ __global__ void build_ns_start(const double* __restrict__ P, int64_t ldp, bool t
   // (GB300's fp64 pipe, conversions included, is far slower than its fp32 one)
   const int k = k0 + tx;
   const float rk = (k < n && dr) ? (float)dr[k] : 1.f;
+  const float gk = (k < n && gdr) ? (float)gdr[k] : 1.f;
   float cs = 0.f;
   for (int a = ty; a < 32; a += 8) {
     const int i = i0 + a;
@@ -795,7 +797,7 @@ __global__ void build_ns_start(const double* __restrict__ P, int64_t ldp, bool t
     A16[o] = to16<T16>(one - e);
     X16[o] = to16<T16>(one + e);
     xs[a][tx] = one + e;
-    const float ae = fabsf(e);
+    const float ae = gen ? ((i < n && k < n) ? fabsf(p * gk) : 0.f) : fabsf(e);
     cs += ae;
     float rs = ae;
     for (int q = 16; q > 0; q >>= 1) rs += __shfl_xor_sync(0xffffffffu, rs, q);
@@ -913,7 +915,8 @@ template <class T16>
 __global__ void scaled_transpose16(const double* __restrict__ R, int64_t ld, int n, int m, int np, int mp,
                                    const unsigned long long* __restrict__ colmax, T16* __restrict__ Rt,
                                    float* __restrict__ colscale, const SweepGuard guard,
-                                   unsigned long long* red_cur, unsigned int* dcolmax) {
+                                   unsigned long long* red_cur, unsigned int* dcolmax,
+                                   const float* __restrict__ rs) {
   __shared__ __align__(16) float tile[32][66];  // [column][row]: a row pair is one 8-byte read
   if (guard.err) {  // one thread per block evaluates the rule (an fp64 division), the block follows
     __shared__ int s_end;
@@ -944,7 +947,10 @@ __global__ void scaled_transpose16(const double* __restrict__ R, int64_t ld, int
     x[r] = (i < n && j < m) ? R[(int64_t)i * ld + j] : 0.0;
   }
 #pragma unroll
-  for (int r = 0; r < 8; ++r) tile[threadIdx.x][threadIdx.y + 8 * r] = scaled_float(x[r], e);
+  for (int r = 0; r < 8; ++r) {
+    const int i = i0 + threadIdx.y + 8 * r;  // rs (a symmetric factorisation's row scale, <= 2^10) is 0 beyond n
+    tile[threadIdx.x][threadIdx.y + 8 * r] = scaled_float(x[r], e) * (rs ? rs[i] : 1.f);
+  }
   __syncthreads();
   // warp w writes columns j0 + w + 8 c, lane l the rows i0 + 2 l, i0 + 2 l + 1
   const int ii = i0 + 2 * threadIdx.x;
@@ -963,7 +969,7 @@ template <class T16>
 __global__ void __launch_bounds__(256) scaled_transpose16_narrow(
     const double* __restrict__ R, int64_t ld, int n, int m, int np, int mp,
     const unsigned long long* __restrict__ colmax, T16* __restrict__ Rt, float* __restrict__ colscale,
-    const SweepGuard guard, unsigned long long* red_cur, unsigned int* dcolmax) {
+    const SweepGuard guard, unsigned long long* red_cur, unsigned int* dcolmax, const float* __restrict__ rs) {
   if (guard.err) {
     __shared__ int s_end;
     if (threadIdx.x == 0) {
@@ -987,7 +993,9 @@ __global__ void __launch_bounds__(256) scaled_transpose16_narrow(
     int e = 0;
     if (mb != 0ull && E < 2047) e = E >= 1 ? E - 1022 : (63 - __clzll((long long)mb)) - 1073;
     if (blockIdx.x == 0 && threadIdx.x == 0) colscale[j] = ldexpf(1.f, e);
-    if (i < np) Rt[(int64_t)j * np + i] = to16<T16>(i < n ? scaled_float(R[(int64_t)i * ld + j], e) : 0.f);
+    if (i < np)
+      Rt[(int64_t)j * np + i] =
+          to16<T16>(i < n ? scaled_float(R[(int64_t)i * ld + j], e) * (rs ? rs[i] : 1.f) : 0.f);
   }
 }
 
@@ -1012,17 +1020,19 @@ struct BalancePre {
   bool trans = false;         // the adjoint (transposed) balance
   bool fp16 = true;
   float* y = nullptr;         // [np] scratch vectors, zero beyond n
-  float* yr = nullptr;
+  float* yr = nullptr;        // the product's input vector
   float* z = nullptr;
+  const float* gin = nullptr;   // W symmetric (W = D^-1 W_sym D): the product's input and
+  const float* gout = nullptr;  // output row scales (d and 1 / d, the adjoint the other way)
 };
 
 // The first kernel of a preconditioned sweep, in fp32: y = diag(t) src (the residual column),
-// z = rho o y and, for the forward balance, yr = (1 - rho) o y; also zeroes the sweep's status
-// words and the correction's column maximum.
+// z = rho o y and the product's input yr = (1 - rho) o y (forward) or y (adjoint), times gin
+// when given; also zeroes the sweep's status words and the correction's column maximum.
 __global__ void pre_first(const double* __restrict__ src, int64_t ld, const double* __restrict__ t,
                           const double* __restrict__ rho, int n, bool trans, float* __restrict__ y,
-                          float* __restrict__ yr, float* __restrict__ z, const SweepGuard guard,
-                          unsigned long long* red_cur, unsigned int* dcolmax) {
+                          float* __restrict__ yr, float* __restrict__ z, const float* __restrict__ gin,
+                          const SweepGuard guard, unsigned long long* red_cur, unsigned int* dcolmax) {
   if (guard.err) {
     __shared__ int s_end;
     if (threadIdx.x == 0) {
@@ -1040,7 +1050,7 @@ __global__ void pre_first(const double* __restrict__ src, int64_t ld, const doub
     const double r = rho[i];
     y[i] = (float)v;
     z[i] = (float)(r * v);
-    if (!trans) yr[i] = (float)((1.0 - r) * v);
+    yr[i] = (float)(trans ? v : (1.0 - r) * v) * (gin ? gin[i] : 1.f);
   }
 }
 
@@ -1053,8 +1063,9 @@ __global__ void pre_first(const double* __restrict__ src, int64_t ld, const doub
 // rows' padding (np is a multiple of 128) adds nothing.
 template <class T16>
 __global__ void pre_w_apply(const void* __restrict__ W, int np, int n, const float* __restrict__ v,
-                            const double* __restrict__ rho, const float* __restrict__ z, float* __restrict__ D,
-                            int64_t ldd, unsigned int* dcolmax, int* nonfinite, const int* skip) {
+                            const double* __restrict__ rho, const float* __restrict__ z,
+                            const float* __restrict__ gout, float* __restrict__ D, int64_t ldd,
+                            unsigned int* dcolmax, int* nonfinite, const int* skip) {
   if (skip && *(volatile const int*)skip) return;
   const int k = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
   const int lane = threadIdx.x & 31;
@@ -1101,11 +1112,68 @@ __global__ void pre_w_apply(const void* __restrict__ W, int np, int n, const flo
   acc += acc2;
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
   if (lane == 0) {
-    const float d = (rho ? (float)(1.0 - rho[k]) : 1.f) * acc + z[k];
+    const float d = (rho ? (float)(1.0 - rho[k]) : 1.f) * (gout ? gout[k] : 1.f) * acc + z[k];
     D[(int64_t)k * ldd] = d;
     if (!isfinite(d)) atomicExch(nonfinite, 1);
     else atomicMax(dcolmax, __float_as_uint(fabsf(d)));
   }
+}
+
+// ------------------------------------------------------------------ symmetric factorisation
+// With reciprocity, A_i F_ij = A_j F_ji, the system matrix I - F_NN diag(rho) is similar to the
+// symmetric I - G, G_ij = d_i F_ij rho_j / d_j with d_i = sqrt(A_i rho_i) (rho = 1 for the
+// balance's I - F_NN): (I - G) = D (I - F diag(rho)) D^-1. Its Newton-Schulz iterates
+// X (2I - A X) = 2X - X A X are symmetric, so the second product of each step computes the tiles
+// on and above the diagonal only (the first, A X, is symmetric only where X and A commute,
+// which rounding breaks: mirroring it lets the error grow step after step). The inverse
+// M = D^-1 M_sym D is applied by scaling the correction's input rows by d and its output rows
+// by 1/d (the transposed system: the other way round). d is normalised to max 1.
+
+// words: [0] bad (a non-positive or non-finite A_i rho_i), [1] / [2] min / max of A_i rho_i
+// (double bits, atomicMin / atomicMax; zeroed / set by the caller).
+__global__ void sym_check(const double* __restrict__ area, const double* __restrict__ rho, int n,
+                          unsigned long long* words) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double w = area[i] * (rho ? rho[i] : 1.0);
+  if (!(w > 0.0) || !isfinite(w)) {
+    atomicExch(&words[0], 1ull);
+    return;
+  }
+  const unsigned long long b = (unsigned long long)__double_as_longlong(w);
+  atomicMin(&words[1], b);
+  atomicMax(&words[2], b);
+}
+
+// d_i = sqrt(A_i rho_i / wmax): dl = d, dr = rho / d (the Newton-Schulz start's scalings), and
+// the correction's row scales fin = d, fout = 1 / d (forward) in fp32; zero beyond n.
+__global__ void sym_fill(const double* __restrict__ area, const double* __restrict__ rho, int n, int np,
+                         double wmax, double* __restrict__ dl, double* __restrict__ dr, float* __restrict__ fin,
+                         float* __restrict__ fout) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= np) return;
+  if (i >= n) {
+    dl[i] = dr[i] = 0.0;
+    fin[i] = fout[i] = 0.f;
+    return;
+  }
+  const double r = rho ? rho[i] : 1.0;
+  const double d = sqrt(area[i] * r / wmax);
+  dl[i] = d;
+  dr[i] = r / d;
+  fin[i] = (float)d;
+  fout[i] = (float)(1.0 / d);
+}
+
+// the transposed system's row scales from a stored d: fin = 1 / d, fout = d (1 where d = 0: a
+// general inverse, stored transposed, needs none)
+__global__ void sym_scales_t(const double* __restrict__ d, int n, int np, float* __restrict__ fin,
+                             float* __restrict__ fout) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= np) return;
+  const double v = i < n ? d[i] : 0.0;
+  fin[i] = i >= n ? 0.f : (v > 0.0 ? (float)(1.0 / v) : 1.f);
+  fout[i] = i >= n ? 0.f : (v > 0.0 ? (float)v : 1.f);
 }
 
 // ------------------------------------------------------------------ solver object
@@ -1136,6 +1204,10 @@ struct Buffers {
   double* Q;    // P' X (ld = mp) when want_q, else null
   double* vec;  // [2][np] per-row scratch (row sums, diagonal scalings)
   double* nsum; // [2][np] row and column sums of |Dl P Dr| (Newton-Schulz start)
+  double* symdl;  // [np] symmetric factorisation: d, and rho / d (its start's scalings)
+  double* symdr;
+  float* sfin;    // [np] the correction's row scales: input d, output 1 / d (or as set)
+  float* sfout;
 };
 
 template <class Take>
@@ -1158,6 +1230,10 @@ void plan(const Layout& L, Take&& t) {
   t.template take<double>(L.want_q ? (size_t)L.np * L.mp : 0);    // Q
   t.template take<double>((size_t)2 * L.np);                      // vec
   t.template take<double>((size_t)2 * L.np);                      // nsum
+  t.template take<double>((size_t)L.np);                          // symdl
+  t.template take<double>((size_t)L.np);                          // symdr
+  t.template take<float>((size_t)L.np);                           // sfin
+  t.template take<float>((size_t)L.np);                           // sfout
 }
 
 // The solver's status words in the context scratch (ints), laid out so that one copy
@@ -1186,6 +1262,10 @@ struct Solver {
   int splits = 1;    // K splits of the last exact product
   const BalancePre* pre = nullptr;  // set: corrections from the shared balance preconditioner
   const void* minv = nullptr;       // set: a stored inverse (16-bit np x np, row-major) replaces factor()
+  const double* sym_area = nullptr; // set: try the symmetric factorisation with these areas (factor_sym)
+  bool sym = false;                 // the last factorisation was the symmetric one
+  const float* rs_in = nullptr;     // the correction's row scales (symmetric inverse), or null
+  const float* rs_out = nullptr;
 
   unsigned long long* red(int parity) { return reinterpret_cast<unsigned long long*>(err + 10 + 6 * parity); }
 
@@ -1237,6 +1317,10 @@ struct Solver {
     b.Q = want_q ? cv.take<double>((size_t)L.np * L.mp) : nullptr;
     b.vec = cv.take<double>((size_t)2 * L.np);
     b.nsum = cv.take<double>((size_t)2 * L.np);
+    b.symdl = cv.take<double>((size_t)L.np);
+    b.symdr = cv.take<double>((size_t)L.np);
+    b.sfin = cv.take<float>((size_t)L.np);
+    b.sfout = cv.take<float>((size_t)L.np);
     err = ctx->d_scratch + kStatus;
     RG_CUDA_TRY(ctx, cudaMemsetAsync(err, 0, 6 * sizeof(int), s));  // error words and the GEMM's
     return RG_OK;
@@ -1260,7 +1344,7 @@ struct Solver {
 
   // Newton-Schulz approximate inverse of A = I - Dl P Dr into b.X16[cur].
   template <class T16>
-  rg_status factor_t(const double* dl, const double* dr) {
+  rg_status factor_t(const double* dl, const double* dr, bool symm, const double* gen_dr) {
     unsigned long long* e0 = reinterpret_cast<unsigned long long*>(err + 6);
     RG_CUDA_TRY(ctx, cudaMemsetAsync(e0, 0, 2 * sizeof(unsigned long long), s));
     T16* A16 = static_cast<T16*>(b.A16);
@@ -1268,8 +1352,8 @@ struct Solver {
     T16* Xt = static_cast<T16*>(b.Xt16);
     T16* Zt = static_cast<T16*>(b.Zt16);
     RG_CUDA_TRY(ctx, cudaMemsetAsync(b.nsum, 0, 2 * L.np * sizeof(double), s));
-    build_ns_start<T16><<<dim3(L.np / 32, L.np / 32), dim3(32, 8), 0, s>>>(P, ldp, transP, dl, dr, L.n, L.np, A16,
-                                                                           X[0], Xt, b.nsum, b.nsum + L.np);
+    build_ns_start<T16><<<dim3(L.np / 32, L.np / 32), dim3(32, 8), 0, s>>>(
+        P, ldp, transP, dl, dr, L.n, L.np, A16, X[0], Xt, b.nsum, b.nsum + L.np, symm, gen_dr);
     ns_norms<<<std::max(1, std::min(ctx->sm_count, (std::max(L.np, L.mp) + 255) / 256)), 256, 0, s>>>(
         b.nsum, b.nsum + L.np, L.np, e0, b.colmax, L.mp);
     ctx->launches += 2;
@@ -1300,22 +1384,59 @@ struct Solver {
     ns_steps = steps;
     cur = 0;
     for (int k = 1; k < steps; ++k) {  // step 1 was taken by build_ns_start
-      // Zt = (2I - A X)^T : A operand A16 [i][k], B operand X^T rows = X columns
-      rg_status st = tc::gemm(ctx, bf16, A16, L.np, Xt, L.np, L.np, L.np, L.np, tc::EpiTwoIMinusT<T16>{Zt, L.np}, s);
+      // Zt = (2I - A X)^T : A operand A16 [i][k], B operand X^T rows = X columns (X itself
+      // when symmetric); the whole product
+      rg_status st = tc::gemm(ctx, bf16, A16, L.np, symm ? X[cur] : Xt, L.np, L.np, L.np, L.np,
+                              tc::EpiTwoIMinusT<T16>{Zt, L.np}, s);
       if (st != RG_OK) return st;
-      // X' = X (2I - A X) : A operand X [i][k], B operand Z^T
-      st = tc::gemm(ctx, bf16, X[cur], L.np, Zt, L.np, L.np, L.np, L.np, tc::EpiStore16Both<T16>{X[cur ^ 1], Xt, L.np},
-                    s);
+      // X' = X (2I - A X) : A operand X [i][k], B operand Z^T; symmetric when X and A are, so
+      // then only its upper tiles are computed
+      st = tc::gemm(ctx, bf16, X[cur], L.np, Zt, L.np, L.np, L.np, L.np,
+                    tc::EpiStore16Both<T16>{X[cur ^ 1], symm ? X[cur ^ 1] : Xt, L.np, symm}, s, nullptr, symm);
       if (st != RG_OK) return st;
       cur ^= 1;
     }
     return RG_OK;
   }
-  rg_status factor(const double* dl, const double* dr) {
+  // symm: Dl P Dr is the symmetric form of P diag(gen_dr); the step count then comes from the
+  // latter's norms (the residual the refinement sees is D^-1 (its residual) D)
+  rg_status factor(const double* dl, const double* dr, bool symm = false, const double* gen_dr = nullptr) {
     const int tok = rg::timer_begin(ctx, rg::kTimeFactor, s);
-    const rg_status st = bf16 ? factor_t<__nv_bfloat16>(dl, dr) : factor_t<__half>(dl, dr);
+    const rg_status st =
+        bf16 ? factor_t<__nv_bfloat16>(dl, dr, symm, gen_dr) : factor_t<__half>(dl, dr, symm, gen_dr);
     rg::timer_end(ctx, tok, s);
     return st;
+  }
+
+  // The factorisation of I - P diag(rho) (rho null: 1) in its symmetric form when the areas
+  // make A P symmetric and every A_i rho_i is positive, within 2^20 of the largest (sym set,
+  // the correction's row scales in rs_in / rs_out); the general one otherwise.
+  rg_status factor_sym(const double* area, const double* rho) {
+    unsigned long long* words = reinterpret_cast<unsigned long long*>(b.nsum);  // free before the start
+    RG_CUDA_TRY(ctx, cudaMemsetAsync(words, 0, 3 * sizeof(unsigned long long), s));
+    RG_CUDA_TRY(ctx, cudaMemsetAsync(words + 1, 0xff, sizeof(unsigned long long), s));
+    sym_check<<<(L.n + 255) / 256, 256, 0, s>>>(area, rho, L.n, words);
+    ++ctx->launches;
+    RG_CUDA_TRY(ctx, cudaGetLastError());
+    int* hs = ctx->h_scratch;
+    RG_CUDA_TRY(ctx, cudaMemcpyAsync(hs, words, 3 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+    RG_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+    unsigned long long w[3];
+    memcpy(w, hs, sizeof(w));
+    double wmin, wmax;
+    memcpy(&wmin, &w[1], sizeof(double));
+    memcpy(&wmax, &w[2], sizeof(double));
+    sym = w[0] == 0ull && wmax > 0.0 && wmin >= wmax * 0x1p-20;
+    if (!sym) {
+      rs_in = rs_out = nullptr;
+      return factor(nullptr, rho, false);
+    }
+    sym_fill<<<(L.np + 255) / 256, 256, 0, s>>>(area, rho, L.n, L.np, wmax, b.symdl, b.symdr, b.sfin, b.sfout);
+    ++ctx->launches;
+    RG_CUDA_TRY(ctx, cudaGetLastError());
+    rs_in = b.sfin;
+    rs_out = b.sfout;
+    return factor(b.symdl, b.symdr, true, rho);
   }
 
   // One sweep: D = M src (src = R0 for the first, R after), D rounded to its one-slice form and
@@ -1334,28 +1455,29 @@ struct Solver {
       // D = W K diag(t) R (forward) or K^T W^T diag(t) R (adjoint), one column, as
       // W ((1 - rho) o y) + rho o y or (1 - rho) o (W^T y) + rho o y with y = diag(t) R
       const int rb = (L.n + 255) / 256, wb = (L.n + 7) / 8;
-      pre_first<<<rb, 256, 0, s>>>(src, L.mp, pre->t, pre->rho, L.n, pre->trans, pre->y, pre->yr, pre->z, g, rc,
-                                   b.dcolmax);
+      pre_first<<<rb, 256, 0, s>>>(src, L.mp, pre->t, pre->rho, L.n, pre->trans, pre->y, pre->yr, pre->z, pre->gin,
+                                   g, rc, b.dcolmax);
       auto wapply = pre->fp16 ? pre_w_apply<__half> : pre_w_apply<__nv_bfloat16>;
       if (!pre->trans)
-        wapply<<<wb, 256, 0, s>>>(pre->W, L.np, L.n, pre->yr, nullptr, pre->z, b.Dbuf, L.mp, b.dcolmax, err + 1, skip);
+        wapply<<<wb, 256, 0, s>>>(pre->W, L.np, L.n, pre->yr, nullptr, pre->z, pre->gout, b.Dbuf, L.mp, b.dcolmax,
+                                  err + 1, skip);
       else
-        wapply<<<wb, 256, 0, s>>>(pre->Wt, L.np, L.n, pre->y, pre->rho, pre->z, b.Dbuf, L.mp, b.dcolmax, err + 1,
-                                  skip);
+        wapply<<<wb, 256, 0, s>>>(pre->Wt, L.np, L.n, pre->yr, pre->rho, pre->z, pre->gout, b.Dbuf, L.mp, b.dcolmax,
+                                  err + 1, skip);
       ctx->launches += 2;
       RG_CUDA_TRY(ctx, cudaGetLastError());
     } else {
       T16* Rt = static_cast<T16*>(b.Rt16);
       if (L.m <= kNarrow)
         scaled_transpose16_narrow<T16><<<nb, 256, 0, s>>>(src, L.mp, L.n, L.m, L.np, L.mp, b.colmax, Rt, b.colscale,
-                                                          g, rc, b.dcolmax);
+                                                          g, rc, b.dcolmax, rs_in);
       else
         scaled_transpose16<T16><<<tg, dim3(32, 8), 0, s>>>(src, L.mp, L.n, L.m, L.np, L.mp, b.colmax, Rt,
-                                                            b.colscale, g, rc, b.dcolmax);
+                                                            b.colscale, g, rc, b.dcolmax, rs_in);
       ++ctx->launches;
       RG_CUDA_TRY(ctx, cudaGetLastError());
       st = tc::gemm(ctx, bf16, minv ? minv : b.X16[cur], L.np, Rt, L.np, L.n, L.m, L.np,
-                    tc::EpiCorrection{b.Dbuf, L.mp, b.colscale, b.dcolmax, err + 1}, s, skip);
+                    tc::EpiCorrection{b.Dbuf, L.mp, b.colscale, b.dcolmax, err + 1, rs_out}, s, skip);
       if (st != RG_OK) return st;
     }
     if (L.m <= kNarrow)
@@ -1437,6 +1559,8 @@ struct Solver {
       // the stored inverse stands in for the factorisation; refine() wants the column maxima
       // zeroed, which the factorisation's norm kernel does otherwise
       RG_CUDA_TRY(ctx, cudaMemsetAsync(b.colmax, 0, L.mp * sizeof(unsigned long long), s));
+    } else if (sym_area && !dl) {
+      st = factor_sym(sym_area, dr);
     } else {
       st = factor(dl, dr);
     }
@@ -1507,12 +1631,22 @@ struct FactorHeader {
 
 size_t factor_store_bytes(int n, int n_sets) {
   const size_t np = (size_t)(n + NB - 1) / NB * NB;
-  return kFactorHeader + (size_t)n_sets * np * np * sizeof(uint16_t);
+  return kFactorHeader + (size_t)n_sets * np * np * sizeof(uint16_t) + (size_t)n_sets * np * sizeof(double);
 }
 
 void* factor_slice(const void* store, int n, int set) {
   const size_t np = (size_t)(n + NB - 1) / NB * NB;
   return static_cast<char*>(const_cast<void*>(store)) + kFactorHeader + (size_t)set * np * np * sizeof(uint16_t);
+}
+
+// the set's scale vector d after all the inverses (store_sets: the sets the store was made
+// for): d > 0 when the set's inverse is the symmetric one (M_sym, with M = D^-1 M_sym D),
+// zeros when it is the transpose of a general inverse
+double* factor_dvec(const void* store, int n, int store_sets, int set) {
+  const size_t np = (size_t)(n + NB - 1) / NB * NB;
+  return reinterpret_cast<double*>(static_cast<char*>(const_cast<void*>(store)) + kFactorHeader +
+                                   (size_t)store_sets * np * np * sizeof(uint16_t)) +
+         (size_t)set * np;
 }
 
 __global__ void write_factor_header(FactorHeader* h, FactorHeader v) {
@@ -1529,9 +1663,10 @@ rg_status check_store_layout(rg_ctx* ctx, const void* store, size_t bytes, int n
 }
 
 // Reads the store's header and checks that it holds factors of n unknowns, in `precision`
-// (the inverse is an operand of a GEMM whose other operand has that type), for n_sets sets.
+// (the inverse is an operand of a GEMM whose other operand has that type), for n_sets sets;
+// *store_sets receives the sets the store was made for.
 rg_status check_stored_factors(rg_ctx* ctx, const void* store, size_t bytes, int n, int n_sets, int precision,
-                               cudaStream_t s, const char* fn) {
+                               cudaStream_t s, const char* fn, int* store_sets) {
   rg_status st = check_store_layout(ctx, store, bytes, n, n_sets, fn);
   if (st != RG_OK) return st;
   FactorHeader h;
@@ -1543,8 +1678,11 @@ rg_status check_stored_factors(rg_ctx* ctx, const void* store, size_t bytes, int
   if (h.precision != precision)
     return rg::fail(ctx, RG_ERR_ARG, "%s: the factors were made in precision %d, the call asks for %d", fn,
                     h.precision, precision);
-  if (h.filled < n_sets)
+  if (h.filled < n_sets || h.n_sets < h.filled)
     return rg::fail(ctx, RG_ERR_ARG, "%s: the factor store holds %d sets, the call has %d", fn, h.filled, n_sets);
+  if (bytes < factor_store_bytes(n, h.n_sets))
+    return rg::fail(ctx, RG_ERR_ARG, "%s: the factor store is shorter than its %d sets", fn, h.n_sets);
+  *store_sets = h.n_sets;
   return RG_OK;
 }
 
@@ -1957,7 +2095,8 @@ rg_status rg_exact_split(rg_ctx* ctx, int32_t n, const double* P_d, int64_t ldp,
 }
 
 rg_status rg_gebhart(rg_ctx* ctx, int32_t n, const double* F_d, int32_t n_sets, const double* eps_d,
-                     const double* rho_d, int32_t precision, double tol, int32_t max_sweeps, double* B_d,
+                     const double* rho_d, const double* area_d, int32_t precision, double tol, int32_t max_sweeps,
+                     double* B_d,
                      int32_t* sweeps_out_h, double* resid_out_h, void* factors_d, size_t factors_bytes,
                      void* workspace_d, size_t workspace_bytes, void* stream) {
   if (!ctx) return RG_ERR_ARG;
@@ -1975,6 +2114,7 @@ rg_status rg_gebhart(rg_ctx* ctx, int32_t n, const double* F_d, int32_t n_sets, 
                 "rg_gebhart");
   if (st == RG_OK) st = sv.set_matrix(F_d, n + 1, false);
   if (st != RG_OK) return st;
+  sv.sym_area = area_d;  // with areas: the symmetric factorisation where it applies
   int max_sw = 0;
   double max_rel = 0.0;
   // the header says "no sets" until every set has been factorised
@@ -2001,6 +2141,18 @@ rg_status rg_gebhart(rg_ctx* ctx, int32_t n, const double* F_d, int32_t n_sets, 
     double rel = 0.0;
     st = sv.run(nullptr, rho, tol, max_sweeps, &sw, &rel);
     if (st != RG_OK && st != RG_ERR_NOT_CONVERGED) return st;
+    if (factors_d) {
+      // the symmetric inverse itself and its scales; a general one is already there (its
+      // transpose, kept by the factorisation) with zero scales
+      double* dv = factor_dvec(factors_d, n, n_sets, set);
+      if (sv.sym) {
+        RG_CUDA_TRY(ctx, cudaMemcpyAsync(sv.b.Xt16, sv.b.X16[sv.cur], (size_t)sv.L.np * sv.L.np * sizeof(uint16_t),
+                                         cudaMemcpyDeviceToDevice, s));
+        RG_CUDA_TRY(ctx, cudaMemcpyAsync(dv, sv.b.symdl, (size_t)sv.L.np * sizeof(double), cudaMemcpyDeviceToDevice, s));
+      } else {
+        RG_CUDA_TRY(ctx, cudaMemsetAsync(dv, 0, (size_t)sv.L.np * sizeof(double), s));
+      }
+    }
     copy_in<<<grid_for((int64_t)n * (n + 1), ctx->sm_count), kThreads, 0, s>>>(
         sv.b.X, sv.L.mp, n, n + 1, B_d + (size_t)set * n * (n + 1), n + 1);
     ++ctx->launches;
@@ -2029,8 +2181,9 @@ rg_status rg_gebhart_adjoint(rg_ctx* ctx, int32_t n, const double* F_d, int32_t 
                "rg_gebhart_adjoint: bad argument");
   RG_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
   cudaStream_t s = (cudaStream_t)stream;
+  int store_sets = 0;
   if (factors_d) {
-    st = check_stored_factors(ctx, factors_d, factors_bytes, n, n_sets, precision, s, "rg_gebhart_adjoint");
+    st = check_stored_factors(ctx, factors_d, factors_bytes, n, n_sets, precision, s, "rg_gebhart_adjoint", &store_sets);
     if (st != RG_OK) return st;
   }
   Solver sv{ctx};
@@ -2047,7 +2200,15 @@ rg_status rg_gebhart_adjoint(rg_ctx* ctx, int32_t n, const double* F_d, int32_t 
                                                                                 sv.b.R0, sv.L.mp);
     ++ctx->launches;
     RG_CUDA_TRY(ctx, cudaGetLastError());
-    if (factors_d) sv.minv = factor_slice(factors_d, n, set);
+    if (factors_d) {
+      sv.minv = factor_slice(factors_d, n, set);
+      sym_scales_t<<<(sv.L.np + 255) / 256, 256, 0, s>>>(factor_dvec(factors_d, n, store_sets, set), n, sv.L.np,
+                                                           sv.b.sfin, sv.b.sfout);
+      ++ctx->launches;
+      RG_CUDA_TRY(ctx, cudaGetLastError());
+      sv.rs_in = sv.b.sfin;
+      sv.rs_out = sv.b.sfout;
+    }
     int sw = 0;
     double rel = 0.0;
     st = sv.run(rho, nullptr, tol, max_sweeps, &sw, &rel, set == 0);
@@ -2172,12 +2333,17 @@ static rg_status temperatures_sets(rg_ctx* ctx, int32_t n, const double* F_d, in
   // only entries below n are ever written: the padding stays zero for the row products
   RG_CUDA_TRY(ctx, cudaMemsetAsync(pre.y, 0, sv.L.np * sizeof(float), s));
   RG_CUDA_TRY(ctx, cudaMemsetAsync(pre.yr, 0, sv.L.np * sizeof(float), s));
-  // W ~ (I - F_NN)^-1, shared by every set
+  // W ~ (I - F_NN)^-1, shared by every set (symmetric via sqrt(A) when the areas allow)
   st = sv.set_matrix(F_d, n + 1, false);
-  if (st == RG_OK) st = sv.factor(nullptr, nullptr);
+  if (st == RG_OK) st = sv.factor_sym(area_d, nullptr);
   if (st != RG_OK) return st;
   pre.W = sv.b.X16[sv.cur];
-  pre.Wt = sv.b.Xt16;
+  pre.Wt = sv.sym ? sv.b.X16[sv.cur] : sv.b.Xt16;
+  if (sv.sym) {
+    pre.gin = adjoint ? sv.b.sfout : sv.b.sfin;
+    pre.gout = adjoint ? sv.b.sfin : sv.b.sfout;
+  }
+  sv.rs_in = sv.rs_out = nullptr;  // the corrections come from the preconditioner
   pre.trans = adjoint;
   pre.fp16 = precision == RG_PREC_FP16_IR;
   sv.pre = &pre;
@@ -2259,8 +2425,10 @@ rg_status rg_gebhart_adjoint_factored(rg_ctx* ctx, int32_t n, const double* F_d,
                "rg_gebhart_adjoint_factored: bad argument");
   RG_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
   cudaStream_t s = (cudaStream_t)stream;
+  int store_sets = 0;
   if (factors_d) {
-    st = check_stored_factors(ctx, factors_d, factors_bytes, n, n_sets, precision, s, "rg_gebhart_adjoint_factored");
+    st = check_stored_factors(ctx, factors_d, factors_bytes, n, n_sets, precision, s, "rg_gebhart_adjoint_factored",
+                              &store_sets);
     if (st != RG_OK) return st;
   }
   Solver sv{ctx};
@@ -2274,7 +2442,15 @@ rg_status rg_gebhart_adjoint_factored(rg_ctx* ctx, int32_t n, const double* F_d,
     factors_in<<<(n + 255) / 256, 256, 0, s>>>(a_d + (size_t)set * rank * n, rank, n, sv.b.R0, sv.L.mp);
     ++ctx->launches;
     RG_CUDA_TRY(ctx, cudaGetLastError());
-    if (factors_d) sv.minv = factor_slice(factors_d, n, set);
+    if (factors_d) {
+      sv.minv = factor_slice(factors_d, n, set);
+      sym_scales_t<<<(sv.L.np + 255) / 256, 256, 0, s>>>(factor_dvec(factors_d, n, store_sets, set), n, sv.L.np,
+                                                           sv.b.sfin, sv.b.sfout);
+      ++ctx->launches;
+      RG_CUDA_TRY(ctx, cudaGetLastError());
+      sv.rs_in = sv.b.sfin;
+      sv.rs_out = sv.b.sfout;
+    }
     int sw = 0;
     double rel = 0.0;
     st = sv.run(rho, nullptr, tol, max_sweeps, &sw, &rel, set == 0);

@@ -242,13 +242,17 @@ __device__ __forceinline__ __nv_bfloat16 to_16<__nv_bfloat16>(float x) { return 
 template <>
 __device__ __forceinline__ __half to_16<__half>(float x) { return __float2half_rn(x); }
 
+// Every epilogue's store() also receives `offdiag`: true for an off-diagonal tile of a
+// symmetric product (GemmArgs::sym), which stands for its transposed tile as well; the
+// epilogues of the Newton-Schulz steps then also write the transposed position.
+
 // C[r][c] = beta * C[r][c] + alpha * acc   (fp32 C)
 struct EpiF32 {
   float* C;
   int64_t ldc;
   float alpha, beta;
   __device__ __forceinline__ void store(int row0, int lane, int c0, int M, int N, const float* v,
-                                        float (*stage)[33]) const {
+                                        float (*stage)[33], bool) const {
     staged_rows(row0, lane, c0, M, N, v, stage, [&](int r, int c, float x) {
       float* p = C + (int64_t)r * ldc + c;
       *p = (beta == 0.f ? 0.f : beta * *p) + alpha * x;
@@ -257,13 +261,14 @@ struct EpiF32 {
 };
 
 // Newton-Schulz half step: Zt[c][r] = 16-bit (2 delta_rc - acc) -- the transposed store is
-// coalesced as it is (the warp's 32 rows are 32 consecutive elements of a row of Zt).
+// coalesced as it is (the warp's 32 rows are 32 consecutive elements of a row of Zt). A X is
+// not symmetric unless X and A commute, which rounding breaks: this product is always whole.
 template <class T16>
 struct EpiTwoIMinusT {
   T16* Zt;
   int64_t ld;
   __device__ __forceinline__ void store(int row0, int lane, int c0, int M, int N, const float* v,
-                                        float (*)[33]) const {
+                                        float (*)[33], bool) const {
     const int r = row0 + lane;
     if (r >= M) return;
 #pragma unroll 8
@@ -274,16 +279,19 @@ struct EpiTwoIMinusT {
   }
 };
 
-// Newton-Schulz step result: X[r][c] and Xt[c][r] = 16-bit acc.
+// Newton-Schulz step result: X[r][c] and Xt[c][r] = 16-bit acc. With `sym` (Xt = X, the
+// product X (2I - A X) = 2X - X A X symmetric for symmetric X and A, whatever their
+// commutation) the transposed write is made for off-diagonal tiles only.
 template <class T16>
 struct EpiStore16Both {
   T16* X;
   T16* Xt;
   int64_t ld;
+  bool sym = false;
   __device__ __forceinline__ void store(int row0, int lane, int c0, int M, int N, const float* v,
-                                        float (*stage)[33]) const {
+                                        float (*stage)[33], bool offdiag) const {
     const int r = row0 + lane;
-    if (r < M) {
+    if (r < M && (!sym || offdiag)) {
 #pragma unroll 8
       for (int i = 0; i < 32; ++i) {
         const int c = c0 + i;
@@ -294,17 +302,18 @@ struct EpiStore16Both {
   }
 };
 
-// D[r][c] = acc * colscale[c] (fp32; the refinement's correction M R before it is rounded to
-// its one-slice form), with max_r |D[r][c]| folded into colmax[c] (float bits, atomicMax) and
-// *nonfinite raised on an inf or NaN.
+// D[r][c] = acc * colscale[c] (* rowscale[r] when given) (fp32; the refinement's correction
+// M R before it is rounded to its one-slice form), with max_r |D[r][c]| folded into colmax[c]
+// (float bits, atomicMax) and *nonfinite raised on an inf or NaN.
 struct EpiCorrection {
   float* D;
   int64_t ld;
   const float* colscale;
   unsigned int* colmax;
   int* nonfinite;
+  const float* rowscale = nullptr;
   __device__ __forceinline__ void store(int row0, int lane, int c0, int M, int N, const float* v,
-                                        float (*stage)[33]) const {
+                                        float (*stage)[33], bool) const {
 #pragma unroll
     for (int i = 0; i < 32; ++i) stage[lane][i] = v[i];
     __syncwarp();
@@ -317,7 +326,7 @@ struct EpiCorrection {
     for (int rr = 0; rr < 32; ++rr) {
       const int r = row0 + rr;
       if (cok && r < M) {
-        const float d = stage[rr][lane] * cs;
+        const float d = stage[rr][lane] * cs * (rowscale ? rowscale[r] : 1.f);
         D[(int64_t)r * ld + c] = d;
         mx = fmaxf(mx, fabsf(d));
         bad |= !isfinite(d);
@@ -337,7 +346,36 @@ struct GemmArgs {
   const int* skip = nullptr;
   // > 0: the inner dimension of the product the launch stands for (kernel timer accounting)
   int alg_k = 0;
+  // 1: the product is symmetric (M = N, square tiles): only the tiles on and above the
+  // diagonal are computed, the epilogue writing each off-diagonal one for its transpose too
+  int sym = 0;
 };
+
+// Tile (I, J), I <= J, of the pid-th tile on or above the diagonal of a T x T tiling, in
+// bands of kGroupM tile rows, each band's tiles column by column (the CTAs running together
+// share their column tiles in L2).
+__device__ __forceinline__ void upper_tile(int pid, int T, int& I, int& J) {
+  int r0 = 0;
+  for (;;) {
+    const int r1 = min(r0 + kGroupM, T);
+    // band rows [r0, r1): column J holds min(r1, J + 1) - r0 tiles, J >= r0
+    const int h = r1 - r0;
+    const int band = h * (h + 1) / 2 + h * (T - r1);
+    if (pid < band) break;
+    pid -= band;
+    r0 = r1;
+  }
+  const int r1 = min(r0 + kGroupM, T);
+  for (int j = r0;; ++j) {
+    const int cnt = min(r1, j + 1) - r0;
+    if (pid < cnt) {
+      I = r0 + pid;
+      J = j;
+      return;
+    }
+    pid -= cnt;
+  }
+}
 
 template <int BN, int kStages, class Epi, bool kBF16>
 __global__ void __launch_bounds__(kThreads, 1)
@@ -366,11 +404,17 @@ __global__ void __launch_bounds__(kThreads, 1)
   // innermost, so that the CTAs resident together share their A and B tiles in L2
   const int tiles_m = (args.M + BM - 1) / BM, tiles_n = (args.N + BN - 1) / BN;
   const int pid = blockIdx.x;
-  const int group = pid / (kGroupM * tiles_n);
-  const int first_m = group * kGroupM;
-  const int group_m = min(tiles_m - first_m, kGroupM);
-  const int tile_m = first_m + (pid % (kGroupM * tiles_n)) % group_m;
-  const int tile_n = (pid % (kGroupM * tiles_n)) / group_m;
+  int tile_m, tile_n;
+  if (args.sym) {  // square tiles (BN == BM), those on and above the diagonal
+    upper_tile(pid, tiles_m, tile_m, tile_n);
+  } else {
+    const int group = pid / (kGroupM * tiles_n);
+    const int first_m = group * kGroupM;
+    const int group_m = min(tiles_m - first_m, kGroupM);
+    tile_m = first_m + (pid % (kGroupM * tiles_n)) % group_m;
+    tile_n = (pid % (kGroupM * tiles_n)) / group_m;
+  }
+  const bool offdiag = args.sym && tile_m != tile_n;
   const int m0 = tile_m * BM, n0 = tile_n * BN;
   const int kb_total = (args.K + BK - 1) / BK;
 
@@ -444,7 +488,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll 1
       for (int c0 = 0; c0 < BN; c0 += 32) {
         tmem_ld32(tmem_base + lane_addr + (uint32_t)c0, v);
-        epi.store(row0, lane, n0 + c0, args.M, args.N, v, stage);
+        epi.store(row0, lane, n0 + c0, args.M, args.N, v, stage, offdiag);
       }
     } else {
       *abort_flag = 1;
@@ -503,11 +547,17 @@ __global__ void __launch_bounds__(kThreads, 1) __cluster_dims__(2, 1, 1)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int tiles_m = (args.M + 2 * BM - 1) / (2 * BM), tiles_n = (args.N + PN - 1) / PN;
   const int pid = blockIdx.x >> 1;
-  const int group = pid / (kGroupM * tiles_n);
-  const int first_m = group * kGroupM;
-  const int group_m = min(tiles_m - first_m, kGroupM);
-  const int tile_m = first_m + (pid % (kGroupM * tiles_n)) % group_m;
-  const int tile_n = (pid % (kGroupM * tiles_n)) / group_m;
+  int tile_m, tile_n;
+  if (args.sym) {  // 256 x 256 tiles on and above the diagonal
+    upper_tile(pid, tiles_m, tile_m, tile_n);
+  } else {
+    const int group = pid / (kGroupM * tiles_n);
+    const int first_m = group * kGroupM;
+    const int group_m = min(tiles_m - first_m, kGroupM);
+    tile_m = first_m + (pid % (kGroupM * tiles_n)) % group_m;
+    tile_n = (pid % (kGroupM * tiles_n)) / group_m;
+  }
+  const bool offdiag = args.sym && tile_m != tile_n;
   const int m0 = tile_m * 2 * BM + (int)rank * BM;         // this CTA's rows
   const int nb0 = tile_n * PN + (int)rank * (PN / 2);      // this CTA's half of B's rows
   const int n0 = tile_n * PN;                              // the tile's columns
@@ -586,7 +636,7 @@ __global__ void __launch_bounds__(kThreads, 1) __cluster_dims__(2, 1, 1)
 #pragma unroll 1
       for (int c0 = 0; c0 < PN; c0 += 32) {
         tmem_ld32(tmem_base + lane_addr + (uint32_t)c0, v);
-        epi.store(row0, lane, n0 + c0, args.M, args.N, v, stage);
+        epi.store(row0, lane, n0 + c0, args.M, args.N, v, stage, offdiag);
       }
     } else {
       *abort_flag = 1;
@@ -1028,9 +1078,13 @@ constexpr size_t exact_pair_smem_bytes() {
 // ------------------------------------------------------------------ host side
 // Launch D = A B^T (A [M x K], B [N x K], 16-bit K-major) with the epilogue `epi`;
 // instantiated in gemm.cu for the epilogues above (bf16 selects the operand type).
+// sym: the product is symmetric (A B^T with M = N, e.g. two commuting symmetric matrices);
+// where the tiles are square only those on and above the diagonal are computed and the
+// epilogue writes the off-diagonal ones for their transposes too (the Newton-Schulz epilogues
+// with their own `sym` set), else the whole product is computed.
 template <class Epi>
 rg_status gemm(rg_ctx* ctx, bool bf16, const void* A, int64_t lda, const void* B, int64_t ldb, int M, int N, int K,
-               const Epi& epi, cudaStream_t s, const int* skip = nullptr);
+               const Epi& epi, cudaStream_t s, const int* skip = nullptr, bool sym = false);
 
 // C (fp32, ldc) = alpha * A B^T + beta * C with A [M x K] (lda), B [N x K] (ldb), 16-bit
 // K-major operands (bf16 when `bf16`, else fp16). lda, ldb: multiples of 8 elements;

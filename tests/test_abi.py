@@ -103,8 +103,8 @@ def test_binding_argument_types_match_the_header():
 
 def test_solver_workspace_sizes_without_a_gpu():
     """The caller-owned workspace sizes are pure host arithmetic: positive, growing with n,
-    the REF query equal to rg_solver_workspace's, the factor store a header and one 16-bit
-    np x np block per set."""
+    the REF query equal to rg_solver_workspace's, the factor store a header, one 16-bit np x np
+    block and one fp64 scale vector of np per set."""
     from paper_2511_04277_gb300 import api
     from paper_2511_04277_gb300._native import RadgebError
     for kind in ("gebhart", "gebhart_adjoint", "temperatures", "temperatures_sets", "enforce_lsq"):
@@ -114,7 +114,7 @@ def test_solver_workspace_sizes_without_a_gpu():
     assert api.gebhart_workspace(700, 3, "fp16") == api.solver_workspace("gebhart", 700)
     # the adjoint keeps F^T Lambda as well: more than the forward solve
     assert api.solver_workspace("gebhart_adjoint", 700) > api.solver_workspace("gebhart", 700)
-    assert api.gebhart_workspace(700, 3, "bf16", keep_factors=True) == 256 + 3 * 768 * 768 * 2
+    assert api.gebhart_workspace(700, 3, "bf16", keep_factors=True) == 256 + 3 * 768 * 768 * 2 + 3 * 768 * 8
     with pytest.raises(RadgebError):
         api.gebhart_workspace(0, 1, "bf16", keep_factors=True)
     with pytest.raises(RadgebError):

@@ -106,7 +106,7 @@ def test_stores_that_do_not_fit_the_call_are_refused(rg_ctx):
     F, eps, rho, rng = _system(N, S, 11)
     Fd, ed, rd = _dev(F), _dev(eps), _dev(rho)
     nbytes = api.gebhart_workspace(N, S, "fp16", keep_factors=True)
-    assert nbytes == 256 + S * 256 * 256 * 2
+    assert nbytes == 256 + S * 256 * 256 * 2 + S * 256 * 8
     store = api.gebhart_factor_store(N, S, "fp16")
     B, _, _ = api.gebhart(rg_ctx, Fd, ed, rd, "fp16", tol=1e-12, factors=store)
     W = _dev(rng.standard_normal((S, N, N + 1)))
@@ -163,3 +163,75 @@ def test_factored_adjoint_ranks_across_the_narrow_and_wide_kernels(rg_ctx, rank)
         deo, dro = G.gebhart_adjoint(F, eps[s], rho[s], Bh[s], ah[s].T @ bh[s])
         assert np.abs(de[s].cpu().numpy() - deo).max() <= 1e-9 * np.abs(deo).max()
         assert np.abs(dr[s].cpu().numpy() - dro).max() <= 1e-9 * np.abs(dro).max()
+
+
+# ------------------------------------------------------------------ symmetric factorisation
+@pytest.mark.parametrize("N", [2500, 3700])
+def test_symmetric_factorisation_matches_the_oracle(rg_ctx, N):
+    # (the step count of the symmetric form comes from the unscaled system's norms)
+    """With the areas of a reciprocal F the REF solve builds its 16-bit inverse in the
+    symmetric form D K D^-1 (D = diag(sqrt(A rho))), computing the tiles on and above the
+    diagonal of the symmetric product X (2I - A X) of each Newton-Schulz step: 128-wide tiles
+    at N = 2,500, CTA pairs (256-wide) at N = 3,700. B against the oracle, and against the
+    general factorisation."""
+    rng = np.random.default_rng(N)
+    A = rng.uniform(0.5, 2.0, N)
+    G_ = rng.random((N, N)) * (rng.random((N, N)) < 0.3)
+    G_ = (G_ + G_.T) / (2 * N) * 0.8
+    np.fill_diagonal(G_, 0.0)
+    F = np.concatenate([G_, (A - G_.sum(axis=1))[:, None]], axis=1) / A[:, None]
+    eps = rng.uniform(0.05, 0.9, (2, N))
+    rho = 1.0 - eps
+    Fd, ed, rd, Ad = _dev(F), _dev(eps), _dev(rho), _dev(A)
+    B, sw, res = api.gebhart(rg_ctx, Fd, ed, rd, "fp16", tol=1e-12, areas=Ad)
+    B0, sw0, _ = api.gebhart(rg_ctx, Fd, ed, rd, "fp16", tol=1e-12)
+    assert res <= 1e-12 and sw <= sw0 + 1
+    assert (B - B0).abs().max().item() <= 1e-10 * B0.abs().max().item()
+    for s in (0, 1):
+        Bo = G.gebhart(F, eps[s], rho[s])
+        got = B[s].cpu().numpy()
+        err = (np.abs(got - Bo).max(axis=1) / np.abs(Bo).max(axis=1)).max()
+        assert err <= 1e-9
+
+
+def test_stored_symmetric_inverse_and_the_adjoints(rg_ctx):
+    """The store keeps M_sym and d for a set factorised symmetrically (M = D^-1 M_sym D is an
+    approximate inverse of K); the adjoints through it match the oracle and the adjoints
+    without a store. A set with a zero reflectivity takes the general factorisation (zero d)."""
+    N, S = 3700, 2
+    rng = np.random.default_rng(5)
+    A = rng.uniform(0.5, 2.0, N)
+    G_ = rng.random((N, N)) * (rng.random((N, N)) < 0.3)
+    G_ = (G_ + G_.T) / (2 * N) * 0.8
+    np.fill_diagonal(G_, 0.0)
+    F = np.concatenate([G_, (A - G_.sum(axis=1))[:, None]], axis=1) / A[:, None]
+    eps = rng.uniform(0.05, 0.9, (S, N))
+    eps[1, 7] = 1.0  # a black face: rho = 0 -> the general factorisation for set 1
+    rho = 1.0 - eps
+    Fd, ed, rd, Ad = _dev(F), _dev(eps), _dev(rho), _dev(A)
+    store = api.gebhart_factor_store(N, S, "fp16")
+    B, _, _ = api.gebhart(rg_ctx, Fd, ed, rd, "fp16", tol=1e-12, factors=store, areas=Ad)
+    np_ = 3712
+    mats = store[256:256 + S * np_ * np_ * 2].view(torch.float16).reshape(S, np_, np_)
+    dv = store[256 + S * np_ * np_ * 2:].view(torch.float64).reshape(S, np_)
+    d0 = dv[0, :N].cpu().numpy()
+    assert (d0 > 0).all() and abs(d0.max() - 1.0) < 1e-12 and not dv[1].any()
+    Msym = mats[0, :N, :N].double().cpu().numpy()
+    # mirrored tiles are exact transposes; diagonal tiles are symmetric to 16-bit rounding
+    assert np.abs(Msym - Msym.T).max() <= 2e-3 * np.abs(Msym).max()
+    K = G.k_matrix(F, rho[0])
+    M = Msym * (d0[None, :] / d0[:, None])             # D^-1 M_sym D
+    assert np.abs(np.eye(N) - K @ M).sum(axis=1).max() <= 0.05
+    W = _dev(rng.standard_normal((S, N, N + 1)))
+    a = _dev(rng.standard_normal((S, 2, N)))
+    b = _dev(rng.standard_normal((S, 2, N + 1)))
+    de, dr = api.gebhart_adjoint(rg_ctx, Fd, ed, rd, B, W, "fp16", tol=1e-12, factors=store)
+    de0, dr0 = api.gebhart_adjoint(rg_ctx, Fd, ed, rd, B, W, "fp16", tol=1e-12)
+    de_f, dr_f = api.gebhart_adjoint_factored(rg_ctx, Fd, ed, rd, B, a, b, "fp16", tol=1e-12, factors=store)
+    de0_f, dr0_f = api.gebhart_adjoint_factored(rg_ctx, Fd, ed, rd, B, a, b, "fp16", tol=1e-12)
+    for got, ref in ((de, de0), (dr, dr0), (de_f, de0_f), (dr_f, dr0_f)):
+        assert (got - ref).abs().max().item() <= 1e-10 * ref.abs().max().item()
+    Bh = B.cpu().numpy()
+    deo, dro = G.gebhart_adjoint(F, eps[0], rho[0], Bh[0], W[0].cpu().numpy())
+    assert np.abs(de[0].cpu().numpy() - deo).max() <= 1e-9 * np.abs(deo).max()
+    assert np.abs(dr[0].cpu().numpy() - dro).max() <= 1e-9 * np.abs(dro).max()
