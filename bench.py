@@ -394,6 +394,16 @@ def rownorm(x, y):
     return float(((x - y).abs().amax(dim=-1) / y.abs().amax(dim=-1).clamp_min(1e-300)).max())
 
 
+def enforce_bytes(n, iters):
+    """Algorithmic HBM bytes of `iters` equal-weight enforcer iterations: the first reads and
+    writes the whole N x (N+1) matrix (16 B per entry); every later one, on the symmetric
+    matrix, the tiles on and above the diagonal and the environment column (16 B per stored
+    entry)."""
+    if iters <= 0:
+        return 0.0
+    return 16.0 * n * (n + 1) + 16.0 * (iters - 1) * (n * (n + 1) / 2.0 + n)
+
+
 def kernel_rooflines(api, ctx, pipe, steps, step_ms, peaks, trace_roof):
     """Per kernel class over the timed steps (the library's kernel timer: CUDA events on the
     launching stream around every launch): share of the step, mean launch time and the
@@ -438,11 +448,12 @@ def kernel_rooflines(api, ctx, pipe, steps, step_ms, peaks, trace_roof):
                         if kind == "residual_gemm" else "achieved = executed tensor flops (2 M N K)"})
         else:
             it = getattr(pipe, "iters", 0)
-            gb = 16.0 * pipe.N * (pipe.N + 1) * it / (per_launch * 1e-3) / 1e9
+            gb = enforce_bytes(pipe.N, it) / (per_launch * 1e-3) / 1e9
             row.update({"kernel": "enforce_persistent", "bound": "hbm", "achieved": round(gb, 1), "peak": hbm,
                         "unit": "GB/s", "frac": round(gb / hbm, 4), "traffic": None,
-                        "note": f"16 B per matrix entry per iteration, {it} iterations per launch; the fp64 pipe "
-                                "(6 fp64 operations per pair of entries) is the limit on this GPU"})
+                        "note": f"{it} iterations per launch: the first reads and writes every entry (16 B), the "
+                                "symmetric ones after it the tiles on and above the diagonal (16 B per stored "
+                                "entry, one fp64 add and multiply each, fixed-point row sums)"})
         out[kind] = row
     r = api.kernel_timer_read(ctx, "factor")
     if r["launches"]:
@@ -644,8 +655,9 @@ def extra_stages(api, torch, ctx, flush, stream, device, peaks):
 
 
 def stage_rooflines(api, torch, ctx, pipe, flush, stream, peaks):
-    """Achieved fractions of the iterative enforcer (HBM bound: 16 B per matrix entry per
-    iteration), the REF solve (tensor bound; LU-equivalent flops, 2/3 N^3 + 2 N^2 (N+1), plus
+    """Achieved fractions of the iterative enforcer (HBM bound: 16 B per entry in the first
+    iteration, 16 B per stored entry of the upper triangle in the later ones), the REF solve
+    (tensor bound; LU-equivalent flops, 2/3 N^3 + 2 N^2 (N+1), plus
     2 N^2 (N+1) per refinement sweep) and the least-squares enforcer on a small workload."""
     N = pipe.N
     F = torch.empty_like(pipe.F)
@@ -658,7 +670,7 @@ def stage_rooflines(api, torch, ctx, pipe, flush, stream, peaks):
                                                                                           tol=1e-12)), stream))
         iters = box[0]
     ms_e = statistics.median(t_enf)
-    gbs = 16.0 * N * (N + 1) * iters / (ms_e * 1e-3) / 1e9
+    gbs = enforce_bytes(N, iters) / (ms_e * 1e-3) / 1e9
     hbm = float(peaks.get("hbm_gbs", 6800.0))
     t_ref, sweeps = [], 0
     for _ in range(3):
@@ -690,7 +702,8 @@ def stage_rooflines(api, torch, ctx, pipe, flush, stream, peaks):
         "enforce_iterative": {"kernel": "enforce_persistent", "bound": "hbm", "achieved": round(gbs, 1),
                               "peak": hbm, "unit": "GB/s", "frac": round(gbs / hbm, 4), "iterations": iters,
                               "ms": round(ms_e, 4),
-                              "note": f"{16 * N * (N + 1) / 1e6:.1f} MB per iteration, L2-resident at N={N}"},
+                              "note": f"{enforce_bytes(N, iters) / max(iters, 1) / 1e6:.1f} MB per iteration on "
+                                      f"average, L2-resident at N={N}"},
         "gebhart": {"kernel": "gemm_kernel (tcgen05) + helpers", "bound": "tensor", "achieved": round(tf, 3),
                     "peak": bf, "unit": "TFLOP/s", "frac": round(tf / bf, 5), "sweeps": sweeps, "ms": round(ms_r, 4),
                     "note": f"N={N}: launch- and latency-bound ({SOLVE_PRECISION} peak = bf16 peak)"},
@@ -981,8 +994,8 @@ def solve_scaling(args):
         F = api.counts_to_F(ctx, api.trace(ctx, mesh, w["rays"], w["seed"]), rays)
         areas = torch.as_tensor(mesh.face_areas(), device=dev)
         n = F.shape[0]
-        # the iterative enforcer on this F: HBM bound above N = 2,048 (16 B per entry and
-        # iteration: eta read and written once), L2 sized below
+        # the iterative enforcer on this F: HBM bound above N = 2,048 (16 B per entry in the
+        # first iteration, per stored entry of the upper triangle after it), L2 sized below
         F0 = F.clone()
         t_e, iters = [], 0
         for _ in range(4):
@@ -994,7 +1007,7 @@ def solve_scaling(args):
             t_e.append(t)
             iters = box["it"]
         ms_e = statistics.median(t_e[1:])
-        gbs = 16.0 * n * (n + 1) * iters / (ms_e * 1e-3) / 1e9
+        gbs = enforce_bytes(n, iters) / (ms_e * 1e-3) / 1e9
         hbm = float(peaks.get("hbm_gbs", 6800.0))
         # the weighted enforcer (fractional-variance kappa, Eq. 3.23-3.25): kappa once, then
         # the iterations with per-pair weights (24 B per entry per iteration)
@@ -1013,9 +1026,8 @@ def solve_scaling(args):
         out["enforce"].append({"workload": name, "n": n, "iterations": iters, "ms": round(ms_e, 3),
                                "ms_per_iteration": round(ms_e / iters, 4), "achieved_gbs": round(gbs, 1),
                                "peak_gbs": hbm, "frac": round(gbs / hbm, 4),
-                               "bytes_per_iteration": 16 * n * (n + 1),
-                               "bound": "fp64 pipe (6 fp64 operations per pair of entries); frac is of the HBM copy "
-                                        "peak, which this GPU's fp64 rate keeps out of reach",
+                               "bytes_per_iteration": round(enforce_bytes(n, iters) / max(iters, 1)),
+                               "bound": "hbm (whole call: also F -> eta and back, 28 B per entry once)",
                                "weighted": {"kappa": "fractional variance", "iterations": iters_k,
                                             "ms": round(ms_k, 3), "ms_per_iteration": round(ms_k / iters_k, 4)}})
         del F0

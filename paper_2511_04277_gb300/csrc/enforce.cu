@@ -1,19 +1,23 @@
 // F from counts (Eq. 3.15), the iterative closure + reciprocity enforcer (Sec. 3.5.5)
-// and the multi-node aggregation (Eq. 5.6-5.7), all fp64.
+// and the multi-node aggregation (Eq. 5.6-5.7), fp64 values.
 //
 // Iterative enforcer layout: the caller's F (N x (N+1), row-major, ld = N+1) is turned
 // into H = Omega_i F_ij in place, and a row scale s (initially 1) is kept beside it, so
-// that the current iterate is eta_ij = s_i H_ij. One iteration is two kernels:
-//   sym_pass  one block per tile pair (I, J), I <= J, of 32 x 32 tiles (64 x 64 for
-//             N > 2,048): loads eta on
-//             both sides of the diagonal, writes H'_ij = kappa_ij eta_ij + (1 - kappa_ij)
-//             eta_ji (kappa = 1/2, or per pair from a kappa matrix), records the largest
-//             |eta_ij - eta_ji|/2 and per-tile row sums;
-//   row_pass  carries the environment column (eta_i,inf = s_i H_i,inf), adds the row
-//             sums, records |r_i - Omega_i| and sets s_i = Omega_i / r_i (Eq. 3.39-3.40
-//             with w = eta); its last block applies the stopping rule.
-// Every entry is read and written once per iteration: 16 bytes of HBM traffic (24 with
-// a kappa matrix).
+// that the current iterate is eta_ij = s_i H_ij. An iteration has two steps:
+//   tiles  per tile pair (I, J), I <= J, of 32 x 32 tiles (64 x 64 for N > 2,048): loads
+//          eta on both sides of the diagonal, writes H'_ij = kappa_ij eta_ij + (1 -
+//          kappa_ij) eta_ji (kappa = 1/2, or per pair from a kappa matrix), records the
+//          largest |eta_ij - eta_ji|/2 and per-tile row sums;
+//   rows   carries the environment column (eta_i,inf = s_i H_i,inf), adds the row sums,
+//          records |r_i - Omega_i| and sets s_i = Omega_i / r_i (Eq. 3.39-3.40 with
+//          w = eta), then applies the stopping rule.
+// On GB300 all iterations run in one cooperative launch (enforce_persistent), and with
+// equal weights every iteration after the first works on the symmetric matrix, reading
+// and writing only the tiles on and above the diagonal (see "symmetric iterations"
+// below). The first iteration reads and writes every entry once: 16 bytes of HBM traffic
+// (24 with a kappa matrix); the symmetric ones 16 bytes per stored entry of the upper
+// triangle. sym_pass and row_pass are the same two steps as separate kernels, for
+// devices without cooperative launches and for the allocation-free entry point.
 #include <cfloat>
 #include <cmath>
 #include <cstring>
@@ -46,11 +50,22 @@ __global__ void to_exchange_kernel(double* __restrict__ H, const double* __restr
   }
 }
 
-__global__ void from_exchange_kernel(double* __restrict__ H, const double* __restrict__ omega,
-                                     const double* __restrict__ s, int32_t n, int64_t total) {
+// q_i = s_i / Omega_i in place of s_i, and the environment column F_i,inf = q_i H_i,inf
+__global__ void row_quotients(double* __restrict__ H, const double* __restrict__ omega, double* __restrict__ s,
+                              int32_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double q = s[i] / omega[i];
+    s[i] = q;
+    H[i * (n + 1) + n] *= q;
+  }
+}
+
+// F = q_i H on the N x N block (one fp64 multiplication per entry: GB300's fp64 divide
+// costs several)
+__global__ void from_exchange_kernel(double* __restrict__ H, const double* __restrict__ q, int32_t n, int64_t total) {
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-    int64_t i = e / (n + 1);
-    H[e] = s[i] * H[e] / omega[i];
+    const int64_t i = e / n;
+    H[i * (n + 1) + e % n] *= q[i];
   }
 }
 
@@ -88,17 +103,28 @@ __device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
 // arrays, which the global writes and the row sums then read; the row sums run over a
 // rotated column order so that the 16 lanes of a half-warp read 16 different banks (the
 // row stride is T + 1 doubles: bank of (r, c) = (r + c) mod 16), in a fixed order that
-// is the same on both paths (kappa = 1/2 given as weights gives the same bits).
+// is the same on both paths (kappa = 1/2 given as weights gives the same bits). A
+// negative symmetrised value raises *neg (when given): the symmetric iterations below
+// need non-negative entries.
+template <int T>
+struct TileSmem {
+  double A[T][T + 1];
+  double B[T][T + 1];
+  double sI[T], sJ[T];  // the tiles' row scales, halved for equal weights
+  unsigned long long red[kThreads / 32];
+};
+
 template <int T, bool kW>
 __device__ __forceinline__ void sym_tile(double* __restrict__ H, const double* __restrict__ s,
                                          const double* __restrict__ kappa, int32_t n, double* __restrict__ P, int I,
-                                         int J, unsigned long long* d_recip) {
+                                         int J, unsigned long long* d_recip, TileSmem<T>& sm, int* neg = nullptr) {
   static_assert(T == 64 || T == 32, "bank rotation for 64- and 32-wide tiles");
   constexpr int kPer = T * T / kThreads;  // entries per thread
-  __shared__ double A[T][T + 1];
-  __shared__ double B[T][T + 1];
-  __shared__ double sI[T], sJ[T];  // the tiles' row scales, halved for equal weights
-  __shared__ unsigned long long red[kThreads / 32];
+  auto& A = sm.A;
+  auto& B = sm.B;
+  auto& sI = sm.sI;
+  auto& sJ = sm.sJ;
+  auto& red = sm.red;
   const int64_t ld = n + 1;
   const int tid = threadIdx.x;
   const bool off = I != J;
@@ -134,12 +160,14 @@ __device__ __forceinline__ void sym_tile(double* __restrict__ H, const double* _
   };
   double v1[kPer], v2[kW ? kPer : 1];
   unsigned long long dmax = 0ull;  // bit pattern of the largest defect (non-negative)
+  bool negative = false;
 #pragma unroll
   for (int k = 0; k < kPer; ++k) {
     const int e = tid + k * kThreads, r = e / T, c = e % T;
     const int64_t i = (int64_t)I * T + r, j = (int64_t)J * T + c;
     const double a = ea(r, c), b = eb(c, r);
     v1[k] = (i < n && j < n) ? pair(a, b, i, j) : 0.0;
+    negative |= v1[k] < 0.0;
     const double d = kW ? 0.5 * fabs(a - b) : fabs(a - b);
     dmax = max(dmax, (unsigned long long)__double_as_longlong(d));
     if constexpr (kW) {
@@ -183,9 +211,10 @@ __device__ __forceinline__ void sym_tile(double* __restrict__ H, const double* _
     acc2 += __shfl_xor_sync(0xffffffffu, acc2, o);
   }
   const int64_t ri = (int64_t)I * T + row, rj = (int64_t)J * T + row;
+  const int nt = (n + T - 1) / T;
   if (part == 0) {
-    if (ri < n) P[(int64_t)J * n + ri] = acc;
-    if (off && rj < n) P[(int64_t)I * n + rj] = acc2;
+    if (ri < n) P[ri * nt + J] = acc;
+    if (off && rj < n) P[rj * nt + I] = acc2;
   }
   for (int o = 16; o > 0; o >>= 1) dmax = max(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
   if ((tid & 31) == 0) red[tid >> 5] = dmax;
@@ -195,7 +224,7 @@ __device__ __forceinline__ void sym_tile(double* __restrict__ H, const double* _
     for (int w = 1; w < kThreads / 32; ++w) m = max(m, red[w]);
     atomicMax(d_recip, m);
   }
-  __syncthreads();  // the tiles are reused by the block's next pair
+  if (__syncthreads_or(negative) && neg && tid == 0) atomicExch(neg, 1);  // also: the tiles are reused next
 }
 
 template <int T, bool kW>
@@ -205,7 +234,8 @@ __global__ void __launch_bounds__(kThreads, 3) sym_pass(double* __restrict__ H, 
   if (st->done) return;
   const int I = blockIdx.y, J = blockIdx.x;
   if (I > J) return;
-  sym_tile<T, kW>(H, s, kappa, n, P, I, J, &st->d_recip);
+  __shared__ TileSmem<T> sm;
+  sym_tile<T, kW>(H, s, kappa, n, P, I, J, &st->d_recip, sm);
 }
 
 // ---------------------------------------------------------------- persistent enforcer
@@ -217,10 +247,14 @@ __global__ void __launch_bounds__(kThreads, 3) sym_pass(double* __restrict__ H, 
 // rows in every iteration; what crosses blocks (row scales, per-tile row sums) is read
 // through L2 (__ldcg), never from a block's L1.
 struct PersistState {
-  unsigned long long d_recip[2], d_close[2];
+  unsigned long long d_recip[2], d_close[2], smax[2];
+  unsigned int d_recip_f[2];
   int32_t bad[2];
   unsigned int arrive, gen;
-  int32_t done, iters, timeout, pad;
+  int32_t done, iters, timeout;
+  int32_t neg;    // a negative entry or non-positive row scale: every iteration on the full path
+  int32_t sym;    // symmetric iterations ran: the tiles below the diagonal are stale
+  int32_t range;  // a fixed-point row-sum term outside its bound (not expected)
 };
 
 constexpr unsigned long long kBarrierNs = 2000000000ull;  // a barrier wait gives up after 2 s
@@ -261,58 +295,350 @@ __device__ bool grid_barrier(PersistState* st, int* s_ok, unsigned long long lim
   return *s_ok != 0;
 }
 
+// ---------------------------------------------------------------- symmetric iterations
+// With equal weights the first iteration leaves the N x N block of H symmetric bit for
+// bit (v_ij = e_ij + e_ji = v_ji), and it stays so: the next iterate is e_ij + e_ji with
+// e_ij = h_i v_ij, that is (h_i + h_j) v_ij with h = s / 2. So from the second iteration
+// on the blocks read and write only the tiles on and above the diagonal (8 bytes of HBM
+// traffic per entry instead of 16), at one fp64 addition and one fp64 multiplication per
+// stored entry. GB300 issues fp64 at about two lanes per clock per SM, so the row sums,
+// which would cost two more fp64 additions per stored entry, are accumulated in 64-bit
+// fixed point: the term of row i is v' 2^-U_i truncated to an integer, U_i = e_H + e_R,i
+// - 61, where 2^e_H bounds max_j h_j and 2^e_R,i bounds the row's previous sum with its
+// slack. Then sum_j v'_ij <= (h_i + h_max) R_i < 2^(U_i + 62): no term or sum reaches
+// 2^63, the integer sum is exact, and each term is short of v' 2^-U_i by less than one
+// unit, 2^-62 of the row's bound (subnormal terms count as zero). The reciprocity defect
+// |eta_ij - eta_ji| / 2 = |h_i - h_j| v_ij only matters to the stop rule in an iteration
+// whose closure defect is already within the tolerance; only then a separate pass takes
+// it, in fp32, as |h_i - h_j| v'_ij / (h_i + h_j) from the fp32 (hi, lo) splits of the
+// iteration's h and a truncated fp32 copy of v' scaled by 2^-e_Omega (e_Omega: the
+// exponent of max Omega), so the stop decisions are those of a defect taken every
+// iteration. The entries must be non-negative: a negative value after the first
+// iteration (or a non-positive row scale) keeps every iteration on the full path.
+
+// e with x < 2^e, for a finite x >= 0 (2^-1022 bounds zero and the subnormals)
+__device__ __forceinline__ int bound_exp(double x) {
+  const int e = (int)((unsigned long long)__double_as_longlong(x) >> 52) & 0x7FF;
+  return e ? e - 1022 : -1022;
+}
+
+// x >> s with the shift count clamped to 64 (PTX shr semantics: the result is 0 for s >= 64)
+__device__ __forceinline__ unsigned long long shr_clamped(unsigned long long x, unsigned s) {
+  unsigned long long r;
+  asm("shr.b64 %0, %1, %2;" : "=l"(r) : "l"(x), "r"(s));
+  return r;
+}
+
+// v 2^-eoff as a truncated fp32 (0 below the fp32 normal range), v >= 0 finite
+__device__ __forceinline__ float scaled_f32(unsigned long long b, int eoff) {
+  const int e = (int)(b >> 52) - 896 - eoff;
+  if (e <= 0) return 0.0f;
+  return __uint_as_float(((unsigned)min(e, 254) << 23) | (unsigned)((b >> 29) & 0x7FFFFFu));
+}
+
+// RN(h_i + h_j) from the fixed-point values X = h 2^54, exact integers for h in [1/4, 1):
+// the exact sum C lies in [2^53, 2^55) and is rounded to 53 bits, ties to even, so the
+// result has the bits of the fp64 addition while GB300's fp64 pipe stays free.
+__device__ __forceinline__ double fixed_sum_rn(unsigned long long Xi, unsigned long long Xj) {
+  const unsigned long long C = Xi + Xj;
+  const unsigned k = 1u + (unsigned)(C >> 54);  // bits below the 53-bit significand
+  const unsigned long long q = (C + (k - 1u) + ((C >> k) & 1ull)) >> k;
+  return __longlong_as_double((long long)(((unsigned long long)(1021u + k) << 52) + q - (1ull << 52)));
+}
+
+// Per-row data of the tile pair a block works on: h = s / 2, its fixed-point form h 2^54
+// (fixed_sum_rn) and K = 1086 + U (the shift of a term is K minus the biased exponent of
+// v'); the fp32 splits of h for the defect pass; column partial sums of the tile.
+template <int T>
+struct SymMeta {
+  double hI[T], hJ[T];
+  unsigned long long xI[T], xJ[T];
+  int KI[T], KJ[T];
+  float2 pI[T], pJ[T];
+  unsigned long long colred[kThreads];
+};
+
+// Tile (I, J) of H into X by asynchronous 8-byte copies (zeros outside the matrix).
+template <int T>
+__device__ __forceinline__ void load_tile(const double* __restrict__ H, int32_t n, int I, int J, double (*X)[T + 1]) {
+  const int64_t ld = n + 1;
+  for (int e = threadIdx.x; e < T * T; e += kThreads) {
+    const int r = e / T, c = e % T;
+    const int64_t i = (int64_t)I * T + r, j = (int64_t)J * T + c;
+    if (i < n && j < n) cp_async8(&X[r][c], H + i * ld + j);
+    else X[r][c] = 0.0;
+  }
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+// h, h 2^54 and K of the tile pair's rows (I) and columns (J); rows outside the matrix
+// get h = 1/4 and a shift that clears every term. False when some h of the tile lies
+// outside [1/4, 1), where h 2^54 is not an integer of the fixed-point sum (a per-thread
+// answer: the caller combines them at its barrier).
+template <int T>
+__device__ __forceinline__ bool load_meta(const double* __restrict__ s, const int* __restrict__ eR, int eH,
+                                          int32_t n, int I, int J, SymMeta<T>& m) {
+  const int t = threadIdx.x;
+  bool ok = true;
+  if (t < 2 * T) {
+    const bool col = t >= T;
+    const int q = t & (T - 1);
+    const int64_t i = (int64_t)(col ? J : I) * T + q;
+    double h = 0.25;
+    int K = 4096;
+    if (i < n) {  // written by other blocks' row steps: read through L2
+      h = 0.5 * __ldcg(s + i);
+      K = 1086 + eH + __ldcg(eR + i) - 61;
+    }
+    const unsigned long long b = (unsigned long long)__double_as_longlong(h);
+    const int e = (int)(b >> 52);
+    ok = e == 1021 || e == 1022;
+    (col ? m.hJ : m.hI)[q] = h;
+    (col ? m.xJ : m.xI)[q] = ok ? ((b & 0xFFFFFFFFFFFFFull) | 0x10000000000000ull) << (e - 1021) : 0ull;
+    (col ? m.KJ : m.KI)[q] = K;
+  }
+  return ok;
+}
+
+// One symmetric iteration on the tile (I, J), I <= J, held in X: v' = (h_i + h_j) v is
+// written to H; the fixed-point row sums go to P[rows of I][J] and (off the diagonal)
+// P[rows of J][I]. emax collects the largest biased exponent of v' (2047: not finite),
+// smin the smallest term shift (below 1: a bound violated). The diagonal tile is
+// processed whole (both of its triangles).
+template <int T, bool kFix>
+__device__ __forceinline__ void sym_tile_fast(double* __restrict__ H, int32_t n, unsigned long long* __restrict__ P,
+                                              int I, int J, double (*X)[T + 1], SymMeta<T>& m, unsigned& emax,
+                                              int& smin) {
+  constexpr int kPer = T * T / kThreads, kStep = kThreads / T;
+  const int tid = threadIdx.x, c = tid % T, r0 = tid / T;
+  const bool off = I != J;
+  const bool inner = (int64_t)(I + 1) * T <= n && (int64_t)(J + 1) * T <= n;
+  const int64_t ld = n + 1;
+  const int64_t j = (int64_t)J * T + c;
+  const double hc = m.hJ[c];
+  const unsigned long long xc = m.xJ[c];
+  const int Kc = m.KJ[c];
+  double* hrow = H + ((int64_t)I * T + r0) * ld + j;
+  unsigned long long colacc = 0;
+#pragma unroll 4
+  for (int k = 0; k < kPer; ++k) {
+    const int r = r0 + k * kStep;
+    const double cij = kFix ? fixed_sum_rn(m.xI[r], xc) : __dadd_rn(m.hI[r], hc);
+    const double w = __dmul_rn(cij, X[r][c]);
+    if (inner || ((int64_t)I * T + r < n && j < n)) hrow[(int64_t)k * kStep * ld] = w;
+    const unsigned hi = (unsigned)__double2hiint(w), lo = (unsigned)__double2loint(w);
+    const int e = (int)(hi >> 20);  // the sign bit (never set here) would make it >= 2048
+    emax = max(emax, (unsigned)e);
+    // the 53-bit significand moved to the top of 64 bits
+    const unsigned long long M = ((unsigned long long)(__funnelshift_l(lo, hi, 11) | 0x80000000u) << 32) | (lo << 11);
+    const int ee = e ? e : -4096;  // zero and subnormal: shifted out entirely
+    const int sr = m.KI[r] - ee, sc = Kc - ee;
+    smin = min(smin, min(sr, sc));
+    if (off) colacc += shr_clamped(M, (unsigned)sc);
+    X[r][c] = __longlong_as_double((long long)shr_clamped(M, (unsigned)sr));  // only this thread reads the slot
+  }
+  __syncthreads();
+  // row sums over the rotated column order of sym_tile (16 distinct banks per half-warp)
+  constexpr int kTpr = kThreads / T, kCpt = T / kTpr;
+  const int row = tid / kTpr, part = tid % kTpr;
+  const int rot = T == 64 ? 4 * part : 2 * (part >> 2);
+  unsigned long long acc = 0;
+  for (int it = 0; it < kCpt; ++it)
+    acc += (unsigned long long)__double_as_longlong(X[row][part * kCpt + ((it + rot) & (kCpt - 1))]);
+#pragma unroll
+  for (int o = 1; o < kTpr; o <<= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  const int64_t ri = (int64_t)I * T + row;
+  const int nt = (n + T - 1) / T;
+  if (part == 0 && ri < n) P[ri * nt + J] = acc;
+  if (off) {
+    m.colred[tid] = colacc;
+    __syncthreads();
+    if (tid < T && j < n) {
+      unsigned long long t = 0;
+      for (int q = 0; q < kStep; ++q) t += m.colred[tid + q * T];
+      P[j * nt + I] = t;
+    }
+  }
+  __syncthreads();  // X and the row data are reused by the next pair
+}
+
+// Largest |h_i - h_j| v_ij = |h_i - h_j| v'_ij / (h_i + h_j) over the tile (I, J) in X
+// (fp32 bits of a non-negative value), from the fp32 splits of the iteration's h.
+template <int T>
+__device__ __forceinline__ unsigned tile_defect(int32_t n, int I, int J, double (*X)[T + 1], const SymMeta<T>& m,
+                                                int eoff) {
+  unsigned dmax = 0u;
+  for (int e = threadIdx.x; e < T * T; e += kThreads) {
+    const int r = e / T, c = e % T;
+    if ((int64_t)I * T + r >= n || (int64_t)J * T + c >= n) continue;
+    const float2 a = m.pI[r], b = m.pJ[c];
+    const float d = fabsf((a.x - b.x) + (a.y - b.y)) *
+                    __fdividef(scaled_f32((unsigned long long)__double_as_longlong(X[r][c]), eoff), a.x + b.x);
+    dmax = max(dmax, __float_as_uint(d));
+  }
+  return dmax;
+}
+
+// Walks the tile pairs p, p + stride, ... (numbered row by row over I <= J) without
+// recounting from the first row at every step.
+struct PairWalker {
+  int I, q, nt;
+  __device__ PairWalker(int p, int n_tiles) : I(0), q(p), nt(n_tiles) { settle(); }
+  __device__ void settle() {
+    while (I < nt && q >= nt - I) {
+      q -= nt - I;
+      ++I;
+    }
+  }
+  __device__ void advance(int stride) {
+    q += stride;
+    settle();
+  }
+  __device__ bool valid() const { return I < nt; }
+  __device__ int J() const { return I + q; }
+};
+
+// fp32 (hi, lo) split of h: h - hi is exact in fp64, lo its rounding
+__device__ __forceinline__ float2 split_f32(double h) {
+  const float hi = __double2float_rn(h);
+  return make_float2(hi, __double2float_rn(h - (double)hi));
+}
+
+// hp holds two buffers of N splits: the row step of iteration k writes buffer k & 1, the
+// next tile step reads the same h through s, and the defect pass of iteration k reads
+// buffer (k - 1) & 1 (the h its tile step used).
 template <int T, bool kW>
 __global__ void __launch_bounds__(kThreads, 3) enforce_persistent(double* __restrict__ H, double* __restrict__ s,
+                                                               float2* __restrict__ hp, int* __restrict__ eR,
                                                                const double* __restrict__ kappa,
                                                                const double* __restrict__ omega, int32_t n,
                                                                int32_t n_tiles, double* __restrict__ P,
-                                                               PersistState* st, double tol_abs, int32_t maxit) {
+                                                               PersistState* st, double tol_abs, int32_t maxit,
+                                                               int eoff) {
+  __shared__ TileSmem<T> sm;
+  __shared__ SymMeta<T> meta;
   __shared__ double red[kThreads];
   __shared__ int s_ok;
-  const int n_pairs = n_tiles * (n_tiles + 1) / 2;
   const int64_t ld = n + 1;
+  unsigned long long* Pu = reinterpret_cast<unsigned long long*>(P);
+  bool fast = false;  // the symmetric iterations (decided after the first, the same in every block)
+  int eH = 0;
   for (int k = 0;; ++k) {
     const int par = k & 1;
     // (1) reciprocity on the tile pairs (I, J), I <= J, numbered row by row
-    for (int p = blockIdx.x; p < n_pairs; p += gridDim.x) {
-      int I = 0, q = p;
-      while (q >= n_tiles - I) {
-        q -= n_tiles - I;
-        ++I;
+    if (!fast) {
+      for (PairWalker w(blockIdx.x, n_tiles); w.valid(); w.advance(gridDim.x))
+        sym_tile<T, kW>(H, s, kappa, n, P, w.I, w.J(), &st->d_recip[par], sm, k == 0 ? &st->neg : nullptr);
+    } else if constexpr (!kW) {
+      unsigned emax = 0u;
+      int smin = 64;
+      PairWalker w(blockIdx.x, n_tiles);
+      if (w.valid()) load_tile<T>(H, n, w.I, w.J(), sm.A);
+      for (int cur = 0; w.valid(); cur ^= 1) {
+        const int I = w.I, J = w.J();
+        w.advance(gridDim.x);
+        if (w.valid()) {  // prefetch the next pair's tile into the other buffer
+          load_tile<T>(H, n, w.I, w.J(), cur ? sm.A : sm.B);
+          asm volatile("cp.async.wait_group 1;" ::: "memory");
+        } else {
+          asm volatile("cp.async.wait_group 0;" ::: "memory");
+        }
+        const bool fixed = !__syncthreads_or(!load_meta<T>(s, eR, eH, n, I, J, meta));
+        if (fixed) sym_tile_fast<T, true>(H, n, Pu, I, J, cur ? sm.B : sm.A, meta, emax, smin);
+        else sym_tile_fast<T, false>(H, n, Pu, I, J, cur ? sm.B : sm.A, meta, emax, smin);
       }
-      sym_tile<T, kW>(H, s, kappa, n, P, I, I + q, &st->d_recip[par]);
+      if (__syncthreads_or(emax >= 2047u) && threadIdx.x == 0) atomicExch(&st->bad[par], 1);
+      if (__syncthreads_or(smin < 1) && threadIdx.x == 0) atomicExch(&st->range, 1);
     }
     if (!grid_barrier(st, &s_ok)) return;
     if (blockIdx.x == 0 && threadIdx.x == 0) {  // last read before the barrier just passed
       st->d_recip[par ^ 1] = 0ull;
       st->d_close[par ^ 1] = 0ull;
+      st->smax[par ^ 1] = 0ull;
+      st->d_recip_f[par ^ 1] = 0u;
       st->bad[par ^ 1] = 0;
     }
-    // (2) environment column carried over, closure by row scaling
+    // (2) environment column carried over, closure by row scaling: one warp per row, its
+    // lanes adding the row's per-tile partial sums (contiguous: P[row][tile])
     double dc = 0.0;
-    bool bad = false;
-    for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kThreads) {
-      const double env = s[i] * H[i * ld + n];
-      H[i * ld + n] = env;
-      double r = 0.0;
-      for (int J = 0; J < n_tiles; ++J) r += __ldcg(P + (int64_t)J * n + i);  // written by other blocks
-      r += env;
-      dc = fmax(dc, fabs(r - omega[i]));
-      s[i] = (r > 0.0) ? omega[i] / r : 1.0;
-      bad |= !isfinite(r);
+    unsigned long long smax = 0ull;
+    bool bad = false, nonpos = false;
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = (int64_t)gridDim.x * (kThreads / 32);
+    for (int64_t i = (blockIdx.x * (int64_t)kThreads + threadIdx.x) >> 5; i < n; i += nwarps) {
+      double R = 0.0, slack = 0.0;
+      if (!fast) {
+        for (int J = lane; J < n_tiles; J += 32) R += __ldcg(P + i * n_tiles + J);  // written by other blocks
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) R += __shfl_xor_sync(0xffffffffu, R, o);
+      } else {
+        unsigned long long t = 0;
+        for (int J = lane; J < n_tiles; J += 32) t += __ldcg(Pu + i * n_tiles + J);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        const int U = eH + eR[i] - 61;  // the unit the tile step used for this row
+        R = ldexp((double)t, U);
+        slack = (double)n * (ldexp(1.0, U) + 0x1p-1022);  // truncation: under a unit per term
+      }
+      __syncwarp();  // every lane has read eR[i] before lane 0 rewrites it
+      if (lane == 0) {
+        const double env = s[i] * H[i * ld + n];
+        H[i * ld + n] = env;
+        const double r = R + env;
+        dc = fmax(dc, fabs(r - omega[i]));
+        const double sn = (r > 0.0) ? omega[i] / r : 1.0;
+        s[i] = sn;
+        if constexpr (!kW) {
+          hp[(int64_t)par * n + i] = split_f32(0.5 * sn);
+          eR[i] = bound_exp(R * (1.0 + 0x1p-30) + slack);
+          smax = max(smax, (unsigned long long)__double_as_longlong(sn));
+          nonpos |= !(sn > 0.0);
+        }
+        bad |= !isfinite(r);
+      }
     }
     red[threadIdx.x] = dc;
     if (__syncthreads_or(bad) && threadIdx.x == 0) atomicExch(&st->bad[par], 1);
+    if (__syncthreads_or(nonpos) && threadIdx.x == 0) atomicExch(&st->neg, 1);
     for (int w = kThreads / 2; w > 0; w >>= 1) {
       if (threadIdx.x < w) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + w]);
       __syncthreads();
     }
     if (threadIdx.x == 0) atomicMax(&st->d_close[par], (unsigned long long)__double_as_longlong(red[0]));
+    for (int o = 16; o > 0; o >>= 1) smax = max(smax, __shfl_xor_sync(0xffffffffu, smax, o));
+    if ((threadIdx.x & 31) == 0 && smax) atomicMax(&st->smax[par], smax);
     if (!grid_barrier(st, &s_ok)) return;
-    // (3) stop rule on this iteration's defects
+    // (3) stop rule on this iteration's defects; on the symmetric path the reciprocity
+    // defect is taken only when the closure defect already meets the tolerance
     volatile PersistState* v = st;
-    const double dr = __longlong_as_double((long long)v->d_recip[par]);
     const double dcl = __longlong_as_double((long long)v->d_close[par]);
+    double dr = __longlong_as_double((long long)v->d_recip[par]);
+    if constexpr (!kW) {
+      if (fast) {
+        dr = INFINITY;
+        if (!v->bad[par] && dcl <= tol_abs) {
+          unsigned dmax = 0u;
+          for (PairWalker w(blockIdx.x, n_tiles); w.valid(); w.advance(gridDim.x)) {
+            const int I = w.I, J = w.J();
+            load_tile<T>(H, n, I, J, sm.A);
+            if (threadIdx.x < 2 * T) {
+              const int q = threadIdx.x & (T - 1);
+              const int64_t i = (int64_t)(threadIdx.x < T ? I : J) * T + q;
+              (threadIdx.x < T ? meta.pI : meta.pJ)[q] =
+                  i < n ? __ldcg(hp + (int64_t)(par ^ 1) * n + i) : make_float2(0.0f, 0.0f);
+            }
+            asm volatile("cp.async.wait_group 0;" ::: "memory");
+            __syncthreads();
+            dmax = max(dmax, tile_defect<T>(n, I, J, sm.A, meta, eoff));
+            __syncthreads();
+          }
+          for (int o = 16; o > 0; o >>= 1) dmax = max(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+          if ((threadIdx.x & 31) == 0 && dmax) atomicMax(&st->d_recip_f[par], dmax);
+          if (!grid_barrier(st, &s_ok)) return;
+          dr = ldexp((double)__uint_as_float(v->d_recip_f[par]), eoff);
+        }
+      }
+    }
     const int done = v->bad[par] ? 3 : (fmax(dr, dcl) <= tol_abs ? 1 : (k + 1 >= maxit ? 2 : 0));
     if (done) {
       if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -321,6 +647,46 @@ __global__ void __launch_bounds__(kThreads, 3) enforce_persistent(double* __rest
       }
       return;
     }
+    if (k == 0 && !kW && !v->neg) {
+      fast = true;
+      if (blockIdx.x == 0 && threadIdx.x == 0) st->sym = 1;
+    }
+    if (fast) eH = bound_exp(0.5 * __longlong_as_double((long long)v->smax[par]));
+  }
+}
+
+// F = q_i H from the tiles on and above the diagonal after symmetric iterations (the
+// tiles below it are stale): one block per tile pair, the tile (J, I) written as the
+// transpose of (I, J) through shared memory. q_i = s_i / Omega_i (row_quotients).
+template <int T>
+__global__ void __launch_bounds__(kThreads) from_exchange_sym(double* __restrict__ H, const double* __restrict__ q,
+                                                              int32_t n, int32_t n_tiles) {
+  __shared__ double X[T][T + 1];
+  __shared__ double qI[T], qJ[T];
+  const int64_t ld = n + 1;
+  for (PairWalker w(blockIdx.x, n_tiles); w.valid(); w.advance(gridDim.x)) {
+    const int I = w.I, J = w.J();
+    load_tile<T>(H, n, I, J, X);
+    if (threadIdx.x < 2 * T) {
+      const int t = threadIdx.x & (T - 1);
+      const int64_t i = (int64_t)(threadIdx.x < T ? I : J) * T + t;
+      (threadIdx.x < T ? qI : qJ)[t] = i < n ? q[i] : 0.0;
+    }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    __syncthreads();
+    for (int e = threadIdx.x; e < T * T; e += kThreads) {
+      const int r = e / T, c = e % T;
+      const int64_t i = (int64_t)I * T + r, j = (int64_t)J * T + c;
+      if (i < n && j < n) H[i * ld + j] = qI[r] * X[r][c];
+    }
+    if (I != J) {
+      for (int e = threadIdx.x; e < T * T; e += kThreads) {
+        const int r = e / T, c = e % T;
+        const int64_t i = (int64_t)J * T + r, j = (int64_t)I * T + c;
+        if (i < n && j < n) H[i * ld + j] = qJ[r] * X[c][r];
+      }
+    }
+    __syncthreads();
   }
 }
 
@@ -390,7 +756,7 @@ __global__ void __launch_bounds__(kThreads) row_pass(double* __restrict__ H, dou
     double env = s[i] * H[i * ld + n];
     H[i * ld + n] = env;
     double r = 0.0;
-    for (int J = 0; J < n_tiles; ++J) r += P[(int64_t)J * n + i];
+    for (int J = 0; J < n_tiles; ++J) r += P[i * n_tiles + J];
     r += env;
     dc = fabs(r - omega[i]);
     s[i] = (r > 0.0) ? omega[i] / r : 1.0;
@@ -518,6 +884,8 @@ rg_status enforce_iterative(rg_ctx* ctx, int32_t n, const double* omega_d, const
   sz.take<double>((size_t)n_tiles * n);        // P
   sz.take<EnforceState>(1);
   sz.take<PersistState>(1);
+  sz.take<float2>(2 * (size_t)n);              // fp32 splits of s / 2, two iterations
+  sz.take<int>(n);                             // row-sum bound exponents
   void* ws = nullptr;
   rg_status rs = rg::workspace(ctx, sz.off, &ws);
   if (rs != RG_OK) return rs;
@@ -526,6 +894,8 @@ rg_status enforce_iterative(rg_ctx* ctx, int32_t n, const double* omega_d, const
   double* P = cv.take<double>((size_t)n_tiles * n);
   EnforceState* st = cv.take<EnforceState>(1);
   PersistState* pst = cv.take<PersistState>(1);
+  float2* hsplit = cv.take<float2>(2 * (size_t)n);
+  int* eR = cv.take<int>(n);
   const int64_t total = (int64_t)n * (n + 1);
   RG_CUDA_TRY(ctx, cudaMemsetAsync(st, 0, sizeof(EnforceState), s));
   // tolerance scale: max Omega
@@ -539,16 +909,18 @@ rg_status enforce_iterative(rg_ctx* ctx, int32_t n, const double* omega_d, const
   double om_max;
   memcpy(&om_max, ctx->h_scratch, 8);
   const double tol_abs = tol * om_max;
+  const int eoff = (om_max > 0.0 && std::isfinite(om_max)) ? std::ilogb(om_max) : 0;
   dim3 sym_grid(n_tiles, n_tiles);
   const int row_blocks = (n + kThreads - 1) / kThreads;
   EnforceState h{};
   // one cooperative launch for all iterations (the two-kernel loop below is the same
   // computation, kept for devices without cooperative launches)
   int coop = 0;
+  bool sym = false;
   RG_CUDA_TRY(ctx, cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, ctx->device));
   if (coop) {
-    void (*kern)(double*, double*, const double*, const double*, int32_t, int32_t, double*, PersistState*, double,
-                 int32_t);
+    void (*kern)(double*, double*, float2*, int*, const double*, const double*, int32_t, int32_t, double*,
+                 PersistState*, double, int32_t, int);
     if (tile == kTSmall) kern = kappa_d ? enforce_persistent<kTSmall, true> : enforce_persistent<kTSmall, false>;
     else kern = kappa_d ? enforce_persistent<kT, true> : enforce_persistent<kT, false>;
     int per_sm = 0;
@@ -557,11 +929,12 @@ rg_status enforce_iterative(rg_ctx* ctx, int32_t n, const double* omega_d, const
     const int grid = std::max(1, std::min(n_pairs, per_sm * ctx->sm_count));
     RG_CUDA_TRY(ctx, cudaMemsetAsync(pst, 0, sizeof(PersistState), s));
     int32_t nn = n, nt = n_tiles, mi = maxit;
+    int eo = eoff;
     double ta = tol_abs;
     double* Fp = F_d;
     const double* kp = kappa_d;
     const double* op = omega_d;
-    void* args[] = {&Fp, &sc, &kp, &op, &nn, &nt, &P, &pst, &ta, &mi};
+    void* args[] = {&Fp, &sc, &hsplit, &eR, &kp, &op, &nn, &nt, &P, &pst, &ta, &mi, &eo};
     const int tok = rg::timer_begin(ctx, rg::kTimeEnforce, s);
     RG_CUDA_TRY(ctx, cudaLaunchCooperativeKernel((const void*)kern, dim3(grid), dim3(kThreads), args, 0, s));
     rg::timer_end(ctx, tok, s);
@@ -570,8 +943,11 @@ rg_status enforce_iterative(rg_ctx* ctx, int32_t n, const double* omega_d, const
     RG_CUDA_TRY(ctx, cudaMemcpyAsync(&hp, pst, sizeof(PersistState), cudaMemcpyDeviceToHost, s));
     RG_CUDA_TRY(ctx, cudaStreamSynchronize(s));
     if (hp.timeout) return rg::fail(ctx, RG_ERR_CUDA, "rg_enforce_iterative: a grid barrier timed out");
+    if (hp.range)
+      return rg::fail(ctx, RG_ERR_NUMERIC, "rg_enforce_iterative: a fixed-point row-sum term left its bound");
     h.done = hp.done;
     h.iters = hp.iters;
+    sym = hp.sym != 0;
   }
   for (int launched = 0; !coop && launched < maxit;) {
     int batch = std::min(8, maxit - launched);
@@ -593,7 +969,16 @@ rg_status enforce_iterative(rg_ctx* ctx, int32_t n, const double* omega_d, const
     RG_CUDA_TRY(ctx, cudaStreamSynchronize(s));
     if (h.done) break;
   }
-  from_exchange_kernel<<<blocks_for(total, ctx->sm_count), kThreads, 0, s>>>(F_d, omega_d, sc, n, total);
+  row_quotients<<<blocks_for(n, ctx->sm_count), kThreads, 0, s>>>(F_d, omega_d, sc, n);
+  ++ctx->launches;
+  if (sym) {
+    const int n_pairs = n_tiles * (n_tiles + 1) / 2;
+    const int grid = std::min(n_pairs, 4 * ctx->sm_count);
+    if (tile == kTSmall) from_exchange_sym<kTSmall><<<grid, kThreads, 0, s>>>(F_d, sc, n, n_tiles);
+    else from_exchange_sym<kT><<<grid, kThreads, 0, s>>>(F_d, sc, n, n_tiles);
+  } else {
+    from_exchange_kernel<<<blocks_for((int64_t)n * n, ctx->sm_count), kThreads, 0, s>>>(F_d, sc, n, (int64_t)n * n);
+  }
   ++ctx->launches;
   RG_CUDA_TRY(ctx, cudaGetLastError());
   if (iters_out_h) *iters_out_h = h.iters;
@@ -706,7 +1091,7 @@ constexpr size_t kNoallocScaleBytes = (size_t)kNoallocMaxN * sizeof(double);
 constexpr size_t kNoallocRowSumBytes = (size_t)kNoallocMaxTiles * kNoallocMaxN * sizeof(double);
 constexpr size_t kNoallocBytes = kNoallocScaleBytes + kNoallocRowSumBytes + 256 + 256;
 
-// Layout: [row scales s: N doubles][per-tile row sums: tiles x N doubles]
+// Layout: [row scales s: N doubles][per-tile row sums: N x tiles doubles]
 //         [EnforceState, 256 B][tolerance scale max|Omega|, 256 B]
 static __device__ __align__(256) unsigned char g_enforce_scratch[kNoallocBytes];
 
@@ -768,7 +1153,8 @@ extern "C" rg_status rg_enforce_iterative_noalloc(int32_t n, const double* omega
       return RG_ERR_CUDA;
     if (h.done) break;
   }
-  from_exchange_kernel<<<blocks_for(total, sm), kThreads, 0, s>>>(F_d, omega_d, sc, n, total);
+  row_quotients<<<blocks_for(n, sm), kThreads, 0, s>>>(F_d, omega_d, sc, n);
+  from_exchange_kernel<<<blocks_for((int64_t)n * n, sm), kThreads, 0, s>>>(F_d, sc, n, (int64_t)n * n);
   if (cudaGetLastError() != cudaSuccess) return RG_ERR_CUDA;
   if (iters_out_h) *iters_out_h = h.iters;
   if (h.done == 3) return RG_ERR_NUMERIC;
