@@ -449,8 +449,11 @@ def kernel_rooflines(api, ctx, pipe, steps, step_ms, peaks, trace_roof):
         else:
             it = getattr(pipe, "iters", 0)
             gb = enforce_bytes(pipe.N, it) / (per_launch * 1e-3) / 1e9
+            # DRAM bytes per algorithmic byte from the committed capture at N = 6,144
+            traffic = profiled_traffic("enforce_persistent_n6144.md", "enforce.cu", enforce_bytes(pipe.N, it))
             row.update({"kernel": "enforce_persistent", "bound": "hbm", "achieved": round(gb, 1), "peak": hbm,
-                        "unit": "GB/s", "frac": round(gb / hbm, 4), "traffic": None,
+                        "unit": "GB/s", "frac": round(gb / hbm, 4),
+                        "traffic": None if traffic is None else round(traffic),
                         "note": f"{it} iterations per launch: the first reads and writes every entry (16 B), the "
                                 "symmetric ones after it the tiles on and above the diagonal (16 B per stored "
                                 "entry, one fp64 add and multiply each, fixed-point row sums)"})
