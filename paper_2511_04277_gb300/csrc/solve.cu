@@ -574,6 +574,148 @@ __global__ void __launch_bounds__(256, 3) finish_residual(
   }
 }
 
+// finish_residual for an unsplit level product (splits == 1), the spacecraft-sized case:
+// the same arithmetic, with each warp's rows brought into shared memory by cp.async
+// kFinStages rows ahead of the one it computes, so that the bytes in flight per SM are not
+// bounded by the registers that would hold them. Block (32 x 8) per 128 columns x
+// kFinRows rows; warp w owns the rows w, w + 8, ...; lane l the columns 4 l .. 4 l + 3.
+// A lane reads back only what it copied itself, so the stages need no barrier.
+constexpr int kFinStages = 3;
+constexpr int kFinRows = 256;
+struct FinStage {
+  int4 lev[kLevels][32];
+  double2 src[2][32];
+  uint2 dn[32];
+};
+constexpr size_t kFinSmem = (size_t)8 * kFinStages * sizeof(FinStage);
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(smem)),
+               "l"(gmem)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((uint32_t)__cvta_generic_to_shared(smem)),
+               "l"(gmem)
+               : "memory");
+}
+
+__global__ void __launch_bounds__(256, 2) finish_residual_staged(
+    const int32_t* __restrict__ lev, int64_t ldl, int64_t plane, const int* __restrict__ rowexp,
+    const int* __restrict__ dexp, const int16_t* __restrict__ Dn, const double* __restrict__ dl, int n, int m, int mp,
+    const double* __restrict__ R0, double* __restrict__ R, double* __restrict__ Q, int first, unsigned long long* red,
+    unsigned long long* colmax, int* nonfinite, const int* skip) {
+  if (skip && *(volatile const int*)skip) return;
+  extern __shared__ __align__(16) unsigned char fin_smem[];
+  __shared__ unsigned long long s_col[8][128];
+  FinStage* stages = reinterpret_cast<FinStage*>(fin_smem) + threadIdx.y * kFinStages;
+  const int L = exact_levels(red);
+  const int lane = threadIdx.x;
+  const int jb = blockIdx.x * 128, j = jb + 4 * lane;
+  const int i0 = blockIdx.y * kFinRows + threadIdx.y;
+  const int i_end = min(n, (int)(blockIdx.y + 1) * kFinRows);
+  const int rows = i0 < i_end ? (i_end - i0 + 7) / 8 : 0;  // rows of this warp
+  const double* src = first ? R0 : R;
+  const bool plain = !dl && !Q;
+  const bool live = j < m;
+  // copies of the warp's k-th row into stage k % kFinStages (an empty group past the end,
+  // so that every lane commits the same number of groups)
+  auto issue = [&](int k) {
+    if (k < rows && live) {
+      FinStage& st = stages[k % kFinStages];
+      const int i = i0 + 8 * k;
+      const int64_t o = (int64_t)i * ldl + j, e = (int64_t)i * mp + j;
+      for (int a = 0; a < L; ++a) cp_async16(&st.lev[a][lane], lev + a * plane + o);
+      cp_async16(&st.src[0][lane], src + e);
+      cp_async16(&st.src[1][lane], src + e + 2);
+      cp_async8(&st.dn[lane], Dn + e);
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  };
+  unsigned long long cmax[4] = {0ull, 0ull, 0ull, 0ull};
+  bool bad = false;
+  int f[4] = {0, 0, 0, 0};
+  if (live) {
+    const int4 fv = *reinterpret_cast<const int4*>(dexp + j);  // dexp holds mp >= j + 4 entries
+    f[0] = fv.x;
+    f[1] = fv.y;
+    f[2] = fv.z;
+    f[3] = fv.w;
+  }
+  const int nc = live ? min(4, m - j) : 0;  // valid columns of this lane
+#pragma unroll
+  for (int k = 0; k < kFinStages - 1; ++k) issue(k);
+  for (int k = 0; k < rows; ++k) {
+    issue(k + kFinStages - 1);
+    asm volatile("cp.async.wait_group %0;" ::"n"(kFinStages - 1) : "memory");
+    if (!live) continue;
+    const FinStage& st = stages[k % kFinStages];
+    const int i = i0 + 8 * k;
+    long long T[4] = {0ll, 0ll, 0ll, 0ll};
+#pragma unroll
+    for (int a = 0; a < kLevels; ++a)
+      if (a < L) {
+        const int4 lv = st.lev[a][lane];
+        T[0] = T[0] * 256 + lv.x;
+        T[1] = T[1] * 256 + lv.y;
+        T[2] = T[2] * 256 + lv.z;
+        T[3] = T[3] * 256 + lv.w;
+      }
+    const double2 s01 = st.src[0][lane], s23 = st.src[1][lane];
+    const uint2 dnv = st.dn[lane];
+    const double sv[4] = {s01.x, s01.y, s23.x, s23.y};
+    const int dn[4] = {(int)(int16_t)(dnv.x & 0xffffu), (int)(int16_t)(dnv.x >> 16), (int)(int16_t)(dnv.y & 0xffffu),
+                       (int)(int16_t)(dnv.y >> 16)};
+    const int re = rowexp[i];
+    const int sh = 7 - re + 8 * (L - 1);
+    const int64_t e = (int64_t)i * mp + j;
+    double r[4];
+    if (plain && re >= -14 && sh >= 0) {  // warp-uniform: the warp shares row i
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const long long U = T[c] - (long long)((unsigned long long)(long long)dn[c] << sh);
+        r[c] = sv[c] + int_scale2(U, re + f[c] - 14 - 8 * (L - 1));
+      }
+    } else {
+      const double w = dl ? dl[i] : 1.0;
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const double S = int_scale2(T[c], re + f[c] - 14 - 8 * (L - 1));
+        r[c] = (sv[c] - int_scale2(dn[c], f[c] - 7)) + w * S;
+        if (Q && c < nc) Q[e + c] = (first ? 0.0 : Q[e + c]) + S;
+      }
+    }
+    if (nc == 4) {
+      *reinterpret_cast<double2*>(R + e) = make_double2(r[0], r[1]);
+      *reinterpret_cast<double2*>(R + e + 2) = make_double2(r[2], r[3]);
+    } else {
+      for (int c = 0; c < nc; ++c) R[e + c] = r[c];
+    }
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const unsigned long long rb = (unsigned long long)__double_as_longlong(r[c]) & 0x7fffffffffffffffull;
+      const bool fin = rb < 0x7ff0000000000000ull;
+      if (c < nc) {
+        bad |= !fin;
+        cmax[c] = max(cmax[c], fin ? rb : 0ull);
+      }
+    }
+  }
+  asm volatile("cp.async.wait_group 0;" ::: "memory");
+#pragma unroll
+  for (int c = 0; c < 4; ++c) s_col[threadIdx.y][4 * lane + c] = cmax[c];
+  if (__syncthreads_or(bad) && threadIdx.x == 0 && threadIdx.y == 0) atomicExch(nonfinite, 1);
+  const int tid = threadIdx.y * 32 + threadIdx.x;
+  if (tid < 128) {  // warps 0 .. 3: one column each
+    unsigned long long cm = s_col[0][tid];
+#pragma unroll
+    for (int y = 1; y < 8; ++y) cm = max(cm, s_col[y][tid]);
+    if (jb + tid < m && cm) atomicMax(&colmax[jb + tid], cm);
+    for (int o = 16; o > 0; o >>= 1) cm = max(cm, __shfl_xor_sync(0xffffffffu, cm, o));
+    if (threadIdx.x == 0 && cm) atomicMax(&red[0], cm);
+  }
+}
+
 // ------------------------------------------------------------------ narrow systems
 // quantize_correction and finish_residual for m <= kNarrow right-hand sides (the balance's one
 // column, a factored cotangent's few): one thread per row and a loop over the columns, so
@@ -1439,6 +1581,18 @@ struct Solver {
     return factor(b.symdl, b.symdr, true, rho);
   }
 
+  // The staged finish_residual's shared memory is above the default limit: raised once per
+  // device and thread.
+  rg_status finish_staged_ready() {
+    static thread_local int configured_device = -1;
+    if (configured_device != ctx->device) {
+      RG_CUDA_TRY(ctx, cudaFuncSetAttribute(finish_residual_staged, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)kFinSmem));
+      configured_device = ctx->device;
+    }
+    return RG_OK;
+  }
+
   // One sweep: D = M src (src = R0 for the first, R after), D rounded to its one-slice form and
   // added to X, R = src - D + Dl P' D exactly, then the sweep's words copied to the pinned
   // slot of its parity (ctx->ev_read[parity] recorded after the copy). With a guard the sweep
@@ -1506,10 +1660,18 @@ struct Solver {
       if (st != RG_OK) return st;
     }
     dim3 fg((L.m + 127) / 128, (L.n + 127) / 128);
+    if (L.m > kNarrow && splits == 1) {
+      st = finish_staged_ready();
+      if (st != RG_OK) return st;
+    }
     if (L.m <= kNarrow)
       finish_residual_narrow<<<nb, 256, 0, s>>>(b.lev, tc::exact_ld(L.m), tc::exact_plane(L.n, L.m), splits,
                                                  b.rowexp, b.dexp, b.Dn, dl, L.n, L.m, L.mp, b.R0, b.R, b.Q,
                                                  first ? 1 : 0, rc, b.colmax, err + 1, skip);
+    else if (splits == 1)
+      finish_residual_staged<<<dim3((L.m + 127) / 128, (L.n + kFinRows - 1) / kFinRows), dim3(32, 8), kFinSmem, s>>>(
+          b.lev, tc::exact_ld(L.m), tc::exact_plane(L.n, L.m), b.rowexp, b.dexp, b.Dn, dl, L.n, L.m, L.mp, b.R0, b.R,
+          b.Q, first ? 1 : 0, rc, b.colmax, err + 1, skip);
     else
       finish_residual<<<fg, dim3(32, 8), 0, s>>>(b.lev, tc::exact_ld(L.m), tc::exact_plane(L.n, L.m), splits,
                                                  b.rowexp, b.dexp, b.Dn, dl, L.n, L.m, L.mp, b.R0, b.R, b.Q,
