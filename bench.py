@@ -102,6 +102,9 @@ def parse():
     ap.add_argument("--solve-n", type=int, default=None, metavar="N",
                     help="with --solve-once: a seeded random N-face system (F_ij ~ U[0, 1.5/N] off the diagonal, "
                          "the rest of each row to the environment, areas U[0.5, 2]) instead of the spacecraft")
+    ap.add_argument("--solve-band", type=int, default=0, metavar="W",
+                    help="with --solve-n: F non-zero only within W of the diagonal (row sums kept), so that most "
+                         "256 x 64 blocks of the exact product's slices are zero, as on the spacecraft")
     ap.add_argument("--reflect", action="store_true",
                     help="instead of the bench line, print one JSON line with the reflection walk's rates "
                          "(REFs by MCRT) on the plates and the cube")
@@ -1199,13 +1202,16 @@ class _RandomSystem:
     """A seeded random open system of n faces with the attributes of Pipeline that the
     solve stages use (no mesh)."""
 
-    def __init__(self, ctx, n, n_sets, device):
+    def __init__(self, ctx, n, n_sets, device, band=0):
         import torch
         import synth
         from paper_2511_04277_gb300 import api
         self.api, self.ctx, self.N, self.S = api, ctx, n, n_sets
         g = torch.Generator(device=device).manual_seed(0)
         F = torch.rand((n, n + 1), dtype=torch.float64, device=device, generator=g) * (1.5 / n)
+        if band > 0:  # non-zero only within `band` of the diagonal (most 256 x 64 blocks zero)
+            i = torch.arange(n, device=device)
+            F[:, :n] *= ((i[:, None] - i[None, :]).abs() < band).double() * (n / (2.0 * band))
         F.diagonal()[:] = 0.0
         F[:, n] = 0.0
         F[:, n] = 1.0 - F.sum(dim=1)
@@ -1232,10 +1238,10 @@ class _RandomSystem:
     adjoint = Pipeline.adjoint
 
 
-def solve_once(n_sets, n=None):
+def solve_once(n_sets, n=None, band=0):
     """The spacecraft solves once for `n_sets` eps / rho sets on an enforced 1e7-ray F (or
-    on a seeded random n-face system): REFs, steady temperatures and their adjoint per
-    set, the REF adjoint (the case the solver's ncu captures use)."""
+    on a seeded random n-face system, banded when band > 0): REFs, steady temperatures and
+    their adjoint per set, the REF adjoint (the case the solver's ncu captures use)."""
     import torch
     from paper_2511_04277_gb300 import api
     ctx = api.Context(0)
@@ -1246,7 +1252,7 @@ def solve_once(n_sets, n=None):
         p.mcrt()
         p.enforce()
     else:
-        p = _RandomSystem(ctx, n, n_sets, torch.device("cuda:0"))
+        p = _RandomSystem(ctx, n, n_sets, torch.device("cuda:0"), band=band)
     torch.cuda.synchronize()
     t = time_region(torch, lambda: (p.refs(), p.thermal(), p.adjoint()), torch.cuda.current_stream())
     print(json.dumps({"kind": "solve_once", "n": p.N, "sets": n_sets, "ms": round(t, 2), "sweeps": p.sweeps,
@@ -1262,7 +1268,7 @@ def main():
         trace_once(args.trace_once, args.mesh, args.sided)
         return
     if args.solve_once is not None:
-        solve_once(args.solve_once, args.solve_n)
+        solve_once(args.solve_once, args.solve_n, args.solve_band)
         return
     if args.solve_scaling:
         print(json.dumps(solve_scaling(args)), flush=True)

@@ -206,8 +206,12 @@ rg_status launch_exact_pair(rg_ctx* ctx, const CUtensorMap& ma, const CUtensorMa
   }
   // two CTAs (one cluster) per 256 x 256 tile, no K splits
   dim3 grid(2 * ((args.N + 255) / 256) * ((args.M + 2 * BM - 1) / (2 * BM)), 1, 1);
-  const int tok = rg::timer_begin(ctx, rg::kTimeResidualGemm, s, flops_per_level, alg);
+  // with block flags the pairs add up the blocks they execute (flops per block), else the
+  // launch records its level count (flops per level)
+  const double flops = args.flags ? 2.0 * (2 * BM) * 256 * BK : flops_per_level;
+  const int tok = rg::timer_begin(ctx, rg::kTimeResidualGemm, s, flops, alg);
   args.level_log = rg::timer_level_slot(ctx, tok);
+  if (args.flags && args.level_log) RG_CUDA_TRY(ctx, cudaMemsetAsync(args.level_log, 0, sizeof(int), s));
   kern<<<grid, exact_threads(256), smem, s>>>(ma, mb, args);
   rg::timer_end(ctx, tok, s);
   ++ctx->launches;
@@ -219,7 +223,8 @@ rg_status launch_exact_pair(rg_ctx* ctx, const CUtensorMap& ma, const CUtensorMa
 
 rg_status gemm_exact(rg_ctx* ctx, const void* A, int64_t lda, const void* B, int64_t ldb, int M, int N, int np,
                      const int* levels_d, const unsigned long long* level_words, int level_bits, int max_levels,
-                     int32_t* lev, int split_max, int* splits_out, cudaStream_t s, const int* skip, int alg_k) {
+                     int32_t* lev, int split_max, int* splits_out, cudaStream_t s, const int* skip, int alg_k,
+                     const uint8_t* flags, int flag_rows, int flag_ld) {
   if (M <= 0 || N <= 0) return RG_OK;
   if (np <= 0 || np % (2 * BK) || max_levels < 1)
     return rg::fail(ctx, RG_ERR_ARG, "gemm_exact: level length %d, %d levels", np, max_levels);
@@ -243,6 +248,15 @@ rg_status gemm_exact(rg_ctx* ctx, const void* A, int64_t lda, const void* B, int
   if (st != RG_OK) return st;
   ExactArgs args{M,   N,        np, levels_d, level_words, level_bits, max_levels, lev, exact_ld(N), exact_plane(M, N),
                  splits > 1 ? kb_level / splits : 0, ctx->d_scratch + kGemmErrorSlot, skip};
+  if (pair && flags) {
+    if (flag_rows < (M + 2 * BM - 1) / (2 * BM) || flag_ld < (kb_level + 15) / 16 * 16 || flag_ld % 16 ||
+        max_levels > 8 || (reinterpret_cast<uintptr_t>(flags) & 15))
+      return rg::fail(ctx, RG_ERR_ARG, "gemm_exact: block flags %d x %d for %d rows, %d blocks", flag_rows, flag_ld, M,
+                      kb_level);
+    args.flags = flags;
+    args.flag_rows = flag_rows;
+    args.flag_ld = flag_ld;
+  }
   const double per_level = 2.0 * M * (double)N * np;
   const double alg = 2.0 * M * (double)N * (alg_k > 0 ? alg_k : np);
   if (pair) return launch_exact_pair(ctx, ma, mb, args, s, per_level, alg);

@@ -152,6 +152,33 @@ __device__ __forceinline__ void split_digits(double x, int s, bool nonzero, uint
   dbits[0] = bf16_bits_of_int((int)q);
 }
 
+// Block flags of the slices for the exact product (tc::ExactArgs): flags[(a rows + i / 256)
+// ld + kb] = 1 when slice a has a non-zero digit in rows [256 (i / 256), + 256) and columns
+// [64 kb, 64 kb + 64); the buffer is zeroed before the split. `bits` has bit a set for each
+// level with a non-zero digit in the caller's block.
+struct SliceFlags {
+  uint8_t* f = nullptr;
+  int rows = 0, ld = 0;
+};
+inline SliceFlags slice_flags(uint8_t* f, int np) {
+  return SliceFlags{f, (np + 255) / 256, ((np / 64) + 15) / 16 * 16};
+}
+inline size_t slice_flag_bytes(int np) {
+  const SliceFlags g = slice_flags(nullptr, np);
+  return (size_t)kLevels * g.rows * g.ld;
+}
+__device__ __forceinline__ void mark_blocks(const SliceFlags& g, int i, int kb, unsigned bits) {
+#pragma unroll
+  for (int a = 0; a < kLevels; ++a)
+    if (bits >> a & 1u) g.f[((int64_t)a * g.rows + i / 256) * g.ld + kb] = 1;
+}
+__device__ __forceinline__ unsigned nonzero_levels(const uint32_t (&d0)[kLevels], const uint32_t (&d1)[kLevels]) {
+  unsigned bits = 0u;
+#pragma unroll
+  for (int a = 0; a < kLevels; ++a) bits |= ((d0[a] | d1[a]) != 0u) ? (1u << a) : 0u;
+  return bits;
+}
+
 // Fixed-point split of P' = P Dr (Dr may be null) into kLevels slices per row: with e_i the
 // exponent of max_k |P'_ik| and q = round(P'_ik 2^(39 - e_i)) (|q| < 2^39, to nearest, ties
 // to even), the slices are q's balanced base-256 digits, q = sum_a s_a 256^(4 - a) with
@@ -162,7 +189,8 @@ __device__ __forceinline__ void split_digits(double x, int s, bool nonzero, uint
 // the bit patterns and the only fp64 arithmetic is the product with Dr (GB300's fp64 pipe is
 // narrow).
 __global__ void build_p_exact(const double* __restrict__ P, int64_t ldp, const double* __restrict__ dr, int n,
-                              int np, __nv_bfloat16* __restrict__ Aex, int* __restrict__ rowexp, int* err) {
+                              int np, __nv_bfloat16* __restrict__ Aex, int* __restrict__ rowexp, int* err,
+                              SliceFlags flags) {
   const int i = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
   const int lane = threadIdx.x & 31;
   if (i >= np) return;
@@ -197,6 +225,10 @@ __global__ void build_p_exact(const double* __restrict__ P, int64_t ldp, const d
     split_digits(k + 1 < n ? (dr ? prow[k + 1] * dr[k + 1] : prow[k + 1]) : 0.0, 39 - e, k + 1 < n && mx, d1);
 #pragma unroll
     for (int a = 0; a < kLevels; ++a) row[(int64_t)a * half + k2] = d0[a] | (d1[a] << 16);
+    if (flags.f) {  // the warp's 64 columns are K block k2 / 32 (half is a multiple of 32)
+      const unsigned bits = __reduce_or_sync(0xffffffffu, nonzero_levels(d0, d1));
+      if (lane == 0 && bits) mark_blocks(flags, i, k2 / 32, bits);
+    }
   }
   if (lane == 0) rowexp[i] = e;
 }
@@ -208,7 +240,7 @@ constexpr int kRowSmem = 12288;
 __global__ void __launch_bounds__(512) build_p_exact_row(const double* __restrict__ P, int64_t ldp,
                                                          const double* __restrict__ dr, int n, int np,
                                                          __nv_bfloat16* __restrict__ Aex, int* __restrict__ rowexp,
-                                                         int* err) {
+                                                         int* err, SliceFlags flags) {
   extern __shared__ double xs[];  // [n]: the row of P'
   __shared__ unsigned long long s_mx[16];
   const int i = blockIdx.x, t = threadIdx.x;
@@ -260,6 +292,10 @@ __global__ void __launch_bounds__(512) build_p_exact_row(const double* __restric
     split_digits(k + 1 < n ? xs[k + 1] : 0.0, 39 - e, k + 1 < n && m, d1);
 #pragma unroll
     for (int a = 0; a < kLevels; ++a) row[(int64_t)a * half + k2] = d0[a] | (d1[a] << 16);
+    if (flags.f) {  // the warp's 64 columns are K block k2 / 32 (half is a multiple of 32)
+      const unsigned bits = __reduce_or_sync(0xffffffffu, nonzero_levels(d0, d1));
+      if ((t & 31) == 0 && bits) mark_blocks(flags, i, k2 / 32, bits);
+    }
   }
   if (t == 0) rowexp[i] = e;
 }
@@ -312,14 +348,18 @@ __global__ void __launch_bounds__(256) p_colmax_t(const double* __restrict__ P, 
 __global__ void __launch_bounds__(256) build_p_exact_t(const double* __restrict__ P, int64_t ldp,
                                                        const double* __restrict__ dr, int n, int np,
                                                        const unsigned long long* __restrict__ colmax,
-                                                       __nv_bfloat16* __restrict__ Aex, int* __restrict__ rowexp) {
+                                                       __nv_bfloat16* __restrict__ Aex, int* __restrict__ rowexp,
+                                                       SliceFlags flags) {
   __shared__ __align__(16) uint16_t tile[kLevels][32][66];  // [a][row of P'][column k]
+  __shared__ unsigned s_bits;
   const int x = threadIdx.x, y = threadIdx.y;
   const int i0 = blockIdx.x * 32, i = i0 + x;
   const int k0 = blockIdx.y * 64;
   const unsigned long long m = i < n ? colmax[i] : 0ull;
   const int e = m ? frexp_exponent_bits(m) : 0;
   if (blockIdx.y == 0 && y == 0 && i < np) rowexp[i] = e;
+  if (x == 0 && y == 0) s_bits = 0u;
+  unsigned bits = 0u;
   double v[8];
 #pragma unroll
   for (int r = 0; r < 8; ++r) {
@@ -334,9 +374,17 @@ __global__ void __launch_bounds__(256) build_p_exact_t(const double* __restrict_
     uint32_t d[kLevels];
     split_digits(xv, 39 - e, in && m, d);
 #pragma unroll
-    for (int a = 0; a < kLevels; ++a) tile[a][x][kl] = (uint16_t)d[a];
+    for (int a = 0; a < kLevels; ++a) {
+      tile[a][x][kl] = (uint16_t)d[a];
+      bits |= d[a] ? (1u << a) : 0u;
+    }
   }
+  bits = __reduce_or_sync(0xffffffffu, bits);
+  __syncthreads();  // s_bits is zeroed
+  if (x == 0 && bits) atomicOr(&s_bits, bits);
   __syncthreads();
+  // the block's 32 rows and 64 columns lie in one 256-row tile and K block (k0 = 64 blockIdx.y)
+  if (flags.f && x == 0 && y == 0 && s_bits) mark_blocks(flags, i0, blockIdx.y, s_bits);
   // warp y writes rows i0 + y + 8 c, lane x the columns k0 + 2 x, k0 + 2 x + 1
 #pragma unroll
   for (int c = 0; c < 4; ++c) {
@@ -354,11 +402,14 @@ __global__ void __launch_bounds__(256) build_p_exact_t(const double* __restrict_
 // definition): the transposed form as a column-maximum pass and a tiled digit pass (colmax:
 // np words of scratch), the row form with the row in shared memory up to kRowSmem columns.
 rg_status launch_build_p(rg_ctx* ctx, const double* P, int64_t ldp, bool trans, const double* dr, int n, int np,
-                         __nv_bfloat16* Aex, int* rowexp, int* err, unsigned long long* colmax, cudaStream_t s) {
+                         __nv_bfloat16* Aex, int* rowexp, int* err, unsigned long long* colmax, cudaStream_t s,
+                         uint8_t* flag_buf = nullptr) {
+  const SliceFlags flags = slice_flags(flag_buf, np);
+  if (flag_buf) RG_CUDA_TRY(ctx, cudaMemsetAsync(flag_buf, 0, slice_flag_bytes(np), s));
   if (trans) {
     RG_CUDA_TRY(ctx, cudaMemsetAsync(colmax, 0, (size_t)np * sizeof(unsigned long long), s));
     p_colmax_t<<<dim3((n + 31) / 32, (n + 255) / 256), dim3(32, 8), 0, s>>>(P, ldp, dr, n, colmax, err);
-    build_p_exact_t<<<dim3(np / 32, np / 64), dim3(32, 8), 0, s>>>(P, ldp, dr, n, np, colmax, Aex, rowexp);
+    build_p_exact_t<<<dim3(np / 32, np / 64), dim3(32, 8), 0, s>>>(P, ldp, dr, n, np, colmax, Aex, rowexp, flags);
     ctx->launches += 2;
   } else if (n <= kRowSmem) {
     static thread_local int configured_device = -1;
@@ -367,10 +418,10 @@ rg_status launch_build_p(rg_ctx* ctx, const double* P, int64_t ldp, bool trans, 
                                             (int)(kRowSmem * sizeof(double))));
       configured_device = ctx->device;
     }
-    build_p_exact_row<<<np, 512, (size_t)n * sizeof(double), s>>>(P, ldp, dr, n, np, Aex, rowexp, err);
+    build_p_exact_row<<<np, 512, (size_t)n * sizeof(double), s>>>(P, ldp, dr, n, np, Aex, rowexp, err, flags);
     ++ctx->launches;
   } else {
-    build_p_exact<<<(np + 7) / 8, 256, 0, s>>>(P, ldp, dr, n, np, Aex, rowexp, err);
+    build_p_exact<<<(np + 7) / 8, 256, 0, s>>>(P, ldp, dr, n, np, Aex, rowexp, err, flags);
     ++ctx->launches;
   }
   RG_CUDA_TRY(ctx, cudaGetLastError());
@@ -1334,6 +1385,7 @@ struct Buffers {
   unsigned long long* colmax;    // mp, column maxima of R (double bits)
   __nv_bfloat16* Aex;            // np x kLevels np, fixed-point slices of P'
   int* rowexp;                   // np
+  uint8_t* flags;                // the slices' non-zero 256 x 64 blocks (SliceFlags)
   float* Dbuf;                   // np x mp, correction M R before rounding
   unsigned int* dcolmax;         // mp, its column maxima (float bits)
   __nv_bfloat16* Bq;             // mp x np, the rounded correction, transposed
@@ -1376,6 +1428,7 @@ void plan(const Layout& L, Take&& t) {
   t.template take<double>((size_t)L.np);                          // symdr
   t.template take<float>((size_t)L.np);                           // sfin
   t.template take<float>((size_t)L.np);                           // sfout
+  t.template take<uint8_t>(slice_flag_bytes(L.np));               // slice flags
 }
 
 // The solver's status words in the context scratch (ints), laid out so that one copy
@@ -1463,6 +1516,7 @@ struct Solver {
     b.symdr = cv.take<double>((size_t)L.np);
     b.sfin = cv.take<float>((size_t)L.np);
     b.sfout = cv.take<float>((size_t)L.np);
+    b.flags = cv.take<uint8_t>(slice_flag_bytes(L.np));
     err = ctx->d_scratch + kStatus;
     RG_CUDA_TRY(ctx, cudaMemsetAsync(err, 0, 6 * sizeof(int), s));  // error words and the GEMM's
     return RG_OK;
@@ -1477,11 +1531,13 @@ struct Solver {
     return RG_OK;
   }
 
-  // Fixed-point slices of P' = P Dr (Dr may be null).
+  // Fixed-point slices of P' = P Dr (Dr may be null), with their block flags where the
+  // right-hand sides are wide enough for the tensor-core level product (the narrow GEMV
+  // reads no flags).
   rg_status build_slices(const double* dr) {
     // nsum (the Newton-Schulz start's sums, read before this) serves as the column maxima
     return launch_build_p(ctx, P, ldp, transP, dr, L.n, L.np, b.Aex, b.rowexp, err,
-                          reinterpret_cast<unsigned long long*>(b.nsum), s);
+                          reinterpret_cast<unsigned long long*>(b.nsum), s, L.m > kNarrow ? b.flags : nullptr);
   }
 
   // Newton-Schulz approximate inverse of A = I - Dl P Dr into b.X16[cur].
@@ -1655,8 +1711,9 @@ struct Solver {
       RG_CUDA_TRY(ctx, cudaGetLastError());
       splits = 1;
     } else {
+      const SliceFlags fl = slice_flags(b.flags, L.np);
       st = tc::gemm_exact(ctx, b.Aex, (int64_t)kLevels * L.np, b.Bq, L.np, L.n, L.m, L.np, nullptr, rc, kLevelBits,
-                          kLevels, b.lev, exact_splits(L.n, L.m), &splits, s, skip, L.n);
+                          kLevels, b.lev, exact_splits(L.n, L.m), &splits, s, skip, L.n, fl.f, fl.rows, fl.ld);
       if (st != RG_OK) return st;
     }
     dim3 fg((L.m + 127) / 128, (L.n + 127) / 128);

@@ -192,6 +192,20 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// 16 columns of this warp's 32 TMEM lanes (one row per thread), as tmem_ld32: the exact
+// product's epilogue, whose 128 int32 column sums per thread leave no room for 32 more.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
 // Shared-memory matrix descriptor of a K-major tile with 128-byte rows, 128-byte
 // swizzle, 8-row core groups 1024 bytes apart (sm_100 descriptor version 1).
 __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
@@ -694,8 +708,18 @@ struct ExactArgs {
   int split_blocks;      // K blocks of one level per CTA z (0: all)
   int* error_word;
   const int* skip = nullptr;
-  int* level_log = nullptr;  // kernel timer: the launch records L here (CTA 0, thread 0)
+  int* level_log = nullptr;  // kernel timer: the launch records L here (CTA 0, thread 0), or with
+                             // flags the executed 256 x 256 x BK blocks (summed by the pairs)
+  // Block flags of A (CTA-pair kernel only; null: every block): flags[(a flag_rows + tile) flag_ld
+  // + kb] != 0 when the 256-row tile `tile` of level a's slice has a non-zero entry in K block kb;
+  // flag_ld is a multiple of 16 (one chunk's flags are one 16-byte word).
+  const uint8_t* flags = nullptr;
+  int flag_rows = 0, flag_ld = 0;
 };
+
+// Chunks of a level in the CTA-pair kernel with block flags: at most kExactMaxChunks per level
+// (np <= 32,768), and at most 8 levels.
+constexpr int kExactMaxChunks = 32;
 
 // 1,024-long K chunks (the last one of a level may be shorter): with operands |a| <= 128 and
 // |b| <= 127 every partial sum of a chunk is an integer below 1,024 x 16,256 = 16,646,144 < 2^24,
@@ -910,12 +934,17 @@ __global__ void __launch_bounds__(exact_threads(256), 1) __cluster_dims__(2, 1, 
   uint64_t* drain = acc_empty + 2;       // [1]
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
   __shared__ int s_abort;
+  __shared__ uint16_t s_mask[kExactMaxChunks * 8];  // [level][chunk]: the chunk's non-zero blocks
+  // per epilogue warp: 32 rows x 16 columns of level sums on their way to HBM (rows 80 bytes
+  // apart: 16-byte aligned, and the eight rows of a quarter-warp's stores in distinct banks)
+  __shared__ __align__(16) uint32_t s_out[8][32][20];
 
   const bool skipped = args.skip && *(volatile const int*)args.skip;
   const int L = skipped ? 0
                         : (args.levels ? *(volatile const int*)args.levels
                                        : exact_level_count(args.level_words, args.level_bits, args.max_levels));
-  if (args.level_log && threadIdx.x == 0 && blockIdx.x == 0 && blockIdx.z == 0) *args.level_log = L;
+  const bool flagged = args.flags != nullptr;
+  if (args.level_log && !flagged && threadIdx.x == 0 && blockIdx.x == 0 && blockIdx.z == 0) *args.level_log = L;
   if (skipped) return;  // uniform over the pair: before any barrier or allocation
   if (L < 1 || L > args.max_levels) {
     if (threadIdx.x == 0 && args.error_word) atomicExch(args.error_word, 1);
@@ -938,8 +967,37 @@ __global__ void __launch_bounds__(exact_threads(256), 1) __cluster_dims__(2, 1, 
   const int kb_first = args.split_blocks > 0 ? blockIdx.z * args.split_blocks : 0;
   const int kb_per = args.split_blocks > 0 ? min(args.split_blocks, kb_level - kb_first) : kb_level;
   const int chunks_per_level = (kb_per + kExactChunkBlocks - 1) / kExactChunkBlocks;
-  const int n_chunks = L * chunks_per_level;
-  const int total_kb = L * kb_per;
+  if (L * chunks_per_level > kExactMaxChunks * 8) {  // the mask table holds 8 levels of 32 chunks
+    if (threadIdx.x == 0 && args.error_word) atomicExch(args.error_word, 1);
+    return;  // uniform over the pair: before any barrier or allocation
+  }
+  // the blocks of chunk c of level a that hold non-zero entries of A (bit q: block 16 c + q);
+  // both CTAs of a pair read the same flags (the pair's 256-row tile), so every role of both
+  // walks the same sequence of blocks. An accumulation takes up to kExactChunkBlocks of a
+  // level's flagged blocks in K order, wherever they lie: the bound on its partial sums
+  // counts the products it adds, not the K range they span
+  for (int idx = threadIdx.x; idx < L * chunks_per_level; idx += blockDim.x) {
+    const int a = idx / chunks_per_level, c = idx % chunks_per_level;
+    const int nq = min(kExactChunkBlocks, kb_per - c * kExactChunkBlocks);
+    unsigned msk = (1u << nq) - 1u;
+    if (flagged) {
+      const uint4 w = __ldg(reinterpret_cast<const uint4*>(
+          args.flags + ((int64_t)a * args.flag_rows + tile_m) * args.flag_ld + c * kExactChunkBlocks));
+      const uint32_t wd[4] = {w.x, w.y, w.z, w.w};
+      unsigned f = 0u;
+#pragma unroll
+      for (int q = 0; q < 16; ++q) f |= ((wd[q >> 2] >> (8 * (q & 3))) & 0xffu) ? (1u << q) : 0u;
+      msk &= f;
+    }
+    s_mask[idx] = (uint16_t)msk;
+  }
+  auto chunk_mask = [&](int a, int c) -> unsigned { return s_mask[a * chunks_per_level + c]; };
+  // flagged blocks of level a (the accumulations of the level: ceil(/ kExactChunkBlocks))
+  auto level_blocks = [&](int a) -> int {
+    int k = 0;
+    for (int c = 0; c < chunks_per_level; ++c) k += __popc(chunk_mask(a, c));
+    return k;
+  };
 
   if (threadIdx.x == 0) {
     s_abort = 0;
@@ -966,47 +1024,68 @@ __global__ void __launch_bounds__(exact_threads(256), 1) __cluster_dims__(2, 1, 
   if (warp == 0) {
     // ---------------- TMA producer (both CTAs): level a, block kb of the CTA's K range
     if (lane == 0) {
-      for (int t = 0; t < total_kb; ++t) {
-        const int s = t % kStages;
-        if (t >= kStages && !mbar_wait_cluster(&empty[s], ((t / kStages) - 1) & 1)) { *abort_flag = 1; break; }
-        if (*abort_flag) break;
-        const int a = t / kb_per, kb = kb_first + t % kb_per;
-        mbar_expect_tx(&full[s], kABytes + kBBytes);
-        tma_load_2d(sA + s * kABytes, &map_a, &full[s], a * args.np + kb * BK, m0);
-        tma_load_2d(sB + s * kBBytes, &map_b, &full[s], kb * BK, nb0);
+      int t = 0;
+      for (int g = 0; g < L * chunks_per_level && !*abort_flag; ++g) {
+        const int a = g / chunks_per_level, c = g % chunks_per_level;
+        for (unsigned msk = chunk_mask(a, c); msk; msk &= msk - 1u, ++t) {
+          const int s = t % kStages;
+          if (t >= kStages && !mbar_wait_cluster(&empty[s], ((t / kStages) - 1) & 1)) { *abort_flag = 1; break; }
+          if (*abort_flag) break;
+          const int kb = kb_first + c * kExactChunkBlocks + (__ffs(msk) - 1);
+          mbar_expect_tx(&full[s], kABytes + kBBytes);
+          tma_load_2d(sA + s * kABytes, &map_a, &full[s], a * args.np + kb * BK, m0);
+          tma_load_2d(sB + s * kBBytes, &map_b, &full[s], kb * BK, nb0);
+        }
       }
     }
   } else if (warp == 1) {
     if (lane == 0) {
       if (leader) {
         // ---------------- MMA issuer of the pair: one accumulation per chunk, two buffers
-        int t = 0;
-        for (int c = 0; c < n_chunks && !*abort_flag; ++c) {
-          const int b = c & 1;
-          if (c >= 2 && !mbar_wait_cluster(&acc_empty[b], ((c >> 1) - 1) & 1)) { *abort_flag = 1; break; }
-          const uint32_t d_tmem = tmem_base + (uint32_t)(b * PN);
-          const int c_in = c % chunks_per_level;
-          const int nq = min(kExactChunkBlocks, kb_per - c_in * kExactChunkBlocks);
-          for (int q = 0; q < nq; ++q, ++t) {
-            const int s = t % kStages;
-            if (!mbar_wait_cluster(&full[s], (t / kStages) & 1)) { *abort_flag = 1; break; }
-            tc_fence_after();
-            const uint32_t a_addr = smem_u32(sA + s * kABytes), b_addr = smem_u32(sB + s * kBBytes);
+        // accumulations of up to kExactChunkBlocks flagged blocks of one level; cc counts them
+        // (the accumulator buffers and their phases follow cc)
+        int t = 0, cc = 0;
+        for (int a = 0; a < L && !*abort_flag; ++a) {
+          int q = 0;  // blocks in the open accumulation
+          uint32_t d_tmem = 0;
+          for (int c = 0; c < chunks_per_level && !*abort_flag; ++c)
+            for (unsigned msk = chunk_mask(a, c); msk; msk &= msk - 1u, ++t) {
+              if (q == 0) {
+                const int b = cc & 1;
+                if (cc >= 2 && !mbar_wait_cluster(&acc_empty[b], ((cc >> 1) - 1) & 1)) { *abort_flag = 1; break; }
+                d_tmem = tmem_base + (uint32_t)(b * PN);
+              }
+              const int s = t % kStages;
+              if (!mbar_wait_cluster(&full[s], (t / kStages) & 1)) { *abort_flag = 1; break; }
+              tc_fence_after();
+              const uint32_t a_addr = smem_u32(sA + s * kABytes), b_addr = smem_u32(sB + s * kBBytes);
 #pragma unroll
-            for (int kk = 0; kk < BK / 16; ++kk)
-              umma_f16_pair(d_tmem, sw128_desc(a_addr + kk * 32), sw128_desc(b_addr + kk * 32), kIdesc,
-                            (q > 0 || kk > 0) ? 1u : 0u);
-            umma_commit_pair_both(&empty[s]);
-          }
+              for (int kk = 0; kk < BK / 16; ++kk)
+                umma_f16_pair(d_tmem, sw128_desc(a_addr + kk * 32), sw128_desc(b_addr + kk * 32), kIdesc,
+                              (q > 0 || kk > 0) ? 1u : 0u);
+              umma_commit_pair_both(&empty[s]);
+              if (++q == kExactChunkBlocks) {
+                umma_commit_pair_both(&acc_full[cc & 1]);
+                ++cc;
+                q = 0;
+              }
+            }
           if (*abort_flag) break;
-          umma_commit_pair_both(&acc_full[b]);
+          if (q > 0) {
+            umma_commit_pair_both(&acc_full[cc & 1]);
+            ++cc;
+          }
         }
+        if (flagged && args.level_log) atomicAdd(args.level_log, t);
         umma_commit_pair_local(drain);
         mbar_wait(drain, 0);
       } else {
         // ---------------- relay of this CTA's full stages to the even CTA
         const uint32_t leader_full = mapa_shared(smem_u32(full), 0);
-        for (int t = 0; t < total_kb; ++t) {
+        int total = 0;
+        for (int g = 0; g < L * chunks_per_level; ++g)
+          total += __popc(chunk_mask(g / chunks_per_level, g % chunks_per_level));
+        for (int t = 0; t < total; ++t) {
           const int s = t % kStages;
           if (!mbar_wait(&full[s], (t / kStages) & 1)) { *abort_flag = 1; break; }
           mbar_arrive_remote(leader_full + 8u * (uint32_t)s);
@@ -1024,38 +1103,51 @@ __global__ void __launch_bounds__(exact_threads(256), 1) __cluster_dims__(2, 1, 
     uint32_t acc[kCols];
 #pragma unroll
     for (int i = 0; i < kCols; ++i) acc[i] = 0u;
-    int in_level = 0;
-    for (int c = 0; c < n_chunks; ++c) {
-      const int b = c & 1;
-      if (!mbar_wait_cluster(&acc_full[b], (c >> 1) & 1)) { *abort_flag = 1; break; }
-      tc_fence_after();
+    int cc = 0;
+    for (int a = 0; a < L && !*abort_flag; ++a) {
+      const int groups = (level_blocks(a) + kExactChunkBlocks - 1) / kExactChunkBlocks;
+      for (int gi = 0; gi < groups; ++gi) {  // a level without blocks: nothing to drain, zero sums
+        const int b = cc & 1;
+        if (!mbar_wait_cluster(&acc_full[b], (cc >> 1) & 1)) { *abort_flag = 1; break; }
+        tc_fence_after();
 #pragma unroll
-      for (int c0 = 0; c0 < kCols; c0 += 32) {
-        float v[32];
-        tmem_ld32(tmem_base + lane_addr + (uint32_t)(b * PN + cbase + c0), v);
-        // v is an integer of magnitude below 2^24, exact in fp32: converted exactly
+        for (int c0 = 0; c0 < kCols; c0 += 16) {
+          float v[16];
+          tmem_ld16(tmem_base + lane_addr + (uint32_t)(b * PN + cbase + c0), v);
+          // v is an integer of magnitude below 2^24, exact in fp32: converted exactly
 #pragma unroll
-        for (int i = 0; i < 32; ++i) acc[c0 + i] += (uint32_t)__float2int_rn(v[i]);
-      }
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive_remote(empty_addr + 8u * (uint32_t)b);
-      if (++in_level == chunks_per_level) {
-        // rows at and beyond M land in the plane's padding (exact_plane rounds M up to 256)
-        const int a = c / chunks_per_level;
-        int32_t* dst = args.lev + ((int64_t)blockIdx.z * args.max_levels + a) * args.plane + (int64_t)row * args.ldl +
-                       n0 + cbase;
-#pragma unroll
-        for (int i = 0; i < kCols; i += 4) {
-          int4 w;
-          w.x = (int32_t)acc[i];
-          w.y = (int32_t)acc[i + 1];
-          w.z = (int32_t)acc[i + 2];
-          w.w = (int32_t)acc[i + 3];
-          *reinterpret_cast<int4*>(dst + i) = w;
-          acc[i] = acc[i + 1] = acc[i + 2] = acc[i + 3] = 0u;
+          for (int i = 0; i < 16; ++i) acc[c0 + i] += (uint32_t)__float2int_rn(v[i]);
         }
-        in_level = 0;
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive_remote(empty_addr + 8u * (uint32_t)b);
+        ++cc;
+      }
+      if (*abort_flag) break;
+      {
+        // the warp's 32 rows go out 16 columns at a time through shared memory, so that each
+        // store instruction writes eight rows' 64 contiguous bytes (rows at and beyond M land
+        // in the plane's padding: exact_plane rounds M up to 256)
+        uint32_t(*buf)[20] = s_out[ew];
+        int32_t* plane = args.lev + ((int64_t)blockIdx.z * args.max_levels + a) * args.plane +
+                         (int64_t)(m0 + quarter * 32) * args.ldl + n0 + cbase;
+#pragma unroll
+        for (int i0 = 0; i0 < kCols; i0 += 16) {
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            *reinterpret_cast<uint4*>(&buf[lane][4 * q]) =
+                make_uint4(acc[i0 + 4 * q], acc[i0 + 4 * q + 1], acc[i0 + 4 * q + 2], acc[i0 + 4 * q + 3]);
+            acc[i0 + 4 * q] = acc[i0 + 4 * q + 1] = acc[i0 + 4 * q + 2] = acc[i0 + 4 * q + 3] = 0u;
+          }
+          __syncwarp();
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            const int v = lane + 32 * k, r = v >> 2, q = v & 3;
+            *reinterpret_cast<uint4*>(plane + (int64_t)r * args.ldl + i0 + 4 * q) =
+                *reinterpret_cast<const uint4*>(&buf[r][4 * q]);
+          }
+          __syncwarp();
+        }
       }
     }
   }
@@ -1102,10 +1194,13 @@ int64_t exact_ld(int N);
 int64_t exact_plane(int M, int N);
 // The level count comes from levels_d (device int) or, when that is null, from
 // exact_level_count(level_words, level_bits, max_levels).
+// flags (optional, see ExactArgs): block flags of A, [max_levels][flag_rows >= ceil(M / 256)]
+// [flag_ld >= np / BK rounded up to 16] bytes; the CTA-pair kernel skips the blocks of A that
+// hold only zeros (the others ignore the flags).
 rg_status gemm_exact(rg_ctx* ctx, const void* A, int64_t lda, const void* B, int64_t ldb, int M, int N, int np,
                      const int* levels_d, const unsigned long long* level_words, int level_bits, int max_levels,
                      int32_t* lev, int split_max, int* splits_out, cudaStream_t s, const int* skip = nullptr,
-                     int alg_k = 0);
+                     int alg_k = 0, const uint8_t* flags = nullptr, int flag_rows = 0, int flag_ld = 0);
 
 // Device error word the GEMM kernels raise on a timed-out wait (ctx scratch slot).
 constexpr int kGemmErrorSlot = 16;

@@ -315,3 +315,39 @@ def test_lsq_plates_config(rg_ctx):
     assert np.abs(got.sum(axis=1) - 1).max() <= 1e-7
     eta = A[:, None] * got[:, :512]
     assert np.abs(eta - eta.T).max() <= 1e-7 * np.abs(eta).max()
+
+
+def _banded_F(N, rng, band=384, extra=3):
+    """A view-factor-like N x (N+1) matrix whose N x N block is non-zero only within `band`
+    of the diagonal and in a few off-diagonal 512-wide squares: most 256 x 64 blocks of its
+    slices are zero, as on the spacecraft (zero blocks skipped by the exact product)."""
+    i = np.arange(N)
+    M = np.abs(i[:, None] - i[None, :]) < band
+    for _ in range(extra):
+        a, b = rng.integers(0, N - 512, 2)
+        M[a:a + 512, b:b + 512] = True
+    F = np.zeros((N, N + 1))
+    F[:, :N] = np.where(M, rng.random((N, N)) ** 3, 0.0)
+    np.fill_diagonal(F[:, :N], 0.0)
+    F[:, N] = 0.05 + 0.3 * rng.random(N)
+    return F / F.sum(axis=1, keepdims=True)
+
+
+def test_gebhart_block_sparse_vs_oracle(rg_ctx):
+    """N = 4,608 (CTA-pair exact product) with mostly zero 256 x 64 blocks: the REFs and
+    both gradients of a random cotangent against the oracle (Eq. B.11 and its adjoint)."""
+    rng = np.random.default_rng(4608)
+    N = 4608
+    F = _banded_F(N, rng)
+    eps = rng.uniform(0.1, 0.9, N)
+    rho = 1 - eps
+    B, sweeps, _ = api.gebhart(rg_ctx, _dev(F), _dev(eps), _dev(rho), tol=1e-12)
+    Bo = G.gebhart(F, eps, rho)
+    got = B[0].cpu().numpy()
+    assert np.all(np.abs(got - Bo).max(axis=1) <= 1e-10 * np.abs(Bo).max(axis=1))
+    assert np.abs(got.sum(axis=1) - 1.0).max() <= 1e-10
+    W = rng.standard_normal((N, N + 1))
+    de, dr = api.gebhart_adjoint(rg_ctx, _dev(F), _dev(eps), _dev(rho), _dev(Bo), _dev(W), tol=1e-12)
+    deo, dro = G.gebhart_adjoint(F, eps, rho, Bo, W)
+    assert np.abs(de[0].cpu().numpy() - deo).max() <= REL * np.abs(deo).max()
+    assert np.abs(dr[0].cpu().numpy() - dro).max() <= REL * np.abs(dro).max()
