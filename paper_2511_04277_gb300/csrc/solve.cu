@@ -962,7 +962,8 @@ template <class T16>
 __global__ void build_ns_start(const double* __restrict__ P, int64_t ldp, bool trans, const double* __restrict__ dl,
                                const double* __restrict__ dr, int n, int np, T16* __restrict__ A16,
                                T16* __restrict__ X16, T16* __restrict__ Xt16, double* __restrict__ rowsum,
-                               double* __restrict__ colsum, bool gen, const double* __restrict__ gdr) {
+                               double* __restrict__ colsum, bool gen, const double* __restrict__ gdr,
+                               uint8_t* __restrict__ aflags) {
   __shared__ double raw[32][33];
   __shared__ float xs[32][33];
   __shared__ float cpart[8][33];
@@ -980,6 +981,7 @@ __global__ void build_ns_start(const double* __restrict__ P, int64_t ldp, bool t
   const float rk = (k < n && dr) ? (float)dr[k] : 1.f;
   const float gk = (k < n && gdr) ? (float)gdr[k] : 1.f;
   float cs = 0.f;
+  bool nonzero = false;  // a non-zero 16-bit entry of A in this 32 x 32 tile
   for (int a = ty; a < 32; a += 8) {
     const int i = i0 + a;
     const float p = (float)(trans ? raw[tx][a] : raw[a][tx]);
@@ -987,7 +989,9 @@ __global__ void build_ns_start(const double* __restrict__ P, int64_t ldp, bool t
     if (i < n && k < n) e = (dl ? (float)dl[i] : 1.f) * p * rk;
     const float one = (i == k) ? 1.f : 0.f;
     const int64_t o = (int64_t)i * np + k;
-    A16[o] = to16<T16>(one - e);
+    const T16 av = to16<T16>(one - e);
+    A16[o] = av;
+    nonzero |= (*reinterpret_cast<const uint16_t*>(&av) & 0x7fffu) != 0u;
     X16[o] = to16<T16>(one + e);
     xs[a][tx] = one + e;
     const float ae = gen ? ((i < n && k < n) ? fabsf(p * gk) : 0.f) : fabsf(e);
@@ -997,13 +1001,18 @@ __global__ void build_ns_start(const double* __restrict__ P, int64_t ldp, bool t
     if (tx == 0 && rs != 0.f) atomicAdd(&rowsum[i], (double)rs);
   }
   cpart[ty][tx] = cs;
-  __syncthreads();
+  // the tile lies in one 256-row tile of A and one 64-wide K block (the pair GEMM's flags)
+  if (__syncthreads_or(nonzero) && aflags && tx == 0 && ty == 0)
+    aflags[(int64_t)(i0 / 256) * ((np / 64 + 31) / 32 * 32) + k0 / 64] = 1;
   if (ty == 0) {
     for (int y = 1; y < 8; ++y) cs += cpart[y][tx];
     if (cs != 0.f) atomicAdd(&colsum[k], (double)cs);
   }
   for (int a = ty; a < 32; a += 8) Xt16[(int64_t)(k0 + a) * np + i0 + tx] = to16<T16>(xs[tx][a]);
 }
+
+// Bytes of the Newton-Schulz matrix's block flags (tc::GemmArgs::aflags) for np unknowns.
+inline size_t a16_flag_bytes(int np) { return (size_t)((np + 255) / 256) * ((np / 64 + 31) / 32 * 32); }
 
 // ||E||_inf = max_i rowsum_i into e0_bits[0], ||E||_1 = max_k colsum_k into e0_bits[1] (bits,
 // atomicMax; zeroed by the caller), and colmax[0 .. mp) = 0 for the first correction.
@@ -1386,6 +1395,7 @@ struct Buffers {
   __nv_bfloat16* Aex;            // np x kLevels np, fixed-point slices of P'
   int* rowexp;                   // np
   uint8_t* flags;                // the slices' non-zero 256 x 64 blocks (SliceFlags)
+  uint8_t* aflags;               // A16's non-zero 256 x 64 blocks (the first Newton-Schulz product)
   float* Dbuf;                   // np x mp, correction M R before rounding
   unsigned int* dcolmax;         // mp, its column maxima (float bits)
   __nv_bfloat16* Bq;             // mp x np, the rounded correction, transposed
@@ -1429,6 +1439,7 @@ void plan(const Layout& L, Take&& t) {
   t.template take<float>((size_t)L.np);                           // sfin
   t.template take<float>((size_t)L.np);                           // sfout
   t.template take<uint8_t>(slice_flag_bytes(L.np));               // slice flags
+  t.template take<uint8_t>(a16_flag_bytes(L.np));                 // A16 flags
 }
 
 // The solver's status words in the context scratch (ints), laid out so that one copy
@@ -1517,6 +1528,7 @@ struct Solver {
     b.sfin = cv.take<float>((size_t)L.np);
     b.sfout = cv.take<float>((size_t)L.np);
     b.flags = cv.take<uint8_t>(slice_flag_bytes(L.np));
+    b.aflags = cv.take<uint8_t>(a16_flag_bytes(L.np));
     err = ctx->d_scratch + kStatus;
     RG_CUDA_TRY(ctx, cudaMemsetAsync(err, 0, 6 * sizeof(int), s));  // error words and the GEMM's
     return RG_OK;
@@ -1550,8 +1562,9 @@ struct Solver {
     T16* Xt = static_cast<T16*>(b.Xt16);
     T16* Zt = static_cast<T16*>(b.Zt16);
     RG_CUDA_TRY(ctx, cudaMemsetAsync(b.nsum, 0, 2 * L.np * sizeof(double), s));
+    RG_CUDA_TRY(ctx, cudaMemsetAsync(b.aflags, 0, a16_flag_bytes(L.np), s));
     build_ns_start<T16><<<dim3(L.np / 32, L.np / 32), dim3(32, 8), 0, s>>>(
-        P, ldp, transP, dl, dr, L.n, L.np, A16, X[0], Xt, b.nsum, b.nsum + L.np, symm, gen_dr);
+        P, ldp, transP, dl, dr, L.n, L.np, A16, X[0], Xt, b.nsum, b.nsum + L.np, symm, gen_dr, b.aflags);
     ns_norms<<<std::max(1, std::min(ctx->sm_count, (std::max(L.np, L.mp) + 255) / 256)), 256, 0, s>>>(
         b.nsum, b.nsum + L.np, L.np, e0, b.colmax, L.mp);
     ctx->launches += 2;
@@ -1585,7 +1598,7 @@ struct Solver {
       // Zt = (2I - A X)^T : A operand A16 [i][k], B operand X^T rows = X columns (X itself
       // when symmetric); the whole product
       rg_status st = tc::gemm(ctx, bf16, A16, L.np, symm ? X[cur] : Xt, L.np, L.np, L.np, L.np,
-                              tc::EpiTwoIMinusT<T16>{Zt, L.np}, s);
+                              tc::EpiTwoIMinusT<T16>{Zt, L.np}, s, nullptr, false, b.aflags);
       if (st != RG_OK) return st;
       // X' = X (2I - A X) : A operand X [i][k], B operand Z^T; symmetric when X and A are, so
       // then only its upper tiles are computed

@@ -363,7 +363,15 @@ struct GemmArgs {
   // 1: the product is symmetric (M = N, square tiles): only the tiles on and above the
   // diagonal are computed, the epilogue writing each off-diagonal one for its transpose too
   int sym = 0;
+  // Block flags of A (CTA-pair kernel only; null: every block): aflags[tile ceil(K / BK / 32) 32
+  // + kb] != 0 when A's 256-row tile `tile` has a non-zero entry in K block kb. With flags the
+  // leader CTAs add the K blocks they execute to *level_log (kernel timer), else nothing.
+  const uint8_t* aflags = nullptr;
+  int* level_log = nullptr;
 };
+
+// K blocks of the CTA-pair GEMM whose A block flags it can hold (K <= 32,768).
+constexpr int kGemmMaxKWords = 16;
 
 // Tile (I, J), I <= J, of the pid-th tile on or above the diagonal of a T x T tiling, in
 // bands of kGroupM tile rows, each band's tiles column by column (the CTAs running together
@@ -553,6 +561,7 @@ __global__ void __launch_bounds__(kThreads, 1) __cluster_dims__(2, 1, 1)
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
   __shared__ int s_abort;
   __shared__ float s_stage[4][32][33];
+  __shared__ uint32_t s_kmask[kGemmMaxKWords];  // the tile's K blocks of A holding non-zeros
 
   // uniform over the pair (both read the same word): before any barrier or allocation
   if (args.skip && *(volatile const int*)args.skip) return;
@@ -576,6 +585,24 @@ __global__ void __launch_bounds__(kThreads, 1) __cluster_dims__(2, 1, 1)
   const int nb0 = tile_n * PN + (int)rank * (PN / 2);      // this CTA's half of B's rows
   const int n0 = tile_n * PN;                              // the tile's columns
   const int kb_total = (args.K + BK - 1) / BK;
+  // K blocks this tile multiplies: every block, or with A's block flags only those where the
+  // pair's 256 rows of A hold a non-zero (both CTAs read the same flags; at least one block
+  // is kept, so that the accumulator is written)
+  const int kwords = (kb_total + 31) / 32;
+  const bool use_flags = args.aflags != nullptr && kwords <= kGemmMaxKWords;
+  for (int w = threadIdx.x; w < kwords && w < kGemmMaxKWords; w += blockDim.x) {
+    uint32_t m = kb_total - 32 * w >= 32 ? ~0u : ((1u << (kb_total - 32 * w)) - 1u);
+    if (use_flags) {
+      const uint4* fp = reinterpret_cast<const uint4*>(args.aflags + ((int64_t)tile_m * kwords + w) * 32);
+      const uint4 f0 = __ldg(fp), f1 = __ldg(fp + 1);
+      const uint32_t fw[8] = {f0.x, f0.y, f0.z, f0.w, f1.x, f1.y, f1.z, f1.w};
+      uint32_t bits = 0u;
+#pragma unroll
+      for (int q = 0; q < 32; ++q) bits |= ((fw[q >> 2] >> (8 * (q & 3))) & 0xffu) ? (1u << q) : 0u;
+      m &= bits;
+    }
+    s_kmask[w] = m;
+  }
 
   if (threadIdx.x == 0) {
     s_abort = 0;
@@ -595,14 +622,31 @@ __global__ void __launch_bounds__(kThreads, 1) __cluster_dims__(2, 1, 1)
   tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
   volatile int* abort_flag = &s_abort;
+  // the K block of the t-th multiplied block (t < n_mult), from the mask table
+  int n_mult = 0;
+  if (use_flags)
+    for (int w = 0; w < kwords; ++w) n_mult += __popc(s_kmask[w]);
+  const bool none = use_flags && n_mult == 0;
+  if (!use_flags) n_mult = kb_total;
+  if (none) n_mult = 1;  // an all-zero row of tiles: one (zero) block initialises the accumulator
+  int it_w = 0;
+  uint32_t it_m = use_flags ? s_kmask[0] : 0u;
+  auto next_kb = [&](int t) -> int {  // called with t = 0, 1, 2, ... in order
+    if (!use_flags || none) return t;
+    while (!it_m) it_m = s_kmask[++it_w];
+    const int kb = 32 * it_w + __ffs(it_m) - 1;
+    it_m &= it_m - 1u;
+    return kb;
+  };
 
   if (warp == 0) {
     // ---------------- TMA producer (both CTAs)
     if (lane == 0) {
-      for (int kb = 0; kb < kb_total; ++kb) {
-        const int s = kb % kStages;
-        if (kb >= kStages && !mbar_wait_cluster(&empty[s], ((kb / kStages) - 1) & 1)) { *abort_flag = 1; break; }
+      for (int t = 0; t < n_mult; ++t) {
+        const int s = t % kStages;
+        if (t >= kStages && !mbar_wait_cluster(&empty[s], ((t / kStages) - 1) & 1)) { *abort_flag = 1; break; }
         if (*abort_flag) break;
+        const int kb = next_kb(t);
         mbar_expect_tx(&full[s], kABytes + kBBytes);
         tma_load_2d(sA + s * kABytes, &map_a, &full[s], kb * BK, m0);
         tma_load_2d(sB + s * kBBytes, &map_b, &full[s], kb * BK, nb0);
@@ -612,17 +656,18 @@ __global__ void __launch_bounds__(kThreads, 1) __cluster_dims__(2, 1, 1)
     if (lane == 0) {
       if (leader) {
         // ---------------- MMA issuer of the pair
-        for (int kb = 0; kb < kb_total && !*abort_flag; ++kb) {
-          const int s = kb % kStages;
-          if (!mbar_wait_cluster(&full[s], (kb / kStages) & 1)) { *abort_flag = 1; break; }
+        for (int t = 0; t < n_mult && !*abort_flag; ++t) {
+          const int s = t % kStages;
+          if (!mbar_wait_cluster(&full[s], (t / kStages) & 1)) { *abort_flag = 1; break; }
           tc_fence_after();
           const uint32_t a_addr = smem_u32(sA + s * kABytes), b_addr = smem_u32(sB + s * kBBytes);
 #pragma unroll
           for (int kk = 0; kk < BK / 16; ++kk)
             umma_f16_pair(tmem_base, sw128_desc(a_addr + kk * 32), sw128_desc(b_addr + kk * 32), kIdesc,
-                          (kb > 0 || kk > 0) ? 1u : 0u);
+                          (t > 0 || kk > 0) ? 1u : 0u);
           umma_commit_pair_both(&empty[s]);
         }
+        if (use_flags && args.level_log) atomicAdd(args.level_log, n_mult);
         if (!*abort_flag) umma_commit_pair_both(acc_full);
         // every MMA this thread issued has completed once `drain` fires
         umma_commit_pair_local(drain);
@@ -630,9 +675,9 @@ __global__ void __launch_bounds__(kThreads, 1) __cluster_dims__(2, 1, 1)
       } else {
         // ---------------- relay: this CTA's stage s is full -> one arrival on the even CTA's full[s]
         const uint32_t leader_full = mapa_shared(smem_u32(full), 0);
-        for (int kb = 0; kb < kb_total; ++kb) {
-          const int s = kb % kStages;
-          if (!mbar_wait(&full[s], (kb / kStages) & 1)) { *abort_flag = 1; break; }
+        for (int t = 0; t < n_mult; ++t) {
+          const int s = t % kStages;
+          if (!mbar_wait(&full[s], (t / kStages) & 1)) { *abort_flag = 1; break; }
           mbar_arrive_remote(leader_full + 8u * (uint32_t)s);
         }
       }
@@ -1127,7 +1172,8 @@ __global__ void __launch_bounds__(exact_threads(256), 1) __cluster_dims__(2, 1, 
       {
         // the warp's 32 rows go out 16 columns at a time through shared memory, so that each
         // store instruction writes eight rows' 64 contiguous bytes (rows at and beyond M land
-        // in the plane's padding: exact_plane rounds M up to 256)
+        // in the plane's padding: exact_plane rounds M up to 256); streaming stores, so that
+        // the level sums (gigabytes per launch) do not evict the operand tiles from L2
         uint32_t(*buf)[20] = s_out[ew];
         int32_t* plane = args.lev + ((int64_t)blockIdx.z * args.max_levels + a) * args.plane +
                          (int64_t)(m0 + quarter * 32) * args.ldl + n0 + cbase;
@@ -1143,8 +1189,8 @@ __global__ void __launch_bounds__(exact_threads(256), 1) __cluster_dims__(2, 1, 
 #pragma unroll
           for (int k = 0; k < 4; ++k) {
             const int v = lane + 32 * k, r = v >> 2, q = v & 3;
-            *reinterpret_cast<uint4*>(plane + (int64_t)r * args.ldl + i0 + 4 * q) =
-                *reinterpret_cast<const uint4*>(&buf[r][4 * q]);
+            __stcs(reinterpret_cast<uint4*>(plane + (int64_t)r * args.ldl + i0 + 4 * q),
+                   *reinterpret_cast<const uint4*>(&buf[r][4 * q]));
           }
           __syncwarp();
         }
@@ -1174,9 +1220,12 @@ constexpr size_t exact_pair_smem_bytes() {
 // where the tiles are square only those on and above the diagonal are computed and the
 // epilogue writes the off-diagonal ones for their transposes too (the Newton-Schulz epilogues
 // with their own `sym` set), else the whole product is computed.
+// aflags (optional): A's block flags, [ceil(M / 256)][ceil(K / 64 / 32) 32] bytes (GemmArgs);
+// the CTA-pair kernel skips A's all-zero K blocks (the others ignore the flags).
 template <class Epi>
 rg_status gemm(rg_ctx* ctx, bool bf16, const void* A, int64_t lda, const void* B, int64_t ldb, int M, int N, int K,
-               const Epi& epi, cudaStream_t s, const int* skip = nullptr, bool sym = false);
+               const Epi& epi, cudaStream_t s, const int* skip = nullptr, bool sym = false,
+               const uint8_t* aflags = nullptr);
 
 // C (fp32, ldc) = alpha * A B^T + beta * C with A [M x K] (lda), B [N x K] (ldb), 16-bit
 // K-major operands (bf16 when `bf16`, else fp16). lda, ldb: multiples of 8 elements;
