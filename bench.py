@@ -397,14 +397,29 @@ def rownorm(x, y):
     return float(((x - y).abs().amax(dim=-1) / y.abs().amax(dim=-1).clamp_min(1e-300)).max())
 
 
-def enforce_bytes(n, iters):
+def enforce_bytes(n, iters, pair_frac=1.0):
     """Algorithmic HBM bytes of `iters` equal-weight enforcer iterations: the first reads and
     writes the whole N x (N+1) matrix (16 B per entry); every later one, on the symmetric
-    matrix, the tiles on and above the diagonal and the environment column (16 B per stored
-    entry)."""
+    matrix, the tiles on and above the diagonal that hold a non-zero (pair_frac of them: the
+    zero ones stay zero and are skipped) and the environment column (16 B per stored entry)."""
     if iters <= 0:
         return 0.0
-    return 16.0 * n * (n + 1) + 16.0 * (iters - 1) * (n * (n + 1) / 2.0 + n)
+    return 16.0 * n * (n + 1) + 16.0 * (iters - 1) * (pair_frac * n * (n + 1) / 2.0 + n)
+
+
+def nonzero_pair_fraction(F):
+    """Fraction of the enforcer's tile pairs (I, J), I <= J, whose tiles (I, J) or (J, I) of
+    the N x N block hold a non-zero (32-wide tiles up to N = 2,048, 64-wide above, as the
+    enforcer takes them)."""
+    import torch
+    n = F.shape[0]
+    t = 32 if n <= 2048 else 64
+    nt = (n + t - 1) // t
+    Z = torch.zeros((nt * t, nt * t), dtype=torch.bool, device=F.device)
+    Z[:n, :n] = F[:, :n] != 0
+    blk = Z.view(nt, t, nt, t).any(dim=3).any(dim=1)
+    blk = blk | blk.T
+    return float(torch.triu(blk).sum()) / (nt * (nt + 1) / 2)
 
 
 def kernel_rooflines(api, ctx, pipe, steps, step_ms, peaks, trace_roof):
@@ -457,15 +472,17 @@ def kernel_rooflines(api, ctx, pipe, steps, step_ms, peaks, trace_roof):
                 row["note"] = "achieved = executed tensor flops (2 M N K)"
         else:
             it = getattr(pipe, "iters", 0)
-            gb = enforce_bytes(pipe.N, it) / (per_launch * 1e-3) / 1e9
+            frac = nonzero_pair_fraction(pipe.F_it)
+            gb = enforce_bytes(pipe.N, it, frac) / (per_launch * 1e-3) / 1e9
             # DRAM bytes per algorithmic byte from the committed capture at N = 6,144
-            traffic = profiled_traffic("enforce_persistent_n6144.md", "enforce.cu", enforce_bytes(pipe.N, it))
+            traffic = profiled_traffic("enforce_persistent_n6144.md", "enforce.cu", enforce_bytes(pipe.N, it, frac))
             row.update({"kernel": "enforce_persistent", "bound": "hbm", "achieved": round(gb, 1), "peak": hbm,
                         "unit": "GB/s", "frac": round(gb / hbm, 4),
                         "traffic": None if traffic is None else round(traffic),
+                        "nonzero_tile_pairs": round(frac, 4),
                         "note": f"{it} iterations per launch: the first reads and writes every entry (16 B), the "
-                                "symmetric ones after it the tiles on and above the diagonal (16 B per stored "
-                                "entry, one fp64 add and multiply each, fixed-point row sums)"})
+                                "symmetric ones after it the tiles on and above the diagonal that hold a non-zero "
+                                "(16 B per stored entry, one fp64 multiplication each, fixed-point row sums)"})
         out[kind] = row
     r = api.kernel_timer_read(ctx, "factor")
     if r["launches"]:
@@ -682,7 +699,8 @@ def stage_rooflines(api, torch, ctx, pipe, flush, stream, peaks):
                                                                                           tol=1e-12)), stream))
         iters = box[0]
     ms_e = statistics.median(t_enf)
-    gbs = enforce_bytes(N, iters) / (ms_e * 1e-3) / 1e9
+    pf = nonzero_pair_fraction(F)
+    gbs = enforce_bytes(N, iters, pf) / (ms_e * 1e-3) / 1e9
     hbm = float(peaks.get("hbm_gbs", 6800.0))
     t_ref, sweeps = [], 0
     for _ in range(3):
@@ -714,7 +732,8 @@ def stage_rooflines(api, torch, ctx, pipe, flush, stream, peaks):
         "enforce_iterative": {"kernel": "enforce_persistent", "bound": "hbm", "achieved": round(gbs, 1),
                               "peak": hbm, "unit": "GB/s", "frac": round(gbs / hbm, 4), "iterations": iters,
                               "ms": round(ms_e, 4),
-                              "note": f"{enforce_bytes(N, iters) / max(iters, 1) / 1e6:.1f} MB per iteration on "
+                              "nonzero_tile_pairs": round(pf, 4),
+                              "note": f"{enforce_bytes(N, iters, pf) / max(iters, 1) / 1e6:.1f} MB per iteration on "
                                       f"average, L2-resident at N={N}"},
         "gebhart": {"kernel": "gemm_kernel (tcgen05) + helpers", "bound": "tensor", "achieved": round(tf, 3),
                     "peak": bf, "unit": "TFLOP/s", "frac": round(tf / bf, 5), "sweeps": sweeps, "ms": round(ms_r, 4),
@@ -1019,7 +1038,8 @@ def solve_scaling(args):
             t_e.append(t)
             iters = box["it"]
         ms_e = statistics.median(t_e[1:])
-        gbs = enforce_bytes(n, iters) / (ms_e * 1e-3) / 1e9
+        pf = nonzero_pair_fraction(F)
+        gbs = enforce_bytes(n, iters, pf) / (ms_e * 1e-3) / 1e9
         hbm = float(peaks.get("hbm_gbs", 6800.0))
         # the weighted enforcer (fractional-variance kappa, Eq. 3.23-3.25): kappa once, then
         # the iterations with per-pair weights (24 B per entry per iteration)
@@ -1038,7 +1058,8 @@ def solve_scaling(args):
         out["enforce"].append({"workload": name, "n": n, "iterations": iters, "ms": round(ms_e, 3),
                                "ms_per_iteration": round(ms_e / iters, 4), "achieved_gbs": round(gbs, 1),
                                "peak_gbs": hbm, "frac": round(gbs / hbm, 4),
-                               "bytes_per_iteration": round(enforce_bytes(n, iters) / max(iters, 1)),
+                               "bytes_per_iteration": round(enforce_bytes(n, iters, pf) / max(iters, 1)),
+                               "nonzero_tile_pairs": round(pf, 4),
                                "bound": "hbm (whole call: also F -> eta and back, 28 B per entry once)",
                                "weighted": {"kappa": "fractional variance", "iterations": iters_k,
                                             "ms": round(ms_k, 3), "ms_per_iteration": round(ms_k / iters_k, 4)}})

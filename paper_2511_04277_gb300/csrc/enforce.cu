@@ -105,7 +105,8 @@ __device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
 // row stride is T + 1 doubles: bank of (r, c) = (r + c) mod 16), in a fixed order that
 // is the same on both paths (kappa = 1/2 given as weights gives the same bits). A
 // negative symmetrised value raises *neg (when given): the symmetric iterations below
-// need non-negative entries.
+// need non-negative entries. With `nz`, *nz records whether the pair's symmetrised tiles
+// hold a non-zero (a zero pair stays zero in every later symmetric iteration).
 template <int T>
 struct TileSmem {
   double A[T][T + 1];
@@ -117,7 +118,8 @@ struct TileSmem {
 template <int T, bool kW>
 __device__ __forceinline__ void sym_tile(double* __restrict__ H, const double* __restrict__ s,
                                          const double* __restrict__ kappa, int32_t n, double* __restrict__ P, int I,
-                                         int J, unsigned long long* d_recip, TileSmem<T>& sm, int* neg = nullptr) {
+                                         int J, unsigned long long* d_recip, TileSmem<T>& sm, int* neg = nullptr,
+                                         uint8_t* nz = nullptr) {
   static_assert(T == 64 || T == 32, "bank rotation for 64- and 32-wide tiles");
   constexpr int kPer = T * T / kThreads;  // entries per thread
   auto& A = sm.A;
@@ -160,7 +162,7 @@ __device__ __forceinline__ void sym_tile(double* __restrict__ H, const double* _
   };
   double v1[kPer], v2[kW ? kPer : 1];
   unsigned long long dmax = 0ull;  // bit pattern of the largest defect (non-negative)
-  bool negative = false;
+  bool negative = false, any = false;
 #pragma unroll
   for (int k = 0; k < kPer; ++k) {
     const int e = tid + k * kThreads, r = e / T, c = e % T;
@@ -168,6 +170,7 @@ __device__ __forceinline__ void sym_tile(double* __restrict__ H, const double* _
     const double a = ea(r, c), b = eb(c, r);
     v1[k] = (i < n && j < n) ? pair(a, b, i, j) : 0.0;
     negative |= v1[k] < 0.0;
+    any |= v1[k] != 0.0;
     const double d = kW ? 0.5 * fabs(a - b) : fabs(a - b);
     dmax = max(dmax, (unsigned long long)__double_as_longlong(d));
     if constexpr (kW) {
@@ -225,6 +228,10 @@ __device__ __forceinline__ void sym_tile(double* __restrict__ H, const double* _
     atomicMax(d_recip, m);
   }
   if (__syncthreads_or(negative) && neg && tid == 0) atomicExch(neg, 1);  // also: the tiles are reused next
+  if (nz) {
+    const int a = __syncthreads_or(any);
+    if (tid == 0) *nz = (uint8_t)(a != 0);
+  }
 }
 
 template <int T, bool kW>
@@ -482,8 +489,8 @@ __device__ __forceinline__ unsigned tile_defect(int32_t n, int I, int J, double 
 // Walks the tile pairs p, p + stride, ... (numbered row by row over I <= J) without
 // recounting from the first row at every step.
 struct PairWalker {
-  int I, q, nt;
-  __device__ PairWalker(int p, int n_tiles) : I(0), q(p), nt(n_tiles) { settle(); }
+  int I, q, nt, p;  // p: the pair's number
+  __device__ PairWalker(int p0, int n_tiles) : I(0), q(p0), nt(n_tiles), p(p0) { settle(); }
   __device__ void settle() {
     while (I < nt && q >= nt - I) {
       q -= nt - I;
@@ -492,10 +499,17 @@ struct PairWalker {
   }
   __device__ void advance(int stride) {
     q += stride;
+    p += stride;
     settle();
   }
   __device__ bool valid() const { return I < nt; }
   __device__ int J() const { return I + q; }
+  // on to the next pair (this one included) whose flag is non-zero; flags written by this
+  // block in an earlier iteration or by an earlier kernel, read through L2
+  __device__ void skip_zero(const uint8_t* nz, int stride) {
+    if (!nz) return;
+    while (valid() && !__ldcg(nz + p)) advance(stride);
+  }
 };
 
 // fp32 (hi, lo) split of h: h - hi is exact in fp64, lo its rounding
@@ -514,7 +528,7 @@ __global__ void __launch_bounds__(kThreads, 3) enforce_persistent(double* __rest
                                                                const double* __restrict__ omega, int32_t n,
                                                                int32_t n_tiles, double* __restrict__ P,
                                                                PersistState* st, double tol_abs, int32_t maxit,
-                                                               int eoff) {
+                                                               int eoff, uint8_t* __restrict__ tile_nz) {
   __shared__ TileSmem<T> sm;
   __shared__ SymMeta<T> meta;
   __shared__ double red[kThreads];
@@ -528,15 +542,19 @@ __global__ void __launch_bounds__(kThreads, 3) enforce_persistent(double* __rest
     // (1) reciprocity on the tile pairs (I, J), I <= J, numbered row by row
     if (!fast) {
       for (PairWalker w(blockIdx.x, n_tiles); w.valid(); w.advance(gridDim.x))
-        sym_tile<T, kW>(H, s, kappa, n, P, w.I, w.J(), &st->d_recip[par], sm, k == 0 ? &st->neg : nullptr);
+        sym_tile<T, kW>(H, s, kappa, n, P, w.I, w.J(), &st->d_recip[par], sm, k == 0 ? &st->neg : nullptr,
+                        (k == 0 && !kW) ? tile_nz + w.p : nullptr);
     } else if constexpr (!kW) {
       unsigned emax = 0u;
       int smin = 64;
+      // the zero pairs (flagged by the first iteration) stay zero, their row sums 0
       PairWalker w(blockIdx.x, n_tiles);
+      w.skip_zero(tile_nz, gridDim.x);
       if (w.valid()) load_tile<T>(H, n, w.I, w.J(), sm.A);
       for (int cur = 0; w.valid(); cur ^= 1) {
         const int I = w.I, J = w.J();
         w.advance(gridDim.x);
+        w.skip_zero(tile_nz, gridDim.x);
         if (w.valid()) {  // prefetch the next pair's tile into the other buffer
           load_tile<T>(H, n, w.I, w.J(), cur ? sm.A : sm.B);
           asm volatile("cp.async.wait_group 1;" ::: "memory");
@@ -618,7 +636,8 @@ __global__ void __launch_bounds__(kThreads, 3) enforce_persistent(double* __rest
         dr = INFINITY;
         if (!v->bad[par] && dcl <= tol_abs) {
           unsigned dmax = 0u;
-          for (PairWalker w(blockIdx.x, n_tiles); w.valid(); w.advance(gridDim.x)) {
+          for (PairWalker w(blockIdx.x, n_tiles); w.skip_zero(tile_nz, gridDim.x), w.valid();
+               w.advance(gridDim.x)) {
             const int I = w.I, J = w.J();
             load_tile<T>(H, n, I, J, sm.A);
             if (threadIdx.x < 2 * T) {
@@ -660,11 +679,13 @@ __global__ void __launch_bounds__(kThreads, 3) enforce_persistent(double* __rest
 // transpose of (I, J) through shared memory. q_i = s_i / Omega_i (row_quotients).
 template <int T>
 __global__ void __launch_bounds__(kThreads) from_exchange_sym(double* __restrict__ H, const double* __restrict__ q,
-                                                              int32_t n, int32_t n_tiles) {
+                                                              int32_t n, int32_t n_tiles,
+                                                              const uint8_t* __restrict__ tile_nz) {
   __shared__ double X[T][T + 1];
   __shared__ double qI[T], qJ[T];
   const int64_t ld = n + 1;
-  for (PairWalker w(blockIdx.x, n_tiles); w.valid(); w.advance(gridDim.x)) {
+  // a zero pair's tiles hold zeros, which q_i H leaves as they are
+  for (PairWalker w(blockIdx.x, n_tiles); w.skip_zero(tile_nz, gridDim.x), w.valid(); w.advance(gridDim.x)) {
     const int I = w.I, J = w.J();
     load_tile<T>(H, n, I, J, X);
     if (threadIdx.x < 2 * T) {
@@ -886,6 +907,7 @@ rg_status enforce_iterative(rg_ctx* ctx, int32_t n, const double* omega_d, const
   sz.take<PersistState>(1);
   sz.take<float2>(2 * (size_t)n);              // fp32 splits of s / 2, two iterations
   sz.take<int>(n);                             // row-sum bound exponents
+  sz.take<uint8_t>((size_t)n_tiles * (n_tiles + 1) / 2);  // non-zero tile pairs
   void* ws = nullptr;
   rg_status rs = rg::workspace(ctx, sz.off, &ws);
   if (rs != RG_OK) return rs;
@@ -896,6 +918,7 @@ rg_status enforce_iterative(rg_ctx* ctx, int32_t n, const double* omega_d, const
   PersistState* pst = cv.take<PersistState>(1);
   float2* hsplit = cv.take<float2>(2 * (size_t)n);
   int* eR = cv.take<int>(n);
+  uint8_t* tile_nz = cv.take<uint8_t>((size_t)n_tiles * (n_tiles + 1) / 2);
   const int64_t total = (int64_t)n * (n + 1);
   RG_CUDA_TRY(ctx, cudaMemsetAsync(st, 0, sizeof(EnforceState), s));
   // tolerance scale: max Omega
@@ -920,7 +943,7 @@ rg_status enforce_iterative(rg_ctx* ctx, int32_t n, const double* omega_d, const
   RG_CUDA_TRY(ctx, cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, ctx->device));
   if (coop) {
     void (*kern)(double*, double*, float2*, int*, const double*, const double*, int32_t, int32_t, double*,
-                 PersistState*, double, int32_t, int);
+                 PersistState*, double, int32_t, int, uint8_t*);
     if (tile == kTSmall) kern = kappa_d ? enforce_persistent<kTSmall, true> : enforce_persistent<kTSmall, false>;
     else kern = kappa_d ? enforce_persistent<kT, true> : enforce_persistent<kT, false>;
     int per_sm = 0;
@@ -934,7 +957,7 @@ rg_status enforce_iterative(rg_ctx* ctx, int32_t n, const double* omega_d, const
     double* Fp = F_d;
     const double* kp = kappa_d;
     const double* op = omega_d;
-    void* args[] = {&Fp, &sc, &hsplit, &eR, &kp, &op, &nn, &nt, &P, &pst, &ta, &mi, &eo};
+    void* args[] = {&Fp, &sc, &hsplit, &eR, &kp, &op, &nn, &nt, &P, &pst, &ta, &mi, &eo, &tile_nz};
     const int tok = rg::timer_begin(ctx, rg::kTimeEnforce, s);
     RG_CUDA_TRY(ctx, cudaLaunchCooperativeKernel((const void*)kern, dim3(grid), dim3(kThreads), args, 0, s));
     rg::timer_end(ctx, tok, s);
@@ -974,8 +997,8 @@ rg_status enforce_iterative(rg_ctx* ctx, int32_t n, const double* omega_d, const
   if (sym) {
     const int n_pairs = n_tiles * (n_tiles + 1) / 2;
     const int grid = std::min(n_pairs, 4 * ctx->sm_count);
-    if (tile == kTSmall) from_exchange_sym<kTSmall><<<grid, kThreads, 0, s>>>(F_d, sc, n, n_tiles);
-    else from_exchange_sym<kT><<<grid, kThreads, 0, s>>>(F_d, sc, n, n_tiles);
+    if (tile == kTSmall) from_exchange_sym<kTSmall><<<grid, kThreads, 0, s>>>(F_d, sc, n, n_tiles, tile_nz);
+    else from_exchange_sym<kT><<<grid, kThreads, 0, s>>>(F_d, sc, n, n_tiles, tile_nz);
   } else {
     from_exchange_kernel<<<blocks_for((int64_t)n * n, ctx->sm_count), kThreads, 0, s>>>(F_d, sc, n, (int64_t)n * n);
   }
