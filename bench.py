@@ -446,11 +446,9 @@ def kernel_rooflines(api, ctx, pipe, steps, step_ms, peaks, trace_roof):
             alg = r["alg_flops"] / r["ms"] / 1e9
             exe = r["flops"] / r["ms"] / 1e9
             if kind == "residual_gemm":
-                # DRAM bytes per output entry and level from the committed full-size capture,
-                # times the entries x levels of a mean launch (executed flops / (2 N_p))
-                np_ = (pipe.N + 127) // 128 * 128
-                traffic = profiled_traffic("exact_gemm_n4096.md", "tc_gemm.cuh",
-                                           r["flops"] / r["launches"] / (2.0 * np_))
+                # DRAM bytes per executed flop from the committed full-size capture of the
+                # spacecraft's exact products, times the executed flops of a mean launch
+                traffic = profiled_traffic("exact_gemm_spacecraft.md", "tc_gemm.cuh", r["flops"] / r["launches"])
             else:
                 # DRAM bytes per executed flop from the committed full-size capture
                 traffic = profiled_traffic("gemm_pair_n4096.md", "tc_gemm.cuh", r["flops"] / r["launches"])
