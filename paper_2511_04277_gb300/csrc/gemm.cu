@@ -67,7 +67,8 @@ int tile_width(const rg_ctx* ctx, int M, int N) {
 
 template <class Epi>
 rg_status gemm(rg_ctx* ctx, bool bf16, const void* A, int64_t lda, const void* B, int64_t ldb, int M, int N, int K,
-               const Epi& epi, cudaStream_t s, const int* skip, bool sym, const uint8_t* aflags) {
+               const Epi& epi, cudaStream_t s, const int* skip, bool sym, const uint8_t* aflags,
+               const uint8_t* bflags) {
   if (M <= 0 || N <= 0) return RG_OK;
   if (K <= 0) return rg::fail(ctx, RG_ERR_ARG, "gemm: K = %d", K);
   const int bn = tile_width(ctx, M, N);
@@ -80,9 +81,11 @@ rg_status gemm(rg_ctx* ctx, bool bf16, const void* A, int64_t lda, const void* B
   args.skip = skip;
   // a symmetric product computes the upper tiles only where the tiles are square
   args.sym = (sym && M == N && (bn == 256 || bn == 128)) ? 1 : 0;
-  if (bn == 256 && aflags) {
-    if (reinterpret_cast<uintptr_t>(aflags) & 15) return rg::fail(ctx, RG_ERR_ARG, "gemm: A block flags not aligned");
+  if (bn == 256 && !args.sym && (aflags || bflags)) {
+    if ((reinterpret_cast<uintptr_t>(aflags) | reinterpret_cast<uintptr_t>(bflags)) & 15)
+      return rg::fail(ctx, RG_ERR_ARG, "gemm: block flags not 16-byte aligned");
     args.aflags = aflags;
+    args.bflags = bflags;
   }
   if (bn == 256)
     return bf16 ? launch_pair<Epi, true>(ctx, ma, mb, args, epi, s) : launch_pair<Epi, false>(ctx, ma, mb, args, epi, s);
@@ -93,15 +96,15 @@ rg_status gemm(rg_ctx* ctx, bool bf16, const void* A, int64_t lda, const void* B
 }
 
 template rg_status gemm<EpiTwoIMinusT<__nv_bfloat16>>(rg_ctx*, bool, const void*, int64_t, const void*, int64_t, int,
-                                                      int, int, const EpiTwoIMinusT<__nv_bfloat16>&, cudaStream_t, const int*, bool, const uint8_t*);
+                                                      int, int, const EpiTwoIMinusT<__nv_bfloat16>&, cudaStream_t, const int*, bool, const uint8_t*, const uint8_t*);
 template rg_status gemm<EpiTwoIMinusT<__half>>(rg_ctx*, bool, const void*, int64_t, const void*, int64_t, int, int,
-                                               int, const EpiTwoIMinusT<__half>&, cudaStream_t, const int*, bool, const uint8_t*);
+                                               int, const EpiTwoIMinusT<__half>&, cudaStream_t, const int*, bool, const uint8_t*, const uint8_t*);
 template rg_status gemm<EpiStore16Both<__nv_bfloat16>>(rg_ctx*, bool, const void*, int64_t, const void*, int64_t, int,
-                                                       int, int, const EpiStore16Both<__nv_bfloat16>&, cudaStream_t, const int*, bool, const uint8_t*);
+                                                       int, int, const EpiStore16Both<__nv_bfloat16>&, cudaStream_t, const int*, bool, const uint8_t*, const uint8_t*);
 template rg_status gemm<EpiStore16Both<__half>>(rg_ctx*, bool, const void*, int64_t, const void*, int64_t, int, int,
-                                                int, const EpiStore16Both<__half>&, cudaStream_t, const int*, bool, const uint8_t*);
+                                                int, const EpiStore16Both<__half>&, cudaStream_t, const int*, bool, const uint8_t*, const uint8_t*);
 template rg_status gemm<EpiCorrection>(rg_ctx*, bool, const void*, int64_t, const void*, int64_t, int, int, int,
-                                       const EpiCorrection&, cudaStream_t, const int*, bool, const uint8_t*);
+                                       const EpiCorrection&, cudaStream_t, const int*, bool, const uint8_t*, const uint8_t*);
 
 namespace {
 
@@ -145,10 +148,11 @@ rg_status launch_pair(rg_ctx* ctx, const CUtensorMap& ma, const CUtensorMap& mb,
   const double executed =
       args.sym ? 2.0 * (double)tiles * 256 * 256 * args.K : 2.0 * args.M * (double)args.N * args.K;
   // with A's block flags the pairs add up the K blocks they execute (flops per block)
-  const int tok = rg::timer_begin(ctx, rg::kTimeGemm, s, args.aflags ? 2.0 * 256 * 256 * BK : executed,
+  const bool flagged = args.aflags || args.bflags;
+  const int tok = rg::timer_begin(ctx, rg::kTimeGemm, s, flagged ? 2.0 * 256 * 256 * BK : executed,
                                   args.alg_k > 0 ? 2.0 * args.M * (double)args.N * args.alg_k : executed);
   GemmArgs a = args;
-  if (a.aflags) {
+  if (flagged) {
     a.level_log = rg::timer_level_slot(ctx, tok);
     if (a.level_log) RG_CUDA_TRY(ctx, cudaMemsetAsync(a.level_log, 0, sizeof(int), s));
   }

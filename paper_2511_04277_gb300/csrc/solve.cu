@@ -1013,6 +1013,8 @@ __global__ void build_ns_start(const double* __restrict__ P, int64_t ldp, bool t
 
 // Bytes of the Newton-Schulz matrix's block flags (tc::GemmArgs::aflags) for np unknowns.
 inline size_t a16_flag_bytes(int np) { return (size_t)((np + 255) / 256) * ((np / 64 + 31) / 32 * 32); }
+// Bytes of the first correction's B block flags (mp right-hand sides, np unknowns).
+inline size_t rt_flag_bytes(int mp, int np) { return (size_t)((mp + 255) / 256) * ((np / 64 + 31) / 32 * 32); }
 
 // ||E||_inf = max_i rowsum_i into e0_bits[0], ||E||_1 = max_k colsum_k into e0_bits[1] (bits,
 // atomicMax; zeroed by the caller), and colmax[0 .. mp) = 0 for the first correction.
@@ -1118,7 +1120,7 @@ __global__ void scaled_transpose16(const double* __restrict__ R, int64_t ld, int
                                    const unsigned long long* __restrict__ colmax, T16* __restrict__ Rt,
                                    float* __restrict__ colscale, const SweepGuard guard,
                                    unsigned long long* red_cur, unsigned int* dcolmax,
-                                   const float* __restrict__ rs) {
+                                   const float* __restrict__ rs, uint8_t* __restrict__ bflags) {
   __shared__ __align__(16) float tile[32][66];  // [column][row]: a row pair is one 8-byte read
   if (guard.err) {  // one thread per block evaluates the rule (an fp64 division), the block follows
     __shared__ int s_end;
@@ -1143,17 +1145,22 @@ __global__ void scaled_transpose16(const double* __restrict__ R, int64_t ld, int
   }
   if (blockIdx.y == 0 && threadIdx.y == 0 && j < mp) colscale[j] = ldexpf(1.f, e);
   double x[8];
+  bool nonzero = false;
 #pragma unroll
   for (int r = 0; r < 8; ++r) {  // warp-uniform rows: threadIdx.y is the warp
     const int i = i0 + threadIdx.y + 8 * r;
     x[r] = (i < n && j < m) ? R[(int64_t)i * ld + j] : 0.0;
+    nonzero |= x[r] != 0.0;
   }
 #pragma unroll
   for (int r = 0; r < 8; ++r) {
     const int i = i0 + threadIdx.y + 8 * r;  // rs (a symmetric factorisation's row scale, <= 2^10) is 0 beyond n
     tile[threadIdx.x][threadIdx.y + 8 * r] = scaled_float(x[r], e) * (rs ? rs[i] : 1.f);
   }
-  __syncthreads();
+  // with bflags: the block's 32 columns of Rt16 lie in one 256-row tile of the correction
+  // GEMM's B and its 64 rows in one K block (tc::GemmArgs::bflags)
+  if (__syncthreads_or(nonzero) && bflags && threadIdx.x == 0 && threadIdx.y == 0)
+    bflags[(int64_t)(j0 / 256) * ((np / 64 + 31) / 32 * 32) + i0 / 64] = 1;
   // warp w writes columns j0 + w + 8 c, lane l the rows i0 + 2 l, i0 + 2 l + 1
   const int ii = i0 + 2 * threadIdx.x;
 #pragma unroll
@@ -1396,6 +1403,7 @@ struct Buffers {
   int* rowexp;                   // np
   uint8_t* flags;                // the slices' non-zero 256 x 64 blocks (SliceFlags)
   uint8_t* aflags;               // A16's non-zero 256 x 64 blocks (the first Newton-Schulz product)
+  uint8_t* bflags;               // Rt16's non-zero 256 x 64 blocks (the first sweep's correction)
   float* Dbuf;                   // np x mp, correction M R before rounding
   unsigned int* dcolmax;         // mp, its column maxima (float bits)
   __nv_bfloat16* Bq;             // mp x np, the rounded correction, transposed
@@ -1440,6 +1448,7 @@ void plan(const Layout& L, Take&& t) {
   t.template take<float>((size_t)L.np);                           // sfout
   t.template take<uint8_t>(slice_flag_bytes(L.np));               // slice flags
   t.template take<uint8_t>(a16_flag_bytes(L.np));                 // A16 flags
+  t.template take<uint8_t>(rt_flag_bytes(L.mp, L.np));            // Rt16 flags
 }
 
 // The solver's status words in the context scratch (ints), laid out so that one copy
@@ -1529,6 +1538,7 @@ struct Solver {
     b.sfout = cv.take<float>((size_t)L.np);
     b.flags = cv.take<uint8_t>(slice_flag_bytes(L.np));
     b.aflags = cv.take<uint8_t>(a16_flag_bytes(L.np));
+    b.bflags = cv.take<uint8_t>(rt_flag_bytes(L.mp, L.np));
     err = ctx->d_scratch + kStatus;
     RG_CUDA_TRY(ctx, cudaMemsetAsync(err, 0, 6 * sizeof(int), s));  // error words and the GEMM's
     return RG_OK;
@@ -1694,13 +1704,19 @@ struct Solver {
       if (L.m <= kNarrow)
         scaled_transpose16_narrow<T16><<<nb, 256, 0, s>>>(src, L.mp, L.n, L.m, L.np, L.mp, b.colmax, Rt, b.colscale,
                                                           g, rc, b.dcolmax, rs_in);
-      else
+      else {
+        // the first sweep's right-hand side keeps F's zero blocks (the REFs' E = [F diag(eps) |
+        // F_inf]): its correction GEMM skips them; the residuals after it are dense
+        if (first) RG_CUDA_TRY(ctx, cudaMemsetAsync(b.bflags, 0, rt_flag_bytes(L.mp, L.np), s));
         scaled_transpose16<T16><<<tg, dim3(32, 8), 0, s>>>(src, L.mp, L.n, L.m, L.np, L.mp, b.colmax, Rt,
-                                                            b.colscale, g, rc, b.dcolmax, rs_in);
+                                                            b.colscale, g, rc, b.dcolmax, rs_in,
+                                                            first ? b.bflags : nullptr);
+      }
       ++ctx->launches;
       RG_CUDA_TRY(ctx, cudaGetLastError());
       st = tc::gemm(ctx, bf16, minv ? minv : b.X16[cur], L.np, Rt, L.np, L.n, L.m, L.np,
-                    tc::EpiCorrection{b.Dbuf, L.mp, b.colscale, b.dcolmax, err + 1, rs_out}, s, skip);
+                    tc::EpiCorrection{b.Dbuf, L.mp, b.colscale, b.dcolmax, err + 1, rs_out}, s, skip, false,
+                    nullptr, (first && L.m > kNarrow) ? b.bflags : nullptr);
       if (st != RG_OK) return st;
     }
     if (L.m <= kNarrow)

@@ -364,9 +364,12 @@ struct GemmArgs {
   // diagonal are computed, the epilogue writing each off-diagonal one for its transpose too
   int sym = 0;
   // Block flags of A (CTA-pair kernel only; null: every block): aflags[tile ceil(K / BK / 32) 32
-  // + kb] != 0 when A's 256-row tile `tile` has a non-zero entry in K block kb. With flags the
-  // leader CTAs add the K blocks they execute to *level_log (kernel timer), else nothing.
+  // + kb] != 0 when A's 256-row tile `tile` has a non-zero entry in K block kb; bflags the same
+  // for B's 256-row tiles (the product's 256-column tiles). A block is multiplied when neither
+  // flag says zero. With flags the leader CTAs add the K blocks they execute to *level_log
+  // (kernel timer), else nothing.
   const uint8_t* aflags = nullptr;
+  const uint8_t* bflags = nullptr;
   int* level_log = nullptr;
 };
 
@@ -589,18 +592,21 @@ __global__ void __launch_bounds__(kThreads, 1) __cluster_dims__(2, 1, 1)
   // pair's 256 rows of A hold a non-zero (both CTAs read the same flags; at least one block
   // is kept, so that the accumulator is written)
   const int kwords = (kb_total + 31) / 32;
-  const bool use_flags = args.aflags != nullptr && kwords <= kGemmMaxKWords;
+  const bool use_flags = (args.aflags != nullptr || args.bflags != nullptr) && kwords <= kGemmMaxKWords;
+  // the 32 flags of word w of a flag row as bits
+  auto flag_bits = [&](const uint8_t* row, int w) -> uint32_t {
+    const uint4* fp = reinterpret_cast<const uint4*>(row + (int64_t)w * 32);
+    const uint4 f0 = __ldg(fp), f1 = __ldg(fp + 1);
+    const uint32_t fw[8] = {f0.x, f0.y, f0.z, f0.w, f1.x, f1.y, f1.z, f1.w};
+    uint32_t bits = 0u;
+#pragma unroll
+    for (int q = 0; q < 32; ++q) bits |= ((fw[q >> 2] >> (8 * (q & 3))) & 0xffu) ? (1u << q) : 0u;
+    return bits;
+  };
   for (int w = threadIdx.x; w < kwords && w < kGemmMaxKWords; w += blockDim.x) {
     uint32_t m = kb_total - 32 * w >= 32 ? ~0u : ((1u << (kb_total - 32 * w)) - 1u);
-    if (use_flags) {
-      const uint4* fp = reinterpret_cast<const uint4*>(args.aflags + ((int64_t)tile_m * kwords + w) * 32);
-      const uint4 f0 = __ldg(fp), f1 = __ldg(fp + 1);
-      const uint32_t fw[8] = {f0.x, f0.y, f0.z, f0.w, f1.x, f1.y, f1.z, f1.w};
-      uint32_t bits = 0u;
-#pragma unroll
-      for (int q = 0; q < 32; ++q) bits |= ((fw[q >> 2] >> (8 * (q & 3))) & 0xffu) ? (1u << q) : 0u;
-      m &= bits;
-    }
+    if (use_flags && args.aflags) m &= flag_bits(args.aflags + (int64_t)tile_m * kwords * 32, w);
+    if (use_flags && args.bflags) m &= flag_bits(args.bflags + (int64_t)tile_n * kwords * 32, w);
     s_kmask[w] = m;
   }
 
@@ -1220,12 +1226,13 @@ constexpr size_t exact_pair_smem_bytes() {
 // where the tiles are square only those on and above the diagonal are computed and the
 // epilogue writes the off-diagonal ones for their transposes too (the Newton-Schulz epilogues
 // with their own `sym` set), else the whole product is computed.
-// aflags (optional): A's block flags, [ceil(M / 256)][ceil(K / 64 / 32) 32] bytes (GemmArgs);
-// the CTA-pair kernel skips A's all-zero K blocks (the others ignore the flags).
+// aflags, bflags (optional): A's and B's block flags, [ceil(M / 256)] and [ceil(N / 256)] rows of
+// ceil(K / 64 / 32) 32 bytes (GemmArgs); the CTA-pair kernel skips the K blocks where either
+// operand's tile is all zero (the others ignore the flags).
 template <class Epi>
 rg_status gemm(rg_ctx* ctx, bool bf16, const void* A, int64_t lda, const void* B, int64_t ldb, int M, int N, int K,
                const Epi& epi, cudaStream_t s, const int* skip = nullptr, bool sym = false,
-               const uint8_t* aflags = nullptr);
+               const uint8_t* aflags = nullptr, const uint8_t* bflags = nullptr);
 
 // C (fp32, ldc) = alpha * A B^T + beta * C with A [M x K] (lda), B [N x K] (ldb), 16-bit
 // K-major operands (bf16 when `bf16`, else fp16). lda, ldb: multiples of 8 elements;
