@@ -284,11 +284,19 @@ rg_status rg_counts_to_F(rg_ctx* ctx, int32_t n, const int64_t* counts_d, const 
  *       i.e. scales row i to sum Omega_i.
  * It stops after the first iteration whose reciprocity defect of the previous
  * iterate and closure defect after step (1) are both <= tol * max_i Omega_i.
+ * Arithmetic: the first iteration in fp64. The N x N block is symmetric after it, so every
+ * later iteration updates the entries on and above the diagonal in fp64 (the sum of the
+ * two halved row scales carries the fp64 addition's bits), accumulates the row sums exactly
+ * in 64-bit fixed point (to 2^-62 of each row's bound) and takes the stop rule's
+ * reciprocity defect in fp32; tile pairs that are zero after the first iteration stay zero
+ * and are skipped. A negative entry keeps every iteration in fp64 on both triangles.
  *   omega_d   device fp64 [n]: Omega_i (A_i for view factors, eps_i A_i for REFs)
  *   F_d       device fp64 [n][n+1], in: F, out: enforced F
  *   iters_out_h  host int32 (may be NULL): iterations performed
  * Rows with a zero sum are left unchanged. Errors: RG_ERR_NOT_CONVERGED (after
- * maxit iterations; F_d holds the last iterate), RG_ERR_NUMERIC, RG_ERR_ARG. */
+ * maxit iterations; F_d holds the last iterate), RG_ERR_NUMERIC (a non-finite row sum, or
+ * a fixed-point term outside its bound, which the bound's construction rules out),
+ * RG_ERR_ARG. */
 rg_status rg_enforce_iterative(rg_ctx* ctx, int32_t n, const double* omega_d, double* F_d, double tol,
                                int32_t maxit, int32_t* iters_out_h, void* stream);
 
@@ -316,10 +324,11 @@ rg_status rg_kappa(rg_ctx* ctx, int32_t n, int32_t mode, const double* F_d, cons
 /* rg_enforce_iterative with per-pair weights in step (1) (Eq. 3.20):
  *   eta-hat_ij = kappa_ij eta_ij + (1 - kappa_ij) eta_ji,
  * kappa_d device fp64 [n][n] as rg_kappa writes it (the thesis combines the
- * fractional-variance weights with the open-system closure, Sec. 3.5.5). With every
- * kappa_ij = 1/2 the result is bit-identical to rg_enforce_iterative. The same stop
- * rule, arguments and errors as rg_enforce_iterative. One iteration reads kappa once
- * more than the unweighted enforcer (24 instead of 16 bytes per matrix entry). */
+ * fractional-variance weights with the open-system closure, Sec. 3.5.5). Every iteration
+ * runs in fp64 on both triangles; with every kappa_ij = 1/2 the iterates are those of
+ * rg_enforce_iterative up to rounding. The same stop rule, arguments and errors as
+ * rg_enforce_iterative. One iteration reads kappa once more than the first iteration of
+ * the unweighted enforcer (24 instead of 16 bytes per matrix entry). */
 rg_status rg_enforce_iterative_kappa(rg_ctx* ctx, int32_t n, const double* omega_d, const double* kappa_d,
                                      double* F_d, double tol, int32_t maxit, int32_t* iters_out_h, void* stream);
 
