@@ -1128,8 +1128,10 @@ __global__ void __launch_bounds__(exact_threads(256), 1) __cluster_dims__(2, 1, 
           }
         }
         if (flagged && args.level_log) atomicAdd(args.level_log, t);
-        umma_commit_pair_local(drain);
-        mbar_wait(drain, 0);
+        if (t > 0) {  // a tile without flagged blocks issued no MMA: nothing to wait for
+          umma_commit_pair_local(drain);
+          mbar_wait(drain, 0);
+        }
       } else {
         // ---------------- relay of this CTA's full stages to the even CTA
         const uint32_t leader_full = mapa_shared(smem_u32(full), 0);
